@@ -1,0 +1,438 @@
+"""FP64 oracle of the lunar nanosecond-pulse hot path (arXiv:1612.06592).
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring.  Every function below
+cites the passage of the paper it follows (section and paragraph), and where
+the paper is silent it states the reading taken.  Nothing here is blocked,
+fused or reordered for speed; every step is its plain definition in float64.
+
+Notation (the paper's and the pipeline's):
+  S stations, P polarisations, K selected subbands (contiguous, starting at
+  bin ``first_bin`` of the 512 bins of a 1024-point polyphase filter bank),
+  B beams, Tr STEC trials, F frames per block, M = 1024, 16 taps, fs = 200 MHz.
+  A *stream* is one (beam, STEC trial, polarisation); its index is
+  j = (b * Tr + t) * P + pol.
+
+Parity pins for everything here live in ``tests/test_oracle_pins.py``.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "FS_HZ", "M", "NBINS", "TAPS", "NU0_HZ", "C_LIGHT", "KAPPA", "TECU",
+    "sky_frequencies", "geometric_weights", "dispersion_coefficient_hz",
+    "dedispersion_cycles", "dedispersion_weights", "beamform",
+    "bessel_i0", "prototype_filter", "synthesis_filter", "fft_radix2",
+    "ippf", "parseval_power", "update_sigma2", "find_triggers",
+    "Pipeline", "stream_window", "brute_force_stream",
+]
+
+# Sec. 2: antennas are sampled every 5 ns  ->  fs = 200 MHz.
+FS_HZ = 200e6
+# Sec. 2: the PPF lowers the time resolution from 5 ns to "about 5 us"; a
+# 1024-point filter bank gives 1024 / 200 MHz = 5.12 us frames and 512 bins.
+M = 1024
+NBINS = M // 2
+# Synthesis filter length in frames (16 taps, Kaiser-windowed sinc, beta = 9).
+TAPS = 16
+# Reading (paper silent): the HBA band 110-240 MHz is sampled in the second
+# Nyquist zone, spectrum already un-flipped, so bin b has sky frequency
+# fs/2 + b * fs / M.
+NU0_HZ = FS_HZ / 2
+C_LIGHT = 299792458.0
+# Dispersion constant e^2 / (8 pi^2 eps0 m_e) in m^3 s^-2 (pinned against
+# CODATA in the tests) and one TEC unit in electrons per m^2.
+KAPPA = 40.308
+TECU = 1e16
+
+
+# --------------------------------------------------------------------------
+# Frequencies and phase weights (Sec. 3)
+# --------------------------------------------------------------------------
+
+def sky_frequencies(first_bin: int, n_subbands: int) -> np.ndarray:
+    """Sky frequency [Hz] of each selected subband (Sec. 2, sampling and PPF).
+
+    Reading: bin b sits at fs/2 + b * fs/M (second Nyquist zone, un-flipped).
+    """
+    b = np.arange(first_bin, first_bin + n_subbands, dtype=np.float64)
+    return NU0_HZ + b * (FS_HZ / M)
+
+
+def geometric_weights(nu_hz: np.ndarray, station_enu_m: np.ndarray,
+                      beam_dir: np.ndarray) -> np.ndarray:
+    """Tied-array beam weights w[k, b, s] (Sec. 3, first paragraph).
+
+    The paper: each station signal is summed "with a complex weight given by
+    the station position and the beam direction".  Reading: a plane wave from
+    unit direction s_b reaches station s (ENU position r_s) earlier by
+    tau = r_s . s_b / c than the array origin, which multiplies that station's
+    subband value by exp(+2 pi i nu tau); the weight undoes it:
+        w[k, b, s] = exp(-2 pi i nu_k (r_s . s_b) / c).
+    """
+    nu = np.asarray(nu_hz, dtype=np.float64)
+    r = np.asarray(station_enu_m, dtype=np.float64)          # [S, 3]
+    d = np.asarray(beam_dir, dtype=np.float64)               # [B, 3]
+    tau = (d @ r.T) / C_LIGHT                                 # [B, S] seconds
+    cycles = nu[:, None, None] * tau[None, :, :]              # [K, B, S]
+    return np.exp(-2j * np.pi * cycles)
+
+
+def dispersion_coefficient_hz(tec_tecu) -> np.ndarray:
+    """A = kappa * STEC / c in Hz; the ionospheric group delay is A / nu^2.
+
+    Sec. 1 and Sec. 3: the signal is dispersed in the ionosphere and the
+    correction depends on the slant electron content (STEC); the paper gives
+    no formula, the standard cold-plasma one is used.
+    """
+    return KAPPA * np.asarray(tec_tecu, dtype=np.float64) * TECU / C_LIGHT
+
+
+def dedispersion_cycles(nu_hz, tec_tecu, nu_ref_hz: float) -> np.ndarray:
+    """De-dispersion phase in cycles, [K, Tr] (Sec. 3, third paragraph).
+
+    The ionosphere multiplies the spectrum by H(nu) = exp(+2 pi i A / nu)
+    (group delay A / nu^2).  Reading of the paper's "complex weight depending
+    on the current electron content": remove that phase relative to the
+    reference frequency nu_ref, keeping the pulse at the delay it has at nu_ref:
+        phi(nu) = A * (1/nu - 2/nu_ref + nu / nu_ref^2)   [cycles].
+    Written out exactly in this expanded form; the tests pin it against the
+    factored form A (nu - nu_ref)^2 / (nu nu_ref^2) in 40-digit arithmetic.
+    """
+    nu = np.asarray(nu_hz, dtype=np.float64)[:, None]
+    a = dispersion_coefficient_hz(tec_tecu)[None, :]
+    return a * (1.0 / nu - 2.0 / nu_ref_hz + nu / (nu_ref_hz * nu_ref_hz))
+
+
+def dedispersion_weights(nu_hz, tec_tecu, nu_ref_hz: float) -> np.ndarray:
+    """D[k, t] = exp(-2 pi i phi(nu_k, STEC_t)) (Sec. 3, third paragraph)."""
+    return np.exp(-2j * np.pi * dedispersion_cycles(nu_hz, tec_tecu, nu_ref_hz))
+
+
+def beamform(x: np.ndarray, w: np.ndarray, d: np.ndarray) -> np.ndarray:
+    """Beamformed, de-dispersed subband data (Sec. 3, first and third paragraphs).
+
+    x: complex [P, K, F, S] station subband samples.
+    w: complex [K, B, S] beam weights.   d: complex [K, Tr] de-dispersion.
+    Returns complex [B, Tr, P, K, F] with
+        beam[b, t, p, k, m] = d[k, t] * sum_s w[k, b, s] * x[p, k, m, s]
+    evaluated as a direct sum over stations.
+    """
+    x = np.asarray(x, dtype=np.complex128)
+    P, K, F, S = x.shape
+    B = w.shape[1]
+    Tr = d.shape[1]
+    acc = np.zeros((B, P, K, F), dtype=np.complex128)
+    for s in range(S):
+        # acc[b, p, k, m] += w[k, b, s] * x[p, k, m, s]
+        acc += w[:, :, s].T[:, None, :, None] * x[None, :, :, :, s]
+    out = acc[:, None, :, :, :] * d.T[None, :, None, :, None]
+    assert out.shape == (B, Tr, P, K, F)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Prototype filter (inverse PPF, Sec. 3 second paragraph; 16-tap synthesis)
+# --------------------------------------------------------------------------
+
+def bessel_i0(x) -> np.ndarray:
+    """Modified Bessel function I0 by its power series sum_k ((x/2)^k / k!)^2."""
+    x = np.asarray(x, dtype=np.float64)
+    term = np.ones_like(x)
+    total = np.ones_like(x)
+    q = (x / 2.0) ** 2
+    for k in range(1, 200):
+        term = term * q / (k * k)
+        total = total + term
+        if np.all(term <= 1e-18 * total):
+            break
+    return total
+
+
+def prototype_filter(m: int = M, taps: int = TAPS, beta: float = 9.0) -> np.ndarray:
+    """Kaiser-windowed sinc prototype h[n], n < L = m * taps, sum(h) = 1.
+
+    h[n] = sinc((n - (L-1)/2) / m) * I0(beta sqrt(1 - (2n/(L-1) - 1)^2)) / I0(beta),
+    sinc(x) = sin(pi x) / (pi x).  Reading of "cutoff one subband": the sinc
+    has its zeros every m samples, i.e. -6 dB at +-half a subband.
+    """
+    L = m * taps
+    n = np.arange(L, dtype=np.float64)
+    xs = (n - (L - 1) / 2.0) / m
+    sinc = np.empty_like(xs)
+    nz = xs != 0.0
+    sinc[nz] = np.sin(np.pi * xs[nz]) / (np.pi * xs[nz])
+    sinc[~nz] = 1.0
+    arg = 1.0 - (2.0 * n / (L - 1) - 1.0) ** 2
+    window = bessel_i0(beta * np.sqrt(np.maximum(arg, 0.0))) / bessel_i0(beta)
+    h = sinc * window
+    return h / np.sum(h)
+
+
+def synthesis_filter(m: int = M, taps: int = TAPS, beta: float = 9.0) -> np.ndarray:
+    """Synthesis filter g = m^2 h: unit round-trip gain for subband-centred tones."""
+    return (m * m) * prototype_filter(m, taps, beta)
+
+
+# --------------------------------------------------------------------------
+# FFT (radix-2 Cooley-Tukey, the algorithm the paper's FLOP count assumes)
+# --------------------------------------------------------------------------
+
+def _bit_reverse_indices(n: int) -> np.ndarray:
+    bits = n.bit_length() - 1
+    idx = np.arange(n)
+    rev = np.zeros(n, dtype=np.int64)
+    for b in range(bits):
+        rev |= ((idx >> b) & 1) << (bits - 1 - b)
+    return rev
+
+
+def fft_radix2(x, sign: int) -> np.ndarray:
+    """Unnormalised DFT along the last axis: X[k] = sum_n x[n] exp(sign 2 pi i k n / N).
+
+    Iterative radix-2 decimation in time (Sec. 3 counts 5 N log2 N FLOP for
+    it).  sign = -1 is the forward transform, sign = +1 the inverse without
+    the 1/N.
+    """
+    a = np.asarray(x, dtype=np.complex128)
+    n = a.shape[-1]
+    if n & (n - 1) or n == 0:
+        raise ValueError("length must be a power of two")
+    a = a[..., _bit_reverse_indices(n)]
+    lead = a.shape[:-1]
+    span = 1
+    while span < n:
+        tw = np.exp(sign * 2j * np.pi * np.arange(span) / (2 * span))
+        a = a.reshape(lead + (n // (2 * span), 2, span))
+        even = a[..., 0, :]
+        odd = a[..., 1, :] * tw
+        a = np.stack([even + odd, even - odd], axis=-2).reshape(lead + (n,))
+        span *= 2
+    return a
+
+
+# --------------------------------------------------------------------------
+# Inverse polyphase filter bank (Sec. 2 and Sec. 3 second paragraph)
+# --------------------------------------------------------------------------
+
+def ippf(frames_ext: np.ndarray, first_bin: int, g: np.ndarray) -> np.ndarray:
+    """Synthesis of the 200 MHz analytic time series from subband frames.
+
+    frames_ext: complex [..., F + 15, K]: 15 history frames, then F new ones.
+    Returns u: complex [..., F, M], u[i, p] is sample n = (m - 15) M + p of the
+    output, m the frame of new row i.
+
+    Step 1 (the paper's inverse FFT): per frame, place 2 * beam in the
+    selected bins (all other bins, DC and Nyquist zero) and take the 1024-point
+    inverse DFT with 1/M: z_m[p] = (1/M) sum_k 2 c_m[k] exp(+2 pi i k p / M);
+    its real part is the PPF branch signal, the imaginary part its Hilbert pair.
+    Step 2 (replaces the paper's sparse LSMR solve by the FIR synthesis):
+        u_m[p] = sum_{t=0}^{15} g[t M + p] * z_{m-t}[p].
+    """
+    frames_ext = np.asarray(frames_ext, dtype=np.complex128)
+    nfr, K = frames_ext.shape[-2], frames_ext.shape[-1]
+    taps = g.shape[0] // M
+    F = nfr - (taps - 1)
+    if F < 0:
+        raise ValueError("need at least taps-1 history frames")
+    if first_bin < 1 or first_bin + K > NBINS:
+        raise ValueError("selected bins must avoid DC and Nyquist")
+    c = np.zeros(frames_ext.shape[:-1] + (M,), dtype=np.complex128)
+    c[..., first_bin:first_bin + K] = 2.0 * frames_ext
+    z = fft_radix2(c, +1) / M
+    u = np.zeros(frames_ext.shape[:-2] + (F, M), dtype=np.complex128)
+    for t in range(taps):
+        u += g[t * M:(t + 1) * M] * z[..., taps - 1 - t:taps - 1 - t + F, :]
+    return u
+
+
+# --------------------------------------------------------------------------
+# Noise level and trigger (Sec. 1 and Sec. 2: trigger on the pulse amplitude)
+# --------------------------------------------------------------------------
+
+def parseval_power(frames_new: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Block estimate of the output mean square <y^2> per stream.
+
+    frames_new: complex [..., F, K] beam frames of this block.
+    Reading (paper silent on the noise estimate): with independent bins of
+    power P_k, the analytic output has E|u|^2 = 4 sum(g^2) sum_k P_k / M^3 and
+    y = Re u half of that, so
+        Pi = (2 sum(g^2) / M^3) * (1/F) * sum_{m,k} |beam_m[k]|^2.
+    """
+    f = np.asarray(frames_new, dtype=np.complex128)
+    F = f.shape[-2]
+    g2 = float(np.sum(np.asarray(g, dtype=np.float64) ** 2))
+    power = np.sum(np.abs(f) ** 2, axis=(-2, -1)) / F
+    return (2.0 * g2 / float(M) ** 3) * power
+
+
+def update_sigma2(prev_sigma2, block_power, alpha: float, first_block: bool):
+    """Running noise variance: s2_0 = Pi_0, s2_j = (1 - alpha) s2_{j-1} + alpha Pi_j."""
+    if first_block:
+        return np.asarray(block_power, dtype=np.float64).copy()
+    return (1.0 - alpha) * np.asarray(prev_sigma2) + alpha * np.asarray(block_power)
+
+
+def find_triggers(env: np.ndarray, theta: float, n_first: int):
+    """Samples with envelope strictly above theta and n >= 0.
+
+    env: [N] envelope of one stream, env[i] at sample n_first + i.
+    Returns (n, env) arrays.  The envelope of Gaussian noise is Rayleigh with
+    scale sigma_y, so theta = k sigma_y gives a rate exp(-k^2/2) per sample.
+    """
+    env = np.asarray(env)
+    n = n_first + np.arange(env.shape[0], dtype=np.int64)
+    hit = (env > theta) & (n >= 0)
+    return n[hit], env[hit]
+
+
+# --------------------------------------------------------------------------
+# Block pipeline with state carried across blocks
+# --------------------------------------------------------------------------
+
+def _as_complex(x: np.ndarray) -> np.ndarray:
+    """Integer station samples [..., 2] (re, im) -> complex128 [...]."""
+    x = np.asarray(x)
+    if np.iscomplexobj(x):
+        return x.astype(np.complex128)
+    return x[..., 0].astype(np.float64) + 1j * x[..., 1].astype(np.float64)
+
+
+@dataclass
+class Pipeline:
+    """The whole hot path, block after block, in float64.
+
+    State carried between blocks: the last 15 beam frames of every stream
+    (synthesis history; frames before the stream start are zero), the running
+    noise variance and the block counter.
+    """
+    stations: int
+    pols: int
+    subbands: int
+    beams: int
+    tec_trials: int
+    block_len: int
+    first_bin: int
+    station_enu: np.ndarray
+    beam_dir: np.ndarray
+    tec: np.ndarray
+    nu_ref_hz: float | None = None
+    k_sigma: float = 6.0
+    sigma_alpha: float = 0.25
+    beta: float = 9.0
+    keep_timeseries: bool = True
+    # state
+    block_index: int = 0
+    history: np.ndarray | None = field(default=None, repr=False)
+    sigma2: np.ndarray | None = None
+
+    def __post_init__(self):
+        self.nu = sky_frequencies(self.first_bin, self.subbands)
+        if self.nu_ref_hz is None:
+            self.nu_ref_hz = 0.5 * (self.nu[0] + self.nu[-1])
+        self.w = geometric_weights(self.nu, self.station_enu, self.beam_dir)
+        self.d = dedispersion_weights(self.nu, np.asarray(self.tec), self.nu_ref_hz)
+        self.g = synthesis_filter(M, TAPS, self.beta)
+        J = self.beams * self.tec_trials * self.pols
+        self.history = np.zeros((J, TAPS - 1, self.subbands), dtype=np.complex128)
+
+    @property
+    def n_streams(self) -> int:
+        return self.beams * self.tec_trials * self.pols
+
+    def stream_index(self, b: int, t: int, p: int) -> int:
+        return (b * self.tec_trials + t) * self.pols + p
+
+    def process_block(self, x):
+        """x: station block [P, K, F, S, 2] integers (or complex [P, K, F, S]).
+
+        Returns dict with beams [J, F, K], sigma [J], theta [J], n_first,
+        y/env [J, F*M] (if keep_timeseries) and triggers: list of
+        (n, beam, tec, pol, env, sigma) sorted by (beam, tec, pol, n).
+        """
+        xc = _as_complex(x)
+        P, K, F, S = xc.shape
+        assert (P, K, F, S) == (self.pols, self.subbands, self.block_len, self.stations)
+        bm = beamform(xc, self.w, self.d)                 # [B, Tr, P, K, F]
+        J = self.n_streams
+        frames = bm.reshape(J, K, F).transpose(0, 2, 1)   # [J, F, K]
+        pi = parseval_power(frames, self.g)
+        self.sigma2 = update_sigma2(self.sigma2, pi, self.sigma_alpha,
+                                    self.block_index == 0)
+        sigma = np.sqrt(self.sigma2)
+        theta = self.k_sigma * sigma
+        n_first = (self.block_index * F - (TAPS - 1)) * M
+        y = np.zeros((J, F * M)) if self.keep_timeseries else None
+        env_all = np.zeros((J, F * M)) if self.keep_timeseries else None
+        trig = []
+        new_history = np.empty_like(self.history)
+        for j in range(J):
+            ext = np.concatenate([self.history[j], frames[j]], axis=0)
+            u = ippf(ext, self.first_bin, self.g).reshape(F * M)
+            env = np.abs(u)
+            if self.keep_timeseries:
+                y[j] = u.real
+                env_all[j] = env
+            n_hit, e_hit = find_triggers(env, theta[j], n_first)
+            b, rem = divmod(j, self.tec_trials * self.pols)
+            t, p = divmod(rem, self.pols)
+            for n, e in zip(n_hit.tolist(), e_hit.tolist()):
+                trig.append((n, b, t, p, e, float(sigma[j])))
+            new_history[j] = ext[-(TAPS - 1):]
+        self.history = new_history
+        self.block_index += 1
+        trig.sort(key=lambda r: (r[1], r[2], r[3], r[0]))
+        return {"beams": frames, "block_power": pi, "sigma": sigma,
+                "theta": theta, "n_first": n_first, "y": y, "env": env_all,
+                "triggers": trig}
+
+
+def stream_window(x, w_bs: np.ndarray, d_kt: np.ndarray, pol: int,
+                  first_bin: int, g: np.ndarray, m0: int, m1: int):
+    """Output u of one stream for block frames [m0, m1), first block of a stream.
+
+    x: station block [P, K, F, S, 2] (or complex).  w_bs: complex [K, S] the
+    weights of the stream's beam; d_kt: complex [K] its de-dispersion column.
+    Frames before the block start are zero (stream start).  Evaluates the same
+    definitions as ``Pipeline`` on only the frames the window needs, so large
+    blocks can be checked at sampled places.  Returns u [m1 - m0, M] whose row
+    i is frame m0 + i, i.e. samples (m0 + i - 15) M + p.
+    """
+    xa = np.asarray(x)
+    lo = max(0, m0 - (TAPS - 1))
+    xc = _as_complex(xa[pol, :, lo:m1])                       # [K, n, S]
+    beam = np.einsum("ks,kns->kn", w_bs, xc) * d_kt[:, None]  # [K, n]
+    ext = np.zeros((m1 - m0 + TAPS - 1, w_bs.shape[0]), dtype=np.complex128)
+    ext[(lo - (m0 - (TAPS - 1))):] = beam.T
+    return ippf(ext, first_bin, g)
+
+
+def brute_force_stream(frames_ext: np.ndarray, first_bin: int, g: np.ndarray) -> np.ndarray:
+    """The synthesis written as one explicit double sum, for tiny inputs only.
+
+    u_m[p] = sum_t g[tM+p] (1/M) sum_k 2 c_{m-t}[k] exp(2 pi i (first_bin+k) p / M)
+    with no FFT and no vectorised reshapes: a check on ``ippf``.
+    """
+    frames_ext = np.asarray(frames_ext, dtype=np.complex128)
+    nfr, K = frames_ext.shape
+    taps = g.shape[0] // M
+    F = nfr - (taps - 1)
+    u = np.zeros((F, M), dtype=np.complex128)
+    for i in range(F):
+        m = i + taps - 1
+        for p in range(M):
+            acc = 0j
+            for t in range(taps):
+                row = frames_ext[m - t]
+                zsum = 0j
+                for k in range(K):
+                    zsum += 2.0 * row[k] * complex(
+                        math.cos(2 * math.pi * (first_bin + k) * p / M),
+                        math.sin(2 * math.pi * (first_bin + k) * p / M))
+                acc += g[t * M + p] * zsum / M
+            u[i, p] = acc
+    return u

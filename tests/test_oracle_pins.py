@@ -1,0 +1,354 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a brute-force
+sum, a library routine on a special case, a closed form, a physical constant, a
+statistical law, or a figure the paper prints.  A plausible slip in the oracle
+(a dropped factor 2, a wrong sign of a phase, a transposed tap index, an
+off-by-one frame) fails at least one of them.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- FFT ------
+
+@pytest.mark.parametrize("n", [2, 4, 8, 32, 256, 1024])
+def test_fft_matches_brute_force_dft(n):
+    rng = np.random.default_rng(n)
+    x = rng.normal(size=(3, n)) + 1j * rng.normal(size=(3, n))
+    k = np.arange(n)
+    for sign in (-1, +1):
+        mat = np.exp(sign * 2j * np.pi * np.outer(k, k) / n)
+        ref = x @ mat.T
+        got = O.fft_radix2(x, sign)
+        assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_fft_matches_library_fft():
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(5, 1024)) + 1j * rng.normal(size=(5, 1024))
+    np.testing.assert_allclose(O.fft_radix2(x, -1), np.fft.fft(x), rtol=0, atol=1e-9)
+    np.testing.assert_allclose(O.fft_radix2(x, +1) / 1024, np.fft.ifft(x), rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------- prototype filter ----
+
+def test_bessel_i0_matches_library():
+    from scipy.special import i0
+    xs = np.array([0.0, 0.1, 1.0, 4.5, 9.0, 20.0])
+    np.testing.assert_allclose(O.bessel_i0(xs), i0(xs), rtol=1e-13)
+
+
+def test_prototype_matches_kaiser_sinc_and_is_normalised():
+    h = O.prototype_filter()
+    L = O.M * O.TAPS
+    assert h.shape == (L,)
+    assert abs(h.sum() - 1.0) < 1e-13
+    np.testing.assert_allclose(h, h[::-1], rtol=1e-13, atol=1e-20)  # linear phase
+    n = np.arange(L)
+    lib = np.sinc((n - (L - 1) / 2) / O.M) * np.kaiser(L, 9.0)
+    np.testing.assert_allclose(h, lib / lib.sum(), rtol=1e-11, atol=1e-17)
+    np.testing.assert_allclose(O.synthesis_filter(), O.M ** 2 * h, rtol=1e-15)
+
+
+def _response(h, f_over_fs):
+    n = np.arange(h.size)
+    return np.array([np.sum(h * np.exp(-2j * np.pi * f * n)) for f in f_over_fs])
+
+
+def test_prototype_cutoff_is_one_subband():
+    """-6 dB at +-half a subband, >80 dB stopband from one subband away."""
+    h = O.prototype_filter()
+    df = 1.0 / O.M
+    r = np.abs(_response(h, [0.0, 0.5 * df, 0.25 * df, 1.0 * df, 1.5 * df, 3.0 * df]))
+    assert abs(r[0] - 1.0) < 1e-12
+    assert abs(r[1] - 0.5) < 5e-3
+    assert r[2] > 0.999
+    assert np.all(r[3:] < 1e-4)
+
+
+# ------------------------------------------------------- inverse PPF -------
+
+def test_ippf_matches_brute_force_tiny():
+    rng = np.random.default_rng(3)
+    g = O.synthesis_filter()
+    fr = rng.normal(size=(O.TAPS + 1, 3)) + 1j * rng.normal(size=(O.TAPS + 1, 3))
+    got = O.ippf(fr, 200, g)
+    ref = O.brute_force_stream(fr, 200, g)
+    assert got.shape == (2, O.M)
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def _tone_frames(freqs_hz, amps, phases, F, first_bin, K):
+    """Real multi-tone series through the generator's forward PPF (analysis side)."""
+    n_start = -(O.TAPS - 1) * O.M
+    n = np.arange(n_start, (F + 1) * O.M)
+    x = np.zeros(n.size)
+    for f, a, ph in zip(freqs_hz, amps, phases):
+        x += a * np.cos(2 * np.pi * f * n / O.FS_HZ + ph)
+    bins = np.arange(first_bin, first_bin + K)
+    fr = synth.forward_ppf(x, n_start, 0, F, bins, synth.analysis_filter())
+    return fr, x, n_start
+
+
+@pytest.mark.parametrize("offset", [0.0, 0.25, -0.25])
+def test_roundtrip_subband_centred_tones(offset):
+    """Forward PPF (generator) -> oracle IPPF returns the tones (<= 1e-3 rel RMS)."""
+    first_bin, K, F = 150, 8, 48
+    df = O.FS_HZ / O.M
+    freqs = [(first_bin + 2 + offset) * df, (first_bin + 5 + offset) * df]
+    fr, x, n_start = _tone_frames(freqs, [3.0, 1.5], [0.3, -1.1], F, first_bin, K)
+    u = O.ippf(fr, first_bin, O.synthesis_filter())          # frames 15..F-1
+    y = u.real.reshape(-1)
+    ref = x[-n_start:-n_start + y.size]                       # samples 0 .. (F-15)M
+    err = np.sqrt(np.mean((y - ref) ** 2) / np.mean(ref ** 2))
+    assert err < 1e-3, err
+
+
+def test_hilbert_envelope_of_tone_is_its_amplitude():
+    first_bin, K, F = 150, 8, 40
+    f = (first_bin + 3) * O.FS_HZ / O.M
+    fr, _, _ = _tone_frames([f], [2.5], [0.7], F, first_bin, K)
+    env = np.abs(O.ippf(fr, first_bin, O.synthesis_filter())).reshape(-1)
+    assert np.max(np.abs(env - 2.5)) < 2.5e-3
+
+
+def test_roundtrip_scales_with_factor_two_of_analytic_bins():
+    """A dropped factor 2 in the analytic IFFT halves the output: caught here."""
+    first_bin, K, F = 150, 4, 24
+    f = (first_bin + 1) * O.FS_HZ / O.M
+    fr, x, n_start = _tone_frames([f], [1.0], [0.0], F, first_bin, K)
+    y = O.ippf(fr, first_bin, O.synthesis_filter()).real.reshape(-1)
+    ref = x[-n_start:-n_start + y.size]
+    assert abs(np.std(y) / np.std(ref) - 1.0) < 1e-3
+
+
+# ------------------------------------------------------- beamforming -------
+
+def test_coherent_gain_equals_station_count():
+    """Plane wave from a beam direction sums to S times the wave (closed form)."""
+    S, K = 9, 5
+    enu = synth.station_positions(S, 11)
+    dirs = synth.hex_beam_directions(3)
+    nu = O.sky_frequencies(100, K)
+    rng = np.random.default_rng(2)
+    x0 = rng.normal(size=(K, 7)) + 1j * rng.normal(size=(K, 7))
+    b = 2
+    tau = enu @ dirs[b] / O.C_LIGHT                       # arrival advance [S]
+    # plane-wave arrival model: station s sees exp(+2 pi i nu tau_s) x0
+    x = x0[:, :, None] * np.exp(2j * np.pi * nu[:, None, None] * tau[None, None, :])
+    w = O.geometric_weights(nu, enu, dirs)
+    d = np.ones((K, 1), dtype=complex)
+    beam = O.beamform(x[None], w, d)[b, 0, 0]              # [K, 7]
+    np.testing.assert_allclose(beam, S * x0, rtol=1e-12, atol=1e-12)
+
+
+def test_two_station_off_beam_response():
+    """|1 + exp(i dphi)| = 2 |cos(dphi / 2)| for a source off the beam."""
+    enu = np.array([[0.0, 0.0, 0.0], [700.0, -300.0, 0.0]])
+    beam = synth.pointing_enu(180, 45)[None]
+    src = synth.pointing_enu(180.3, 45.2)
+    nu = O.sky_frequencies(200, 3)
+    tau = enu @ src / O.C_LIGHT
+    x = np.exp(2j * np.pi * nu[:, None] * tau[None, :])[:, None, :]   # [K, 1, S]
+    out = O.beamform(x[None], O.geometric_weights(nu, enu, beam), np.ones((3, 1)))
+    dphi = 2 * np.pi * nu * ((enu[1] - enu[0]) @ (src - beam[0])) / O.C_LIGHT
+    np.testing.assert_allclose(np.abs(out[0, 0, 0, :, 0]), 2 * np.abs(np.cos(dphi / 2)),
+                               rtol=1e-10)
+
+
+# ------------------------------------------------------- dispersion --------
+
+def test_kappa_from_codata():
+    from scipy.constants import e, epsilon_0, m_e
+    kappa = e ** 2 / (8 * np.pi ** 2 * epsilon_0 * m_e)
+    assert abs(kappa / O.KAPPA - 1) < 1e-4
+
+
+def test_dedispersion_phase_against_40_digit_factored_form():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    nu = O.sky_frequencies(12, 488)
+    tec = np.array([0.0, 5.0, 17.5, 40.0])
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    got = O.dedispersion_cycles(nu, tec, nu_ref)
+    assert np.all(got[:, 0] == 0.0)                     # TEC = 0 -> D == 1
+    for ki in (0, 100, 243, 487):
+        for ti in range(1, 4):
+            a = mpmath.mpf(O.KAPPA) * mpmath.mpf(tec[ti]) * mpmath.mpf(O.TECU) / mpmath.mpf(O.C_LIGHT)
+            v = mpmath.mpf(nu[ki])
+            r = mpmath.mpf(nu_ref)
+            ref = a * (v - r) ** 2 / (v * r * r)
+            assert abs(float(ref) - got[ki, ti]) < 1e-9
+
+
+def _single_pulse_block(tec, F=96, first_bin=60, K=192, S=1, beam_dir=None):
+    w = synth.Workload("pin", S, 1, K, first_bin, 1, (tec,), F, "int16", 1.0)
+    h = synth.analysis_filter()
+    n0 = 40 * O.M + 100
+    p = synth.Pulse(n0, 5.0e4, tec, 0.0, 0)
+    m_lo, m_hi, xs = synth.pulse_subbands(p, w, h, 0)
+    frames = np.zeros((F, K), dtype=complex)
+    frames[m_lo:m_hi] = xs
+    return frames, n0
+
+
+def test_group_delay_follows_inverse_square_law():
+    """Per-subband-group arrival times of a dispersed pulse fit t0 + A / nu^2."""
+    tec = 30.0
+    frames, n0 = _single_pulse_block(tec)
+    g = O.synthesis_filter()
+    first_bin, K = 60, 192
+    nu = O.sky_frequencies(first_bin, K)
+    t_peak, nu_c = [], []
+    for grp in range(8):
+        sel = slice(grp * 24, (grp + 1) * 24)
+        fr = np.zeros_like(frames)
+        fr[:, sel] = frames[:, sel]
+        ext = np.concatenate([np.zeros((15, K)), fr])
+        env = np.abs(O.ippf(ext, first_bin, g)).reshape(-1)
+        i = int(np.argmax(env))
+        # parabolic refinement of the envelope peak
+        a, b, c = env[i - 1], env[i], env[i + 1]
+        # output row 0 is block frame 0, i.e. sample n = -15 M
+        t_peak.append((i - 15 * O.M + 0.5 * (a - c) / (a - 2 * b + c)) / O.FS_HZ)
+        nu_c.append(np.mean(nu[sel]))
+    nu_c = np.array(nu_c)
+    coef = np.polyfit(1.0 / nu_c ** 2, np.array(t_peak), 1)
+    a_fit = coef[0]
+    a_true = O.dispersion_coefficient_hz(tec)
+    assert abs(a_fit / a_true - 1) < 0.02
+    assert abs(coef[1] * O.FS_HZ - n0) < 3.0                  # undispersed time
+
+
+def test_dedispersion_at_true_tec_recovers_the_pulse():
+    tec = 25.0
+    first_bin, K = 60, 192
+    frames, n0 = _single_pulse_block(tec)
+    g = O.synthesis_filter()
+    nu = O.sky_frequencies(first_bin, K)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    ext = lambda f: np.concatenate([np.zeros((15, K)), f])
+    peaks = {}
+    for trial in (0.0, tec - 5.0, tec, tec + 5.0):
+        d = O.dedispersion_weights(nu, [trial], nu_ref)[:, 0]
+        env = np.abs(O.ippf(ext(frames * d[None, :]), first_bin, g)).reshape(-1)
+        peaks[trial] = (env.max(), int(np.argmax(env)) - 15 * O.M)
+    # undispersed reference pulse through the same path
+    ref, _ = _single_pulse_block(0.0)
+    env0 = np.abs(O.ippf(ext(ref), first_bin, g)).reshape(-1)
+    best = peaks[tec][0]
+    # a phase fixed at each subband centre leaves the in-subband dispersion
+    # slope: about 14 % of the peak is lost at 25 TECU over 112-149 MHz
+    assert best > 0.8 * env0.max()
+    assert best > 1.5 * peaks[0.0][0]
+    assert best > peaks[tec - 5.0][0] and best > peaks[tec + 5.0][0]
+    # the de-dispersed pulse sits at the reference-frequency delay
+    tau_ref = O.dispersion_coefficient_hz(tec) / nu_ref ** 2
+    assert abs(peaks[tec][1] - (n0 + tau_ref * O.FS_HZ)) < 30
+
+
+# ------------------------------------------------------- noise / trigger ---
+
+@pytest.fixture(scope="module")
+def noise_run():
+    """White complex Gaussian station noise (float) through the whole oracle."""
+    S, K, F, first_bin, sig = 4, 64, 384, 100, 3.0
+    rng = np.random.default_rng(5)
+    x = (rng.normal(scale=sig, size=(1, K, F, S)) + 1j * rng.normal(scale=sig, size=(1, K, F, S)))
+    pipe = O.Pipeline(S, 1, K, 1, 1, F, first_bin, synth.station_positions(S, 1),
+                      synth.pointing_enu()[None], np.array([12.0]))
+    out = pipe.process_block(x)
+    g2 = float(np.sum(O.synthesis_filter() ** 2))
+    sigma_y2 = 4 * K * S * sig ** 2 * g2 / O.M ** 3
+    return out, sigma_y2
+
+
+def test_output_variance_matches_closed_form(noise_run):
+    out, sigma_y2 = noise_run
+    y = out["y"][0, 15 * O.M:]
+    assert abs(np.mean(y ** 2) / sigma_y2 - 1) < 0.04
+    # the block statistic is an estimate of the same quantity
+    assert abs(out["block_power"][0] / sigma_y2 - 1) < 0.03
+
+
+@pytest.mark.parametrize("k", [1.5, 2.0, 2.5])
+def test_rayleigh_exceedance(noise_run, k):
+    out, sigma_y2 = noise_run
+    env = out["env"][0, 15 * O.M:]
+    frac = np.mean(env > k * np.sqrt(sigma_y2))
+    assert abs(frac / math.exp(-k * k / 2) - 1) < 0.08
+
+
+def test_trigger_is_strict_and_skips_negative_samples():
+    env = np.array([9.0, 6.0, 6.0000001, 7.0, 2.0])
+    n, e = O.find_triggers(env, 6.0, -1)     # samples -1 .. 3
+    assert n.tolist() == [1, 2]
+    np.testing.assert_array_equal(e, [6.0000001, 7.0])
+
+
+def test_sigma_running_update():
+    s = O.update_sigma2(None, np.array([4.0]), 0.25, True)
+    assert s.tolist() == [4.0]
+    s = O.update_sigma2(s, np.array([8.0]), 0.25, False)
+    assert s.tolist() == [5.0]
+
+
+# ------------------------------------------------------- block state -------
+
+def test_two_blocks_equal_one_long_block():
+    S, K, F, first_bin = 3, 6, 40, 300
+    rng = np.random.default_rng(9)
+    x = rng.integers(-20, 20, size=(2, K, 2 * F, S, 2)).astype(np.int16)
+    enu = synth.station_positions(S, 4)
+    dirs = synth.hex_beam_directions(2)
+    tec = np.array([3.0, 9.0])
+    long = O.Pipeline(S, 2, K, 2, 2, 2 * F, first_bin, enu, dirs, tec).process_block(x)
+    p = O.Pipeline(S, 2, K, 2, 2, F, first_bin, enu, dirs, tec)
+    a = p.process_block(x[:, :, :F])
+    b = p.process_block(x[:, :, F:])
+    assert b["n_first"] == (F - 15) * O.M
+    np.testing.assert_allclose(np.concatenate([a["y"], b["y"]], axis=1), long["y"],
+                               rtol=0, atol=1e-9)
+
+
+def test_stream_window_matches_pipeline():
+    S, K, F, first_bin = 3, 5, 48, 220
+    rng = np.random.default_rng(10)
+    x = rng.integers(-9, 9, size=(2, K, F, S, 2)).astype(np.int8)
+    enu = synth.station_positions(S, 2)
+    dirs = synth.hex_beam_directions(3)
+    pipe = O.Pipeline(S, 2, K, 3, 1, F, first_bin, enu, dirs, np.array([7.0]))
+    out = pipe.process_block(x)
+    j = pipe.stream_index(2, 0, 1)
+    u = O.stream_window(x, pipe.w[:, 2, :], pipe.d[:, 0], 1, first_bin, pipe.g, 10, 30)
+    np.testing.assert_allclose(u.real.reshape(-1), out["y"][j, 10 * O.M:30 * O.M],
+                               rtol=0, atol=1e-9)
+
+
+# ------------------------------------------------------- paper figures -----
+
+def test_constants_agree_with_paper_figures():
+    gold = json.load(open(os.path.join(GOLDEN, "paper_figures.json")))
+    assert 1.0 / O.FS_HZ == gold["sample_interval_s"]["value"]
+    res = O.M / O.FS_HZ
+    assert abs(res / gold["subband_resolution_s"]["value"] - 1) < gold["subband_resolution_s"]["rel_tol"]
+    # 200e6 complex samples/s, 2 x 16 bit each
+    assert O.FS_HZ * 2 * 16 == gold["station_rate_bit_per_s"]["value"]
+    assert 8 * O.FS_HZ == gold["beamform_flops_per_station"]["value"]
+    n = 2 ** gold["dedispersion_fft_log2_len"]["value"]
+    flops = O.FS_HZ * (6 + 5 * math.log2(n))
+    g = gold["dedispersion_flops_per_beam"]
+    assert abs(flops / g["value"] - 1) < g["rel_tol"]
+    # one 2^26-sample block lasts 0.336 s, inside the 5 s budget
+    assert n / O.FS_HZ < gold["realtime_budget_s"]["value"]
