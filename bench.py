@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Realtime factor of the lunar-pulse hot path on GB300.
+
+A step is one block of station data through the whole path (beamform +
+de-disperse, noise level, inverse FFT + synthesis FIR + envelope trigger,
+history shift): 48 stations x 2 pols x 488 subbands x 65536 frames of complex
+int8 (6.14 GB, 0.336 s of data) into 50 beams.  The realtime factor is the
+block duration divided by the device time per block.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp16|fp32]
+
+With N > 1 (torchrun) every rank runs its own replica on its own GPU (the
+streams are independent; there is no exchange step) and rank 0 reports the
+whole-job rate from the slowest rank's time.  --impl reference times the FP64
+CPU oracle on bounded samples of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FS_HZ = 200e6
+M = 1024
+# algorithmic work per output sample of the synthesis kernel: inverse FFT
+# 5 N log2 N / N = 50 FLOP (the paper's radix-2 count), 16-tap complex FIR
+# with real taps 64 FLOP, envelope |u|^2 and compare 4 FLOP
+SYNTH_FLOP_PER_SAMPLE = 50 + 64 + 4
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "fp32"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-frames", type=int, default=16384)
+    return ap.parse_args()
+
+
+def workload_config(w, precision):
+    return {
+        "workload": w.name.replace("fp16", precision),
+        "stations": w.stations, "pols": w.pols, "subbands": w.subbands,
+        "first_bin": w.first_bin, "beams": w.beams, "tec_trials": list(w.tec_trials),
+        "block_frames": w.block_len, "input": w.dtype, "noise_sigma": w.noise_sigma,
+        "beamformer": "tensor-core fp16 hi/lo, fp32 accumulate" if precision == "fp16"
+        else "fp32 fma", "synthesis": "fp32",
+        "l2": "inputs larger than L2 (6.14 GB station block, 25.6 GB beam intermediate)",
+        "block_seconds": w.block_len * M / FS_HZ,
+    }
+
+
+# ------------------------------------------------------------ clocks -------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ inputs -------
+
+def device_block(w, seed, device):
+    """Seeded synthetic block on the device (rounded Gaussian table lookup)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    table = torch.from_numpy(synth.gaussian_table(w.noise_sigma, w.dtype).astype(np.int16)).to(device)
+    dt = torch.int8 if w.dtype == "int8" else torch.int16
+    x = torch.empty((w.pols, w.subbands, w.block_len, w.stations, 2), dtype=dt, device=device)
+    for pol in range(w.pols):
+        for k in range(w.subbands):
+            idx = torch.randint(0, 65536, (w.block_len, w.stations, 2), generator=g,
+                                device=device, dtype=torch.int32)
+            x[pol, k] = table[idx].to(dt)
+    return x
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+def oracle_sample(w, x_host_window, frames, chunk=2048):
+    """Time the FP64 oracle on one stream (beam 0, trial 0, pol 0) over `frames`
+    frames (in chunks of `chunk` frames with their 15 history frames).
+    Returns seconds and the extrapolated seconds per block of the workload."""
+    import oracle as O
+    enu, dirs, tec = synth.make_geometry(w)
+    nu = O.sky_frequencies(w.first_bin, w.subbands)
+    wts = O.geometric_weights(nu, enu, dirs[:1])[:, 0, :]
+    dd = O.dedispersion_weights(nu, tec, 0.5 * (nu[0] + nu[-1]))[:, 0]
+    g = O.synthesis_filter()
+    t0 = time.perf_counter()
+    done = 0
+    while done < frames:
+        n = min(chunk, frames - done)
+        lo = max(0, done - 15)
+        sub = x_host_window[:, :, lo:done + n]
+        u = O.stream_window(sub, wts, dd, 0, w.first_bin, g, done - lo, done - lo + n)
+        env = np.abs(u)
+        _ = int(np.count_nonzero(env > 1e30))
+        done += n
+    dt = time.perf_counter() - t0
+    per_block = dt * w.n_streams * (w.block_len / frames)
+    return dt, per_block
+
+
+def cpu_baseline(w, x_dev, frames):
+    xs = x_dev[:, :, :frames].cpu().numpy()
+    dt, per_block = oracle_sample(w, xs, frames)
+    block_s = w.block_len * M / FS_HZ
+    return {"value": block_s / per_block, "unit": "x realtime", "cores": 1, "kind": "oracle",
+            "sample": f"1 of {w.n_streams} streams x {frames} of {w.block_len} frames "
+                      f"({dt:.1f} s, numpy FP64 single thread), scaled by streams x frames",
+            "seconds_per_block_extrapolated": per_block}
+
+
+# ------------------------------------------------------------ ncu traffic --
+
+def recorded_traffic(kernel_file):
+    """DRAM bytes per launch of the synthesis kernel from the committed ncu
+    summary, if it was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = os.path.join(ROOT, "paper_1612_06592_gb300", "csrc", kernel_file)
+    try:
+        rec = json.load(open(path))
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        ent = rec.get(kernel_file)
+        if ent and ent.get("source_sha256_16") == digest:
+            return ent["bytes_per_full_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+# ------------------------------------------------------------ main ---------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1612_06592_gb300 import build
+    build()
+    from paper_1612_06592_gb300 import lp
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = synth.PRECISION
+    enu, dirs, tec = synth.make_geometry(w)
+    x = device_block(w, 1000 + rank, dev)
+    plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(w.tec_trials), w.block_len,
+                   input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
+                   host_input=not args.no_e2e)
+    plan.lp_set_weights(enu, dirs)
+    plan.lp_set_tec(tec)
+    stream = torch.cuda.current_stream()
+    plan.lp_profile_enable(True)
+    for _ in range(args.warmup):
+        plan.lp_process_block(x)
+    torch.cuda.synchronize()
+    plan.lp_profile_read()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.lp_process_block(x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stages, nrec = plan.lp_profile_read()
+    _, ntrig, _ = plan.lp_get_triggers()
+
+    # end to end through the same API from pinned host memory, triggers back
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        xh.copy_(x)
+        for _ in range(2):
+            plan.lp_process_block(xh)
+            plan.lp_get_triggers()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            plan.lp_process_block(xh)
+            trig, n, _ = plan.lp_get_triggers()
+            d2h += 8 + 32 * len(trig)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        barrier()
+        e2e = (t_e2e, d2h / args.steps, x.numel() * x.element_size())
+
+    if world > 1:
+        t = torch.tensor([ms, e2e[0] if e2e else 0.0], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, t_max_e2e = float(t[0]), float(t[1])
+        if e2e:
+            e2e = (t_max_e2e, e2e[1], e2e[2])
+    if rank != 0:
+        return None
+
+    block_s = w.block_len * M / FS_HZ
+    ms_step = ms / args.steps
+    rtf = world * block_s / (ms_step / 1e3)
+    synth_ms = stages["synth"] / max(nrec, 1)
+    bf_ms = stages["beamform"] / max(nrec, 1)
+    samples = w.n_streams * w.block_len * M
+    flop = samples * SYNTH_FLOP_PER_SAMPLE
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flop / (synth_ms / 1e3) / 1e12
+    traffic = recorded_traffic("k_ippf.cu")
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    in_bytes = x.numel() * x.element_size()
+    beams_bytes = w.n_streams * w.subbands * w.block_len * 8
+    bf_gbs = (in_bytes + beams_bytes) / (bf_ms / 1e3) / 1e9
+    line = {
+        "metric": "realtime factor at 48 stations×488 subbands×50 beams",
+        "value": rtf, "unit": "x realtime", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 tensor-core beamformer, f32" if args.precision == "fp16" else "f32",
+        "data": "synthetic (seeded rounded-Gaussian int8 station noise)",
+        "config": workload_config(w, args.precision),
+        "samples_per_s": {"station_complex": w.pols * w.subbands * w.block_len * w.stations
+                          * world / (ms_step / 1e3),
+                          "output_200MHz": samples * world / (ms_step / 1e3)},
+        "stage_ms": {k: v / max(nrec, 1) for k, v in stages.items()},
+        "roofline": {"bound": "alu", "kernel": "k_ippf (inverse FFT + synthesis FIR + trigger)",
+                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": traffic,
+                     "peak_note": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
+                                  f"{sm_max:.0f} MHz (max SM clock)",
+                     "flop_per_sample": SYNTH_FLOP_PER_SAMPLE,
+                     "frac_at_sampled_clock": (achieved / (alu_peak * clk["sm_mhz"] / sm_max))
+                     if clk.get("sm_mhz") else None},
+        "roofline_beamform": {"bound": "hbm", "achieved": bf_gbs, "peak": hbm_peak,
+                              "unit": "GB/s", "frac": bf_gbs / hbm_peak,
+                              "bytes": in_bytes + beams_bytes,
+                              "note": "input read + FP32 beam intermediate write"},
+        "gpu_launches": plan.lp_launches_per_block() * args.steps,
+        "triggers_last_block": int(ntrig),
+        "clocks": clk,
+    }
+    if e2e:
+        t_e2e, d2h, h2d = e2e
+        line["e2e"] = {"value": world * block_s / (t_e2e / args.steps), "unit": "x realtime",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": t_e2e / args.steps * 1e3,
+                       "path": "lp_process_block(pinned host block) + lp_get_triggers"}
+    if world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, x, args.cpu_sample_frames)
+    return line
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = synth.PRECISION
+    frames = 256
+    rng = np.random.default_rng(7)
+    table = synth.gaussian_table(w.noise_sigma, w.dtype)
+    xs = table[rng.integers(0, 65536, size=(w.pols, w.subbands, frames, w.stations, 2))]
+    for _ in range(args.warmup):
+        oracle_sample(w, xs, frames)
+    t0 = time.perf_counter()
+    per = []
+    for _ in range(args.steps):
+        per.append(oracle_sample(w, xs, frames)[1])
+    dt = time.perf_counter() - t0
+    block_s = w.block_len * M / FS_HZ
+    per_block = float(np.mean(per))
+    v = block_s / per_block
+    return {
+        "impl": "reference", "metric": "realtime factor at 48 stations×488 subbands×50 beams",
+        "value": v, "unit": "x realtime", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_block * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w, "fp64-oracle"),
+        "cpu_baseline": {"value": v, "unit": "x realtime", "cores": 1, "kind": "oracle",
+                         "sample": f"per step 1 of {w.n_streams} streams x {frames} frames, "
+                                   "scaled by streams x frames"},
+        "e2e": {"value": v, "unit": "x realtime", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": dt,
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

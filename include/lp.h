@@ -1,0 +1,188 @@
+/*
+ * lp.h -- C ABI of the GB300 lunar nanosecond-pulse hot path.
+ *
+ * The pipeline follows arXiv:1612.06592 (Winchen et al., "Realtime processing
+ * of LOFAR data for the detection of nano-second pulses from the Moon"):
+ * station subband data are combined into tied-array beams (Sec. 3, first
+ * paragraph), corrected for ionospheric dispersion by a STEC-dependent phase in
+ * the frequency domain (Sec. 3, third paragraph), turned back into a 200 MHz
+ * time series by inverting the polyphase filter bank (Sec. 2 last paragraph and
+ * Sec. 3 second paragraph; here an inverse FFT followed by a 16-tap synthesis
+ * FIR instead of the paper's sparse solve) and triggered on the envelope
+ * amplitude (Sec. 2, Fig. 1).
+ *
+ * Conventions used by every entry point:
+ *   S stations, P polarisations, K contiguous subbands starting at bin
+ *   first_bin of a 1024-point filter bank (512 bins, bin b at sky frequency
+ *   100 MHz + b * 195.3125 kHz), B beams, Tr STEC trials, F frames per block
+ *   (one frame = 1024 samples at 200 MHz = 5.12 us).
+ *   A stream is one (beam b, trial t, polarisation p), index j = (b*Tr + t)*P + p.
+ *   Output sample n counts 200 MHz samples from the stream start; block i
+ *   covers n in [(i*F - 15)*1024, ((i+1)*F - 15)*1024); samples n < 0 (the
+ *   first 15 frames of block 0) are computed from zero history and never
+ *   trigger.
+ *
+ * Memory: the library allocates no device memory.  The caller asks for the
+ * workspace size, allocates it (cudaMalloc, a PyTorch tensor, ...) and binds
+ * it; the plan keeps device pointers into it and all state (synthesis history,
+ * running noise level, trigger buffer, phase tables) lives there.  The caller
+ * keeps ownership and frees it after lp_plan_destroy.
+ *
+ * Errors: no entry point aborts.  Every call returns an lp_status; on failure
+ * lp_last_error(plan) holds a message.  CUDA errors are caught and reported
+ * as LP_ERR_CUDA.  Calls on one plan must not run concurrently from several
+ * host threads.
+ */
+#ifndef LP_H
+#define LP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lp_plan lp_plan;
+
+typedef enum {
+  LP_OK = 0,
+  LP_ERR_ARG = 1,       /* invalid argument or shape                          */
+  LP_ERR_CUDA = 2,      /* a CUDA call or kernel failed                       */
+  LP_ERR_OOM = 3,       /* workspace too small                                */
+  LP_ERR_STATE = 4,     /* call out of order (e.g. process before set_weights) */
+  LP_ERR_OVERFLOW = 5,  /* more triggers than the buffer holds                */
+  LP_ERR_TIMEOUT = 6,   /* a bounded device wait gave up                      */
+  LP_ERR_BUSY = 7       /* resource in use                                    */
+} lp_status;
+
+enum { LP_INPUT_INT8 = 1, LP_INPUT_INT16 = 2 };
+
+/* Beamformer arithmetic.  LP_PREC_FP32: plain FP32 FMA station sum.
+ * LP_PREC_FP16: tensor-core CGEMM, int8 samples exact in FP16, weights split
+ * into an FP16 high and low part, FP32 accumulation (int8 input only). */
+enum { LP_PREC_FP32 = 0, LP_PREC_FP16 = 1 };
+
+typedef struct {
+  int32_t input_dtype;      /* LP_INPUT_INT8 or LP_INPUT_INT16                  */
+  int32_t precision;        /* LP_PREC_FP32 or LP_PREC_FP16                     */
+  int32_t first_bin;        /* first selected bin, 1 <= first_bin, first_bin+K <= 512 */
+  int32_t taps;             /* synthesis taps; must be 16                       */
+  double kaiser_beta;       /* Kaiser window beta of the prototype (9)          */
+  double k_sigma;           /* trigger threshold in units of sigma_y (6)        */
+  double sigma_alpha;       /* weight of the newest block in the running sigma  */
+  double nu_ref_hz;         /* de-dispersion reference; <= 0: band centre       */
+  int64_t trigger_cap;      /* device trigger buffer capacity (records)         */
+  int32_t store_timeseries; /* 1: keep y = Re u of every stream for lp_get_timeseries */
+  int32_t host_input;       /* 1: reserve a device copy of one block so that
+                               lp_process_block accepts host pointers            */
+  int32_t frames_per_cta;   /* synthesis frames per thread block; 0 = automatic */
+  int32_t reserved;
+} lp_config;
+
+/* One trigger: envelope sample above k_sigma * sigma of its stream. */
+typedef struct {
+  int64_t n;        /* 200 MHz sample index from the stream start */
+  int32_t beam;
+  int32_t tec;      /* STEC trial index */
+  int32_t pol;
+  int32_t stream;   /* j = (beam*Tr + tec)*P + pol */
+  float env;        /* envelope |u[n]| */
+  float sigma;      /* sigma_y of the stream for this block */
+} lp_trigger;
+
+/* Fill *cfg with the defaults: int8, FP32, first_bin 12, 16 taps, beta 9,
+ * k_sigma 6, alpha 0.25, band-centre reference, 1<<20 triggers, no time
+ * series, device input, automatic tiling. */
+void lp_config_default(lp_config* cfg);
+
+/* Create a host-side plan for the given shape (Sec. 3: N_S stations, beams
+ * toward the Moon, several STEC values).  No device work.  Limits:
+ * 1 <= stations <= 64, pols in {1,2}, 1 <= subbands <= 511, 1 <= beams <= 1024,
+ * 1 <= tec_trials <= 64, 16 <= block_len <= 2^22 and a multiple of 8. */
+lp_status lp_plan_create(lp_plan** out, int stations, int pols, int subbands,
+                         int beams, int tec_trials, int64_t block_len);
+
+/* Validate and store a configuration (host only).  Must precede
+ * lp_plan_workspace_bytes. */
+lp_status lp_plan_configure(lp_plan* plan, const lp_config* cfg);
+
+/* Device workspace the plan needs, in bytes. */
+lp_status lp_plan_workspace_bytes(const lp_plan* plan, size_t* bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, >= workspace bytes) on
+ * the current device.  Zeroes the stream state and builds the synthesis
+ * filter on the device, asynchronously on `stream` (a cudaStream_t, NULL for
+ * the legacy default stream). */
+lp_status lp_plan_bind_workspace(lp_plan* plan, void* device_ptr, size_t bytes,
+                                 void* stream);
+
+/* Beam weights w[k,b,s] = exp(-2 pi i nu_k (r_s . s_b) / c) from station
+ * positions and beam directions (Sec. 3, first paragraph: "a complex weight
+ * given by the station position and the beam direction").
+ * station_enu_m: host doubles [S][3] (east, north, up in metres);
+ * beam_dir: host doubles [B][3] unit vectors in the same frame.
+ * The phase is formed and range-reduced in FP64 on the device, then FP32
+ * sincos.  Asynchronous on `stream`; the host arrays may be reused on return. */
+lp_status lp_set_weights(lp_plan* plan, const double* station_enu_m,
+                         const double* beam_dir, void* stream);
+
+/* STEC trials in TEC units, host doubles [Tr] (Sec. 3, third paragraph:
+ * multiply in the frequency domain by a complex weight depending on STEC;
+ * several values are tried).  D[k,t] = exp(-2 pi i A_t (nu_k - nu_ref)^2 /
+ * (nu_k nu_ref^2)), A_t = 40.308 * STEC_t * 1e16 / c, formed in FP64. */
+lp_status lp_set_tec(lp_plan* plan, const double* tec_tecu, void* stream);
+
+/* Process one block of station data, asynchronously on `stream`.
+ * x: [P][K][F][S][2] (re, im) int8 or int16, C order, host or device
+ * pointer (host pointers need host_input = 1; the copy is part of the call).
+ * Runs: beamform + de-disperse, block noise power and running sigma, inverse
+ * FFT + synthesis FIR + envelope threshold, history shift.  Triggers of the
+ * previous block are discarded. */
+lp_status lp_process_block(lp_plan* plan, const void* x, void* stream);
+
+/* Synchronise and copy the triggers of the last processed block to host
+ * memory `out` (capacity `cap`, may be NULL when cap == 0), sorted by
+ * (beam, tec, pol, n).  *n_total receives the number found.  Returns
+ * LP_ERR_OVERFLOW when *n_total exceeds cap or the device buffer (the first
+ * min(cap, trigger_cap) records, in sorted order of those kept, are copied). */
+lp_status lp_get_triggers(lp_plan* plan, lp_trigger* out, int64_t cap,
+                          int64_t* n_total);
+
+/* Synchronise and copy y = Re u of one stream for the last block, F*1024
+ * floats to host memory (store_timeseries = 1 only). */
+lp_status lp_get_timeseries(lp_plan* plan, int beam, int tec, int pol,
+                            float* out_host);
+
+/* Synchronise and copy the beamformed, de-dispersed subband data of one
+ * stream for the last block, host floats [K][F][2]. */
+lp_status lp_get_beams(lp_plan* plan, int beam, int tec, int pol, float* out_host);
+
+/* Synchronise and copy the running sigma_y of every stream, host doubles [J]. */
+lp_status lp_get_sigma(lp_plan* plan, double* sigma_host);
+
+/* Forget the stream: zero synthesis history and noise state, block counter 0. */
+lp_status lp_reset_stream(lp_plan* plan, void* stream);
+
+/* Number of kernel launches lp_process_block makes (for accounting). */
+int lp_launches_per_block(const lp_plan* plan);
+
+/* Stage timing.  When enabled, lp_process_block records a CUDA event pair
+ * around each stage on the stream it launches on (the host-to-device copy,
+ * the beamformer, the noise level, the synthesis, the history shift), for up
+ * to 256 blocks.  lp_profile_read synchronises, adds the durations of every
+ * recorded block into total_ms[LP_NUM_STAGES] (milliseconds), stores their
+ * number in *blocks and forgets them. */
+enum { LP_STAGE_H2D = 0, LP_STAGE_BEAMFORM = 1, LP_STAGE_SIGMA = 2, LP_STAGE_SYNTH = 3,
+       LP_STAGE_SHIFT = 4, LP_NUM_STAGES = 5 };
+lp_status lp_profile_enable(lp_plan* plan, int enable);
+lp_status lp_profile_read(lp_plan* plan, double* total_ms, int64_t* blocks);
+
+void lp_plan_destroy(lp_plan* plan);
+const char* lp_last_error(const lp_plan* plan);
+const char* lp_status_string(lp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LP_H */

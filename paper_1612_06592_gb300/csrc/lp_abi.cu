@@ -1,0 +1,442 @@
+// C ABI of the lunar-pulse pipeline: plan life cycle, workspace carving,
+// argument checks and the per-block launch sequence.  See include/lp.h for
+// the contract of every entry point.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+using lp::kM;
+
+namespace {
+
+lp_status fail(lp_plan* p, lp_status st, const char* fmt, ...) {
+  if (p) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    p->err = buf;
+  }
+  return st;
+}
+
+#define LP_CUDA(plan, call)                                                        \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(plan, LP_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                             \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Carve the workspace.  With base == nullptr only the size is computed.
+size_t carve(lp_plan& p, char* base) {
+  const auto& sh = p.shape;
+  const long long J = sh.J();
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = align_up(off, 256);
+    char* ptr = base ? base + off : nullptr;
+    off += bytes;
+    return ptr;
+  };
+  auto& b = p.buf;
+  b.station_enu = (double*)take(sizeof(double) * 3 * sh.S);
+  b.beam_dir = (double*)take(sizeof(double) * 3 * sh.B);
+  b.tec = (double*)take(sizeof(double) * sh.Tr);
+  b.w32 = (float2*)take(sizeof(float2) * (size_t)sh.K * sh.B * sh.S);
+  b.wtc = p.cfg.precision == LP_PREC_FP16 ? (__half*)take(lp::beamform_tc_weight_bytes(sh)) : nullptr;
+  b.dd = (float2*)take(sizeof(float2) * (size_t)sh.K * sh.Tr);
+  b.proto = (double*)take(sizeof(double) * kM * lp::kTaps);
+  b.g = (float*)take(sizeof(float) * kM * lp::kTaps);
+  b.filter_sums = (double*)take(sizeof(double) * 2);
+  b.beams = (float2*)take(sizeof(float2) * (size_t)J * sh.K * sh.row());
+  b.power_part = (float*)take(sizeof(float) * (size_t)J * sh.K * p.n_ftiles_bf);
+  b.sigma2 = (double*)take(sizeof(double) * J);
+  b.theta = (float*)take(sizeof(float) * J);
+  b.theta2 = (float*)take(sizeof(float) * J);
+  b.trig_count = (unsigned long long*)take(sizeof(unsigned long long));
+  b.trig = (lp::TriggerRec*)take(sizeof(lp::TriggerRec) * (size_t)p.cfg.trigger_cap);
+  b.y = p.cfg.store_timeseries ? (float*)take(sizeof(float) * (size_t)J * sh.F * kM) : nullptr;
+  const size_t in_bytes = (size_t)sh.P * sh.K * sh.F * sh.S * 2 *
+                          (p.cfg.input_dtype == LP_INPUT_INT8 ? 1 : 2);
+  b.staging = p.cfg.host_input ? (void*)take(in_bytes) : nullptr;
+  return align_up(off, 256);
+}
+
+size_t input_bytes(const lp_plan& p) {
+  const auto& sh = p.shape;
+  return (size_t)sh.P * sh.K * sh.F * sh.S * 2 * (p.cfg.input_dtype == LP_INPUT_INT8 ? 1 : 2);
+}
+
+lp_status need_bound(lp_plan* p) {
+  if (!p) return LP_ERR_ARG;
+  if (!p->bound) return fail(p, LP_ERR_STATE, "workspace not bound");
+  return LP_OK;
+}
+
+lp_status set_device(lp_plan* p) {
+  int cur = -1;
+  LP_CUDA(p, cudaGetDevice(&cur));
+  if (cur != p->device) LP_CUDA(p, cudaSetDevice(p->device));
+  return LP_OK;
+}
+
+lp_status sync_last(lp_plan* p) {
+  LP_CUDA(p, cudaStreamSynchronize(p->last_stream));
+  LP_CUDA(p, cudaGetLastError());
+  return LP_OK;
+}
+
+// Record the start / end event of a stage for the current block (profiling).
+void prof_mark(lp_plan* p, int stage, int end, cudaStream_t s) {
+  if (!p->profiling) return;
+  const int slot = p->prof_n % lp_plan::kProfSlots;
+  cudaEvent_t& ev = p->prof_ev[slot][stage][end];
+  if (!ev) cudaEventCreate(&ev);
+  cudaEventRecord(ev, s);
+  if (end) p->prof_used[slot][stage] = true;
+}
+
+int stream_of(const lp_plan* p, int beam, int tec, int pol) {
+  const auto& sh = p->shape;
+  if (beam < 0 || beam >= sh.B || tec < 0 || tec >= sh.Tr || pol < 0 || pol >= sh.P) return -1;
+  return (beam * sh.Tr + tec) * sh.P + pol;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lp_config_default(lp_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof *c);
+  c->input_dtype = LP_INPUT_INT8;
+  c->precision = LP_PREC_FP32;
+  c->first_bin = 12;
+  c->taps = 16;
+  c->kaiser_beta = 9.0;
+  c->k_sigma = 6.0;
+  c->sigma_alpha = 0.25;
+  c->nu_ref_hz = 0.0;
+  c->trigger_cap = 1 << 20;
+  c->store_timeseries = 0;
+  c->host_input = 0;
+  c->frames_per_cta = 0;
+}
+
+lp_status lp_plan_create(lp_plan** out, int stations, int pols, int subbands, int beams,
+                         int tec_trials, int64_t block_len) {
+  if (!out) return LP_ERR_ARG;
+  *out = nullptr;
+  if (stations < 1 || stations > 64 || pols < 1 || pols > 2 || subbands < 1 || subbands > 511 ||
+      beams < 1 || beams > 1024 || tec_trials < 1 || tec_trials > 64 || block_len < 16 ||
+      block_len > (1 << 22) || block_len % 8 != 0)
+    return LP_ERR_ARG;
+  lp_plan* p = new (std::nothrow) lp_plan();
+  if (!p) return LP_ERR_OOM;
+  p->shape = lp::Shape{stations, pols, subbands, beams, tec_trials, (long long)block_len};
+  lp_config_default(&p->cfg);
+  *out = p;
+  return LP_OK;
+}
+
+lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
+  if (!p || !c) return LP_ERR_ARG;
+  if (p->bound) return fail(p, LP_ERR_STATE, "configure after bind");
+  const auto& sh = p->shape;
+  if (c->input_dtype != LP_INPUT_INT8 && c->input_dtype != LP_INPUT_INT16)
+    return fail(p, LP_ERR_ARG, "input_dtype must be LP_INPUT_INT8 or LP_INPUT_INT16");
+  if (c->precision != LP_PREC_FP32 && c->precision != LP_PREC_FP16)
+    return fail(p, LP_ERR_ARG, "precision must be LP_PREC_FP32 or LP_PREC_FP16");
+  if (c->precision == LP_PREC_FP16 && c->input_dtype != LP_INPUT_INT8)
+    return fail(p, LP_ERR_ARG, "the FP16 tensor-core form takes int8 input only");
+  if (c->first_bin < 1 || c->first_bin + sh.K > lp::kBins)
+    return fail(p, LP_ERR_ARG, "bins [%d, %d) must lie inside [1, 512)", c->first_bin,
+                c->first_bin + sh.K);
+  if (c->taps != lp::kTaps) return fail(p, LP_ERR_ARG, "taps must be 16");
+  if (!(c->kaiser_beta >= 0.0 && c->kaiser_beta <= 50.0))
+    return fail(p, LP_ERR_ARG, "kaiser_beta out of range");
+  if (!(c->k_sigma > 0.0)) return fail(p, LP_ERR_ARG, "k_sigma must be positive");
+  if (!(c->sigma_alpha > 0.0 && c->sigma_alpha <= 1.0))
+    return fail(p, LP_ERR_ARG, "sigma_alpha must be in (0, 1]");
+  if (c->trigger_cap < 1 || c->trigger_cap > (1LL << 32))
+    return fail(p, LP_ERR_ARG, "trigger_cap out of range");
+  if (c->frames_per_cta != 0 && (c->frames_per_cta < 8 || c->frames_per_cta % 8 != 0))
+    return fail(p, LP_ERR_ARG, "frames_per_cta must be 0 or a positive multiple of 8");
+  p->cfg = *c;
+  p->frames_per_cta = c->frames_per_cta ? c->frames_per_cta : lp::ippf_default_frames_per_cta(sh);
+  const int ft = c->precision == LP_PREC_FP16 ? lp::beamform_tc_frame_tile()
+                                              : lp::beamform_f32_frame_tile();
+  p->n_ftiles_bf = (int)((sh.F + ft - 1) / ft);
+  const double nu_lo = lp::kNu0 + c->first_bin * (lp::kFs / kM);
+  const double nu_hi = lp::kNu0 + (c->first_bin + sh.K - 1) * (lp::kFs / kM);
+  p->nu_ref = c->nu_ref_hz > 0 ? c->nu_ref_hz : 0.5 * (nu_lo + nu_hi);
+  p->configured = true;
+  return LP_OK;
+}
+
+lp_status lp_plan_workspace_bytes(const lp_plan* p, size_t* bytes) {
+  if (!p || !bytes) return LP_ERR_ARG;
+  if (!p->configured) return LP_ERR_STATE;
+  lp_plan tmp = *p;
+  *bytes = carve(tmp, nullptr);
+  return LP_OK;
+}
+
+lp_status lp_plan_bind_workspace(lp_plan* p, void* dev, size_t bytes, void* stream) {
+  if (!p) return LP_ERR_ARG;
+  if (!p->configured) return fail(p, LP_ERR_STATE, "configure before bind");
+  if (!dev || (reinterpret_cast<uintptr_t>(dev) & 255u))
+    return fail(p, LP_ERR_ARG, "workspace must be a 256-byte aligned device pointer");
+  lp_plan tmp = *p;
+  const size_t need = carve(tmp, nullptr);
+  if (bytes < need) return fail(p, LP_ERR_OOM, "workspace %zu bytes < %zu needed", bytes, need);
+  cudaPointerAttributes attr;
+  LP_CUDA(p, cudaPointerGetAttributes(&attr, dev));
+  if (attr.type != cudaMemoryTypeDevice)
+    return fail(p, LP_ERR_ARG, "workspace is not device memory");
+  p->device = attr.device;
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  p->ws = dev;
+  p->ws_bytes = bytes;
+  carve(*p, static_cast<char*>(dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LP_CUDA(p, cudaMemsetAsync(dev, 0, need, s));
+  LP_CUDA(p, lp::launch_prototype(*p, s));
+  p->last_stream = s;
+  p->bound = true;
+  p->block_index = 0;
+  return LP_OK;
+}
+
+lp_status lp_set_weights(lp_plan* p, const double* enu, const double* dir, void* stream) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!enu || !dir) return fail(p, LP_ERR_ARG, "null geometry");
+  const auto& sh = p->shape;
+  for (int b = 0; b < sh.B; ++b) {
+    const double n2 = dir[3 * b] * dir[3 * b] + dir[3 * b + 1] * dir[3 * b + 1] +
+                      dir[3 * b + 2] * dir[3 * b + 2];
+    if (!(std::fabs(n2 - 1.0) < 1e-6)) return fail(p, LP_ERR_ARG, "beam %d is not a unit vector", b);
+  }
+  for (int i = 0; i < 3 * sh.S; ++i)
+    if (!std::isfinite(enu[i])) return fail(p, LP_ERR_ARG, "station position not finite");
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // pageable host memory: the copy is complete for the host on return
+  LP_CUDA(p, cudaMemcpyAsync(p->buf.station_enu, enu, sizeof(double) * 3 * sh.S,
+                             cudaMemcpyHostToDevice, s));
+  LP_CUDA(p, cudaMemcpyAsync(p->buf.beam_dir, dir, sizeof(double) * 3 * sh.B,
+                             cudaMemcpyHostToDevice, s));
+  LP_CUDA(p, lp::launch_weights(*p, s));
+  p->last_stream = s;
+  p->weights_set = true;
+  return LP_OK;
+}
+
+lp_status lp_set_tec(lp_plan* p, const double* tec, void* stream) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!tec) return fail(p, LP_ERR_ARG, "null tec");
+  const auto& sh = p->shape;
+  for (int t = 0; t < sh.Tr; ++t)
+    if (!std::isfinite(tec[t]) || std::fabs(tec[t]) > 1e4)
+      return fail(p, LP_ERR_ARG, "tec[%d] out of range", t);
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LP_CUDA(p, cudaMemcpyAsync(p->buf.tec, tec, sizeof(double) * sh.Tr, cudaMemcpyHostToDevice, s));
+  LP_CUDA(p, lp::launch_dedisp(*p, s));
+  p->last_stream = s;
+  p->tec_set = true;
+  return LP_OK;
+}
+
+lp_status lp_process_block(lp_plan* p, const void* x, void* stream) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!p->weights_set || !p->tec_set)
+    return fail(p, LP_ERR_STATE, "lp_set_weights and lp_set_tec must precede lp_process_block");
+  if (!x) return fail(p, LP_ERR_ARG, "null input");
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaPointerAttributes attr;
+  LP_CUDA(p, cudaPointerGetAttributes(&attr, x));
+  const void* xd = x;
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+    if (!p->buf.staging)
+      return fail(p, LP_ERR_ARG, "host input needs host_input = 1 in the configuration");
+    prof_mark(p, LP_STAGE_H2D, 0, s);
+    LP_CUDA(p, cudaMemcpyAsync(p->buf.staging, x, input_bytes(*p), cudaMemcpyHostToDevice, s));
+    prof_mark(p, LP_STAGE_H2D, 1, s);
+    xd = p->buf.staging;
+  } else if (attr.device != p->device) {
+    return fail(p, LP_ERR_ARG, "input lives on device %d, plan on %d", attr.device, p->device);
+  }
+  const size_t align = p->cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4;
+  if (reinterpret_cast<uintptr_t>(xd) % align)
+    return fail(p, LP_ERR_ARG, "input must be %zu-byte aligned", align);
+  LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
+  prof_mark(p, LP_STAGE_BEAMFORM, 0, s);
+  if (p->cfg.precision == LP_PREC_FP16) {
+    LP_CUDA(p, lp::launch_beamform_tc(*p, xd, s));
+  } else {
+    LP_CUDA(p, lp::launch_beamform_f32(*p, xd, s));
+  }
+  prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
+  prof_mark(p, LP_STAGE_SIGMA, 0, s);
+  LP_CUDA(p, lp::launch_sigma(*p, p->block_index == 0, s));
+  prof_mark(p, LP_STAGE_SIGMA, 1, s);
+  prof_mark(p, LP_STAGE_SYNTH, 0, s);
+  LP_CUDA(p, lp::launch_ippf(*p, s));
+  prof_mark(p, LP_STAGE_SYNTH, 1, s);
+  prof_mark(p, LP_STAGE_SHIFT, 0, s);
+  LP_CUDA(p, lp::launch_history_shift(*p, s));
+  prof_mark(p, LP_STAGE_SHIFT, 1, s);
+  if (p->profiling && p->prof_n < lp_plan::kProfSlots) p->prof_n += 1;
+  p->last_stream = s;
+  p->block_index += 1;
+  return LP_OK;
+}
+
+lp_status lp_get_triggers(lp_plan* p, lp_trigger* out, int64_t cap, int64_t* n_total) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!n_total || cap < 0 || (cap > 0 && !out)) return fail(p, LP_ERR_ARG, "bad output buffer");
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
+  unsigned long long cnt = 0;
+  LP_CUDA(p, cudaMemcpy(&cnt, p->buf.trig_count, sizeof cnt, cudaMemcpyDeviceToHost));
+  *n_total = (int64_t)cnt;
+  const long long kept = std::min<long long>((long long)cnt, p->cfg.trigger_cap);
+  std::vector<lp_trigger> all((size_t)kept);
+  if (kept > 0)
+    LP_CUDA(p, cudaMemcpy(all.data(), p->buf.trig, sizeof(lp_trigger) * (size_t)kept,
+                          cudaMemcpyDeviceToHost));
+  std::sort(all.begin(), all.end(), [](const lp_trigger& a, const lp_trigger& b) {
+    if (a.beam != b.beam) return a.beam < b.beam;
+    if (a.tec != b.tec) return a.tec < b.tec;
+    if (a.pol != b.pol) return a.pol < b.pol;
+    return a.n < b.n;
+  });
+  const long long ncopy = std::min<long long>(kept, cap);
+  if (ncopy > 0) std::memcpy(out, all.data(), sizeof(lp_trigger) * (size_t)ncopy);
+  if ((long long)cnt > cap || (long long)cnt > p->cfg.trigger_cap)
+    return fail(p, LP_ERR_OVERFLOW, "%llu triggers, %lld copied", cnt, ncopy);
+  return LP_OK;
+}
+
+lp_status lp_get_timeseries(lp_plan* p, int beam, int tec, int pol, float* out) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!p->buf.y) return fail(p, LP_ERR_STATE, "store_timeseries is off");
+  const int j = stream_of(p, beam, tec, pol);
+  if (j < 0 || !out) return fail(p, LP_ERR_ARG, "bad stream or buffer");
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
+  const size_t n = (size_t)p->shape.F * kM;
+  LP_CUDA(p, cudaMemcpy(out, p->buf.y + (size_t)j * n, n * sizeof(float), cudaMemcpyDeviceToHost));
+  return LP_OK;
+}
+
+lp_status lp_get_beams(lp_plan* p, int beam, int tec, int pol, float* out) {
+  if (lp_status st = need_bound(p)) return st;
+  const int j = stream_of(p, beam, tec, pol);
+  if (j < 0 || !out) return fail(p, LP_ERR_ARG, "bad stream or buffer");
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
+  const auto& sh = p->shape;
+  // After a block the row holds [prefix = last 16 frames][F frames]; the
+  // block's frames sit at positions 16 .. F+15.
+  LP_CUDA(p, cudaMemcpy2D(out, sizeof(float2) * sh.F,
+                          p->buf.beams + (size_t)j * sh.K * sh.row() + lp::kPrefix,
+                          sizeof(float2) * sh.row(), sizeof(float2) * sh.F, sh.K,
+                          cudaMemcpyDeviceToHost));
+  return LP_OK;
+}
+
+lp_status lp_get_sigma(lp_plan* p, double* out) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!out) return fail(p, LP_ERR_ARG, "null output");
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
+  const int J = p->shape.J();
+  std::vector<double> s2(J);
+  LP_CUDA(p, cudaMemcpy(s2.data(), p->buf.sigma2, sizeof(double) * J, cudaMemcpyDeviceToHost));
+  for (int j = 0; j < J; ++j) out[j] = std::sqrt(s2[j]);
+  return LP_OK;
+}
+
+lp_status lp_reset_stream(lp_plan* p, void* stream) {
+  if (lp_status st = need_bound(p)) return st;
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto& sh = p->shape;
+  LP_CUDA(p, cudaMemsetAsync(p->buf.beams, 0,
+                             sizeof(float2) * (size_t)sh.J() * sh.K * sh.row(), s));
+  LP_CUDA(p, cudaMemsetAsync(p->buf.sigma2, 0, sizeof(double) * sh.J(), s));
+  LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
+  p->last_stream = s;
+  p->block_index = 0;
+  return LP_OK;
+}
+
+int lp_launches_per_block(const lp_plan* p) {
+  (void)p;
+  return 4;  // beamformer, sigma, synthesis, history shift
+}
+
+lp_status lp_profile_enable(lp_plan* p, int enable) {
+  if (!p) return LP_ERR_ARG;
+  p->profiling = enable != 0;
+  return LP_OK;
+}
+
+lp_status lp_profile_read(lp_plan* p, double* total_ms, int64_t* blocks) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!total_ms || !blocks) return fail(p, LP_ERR_ARG, "null output");
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
+  for (int st = 0; st < LP_NUM_STAGES; ++st) total_ms[st] = 0.0;
+  for (int slot = 0; slot < p->prof_n; ++slot) {
+    for (int st = 0; st < LP_NUM_STAGES; ++st) {
+      if (!p->prof_used[slot][st]) continue;
+      float ms = 0.f;
+      LP_CUDA(p, cudaEventElapsedTime(&ms, p->prof_ev[slot][st][0], p->prof_ev[slot][st][1]));
+      total_ms[st] += ms;
+      p->prof_used[slot][st] = false;
+    }
+  }
+  *blocks = p->prof_n;
+  p->prof_n = 0;
+  return LP_OK;
+}
+
+void lp_plan_destroy(lp_plan* p) {
+  if (!p) return;
+  for (auto& slot : p->prof_ev)
+    for (auto& st : slot)
+      for (auto& ev : st)
+        if (ev) cudaEventDestroy(ev);
+  delete p;
+}
+
+const char* lp_last_error(const lp_plan* p) { return p ? p->err.c_str() : "null plan"; }
+
+const char* lp_status_string(lp_status s) {
+  switch (s) {
+    case LP_OK: return "ok";
+    case LP_ERR_ARG: return "invalid argument";
+    case LP_ERR_CUDA: return "CUDA error";
+    case LP_ERR_OOM: return "workspace too small";
+    case LP_ERR_STATE: return "call out of order";
+    case LP_ERR_OVERFLOW: return "trigger buffer overflow";
+    case LP_ERR_TIMEOUT: return "device wait timed out";
+    case LP_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal declarations shared by the kernels and the C ABI of the GB300
+// lunar-pulse pipeline.  Not part of the public interface (see include/lp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/lp.h"
+
+namespace lp {
+
+constexpr int kM = 1024;              // filter-bank size: 1024 samples per frame
+constexpr int kBins = kM / 2;         // 512 bins of a real 200 MHz input
+constexpr int kTaps = 16;             // synthesis taps (frames)
+constexpr int kHist = kTaps - 1;      // 15 history frames per stream
+constexpr int kPrefix = 16;           // frames stored before a block's first frame
+constexpr double kFs = 200e6;         // 5 ns sampling (Sec. 2)
+constexpr double kNu0 = kFs / 2;      // sky frequency of bin 0 (second Nyquist zone)
+constexpr double kC = 299792458.0;
+constexpr double kKappa = 40.308;     // e^2 / (8 pi^2 eps0 m_e), m^3 s^-2
+constexpr double kTecu = 1e16;
+
+// Device trigger record; same layout as lp_trigger.
+struct TriggerRec {
+  long long n;
+  int beam, tec, pol, stream;
+  float env, sigma;
+};
+static_assert(sizeof(TriggerRec) == sizeof(lp_trigger), "trigger layout");
+
+// Views into the bound workspace.
+struct Buffers {
+  double* station_enu;     // [S][3]
+  double* beam_dir;        // [B][3]
+  double* tec;             // [Tr]
+  float2* w32;             // [K][B][S] FP32 weights (FP32 form)
+  __half* wtc;             // tensor-core A operand (FP16 form), see k_beamform_tc.cu
+  float2* dd;              // [K][Tr] de-dispersion phasors
+  double* proto;           // [16384] unnormalised prototype (scratch for filter build)
+  float* g;                // [16384] synthesis filter * 2/M
+  double* filter_sums;     // [2]: sum h, sum h^2 of the unnormalised prototype
+  float2* beams;           // [J][K][row], row = F + 16, frame m at m + 16
+  float* power_part;       // [J][K][n_ftiles] partial sums of |beam|^2
+  double* sigma2;          // [J]
+  float* theta;            // [J] k_sigma * sigma
+  float* theta2;           // [J] theta^2 in FP32 (threshold on |u|^2)
+  unsigned long long* trig_count;  // [1]
+  TriggerRec* trig;        // [trigger_cap]
+  float* y;                // [J][F*M] or null
+  void* staging;           // one block of input or null
+};
+
+struct Shape {
+  int S, P, K, B, Tr;
+  long long F;
+  int J() const { return B * Tr * P; }
+  long long row() const { return F + kPrefix; }
+};
+
+}  // namespace lp
+
+struct lp_plan {
+  lp::Shape shape;
+  lp_config cfg;
+  bool configured = false;
+  bool bound = false;
+  bool weights_set = false;
+  bool tec_set = false;
+  int device = -1;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  lp::Buffers buf{};
+  long long block_index = 0;
+  cudaStream_t last_stream = nullptr;
+  int n_ftiles_bf = 0;     // frame tiles of the beamformer (power partials)
+  int frames_per_cta = 0;  // synthesis tiling
+  double nu_ref = 0;
+  std::string err;
+  // stage timing (lp_profile_enable): event pairs per recorded block
+  bool profiling = false;
+  static constexpr int kProfSlots = 256;
+  cudaEvent_t prof_ev[kProfSlots][LP_NUM_STAGES][2] = {};
+  bool prof_used[kProfSlots][LP_NUM_STAGES] = {};
+  int prof_n = 0;
+};
+
+namespace lp {
+
+// ---- kernel launchers (each returns the cudaError of the launch) ----------
+cudaError_t launch_prototype(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_weights(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_dedisp(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, cudaStream_t s);
+cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, cudaStream_t s);
+cudaError_t launch_sigma(const lp_plan& p, bool first_block, cudaStream_t s);
+cudaError_t launch_ippf(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_history_shift(const lp_plan& p, cudaStream_t s);
+
+int beamform_f32_frame_tile();
+int beamform_tc_frame_tile();
+size_t beamform_tc_weight_bytes(const Shape& sh);
+int ippf_default_frames_per_cta(const Shape& sh);
+
+}  // namespace lp

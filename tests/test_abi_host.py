@@ -1,0 +1,96 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+entry point include/lp.h declares, and its host-only calls validate arguments.
+No CUDA call is made here (no GPU in this environment)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1612_06592_gb300 import build
+    build()
+    from paper_1612_06592_gb300 import lp
+    return lp
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    names = declared_functions()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(lib._lib, n), n
+        assert n in lib.SIGNATURES, n
+
+
+def test_struct_layouts(lib):
+    assert ctypes.sizeof(lib.lp_trigger) == 32
+    assert lib.TRIGGER_DTYPE.itemsize == 32
+    assert ctypes.sizeof(lib.lp_config) == 72
+
+
+def _create(lib, *shape):
+    h = ctypes.c_void_p()
+    st = lib._lib.lp_plan_create(ctypes.byref(h), *shape)
+    return st, h
+
+
+def test_plan_create_validates_shape(lib):
+    ok, h = _create(lib, 48, 2, 488, 50, 1, 65536)
+    assert ok == lib.LP_OK and h.value
+    lib._lib.lp_plan_destroy(h)
+    for bad in [(0, 2, 16, 1, 1, 64), (6, 3, 16, 1, 1, 64), (6, 2, 0, 1, 1, 64),
+                (6, 2, 16, 0, 1, 64), (6, 2, 16, 1, 0, 64), (6, 2, 16, 1, 1, 8),
+                (6, 2, 16, 1, 1, 100), (65, 2, 16, 1, 1, 64)]:
+        st, h = _create(lib, *bad)
+        assert st == lib.LP_ERR_ARG and not h.value, bad
+
+
+def test_configure_validates_and_sizes_workspace(lib):
+    st, h = _create(lib, 6, 2, 16, 1, 1, 4096)
+    assert st == lib.LP_OK
+    c = lib.config_default()
+    c.first_bin = 154
+    c.input_dtype = lib.LP_INPUT_INT16
+    assert lib._lib.lp_plan_configure(h, ctypes.byref(c)) == lib.LP_OK
+    n = ctypes.c_size_t()
+    assert lib._lib.lp_plan_workspace_bytes(h, ctypes.byref(n)) == lib.LP_OK
+    # beams intermediate dominates: J * K * (F + 16) complex floats
+    assert n.value >= 2 * 16 * (4096 + 16) * 8
+    bad = lib.config_default()
+    bad.first_bin = 500                       # 500 + 16 > 512
+    assert lib._lib.lp_plan_configure(h, ctypes.byref(bad)) == lib.LP_ERR_ARG
+    bad = lib.config_default()
+    bad.first_bin = 154
+    bad.precision = lib.LP_PREC_FP16
+    bad.input_dtype = lib.LP_INPUT_INT16     # FP16 form takes int8 only
+    assert lib._lib.lp_plan_configure(h, ctypes.byref(bad)) == lib.LP_ERR_ARG
+    assert b"int8" in lib._lib.lp_last_error(h)
+    bad = lib.config_default()
+    bad.first_bin = 154
+    bad.taps = 8
+    assert lib._lib.lp_plan_configure(h, ctypes.byref(bad)) == lib.LP_ERR_ARG
+    bad.taps = 16
+    bad.frames_per_cta = 12
+    assert lib._lib.lp_plan_configure(h, ctypes.byref(bad)) == lib.LP_ERR_ARG
+    lib._lib.lp_plan_destroy(h)
+
+
+def test_calls_before_bind_report_state_errors(lib):
+    st, h = _create(lib, 6, 2, 16, 1, 1, 64)
+    n = ctypes.c_int64()
+    assert lib._lib.lp_get_triggers(h, None, 0, ctypes.byref(n)) == lib.LP_ERR_STATE
+    assert lib._lib.lp_process_block(h, None, None) == lib.LP_ERR_STATE
+    # workspace size needs a configuration first
+    assert lib._lib.lp_plan_workspace_bytes(h, ctypes.byref(ctypes.c_size_t())) == lib.LP_ERR_STATE
+    lib._lib.lp_plan_destroy(h)
