@@ -53,7 +53,19 @@ def parse():
     ap.add_argument("--precision", default="fp16", choices=["fp16", "fp32"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=16384)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="block length override for small profiling cases (not a bench line)")
     return ap.parse_args()
+
+
+def bench_workload(args):
+    w = synth.PRECISION
+    if args.frames:
+        import dataclasses
+        w = dataclasses.replace(w, name=w.name.replace("65536fr", f"{args.frames}fr"),
+                                block_len=args.frames)
+    return w
 
 
 def workload_config(w, precision):
@@ -64,7 +76,8 @@ def workload_config(w, precision):
         "block_frames": w.block_len, "input": w.dtype, "noise_sigma": w.noise_sigma,
         "beamformer": "tensor-core fp16 hi/lo, fp32 accumulate" if precision == "fp16"
         else "fp32 fma", "synthesis": "fp32",
-        "l2": "inputs larger than L2 (6.14 GB station block, 25.6 GB beam intermediate)",
+        "l2": "inputs larger than L2 (%.2f GB station block, %.1f GB beam intermediate)" % (
+            w.input_bytes / 1e9, w.n_streams * w.subbands * w.block_len * 8 / 1e9),
         "block_seconds": w.block_len * M / FS_HZ,
     }
 
@@ -207,7 +220,7 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    w = synth.PRECISION
+    w = bench_workload(args)
     enu, dirs, tec = synth.make_geometry(w)
     x = device_block(w, 1000 + rank, dev)
     plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(w.tec_trials), w.block_len,
@@ -327,8 +340,8 @@ def run_ours(args, rank, world, local_rank):
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": t_e2e / args.steps * 1e3,
                        "path": "lp_process_block(pinned host block) + lp_get_triggers"}
-    if world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, x, args.cpu_sample_frames)
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, x, min(args.cpu_sample_frames, w.block_len))
     return line
 
 
