@@ -178,6 +178,41 @@ enum { LP_STAGE_H2D = 0, LP_STAGE_BEAMFORM = 1, LP_STAGE_SIGMA = 2, LP_STAGE_SYN
 lp_status lp_profile_enable(lp_plan* plan, int enable);
 lp_status lp_profile_read(lp_plan* plan, double* total_ms, int64_t* blocks);
 
+/* Size of the static device scratch of lp_process_block_noalloc: 16 MiB,
+ * held by every GPU that loads the library until the process exits. */
+#define LP_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (a host that owns the device heap or forbids
+ * allocation once running, code that must not allocate during stream
+ * capture) and so cannot bind a plan workspace.  It runs one block of the
+ * FP32 form (beam weights and de-dispersion tables, beamforming, noise level,
+ * synthesis and trigger) as the first block of a stream (zero history) and
+ * allocates nothing: its scratch is a static device array of
+ * LP_NOALLOC_SCRATCH_BYTES.
+ *   Shape arguments as lp_plan_create; cfg as lp_plan_configure (precision
+ *   must be LP_PREC_FP32; store_timeseries and host_input are ignored).
+ *   station_enu_m [S][3], beam_dir [B][3], tec_tecu [Tr]: host doubles.
+ *   x: device block [P][K][F][S][2] on the current device.
+ *   y: device floats [J][F*1024], y = Re u of every stream (written).
+ *   sigma2: device doubles [J] (written) or NULL: the block's sigma_y^2.
+ *   triggers: device records, capacity trigger_cap (>= 0), unsorted;
+ *   trigger_count: device counter (set to the number found) or NULL.
+ *   err/errlen: optional host buffer for a message.
+ * Returns LP_ERR_ARG, without touching the device, for a shape whose scratch
+ * would exceed LP_NOALLOC_SCRATCH_BYTES.  Asynchronous on `stream`.  All
+ * calls on a device share the scratch (it keeps the last call's contents;
+ * the call clears what must start at zero), so calls whose GPU work overlaps
+ * race and must be serialised by the caller.  The first call on a device
+ * looks up the scratch address and must come before any stream capture. */
+lp_status lp_process_block_noalloc(int stations, int pols, int subbands, int beams,
+                                   int tec_trials, int64_t block_len, const lp_config* cfg,
+                                   const double* station_enu_m, const double* beam_dir,
+                                   const double* tec_tecu, const void* x, float* y,
+                                   double* sigma2, lp_trigger* triggers, int64_t trigger_cap,
+                                   unsigned long long* trigger_count, void* stream, char* err,
+                                   size_t errlen);
+
 void lp_plan_destroy(lp_plan* plan);
 const char* lp_last_error(const lp_plan* plan);
 const char* lp_status_string(lp_status s);

@@ -20,6 +20,7 @@ LP_OK, LP_ERR_ARG, LP_ERR_CUDA, LP_ERR_OOM, LP_ERR_STATE, LP_ERR_OVERFLOW, LP_ER
     LP_ERR_BUSY = range(8)
 LP_INPUT_INT8, LP_INPUT_INT16 = 1, 2
 LP_PREC_FP32, LP_PREC_FP16 = 0, 1
+LP_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
 class lp_config(ctypes.Structure):
@@ -76,6 +77,10 @@ SIGNATURES = {
     "lp_launches_per_block": (ctypes.c_int, [_P]),
     "lp_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "lp_profile_read": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "lp_process_block_noalloc": (ctypes.c_int, [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+        ctypes.POINTER(lp_config), _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P,
+        ctypes.c_char_p, ctypes.c_size_t]),
     "lp_plan_destroy": (None, [_P]),
     "lp_last_error": (ctypes.c_char_p, [_P]),
     "lp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
