@@ -4,14 +4,15 @@
 // k_ippf: one thread block owns one stream j and a run of output frames
 // [m0, m1).  It walks frames m0-16 .. m1-1 in batches of 8 (one per warp):
 //   1. the batch's beam bins (8 frames x K bins, frames contiguous per bin
-//      row) are read coalesced into shared memory;
+//      row) are copied into a zero-padded 512-bin stage with cp.async while
+//      the previous batch's FIR runs;
 //   2. each warp takes the 1024-point inverse DFT of one frame,
 //        z[p] = sum_k c[k] exp(+2 pi i k p / 1024),  c nonzero only in the
 //      selected bins (< 512), as 32 x 32: a register-resident 32-point DFT
 //      over k = 32 k1 + lane (upper half of the inputs zero), the twiddle
 //      exp(2 pi i lane p1 / 1024), a transpose through shared memory and a
-//      second 32-point DFT; the result lands in a 23-frame ring in shared
-//      memory;
+//      second 32-point DFT; the result lands in a 24-frame ring in shared
+//      memory (three groups of 8 frames, addressed by group base pointers);
 //   3. every thread owns 4 output phases p and computes, for the 8 new frames,
 //        u_m[p] = sum_{t<16} g[t M + p] z_{m-t}[p]     (g holds the 2/M scale),
 //      y = Re u (optionally stored), |u|^2 against theta^2; warps vote and
@@ -25,8 +26,8 @@ namespace {
 
 constexpr int NT = 256;            // threads per block
 constexpr int NW = NT / 32;        // warps = frames per batch
-constexpr int RING = 23;           // >= 15 history + 8 new frames
-constexpr int SK = 516;            // stage row stride (float2), 2*SK = 8 mod 32 banks
+constexpr int RING = 24;           // 3 groups of 8 frames: 15 history + 8 new fit
+constexpr int SK = 516;            // stage row: 512 bins + pad, 2*SK = 8 mod 32 banks
 constexpr int PPT = kM / NT;       // output phases per thread
 
 __host__ __device__ constexpr int br5(int i) {
@@ -116,16 +117,41 @@ __device__ __forceinline__ void dft32_halfzero(float2 (&v)[32]) {
 
 __device__ __forceinline__ void dft32(float2 (&v)[32]) { dif32_from<16>(v); }
 
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Stage the beam bins of CTA frames r0 .. r0+7 into stage[f][first_bin + k]
+// (asynchronous copies; frames outside the run are zeroed).
+__device__ __forceinline__ void stage_batch(float2* stage, const float2* __restrict__ brow, int K,
+                                            int first_bin, long long row, long long m0, int r0,
+                                            int nfr, int tid) {
+  for (int e = tid; e < K * NW; e += NT) {
+    const int k = e >> 3, f = e & 7;
+    float2* dst = stage + f * SK + first_bin + k;
+    if (r0 + f < nfr && m0 + r0 + f < row)
+      cp_async8(dst, brow + (long long)k * row + r0 + f);
+    else
+      *dst = make_float2(0.f, 0.f);
+  }
+  cp_async_commit();
+}
+
 __global__ void __launch_bounds__(NT, 1) k_ippf(
     const float2* __restrict__ beams, int K, int first_bin, long long F, long long row,
-    int frames_per_cta, const float* __restrict__ g, const float* __restrict__ theta,
-    const float* __restrict__ theta2, float k_sigma, long long n_first, int P, int Tr,
-    float* __restrict__ y, TriggerRec* __restrict__ trig,
-    unsigned long long* __restrict__ trig_count, long long trig_cap) {
+    int frames_per_cta, const float* __restrict__ g, const float2* __restrict__ tw,
+    const float* __restrict__ theta, const float* __restrict__ theta2, float k_sigma,
+    long long n_first, int frame_min_trigger, int P, int Tr, float* __restrict__ y,
+    TriggerRec* __restrict__ trig, unsigned long long* __restrict__ trig_count,
+    long long trig_cap) {
   extern __shared__ float2 smem[];
-  float2* ring = smem;                      // [RING][1024]
-  float2* stage = ring + RING * kM;         // [NW][SK]
-  float2* tw = stage + NW * SK;             // [32 p1][32 lane]
+  float2* ring = smem;                      // [3 groups][8 frames][1024]
+  float2* stage = ring + RING * kM;         // [8 frames][SK], bins 0..511
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int j = blockIdx.y;
@@ -134,15 +160,12 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   const int nout = (int)(m1 - m0);
   const int nfr = nout + kPrefix;          // frames run through the inverse DFT
   const int nbatch = (nfr + NW - 1) / NW;
+  const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
 
-  for (int i = tid; i < 32 * 32; i += NT) {
-    const int p1 = i >> 5, l = i & 31;
-    float sn, cs;
-    sincospif((float)(p1 * l) / 512.0f, &sn, &cs);
-    tw[i] = make_float2(cs, sn);
-  }
-  // zero the stage rows once: bins outside the selection stay zero
+  // bins outside the selection stay zero for the whole run
   for (int i = tid; i < NW * SK; i += NT) stage[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  stage_batch(stage, brow, K, first_bin, row, m0, 0, nfr, tid);
 
   float gr[PPT][kTaps];
 #pragma unroll
@@ -151,38 +174,25 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     for (int t = 0; t < kTaps; ++t) gr[q][t] = g[t * kM + tid + q * NT];
 
   const float th2 = theta2[j];
-  const float sig = theta[j] / k_sigma;
-  const int pol = j % P, tec = (j / P) % Tr, beam = j / (P * Tr);
-  const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
   float* yj = y ? y + (long long)j * F * kM : nullptr;
 
   for (int bi = 0; bi < nbatch; ++bi) {
     const int r0 = bi * NW;
-    __syncthreads();   // previous batch's FIR is done with the ring and stage
-    // 1. stage the batch: stage[f][k] = beam(frame r0+f, bin first_bin+k)
-    for (int e = tid; e < K * NW; e += NT) {
-      const int k = e / NW, f = e - k * NW;
-      const long long pos = m0 + r0 + f;   // row position of CTA frame r0+f
-      float2 v = make_float2(0.f, 0.f);
-      if (r0 + f < nfr && pos < row) v = brow[(long long)k * row + r0 + f];
-      stage[f * SK + k] = v;
-    }
-    __syncthreads();
-    // 2. inverse DFT of frame r0+warp into its ring slot
+    const int gi = bi % 3;
+    cp_async_wait_all();
+    __syncthreads();   // stage of this batch landed; previous FIR is done with the ring
+    // inverse DFT of frame r0+warp into ring group gi, slot warp
     {
-      const int r = r0 + warp;
-      float2* slot = ring + (r % RING) * kM;
+      float2* slot = ring + (gi * NW + warp) * kM;
+      const float2* st = stage + warp * SK + lane;
       float2 v[32];
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) {
-        const int kk = lane + 32 * k1 - first_bin;
-        v[k1] = (kk >= 0 && kk < K) ? stage[warp * SK + kk] : make_float2(0.f, 0.f);
-      }
+      for (int k1 = 0; k1 < 16; ++k1) v[k1] = st[32 * k1];
       dft32_halfzero(v);                  // v[i] = T[p1 = br5(i)]
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const int p1 = br5(i);
-        const float2 t = tw[p1 * 32 + lane];
+        const float2 t = __ldg(tw + p1 * 32 + lane);
         const float2 a = v[i];
         slot[lane * 32 + (p1 ^ lane)] =
             make_float2(fmaf(a.x, t.x, -a.y * t.y), fmaf(a.x, t.y, a.y * t.x));
@@ -195,32 +205,56 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
 #pragma unroll
       for (int i = 0; i < 32; ++i) slot[lane + 32 * br5(i)] = v[i];
     }
-    __syncthreads();
-    // 3. synthesis FIR + envelope threshold for the batch's output frames
+    __syncthreads();   // ring group gi written; stage consumed
+    if (bi + 1 < nbatch) stage_batch(stage, brow, K, first_bin, row, m0, r0 + NW, nfr, tid);
     if (r0 + NW <= kPrefix) continue;     // history-only batch (uniform)
+
+    // synthesis FIR + envelope threshold for frames r0 .. r0+7.  History frames
+    // r0-15 .. r0-9 sit in group gi+1 (slots 1..7), r0-8 .. r0-1 in group gi+2.
+    const float2* ga = ring + (((gi + 1) % 3) * NW) * kM + tid;
+    const float2* gb = ring + (((gi + 2) % 3) * NW) * kM + tid;
+    const float2* gc = ring + (gi * NW) * kM + tid;
+    unsigned vmask = 0;                    // frames of the batch that are output frames
+#pragma unroll
+    for (int f = 0; f < NW; ++f) {
+      const int r = r0 + f;
+      const long long m = m0 - kPrefix + r;
+      if (r >= kPrefix && r < nfr && m >= frame_min_trigger) vmask |= 1u << f;
+    }
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-      const int p = tid + q * NT;
       float2 zw[kHist + NW];
 #pragma unroll
-      for (int w = 0; w < kHist + NW; ++w) zw[w] = ring[((r0 - kHist + w) % RING) * kM + p];
+      for (int w = 0; w < 7; ++w) zw[w] = ga[(w + 1) * kM + q * NT];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) zw[7 + w] = gb[w * kM + q * NT];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) zw[15 + w] = gc[w * kM + q * NT];
+      float e2v[NW];
+      unsigned hm = 0;
 #pragma unroll
       for (int f = 0; f < NW; ++f) {
-        const int r = r0 + f;
         float ur = 0.f, ui = 0.f;
 #pragma unroll
         for (int t = 0; t < kTaps; ++t) {
           ur = fmaf(gr[q][t], zw[f + kHist - t].x, ur);
           ui = fmaf(gr[q][t], zw[f + kHist - t].y, ui);
         }
-        const bool valid = r >= kPrefix && r < nfr;
-        const long long m = m0 - kPrefix + r;
-        if (valid && yj) yj[m * kM + p] = ur;
-        const float e2 = fmaf(ur, ur, ui * ui);
-        const long long n = n_first + m * kM + p;
-        const bool hit = valid && (e2 > th2) && (n >= 0);
-        const unsigned mask = __ballot_sync(0xffffffffu, hit);
-        if (mask) {
+        if (yj) {
+          const int r = r0 + f;
+          if (r >= kPrefix && r < nfr) yj[(m0 - kPrefix + r) * kM + tid + q * NT] = ur;
+        }
+        e2v[f] = fmaf(ur, ur, ui * ui);
+        hm |= (e2v[f] > th2 ? 1u : 0u) << f;
+      }
+      hm &= vmask;
+      if (__any_sync(0xffffffffu, hm != 0)) {   // rare: compact this phase's hits
+        const int p = tid + q * NT;
+#pragma unroll
+        for (int f = 0; f < NW; ++f) {
+          const bool hit = (hm >> f) & 1u;
+          const unsigned mask = __ballot_sync(0xffffffffu, hit);
+          if (!mask) continue;
           const int leader = __ffs(mask) - 1;
           unsigned long long base = 0;
           if (lane == leader) base = atomicAdd(trig_count, (unsigned long long)__popc(mask));
@@ -229,8 +263,13 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
             const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
             if ((long long)idx < trig_cap) {
               TriggerRec rec;
-              rec.n = n; rec.beam = beam; rec.tec = tec; rec.pol = pol; rec.stream = j;
-              rec.env = sqrtf(e2); rec.sigma = sig;
+              rec.n = n_first + (m0 - kPrefix + r0 + f) * kM + p;
+              rec.pol = j % P;
+              rec.tec = (j / P) % Tr;
+              rec.beam = j / (P * Tr);
+              rec.stream = j;
+              rec.env = sqrtf(e2v[f]);
+              rec.sigma = theta[j] / k_sigma;
               trig[idx] = rec;
             }
           }
@@ -282,7 +321,7 @@ __global__ void k_history_shift(float2* __restrict__ beams, long long rows, long
   beams[r * row + f] = beams[r * row + F + f];
 }
 
-size_t ippf_smem_bytes() { return (size_t)(RING * kM + NW * SK + 32 * 32) * sizeof(float2); }
+size_t ippf_smem_bytes() { return (size_t)(RING * kM + NW * SK) * sizeof(float2); }
 
 }  // namespace
 
@@ -301,9 +340,12 @@ cudaError_t launch_ippf(const lp_plan& p, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_ippf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long n_first = (p.block_index * sh.F - kHist) * (long long)kM;
+  // samples n < 0 (frames m < 15 of the first block) never trigger
+  const int frame_min_trigger = p.block_index == 0 ? kHist : 0;
   k_ippf<<<grid, NT, smem, s>>>(p.buf.beams, sh.K, p.cfg.first_bin, sh.F, sh.row(), fpc, p.buf.g,
-                                p.buf.theta, p.buf.theta2, (float)p.cfg.k_sigma, n_first, sh.P,
-                                sh.Tr, p.buf.y, p.buf.trig, p.buf.trig_count, p.cfg.trigger_cap);
+                                p.buf.tw1024, p.buf.theta, p.buf.theta2, (float)p.cfg.k_sigma,
+                                n_first, frame_min_trigger, sh.P, sh.Tr, p.buf.y, p.buf.trig,
+                                p.buf.trig_count, p.cfg.trigger_cap);
   return cudaGetLastError();
 }
 

@@ -10,7 +10,8 @@
 //    factored form has no cancellation; FP64 keeps phi exact to ~1e-13 cycles.
 //  * Synthesis filter: g[n] = (2/M) M^2 h[n], h the Kaiser-windowed sinc
 //    (beta = 9, zeros every M samples) normalised to sum 1; the factor 2/M is
-//    the analytic inverse FFT's scale folded in.
+//    the analytic inverse FFT's scale folded in.  The same set-up kernel
+//    writes the 32 x 32 twiddles exp(+2 pi i p1 l / 1024) of the inverse DFT.
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -31,7 +32,8 @@ __device__ double bessel_i0_series(double x) {
 // One block of 1024 threads builds the whole 16384-tap filter deterministically.
 __global__ void __launch_bounds__(1024) k_prototype(double beta, double* __restrict__ proto,
                                                     double* __restrict__ sums,
-                                                    float* __restrict__ g) {
+                                                    float* __restrict__ g,
+                                                    float2* __restrict__ tw1024) {
   constexpr int L = kM * kTaps;
   __shared__ double red_h[1024];
   __shared__ double red_h2[1024];
@@ -64,6 +66,13 @@ __global__ void __launch_bounds__(1024) k_prototype(double beta, double* __restr
   }
   const double scale = 2.0 * kM / total;   // (2/M) * M^2 / sum(h)
   for (int n = threadIdx.x; n < L; n += blockDim.x) g[n] = (float)(proto[n] * scale);
+  // twiddles of the 32 x 32 inverse DFT: tw[p1][l] = exp(+2 pi i p1 l / 1024)
+  {
+    const int i = threadIdx.x;
+    double sn, cs;
+    sincospi((double)((i >> 5) * (i & 31)) / 512.0, &sn, &cs);
+    tw1024[i] = make_float2((float)cs, (float)sn);
+  }
 }
 
 __global__ void k_weights(const double* __restrict__ enu, const double* __restrict__ dir,
@@ -104,7 +113,8 @@ __global__ void k_dedisp(const double* __restrict__ tec, int K, int Tr, int firs
 }  // namespace
 
 cudaError_t launch_prototype(const lp_plan& p, cudaStream_t s) {
-  k_prototype<<<1, 1024, 0, s>>>(p.cfg.kaiser_beta, p.buf.proto, p.buf.filter_sums, p.buf.g);
+  k_prototype<<<1, 1024, 0, s>>>(p.cfg.kaiser_beta, p.buf.proto, p.buf.filter_sums, p.buf.g,
+                                 p.buf.tw1024);
   return cudaGetLastError();
 }
 
