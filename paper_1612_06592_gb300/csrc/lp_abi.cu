@@ -64,6 +64,7 @@ size_t carve(lp_plan& p, char* base) {
   b.theta = (float*)take(sizeof(float) * J);
   b.theta2 = (float*)take(sizeof(float) * J);
   b.trig_count = (unsigned long long*)take(sizeof(unsigned long long));
+  b.err = (int*)take(sizeof(int));
   b.trig = (lp::TriggerRec*)take(sizeof(lp::TriggerRec) * (size_t)p.cfg.trigger_cap);
   b.y = p.cfg.store_timeseries ? (float*)take(sizeof(float) * (size_t)J * sh.F * kM) : nullptr;
   const size_t in_bytes = (size_t)sh.P * sh.K * sh.F * sh.S * 2 *
@@ -93,6 +94,12 @@ lp_status set_device(lp_plan* p) {
 lp_status sync_last(lp_plan* p) {
   LP_CUDA(p, cudaStreamSynchronize(p->last_stream));
   LP_CUDA(p, cudaGetLastError());
+  int err = 0;
+  LP_CUDA(p, cudaMemcpy(&err, p->buf.err, sizeof err, cudaMemcpyDeviceToHost));
+  if (err) {
+    LP_CUDA(p, cudaMemset(p->buf.err, 0, sizeof err));
+    return fail(p, LP_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core beamformer)");
+  }
   return LP_OK;
 }
 
@@ -159,6 +166,8 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
     return fail(p, LP_ERR_ARG, "precision must be LP_PREC_FP32 or LP_PREC_FP16");
   if (c->precision == LP_PREC_FP16 && c->input_dtype != LP_INPUT_INT8)
     return fail(p, LP_ERR_ARG, "the FP16 tensor-core form takes int8 input only");
+  if (c->precision == LP_PREC_FP16 && sh.S % 4 != 0)
+    return fail(p, LP_ERR_ARG, "the FP16 tensor-core form needs a multiple of 4 stations");
   if (c->first_bin < 1 || c->first_bin + sh.K > lp::kBins)
     return fail(p, LP_ERR_ARG, "bins [%d, %d) must lie inside [1, 512)", c->first_bin,
                 c->first_bin + sh.K);
@@ -237,6 +246,7 @@ lp_status lp_set_weights(lp_plan* p, const double* enu, const double* dir, void*
   LP_CUDA(p, cudaMemcpyAsync(p->buf.beam_dir, dir, sizeof(double) * 3 * sh.B,
                              cudaMemcpyHostToDevice, s));
   LP_CUDA(p, lp::launch_weights(*p, s));
+  if (p->cfg.precision == LP_PREC_FP16) LP_CUDA(p, lp::launch_weights_tc(*p, s));
   p->last_stream = s;
   p->weights_set = true;
   return LP_OK;
@@ -278,7 +288,8 @@ lp_status lp_process_block(lp_plan* p, const void* x, void* stream) {
   } else if (attr.device != p->device) {
     return fail(p, LP_ERR_ARG, "input lives on device %d, plan on %d", attr.device, p->device);
   }
-  const size_t align = p->cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4;
+  const size_t align = p->cfg.precision == LP_PREC_FP16 ? 8
+                       : p->cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4;
   if (reinterpret_cast<uintptr_t>(xd) % align)
     return fail(p, LP_ERR_ARG, "input must be %zu-byte aligned", align);
   LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));

@@ -51,6 +51,7 @@ struct Buffers {
   TriggerRec* trig;        // [trigger_cap]
   float* y;                // [J][F*M] or null
   void* staging;           // one block of input or null
+  int* err;                // device error word: 1 = a bounded wait gave up
 };
 
 struct Shape {
@@ -92,6 +93,7 @@ namespace lp {
 // ---- kernel launchers (each returns the cudaError of the launch) ----------
 cudaError_t launch_prototype(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_weights(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_weights_tc(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_dedisp(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, cudaStream_t s);
 cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, cudaStream_t s);

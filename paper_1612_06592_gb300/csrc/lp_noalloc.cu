@@ -108,6 +108,7 @@ extern "C" lp_status lp_process_block_noalloc(
   size_t o_th = off;  off = up256(off + sizeof(float) * J);
   size_t o_t2 = off;  off = up256(off + sizeof(float) * J);
   size_t o_tc = off;  off = up256(off + sizeof(unsigned long long));
+  size_t o_er = off;  off = up256(off + sizeof(int));
   if (off > (size_t)LP_NOALLOC_SCRATCH_BYTES) {
     snprintf(msg, sizeof msg,
              "this shape needs %zu bytes of scratch; the static buffer holds %zu bytes",
@@ -147,6 +148,7 @@ extern "C" lp_status lp_process_block_noalloc(
   buf.trig = reinterpret_cast<lp::TriggerRec*>(triggers);
   buf.y = y;
   buf.staging = nullptr;
+  buf.err = (int*)(b + o_er);
   p.device = dev;
   p.block_index = 0;
 

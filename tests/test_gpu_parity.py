@@ -10,8 +10,8 @@ import pytest
 
 import oracle as O
 import synth
-from gpu_common import (TAU_FP32, TOL_TS_FP32, compare_triggers, gpu_blocks, make_plan,
-                        oracle_blocks, random_case, rel_rms)
+from gpu_common import (TAU_FP16, TAU_FP32, TOL_TS_FP16, TOL_TS_FP32, compare_triggers,
+                        gpu_blocks, make_plan, oracle_blocks, random_case, rel_rms)
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +42,46 @@ def test_fp32_path_matches_oracle(cuda_lib, case):
         np.testing.assert_allclose(gb["sigma"], ob["sigma"], rtol=1e-5)
         ng, no, nd, bad = compare_triggers(gb["trig"], ob, P, Tr, TAU_FP32)
         assert not bad, bad[:5]
+
+
+FP16_CASES = [
+    # S, P, K, B, Tr, F, first_bin, nblocks: int8 input, tensor-core beamformer
+    (4, 2, 8, 3, 1, 256, 200, 2),
+    (48, 2, 12, 50, 1, 600, 100, 2),              # 50 beams, ragged 256-frame tile
+    (8, 1, 5, 70, 2, 2104, 300, 1),               # two beam tiles, two 2048-frame chunks
+    (64, 2, 3, 64, 1, 72, 12, 1),                 # 64 stations (K = 128), exactly one tile
+    (12, 1, 2, 1, 3, 40, 450, 2),                 # one beam, three trials, tiny block
+]
+
+
+@pytest.mark.parametrize("case", FP16_CASES, ids=lambda c: "S%d_P%d_K%d_B%d_T%d_F%d_b%d_x%d" % c)
+def test_fp16_tensor_core_path_matches_oracle(cuda_lib, case):
+    S, P, K, B, Tr, F, fb, nb = case
+    blocks, enu, dirs, tec = random_case(31, S, P, K, B, Tr, F, fb, "int8", nb, amp=127)
+    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision="fp16",
+                     store_timeseries=True, frames_per_cta=64 if F >= 64 else 8, k_sigma=4.0)
+    g = gpu_blocks(cuda_lib, plan, blocks, enu, dirs, tec)
+    _, o = oracle_blocks(S, P, K, B, Tr, F, fb, blocks, enu, dirs, tec, k_sigma=4.0)
+    for gb, ob in zip(g, o):
+        eb = rel_rms(gb["beams"], ob["beams"].transpose(0, 2, 1))
+        ey = rel_rms(gb["y"], ob["y"])
+        # hi/lo FP16 weights keep the beams near FP32 accuracy
+        assert eb < 1e-5, eb
+        assert ey < TOL_TS_FP16 and ey < 1e-5, ey
+        np.testing.assert_allclose(gb["sigma"], ob["sigma"], rtol=1e-5)
+        ng, no, nd, bad = compare_triggers(gb["trig"], ob, P, Tr, TAU_FP16)
+        assert not bad, bad[:5]
+
+
+def test_fp16_and_fp32_forms_agree(cuda_lib):
+    S, P, K, B, Tr, F, fb = 16, 2, 20, 9, 2, 512, 250
+    blocks, enu, dirs, tec = random_case(32, S, P, K, B, Tr, F, fb, "int8", 1, amp=100)
+    ys = []
+    for prec in ("fp32", "fp16"):
+        plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision=prec,
+                         store_timeseries=True)
+        ys.append(gpu_blocks(cuda_lib, plan, blocks, enu, dirs, tec)[0]["y"])
+    assert rel_rms(ys[1], ys[0]) < 2e-6
 
 
 def test_many_triggers_compaction(cuda_lib):
