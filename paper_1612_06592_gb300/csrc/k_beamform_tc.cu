@@ -15,12 +15,14 @@
 // A persistent grid of 2 blocks per SM walks contiguous item ranges, so the
 // A tiles (hi and lo, 128 x 2S FP16 each, pre-arranged by k_weights_tc) are
 // loaded once per (k, beam tile).  Per 256-frame tile: 128 threads convert the
-// int8 samples (256 frames x 2S contiguous bytes) into the canonical K-major,
+// int8 samples (256 frames x 2S contiguous bytes, fetched into registers while
+// the previous tile's MMA and epilogue ran) into the canonical K-major,
 // no-swizzle FP16 layout (8-row x 16-byte core matrices), one thread issues
 // 2 * 2S/16 tcgen05.mma (M = 128, N = 256, K = 16, FP32 accumulator in 256
-// TMEM columns) and commits to an mbarrier; then the four warps read their
-// 32 TMEM lanes with tcgen05.ld, pair Re/Im lanes by shuffle, multiply by
-// D[k,t] and write 64-byte runs of the [stream][k][frame] beam rows.
+// TMEM columns) and commits to an mbarrier; then the eight warps (two per
+// 32-lane TMEM quarter, one per column half) read TMEM with tcgen05.ld, pair
+// Re/Im lanes by shuffle, multiply by D[k,t] and write 64-byte runs of the
+// [stream][k][frame] beam rows.
 // Every mbarrier wait is bounded: on timeout the block raises the device
 // error word, frees its TMEM and returns.
 #include "lp_internal.cuh"
@@ -28,12 +30,13 @@
 namespace lp {
 namespace {
 
-constexpr int NT = 128;          // threads per block (4 warps = 128 TMEM lanes)
+constexpr int NT = 256;          // threads per block: 2 warps per 32-lane TMEM quarter
 constexpr int TM = 128;          // M rows per tile: 64 beams x (re, im)
 constexpr int TN = 256;          // frames per MMA tile
 constexpr int CHUNK = 2048;      // frames per work item (one noise partial sum)
 constexpr int TMEM_COLS = 256;
 constexpr long long WAIT_LIMIT = 1LL << 22;   // bounded mbarrier polls
+constexpr int MAXR = TN * 16 / NT;             // prefetch entries per thread (2S <= 128)
 
 __host__ __device__ constexpr int kpad(int S) { return (2 * S + 15) / 16 * 16; }
 
@@ -159,7 +162,7 @@ struct TcArgs {
   long long n_items;
 };
 
-__global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a) {
+__global__ void __launch_bounds__(NT, 2) k_beamform_tc(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int KP = kpad(a.S);
   const int nkg = KP / 8;
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a) {
   unsigned char* sb = smem + 2 * a_bytes;
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
+  __shared__ float pw_half[2][TM / 2];   // noise partials of the two column halves
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tmem_alloc(&tmem_base, TMEM_COLS);
@@ -179,23 +183,52 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a) {
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = idesc_f16(TM, TN);
   uint32_t phase = 0;
-  bool failed = false;
 
   const long long per = (a.n_items + gridDim.x - 1) / gridDim.x;
   const long long it0 = blockIdx.x * per;
   const long long it1 = min(a.n_items, it0 + per);
   long long cur_km = -1;
 
-  // row of this thread in the accumulator: beam-in-tile rb, component comp
-  const int trow = warp * 32 + lane;
+  // accumulator row of this thread (TMEM lane quarter warp & 3) and the half
+  // of the 256 columns it drains (warp >> 2); beam-in-tile rb, Re/Im = lane & 1
+  const int quarter = warp & 3, col_half = warp >> 2;
+  const int trow = quarter * 32 + lane;
   const int rb = trow >> 1;
+  const bool odd = lane & 1;
 
-  for (long long it = it0; it < it1 && !failed; ++it) {
+  // Samples of the next tile, loaded into registers while the current tile's
+  // MMA and epilogue run: 8 int8 (one core-matrix row) per entry.
+  uint2 q[MAXR];
+  auto prefetch = [&](long long it, long long n0) {
+    const int chunk = (int)(it % a.n_chunks);
+    const int pol = (int)((it / a.n_chunks) % a.P);
+    const int k = (int)((it / ((long long)a.n_chunks * a.P)) / a.n_mt);
+    const long long f_hi = min(a.F, (long long)(chunk + 1) * CHUNK);
+    const int nvalid = (int)min((long long)TN, f_hi - n0);
+    const int8_t* xk = a.x + (((long long)pol * a.K + k) * a.F + n0) * (2LL * a.S);
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+      const int e = tid + NT * r;
+      const int c = e / TN, n = e - c * TN;   // 8 consecutive threads: 8 rows
+      q[r] = make_uint2(0, 0);
+      if (e < TN * nkg && n < nvalid && 8 * c < 2 * a.S)
+        q[r] = __ldg(reinterpret_cast<const uint2*>(xk + n * (2LL * a.S) + 8 * c));
+    }
+  };
+
+  long long it = it0;
+  long long n0 = it < it1 ? (long long)(it % a.n_chunks) * CHUNK : 0;
+  if (it < it1) prefetch(it, n0);
+  float pw = 0.f;
+  while (it < it1) {
     const int chunk = (int)(it % a.n_chunks);
     const int pol = (int)((it / a.n_chunks) % a.P);
     const long long km = it / ((long long)a.n_chunks * a.P);
     const int mt = (int)(km % a.n_mt);
     const int k = (int)(km / a.n_mt);
+    const long long f_hi = min(a.F, (long long)(chunk + 1) * CHUNK);
+    const int b = mt * (TM / 2) + rb;
+    const bool beam_ok = b < a.B;
     if (km != cur_km) {
       // A images of (k, mt): 2 * a_bytes contiguous bytes -> shared memory
       const uint4* src = reinterpret_cast<const uint4*>(a.wtc + km * 2 * (long long)TM * KP);
@@ -203,87 +236,90 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a) {
       for (uint32_t i = tid; i < 2 * a_bytes / 16; i += NT) dst[i] = src[i];
       cur_km = km;
     }
-    const int b = mt * (TM / 2) + rb;
-    const bool beam_ok = b < a.B;
-    float pw = 0.f;
-    const long long f_lo = (long long)chunk * CHUNK;
-    const long long f_hi = min(a.F, f_lo + CHUNK);
-    const int8_t* xk = a.x + (((long long)pol * a.K + k) * a.F) * (2LL * a.S);
-    for (long long n0 = f_lo; n0 < f_hi; n0 += TN) {
-      // 1. int8 tile -> FP16 K-major core-matrix layout
-      const int nvalid = (int)min((long long)TN, f_hi - n0);
-      for (int e = tid; e < TN * nkg; e += NT) {
-        const int c = e / TN, n = e - c * TN;   // 8 consecutive threads: 8 rows
-        uint4 h8 = make_uint4(0, 0, 0, 0);
-        if (n < nvalid && 8 * c < 2 * a.S) {
-          const uint2 q = *reinterpret_cast<const uint2*>(xk + (n0 + n) * (2LL * a.S) + 8 * c);
-          const char4 lo4 = *reinterpret_cast<const char4*>(&q.x);
-          const char4 hi4 = *reinterpret_cast<const char4*>(&q.y);
-          __half2 p0 = __floats2half2_rn((float)lo4.x, (float)lo4.y);
-          __half2 p1 = __floats2half2_rn((float)lo4.z, (float)lo4.w);
-          __half2 p2 = __floats2half2_rn((float)hi4.x, (float)hi4.y);
-          __half2 p3 = __floats2half2_rn((float)hi4.z, (float)hi4.w);
-          h8 = make_uint4(*reinterpret_cast<uint32_t*>(&p0), *reinterpret_cast<uint32_t*>(&p1),
-                          *reinterpret_cast<uint32_t*>(&p2), *reinterpret_cast<uint32_t*>(&p3));
-        }
-        *reinterpret_cast<uint4*>(sb + core_off(n, 8 * c, KP)) = h8;
+    // 1. int8 samples -> FP16 K-major core-matrix layout
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+      const int e = tid + NT * r;
+      if (e < TN * nkg) {
+        const int c = e / TN, n = e - c * TN;
+        const char4 lo4 = *reinterpret_cast<const char4*>(&q[r].x);
+        const char4 hi4 = *reinterpret_cast<const char4*>(&q[r].y);
+        __half2 p0 = __floats2half2_rn((float)lo4.x, (float)lo4.y);
+        __half2 p1 = __floats2half2_rn((float)lo4.z, (float)lo4.w);
+        __half2 p2 = __floats2half2_rn((float)hi4.x, (float)hi4.y);
+        __half2 p3 = __floats2half2_rn((float)hi4.z, (float)hi4.w);
+        *reinterpret_cast<uint4*>(sb + core_off(n, 8 * c, KP)) =
+            make_uint4(*reinterpret_cast<uint32_t*>(&p0), *reinterpret_cast<uint32_t*>(&p1),
+                       *reinterpret_cast<uint32_t*>(&p2), *reinterpret_cast<uint32_t*>(&p3));
       }
-      fence_proxy_async();
-      __syncthreads();
-      // 2. one thread issues the MMAs: hi and lo weights against the same samples
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
-        const uint32_t sbo = nkg * 128;
-        for (int ks = 0; ks < KP / 16; ++ks) {
-          const uint64_t bd = smem_desc(b0 + ks * 256, 128, sbo);
-          mma_f16(tmem, smem_desc(a0 + ks * 256, 128, sbo), bd, idesc, ks > 0 ? 1u : 0u);
-          mma_f16(tmem, smem_desc(a0 + a_bytes + ks * 256, 128, sbo), bd, idesc, 1u);
-        }
-        mma_commit(&mbar);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    // 2. one thread issues the MMAs: hi and lo weights against the same samples
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+      const uint32_t sbo = nkg * 128;
+      for (int ks = 0; ks < KP / 16; ++ks) {
+        const uint64_t bd = smem_desc(b0 + ks * 256, 128, sbo);
+        mma_f16(tmem, smem_desc(a0 + ks * 256, 128, sbo), bd, idesc, ks > 0 ? 1u : 0u);
+        mma_f16(tmem, smem_desc(a0 + a_bytes + ks * 256, 128, sbo), bd, idesc, 1u);
       }
-      // 3. wait for the accumulator (bounded)
-      long long polls = 0;
-      while (!mbar_try_wait(&mbar, phase)) {
-        if (++polls > WAIT_LIMIT) {
-          failed = true;
-          break;
-        }
-      }
-      phase ^= 1u;
-      failed = __syncthreads_or(failed) != 0;   // every thread takes the same branch
-      if (failed) {
-        if (tid == 0) atomicExch(a.err, 1);
+      mma_commit(&mbar);
+    }
+    // 3. next tile's samples into registers (in flight during the MMA and epilogue)
+    long long nit = it, nn0 = n0 + TN;
+    if (nn0 >= f_hi) {
+      nit = it + 1;
+      nn0 = (long long)(nit % a.n_chunks) * CHUNK;
+    }
+    if (nit < it1) prefetch(nit, nn0);
+    // 4. wait for the accumulator (bounded)
+    bool failed = false;
+    long long polls = 0;
+    while (!mbar_try_wait(&mbar, phase)) {
+      if (++polls > WAIT_LIMIT) {
+        failed = true;
         break;
       }
-      tc_fence_after();
-      // 4. epilogue: 16 frames per TMEM load; even lane writes frames 0-7, odd 8-15
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-      for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(lane_addr + c0, r);
-        tmem_ld_wait();
-        float own[16], oth[16];
+    }
+    phase ^= 1u;
+    failed = __syncthreads_or(failed) != 0;   // every thread takes the same branch
+    if (failed) {
+      if (tid == 0) atomicExch(a.err, 1);
+      break;
+    }
+    tc_fence_after();
+    // 5. epilogue: this warp's 128 columns, 32 per TMEM wait; per 16 columns the
+    //    even lane writes frames 0-7 and the odd lane frames 8-15
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + col_half * (TN / 2);
+    const float2 d0 = a.dd[k * a.Tr];
+    for (int c0 = 0; c0 < TN / 2; c0 += 32) {
+      uint32_t r[2][16];
+      tmem_ld16(lane_addr + c0, r[0]);
+      tmem_ld16(lane_addr + c0 + 16, r[1]);
+      tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          own[i] = __uint_as_float(r[i]);
-          oth[i] = __shfl_xor_sync(0xffffffffu, own[i], 1);
-        }
-        const bool odd = lane & 1;
-        const int fbase = c0 + (odd ? 8 : 0);
-        if (beam_ok && n0 + fbase < f_hi) {
+      for (int h = 0; h < 2; ++h) {
+        float recv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)   // even lane sends Re 8-15, odd lane sends Im 0-7
+          recv[i] = __shfl_xor_sync(0xffffffffu,
+                                    __uint_as_float(odd ? r[h][i] : r[h][i + 8]), 1);
+        const long long f0 = n0 + col_half * (TN / 2) + c0 + 16 * h + (odd ? 8 : 0);
+        if (beam_ok && f0 < f_hi) {
           float2 bv[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            // even lane: own = Re, frames 0-7; odd lane: own = Im, frames 8-15
-            bv[i] = odd ? make_float2(oth[i + 8], own[i + 8]) : make_float2(own[i], oth[i]);
-            if (n0 + fbase + i < f_hi) pw = fmaf(bv[i].x, bv[i].x, fmaf(bv[i].y, bv[i].y, pw));
+            bv[i] = odd ? make_float2(recv[i], __uint_as_float(r[h][i + 8]))
+                        : make_float2(__uint_as_float(r[h][i]), recv[i]);
+            if (f0 + i < f_hi) pw = fmaf(bv[i].x, bv[i].x, fmaf(bv[i].y, bv[i].y, pw));
           }
-          const bool full = n0 + fbase + 8 <= f_hi;
+          const bool full = f0 + 8 <= f_hi;
           for (int t = 0; t < a.Tr; ++t) {
-            const float2 d = a.dd[k * a.Tr + t];
+            const float2 d = t == 0 ? d0 : a.dd[k * a.Tr + t];
             const long long j = ((long long)b * a.Tr + t) * a.P + pol;
-            float2* dst = a.beams + (j * a.K + k) * a.row + kPrefix + n0 + fbase;
+            float2* dst = a.beams + (j * a.K + k) * a.row + kPrefix + f0;
             float2 v[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -294,23 +330,31 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a) {
               for (int i = 0; i < 4; ++i)
                 d4[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
             } else {
-              for (int i = 0; i < 8 && n0 + fbase + i < f_hi; ++i) dst[i] = v[i];
+              for (int i = 0; i < 8 && f0 + i < f_hi; ++i) dst[i] = v[i];
             }
           }
         }
       }
-      tc_fence_before();
-      __syncthreads();   // TMEM drained and B tile free before the next tile
     }
-    if (failed) break;
-    // noise partial of this chunk: lanes 2r and 2r+1 hold the two halves of beam rb
-    pw += __shfl_xor_sync(0xffffffffu, pw, 1);
-    if (beam_ok && !(lane & 1)) {
-      for (int t = 0; t < a.Tr; ++t) {
-        const long long j = ((long long)b * a.Tr + t) * a.P + pol;
-        a.power_part[(j * a.K + k) * a.n_chunks + chunk] = pw;
+    tc_fence_before();
+    __syncthreads();   // TMEM drained and B tile free before the next tile
+    if (nit != it) {
+      // noise partial of the finished chunk: lanes 2r, 2r+1 of the two column
+      // halves hold the four parts of beam rb; two-term sums are order-free
+      pw += __shfl_xor_sync(0xffffffffu, pw, 1);
+      if (!odd) pw_half[col_half][rb] = pw;
+      __syncthreads();
+      if (beam_ok && !odd && col_half == 0) {
+        const float tot = pw_half[0][rb] + pw_half[1][rb];
+        for (int t = 0; t < a.Tr; ++t) {
+          const long long j = ((long long)b * a.Tr + t) * a.P + pol;
+          a.power_part[(j * a.K + k) * a.n_chunks + chunk] = tot;
+        }
       }
+      pw = 0.f;
     }
+    it = nit;
+    n0 = nn0;
   }
   tc_fence_before();
   __syncthreads();

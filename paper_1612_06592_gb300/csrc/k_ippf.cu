@@ -1,22 +1,25 @@
 // Inverse polyphase filter bank + envelope trigger (Sec. 2 last paragraph,
 // Sec. 3 second paragraph, Fig. 1), and the per-block noise level.
 //
-// k_ippf: one thread block owns one stream j and a run of output frames
-// [m0, m1).  It walks frames m0-16 .. m1-1 in batches of 8 (one per warp):
+// k_ippf: one thread block (16 warps) owns one stream j and a run of output
+// frames [m0, m1).  It walks frames m0-16 .. m1-1 in batches of 8:
 //   1. the batch's beam bins (8 frames x K bins, frames contiguous per bin
 //      row) are copied into a zero-padded 512-bin stage with cp.async while
 //      the previous batch's FIR runs;
-//   2. each warp takes the 1024-point inverse DFT of one frame,
+//   2. two warps take the 1024-point inverse DFT of one frame,
 //        z[p] = sum_k c[k] exp(+2 pi i k p / 1024),  c nonzero only in the
-//      selected bins (< 512), as 32 x 32: a register-resident 32-point DFT
-//      over k = 32 k1 + lane (upper half of the inputs zero), the twiddle
-//      exp(2 pi i lane p1 / 1024), a transpose through shared memory and a
-//      second 32-point DFT; the result lands in a 24-frame ring in shared
-//      memory (three groups of 8 frames, addressed by group base pointers);
-//   3. every thread owns 4 output phases p and computes, for the 8 new frames,
+//      selected bins (< 512), as 32 x 32: a 32-point DFT over k = 32 k1 + lane
+//      whose inputs 16..31 are zero, the twiddle exp(2 pi i lane p1 / 1024), a
+//      transpose through shared memory and a second 32-point DFT.  Each
+//      32-point DFT is split between the two warps by output parity (two
+//      16-point DFTs of the folded inputs).  z lands in a 24-frame ring in
+//      shared memory (three groups of 8 frames, addressed by group pointers);
+//   3. every thread owns the output phases p = t and p' = 1023 - t, which share
+//      one set of 16 taps (g[n] = g[L-1-n] gives g_t[p'] = g_{15-t}[p]), and
+//      computes for the 8 new frames
 //        u_m[p] = sum_{t<16} g[t M + p] z_{m-t}[p]     (g holds the 2/M scale),
-//      y = Re u (optionally stored), |u|^2 against theta^2; warps vote and
-//      compact the (rare) samples above threshold into the trigger list.
+//      y = Re u (optionally stored) and |u|^2 against theta^2; the warps vote
+//      and compact the (rare) samples above threshold into the trigger list.
 // The first 16 frames of a run only fill the FIR history (16/frames_per_cta
 // of extra inverse DFTs).  FP32 throughout.
 #include "lp_internal.cuh"
@@ -24,14 +27,14 @@
 namespace lp {
 namespace {
 
-constexpr int NT = 256;            // threads per block
-constexpr int NW = NT / 32;        // warps = frames per batch
+constexpr int NT = 512;            // threads per block
+constexpr int NW = NT / 32;        // 16 warps
+constexpr int FB = 8;              // frames per batch (two warps per frame)
 constexpr int RING = 24;           // 3 groups of 8 frames: 15 history + 8 new fit
 constexpr int SK = 516;            // stage row: 512 bins + pad, 2*SK = 8 mod 32 banks
-constexpr int PPT = kM / NT;       // output phases per thread
 
-__host__ __device__ constexpr int br5(int i) {
-  return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
+__host__ __device__ constexpr int br4(int i) {
+  return ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3);
 }
 
 // cos(2 pi e / 32) for any integer e.
@@ -89,33 +92,23 @@ __device__ __forceinline__ float2 rot32_rt(float2 d, int e) {
 }
 #undef LP_ROT_CASE
 
-// Radix-2 decimation-in-frequency stages of a 32-point DFT with kernel
-// exp(+2 pi i k n / 32), from half-size SPAN0 down to 1.  Natural-order
-// input, bit-reversed output: v[i] = X[br5(i)].
-template <int SPAN0>
-__device__ __forceinline__ void dif32_from(float2 (&v)[32]) {
+// 16-point DFT with kernel exp(+2 pi i k n / 16), radix-2 decimation in
+// frequency: natural-order input, bit-reversed output v[i] = X[br4(i)].
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
 #pragma unroll
-  for (int span = SPAN0; span >= 1; span >>= 1) {
+  for (int span = 8; span >= 1; span >>= 1) {
 #pragma unroll
-    for (int start = 0; start < 32; start += 2 * span) {
+    for (int start = 0; start < 16; start += 2 * span) {
 #pragma unroll
       for (int j = 0; j < span; ++j) {
         const float2 a = v[start + j], b = v[start + j + span];
         v[start + j] = make_float2(a.x + b.x, a.y + b.y);
+        // exp(+2 pi i j / (2 span)) = exp(+2 pi i (16 j / span) / 32)
         v[start + j + span] = rot32_rt(make_float2(a.x - b.x, a.y - b.y), j * (16 / span));
       }
     }
   }
 }
-
-// 32-point DFT whose inputs 16..31 are zero: the first stage is a rotation.
-__device__ __forceinline__ void dft32_halfzero(float2 (&v)[32]) {
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j + 16] = rot32_rt(v[j], j);
-  dif32_from<8>(v);
-}
-
-__device__ __forceinline__ void dft32(float2 (&v)[32]) { dif32_from<16>(v); }
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -125,21 +118,178 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+// Barrier for the two warps (64 threads) of one frame.
+__device__ __forceinline__ void pair_sync(int id) {
+  asm volatile("bar.sync %0, 64;\n" ::"r"(id) : "memory");
+}
 
-// Stage the beam bins of CTA frames r0 .. r0+7 into stage[f][first_bin + k]
-// (asynchronous copies; frames outside the run are zeroed).
-__device__ __forceinline__ void stage_batch(float2* stage, const float2* __restrict__ brow, int K,
-                                            int first_bin, long long row, long long m0, int r0,
-                                            int nfr, int tid) {
-  for (int e = tid; e < K * NW; e += NT) {
-    const int k = e >> 3, f = e & 7;
-    float2* dst = stage + f * SK + first_bin + k;
-    if (r0 + f < nfr && m0 + r0 + f < row)
-      cp_async8(dst, brow + (long long)k * row + r0 + f);
+// Staging of the beam bins of CTA frames r0 .. r0+7 into stage[f][first_bin + k]
+// (asynchronous copies).  Thread t always copies frame f = t & 7 of bins
+// k = t/8 + 64 i, so its source and destination advance by constants.
+struct Stager {
+  const float2* src;      // bin t/8, frame t&7 of CTA frame 0
+  float2* dst;            // stage[t&7][first_bin + t/8]
+  long long src_step;     // 64 rows
+  int n;                  // bins this thread copies
+  int f;                  // its frame within the batch
+};
+
+__device__ __forceinline__ Stager make_stager(float2* stage, const float2* brow, int K,
+                                              int first_bin, long long row, int tid) {
+  Stager st;
+  st.f = tid & 7;
+  const int k0 = tid >> 3;
+  st.src = brow + (long long)k0 * row + st.f;
+  st.dst = stage + st.f * SK + first_bin + k0;
+  st.src_step = 64 * row;
+  st.n = k0 < K ? (K - k0 + 63) / 64 : 0;
+  return st;
+}
+
+__device__ __forceinline__ void stage_batch(const Stager& st, long long m0, long long row, int r0,
+                                            int nfr) {
+  const bool live = r0 + st.f < nfr && m0 + r0 + st.f < row;
+  const float2* src = st.src + r0;
+#pragma unroll 4
+  for (int i = 0; i < st.n; ++i) {
+    if (live)
+      cp_async8(st.dst + 64 * i, src + i * st.src_step);
     else
-      *dst = make_float2(0.f, 0.f);
+      st.dst[64 * i] = make_float2(0.f, 0.f);
   }
   cp_async_commit();
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 t) {
+  return make_float2(fmaf(a.x, t.x, -a.y * t.y), fmaf(a.x, t.y, a.y * t.x));
+}
+
+// One warp's half of the 32 x 32 inverse DFT of a frame: HALF = 0 computes
+// the even outputs of both 32-point stages, HALF = 1 the odd ones.
+template <int HALF>
+__device__ __forceinline__ void frame_dft(float2* slot, const float2* st,
+                                          const float2* __restrict__ tw, int lane, int pair_id) {
+  float2 v[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) v[k1] = st[32 * k1];
+  if constexpr (HALF) {
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) v[k1] = rot32_rt(v[k1], k1);
+  }
+  dft16(v);                               // v[i] = T[p1 = 2 br4(i) + HALF]
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int p1 = 2 * br4(i) + HALF;
+    slot[lane * 32 + (p1 ^ lane)] = cmul(v[i], __ldg(tw + p1 * 32 + lane));
+  }
+  pair_sync(pair_id);
+  float2 u[16];
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    const float2 a = slot[k2 * 32 + (lane ^ k2)];
+    const float2 b = slot[(k2 + 16) * 32 + (lane ^ (k2 + 16))];
+    if constexpr (HALF)
+      u[k2] = rot32_rt(make_float2(a.x - b.x, a.y - b.y), k2);
+    else
+      u[k2] = make_float2(a.x + b.x, a.y + b.y);
+  }
+  pair_sync(pair_id);                     // both warps read the slot before it is overwritten
+  dft16(u);                               // u[i] = z[lane + 32 (2 br4(i) + HALF)]
+#pragma unroll
+  for (int i = 0; i < 16; ++i) slot[lane + 32 * (2 * br4(i) + HALF)] = u[i];
+}
+
+// FIR over the batch for one output phase; TAP_REV selects g_{15-t} (the
+// mirror phase).  Fills e2v = |u|^2 and returns its maximum over the batch.
+template <bool TAP_REV, bool WRITE_Y>
+__device__ __forceinline__ float fir_phase(const float (&gq)[kTaps], const float2* ga,
+                                           const float2* gb, const float2* gc, int off,
+                                           float* yrow, unsigned ymask, float (&e2v)[FB]) {
+  float2 zw[kHist + FB];
+#pragma unroll
+  for (int w = 0; w < 7; ++w) zw[w] = ga[(w + 1) * kM + off];
+#pragma unroll
+  for (int w = 0; w < FB; ++w) zw[7 + w] = gb[w * kM + off];
+#pragma unroll
+  for (int w = 0; w < FB; ++w) zw[15 + w] = gc[w * kM + off];
+  float emax = 0.f;
+#pragma unroll
+  for (int f = 0; f < FB; ++f) {
+    float ur = 0.f, ui = 0.f;
+#pragma unroll
+    for (int t = 0; t < kTaps; ++t) {
+      const float gt = TAP_REV ? gq[kTaps - 1 - t] : gq[t];
+      ur = fmaf(gt, zw[f + kHist - t].x, ur);
+      ui = fmaf(gt, zw[f + kHist - t].y, ui);
+    }
+    if constexpr (WRITE_Y) {
+      if ((ymask >> f) & 1u) yrow[f * kM + off] = ur;
+    }
+    e2v[f] = fmaf(ur, ur, ui * ui);
+    emax = fmaxf(emax, e2v[f]);          // frames outside the run are filtered later
+  }
+  return emax;
+}
+
+template <bool WRITE_Y>
+__device__ __forceinline__ void fir_batch(const float (&gq)[kTaps], const float2* ga,
+                                          const float2* gb, const float2* gc, int tid, int lane,
+                                          float* yrow, unsigned ymask, unsigned vmask, float th2,
+                                          long long n_row0, int j, int P, int Tr, float sig,
+                                          TriggerRec* trig, unsigned long long* trig_count,
+                                          long long trig_cap);
+
+__device__ __forceinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmask, float th2,
+                                              int lane, int p, long long n_row0, int j, int P,
+                                              int Tr, float sig, TriggerRec* trig,
+                                              unsigned long long* trig_count, long long trig_cap) {
+#pragma unroll
+  for (int f = 0; f < FB; ++f) {
+    const bool hit = ((vmask >> f) & 1u) && e2v[f] > th2;
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (!mask) continue;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(trig_count, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (hit) {
+      const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
+      if ((long long)idx < trig_cap) {
+        TriggerRec rec;
+        rec.n = n_row0 + (long long)f * kM + p;
+        rec.pol = j % P;
+        rec.tec = (j / P) % Tr;
+        rec.beam = j / (P * Tr);
+        rec.stream = j;
+        rec.env = sqrtf(e2v[f]);
+        rec.sigma = sig;
+        trig[idx] = rec;
+      }
+    }
+  }
+}
+
+template <bool WRITE_Y>
+__device__ __forceinline__ void fir_batch(const float (&gq)[kTaps], const float2* ga,
+                                          const float2* gb, const float2* gc, int tid, int lane,
+                                          float* yrow, unsigned ymask, unsigned vmask, float th2,
+                                          long long n_row0, int j, int P, int Tr, float sig,
+                                          TriggerRec* trig, unsigned long long* trig_count,
+                                          long long trig_cap) {
+  float e2v[FB];
+  {
+    const float em = fir_phase<false, WRITE_Y>(gq, ga, gb, gc, tid, yrow, ymask, e2v);
+    if (__any_sync(0xffffffffu, em > th2))
+      emit_triggers(e2v, vmask, th2, lane, tid, n_row0, j, P, Tr, sig, trig, trig_count,
+                    trig_cap);
+  }
+  {
+    const int p = kM - 1 - tid;
+    const float em = fir_phase<true, WRITE_Y>(gq, ga, gb, gc, p, yrow, ymask, e2v);
+    if (__any_sync(0xffffffffu, em > th2))
+      emit_triggers(e2v, vmask, th2, lane, p, n_row0, j, P, Tr, sig, trig, trig_count,
+                    trig_cap);
+  }
 }
 
 __global__ void __launch_bounds__(NT, 1) k_ippf(
@@ -154,128 +304,70 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   float2* stage = ring + RING * kM;         // [8 frames][SK], bins 0..511
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int fr = warp >> 1, half = warp & 1;   // frame of the batch, output parity
   const int j = blockIdx.y;
   const long long m0 = (long long)blockIdx.x * frames_per_cta;
   const long long m1 = min((long long)(m0 + frames_per_cta), (long long)(F));
   const int nout = (int)(m1 - m0);
   const int nfr = nout + kPrefix;          // frames run through the inverse DFT
-  const int nbatch = (nfr + NW - 1) / NW;
+  const int nbatch = (nfr + FB - 1) / FB;
   const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
 
   // bins outside the selection stay zero for the whole run
-  for (int i = tid; i < NW * SK; i += NT) stage[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < FB * SK; i += NT) stage[i] = make_float2(0.f, 0.f);
   __syncthreads();
-  stage_batch(stage, brow, K, first_bin, row, m0, 0, nfr, tid);
+  const Stager stg = make_stager(stage, brow, K, first_bin, row, tid);
+  stage_batch(stg, m0, row, 0, nfr);
 
-  float gr[PPT][kTaps];
+  float gq[kTaps];                         // taps of phase tid (mirrored for 1023 - tid)
 #pragma unroll
-  for (int q = 0; q < PPT; ++q)
-#pragma unroll
-    for (int t = 0; t < kTaps; ++t) gr[q][t] = g[t * kM + tid + q * NT];
-
+  for (int t = 0; t < kTaps; ++t) gq[t] = g[t * kM + tid];
   const float th2 = theta2[j];
   float* yj = y ? y + (long long)j * F * kM : nullptr;
 
   for (int bi = 0; bi < nbatch; ++bi) {
-    const int r0 = bi * NW;
+    const int r0 = bi * FB;
     const int gi = bi % 3;
     cp_async_wait_all();
     __syncthreads();   // stage of this batch landed; previous FIR is done with the ring
-    // inverse DFT of frame r0+warp into ring group gi, slot warp
+    // inverse DFT of frame r0+fr by warps (2 fr, 2 fr + 1) into ring group gi, slot fr
     {
-      float2* slot = ring + (gi * NW + warp) * kM;
-      const float2* st = stage + warp * SK + lane;
-      float2 v[32];
-#pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) v[k1] = st[32 * k1];
-      dft32_halfzero(v);                  // v[i] = T[p1 = br5(i)]
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int p1 = br5(i);
-        const float2 t = __ldg(tw + p1 * 32 + lane);
-        const float2 a = v[i];
-        slot[lane * 32 + (p1 ^ lane)] =
-            make_float2(fmaf(a.x, t.x, -a.y * t.y), fmaf(a.x, t.y, a.y * t.x));
-      }
-      __syncwarp();
-#pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) v[k2] = slot[k2 * 32 + (lane ^ k2)];
-      __syncwarp();
-      dft32(v);                           // v[i] = z[lane + 32 br5(i)]
-#pragma unroll
-      for (int i = 0; i < 32; ++i) slot[lane + 32 * br5(i)] = v[i];
+      float2* slot = ring + (gi * FB + fr) * kM;
+      const float2* st = stage + fr * SK + lane;
+      if (half)
+        frame_dft<1>(slot, st, tw, lane, 1 + fr);
+      else
+        frame_dft<0>(slot, st, tw, lane, 1 + fr);
     }
     __syncthreads();   // ring group gi written; stage consumed
-    if (bi + 1 < nbatch) stage_batch(stage, brow, K, first_bin, row, m0, r0 + NW, nfr, tid);
-    if (r0 + NW <= kPrefix) continue;     // history-only batch (uniform)
+    if (bi + 1 < nbatch) stage_batch(stg, m0, row, r0 + FB, nfr);
+    if (r0 + FB <= kPrefix) continue;     // history-only batch (uniform)
 
     // synthesis FIR + envelope threshold for frames r0 .. r0+7.  History frames
     // r0-15 .. r0-9 sit in group gi+1 (slots 1..7), r0-8 .. r0-1 in group gi+2.
-    const float2* ga = ring + (((gi + 1) % 3) * NW) * kM + tid;
-    const float2* gb = ring + (((gi + 2) % 3) * NW) * kM + tid;
-    const float2* gc = ring + (gi * NW) * kM + tid;
-    unsigned vmask = 0;                    // frames of the batch that are output frames
+    const float2* ga = ring + (((gi + 1) % 3) * FB) * kM;
+    const float2* gb = ring + (((gi + 2) % 3) * FB) * kM;
+    const float2* gc = ring + (gi * FB) * kM;
+    unsigned vmask = 0;                    // output frames of the batch that may trigger
+    unsigned ymask = 0;                    // output frames of the batch
 #pragma unroll
-    for (int f = 0; f < NW; ++f) {
+    for (int f = 0; f < FB; ++f) {
       const int r = r0 + f;
       const long long m = m0 - kPrefix + r;
-      if (r >= kPrefix && r < nfr && m >= frame_min_trigger) vmask |= 1u << f;
-    }
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      float2 zw[kHist + NW];
-#pragma unroll
-      for (int w = 0; w < 7; ++w) zw[w] = ga[(w + 1) * kM + q * NT];
-#pragma unroll
-      for (int w = 0; w < NW; ++w) zw[7 + w] = gb[w * kM + q * NT];
-#pragma unroll
-      for (int w = 0; w < NW; ++w) zw[15 + w] = gc[w * kM + q * NT];
-      float e2v[NW];
-      unsigned hm = 0;
-#pragma unroll
-      for (int f = 0; f < NW; ++f) {
-        float ur = 0.f, ui = 0.f;
-#pragma unroll
-        for (int t = 0; t < kTaps; ++t) {
-          ur = fmaf(gr[q][t], zw[f + kHist - t].x, ur);
-          ui = fmaf(gr[q][t], zw[f + kHist - t].y, ui);
-        }
-        if (yj) {
-          const int r = r0 + f;
-          if (r >= kPrefix && r < nfr) yj[(m0 - kPrefix + r) * kM + tid + q * NT] = ur;
-        }
-        e2v[f] = fmaf(ur, ur, ui * ui);
-        hm |= (e2v[f] > th2 ? 1u : 0u) << f;
-      }
-      hm &= vmask;
-      if (__any_sync(0xffffffffu, hm != 0)) {   // rare: compact this phase's hits
-        const int p = tid + q * NT;
-#pragma unroll
-        for (int f = 0; f < NW; ++f) {
-          const bool hit = (hm >> f) & 1u;
-          const unsigned mask = __ballot_sync(0xffffffffu, hit);
-          if (!mask) continue;
-          const int leader = __ffs(mask) - 1;
-          unsigned long long base = 0;
-          if (lane == leader) base = atomicAdd(trig_count, (unsigned long long)__popc(mask));
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (hit) {
-            const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
-            if ((long long)idx < trig_cap) {
-              TriggerRec rec;
-              rec.n = n_first + (m0 - kPrefix + r0 + f) * kM + p;
-              rec.pol = j % P;
-              rec.tec = (j / P) % Tr;
-              rec.beam = j / (P * Tr);
-              rec.stream = j;
-              rec.env = sqrtf(e2v[f]);
-              rec.sigma = theta[j] / k_sigma;
-              trig[idx] = rec;
-            }
-          }
-        }
+      if (r >= kPrefix && r < nfr) {
+        ymask |= 1u << f;
+        if (m >= frame_min_trigger) vmask |= 1u << f;
       }
     }
+    const long long m_row0 = m0 - kPrefix + r0;             // frame of batch row 0
+    float* yrow = yj ? yj + m_row0 * kM : nullptr;
+    const long long n_row0 = n_first + m_row0 * kM;
+    if (yrow)
+      fir_batch<true>(gq, ga, gb, gc, tid, lane, yrow, ymask, vmask, th2, n_row0, j, P, Tr,
+                      theta[j] / k_sigma, trig, trig_count, trig_cap);
+    else
+      fir_batch<false>(gq, ga, gb, gc, tid, lane, yrow, ymask, vmask, th2, n_row0, j, P, Tr,
+                       theta[j] / k_sigma, trig, trig_count, trig_cap);
   }
 }
 
@@ -321,7 +413,7 @@ __global__ void k_history_shift(float2* __restrict__ beams, long long rows, long
   beams[r * row + f] = beams[r * row + F + f];
 }
 
-size_t ippf_smem_bytes() { return (size_t)(RING * kM + NW * SK) * sizeof(float2); }
+size_t ippf_smem_bytes() { return (size_t)(RING * kM + FB * SK) * sizeof(float2); }
 
 }  // namespace
 

@@ -39,16 +39,20 @@ __global__ void __launch_bounds__(1024) k_prototype(double beta, double* __restr
   __shared__ double red_h2[1024];
   const double i0b = bessel_i0_series(beta);
   double sh = 0.0, sh2 = 0.0;
-  for (int n = threadIdx.x; n < L; n += blockDim.x) {
+  // the lower half, mirrored: h[L-1-n] = h[n] holds exactly (the synthesis
+  // kernel relies on it to share taps between phases p and M-1-p)
+  for (int n = threadIdx.x; n < L / 2; n += blockDim.x) {
     const double xs = ((double)n - 0.5 * (L - 1)) / kM;
     const double sinc = (xs == 0.0) ? 1.0 : sinpi(xs) / (M_PI * xs);
     const double t = 2.0 * n / (L - 1) - 1.0;
     const double arg = fmax(1.0 - t * t, 0.0);
     const double h = sinc * bessel_i0_series(beta * sqrt(arg)) / i0b;
     proto[n] = h;
-    sh += h;
-    sh2 += h * h;
+    proto[L - 1 - n] = h;
+    sh += 2.0 * h;
+    sh2 += 2.0 * h * h;
   }
+  __syncthreads();
   red_h[threadIdx.x] = sh;
   red_h2[threadIdx.x] = sh2;
   __syncthreads();
