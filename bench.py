@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=16384)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--serve-blocks", type=int, default=32,
+                    help="blocks of the realtime serving leg (p50/p99 latency); 0 skips it")
     ap.add_argument("--frames", type=int, default=0,
                     help="block length override for small profiling cases (not a bench line)")
     return ap.parse_args()
@@ -141,18 +143,7 @@ class ClockSampler:
 
 def device_block(w, seed, device):
     """Seeded synthetic block on the device (rounded Gaussian table lookup)."""
-    import torch
-    g = torch.Generator(device=device)
-    g.manual_seed(seed)
-    table = torch.from_numpy(synth.gaussian_table(w.noise_sigma, w.dtype).astype(np.int16)).to(device)
-    dt = torch.int8 if w.dtype == "int8" else torch.int16
-    x = torch.empty((w.pols, w.subbands, w.block_len, w.stations, 2), dtype=dt, device=device)
-    for pol in range(w.pols):
-        for k in range(w.subbands):
-            idx = torch.randint(0, 65536, (w.block_len, w.stations, 2), generator=g,
-                                device=device, dtype=torch.int32)
-            x[pol, k] = table[idx].to(dt)
-    return x
+    return synth.device_noise_block(w, seed, device)
 
 
 # ------------------------------------------------------------ CPU oracle ---
@@ -208,6 +199,23 @@ def recorded_traffic(kernel_file):
     except (OSError, ValueError, KeyError):
         pass
     return None
+
+
+# ------------------------------------------------------------ ranks --------
+
+def max_over_ranks(values, device=None):
+    """Element-wise maximum over all ranks of a list of timings (the slowest
+    rank sets the whole-job time); works with the nccl and gloo backends."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(world, block_s, ms_step_max):
+    """Realtime factor of N replicas each processing one block per step."""
+    return world * block_s / (ms_step_max / 1e3)
 
 
 # ------------------------------------------------------------ main ---------
@@ -278,9 +286,7 @@ def run_ours(args, rank, world, local_rank):
         e2e = (t_e2e, d2h / args.steps, x.numel() * x.element_size())
 
     if world > 1:
-        t = torch.tensor([ms, e2e[0] if e2e else 0.0], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, t_max_e2e = float(t[0]), float(t[1])
+        ms, t_max_e2e = max_over_ranks([ms, e2e[0] if e2e else 0.0], dev)
         if e2e:
             e2e = (t_max_e2e, e2e[1], e2e[2])
     if rank != 0:
@@ -288,7 +294,7 @@ def run_ours(args, rank, world, local_rank):
 
     block_s = w.block_len * M / FS_HZ
     ms_step = ms / args.steps
-    rtf = world * block_s / (ms_step / 1e3)
+    rtf = whole_job_rate(world, block_s, ms_step)
     synth_ms = stages["synth"] / max(nrec, 1)
     bf_ms = stages["beamform"] / max(nrec, 1)
     samples = w.n_streams * w.block_len * M
@@ -342,6 +348,14 @@ def run_ours(args, rank, world, local_rank):
                        "path": "lp_process_block(pinned host block) + lp_get_triggers"}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, x, min(args.cpu_sample_frames, w.block_len))
+    if args.serve_blocks > 0 and not args.frames:
+        plan.close()
+        del x
+        torch.cuda.empty_cache()
+        from paper_1612_06592_gb300 import serve
+        sargs = serve.build_parser().parse_args(["--blocks", str(args.serve_blocks),
+                                                 "--precision", args.precision])
+        line["serving"] = serve.run(sargs)
     return line
 
 

@@ -77,7 +77,10 @@ typedef struct {
   int32_t host_input;       /* 1: reserve a device copy of one block so that
                                lp_process_block accepts host pointers            */
   int32_t frames_per_cta;   /* synthesis frames per thread block; 0 = automatic */
-  int32_t reserved;
+  int32_t use_graph;        /* 1: lp_process_block replays a captured CUDA graph of the
+                               block's launches (needs a non-default stream; recaptured
+                               when the input address or pol stride changes; not with
+                               profiling) */
 } lp_config;
 
 /* One trigger: envelope sample above k_sigma * sigma of its stream. */
@@ -140,6 +143,14 @@ lp_status lp_set_tec(lp_plan* plan, const double* tec_tecu, void* stream);
  * FFT + synthesis FIR + envelope threshold, history shift.  Triggers of the
  * previous block are discarded. */
 lp_status lp_process_block(lp_plan* plan, const void* x, void* stream);
+
+/* As lp_process_block, for a view of a larger array: pol slab p starts
+ * pol_stride complex samples after slab p-1 (each slab [K][F][S][2]
+ * contiguous).  Used to hand several plans different subband ranges of one
+ * resident station block.  pol_stride must be >= K*F*S (when P = 2) and keep
+ * 8-byte alignment for the FP16 form. */
+lp_status lp_process_block_strided(lp_plan* plan, const void* x, int64_t pol_stride,
+                                   void* stream);
 
 /* Synchronise and copy the triggers of the last processed block to host
  * memory `out` (capacity `cap`, may be NULL when cap == 0), sorted by

@@ -22,8 +22,8 @@ constexpr int BR = 4;          // beams per register block
 
 template <typename T2>
 __global__ void __launch_bounds__(FT) k_beamform_f32(
-    const T2* __restrict__ x, const float2* __restrict__ w, const float2* __restrict__ dd,
-    int S, int P, int K, int B, int Tr, long long F, long long row,
+    const T2* __restrict__ x, long long pol_stride, const float2* __restrict__ w,
+    const float2* __restrict__ dd, int S, int P, int K, int B, int Tr, long long F, long long row,
     float2* __restrict__ beams, float* __restrict__ power_part, int n_ftiles) {
   extern __shared__ float2 smem[];
   float2* xs = smem;                 // [S][FT]
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(FT) k_beamform_f32(
   const bool valid = f < F;
 
   // station samples of this (pol, k) and frame tile -> xs[s][frame]
-  const T2* xk = x + (((long long)pol * K + k) * F + f0) * S;
+  const T2* xk = x + (long long)pol * pol_stride + ((long long)k * F + f0) * S;
   const int nvalid = (int)min((long long)(FT), (long long)(F - f0));
   for (int e = tid; e < FT * S; e += FT) {
     const int fr = e / S, s = e - fr * S;
@@ -107,23 +107,31 @@ __global__ void __launch_bounds__(FT) k_beamform_f32(
 
 int beamform_f32_frame_tile() { return FT; }
 
-cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, cudaStream_t s) {
+
+size_t f32_smem(const Shape& sh) { return (size_t)(sh.S * FT + BC * sh.S) * sizeof(float2); }
+
+cudaError_t init_f32_attributes(const Shape& sh) {
+  cudaError_t e = cudaFuncSetAttribute(k_beamform_f32<char2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32_smem(sh));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_beamform_f32<short2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)f32_smem(sh));
+}
+
+cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_stride,
+                                cudaStream_t s) {
   const auto& sh = p.shape;
   const int ntile = (int)((sh.F + FT - 1) / FT);
   const dim3 grid(ntile, sh.K, sh.P);
-  const size_t smem = (size_t)(sh.S * FT + BC * sh.S) * sizeof(float2);
+  const size_t smem = f32_smem(sh);
   if (p.cfg.input_dtype == LP_INPUT_INT8) {
-    auto kern = k_beamform_f32<char2>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, FT, smem, s>>>((const char2*)x, p.buf.w32, p.buf.dd, sh.S, sh.P, sh.K, sh.B,
-                                sh.Tr, sh.F, sh.row(), p.buf.beams, p.buf.power_part, ntile);
+    k_beamform_f32<char2><<<grid, FT, smem, s>>>((const char2*)x, pol_stride, p.buf.w32, p.buf.dd,
+                                                 sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F, sh.row(),
+                                                 p.buf.beams, p.buf.power_part, ntile);
   } else {
-    auto kern = k_beamform_f32<short2>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, FT, smem, s>>>((const short2*)x, p.buf.w32, p.buf.dd, sh.S, sh.P, sh.K, sh.B,
-                                sh.Tr, sh.F, sh.row(), p.buf.beams, p.buf.power_part, ntile);
+    k_beamform_f32<short2><<<grid, FT, smem, s>>>((const short2*)x, pol_stride, p.buf.w32,
+                                                  p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F,
+                                                  sh.row(), p.buf.beams, p.buf.power_part, ntile);
   }
   return cudaGetLastError();
 }

@@ -151,7 +151,8 @@ __global__ void k_weights_tc(const float2* __restrict__ w32, int K, int B, int S
 }
 
 struct TcArgs {
-  const int8_t* x;          // [P][K][F][S][2]
+  const int8_t* x;          // pol slabs [K][F][S][2], pol_stride complex samples apart
+  long long pol_stride;
   const __half* wtc;        // A images
   const float2* dd;         // [K][Tr]
   float2* beams;            // [J][K][row]
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(NT, 2) k_beamform_tc(const TcArgs a) {
     const int k = (int)((it / ((long long)a.n_chunks * a.P)) / a.n_mt);
     const long long f_hi = min(a.F, (long long)(chunk + 1) * CHUNK);
     const int nvalid = (int)min((long long)TN, f_hi - n0);
-    const int8_t* xk = a.x + (((long long)pol * a.K + k) * a.F + n0) * (2LL * a.S);
+    const int8_t* xk = a.x + 2 * (pol * a.pol_stride + ((long long)k * a.F + n0) * a.S);
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       const int e = tid + NT * r;
@@ -386,10 +387,22 @@ cudaError_t launch_weights_tc(const lp_plan& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, cudaStream_t s) {
+size_t tc_smem(const Shape& sh) {
+  // at least 80 KB so that no more than two blocks (2 x 256 TMEM columns) share an SM
+  return std::max<size_t>((size_t)(2 * TM + TN) * kpad(sh.S) * 2, 80 * 1024);
+}
+
+cudaError_t init_tc_attributes(const Shape& sh) {
+  return cudaFuncSetAttribute(k_beamform_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem(sh));
+}
+
+cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_stride,
+                               cudaStream_t s) {
   const auto& sh = p.shape;
   TcArgs a;
   a.x = static_cast<const int8_t*>(x);
+  a.pol_stride = pol_stride;
   a.wtc = p.buf.wtc;
   a.dd = p.buf.dd;
   a.beams = p.buf.beams;
@@ -405,14 +418,8 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, cudaStream_t s) 
   a.F = sh.F;
   a.row = sh.row();
   a.n_items = (long long)sh.K * a.n_mt * sh.P * a.n_chunks;
-  const int KP = kpad(sh.S);
-  // at least 80 KB so that no more than two blocks (2 x 256 TMEM columns) share an SM
-  const size_t smem = std::max<size_t>((size_t)(2 * TM + TN) * KP * 2, 80 * 1024);
-  cudaError_t e = cudaFuncSetAttribute(k_beamform_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
   const long long grid = std::min<long long>(a.n_items, 2LL * num_sms());
-  k_beamform_tc<<<(unsigned)grid, NT, smem, s>>>(a);
+  k_beamform_tc<<<(unsigned)grid, NT, tc_smem(sh), s>>>(a);
   return cudaGetLastError();
 }
 

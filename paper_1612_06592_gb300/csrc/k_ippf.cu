@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     const float2* __restrict__ beams, int K, int first_bin, long long F, long long row,
     int frames_per_cta, const float* __restrict__ g, const float2* __restrict__ tw,
     const float* __restrict__ theta, const float* __restrict__ theta2, float k_sigma,
-    long long n_first, int frame_min_trigger, int P, int Tr, float* __restrict__ y,
+    const long long* __restrict__ blk, int P, int Tr, float* __restrict__ y,
     TriggerRec* __restrict__ trig, unsigned long long* __restrict__ trig_count,
     long long trig_cap) {
   extern __shared__ float2 smem[];
@@ -324,6 +324,11 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   for (int t = 0; t < kTaps; ++t) gq[t] = g[t * kM + tid];
   const float th2 = theta2[j];
   float* yj = y ? y + (long long)j * F * kM : nullptr;
+  // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
+  // m < 15 of the first block) never trigger
+  const long long bidx = *blk;
+  const long long n_first = (bidx * F - kHist) * (long long)kM;
+  const int frame_min_trigger = bidx == 0 ? kHist : 0;
 
   for (int bi = 0; bi < nbatch; ++bi) {
     const int r0 = bi * FB;
@@ -376,7 +381,8 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
 // s2 = Pi (first block) or (1 - alpha) s2 + alpha Pi; theta = k_sigma sqrt(s2).
 __global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, int n_per_stream,
                                                const double* __restrict__ sums, long long F,
-                                               double alpha, double k_sigma, int first_block,
+                                               double alpha, double k_sigma,
+                                               const long long* __restrict__ blk,
                                                double* __restrict__ sigma2,
                                                float* __restrict__ theta,
                                                float* __restrict__ theta2) {
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, i
     const double m = (double)kM;
     const double g2 = m * m * m * m * sums[1] / (sums[0] * sums[0]);
     const double pi = 2.0 * g2 / (m * m * m) * red[0] / (double)F;
-    const double s2 = first_block ? pi : (1.0 - alpha) * sigma2[j] + alpha * pi;
+    const double s2 = *blk == 0 ? pi : (1.0 - alpha) * sigma2[j] + alpha * pi;
     sigma2[j] = s2;
     const double th = k_sigma * sqrt(s2);
     theta[j] = (float)th;
@@ -403,10 +409,12 @@ __global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, i
   }
 }
 
-// Carry the last 16 frames of every (stream, bin) row into the row prefix.
+// Carry the last 16 frames of every (stream, bin) row into the row prefix and
+// advance the device block counter.
 __global__ void k_history_shift(float2* __restrict__ beams, long long rows, long long F,
-                                long long row) {
+                                long long row, long long* __restrict__ blk) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i == 0) *blk += 1;
   if (i >= rows * kPrefix) return;
   const long long r = i / kPrefix;
   const int f = (int)(i % kPrefix);
@@ -417,6 +425,9 @@ size_t ippf_smem_bytes() { return (size_t)(RING * kM + FB * SK) * sizeof(float2)
 
 }  // namespace
 
+cudaError_t init_f32_attributes(const Shape& sh);
+cudaError_t init_tc_attributes(const Shape& sh);
+
 int ippf_default_frames_per_cta(const Shape& sh) {
   // enough blocks for several waves on 152 SMs, few history frames per block
   long long fpc = 512;
@@ -424,28 +435,27 @@ int ippf_default_frames_per_cta(const Shape& sh) {
   return (int)fpc;
 }
 
+cudaError_t init_ippf_attributes() {
+  return cudaFuncSetAttribute(k_ippf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ippf_smem_bytes());
+}
+
 cudaError_t launch_ippf(const lp_plan& p, cudaStream_t s) {
   const auto& sh = p.shape;
   const int fpc = p.frames_per_cta;
   const dim3 grid((unsigned)((sh.F + fpc - 1) / fpc), (unsigned)sh.J());
-  const size_t smem = ippf_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_ippf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const long long n_first = (p.block_index * sh.F - kHist) * (long long)kM;
-  // samples n < 0 (frames m < 15 of the first block) never trigger
-  const int frame_min_trigger = p.block_index == 0 ? kHist : 0;
-  k_ippf<<<grid, NT, smem, s>>>(p.buf.beams, sh.K, p.cfg.first_bin, sh.F, sh.row(), fpc, p.buf.g,
-                                p.buf.tw1024, p.buf.theta, p.buf.theta2, (float)p.cfg.k_sigma,
-                                n_first, frame_min_trigger, sh.P, sh.Tr, p.buf.y, p.buf.trig,
-                                p.buf.trig_count, p.cfg.trigger_cap);
+  k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(p.buf.beams, sh.K, p.cfg.first_bin, sh.F, sh.row(), fpc,
+                                             p.buf.g, p.buf.tw1024, p.buf.theta, p.buf.theta2,
+                                             (float)p.cfg.k_sigma, p.buf.blk, sh.P, sh.Tr, p.buf.y,
+                                             p.buf.trig, p.buf.trig_count, p.cfg.trigger_cap);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sigma(const lp_plan& p, bool first_block, cudaStream_t s) {
+cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s) {
   const auto& sh = p.shape;
   k_sigma<<<sh.J(), 256, 0, s>>>(p.buf.power_part, sh.K * p.n_ftiles_bf, p.buf.filter_sums, sh.F,
-                                 p.cfg.sigma_alpha, p.cfg.k_sigma, first_block ? 1 : 0,
-                                 p.buf.sigma2, p.buf.theta, p.buf.theta2);
+                                 p.cfg.sigma_alpha, p.cfg.k_sigma, p.buf.blk, p.buf.sigma2,
+                                 p.buf.theta, p.buf.theta2);
   return cudaGetLastError();
 }
 
@@ -453,8 +463,16 @@ cudaError_t launch_history_shift(const lp_plan& p, cudaStream_t s) {
   const auto& sh = p.shape;
   const long long rows = (long long)sh.J() * sh.K;
   const long long n = rows * kPrefix;
-  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, rows, sh.F, sh.row());
+  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, rows, sh.F, sh.row(),
+                                                              p.buf.blk);
   return cudaGetLastError();
+}
+
+cudaError_t init_kernel_attributes(const Shape& sh) {
+  cudaError_t e = init_ippf_attributes();
+  if (e == cudaSuccess) e = init_f32_attributes(sh);
+  if (e == cudaSuccess) e = init_tc_attributes(sh);
+  return e;
 }
 
 }  // namespace lp

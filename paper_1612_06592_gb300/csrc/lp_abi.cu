@@ -65,6 +65,7 @@ size_t carve(lp_plan& p, char* base) {
   b.theta2 = (float*)take(sizeof(float) * J);
   b.trig_count = (unsigned long long*)take(sizeof(unsigned long long));
   b.err = (int*)take(sizeof(int));
+  b.blk = (long long*)take(sizeof(long long));
   b.trig = (lp::TriggerRec*)take(sizeof(lp::TriggerRec) * (size_t)p.cfg.trigger_cap);
   b.y = p.cfg.store_timeseries ? (float*)take(sizeof(float) * (size_t)J * sh.F * kM) : nullptr;
   const size_t in_bytes = (size_t)sh.P * sh.K * sh.F * sh.S * 2 *
@@ -138,6 +139,7 @@ void lp_config_default(lp_config* c) {
   c->store_timeseries = 0;
   c->host_input = 0;
   c->frames_per_cta = 0;
+  c->use_graph = 0;
 }
 
 lp_status lp_plan_create(lp_plan** out, int stations, int pols, int subbands, int beams,
@@ -219,6 +221,7 @@ lp_status lp_plan_bind_workspace(lp_plan* p, void* dev, size_t bytes, void* stre
   p->ws_bytes = bytes;
   carve(*p, static_cast<char*>(dev));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LP_CUDA(p, lp::init_kernel_attributes(p->shape));
   LP_CUDA(p, cudaMemsetAsync(dev, 0, need, s));
   LP_CUDA(p, lp::launch_prototype(*p, s));
   p->last_stream = s;
@@ -269,46 +272,85 @@ lp_status lp_set_tec(lp_plan* p, const double* tec, void* stream) {
 }
 
 lp_status lp_process_block(lp_plan* p, const void* x, void* stream) {
+  if (!p) return LP_ERR_ARG;
+  const auto& sh = p->shape;
+  return lp_process_block_strided(p, x, (int64_t)sh.K * sh.F * sh.S, stream);
+}
+
+lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride, void* stream) {
   if (lp_status st = need_bound(p)) return st;
   if (!p->weights_set || !p->tec_set)
     return fail(p, LP_ERR_STATE, "lp_set_weights and lp_set_tec must precede lp_process_block");
   if (!x) return fail(p, LP_ERR_ARG, "null input");
+  const auto& sh = p->shape;
+  const long long slab = (long long)sh.K * sh.F * sh.S;
+  if (pol_stride < slab && sh.P > 1)
+    return fail(p, LP_ERR_ARG, "pol_stride %lld is smaller than one pol slab (%lld)",
+                (long long)pol_stride, slab);
   if (set_device(p) != LP_OK) return LP_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaPointerAttributes attr;
   LP_CUDA(p, cudaPointerGetAttributes(&attr, x));
   const void* xd = x;
+  long long stride = pol_stride;
+  const size_t bpc = p->cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4;   // bytes per complex sample
   if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
     if (!p->buf.staging)
       return fail(p, LP_ERR_ARG, "host input needs host_input = 1 in the configuration");
     prof_mark(p, LP_STAGE_H2D, 0, s);
-    LP_CUDA(p, cudaMemcpyAsync(p->buf.staging, x, input_bytes(*p), cudaMemcpyHostToDevice, s));
+    for (int pol = 0; pol < sh.P; ++pol)
+      LP_CUDA(p, cudaMemcpyAsync(static_cast<char*>(p->buf.staging) + pol * slab * bpc,
+                                 static_cast<const char*>(x) + pol * pol_stride * bpc, slab * bpc,
+                                 cudaMemcpyHostToDevice, s));
     prof_mark(p, LP_STAGE_H2D, 1, s);
     xd = p->buf.staging;
+    stride = slab;
   } else if (attr.device != p->device) {
     return fail(p, LP_ERR_ARG, "input lives on device %d, plan on %d", attr.device, p->device);
   }
-  const size_t align = p->cfg.precision == LP_PREC_FP16 ? 8
-                       : p->cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4;
-  if (reinterpret_cast<uintptr_t>(xd) % align)
-    return fail(p, LP_ERR_ARG, "input must be %zu-byte aligned", align);
-  LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
-  prof_mark(p, LP_STAGE_BEAMFORM, 0, s);
-  if (p->cfg.precision == LP_PREC_FP16) {
-    LP_CUDA(p, lp::launch_beamform_tc(*p, xd, s));
+  const size_t align = p->cfg.precision == LP_PREC_FP16 ? 8 : bpc;
+  if (reinterpret_cast<uintptr_t>(xd) % align || (stride * bpc) % align)
+    return fail(p, LP_ERR_ARG, "input and pol stride must be %zu-byte aligned", align);
+
+  const bool graph = p->cfg.use_graph && !p->profiling;
+  if (graph && !s) return fail(p, LP_ERR_ARG, "graph mode needs a non-default stream");
+  if (graph && p->graph_exec && p->graph_x == xd && p->graph_stride == stride) {
+    LP_CUDA(p, cudaGraphLaunch(p->graph_exec, s));
   } else {
-    LP_CUDA(p, lp::launch_beamform_f32(*p, xd, s));
+    if (graph) LP_CUDA(p, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
+    prof_mark(p, LP_STAGE_BEAMFORM, 0, s);
+    if (e == cudaSuccess)
+      e = p->cfg.precision == LP_PREC_FP16 ? lp::launch_beamform_tc(*p, xd, stride, s)
+                                           : lp::launch_beamform_f32(*p, xd, stride, s);
+    prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
+    prof_mark(p, LP_STAGE_SIGMA, 0, s);
+    if (e == cudaSuccess) e = lp::launch_sigma(*p, s);
+    prof_mark(p, LP_STAGE_SIGMA, 1, s);
+    prof_mark(p, LP_STAGE_SYNTH, 0, s);
+    if (e == cudaSuccess) e = lp::launch_ippf(*p, s);
+    prof_mark(p, LP_STAGE_SYNTH, 1, s);
+    prof_mark(p, LP_STAGE_SHIFT, 0, s);
+    if (e == cudaSuccess) e = lp::launch_history_shift(*p, s);
+    prof_mark(p, LP_STAGE_SHIFT, 1, s);
+    if (graph) {
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(s, &g);
+      if (e == cudaSuccess) e = ec;
+      if (e == cudaSuccess) {
+        if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+        e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+      }
+      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) {
+        p->graph_x = xd;
+        p->graph_stride = stride;
+        e = cudaGraphLaunch(p->graph_exec, s);
+      }
+    }
+    LP_CUDA(p, e);
   }
-  prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
-  prof_mark(p, LP_STAGE_SIGMA, 0, s);
-  LP_CUDA(p, lp::launch_sigma(*p, p->block_index == 0, s));
-  prof_mark(p, LP_STAGE_SIGMA, 1, s);
-  prof_mark(p, LP_STAGE_SYNTH, 0, s);
-  LP_CUDA(p, lp::launch_ippf(*p, s));
-  prof_mark(p, LP_STAGE_SYNTH, 1, s);
-  prof_mark(p, LP_STAGE_SHIFT, 0, s);
-  LP_CUDA(p, lp::launch_history_shift(*p, s));
-  prof_mark(p, LP_STAGE_SHIFT, 1, s);
   if (p->profiling && p->prof_n < lp_plan::kProfSlots) p->prof_n += 1;
   p->last_stream = s;
   p->block_index += 1;
@@ -390,6 +432,7 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
                              sizeof(float2) * (size_t)sh.J() * sh.K * sh.row(), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.sigma2, 0, sizeof(double) * sh.J(), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
+  LP_CUDA(p, cudaMemsetAsync(p->buf.blk, 0, sizeof(long long), s));
   p->last_stream = s;
   p->block_index = 0;
   return LP_OK;
@@ -397,7 +440,7 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
 
 int lp_launches_per_block(const lp_plan* p) {
   (void)p;
-  return 4;  // beamformer, sigma, synthesis, history shift
+  return 4;  // beamformer, sigma, synthesis, history shift (one graph launch in graph mode)
 }
 
 lp_status lp_profile_enable(lp_plan* p, int enable) {
@@ -428,6 +471,7 @@ lp_status lp_profile_read(lp_plan* p, double* total_ms, int64_t* blocks) {
 
 void lp_plan_destroy(lp_plan* p) {
   if (!p) return;
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (auto& slot : p->prof_ev)
     for (auto& st : slot)
       for (auto& ev : st)

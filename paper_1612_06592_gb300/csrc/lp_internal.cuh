@@ -52,6 +52,7 @@ struct Buffers {
   float* y;                // [J][F*M] or null
   void* staging;           // one block of input or null
   int* err;                // device error word: 1 = a bounded wait gave up
+  long long* blk;          // device block counter (advanced by the history shift)
 };
 
 struct Shape {
@@ -86,6 +87,10 @@ struct lp_plan {
   cudaEvent_t prof_ev[kProfSlots][LP_NUM_STAGES][2] = {};
   bool prof_used[kProfSlots][LP_NUM_STAGES] = {};
   int prof_n = 0;
+  // graph mode (cfg.use_graph): the per-block launch sequence captured once
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* graph_x = nullptr;
+  long long graph_stride = -1;
 };
 
 namespace lp {
@@ -95,11 +100,18 @@ cudaError_t launch_prototype(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_weights(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_weights_tc(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_dedisp(const lp_plan& p, cudaStream_t s);
-cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, cudaStream_t s);
-cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, cudaStream_t s);
-cudaError_t launch_sigma(const lp_plan& p, bool first_block, cudaStream_t s);
+// x: station block, pol slab p at x + p * pol_stride complex samples, each
+// slab [K][F][S] complex samples contiguous
+cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_stride,
+                                cudaStream_t s);
+cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_stride,
+                               cudaStream_t s);
+cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_ippf(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_history_shift(const lp_plan& p, cudaStream_t s);
+
+// Opt-in shared-memory limits of the kernels (per device; call with it current).
+cudaError_t init_kernel_attributes(const Shape& sh);
 
 int beamform_f32_frame_tile();
 int beamform_tc_frame_tile();

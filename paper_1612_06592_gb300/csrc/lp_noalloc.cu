@@ -14,7 +14,7 @@
 //
 // The array is shared by all calls on a device and keeps the last call's
 // contents; the call clears what must start at zero (the history prefix of
-// the beam rows and the trigger counter).  Calls whose GPU work overlaps
+// the beam rows, the block counter and the trigger counter).  Calls whose GPU work overlaps
 // (different streams, or host threads) race on the array and must be
 // serialised by the caller.  The first call on a device looks up the array's
 // device address (cudaGetSymbolAddress, with that device current) and caches
@@ -109,6 +109,7 @@ extern "C" lp_status lp_process_block_noalloc(
   size_t o_t2 = off;  off = up256(off + sizeof(float) * J);
   size_t o_tc = off;  off = up256(off + sizeof(unsigned long long));
   size_t o_er = off;  off = up256(off + sizeof(int));
+  size_t o_bk = off;  off = up256(off + sizeof(long long));
   if (off > (size_t)LP_NOALLOC_SCRATCH_BYTES) {
     snprintf(msg, sizeof msg,
              "this shape needs %zu bytes of scratch; the static buffer holds %zu bytes",
@@ -149,6 +150,7 @@ extern "C" lp_status lp_process_block_noalloc(
   buf.y = y;
   buf.staging = nullptr;
   buf.err = (int*)(b + o_er);
+  buf.blk = (long long*)(b + o_bk);
   p.device = dev;
   p.block_index = 0;
 
@@ -158,8 +160,11 @@ extern "C" lp_status lp_process_block_noalloc(
     const cudaError_t e_ = (call);                                                 \
     if (e_ != cudaSuccess) return report(err, errlen, LP_ERR_CUDA, cudaGetErrorString(e_)); \
   } while (0)
-  // what must start at zero: zero history (beam rows) and the trigger counter
+  // what must start at zero: zero history (beam rows), the block counter (a
+  // first block) and the trigger counter
+  NA_CUDA(lp::init_kernel_attributes(p.shape));
   NA_CUDA(cudaMemsetAsync(buf.beams, 0, o_pp - o_bm, s));
+  NA_CUDA(cudaMemsetAsync(buf.blk, 0, sizeof(long long), s));
   NA_CUDA(cudaMemsetAsync(buf.trig_count, 0, sizeof(unsigned long long), s));
   NA_CUDA(cudaMemcpyAsync(buf.station_enu, station_enu_m, sizeof(double) * 3 * sh.S,
                           cudaMemcpyHostToDevice, s));
@@ -169,8 +174,8 @@ extern "C" lp_status lp_process_block_noalloc(
   NA_CUDA(lp::launch_prototype(p, s));
   NA_CUDA(lp::launch_weights(p, s));
   NA_CUDA(lp::launch_dedisp(p, s));
-  NA_CUDA(lp::launch_beamform_f32(p, x, s));
-  NA_CUDA(lp::launch_sigma(p, true, s));
+  NA_CUDA(lp::launch_beamform_f32(p, x, (long long)sh.K * sh.F * sh.S, s));
+  NA_CUDA(lp::launch_sigma(p, s));
   NA_CUDA(lp::launch_ippf(p, s));
 #undef NA_CUDA
   return LP_OK;

@@ -37,7 +37,7 @@ class lp_config(ctypes.Structure):
         ("store_timeseries", ctypes.c_int32),
         ("host_input", ctypes.c_int32),
         ("frames_per_cta", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
     ]
 
 
@@ -69,6 +69,7 @@ SIGNATURES = {
     "lp_set_weights": (ctypes.c_int, [_P, _P, _P, _P]),
     "lp_set_tec": (ctypes.c_int, [_P, _P, _P]),
     "lp_process_block": (ctypes.c_int, [_P, _P, _P]),
+    "lp_process_block_strided": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "lp_get_triggers": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "lp_get_timeseries": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "lp_get_beams": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
@@ -146,7 +147,7 @@ class Plan:
                  input_dtype="int8", precision="fp32", first_bin=12, k_sigma=6.0,
                  sigma_alpha=0.25, nu_ref_hz=0.0, trigger_cap=1 << 20,
                  store_timeseries=False, host_input=False, frames_per_cta=0,
-                 kaiser_beta=9.0, stream=None, workspace=None):
+                 kaiser_beta=9.0, use_graph=False, stream=None, workspace=None):
         import torch
         self.shape = (stations, pols, subbands, beams, tec_trials, block_len)
         self._h = _P()
@@ -164,6 +165,7 @@ class Plan:
         c.host_input = int(bool(host_input))
         c.frames_per_cta = frames_per_cta
         c.kaiser_beta = kaiser_beta
+        c.use_graph = int(bool(use_graph))
         self.config = c
         self._check(_lib.lp_plan_configure(self._h, ctypes.byref(c)), "lp_plan_configure")
         nbytes = ctypes.c_size_t()
@@ -210,6 +212,12 @@ class Plan:
             raise ValueError(f"block shape {shape} != {(P, K, F, S, 2)}")
         self._check(_lib.lp_process_block(self._h, _ptr(x), _stream_ptr(stream)),
                     "lp_process_block")
+
+    def lp_process_block_strided(self, x, pol_stride, stream=None):
+        """x: tensor whose data_ptr is pol 0 / subband 0 of the view; pol_stride in
+        complex samples."""
+        self._check(_lib.lp_process_block_strided(self._h, _ptr(x), int(pol_stride),
+                                                  _stream_ptr(stream)), "lp_process_block_strided")
 
     def lp_get_triggers(self, cap=None):
         n = ctypes.c_int64()

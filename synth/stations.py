@@ -25,7 +25,7 @@ __all__ = [
     "station_positions", "pointing_enu", "hex_beam_directions", "gaussian_table",
     "noise_slab", "analysis_filter", "forward_ppf", "dispersed_pulse",
     "pulse_amplitude", "pulse_subbands", "Pulse", "make_geometry", "make_block",
-    "SAMPLE_RATE_HZ", "FFT_LEN",
+    "SAMPLE_RATE_HZ", "FFT_LEN", "device_noise_block",
 ]
 
 SAMPLE_RATE_HZ = 200e6
@@ -322,3 +322,21 @@ def make_block(w: Workload, block: int = 0, station_enu=None, beam_dir=None,
                 seg[..., 1] += c.imag
                 x[pol, :, m_lo:m_hi] = np.clip(np.rint(seg), info.min, info.max).astype(w.dtype)
     return x, plist
+
+
+def device_noise_block(w: Workload, seed: int, device):
+    """Seeded noise block [P, K, F, S, 2] generated directly in device memory
+    (PyTorch's generator indexing the same rounded-Gaussian table); for
+    timing runs at full size, where host generation would dominate."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    table = torch.from_numpy(gaussian_table(w.noise_sigma, w.dtype).astype(np.int16)).to(device)
+    dt = torch.int8 if w.dtype == "int8" else torch.int16
+    x = torch.empty((w.pols, w.subbands, w.block_len, w.stations, 2), dtype=dt, device=device)
+    for pol in range(w.pols):
+        for k in range(w.subbands):
+            idx = torch.randint(0, 65536, (w.block_len, w.stations, 2), generator=g,
+                                device=device, dtype=torch.int32)
+            x[pol, k] = table[idx].to(dt)
+    return x

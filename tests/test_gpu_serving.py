@@ -1,0 +1,129 @@
+"""Strided block views, captured-graph mode and the continuous-batching loop.
+
+The serving test runs several sessions of different shapes alone and then
+all together on their own CUDA streams against one resident station block:
+every session's triggers and noise level must be identical (the kernels are
+deterministic, so the mix can change nothing).  A small HBM budget checks that
+admission waits for memory to free up.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import TOL_TS_FP32, gpu_blocks, make_plan, random_case, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_strided_view_equals_contiguous_block(cuda_lib, precision):
+    import torch
+    S, P, Kfull, F, fb0 = 8, 2, 30, 96, 100
+    k0, K, B, Tr = 7, 12, 3, 2
+    blocks, enu, dirs, tec = random_case(41, S, P, Kfull, B, Tr, F, fb0, "int8", 2, amp=100)
+    ys = []
+    for view in (False, True):
+        plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb0 + k0, "int8", precision=precision,
+                         store_timeseries=True, k_sigma=3.0)
+        plan.lp_set_weights(enu, dirs)
+        plan.lp_set_tec(tec)
+        out = []
+        for xb in blocks:
+            if view:
+                full = torch.from_numpy(np.ascontiguousarray(xb)).cuda()
+                flat = full.view(-1)
+                off = k0 * F * S * 2
+                plan.lp_process_block_strided(flat[off:], Kfull * F * S)
+            else:
+                sub = np.ascontiguousarray(xb[:, k0:k0 + K])
+                plan.lp_process_block(torch.from_numpy(sub).cuda())
+            out.append((plan.lp_get_timeseries(2, 1, 1), plan.lp_get_triggers()[0]))
+        ys.append(out)
+    for (ya, ta), (yb, tb) in zip(*ys):
+        np.testing.assert_array_equal(ya, yb)
+        np.testing.assert_array_equal(ta, tb)
+
+
+def test_graph_mode_equals_direct_launches(cuda_lib):
+    import torch
+    S, P, K, B, Tr, F, fb = 8, 2, 20, 4, 2, 128, 210
+    blocks, enu, dirs, tec = random_case(42, S, P, K, B, Tr, F, fb, "int8", 3, amp=100)
+    res = []
+    for graph in (False, True):
+        stream = torch.cuda.Stream()
+        plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision="fp16",
+                         store_timeseries=True, k_sigma=3.0, use_graph=graph, stream=stream)
+        plan.lp_set_weights(enu, dirs, stream=stream)
+        plan.lp_set_tec(tec, stream=stream)
+        xd = torch.empty((P, K, F, S, 2), dtype=torch.int8, device="cuda")
+        out = []
+        for xb in blocks:              # same device address every block: one capture
+            with torch.cuda.stream(stream):
+                xd.copy_(torch.from_numpy(xb))
+            plan.lp_process_block(xd, stream=stream)
+            out.append((plan.lp_get_timeseries(3, 1, 0), plan.lp_get_triggers()[0],
+                        plan.lp_get_sigma()))
+        res.append(out)
+    for a, b in zip(*res):
+        for u, v in zip(a, b):
+            np.testing.assert_array_equal(u, v)
+
+
+def _serve(lp, reqs, budget, enu, grid, blocks, F, n_sub, fb0, S=8):
+    import torch
+    from paper_1612_06592_gb300.serve import Server
+    srv = Server(S, 2, n_sub, fb0, F, enu, grid, budget, precision="fp16", k_sigma=3.5)
+    hosts = [torch.from_numpy(np.ascontiguousarray(b).reshape(-1)).pin_memory() for b in blocks]
+    got = {r.rid: [] for r in reqs}
+    admitted_at = {}
+    for bi, h in enumerate(hosts):
+        for r in reqs:
+            if r.arrival == bi:
+                srv.submit(r)
+        srv.retire()
+        for rid in srv.admit():
+            admitted_at[rid] = bi
+        out = srv.run_block(h)
+        for rid, (trig, n) in out.items():
+            got[rid].append((bi, trig.copy(), srv.active[rid].plan.lp_get_sigma().copy()))
+    return got, admitted_at
+
+
+def test_serving_results_identical_alone_and_in_the_mix(cuda_lib):
+    from paper_1612_06592_gb300.serve import Request
+    S, F, n_sub, fb0 = 8, 256, 40, 150
+    grid = synth.hex_beam_directions(6)
+    enu = synth.station_positions(S, 3)
+    rng = np.random.default_rng(43)
+    blocks = [rng.integers(-90, 91, size=(2, n_sub, F, S, 2)).astype(np.int8) for _ in range(4)]
+    reqs = [Request(0, np.array([0, 2, 5]), 3, 20, np.array([8.0]), 0, 4),
+            Request(1, np.array([1]), 0, 40, np.array([5.0, 12.0, 30.0]), 0, 3),
+            Request(2, np.array([0, 1, 2, 3, 4, 5]), 10, 24, np.array([20.0, 35.0]), 1, 3)]
+    mixed, _ = _serve(cuda_lib, reqs, 1e12, enu, grid, blocks, F, n_sub, fb0)
+    for r in reqs:
+        alone, _ = _serve(cuda_lib, [r], 1e12, enu, grid, blocks, F, n_sub, fb0)
+        assert len(alone[r.rid]) == len(mixed[r.rid]) == r.blocks
+        for (ba, ta, sa), (bm, tm, sm) in zip(alone[r.rid], mixed[r.rid]):
+            assert ba == bm
+            np.testing.assert_array_equal(ta, tm)
+            np.testing.assert_array_equal(sa, sm)
+
+
+def test_serving_admission_waits_for_memory(cuda_lib):
+    from paper_1612_06592_gb300.serve import Request, workspace_bytes
+    S, F, n_sub, fb0 = 8, 128, 30, 150
+    grid = synth.hex_beam_directions(4)
+    enu = synth.station_positions(S, 5)
+    rng = np.random.default_rng(44)
+    blocks = [rng.integers(-90, 91, size=(2, n_sub, F, S, 2)).astype(np.int8) for _ in range(5)]
+    reqs = [Request(0, np.array([0, 1, 2, 3]), 0, 30, np.array([10.0]), 0, 2),
+            Request(1, np.array([0, 1, 2, 3]), 0, 30, np.array([10.0]), 0, 2),
+            Request(2, np.array([0] * 1), 0, 30, np.array([10.0] * 1), 0, 1)]
+    one = workspace_bytes(S, 2, 30, 4, 1, F, fb0, "fp16")
+    got, admitted_at = _serve(cuda_lib, reqs, int(one * 1.5), enu, grid, blocks, F, n_sub, fb0)
+    # only one big session fits: the second waits until the first has finished
+    assert admitted_at[0] == 0 and admitted_at[1] == 2
+    assert len(got[0]) == 2 and len(got[1]) == 2
+    # the small one is queued behind request 1 (arrival order) and runs after it
+    assert admitted_at[2] >= 2
