@@ -11,32 +11,45 @@
 // tensor memory, which keeps the weight error near 1e-7 (one FP16 part alone
 // would leave ~1.5e-4 relative error in the beams).
 //
-// Work items: (subband k, beam tile of 64 beams, pol, chunk of 2048 frames).
-// A persistent grid of 2 blocks per SM walks contiguous item ranges, so the
-// A tiles (hi and lo, 128 x 2S FP16 each, pre-arranged by k_weights_tc) are
-// loaded once per (k, beam tile).  Per 256-frame tile: 128 threads convert the
-// int8 samples (256 frames x 2S contiguous bytes, fetched into registers while
-// the previous tile's MMA and epilogue ran) into the canonical K-major,
-// no-swizzle FP16 layout (8-row x 16-byte core matrices), one thread issues
-// 2 * 2S/16 tcgen05.mma (M = 128, N = 256, K = 16, FP32 accumulator in 256
-// TMEM columns) and commits to an mbarrier; then the eight warps (two per
-// 32-lane TMEM quarter, one per column half) read TMEM with tcgen05.ld, pair
-// Re/Im lanes by shuffle, multiply by D[k,t] and write 64-byte runs of the
-// [stream][k][frame] beam rows.
-// Every mbarrier wait is bounded: on timeout the block raises the device
-// error word, frees its TMEM and returns.
+// Work items: (subband k, beam tile of 64 beams, pol, chunk of 2048 frames),
+// eight 256-frame tiles each.  One persistent block per SM walks a contiguous
+// item range as a warp-specialised pipeline:
+//   warp 0      producer: cp.async.bulk copies of each tile's int8 samples
+//               (256 frames x 2S contiguous bytes) into a ring of stages, and of
+//               the A images (hi and lo weights, pre-arranged by k_weights_tc)
+//               whenever (k, beam tile) changes;
+//   warps 2-5   converters: int8 -> FP16 in the canonical K-major no-swizzle
+//               layout (8-row x 16-byte core matrices), a ring of B stages;
+//   warp 1      MMA: one thread issues 2 * 2S/16 tcgen05.mma (M = 128, N = 256,
+//               K = 16) into one of two 256-column TMEM accumulators and
+//               commits to mbarriers that free the B stage and publish the
+//               accumulator;
+//   warps 6-13  epilogue: two warps per 32-lane TMEM quarter (one per column
+//               half) read the accumulator with tcgen05.ld, pair Re/Im lanes
+//               by shuffle, multiply by D[k,t], write 64-byte runs of the
+//               [stream][k][frame] beam rows, sum |beam|^2 per chunk.
+// The epilogue of tile i, the MMAs of tile i+1, the conversion of tile i+2
+// and the copies of tiles i+3.. overlap.  Every mbarrier wait is bounded and
+// watches a block-wide abort flag: on timeout the block raises the device
+// error word, waits (bounded) for its copies in flight, frees its TMEM and
+// returns.
+#include <cuda.h>
+
 #include "lp_internal.cuh"
 
 namespace lp {
 namespace {
 
-constexpr int NT = 256;          // threads per block: 2 warps per 32-lane TMEM quarter
+constexpr int NT = 448;          // 14 warps: producer, MMA, 4 converters, 8 epilogue
 constexpr int TM = 128;          // M rows per tile: 64 beams x (re, im)
 constexpr int TN = 256;          // frames per MMA tile
 constexpr int CHUNK = 2048;      // frames per work item (one noise partial sum)
-constexpr int TMEM_COLS = 256;
-constexpr long long WAIT_LIMIT = 1LL << 22;   // bounded mbarrier polls
-constexpr int MAXR = TN * 16 / NT;             // prefetch entries per thread (2S <= 128)
+constexpr int TMEM_COLS = 512;   // two 256-column accumulators
+constexpr long long WAIT_LIMIT = 1LL << 24;   // bounded mbarrier polls
+constexpr int W_PROD = 0, W_MMA = 1, W_CONV0 = 2, N_CONV = 4, W_EPI0 = 6, N_EPI = 8;
+constexpr int MAX_S8 = 3, MAX_SB = 2;
+constexpr int STG_BOX = 16 * 128;             // staged output box: 16 beams x 16 frames x 8 B
+constexpr int STG_BYTES = N_EPI * 2 * STG_BOX; // two boxes per epilogue warp
 
 __host__ __device__ constexpr int kpad(int S) { return (2 * S + 15) / 16 * 16; }
 
@@ -150,6 +163,56 @@ __global__ void k_weights_tc(const float2* __restrict__ w32, int K, int B, int S
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1D bulk copy global -> shared, completion counted on `bar` (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// TMA store of one staged box to the beam rows (5-D map [beam][trial][pol][k][frame]).
+__device__ __forceinline__ void tma_store_box(const CUtensorMap* map, const void* src, int frame,
+                                              int k, int pol, int t, int beam) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(frame), "r"(k), "r"(pol), "r"(t), "r"(beam), "r"(smem_u32(src))
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// At most N committed bulk stores may still be reading shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+
+// Bounded wait on an mbarrier phase; gives up when the block aborts.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  long long polls = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (++polls > WAIT_LIMIT) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
 struct TcArgs {
   const int8_t* x;          // pol slabs [K][F][S][2], pol_stride complex samples apart
   long long pol_stride;
@@ -161,204 +224,299 @@ struct TcArgs {
   int S, P, K, B, Tr, n_mt, n_chunks;
   long long F, row;
   long long n_items;
+  int n_s8, n_sb;           // pipeline depths (int8 ring, FP16 ring)
 };
 
-__global__ void __launch_bounds__(NT, 2) k_beamform_tc(const TcArgs a) {
+// The tile sequence every role walks: items [it0, it1), 256-frame tiles each.
+struct TileSeq {
+  long long it, it1, n0, f_hi;
+  int n_chunks, P;
+  long long F;
+  __device__ void start(long long a, long long b, int nc, int p, long long f) {
+    it = a; it1 = b; n_chunks = nc; P = p; F = f;
+    if (it < it1) set_item();
+  }
+  __device__ void set_item() {
+    const long long chunk = it % n_chunks;
+    n0 = chunk * CHUNK;
+    f_hi = min(F, n0 + CHUNK);
+  }
+  __device__ bool valid() const { return it < it1; }
+  __device__ int chunk() const { return (int)(it % n_chunks); }
+  __device__ int pol() const { return (int)((it / n_chunks) % P); }
+  __device__ long long km() const { return it / ((long long)n_chunks * P); }
+  __device__ bool last_of_item() const { return n0 + TN >= f_hi; }
+  __device__ void next() {
+    n0 += TN;
+    if (n0 >= f_hi) {
+      ++it;
+      if (it < it1) set_item();
+    }
+  }
+};
+
+__global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
+                                                       const __grid_constant__ CUtensorMap out_map) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int KP = kpad(a.S);
   const int nkg = KP / 8;
   const uint32_t a_bytes = TM * KP * 2;          // one of hi / lo
   const uint32_t b_bytes = TN * KP * 2;
-  unsigned char* sa = smem;                      // hi, then lo
-  unsigned char* sb = smem + 2 * a_bytes;
-  __shared__ uint64_t mbar;
+  const uint32_t t8_bytes = TN * 2 * a.S;        // int8 tile
+  // output staging boxes, aligned to 1024 bytes of the shared window (128-byte swizzle)
+  unsigned char* stg = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);
+  unsigned char* sa = stg + STG_BYTES;           // A hi, A lo
+  unsigned char* s8 = sa + 2 * a_bytes;          // int8 ring
+  unsigned char* sbuf = s8 + a.n_s8 * t8_bytes;  // FP16 ring
+  __shared__ uint64_t full8[MAX_S8], empty8[MAX_S8], fullB[MAX_SB], emptyB[MAX_SB];
+  __shared__ uint64_t tfull[2], tempty[2], a_full, a_empty;
   __shared__ uint32_t tmem_base;
-  __shared__ float pw_half[2][TM / 2];   // noise partials of the two column halves
+  __shared__ int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tmem_alloc(&tmem_base, TMEM_COLS);
-  if (tid == 0) mbar_init(&mbar, 1);
+  if (tid == 0) {
+    for (int i = 0; i < a.n_s8; ++i) { mbar_init(&full8[i], 1); mbar_init(&empty8[i], 32 * N_CONV); }
+    for (int i = 0; i < a.n_sb; ++i) { mbar_init(&fullB[i], 32 * N_CONV); mbar_init(&emptyB[i], 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 32 * N_EPI); }
+    mbar_init(&a_full, 1);
+    mbar_init(&a_empty, 1);
+    abort_flag = 0;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_f16(TM, TN);
-  uint32_t phase = 0;
+  volatile int* abort_p = &abort_flag;
 
   const long long per = (a.n_items + gridDim.x - 1) / gridDim.x;
   const long long it0 = blockIdx.x * per;
   const long long it1 = min(a.n_items, it0 + per);
-  long long cur_km = -1;
+  TileSeq q;
+  q.start(it0, it1, a.n_chunks, a.P, a.F);
 
-  // accumulator row of this thread (TMEM lane quarter warp & 3) and the half
-  // of the 256 columns it drains (warp >> 2); beam-in-tile rb, Re/Im = lane & 1
-  const int quarter = warp & 3, col_half = warp >> 2;
-  const int trow = quarter * 32 + lane;
-  const int rb = trow >> 1;
-  const bool odd = lane & 1;
-
-  // Samples of the next tile, loaded into registers while the current tile's
-  // MMA and epilogue run: 8 int8 (one core-matrix row) per entry.
-  uint2 q[MAXR];
-  auto prefetch = [&](long long it, long long n0) {
-    const int chunk = (int)(it % a.n_chunks);
-    const int pol = (int)((it / a.n_chunks) % a.P);
-    const int k = (int)((it / ((long long)a.n_chunks * a.P)) / a.n_mt);
-    const long long f_hi = min(a.F, (long long)(chunk + 1) * CHUNK);
-    const int nvalid = (int)min((long long)TN, f_hi - n0);
-    const int8_t* xk = a.x + 2 * (pol * a.pol_stride + ((long long)k * a.F + n0) * a.S);
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) {
-      const int e = tid + NT * r;
-      const int c = e / TN, n = e - c * TN;   // 8 consecutive threads: 8 rows
-      q[r] = make_uint2(0, 0);
-      if (e < TN * nkg && n < nvalid && 8 * c < 2 * a.S)
-        q[r] = __ldg(reinterpret_cast<const uint2*>(xk + n * (2LL * a.S) + 8 * c));
-    }
-  };
-
-  long long it = it0;
-  long long n0 = it < it1 ? (long long)(it % a.n_chunks) * CHUNK : 0;
-  if (it < it1) prefetch(it, n0);
-  float pw = 0.f;
-  while (it < it1) {
-    const int chunk = (int)(it % a.n_chunks);
-    const int pol = (int)((it / a.n_chunks) % a.P);
-    const long long km = it / ((long long)a.n_chunks * a.P);
-    const int mt = (int)(km % a.n_mt);
-    const int k = (int)(km / a.n_mt);
-    const long long f_hi = min(a.F, (long long)(chunk + 1) * CHUNK);
-    const int b = mt * (TM / 2) + rb;
-    const bool beam_ok = b < a.B;
-    if (km != cur_km) {
-      // A images of (k, mt): 2 * a_bytes contiguous bytes -> shared memory
-      const uint4* src = reinterpret_cast<const uint4*>(a.wtc + km * 2 * (long long)TM * KP);
-      uint4* dst = reinterpret_cast<uint4*>(sa);
-      for (uint32_t i = tid; i < 2 * a_bytes / 16; i += NT) dst[i] = src[i];
-      cur_km = km;
-    }
-    // 1. int8 samples -> FP16 K-major core-matrix layout
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) {
-      const int e = tid + NT * r;
-      if (e < TN * nkg) {
-        const int c = e / TN, n = e - c * TN;
-        const char4 lo4 = *reinterpret_cast<const char4*>(&q[r].x);
-        const char4 hi4 = *reinterpret_cast<const char4*>(&q[r].y);
-        __half2 p0 = __floats2half2_rn((float)lo4.x, (float)lo4.y);
-        __half2 p1 = __floats2half2_rn((float)lo4.z, (float)lo4.w);
-        __half2 p2 = __floats2half2_rn((float)hi4.x, (float)hi4.y);
-        __half2 p3 = __floats2half2_rn((float)hi4.z, (float)hi4.w);
-        *reinterpret_cast<uint4*>(sb + core_off(n, 8 * c, KP)) =
-            make_uint4(*reinterpret_cast<uint32_t*>(&p0), *reinterpret_cast<uint32_t*>(&p1),
-                       *reinterpret_cast<uint32_t*>(&p2), *reinterpret_cast<uint32_t*>(&p3));
+  if (warp == W_PROD) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0, aph = 0;
+      long long cur_km = -1;
+      uint32_t issued = 0, last_par = 0;        // per stage: copy issued, its phase parity
+      bool a_issued = false;
+      for (; q.valid(); q.next()) {
+        const long long km = q.km();
+        if (km != cur_km) {
+          if (cur_km >= 0) {
+            if (!wait_phase(&a_empty, aph, abort_p)) break;
+            aph ^= 1u;
+          }
+          mbar_expect_tx(&a_full, 2 * a_bytes);
+          bulk_g2s(sa, a.wtc + km * 2 * (long long)TM * KP, 2 * a_bytes, &a_full);
+          a_issued = true;
+          cur_km = km;
+        }
+        if (!wait_phase(&empty8[st], ph ^ 1u, abort_p)) break;
+        const int k = (int)(km / a.n_mt);
+        const int nvalid = (int)min((long long)TN, q.f_hi - q.n0);
+        const int8_t* src = a.x + 2 * (q.pol() * a.pol_stride + ((long long)k * a.F + q.n0) * a.S);
+        const uint32_t bytes = (uint32_t)nvalid * 2 * a.S;
+        mbar_expect_tx(&full8[st], bytes);
+        bulk_g2s(s8 + st * t8_bytes, src, bytes, &full8[st]);
+        issued |= 1u << st;
+        last_par = (last_par & ~(1u << st)) | (ph << st);
+        if (++st == a.n_s8) { st = 0; ph ^= 1u; }
+      }
+      if (*abort_p) {
+        // let the copies already issued land before the block's memory goes
+        for (int i = 0; i < a.n_s8; ++i) {
+          if (!((issued >> i) & 1u)) continue;
+          long long polls = 0;
+          while (!mbar_try_wait(&full8[i], (last_par >> i) & 1u) && ++polls < WAIT_LIMIT) {
+          }
+        }
+        if (a_issued) {
+          long long polls = 0;
+          // the last A copy completes the a_full phase of parity aph
+          while (!mbar_try_wait(&a_full, aph) && ++polls < WAIT_LIMIT) {
+          }
+        }
       }
     }
-    fence_proxy_async();
-    __syncthreads();
-    // 2. one thread issues the MMAs: hi and lo weights against the same samples
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+  } else if (warp == W_MMA) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int sb = 0, acc = 0;
+      uint32_t phb = 0, pha = 0, aph = 0;
+      long long cur_km = -1;
+      const uint32_t idesc = idesc_f16(TM, TN);
       const uint32_t sbo = nkg * 128;
-      for (int ks = 0; ks < KP / 16; ++ks) {
-        const uint64_t bd = smem_desc(b0 + ks * 256, 128, sbo);
-        mma_f16(tmem, smem_desc(a0 + ks * 256, 128, sbo), bd, idesc, ks > 0 ? 1u : 0u);
-        mma_f16(tmem, smem_desc(a0 + a_bytes + ks * 256, 128, sbo), bd, idesc, 1u);
+      const uint32_t a0 = smem_u32(sa);
+      int last_acc = -1;
+      uint32_t last_par = 0;
+      for (; q.valid(); q.next()) {
+        const long long km = q.km();
+        if (km != cur_km) {
+          if (cur_km >= 0) mma_commit(&a_empty);   // old A free once its MMAs finish
+          if (!wait_phase(&a_full, aph, abort_p)) break;
+          aph ^= 1u;
+          cur_km = km;
+        }
+        if (!wait_phase(&fullB[sb], phb, abort_p)) break;
+        if (!wait_phase(&tempty[acc], pha ^ 1u, abort_p)) break;
+        tc_fence_after();
+        const uint32_t b0 = smem_u32(sbuf + sb * b_bytes);
+        const uint32_t d = tmem + acc * TN;
+        for (int ks = 0; ks < KP / 16; ++ks) {
+          const uint64_t bd = smem_desc(b0 + ks * 256, 128, sbo);
+          mma_f16(d, smem_desc(a0 + ks * 256, 128, sbo), bd, idesc, ks > 0 ? 1u : 0u);
+          mma_f16(d, smem_desc(a0 + a_bytes + ks * 256, 128, sbo), bd, idesc, 1u);
+        }
+        mma_commit(&emptyB[sb]);
+        mma_commit(&tfull[acc]);
+        last_acc = acc;
+        last_par = pha;
+        if (++sb == a.n_sb) { sb = 0; phb ^= 1u; }
+        if (++acc == 2) { acc = 0; pha ^= 1u; }
       }
-      mma_commit(&mbar);
-    }
-    // 3. next tile's samples into registers (in flight during the MMA and epilogue)
-    long long nit = it, nn0 = n0 + TN;
-    if (nn0 >= f_hi) {
-      nit = it + 1;
-      nn0 = (long long)(nit % a.n_chunks) * CHUNK;
-    }
-    if (nit < it1) prefetch(nit, nn0);
-    // 4. wait for the accumulator (bounded)
-    bool failed = false;
-    long long polls = 0;
-    while (!mbar_try_wait(&mbar, phase)) {
-      if (++polls > WAIT_LIMIT) {
-        failed = true;
-        break;
+      if (last_acc >= 0) {
+        // the tensor core must be done with shared and tensor memory before exit
+        long long polls = 0;
+        while (!mbar_try_wait(&tfull[last_acc], last_par) && ++polls < WAIT_LIMIT) {
+        }
       }
     }
-    phase ^= 1u;
-    failed = __syncthreads_or(failed) != 0;   // every thread takes the same branch
-    if (failed) {
-      if (tid == 0) atomicExch(a.err, 1);
-      break;
+  } else if (warp < W_EPI0) {
+    // ---------------- converters (128 threads) ----------------
+    const int ct = tid - W_CONV0 * 32;          // 0..127
+    const int cw = ct >> 5;                     // converter warp 0..3
+    const int n_sub = lane & 7, c_sub = lane >> 3;
+    int st = 0, sb = 0;
+    uint32_t ph = 0, phb = 0;
+    for (; q.valid(); q.next()) {
+      if (!wait_phase(&full8[st], ph, abort_p)) break;
+      if (!wait_phase(&emptyB[sb], phb ^ 1u, abort_p)) break;
+      const unsigned char* src = s8 + st * t8_bytes;
+      unsigned char* dst = sbuf + sb * b_bytes;
+      // a warp converts 8 frames x 4 chunks of 8 samples per step
+      const int nsteps = (TN / 8) * ((nkg + 3) / 4);
+      for (int u = cw; u < nsteps; u += N_CONV) {
+        const int ng = u % (TN / 8), cg = u / (TN / 8);
+        const int n = ng * 8 + n_sub, c = cg * 4 + c_sub;
+        if (c >= nkg) continue;
+        uint4 h8 = make_uint4(0, 0, 0, 0);
+        if (8 * c < 2 * a.S) {
+          const uint2 qv = *reinterpret_cast<const uint2*>(src + n * (2 * a.S) + 8 * c);
+          const char4 lo4 = *reinterpret_cast<const char4*>(&qv.x);
+          const char4 hi4 = *reinterpret_cast<const char4*>(&qv.y);
+          __half2 p0 = __floats2half2_rn((float)lo4.x, (float)lo4.y);
+          __half2 p1 = __floats2half2_rn((float)lo4.z, (float)lo4.w);
+          __half2 p2 = __floats2half2_rn((float)hi4.x, (float)hi4.y);
+          __half2 p3 = __floats2half2_rn((float)hi4.z, (float)hi4.w);
+          h8 = make_uint4(*reinterpret_cast<uint32_t*>(&p0), *reinterpret_cast<uint32_t*>(&p1),
+                          *reinterpret_cast<uint32_t*>(&p2), *reinterpret_cast<uint32_t*>(&p3));
+        }
+        *reinterpret_cast<uint4*>(dst + core_off(n, 8 * c, KP)) = h8;
+      }
+      fence_proxy_async();
+      mbar_arrive(&fullB[sb]);
+      mbar_arrive(&empty8[st]);
+      if (++st == a.n_s8) { st = 0; ph ^= 1u; }
+      if (++sb == a.n_sb) { sb = 0; phb ^= 1u; }
     }
-    tc_fence_after();
-    // 5. epilogue: this warp's 128 columns, 32 per TMEM wait; per 16 columns the
-    //    even lane writes frames 0-7 and the odd lane frames 8-15
-    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + col_half * (TN / 2);
-    const float2 d0 = a.dd[k * a.Tr];
-    for (int c0 = 0; c0 < TN / 2; c0 += 32) {
-      uint32_t r[2][16];
-      tmem_ld16(lane_addr + c0, r[0]);
-      tmem_ld16(lane_addr + c0 + 16, r[1]);
-      tmem_ld_wait();
+  } else {
+    // ---------------- epilogue (256 threads) ----------------
+    const int ew = warp - W_EPI0;               // 0..7
+    const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
+    const int col_half = ew >> 2;
+    const int rb = (quarter * 32 + lane) >> 1;  // beam in tile
+    const bool odd = lane & 1;
+    int acc = 0;
+    uint32_t pha = 0;
+    float pw = 0.f;
+    for (; q.valid(); q.next()) {
+      if (!wait_phase(&tfull[acc], pha, abort_p)) break;
+      tc_fence_after();
+      const int pol = q.pol();
+      const long long km = q.km();
+      const int k = (int)(km / a.n_mt), mt = (int)(km % a.n_mt);
+      const int b = mt * (TM / 2) + rb;
+      const bool beam_ok = b < a.B;
+      const long long f_hi = q.f_hi, n0 = q.n0;
+      const uint32_t lane_addr =
+          tmem + acc * TN + ((uint32_t)(quarter * 32) << 16) + col_half * (TN / 2);
+      const float2 d0 = a.dd[k * a.Tr];
+      const int rloc = lane >> 1;                // beam row inside the warp's 16-beam box
+      for (int c0 = 0; c0 < TN / 2; c0 += 32) {
+        uint32_t r[2][16];
+        tmem_ld16(lane_addr + c0, r[0]);
+        tmem_ld16(lane_addr + c0 + 16, r[1]);
+        tmem_ld_wait();
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float recv[8];
+        for (int h = 0; h < 2; ++h) {
+          float recv[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)   // even lane sends Re 8-15, odd lane sends Im 0-7
-          recv[i] = __shfl_xor_sync(0xffffffffu,
-                                    __uint_as_float(odd ? r[h][i] : r[h][i + 8]), 1);
-        const long long f0 = n0 + col_half * (TN / 2) + c0 + 16 * h + (odd ? 8 : 0);
-        if (beam_ok && f0 < f_hi) {
+          for (int i = 0; i < 8; ++i)   // even lane sends Re 8-15, odd lane sends Im 0-7
+            recv[i] = __shfl_xor_sync(0xffffffffu,
+                                      __uint_as_float(odd ? r[h][i] : r[h][i + 8]), 1);
+          const long long fb = n0 + col_half * (TN / 2) + c0 + 16 * h;   // box's first frame
+          const long long f0 = fb + (odd ? 8 : 0);
           float2 bv[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             bv[i] = odd ? make_float2(recv[i], __uint_as_float(r[h][i + 8]))
                         : make_float2(__uint_as_float(r[h][i]), recv[i]);
-            if (f0 + i < f_hi) pw = fmaf(bv[i].x, bv[i].x, fmaf(bv[i].y, bv[i].y, pw));
+            if (beam_ok && f0 + i < f_hi) pw = fmaf(bv[i].x, bv[i].x, fmaf(bv[i].y, bv[i].y, pw));
           }
-          const bool full = f0 + 8 <= f_hi;
+          if (fb >= f_hi) continue;                 // warp-uniform
+          unsigned char* box = stg + (ew * 2 + h) * STG_BOX;
           for (int t = 0; t < a.Tr; ++t) {
-            const float2 d = t == 0 ? d0 : a.dd[k * a.Tr + t];
-            const long long j = ((long long)b * a.Tr + t) * a.P + pol;
-            float2* dst = a.beams + (j * a.K + k) * a.row + kPrefix + f0;
-            float2 v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              v[i] = make_float2(d.x * bv[i].x - d.y * bv[i].y, d.x * bv[i].y + d.y * bv[i].x);
-            if (full) {
-              float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-                d4[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
-            } else {
-              for (int i = 0; i < 8 && f0 + i < f_hi; ++i) dst[i] = v[i];
+            const float2 dv = t == 0 ? d0 : a.dd[k * a.Tr + t];
+            // the previous store from this box must have read it (with one trial the
+            // other box's store may still be running)
+            if (lane == 0) {
+              if (a.Tr > 1)
+                bulk_wait_read<0>();
+              else
+                bulk_wait_read<1>();
             }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {           // 16-byte chunk c of row rloc, 128B swizzle
+              const float2 u = bv[2 * i], w = bv[2 * i + 1];
+              const int c = (odd ? 4 : 0) + i;
+              *reinterpret_cast<float4*>(box + rloc * 128 + ((c ^ (rloc & 7)) << 4)) =
+                  make_float4(dv.x * u.x - dv.y * u.y, dv.x * u.y + dv.y * u.x,
+                              dv.x * w.x - dv.y * w.y, dv.x * w.y + dv.y * w.x);
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0)
+              tma_store_box(&out_map, box, (int)(kPrefix + fb), k, pol, t,
+                            mt * (TM / 2) + quarter * 16);
           }
         }
       }
-    }
-    tc_fence_before();
-    __syncthreads();   // TMEM drained and B tile free before the next tile
-    if (nit != it) {
-      // noise partial of the finished chunk: lanes 2r, 2r+1 of the two column
-      // halves hold the four parts of beam rb; two-term sums are order-free
-      pw += __shfl_xor_sync(0xffffffffu, pw, 1);
-      if (!odd) pw_half[col_half][rb] = pw;
-      __syncthreads();
-      if (beam_ok && !odd && col_half == 0) {
-        const float tot = pw_half[0][rb] + pw_half[1][rb];
-        for (int t = 0; t < a.Tr; ++t) {
-          const long long j = ((long long)b * a.Tr + t) * a.P + pol;
-          a.power_part[(j * a.K + k) * a.n_chunks + chunk] = tot;
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      if (++acc == 2) { acc = 0; pha ^= 1u; }
+      if (q.last_of_item()) {
+        // noise partial of the chunk and column half: lanes 2r, 2r+1 hold the
+        // two halves of beam rb; k_sigma adds the two column halves
+        pw += __shfl_xor_sync(0xffffffffu, pw, 1);
+        if (beam_ok && !odd) {
+          for (int t = 0; t < a.Tr; ++t) {
+            const long long j = ((long long)b * a.Tr + t) * a.P + pol;
+            a.power_part[(j * a.K + k) * (2LL * a.n_chunks) + 2 * q.chunk() + col_half] = pw;
+          }
         }
+        pw = 0.f;
       }
-      pw = 0.f;
     }
-    it = nit;
-    n0 = nn0;
+    if (lane == 0) bulk_wait_all();     // staged boxes read and written before exit
   }
   tc_fence_before();
   __syncthreads();
+  if (tid == 0 && abort_flag) atomicExch(a.err, 1);
   if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
@@ -372,6 +530,8 @@ int num_sms() {
 }  // namespace
 
 int beamform_tc_frame_tile() { return CHUNK; }
+// noise partials per (stream, subband): two column halves per 2048-frame chunk
+int beamform_tc_partials(long long F) { return 2 * (int)((F + CHUNK - 1) / CHUNK); }
 
 size_t beamform_tc_weight_bytes(const Shape& sh) {
   const int n_mt = (sh.B + TM / 2 - 1) / (TM / 2);
@@ -387,9 +547,57 @@ cudaError_t launch_weights_tc(const lp_plan& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Pipeline depths that fit the 227 KB of shared memory: A (hi + lo), int8
+// stages, FP16 stages.
+void tc_depths(const Shape& sh, int* n_s8, int* n_sb) {
+  const size_t limit = 227 * 1024 - 2048 - STG_BYTES - 1024;
+  const size_t KP = kpad(sh.S);
+  const size_t a = 2 * TM * KP * 2, t8 = (size_t)TN * 2 * sh.S, b = TN * KP * 2;
+  *n_sb = a + 2 * b + t8 <= limit ? 2 : 1;
+  *n_s8 = 1;
+  while (*n_s8 < MAX_S8 && a + *n_sb * b + (*n_s8 + 1) * t8 <= limit) ++*n_s8;
+}
+
+// 5-D map of the beam rows for the epilogue's TMA stores: element = one complex
+// FP32 (8 bytes); dims (frame position, k, pol, trial, beam); box 16 x 1 x 1 x 1 x 16
+// with 128-byte swizzle.
+cudaError_t encode_beams_map(lp_plan& p) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<Encode>(fn);
+  }
+  const auto& sh = p.shape;
+  const cuuint64_t row = (cuuint64_t)sh.row() * 8;
+  const cuuint64_t dims[5] = {(cuuint64_t)sh.row(), (cuuint64_t)sh.K, (cuuint64_t)sh.P,
+                              (cuuint64_t)sh.Tr, (cuuint64_t)sh.B};
+  const cuuint64_t strides[4] = {row, row * sh.K, row * sh.K * sh.P, row * sh.K * sh.P * sh.Tr};
+  const cuuint32_t box[5] = {16, 1, 1, 1, 16};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = encode(reinterpret_cast<CUtensorMap*>(p.beams_map),
+                            CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, p.buf.beams, dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 size_t tc_smem(const Shape& sh) {
-  // at least 80 KB so that no more than two blocks (2 x 256 TMEM columns) share an SM
-  return std::max<size_t>((size_t)(2 * TM + TN) * kpad(sh.S) * 2, 80 * 1024);
+  int n8, nb;
+  tc_depths(sh, &n8, &nb);
+  const size_t KP = kpad(sh.S);
+  // at least 120 KB: one block per SM (it takes all 512 TMEM columns)
+  return std::max<size_t>(1024 + STG_BYTES + 2 * TM * KP * 2 + (size_t)n8 * TN * 2 * sh.S +
+                              (size_t)nb * TN * KP * 2,
+                          120 * 1024);
 }
 
 cudaError_t init_tc_attributes(const Shape& sh) {
@@ -418,8 +626,10 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_st
   a.F = sh.F;
   a.row = sh.row();
   a.n_items = (long long)sh.K * a.n_mt * sh.P * a.n_chunks;
-  const long long grid = std::min<long long>(a.n_items, 2LL * num_sms());
-  k_beamform_tc<<<(unsigned)grid, NT, tc_smem(sh), s>>>(a);
+  tc_depths(sh, &a.n_s8, &a.n_sb);
+  const long long grid = std::min<long long>(a.n_items, (long long)num_sms());
+  k_beamform_tc<<<(unsigned)grid, NT, tc_smem(sh), s>>>(
+      a, *reinterpret_cast<const CUtensorMap*>(p.beams_map));
   return cudaGetLastError();
 }
 

@@ -185,9 +185,10 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
     return fail(p, LP_ERR_ARG, "frames_per_cta must be 0 or a positive multiple of 8");
   p->cfg = *c;
   p->frames_per_cta = c->frames_per_cta ? c->frames_per_cta : lp::ippf_default_frames_per_cta(sh);
-  const int ft = c->precision == LP_PREC_FP16 ? lp::beamform_tc_frame_tile()
-                                              : lp::beamform_f32_frame_tile();
-  p->n_ftiles_bf = (int)((sh.F + ft - 1) / ft);
+  p->n_ftiles_bf = c->precision == LP_PREC_FP16
+                       ? lp::beamform_tc_partials(sh.F)
+                       : (int)((sh.F + lp::beamform_f32_frame_tile() - 1) /
+                               lp::beamform_f32_frame_tile());
   const double nu_lo = lp::kNu0 + c->first_bin * (lp::kFs / kM);
   const double nu_hi = lp::kNu0 + (c->first_bin + sh.K - 1) * (lp::kFs / kM);
   p->nu_ref = c->nu_ref_hz > 0 ? c->nu_ref_hz : 0.5 * (nu_lo + nu_hi);
@@ -222,6 +223,7 @@ lp_status lp_plan_bind_workspace(lp_plan* p, void* dev, size_t bytes, void* stre
   carve(*p, static_cast<char*>(dev));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LP_CUDA(p, lp::init_kernel_attributes(p->shape));
+  if (p->cfg.precision == LP_PREC_FP16) LP_CUDA(p, lp::encode_beams_map(*p));
   LP_CUDA(p, cudaMemsetAsync(dev, 0, need, s));
   LP_CUDA(p, lp::launch_prototype(*p, s));
   p->last_stream = s;
@@ -308,8 +310,9 @@ lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride
   } else if (attr.device != p->device) {
     return fail(p, LP_ERR_ARG, "input lives on device %d, plan on %d", attr.device, p->device);
   }
-  const size_t align = p->cfg.precision == LP_PREC_FP16 ? 8 : bpc;
-  if (reinterpret_cast<uintptr_t>(xd) % align || (stride * bpc) % align)
+  const size_t align = p->cfg.precision == LP_PREC_FP16 ? 16 : bpc;   // bulk copies
+  if (reinterpret_cast<uintptr_t>(xd) % align || (stride * bpc) % align ||
+      (p->cfg.precision == LP_PREC_FP16 && ((long long)sh.F * sh.S * bpc) % align))
     return fail(p, LP_ERR_ARG, "input and pol stride must be %zu-byte aligned", align);
 
   const bool graph = p->cfg.use_graph && !p->profiling;

@@ -91,6 +91,8 @@ struct lp_plan {
   cudaGraphExec_t graph_exec = nullptr;
   const void* graph_x = nullptr;
   long long graph_stride = -1;
+  // TMA map of the beam rows (CUtensorMap, 128 bytes) for the FP16 form
+  alignas(64) unsigned char beams_map[128] = {};
 };
 
 namespace lp {
@@ -99,6 +101,7 @@ namespace lp {
 cudaError_t launch_prototype(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_weights(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_weights_tc(const lp_plan& p, cudaStream_t s);
+cudaError_t encode_beams_map(lp_plan& p);
 cudaError_t launch_dedisp(const lp_plan& p, cudaStream_t s);
 // x: station block, pol slab p at x + p * pol_stride complex samples, each
 // slab [K][F][S] complex samples contiguous
@@ -115,6 +118,7 @@ cudaError_t init_kernel_attributes(const Shape& sh);
 
 int beamform_f32_frame_tile();
 int beamform_tc_frame_tile();
+int beamform_tc_partials(long long F);
 size_t beamform_tc_weight_bytes(const Shape& sh);
 int ippf_default_frames_per_cta(const Shape& sh);
 
