@@ -92,6 +92,11 @@ __device__ __forceinline__ float2 rot32_rt(float2 d, int e) {
 }
 #undef LP_ROT_CASE
 
+__device__ __forceinline__ float2 badd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 bsub(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+
 // 16-point DFT with kernel exp(+2 pi i k n / 16), radix-2 decimation in
 // frequency: natural-order input, bit-reversed output v[i] = X[br4(i)].
 __device__ __forceinline__ void dft16(float2 (&v)[16]) {
@@ -102,9 +107,9 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 #pragma unroll
       for (int j = 0; j < span; ++j) {
         const float2 a = v[start + j], b = v[start + j + span];
-        v[start + j] = make_float2(a.x + b.x, a.y + b.y);
+        v[start + j] = badd(a, b);
         // exp(+2 pi i j / (2 span)) = exp(+2 pi i (16 j / span) / 32)
-        v[start + j + span] = rot32_rt(make_float2(a.x - b.x, a.y - b.y), j * (16 / span));
+        v[start + j + span] = rot32_rt(bsub(a, b), j * (16 / span));
       }
     }
   }
@@ -160,6 +165,12 @@ __device__ __forceinline__ void stage_batch(const Stager& st, long long m0, long
   cp_async_commit();
 }
 
+// Packed FP32 pairs (one instruction for both components of a complex value).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 t) {
   return make_float2(fmaf(a.x, t.x, -a.y * t.y), fmaf(a.x, t.y, a.y * t.x));
 }
@@ -189,9 +200,9 @@ __device__ __forceinline__ void frame_dft(float2* slot, const float2* st,
     const float2 a = slot[k2 * 32 + (lane ^ k2)];
     const float2 b = slot[(k2 + 16) * 32 + (lane ^ (k2 + 16))];
     if constexpr (HALF)
-      u[k2] = rot32_rt(make_float2(a.x - b.x, a.y - b.y), k2);
+      u[k2] = rot32_rt(bsub(a, b), k2);
     else
-      u[k2] = make_float2(a.x + b.x, a.y + b.y);
+      u[k2] = badd(a, b);
   }
   pair_sync(pair_id);                     // both warps read the slot before it is overwritten
   dft16(u);                               // u[i] = z[lane + 32 (2 br4(i) + HALF)]
@@ -202,7 +213,7 @@ __device__ __forceinline__ void frame_dft(float2* slot, const float2* st,
 // FIR over the batch for one output phase; TAP_REV selects g_{15-t} (the
 // mirror phase).  Fills e2v = |u|^2 and returns its maximum over the batch.
 template <bool TAP_REV, bool WRITE_Y>
-__device__ __forceinline__ float fir_phase(const float (&gq)[kTaps], const float2* ga,
+__device__ __forceinline__ float fir_phase(const float2 (&gq)[kTaps], const float2* ga,
                                            const float2* gb, const float2* gc, int off,
                                            float* yrow, unsigned ymask, float (&e2v)[FB]) {
   float2 zw[kHist + FB];
@@ -215,24 +226,21 @@ __device__ __forceinline__ float fir_phase(const float (&gq)[kTaps], const float
   float emax = 0.f;
 #pragma unroll
   for (int f = 0; f < FB; ++f) {
-    float ur = 0.f, ui = 0.f;
+    float2 u = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int t = 0; t < kTaps; ++t) {
-      const float gt = TAP_REV ? gq[kTaps - 1 - t] : gq[t];
-      ur = fmaf(gt, zw[f + kHist - t].x, ur);
-      ui = fmaf(gt, zw[f + kHist - t].y, ui);
-    }
+    for (int t = 0; t < kTaps; ++t)   // both components per instruction, tap (g, g)
+      u = __ffma2_rn(TAP_REV ? gq[kTaps - 1 - t] : gq[t], zw[f + kHist - t], u);
     if constexpr (WRITE_Y) {
-      if ((ymask >> f) & 1u) yrow[f * kM + off] = ur;
+      if ((ymask >> f) & 1u) yrow[f * kM + off] = u.x;
     }
-    e2v[f] = fmaf(ur, ur, ui * ui);
+    e2v[f] = fmaf(u.x, u.x, u.y * u.y);
     emax = fmaxf(emax, e2v[f]);          // frames outside the run are filtered later
   }
   return emax;
 }
 
 template <bool WRITE_Y>
-__device__ __forceinline__ void fir_batch(const float (&gq)[kTaps], const float2* ga,
+__device__ __forceinline__ void fir_batch(const float2 (&gq)[kTaps], const float2* ga,
                                           const float2* gb, const float2* gc, int tid, int lane,
                                           float* yrow, unsigned ymask, unsigned vmask, float th2,
                                           long long n_row0, int j, int P, int Tr, float sig,
@@ -270,7 +278,7 @@ __device__ __forceinline__ void emit_triggers(const float (&e2v)[FB], unsigned v
 }
 
 template <bool WRITE_Y>
-__device__ __forceinline__ void fir_batch(const float (&gq)[kTaps], const float2* ga,
+__device__ __forceinline__ void fir_batch(const float2 (&gq)[kTaps], const float2* ga,
                                           const float2* gb, const float2* gc, int tid, int lane,
                                           float* yrow, unsigned ymask, unsigned vmask, float th2,
                                           long long n_row0, int j, int P, int Tr, float sig,
@@ -319,9 +327,12 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   const Stager stg = make_stager(stage, brow, K, first_bin, row, tid);
   stage_batch(stg, m0, row, 0, nfr);
 
-  float gq[kTaps];                         // taps of phase tid (mirrored for 1023 - tid)
+  float2 gq[kTaps];                        // taps (g, g) of phase tid (mirrored for 1023 - tid)
 #pragma unroll
-  for (int t = 0; t < kTaps; ++t) gq[t] = g[t * kM + tid];
+  for (int t = 0; t < kTaps; ++t) {
+    const float gt = g[t * kM + tid];
+    gq[t] = make_float2(gt, gt);
+  }
   const float th2 = theta2[j];
   float* yj = y ? y + (long long)j * F * kM : nullptr;
   // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
