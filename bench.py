@@ -335,6 +335,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline_beamform": {"bound": "hbm", "achieved": bf_gbs, "peak": hbm_peak,
                               "unit": "GB/s", "frac": bf_gbs / hbm_peak,
                               "bytes": in_bytes + beams_bytes,
+                              "traffic": recorded_traffic("k_beamform_tc.cu")
+                              if args.precision == "fp16" else None,
                               "note": "input read + FP32 beam intermediate write"},
         "gpu_launches": plan.lp_launches_per_block() * args.steps,
         "triggers_last_block": int(ntrig),
