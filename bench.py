@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--serve-blocks", type=int, default=32,
                     help="blocks of the realtime serving leg (p50/p99 latency); 0 skips it")
+    ap.add_argument("--workload", default="precision", choices=["precision", "stress"],
+                    help="precision: the 48x488x50 headline block; stress: 200 beams x 8 "
+                         "trials x 262144 frames with injected pulses (recall)")
     ap.add_argument("--frames", type=int, default=0,
                     help="block length override for small profiling cases (not a bench line)")
     return ap.parse_args()
@@ -361,6 +364,93 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+def run_stress(args):
+    """200 beams x 8 STEC trials x 262144 frames (1.34 s blocks) with 200 pulses:
+    chunked processing (the beam intermediate of a whole block would be 3.3 TB),
+    realtime factor and trigger recall against the injected pulses."""
+    import torch
+    from paper_1612_06592_gb300 import build
+    build()
+    from paper_1612_06592_gb300 import lp
+    w = synth.STRESS
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    enu, dirs, tec = synth.make_geometry(w)
+    x = device_block(w, 5000, dev)
+    plist, contrib = synth.pulse_contributions(w, 0, enu, dirs)
+    for (m_lo, m_hi, c) in contrib:           # add before rounding, as the generator does
+        add = torch.from_numpy(np.stack([c.real, c.imag], axis=-1).astype(np.float32)).to(dev)
+        for pol in range(w.pols):
+            seg = x[pol, :, m_lo:m_hi].float() + add
+            x[pol, :, m_lo:m_hi] = torch.clamp(torch.round(seg), -128, 127).to(torch.int8)
+    chunk = 8192
+    plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(tec), w.block_len,
+                   input_dtype="int8", precision="fp16", first_bin=w.first_bin,
+                   chunk_frames=chunk, trigger_cap=1 << 22)
+    plan.lp_set_weights(enu, dirs)
+    plan.lp_set_tec(tec)
+    plan.lp_profile_enable(True)
+    for _ in range(max(1, args.warmup)):
+        plan.lp_process_block(x)
+        plan.lp_reset_stream()          # every timed block is block 0 of the stream
+    torch.cuda.synchronize()
+    plan.lp_profile_read()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 3))
+    ms_tot = 0.0
+    for _ in range(steps):
+        plan.lp_reset_stream()
+        e0.record(stream)
+        plan.lp_process_block(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_tot += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    trig, n_trig, st = plan.lp_get_triggers()
+    ms = ms_tot / steps
+    block_s = w.block_len * M / FS_HZ
+    # recall: a pulse counts when its beam has a trigger near the arrival time of
+    # some trial (the de-dispersed pulse sits at n0 + A_trial / nu_ref^2)
+    import oracle as O
+    nu = O.sky_frequencies(w.first_bin, w.subbands)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    delay = O.dispersion_coefficient_hz(tec) / nu_ref ** 2 * FS_HZ
+    by_beam = {}
+    for r in trig:
+        by_beam.setdefault(int(r["beam"]), []).append((int(r["n"]), int(r["tec"])))
+    found, snrs, used = [], [], set()
+    for p in plist:
+        hit = False
+        for (n, t) in by_beam.get(p.beam, []):
+            if abs(n - (p.n0 + delay[t])) <= 512:
+                hit = True
+                used.add((p.beam, n, t))
+        found.append(hit)
+        snrs.append(p.snr)
+    found, snrs = np.array(found), np.array(snrs)
+    bins = [(5, 10), (10, 15), (15, 20.01)]
+    samples = w.n_streams * w.block_len * M
+    return {
+        "workload": w.name, "metric": "realtime factor at 48x488x200 beams x 8 trials",
+        "value": block_s / (ms / 1e3), "unit": "x realtime", "ms_per_block": ms,
+        "block_seconds": block_s, "chunk_frames": chunk,
+        "launches_per_block": plan.lp_launches_per_block(),
+        "output_samples_per_s": samples / (ms / 1e3),
+        "synth_tflops": samples * SYNTH_FLOP_PER_SAMPLE / (ms / 1e3) / 1e12,
+        "pulses": len(plist), "recall": float(found.mean()),
+        "recall_by_snr": {f"{a}-{int(b)}": float(found[(snrs >= a) & (snrs < b)].mean())
+                          for a, b in bins},
+        "triggers": int(n_trig), "trigger_status": int(st),
+        "triggers_not_near_a_pulse": int(len(trig) - sum(
+            1 for r in trig if (int(r["beam"]), int(r["n"]), int(r["tec"])) in used)),
+        "clocks": clk, "data": "synthetic (device noise + host-built dispersed pulses)",
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -401,6 +491,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.workload == "stress":
+        line = run_stress(args) if rank == 0 else None
     else:
         if world > 1:
             import torch

@@ -81,6 +81,13 @@ typedef struct {
                                block's launches (needs a non-default stream; recaptured
                                when the input address or pol stride changes; not with
                                profiling) */
+  int32_t chunk_frames;     /* 0: the beam rows hold the whole block.  > 0 (FP16 form,
+                               multiple of 2048 dividing block_len): the block is
+                               processed in chunks of this many frames, so the beam
+                               intermediate is sized for one chunk; a first beamformer
+                               pass sums |beam|^2 over the whole block for the noise
+                               level (the same sigma as unchunked) */
+  int32_t reserved;
 } lp_config;
 
 /* One trigger: envelope sample above k_sigma * sigma of its stream. */
@@ -148,7 +155,7 @@ lp_status lp_process_block(lp_plan* plan, const void* x, void* stream);
  * pol_stride complex samples after slab p-1 (each slab [K][F][S][2]
  * contiguous).  Used to hand several plans different subband ranges of one
  * resident station block.  pol_stride must be >= K*F*S (when P = 2) and keep
- * 8-byte alignment for the FP16 form. */
+ * 16-byte alignment for the FP16 form. */
 lp_status lp_process_block_strided(lp_plan* plan, const void* x, int64_t pol_stride,
                                    void* stream);
 

@@ -126,12 +126,12 @@ cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_s
   const size_t smem = f32_smem(sh);
   if (p.cfg.input_dtype == LP_INPUT_INT8) {
     k_beamform_f32<char2><<<grid, FT, smem, s>>>((const char2*)x, pol_stride, p.buf.w32, p.buf.dd,
-                                                 sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F, sh.row(),
+                                                 sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F, p.row(),
                                                  p.buf.beams, p.buf.power_part, ntile);
   } else {
     k_beamform_f32<short2><<<grid, FT, smem, s>>>((const short2*)x, pol_stride, p.buf.w32,
                                                   p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F,
-                                                  sh.row(), p.buf.beams, p.buf.power_part, ntile);
+                                                  p.row(), p.buf.beams, p.buf.power_part, ntile);
   }
   return cudaGetLastError();
 }

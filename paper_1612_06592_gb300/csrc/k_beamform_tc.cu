@@ -222,7 +222,10 @@ struct TcArgs {
   float* power_part;        // [J][K][n_chunks]
   int* err;                 // device error word
   int S, P, K, B, Tr, n_mt, n_chunks;
-  long long F, row;
+  long long F, row;         // frames of this launch, beam-row length (chunk + prefix)
+  long long F_in, f_base;   // input frames per subband row, first input frame of the launch
+  int chunk_base, n_chunks_total;   // noise-partial chunk index offset, chunks per block
+  int write_beams, write_power;
   long long n_items;
   int n_s8, n_sb;           // pipeline depths (int8 ring, FP16 ring)
 };
@@ -318,7 +321,8 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
         if (!wait_phase(&empty8[st], ph ^ 1u, abort_p)) break;
         const int k = (int)(km / a.n_mt);
         const int nvalid = (int)min((long long)TN, q.f_hi - q.n0);
-        const int8_t* src = a.x + 2 * (q.pol() * a.pol_stride + ((long long)k * a.F + q.n0) * a.S);
+        const int8_t* src =
+            a.x + 2 * (q.pol() * a.pol_stride + ((long long)k * a.F_in + a.f_base + q.n0) * a.S);
         const uint32_t bytes = (uint32_t)nvalid * 2 * a.S;
         mbar_expect_tx(&full8[st], bytes);
         bulk_g2s(s8 + st * t8_bytes, src, bytes, &full8[st]);
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
                         : make_float2(__uint_as_float(r[h][i]), recv[i]);
             if (beam_ok && f0 + i < f_hi) pw = fmaf(bv[i].x, bv[i].x, fmaf(bv[i].y, bv[i].y, pw));
           }
-          if (fb >= f_hi) continue;                 // warp-uniform
+          if (fb >= f_hi || !a.write_beams) continue;   // warp-uniform
           unsigned char* box = stg + (ew * 2 + h) * STG_BOX;
           for (int t = 0; t < a.Tr; ++t) {
             const float2 dv = t == 0 ? d0 : a.dd[k * a.Tr + t];
@@ -503,10 +507,11 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
         // noise partial of the chunk and column half: lanes 2r, 2r+1 hold the
         // two halves of beam rb; k_sigma adds the two column halves
         pw += __shfl_xor_sync(0xffffffffu, pw, 1);
-        if (beam_ok && !odd) {
+        if (beam_ok && !odd && a.write_power) {
           for (int t = 0; t < a.Tr; ++t) {
             const long long j = ((long long)b * a.Tr + t) * a.P + pol;
-            a.power_part[(j * a.K + k) * (2LL * a.n_chunks) + 2 * q.chunk() + col_half] = pw;
+            a.power_part[(j * a.K + k) * (2LL * a.n_chunks_total) +
+                         2 * (a.chunk_base + q.chunk()) + col_half] = pw;
           }
         }
         pw = 0.f;
@@ -577,8 +582,8 @@ cudaError_t encode_beams_map(lp_plan& p) {
     encode = reinterpret_cast<Encode>(fn);
   }
   const auto& sh = p.shape;
-  const cuuint64_t row = (cuuint64_t)sh.row() * 8;
-  const cuuint64_t dims[5] = {(cuuint64_t)sh.row(), (cuuint64_t)sh.K, (cuuint64_t)sh.P,
+  const cuuint64_t row = (cuuint64_t)p.row() * 8;
+  const cuuint64_t dims[5] = {(cuuint64_t)p.row(), (cuuint64_t)sh.K, (cuuint64_t)sh.P,
                               (cuuint64_t)sh.Tr, (cuuint64_t)sh.B};
   const cuuint64_t strides[4] = {row, row * sh.K, row * sh.K * sh.P, row * sh.K * sh.P * sh.Tr};
   const cuuint32_t box[5] = {16, 1, 1, 1, 16};
@@ -606,7 +611,7 @@ cudaError_t init_tc_attributes(const Shape& sh) {
 }
 
 cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_stride,
-                               cudaStream_t s) {
+                               const Chunk& c, cudaStream_t s) {
   const auto& sh = p.shape;
   TcArgs a;
   a.x = static_cast<const int8_t*>(x);
@@ -622,9 +627,15 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_st
   a.B = sh.B;
   a.Tr = sh.Tr;
   a.n_mt = (sh.B + TM / 2 - 1) / (TM / 2);
-  a.n_chunks = (int)((sh.F + CHUNK - 1) / CHUNK);
-  a.F = sh.F;
-  a.row = sh.row();
+  a.n_chunks = (int)((c.nf + CHUNK - 1) / CHUNK);
+  a.F = c.nf;
+  a.row = p.row();
+  a.F_in = sh.F;
+  a.f_base = c.f_base;
+  a.chunk_base = (int)(c.f_base / CHUNK);
+  a.n_chunks_total = (int)((sh.F + CHUNK - 1) / CHUNK);
+  a.write_beams = c.write_beams ? 1 : 0;
+  a.write_power = c.write_power ? 1 : 0;
   a.n_items = (long long)sh.K * a.n_mt * sh.P * a.n_chunks;
   tc_depths(sh, &a.n_s8, &a.n_sb);
   const long long grid = std::min<long long>(a.n_items, (long long)num_sms());

@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     const float2* __restrict__ beams, int K, int first_bin, long long F, long long row,
     int frames_per_cta, const float* __restrict__ g, const float2* __restrict__ tw,
     const float* __restrict__ theta, const float* __restrict__ theta2, float k_sigma,
-    const long long* __restrict__ blk, int P, int Tr, float* __restrict__ y,
+    const long long* __restrict__ blk, long long F_total, long long f_base, int P, int Tr,
+    float* __restrict__ y,
     TriggerRec* __restrict__ trig, unsigned long long* __restrict__ trig_count,
     long long trig_cap) {
   extern __shared__ float2 smem[];
@@ -334,12 +335,13 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     gq[t] = make_float2(gt, gt);
   }
   const float th2 = theta2[j];
-  float* yj = y ? y + (long long)j * F * kM : nullptr;
+  // this launch covers block frames [f_base, f_base + F) (one chunk, or the block)
+  float* yj = y ? y + ((long long)j * F_total + f_base) * kM : nullptr;
   // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
   // m < 15 of the first block) never trigger
   const long long bidx = *blk;
-  const long long n_first = (bidx * F - kHist) * (long long)kM;
-  const int frame_min_trigger = bidx == 0 ? kHist : 0;
+  const long long n_first = (bidx * F_total + f_base - kHist) * (long long)kM;
+  const int frame_min_trigger = (bidx == 0 && f_base == 0) ? kHist : 0;
 
   for (int bi = 0; bi < nbatch; ++bi) {
     const int r0 = bi * FB;
@@ -423,9 +425,9 @@ __global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, i
 // Carry the last 16 frames of every (stream, bin) row into the row prefix and
 // advance the device block counter.
 __global__ void k_history_shift(float2* __restrict__ beams, long long rows, long long F,
-                                long long row, long long* __restrict__ blk) {
+                                long long row, long long* __restrict__ blk, int advance) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i == 0) *blk += 1;
+  if (i == 0 && advance) *blk += 1;
   if (i >= rows * kPrefix) return;
   const long long r = i / kPrefix;
   const int f = (int)(i % kPrefix);
@@ -451,14 +453,15 @@ cudaError_t init_ippf_attributes() {
                               (int)ippf_smem_bytes());
 }
 
-cudaError_t launch_ippf(const lp_plan& p, cudaStream_t s) {
+cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s) {
   const auto& sh = p.shape;
   const int fpc = p.frames_per_cta;
-  const dim3 grid((unsigned)((sh.F + fpc - 1) / fpc), (unsigned)sh.J());
-  k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(p.buf.beams, sh.K, p.cfg.first_bin, sh.F, sh.row(), fpc,
+  const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)sh.J());
+  k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(p.buf.beams, sh.K, p.cfg.first_bin, c.nf, p.row(), fpc,
                                              p.buf.g, p.buf.tw1024, p.buf.theta, p.buf.theta2,
-                                             (float)p.cfg.k_sigma, p.buf.blk, sh.P, sh.Tr, p.buf.y,
-                                             p.buf.trig, p.buf.trig_count, p.cfg.trigger_cap);
+                                             (float)p.cfg.k_sigma, p.buf.blk, sh.F, c.f_base, sh.P,
+                                             sh.Tr, p.buf.y, p.buf.trig, p.buf.trig_count,
+                                             p.cfg.trigger_cap);
   return cudaGetLastError();
 }
 
@@ -470,12 +473,12 @@ cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_history_shift(const lp_plan& p, cudaStream_t s) {
+cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s) {
   const auto& sh = p.shape;
   const long long rows = (long long)sh.J() * sh.K;
   const long long n = rows * kPrefix;
-  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, rows, sh.F, sh.row(),
-                                                              p.buf.blk);
+  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, rows, c.nf, p.row(),
+                                                              p.buf.blk, c.last ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ size_t carve(lp_plan& p, char* base) {
   b.g = (float*)take(sizeof(float) * kM * lp::kTaps);
   b.tw1024 = (float2*)take(sizeof(float2) * kM);
   b.filter_sums = (double*)take(sizeof(double) * 2);
-  b.beams = (float2*)take(sizeof(float2) * (size_t)J * sh.K * sh.row());
+  b.beams = (float2*)take(sizeof(float2) * (size_t)J * sh.K * p.row());
   b.power_part = (float*)take(sizeof(float) * (size_t)J * sh.K * p.n_ftiles_bf);
   b.sigma2 = (double*)take(sizeof(double) * J);
   b.theta = (float*)take(sizeof(float) * J);
@@ -140,6 +140,7 @@ void lp_config_default(lp_config* c) {
   c->host_input = 0;
   c->frames_per_cta = 0;
   c->use_graph = 0;
+  c->chunk_frames = 0;
 }
 
 lp_status lp_plan_create(lp_plan** out, int stations, int pols, int subbands, int beams,
@@ -183,7 +184,16 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
     return fail(p, LP_ERR_ARG, "trigger_cap out of range");
   if (c->frames_per_cta != 0 && (c->frames_per_cta < 8 || c->frames_per_cta % 8 != 0))
     return fail(p, LP_ERR_ARG, "frames_per_cta must be 0 or a positive multiple of 8");
+  if (c->chunk_frames != 0) {
+    if (c->precision != LP_PREC_FP16)
+      return fail(p, LP_ERR_ARG, "chunk_frames needs the FP16 form");
+    if (c->chunk_frames < lp::beamform_tc_frame_tile() ||
+        c->chunk_frames % lp::beamform_tc_frame_tile() != 0 || sh.F % c->chunk_frames != 0)
+      return fail(p, LP_ERR_ARG, "chunk_frames must be a multiple of %d that divides block_len",
+                  lp::beamform_tc_frame_tile());
+  }
   p->cfg = *c;
+  p->fc = c->chunk_frames && c->chunk_frames < sh.F ? c->chunk_frames : sh.F;
   p->frames_per_cta = c->frames_per_cta ? c->frames_per_cta : lp::ippf_default_frames_per_cta(sh);
   p->n_ftiles_bf = c->precision == LP_PREC_FP16
                        ? lp::beamform_tc_partials(sh.F)
@@ -322,20 +332,48 @@ lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride
   } else {
     if (graph) LP_CUDA(p, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
-    prof_mark(p, LP_STAGE_BEAMFORM, 0, s);
-    if (e == cudaSuccess)
-      e = p->cfg.precision == LP_PREC_FP16 ? lp::launch_beamform_tc(*p, xd, stride, s)
-                                           : lp::launch_beamform_f32(*p, xd, stride, s);
-    prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
-    prof_mark(p, LP_STAGE_SIGMA, 0, s);
-    if (e == cudaSuccess) e = lp::launch_sigma(*p, s);
-    prof_mark(p, LP_STAGE_SIGMA, 1, s);
-    prof_mark(p, LP_STAGE_SYNTH, 0, s);
-    if (e == cudaSuccess) e = lp::launch_ippf(*p, s);
-    prof_mark(p, LP_STAGE_SYNTH, 1, s);
-    prof_mark(p, LP_STAGE_SHIFT, 0, s);
-    if (e == cudaSuccess) e = lp::launch_history_shift(*p, s);
-    prof_mark(p, LP_STAGE_SHIFT, 1, s);
+    const bool fp16 = p->cfg.precision == LP_PREC_FP16;
+    if (p->fc == sh.F) {
+      lp::Chunk c;
+      c.nf = sh.F;
+      prof_mark(p, LP_STAGE_BEAMFORM, 0, s);
+      if (e == cudaSuccess)
+        e = fp16 ? lp::launch_beamform_tc(*p, xd, stride, c, s)
+                 : lp::launch_beamform_f32(*p, xd, stride, s);
+      prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
+      prof_mark(p, LP_STAGE_SIGMA, 0, s);
+      if (e == cudaSuccess) e = lp::launch_sigma(*p, s);
+      prof_mark(p, LP_STAGE_SIGMA, 1, s);
+      prof_mark(p, LP_STAGE_SYNTH, 0, s);
+      if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s);
+      prof_mark(p, LP_STAGE_SYNTH, 1, s);
+      prof_mark(p, LP_STAGE_SHIFT, 0, s);
+      if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
+      prof_mark(p, LP_STAGE_SHIFT, 1, s);
+    } else {
+      // chunked block: the noise level needs the whole block, so a first
+      // beamformer pass only sums |beam|^2; then each chunk is beamformed into
+      // the beam rows, synthesised and shifted.  Stage times cover all chunks.
+      lp::Chunk all;
+      all.nf = sh.F;
+      all.write_beams = false;
+      prof_mark(p, LP_STAGE_BEAMFORM, 0, s);
+      if (e == cudaSuccess) e = lp::launch_beamform_tc(*p, xd, stride, all, s);
+      prof_mark(p, LP_STAGE_SIGMA, 0, s);
+      if (e == cudaSuccess) e = lp::launch_sigma(*p, s);
+      prof_mark(p, LP_STAGE_SIGMA, 1, s);
+      for (long long f0 = 0; f0 < sh.F && e == cudaSuccess; f0 += p->fc) {
+        lp::Chunk c;
+        c.f_base = f0;
+        c.nf = p->fc;
+        c.write_power = false;
+        c.last = f0 + p->fc >= sh.F;
+        e = lp::launch_beamform_tc(*p, xd, stride, c, s);
+        if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s);
+        if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
+      }
+      prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
+    }
     if (graph) {
       cudaGraph_t g = nullptr;
       const cudaError_t ec = cudaStreamEndCapture(s, &g);
@@ -400,6 +438,8 @@ lp_status lp_get_timeseries(lp_plan* p, int beam, int tec, int pol, float* out) 
 
 lp_status lp_get_beams(lp_plan* p, int beam, int tec, int pol, float* out) {
   if (lp_status st = need_bound(p)) return st;
+  if (p->fc != p->shape.F)
+    return fail(p, LP_ERR_STATE, "a chunked plan keeps only one chunk of beam rows");
   const int j = stream_of(p, beam, tec, pol);
   if (j < 0 || !out) return fail(p, LP_ERR_ARG, "bad stream or buffer");
   if (set_device(p) != LP_OK) return LP_ERR_CUDA;
@@ -408,8 +448,8 @@ lp_status lp_get_beams(lp_plan* p, int beam, int tec, int pol, float* out) {
   // After a block the row holds [prefix = last 16 frames][F frames]; the
   // block's frames sit at positions 16 .. F+15.
   LP_CUDA(p, cudaMemcpy2D(out, sizeof(float2) * sh.F,
-                          p->buf.beams + (size_t)j * sh.K * sh.row() + lp::kPrefix,
-                          sizeof(float2) * sh.row(), sizeof(float2) * sh.F, sh.K,
+                          p->buf.beams + (size_t)j * sh.K * p->row() + lp::kPrefix,
+                          sizeof(float2) * p->row(), sizeof(float2) * sh.F, sh.K,
                           cudaMemcpyDeviceToHost));
   return LP_OK;
 }
@@ -432,7 +472,7 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const auto& sh = p->shape;
   LP_CUDA(p, cudaMemsetAsync(p->buf.beams, 0,
-                             sizeof(float2) * (size_t)sh.J() * sh.K * sh.row(), s));
+                             sizeof(float2) * (size_t)sh.J() * sh.K * p->row(), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.sigma2, 0, sizeof(double) * sh.J(), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.blk, 0, sizeof(long long), s));
@@ -442,8 +482,9 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
 }
 
 int lp_launches_per_block(const lp_plan* p) {
-  (void)p;
-  return 4;  // beamformer, sigma, synthesis, history shift (one graph launch in graph mode)
+  // beamformer, sigma, synthesis, history shift; chunked: power pass + sigma + 3 per chunk
+  if (!p || p->fc == 0 || p->fc == p->shape.F) return 4;
+  return 2 + 3 * (int)(p->shape.F / p->fc);
 }
 
 lp_status lp_profile_enable(lp_plan* p, int enable) {

@@ -64,8 +64,20 @@ struct Shape {
 
 }  // namespace lp
 
+namespace lp {
+// One launch range of a block: frames [f_base, f_base + nf) of the block.
+struct Chunk {
+  long long f_base = 0, nf = 0;
+  bool write_beams = true;   // beamformer writes beam rows (false: noise partials only)
+  bool write_power = true;   // beamformer writes noise partials
+  bool last = true;          // last chunk of the block: the history shift advances the block
+};
+}  // namespace lp
+
 struct lp_plan {
   lp::Shape shape;
+  long long fc = 0;          // frames per chunk held in the beam rows (F unless chunked)
+  long long row() const { return fc + lp::kPrefix; }
   lp_config cfg;
   bool configured = false;
   bool bound = false;
@@ -108,10 +120,10 @@ cudaError_t launch_dedisp(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_stride,
                                 cudaStream_t s);
 cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_stride,
-                               cudaStream_t s);
+                               const Chunk& c, cudaStream_t s);
 cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s);
-cudaError_t launch_ippf(const lp_plan& p, cudaStream_t s);
-cudaError_t launch_history_shift(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s);
+cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s);
 
 // Opt-in shared-memory limits of the kernels (per device; call with it current).
 cudaError_t init_kernel_attributes(const Shape& sh);

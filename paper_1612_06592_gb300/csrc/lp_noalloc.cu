@@ -86,6 +86,7 @@ extern "C" lp_status lp_process_block_noalloc(
   c.store_timeseries = 1;
   c.host_input = 0;
   c.trigger_cap = trigger_cap > 0 ? trigger_cap : 1;
+  c.chunk_frames = 0;
   if (lp_plan_configure(&p, &c) != LP_OK) return report(err, errlen, LP_ERR_ARG, p.err.c_str());
   p.cfg.trigger_cap = trigger_cap;
 
@@ -102,7 +103,7 @@ extern "C" lp_status lp_process_block_noalloc(
   size_t o_g = off;   off = up256(off + sizeof(float) * lp::kM * lp::kTaps);
   size_t o_fs = off;  off = up256(off + sizeof(double) * 2);
   size_t o_tw = off;  off = up256(off + sizeof(float2) * lp::kM);
-  size_t o_bm = off;  off = up256(off + sizeof(float2) * J * sh.K * sh.row());
+  size_t o_bm = off;  off = up256(off + sizeof(float2) * J * sh.K * p.row());
   size_t o_pp = off;  off = up256(off + sizeof(float) * J * sh.K * p.n_ftiles_bf);
   size_t o_s2 = off;  off = up256(off + sizeof(double) * J);
   size_t o_th = off;  off = up256(off + sizeof(float) * J);
@@ -176,7 +177,9 @@ extern "C" lp_status lp_process_block_noalloc(
   NA_CUDA(lp::launch_dedisp(p, s));
   NA_CUDA(lp::launch_beamform_f32(p, x, (long long)sh.K * sh.F * sh.S, s));
   NA_CUDA(lp::launch_sigma(p, s));
-  NA_CUDA(lp::launch_ippf(p, s));
+  lp::Chunk whole;
+  whole.nf = sh.F;
+  NA_CUDA(lp::launch_ippf(p, whole, s));
 #undef NA_CUDA
   return LP_OK;
 }

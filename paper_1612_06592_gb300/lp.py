@@ -38,6 +38,8 @@ class lp_config(ctypes.Structure):
         ("host_input", ctypes.c_int32),
         ("frames_per_cta", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
+        ("chunk_frames", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -147,7 +149,8 @@ class Plan:
                  input_dtype="int8", precision="fp32", first_bin=12, k_sigma=6.0,
                  sigma_alpha=0.25, nu_ref_hz=0.0, trigger_cap=1 << 20,
                  store_timeseries=False, host_input=False, frames_per_cta=0,
-                 kaiser_beta=9.0, use_graph=False, stream=None, workspace=None):
+                 kaiser_beta=9.0, use_graph=False, chunk_frames=0, stream=None,
+                 workspace=None):
         import torch
         self.shape = (stations, pols, subbands, beams, tec_trials, block_len)
         self._h = _P()
@@ -166,6 +169,7 @@ class Plan:
         c.frames_per_cta = frames_per_cta
         c.kaiser_beta = kaiser_beta
         c.use_graph = int(bool(use_graph))
+        c.chunk_frames = int(chunk_frames)
         self.config = c
         self._check(_lib.lp_plan_configure(self._h, ctypes.byref(c)), "lp_plan_configure")
         nbytes = ctypes.c_size_t()

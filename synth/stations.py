@@ -25,7 +25,7 @@ __all__ = [
     "station_positions", "pointing_enu", "hex_beam_directions", "gaussian_table",
     "noise_slab", "analysis_filter", "forward_ppf", "dispersed_pulse",
     "pulse_amplitude", "pulse_subbands", "Pulse", "make_geometry", "make_block",
-    "SAMPLE_RATE_HZ", "FFT_LEN", "device_noise_block",
+    "SAMPLE_RATE_HZ", "FFT_LEN", "device_noise_block", "pulse_contributions",
 ]
 
 SAMPLE_RATE_HZ = 200e6
@@ -286,6 +286,24 @@ def _draw_pulses(w: Workload, block: int):
         beam = int(rng.integers(0, w.beams))
         pulses.append(Pulse(n0, pulse_amplitude(snr, w), tec, snr, beam))
     return pulses
+
+
+def pulse_contributions(w: Workload, block: int, station_enu, beam_dir):
+    """The injected pulses of a block and their station subband contributions:
+    list of (m_lo, m_hi, complex [K, m_hi - m_lo, S]) to add before rounding."""
+    plist = _draw_pulses(w, block)
+    h = analysis_filter()
+    nu = _NU0 + np.arange(w.first_bin, w.first_bin + w.subbands) * (SAMPLE_RATE_HZ / FFT_LEN)
+    out = []
+    for p in plist:
+        m_lo, m_hi, xs = pulse_subbands(p, w, h, block)
+        p.frames = (m_lo, m_hi)
+        if m_hi <= m_lo:
+            continue
+        tau = station_enu @ beam_dir[p.beam] / _C
+        phase = np.exp(2j * np.pi * nu[:, None] * tau[None, :])
+        out.append((m_lo, m_hi, xs.T[:, :, None] * phase[:, None, :]))
+    return plist, out
 
 
 def make_block(w: Workload, block: int = 0, station_enu=None, beam_dir=None,

@@ -127,3 +127,30 @@ def test_serving_admission_waits_for_memory(cuda_lib):
     assert len(got[0]) == 2 and len(got[1]) == 2
     # the small one is queued behind request 1 (arrival order) and runs after it
     assert admitted_at[2] >= 2
+
+
+def test_chunked_block_equals_whole_block(cuda_lib):
+    """Frame chunks inside a block (beam rows sized for one chunk, noise level
+    from a first power-only pass) give exactly the unchunked results."""
+    import torch
+    S, P, K, B, Tr, F, fb = 8, 2, 12, 5, 2, 8192, 140
+    blocks, enu, dirs, tec = random_case(45, S, P, K, B, Tr, F, fb, "int8", 2, amp=100)
+    res = []
+    for chunk in (0, 2048):
+        plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision="fp16",
+                         store_timeseries=True, k_sigma=3.5, chunk_frames=chunk)
+        plan.lp_set_weights(enu, dirs)
+        plan.lp_set_tec(tec)
+        out = []
+        for xb in blocks:
+            plan.lp_process_block(torch.from_numpy(xb).cuda())
+            out.append((plan.lp_get_timeseries(4, 1, 1), plan.lp_get_timeseries(0, 0, 0),
+                        plan.lp_get_triggers()[0], plan.lp_get_sigma()))
+        if chunk:
+            with pytest.raises(cuda_lib.LPError):
+                plan.lp_get_beams(0, 0, 0)       # only one chunk of rows is kept
+            assert plan.lp_launches_per_block() == 2 + 3 * (F // chunk)
+        res.append(out)
+    for a, b in zip(*res):
+        for u, v in zip(a, b):
+            np.testing.assert_array_equal(u, v)
