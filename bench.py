@@ -144,9 +144,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------ inputs -------
 
-def device_block(w, seed, device):
-    """Seeded synthetic block on the device (rounded Gaussian table lookup)."""
-    return synth.device_noise_block(w, seed, device)
+def device_block(w, seed, device, contrib=None):
+    """Seeded synthetic block on the device (Gaussian quantile table, rounded)."""
+    return synth.device_noise_block(w, seed, device, contrib)
 
 
 # ------------------------------------------------------------ CPU oracle ---
@@ -376,13 +376,8 @@ def run_stress(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     enu, dirs, tec = synth.make_geometry(w)
-    x = device_block(w, 5000, dev)
     plist, contrib = synth.pulse_contributions(w, 0, enu, dirs)
-    for (m_lo, m_hi, c) in contrib:           # add before rounding, as the generator does
-        add = torch.from_numpy(np.stack([c.real, c.imag], axis=-1).astype(np.float32)).to(dev)
-        for pol in range(w.pols):
-            seg = x[pol, :, m_lo:m_hi].float() + add
-            x[pol, :, m_lo:m_hi] = torch.clamp(torch.round(seg), -128, 127).to(torch.int8)
+    x = device_block(w, 5000, dev, contrib)     # pulses added before rounding
     chunk = 8192
     plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(tec), w.block_len,
                    input_dtype="int8", precision="fp16", first_bin=w.first_bin,

@@ -161,15 +161,24 @@ def make_geometry(w: Workload):
 # Noise
 # ----------------------------------------------------------------------------
 
-def gaussian_table(sigma: float, dtype: str) -> np.ndarray:
-    """65536 rounded Gaussian quantiles sigma * Phi^-1((i + 1/2) / 65536), clipped."""
+def gaussian_quantiles(sigma: float) -> np.ndarray:
+    """65536 Gaussian quantiles sigma * Phi^-1((i + 1/2) / 65536) (continuous)."""
     q = (np.arange(65536, dtype=np.float64) + 0.5) / 65536.0
-    v = np.rint(sigma * ndtri(q))
+    return sigma * ndtri(q)
+
+
+def gaussian_table(sigma: float, dtype: str) -> np.ndarray:
+    """The quantiles rounded and clipped to the sample type (noise-only samples)."""
     info = np.iinfo(np.dtype(dtype))
-    return np.clip(v, info.min, info.max).astype(dtype)
+    return np.clip(np.rint(gaussian_quantiles(sigma)), info.min, info.max).astype(dtype)
 
 
 _TABLES: dict = {}
+
+
+def _noise_index(seed, block, pol, k, frames, stations):
+    rng = _rng(seed, block, pol, k)
+    return np.frombuffer(rng.bytes(frames * stations * 2 * 2), dtype=np.uint16)
 
 
 def noise_slab(seed: int, block: int, pol: int, k: int, frames: int, stations: int,
@@ -178,9 +187,26 @@ def noise_slab(seed: int, block: int, pol: int, k: int, frames: int, stations: i
     key = (sigma, dtype)
     if key not in _TABLES:
         _TABLES[key] = gaussian_table(sigma, dtype)
-    rng = _rng(seed, block, pol, k)
-    idx = np.frombuffer(rng.bytes(frames * stations * 2 * 2), dtype=np.uint16)
+    idx = _noise_index(seed, block, pol, k, frames, stations)
     return _TABLES[key][idx].reshape(frames, stations, 2)
+
+
+def noisy_slab(seed: int, block: int, pol: int, k: int, frames: int, stations: int,
+               sigma: float, dtype: str, adds) -> np.ndarray:
+    """One slab of continuous Gaussian noise plus signal, rounded and clipped
+    to the sample type (the station's quantiser).  adds: list of (m_lo, m_hi,
+    complex [m_hi - m_lo, stations]) signal contributions of this subband.
+    Without signal it equals ``noise_slab``."""
+    key = ("q", sigma)
+    if key not in _TABLES:
+        _TABLES[key] = gaussian_quantiles(sigma)
+    idx = _noise_index(seed, block, pol, k, frames, stations)
+    v = _TABLES[key][idx].reshape(frames, stations, 2)
+    for (m_lo, m_hi, c) in adds:
+        v[m_lo:m_hi, :, 0] += c.real
+        v[m_lo:m_hi, :, 1] += c.imag
+    info = np.iinfo(np.dtype(dtype))
+    return np.clip(np.rint(v), info.min, info.max).astype(dtype)
 
 
 # ----------------------------------------------------------------------------
@@ -308,53 +334,54 @@ def pulse_contributions(w: Workload, block: int, station_enu, beam_dir):
 
 def make_block(w: Workload, block: int = 0, station_enu=None, beam_dir=None,
                noise: bool = True, pulses: bool = True):
-    """Station block [P, K, F, S, 2] of w.dtype plus the list of injected pulses."""
+    """Station block [P, K, F, S, 2] of w.dtype plus the list of injected pulses.
+
+    Pulses are added to the continuous noise before the rounding to integers,
+    as a station quantises signal and noise together (a pulse weaker than half a
+    quantisation step per station still survives, dithered by the noise)."""
     if station_enu is None or beam_dir is None:
         station_enu, beam_dir, _ = make_geometry(w)
     P, K, F, S = w.pols, w.subbands, w.block_len, w.stations
+    plist, contrib = (pulse_contributions(w, block, station_enu, beam_dir) if pulses
+                      else ([], []))
     x = np.zeros((P, K, F, S, 2), dtype=w.dtype)
-    if noise:
-        for pol in range(P):
-            for k in range(K):
-                x[pol, k] = noise_slab(w.seed, block, pol, k, F, S, w.noise_sigma, w.dtype)
-    plist = _draw_pulses(w, block) if pulses else []
-    if plist:
-        h = analysis_filter()
-        nu = _NU0 + np.arange(w.first_bin, w.first_bin + K) * (SAMPLE_RATE_HZ / FFT_LEN)
-        acc = {}
-        for p in plist:
-            m_lo, m_hi, xs = pulse_subbands(p, w, h, block)
-            p.frames = (m_lo, m_hi)
-            if m_hi <= m_lo:
-                continue
-            tau = station_enu @ beam_dir[p.beam] / _C                 # [S]
-            phase = np.exp(2j * np.pi * nu[:, None] * tau[None, :])   # [K, S]
-            contrib = xs.T[:, :, None] * phase[:, None, :]            # [K, n, S]
-            key = (m_lo, m_hi)
-            acc[key] = acc.get(key, 0) + contrib
-        info = np.iinfo(np.dtype(w.dtype))
-        for (m_lo, m_hi), c in acc.items():
-            for pol in range(P):
-                seg = x[pol, :, m_lo:m_hi].astype(np.float64)
-                seg[..., 0] += c.real
-                seg[..., 1] += c.imag
-                x[pol, :, m_lo:m_hi] = np.clip(np.rint(seg), info.min, info.max).astype(w.dtype)
+    info = np.iinfo(np.dtype(w.dtype))
+    for pol in range(P):
+        for k in range(K):
+            adds = [(m_lo, m_hi, c[k]) for (m_lo, m_hi, c) in contrib]
+            if noise:
+                x[pol, k] = noisy_slab(w.seed, block, pol, k, F, S, w.noise_sigma, w.dtype, adds)
+            elif adds:
+                v = np.zeros((F, S, 2))
+                for (m_lo, m_hi, c) in adds:
+                    v[m_lo:m_hi, :, 0] += c.real
+                    v[m_lo:m_hi, :, 1] += c.imag
+                x[pol, k] = np.clip(np.rint(v), info.min, info.max).astype(w.dtype)
     return x, plist
 
 
-def device_noise_block(w: Workload, seed: int, device):
+def device_noise_block(w: Workload, seed: int, device, contrib=None):
     """Seeded noise block [P, K, F, S, 2] generated directly in device memory
-    (PyTorch's generator indexing the same rounded-Gaussian table); for
+    (PyTorch's generator indexing the same Gaussian quantiles); signal
+    contributions (``pulse_contributions``) are added before rounding.  For
     timing runs at full size, where host generation would dominate."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(seed)
-    table = torch.from_numpy(gaussian_table(w.noise_sigma, w.dtype).astype(np.int16)).to(device)
+    table = torch.from_numpy(gaussian_quantiles(w.noise_sigma).astype(np.float32)).to(device)
     dt = torch.int8 if w.dtype == "int8" else torch.int16
+    info = np.iinfo(np.dtype(w.dtype))
     x = torch.empty((w.pols, w.subbands, w.block_len, w.stations, 2), dtype=dt, device=device)
+    adds = []
+    for (m_lo, m_hi, c) in contrib or []:
+        adds.append((m_lo, m_hi, torch.from_numpy(
+            np.stack([c.real, c.imag], axis=-1).astype(np.float32)).to(device)))
     for pol in range(w.pols):
         for k in range(w.subbands):
             idx = torch.randint(0, 65536, (w.block_len, w.stations, 2), generator=g,
                                 device=device, dtype=torch.int32)
-            x[pol, k] = table[idx].to(dt)
+            v = table[idx]
+            for (m_lo, m_hi, a) in adds:
+                v[m_lo:m_hi] += a[k]
+            x[pol, k] = torch.clamp(torch.round(v), info.min, info.max).to(dt)
     return x
