@@ -97,13 +97,16 @@ def make_requests(seed, n_blocks, n_beams_grid=50, n_sub=488, rate=0.25, min_sub
     return reqs
 
 
-# Device time of one session per block, ms, on GB300 (FP16 form): the synthesis
-# costs ~0.30 ms per stream of 65536 frames whatever the subband count (the
-# inverse DFT is always 1024 points); the beamformer ~16.7 ms per 50 beams x 2
-# pols x 488 subbands.  Admission multiplies it by a correction learned from
-# the measured block times.
+# Device time of one session per block, ms, on GB300 (FP16 form), measured
+# alone: the synthesis costs ~0.30 ms per stream of 65536 frames whatever the
+# subband count (the inverse DFT is always 1024 points); the beamformer ~7.5 ms
+# per 50 beams x 2 pols x 488 subbands.  Sessions sharing the GPU run slower
+# than the sum of their lone times suggests (small grids, interference), so
+# admission multiplies the sum by a correction learned from the measured block
+# times, starting from a conservative value.
 MS_PER_STREAM = 0.30
-MS_PER_BEAM_POL_SUBBAND = 16.7 / (50 * 2 * 488)
+MS_PER_BEAM_POL_SUBBAND = 7.5 / (50 * 2 * 488)
+INITIAL_CORRECTION = 2.0
 
 
 def session_cost_ms(P, K, B, Tr, F):
@@ -142,8 +145,9 @@ class Server:
         self.block_dev = torch.empty(nbytes, dtype=torch.int8, device=self.device)
         self.copy_stream = torch.cuda.Stream(device=self.device)
         self.time_budget_ms = time_budget_ms
-        self.cost_corr = 1.0          # measured / modelled block time (running average)
+        self.cost_corr = INITIAL_CORRECTION   # measured / modelled session time
         self.cost_used = 0.0
+        self.copy_ms = 0.0                    # measured ingest time of a block
 
     # -- admission ---------------------------------------------------------
     def submit(self, req: Request):
@@ -168,15 +172,15 @@ class Server:
             need = self._ws(req)
             cost = self._cost(req)
             too_slow = (self.time_budget_ms is not None
-                        and cost * self.cost_corr > self.time_budget_ms)
+                        and self.copy_ms + cost * self.cost_corr > self.time_budget_ms)
             if need > self.budget or too_slow:
                 self.pending.popleft()          # can never fit: refuse
                 self.log.append(("refused", req.rid, need))
                 continue
             if self.used + need > self.budget:
                 break                           # wait for memory to free up
-            if (self.time_budget_ms is not None
-                    and (self.cost_used + cost) * self.cost_corr > self.time_budget_ms):
+            if (self.time_budget_ms is not None and self.active and
+                    self.copy_ms + (self.cost_used + cost) * self.cost_corr > self.time_budget_ms):
                 break                           # wait for a time slot
             self.pending.popleft()
             stream = self.torch.cuda.Stream(device=self.device)
@@ -207,12 +211,15 @@ class Server:
         triggers are on the host.  host_block: pinned uint8/int8 tensor to copy
         in first (the block's arrival), or None if the buffer is already filled."""
         torch = self.torch
-        ready = torch.cuda.Event()
+        ready = torch.cuda.Event(enable_timing=True)
+        start = torch.cuda.Event(enable_timing=True)
         if host_block is not None:
             with torch.cuda.stream(self.copy_stream):
+                start.record(self.copy_stream)
                 self.block_dev.copy_(host_block.view(torch.int8), non_blocking=True)
                 ready.record(self.copy_stream)
         else:
+            start.record(torch.cuda.current_stream(self.device))
             ready.record(torch.cuda.current_stream(self.device))
         pol_stride = self.n_sub * self.F * self.S           # complex samples
         for s in self.active.values():
@@ -224,12 +231,15 @@ class Server:
             trig, n, _ = s.plan.lp_get_triggers()
             s.blocks_done += 1
             out[rid] = (trig, n)
+        ready.synchronize()
+        copy = start.elapsed_time(ready) if host_block is not None else 0.0
+        self.copy_ms = copy if self.copy_ms == 0.0 else 0.8 * self.copy_ms + 0.2 * copy
         return out
 
     def observe(self, block_ms):
         """Update the cost correction from the measured time of the last block."""
-        if self.cost_used > 0 and block_ms > 0:
-            r = block_ms / self.cost_used
+        if self.cost_used > 0 and block_ms > self.copy_ms:
+            r = (block_ms - self.copy_ms) / self.cost_used
             self.cost_corr = 0.8 * self.cost_corr + 0.2 * r
 
 
@@ -287,6 +297,7 @@ def run(args):
         "requests": len(reqs), "refused": sum(1 for e in srv.log if e[0] == "refused"),
         "hbm_budget_gb": args.budget_gb,
         "time_budget_frac": args.time_budget, "cost_correction": srv.cost_corr,
+        "ingest_ms": srv.copy_ms,
         "sustained_blocks_per_s": args.blocks / wall,
         "stream_samples_per_s": n_out * w.block_len * M / wall,
         "station_samples_per_s": args.blocks * w.pols * w.subbands * w.block_len * w.stations / wall,
