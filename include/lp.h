@@ -182,6 +182,17 @@ lp_status lp_get_sigma(lp_plan* plan, double* sigma_host);
 /* Forget the stream: zero synthesis history and noise state, block counter 0. */
 lp_status lp_reset_stream(lp_plan* plan, void* stream);
 
+/* Autotuner (the paper has no counterpart; it tunes the synthesis kernel's
+ * tiling): processes block x exactly as lp_process_block does, and inside that
+ * block times the synthesis kernel for frames_per_cta in {64, 128, ..., 2048}
+ * (<= the chunk length) on the same beam rows, keeps the fastest for later
+ * blocks and returns it in *best (ms per candidate in ms_out[6] when not NULL,
+ * 0 for skipped candidates).  The outputs do not depend on the tiling, so the
+ * block's results are those of lp_process_block.  Synchronises `stream`;
+ * drops a captured graph.  Device input only (contiguous layout). */
+lp_status lp_plan_autotune(lp_plan* plan, const void* x, void* stream, int32_t* best,
+                           double* ms_out);
+
 /* Number of kernel launches lp_process_block makes (for accounting). */
 int lp_launches_per_block(const lp_plan* plan);
 

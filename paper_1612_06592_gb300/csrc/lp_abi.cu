@@ -283,13 +283,78 @@ lp_status lp_set_tec(lp_plan* p, const double* tec, void* stream) {
   return LP_OK;
 }
 
+namespace {
+
+// Synthesis of one chunk while timing the candidate tilings (autotuner): each
+// candidate reruns the same launch on the same beam rows (before the history
+// shift), the fastest is kept and run last, so the outputs are a normal run's.
+cudaError_t tune_ippf(lp_plan* p, const lp::Chunk& c, cudaStream_t s, double* ms_out) {
+  const int cand[6] = {64, 128, 256, 512, 1024, 2048};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best_ms = 1e30;
+  int best_fpc = p->frames_per_cta;
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
+    if (ms_out) ms_out[i] = 0.0;
+    if (cand[i] > c.nf) continue;
+    p->frames_per_cta = cand[i];
+    double ms_sum = 0.0;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_sum += ms;                 // the first run warms up
+    }
+    if (e == cudaSuccess) {
+      const double ms = ms_sum / 3.0;
+      if (ms_out) ms_out[i] = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_fpc = cand[i];
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  p->frames_per_cta = best_fpc;
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s);
+  return e;
+}
+
+lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, bool tune,
+                  double* tune_ms);
+
+}  // namespace
+
 lp_status lp_process_block(lp_plan* p, const void* x, void* stream) {
   if (!p) return LP_ERR_ARG;
   const auto& sh = p->shape;
-  return lp_process_block_strided(p, x, (int64_t)sh.K * sh.F * sh.S, stream);
+  return process(p, x, (int64_t)sh.K * sh.F * sh.S, stream, false, nullptr);
 }
 
 lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride, void* stream) {
+  return process(p, x, pol_stride, stream, false, nullptr);
+}
+
+lp_status lp_plan_autotune(lp_plan* p, const void* x, void* stream, int32_t* best,
+                           double* ms_out) {
+  if (!p || !best) return LP_ERR_ARG;
+  const auto& sh = p->shape;
+  const lp_status st = process(p, x, (int64_t)sh.K * sh.F * sh.S, stream, true, ms_out);
+  if (st == LP_OK) *best = p->frames_per_cta;
+  return st;
+}
+
+namespace {
+
+lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, bool tune,
+                  double* tune_ms) {
   if (lp_status st = need_bound(p)) return st;
   if (!p->weights_set || !p->tec_set)
     return fail(p, LP_ERR_STATE, "lp_set_weights and lp_set_tec must precede lp_process_block");
@@ -325,7 +390,11 @@ lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride
       (p->cfg.precision == LP_PREC_FP16 && ((long long)sh.F * sh.S * bpc) % align))
     return fail(p, LP_ERR_ARG, "input and pol stride must be %zu-byte aligned", align);
 
-  const bool graph = p->cfg.use_graph && !p->profiling;
+  const bool graph = p->cfg.use_graph && !p->profiling && !tune;
+  if (tune && p->graph_exec) {
+    cudaGraphExecDestroy(p->graph_exec);     // the tiling changes
+    p->graph_exec = nullptr;
+  }
   if (graph && !s) return fail(p, LP_ERR_ARG, "graph mode needs a non-default stream");
   if (graph && p->graph_exec && p->graph_x == xd && p->graph_stride == stride) {
     LP_CUDA(p, cudaGraphLaunch(p->graph_exec, s));
@@ -345,7 +414,7 @@ lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride
       if (e == cudaSuccess) e = lp::launch_sigma(*p, s);
       prof_mark(p, LP_STAGE_SIGMA, 1, s);
       prof_mark(p, LP_STAGE_SYNTH, 0, s);
-      if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s);
+      if (e == cudaSuccess) e = tune ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
       prof_mark(p, LP_STAGE_SYNTH, 1, s);
       prof_mark(p, LP_STAGE_SHIFT, 0, s);
       if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
@@ -369,7 +438,8 @@ lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride
         c.write_power = false;
         c.last = f0 + p->fc >= sh.F;
         e = lp::launch_beamform_tc(*p, xd, stride, c, s);
-        if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s);
+        if (e == cudaSuccess)
+          e = tune && f0 == 0 ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
         if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
       }
       prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
@@ -397,6 +467,8 @@ lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride
   p->block_index += 1;
   return LP_OK;
 }
+
+}  // namespace
 
 lp_status lp_get_triggers(lp_plan* p, lp_trigger* out, int64_t cap, int64_t* n_total) {
   if (lp_status st = need_bound(p)) return st;

@@ -103,6 +103,7 @@ struct lp_plan {
   cudaGraphExec_t graph_exec = nullptr;
   const void* graph_x = nullptr;
   long long graph_stride = -1;
+  long long tune_blk = 0;    // host copy of the device block counter (autotuner)
   // TMA map of the beam rows (CUtensorMap, 128 bytes) for the FP16 form
   alignas(64) unsigned char beams_map[128] = {};
 };

@@ -78,6 +78,7 @@ SIGNATURES = {
     "lp_get_sigma": (ctypes.c_int, [_P, _P]),
     "lp_reset_stream": (ctypes.c_int, [_P, _P]),
     "lp_launches_per_block": (ctypes.c_int, [_P]),
+    "lp_plan_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
     "lp_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "lp_profile_read": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
     "lp_process_block_noalloc": (ctypes.c_int, [
@@ -261,6 +262,16 @@ class Plan:
 
     def lp_launches_per_block(self):
         return _lib.lp_launches_per_block(self._h)
+
+    def lp_plan_autotune(self, x, stream=None):
+        """Process block x while picking the synthesis tiling by timing; returns
+        (frames_per_cta, {candidate: ms})."""
+        best = ctypes.c_int32()
+        ms = np.zeros(6, dtype=np.float64)
+        self._check(_lib.lp_plan_autotune(self._h, _ptr(x), _stream_ptr(stream),
+                                          ctypes.byref(best), ms.ctypes.data), "lp_plan_autotune")
+        cand = (64, 128, 256, 512, 1024, 2048)
+        return best.value, {c: m for c, m in zip(cand, ms.tolist()) if m > 0}
 
     STAGES = ("h2d", "beamform", "sigma", "synth", "shift")
 

@@ -315,7 +315,7 @@ def build_parser():
     ap.add_argument("--distinct-blocks", type=int, default=2)
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--realtime", action=argparse.BooleanOptionalAction, default=True)
-    ap.add_argument("--time-budget", type=float, default=0.8,
+    ap.add_argument("--time-budget", type=float, default=0.75,
                     help="admit while the predicted block time stays below this fraction "
                          "of the block period (0: memory budget only)")
     return ap

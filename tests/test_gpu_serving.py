@@ -154,3 +154,27 @@ def test_chunked_block_equals_whole_block(cuda_lib):
     for a, b in zip(*res):
         for u, v in zip(a, b):
             np.testing.assert_array_equal(u, v)
+
+
+def test_autotune_keeps_results(cuda_lib):
+    import torch
+    S, P, K, B, Tr, F, fb = 8, 2, 16, 6, 1, 4096, 200
+    blocks, enu, dirs, tec = random_case(46, S, P, K, B, Tr, F, fb, "int8", 2, amp=100)
+    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision="fp16",
+                     store_timeseries=True, k_sigma=3.5)
+    ref = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision="fp16",
+                    store_timeseries=True, k_sigma=3.5)
+    for p in (plan, ref):
+        p.lp_set_weights(enu, dirs)
+        p.lp_set_tec(tec)
+    for i, xb in enumerate(blocks):
+        xd = torch.from_numpy(xb).cuda()
+        ref.lp_process_block(xd)
+        if i == 0:                     # the tuned block's outputs are a normal block's
+            best, ms = plan.lp_plan_autotune(xd)
+            assert best in ms and len(ms) >= 5 and all(v > 0 for v in ms.values())
+        else:
+            plan.lp_process_block(xd)
+        np.testing.assert_array_equal(plan.lp_get_timeseries(5, 0, 1), ref.lp_get_timeseries(5, 0, 1))
+        np.testing.assert_array_equal(plan.lp_get_triggers()[0], ref.lp_get_triggers()[0])
+        np.testing.assert_array_equal(plan.lp_get_sigma(), ref.lp_get_sigma())
