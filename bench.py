@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--workload", default="precision", choices=["precision", "stress"],
                     help="precision: the 48x488x50 headline block; stress: 200 beams x 8 "
                          "trials x 262144 frames with injected pulses (recall)")
+    ap.add_argument("--synth-frames", type=int, default=0,
+                    help="fixed synthesis frames per thread block (0: autotune)")
     ap.add_argument("--frames", type=int, default=0,
                     help="block length override for small profiling cases (not a bench line)")
     return ap.parse_args()
@@ -238,12 +240,15 @@ def run_ours(args, rank, world, local_rank):
     x = device_block(w, 1000 + rank, dev)
     plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(w.tec_trials), w.block_len,
                    input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
-                   host_input=not args.no_e2e)
+                   host_input=not args.no_e2e, frames_per_cta=args.synth_frames)
     plan.lp_set_weights(enu, dirs)
     plan.lp_set_tec(tec)
     stream = torch.cuda.current_stream()
     # one untimed block picks the synthesis tiling (autotuner), then warm-up
-    tuned_fpc, tune_ms = plan.lp_plan_autotune(x)
+    if args.synth_frames:
+        tuned_fpc, tune_ms = args.synth_frames, {}
+    else:
+        tuned_fpc, tune_ms = plan.lp_plan_autotune(x)
     plan.lp_profile_enable(True)
     for _ in range(args.warmup):
         plan.lp_process_block(x)

@@ -1,37 +1,60 @@
 // Inverse polyphase filter bank + envelope trigger (Sec. 2 last paragraph,
 // Sec. 3 second paragraph, Fig. 1), and the per-block noise level.
 //
-// k_ippf: one thread block (16 warps) owns one stream j and a run of output
-// frames [m0, m1).  It walks frames m0-16 .. m1-1 in batches of 8:
-//   1. the batch's beam bins (8 frames x K bins, frames contiguous per bin
-//      row) are copied into a zero-padded 512-bin stage with cp.async while
-//      the previous batch's FIR runs;
-//   2. two warps take the 1024-point inverse DFT of one frame,
+// k_ippf: one thread block owns one stream j and a run of output frames
+// [m0, m1) and walks frames m0-16 .. m1-1 in batches of 8 (four frame pairs).
+// Its 16 warps have two roles that run concurrently on a double-buffered ring:
+//
+//  * DFT warps 0..7 (two per frame pair) copy the batch's beam bins into a
+//    zero-padded 512-bin stage with 16-byte cp.async (one batch ahead) and take
+//    the 1024-point inverse DFT
 //        z[p] = sum_k c[k] exp(+2 pi i k p / 1024),  c nonzero only in the
-//      selected bins (< 512), as 32 x 32: a 32-point DFT over k = 32 k1 + lane
-//      whose inputs 16..31 are zero, the twiddle exp(2 pi i lane p1 / 1024), a
-//      transpose through shared memory and a second 32-point DFT.  Each
-//      32-point DFT is split between the two warps by output parity (two
-//      16-point DFTs of the folded inputs).  z lands in a 24-frame ring in
-//      shared memory (three groups of 8 frames, addressed by group pointers);
-//   3. every thread owns the output phases p = t and p' = 1023 - t, which share
-//      one set of 16 taps (g[n] = g[L-1-n] gives g_t[p'] = g_{15-t}[p]), and
-//      computes for the 8 new frames
+//    selected bins (< 512), as 32 x 32 with k = 32 k1 + k2, p = p1 + 32 p2.
+//    Every value is a pair of frames, so each packed FP32 instruction (FADD2 /
+//    FMUL2 / FFMA2) does the same step for both frames.  Warp h = warp mod 2
+//    owns the outputs p1 = h (mod 2) of the first 32-point stage (a 16-point
+//    DFT of the 16 nonzero inputs k1 < 16, pre-rotated by exp(+2 pi i k1 h/32))
+//    and p2 = h (mod 2) of the second (the inputs folded as
+//    (a + (-1)^h b) exp(+2 pi i k2 h / 32), then a 16-point DFT).  Between the
+//    stages come the twiddle exp(+2 pi i k2 p1 / 1024) and a transpose through
+//    the pair's ring slots (16-byte granules, column XOR-swizzled by row mod 8:
+//    free of bank conflicts both ways, addresses affine in the unrolled index).
+//  * FIR warps 8..15: thread t owns the output phases t, 1023 - t, t + 256 and
+//    767 - t.  Mirror phases share one set of 16 taps (g[n] = g[L-1-n] gives
+//    g_t[M-1-p] = g_{15-t}[p]).  The taps, as (g, g) pairs, and the last 16
+//    frames of z of each phase live in the thread's own tensor-memory columns
+//    (tcgen05.ld / tcgen05.st), so the ring holds only the batch in flight and
+//    the FIR reads each new z once from shared memory.  Per phase it computes
 //        u_m[p] = sum_{t<16} g[t M + p] z_{m-t}[p]     (g holds the 2/M scale),
-//      y = Re u (optionally stored) and |u|^2 against theta^2; the warps vote
-//      and compact the (rare) samples above threshold into the trigger list.
-// The first 16 frames of a run only fill the FIR history (16/frames_per_cta
-// of extra inverse DFTs).  FP32 throughout.
+//    y = Re u (optionally stored) and |u|^2 against theta^2; the warps vote
+//    and compact the (rare) samples above threshold into the trigger list.
+//
+// The roles hand batches over with named barriers: "ready[s]" (DFT warps
+// arrive, FIR warps wait) and "free[s]" (the reverse) for ring buffer s.
+// The first 16 frames of a run only fill the FIR history (16/frames_per_cta of
+// extra inverse DFTs).  FP32 throughout.
 #include "lp_internal.cuh"
+
+#include <cstdint>
 
 namespace lp {
 namespace {
 
 constexpr int NT = 512;            // threads per block
-constexpr int NW = NT / 32;        // 16 warps
-constexpr int FB = 8;              // frames per batch (two warps per frame)
-constexpr int RING = 24;           // 3 groups of 8 frames: 15 history + 8 new fit
-constexpr int SK = 516;            // stage row: 512 bins + pad, 2*SK = 8 mod 32 banks
+constexpr int NDFT = 256;          // threads of the DFT role (warps 0..7)
+constexpr int FB = 8;              // frames per batch (four pairs, two warps each)
+constexpr int NPAIR = FB / 2;
+constexpr int SPAIR = 514;         // stage granules per frame pair: 512 bins + pad
+constexpr int TMEM_COLS = 512;
+// named barriers (0 is __syncthreads)
+constexpr int BAR_PAIR = 1;        // 1..4: the two warps of a frame pair
+constexpr int BAR_DFT = 5;         // the eight DFT warps
+constexpr int BAR_READY = 6;       // 6, 7: ring buffer s written
+constexpr int BAR_FREE = 8;        // 8, 9: ring buffer s read
+// tensor-memory columns of a FIR thread (256 per thread: two FIR warps per
+// lane quarter)
+constexpr int TC_TAPS = 0;         // 2 x 32: (g, g) of phases t and t + 256
+constexpr int TC_HIST = 64;        // 4 x 32: 16 frames (re, im) of each phase
 
 __host__ __device__ constexpr int br4(int i) {
   return ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3);
@@ -53,204 +76,271 @@ __host__ __device__ constexpr float cos32v(int e) {
 }
 __host__ __device__ constexpr float sin32v(int e) { return cos32v(e - 8); }
 
-// d * exp(+2 pi i E / 32), with the trivial rotations spelled out.
-template <int E>
-__device__ __forceinline__ float2 rot32(float2 d) {
-  constexpr int e = E & 31;
-  if constexpr (e == 0) {
-    return d;
-  } else if constexpr (e == 8) {
-    return make_float2(-d.y, d.x);
-  } else if constexpr (e == 16) {
-    return make_float2(-d.x, -d.y);
-  } else if constexpr (e == 24) {
-    return make_float2(d.y, -d.x);
-  } else if constexpr (e == 4) {
-    constexpr float r = 0.70710678118654752440f;
-    return make_float2((d.x - d.y) * r, (d.x + d.y) * r);
-  } else if constexpr (e == 12) {
-    constexpr float r = 0.70710678118654752440f;
-    return make_float2(-(d.x + d.y) * r, (d.x - d.y) * r);
-  } else {
-    constexpr float c = cos32v(e), s = sin32v(e);
-    return make_float2(fmaf(d.x, c, -d.y * s), fmaf(d.x, s, d.y * c));
-  }
-}
-
-#define LP_ROT_CASE(n) case n: return rot32<n>(d);
-__device__ __forceinline__ float2 rot32_rt(float2 d, int e) {
-  switch (e & 31) {
-    LP_ROT_CASE(0) LP_ROT_CASE(1) LP_ROT_CASE(2) LP_ROT_CASE(3) LP_ROT_CASE(4)
-    LP_ROT_CASE(5) LP_ROT_CASE(6) LP_ROT_CASE(7) LP_ROT_CASE(8) LP_ROT_CASE(9)
-    LP_ROT_CASE(10) LP_ROT_CASE(11) LP_ROT_CASE(12) LP_ROT_CASE(13) LP_ROT_CASE(14)
-    LP_ROT_CASE(15) LP_ROT_CASE(16) LP_ROT_CASE(17) LP_ROT_CASE(18) LP_ROT_CASE(19)
-    LP_ROT_CASE(20) LP_ROT_CASE(21) LP_ROT_CASE(22) LP_ROT_CASE(23) LP_ROT_CASE(24)
-    LP_ROT_CASE(25) LP_ROT_CASE(26) LP_ROT_CASE(27) LP_ROT_CASE(28) LP_ROT_CASE(29)
-    LP_ROT_CASE(30) LP_ROT_CASE(31)
-  }
-  return d;
-}
-#undef LP_ROT_CASE
-
-__device__ __forceinline__ float2 badd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 bsub(float2 a, float2 b) {
+// Packed FP32 pairs: one instruction for the same operation on two frames.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
 
-// 16-point DFT with kernel exp(+2 pi i k n / 16), radix-2 decimation in
-// frequency: natural-order input, bit-reversed output v[i] = X[br4(i)].
-__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+// One complex value of a frame pair: re = (re_a, re_b), im = (im_a, im_b).
+struct CP {
+  float2 re, im;
+};
+
+__device__ __forceinline__ CP cadd(CP a, CP b) { return CP{add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ CP csub(CP a, CP b) { return CP{sub2(a.re, b.re), sub2(a.im, b.im)}; }
+
+// a * exp(+2 pi i E / 32), the trivial and 45-degree rotations spelled out.
+template <int E>
+__device__ __forceinline__ CP rot32(CP a) {
+  constexpr int e = E & 31;
+  constexpr float r = 0.70710678118654752440f;
+  if constexpr (e == 0) {
+    return a;
+  } else if constexpr (e == 8) {
+    return CP{make_float2(-a.im.x, -a.im.y), a.re};
+  } else if constexpr (e == 16) {
+    return CP{make_float2(-a.re.x, -a.re.y), make_float2(-a.im.x, -a.im.y)};
+  } else if constexpr (e == 24) {
+    return CP{a.im, make_float2(-a.re.x, -a.re.y)};
+  } else if constexpr (e == 4) {
+    return CP{mul2(sub2(a.re, a.im), bc(r)), mul2(add2(a.re, a.im), bc(r))};
+  } else if constexpr (e == 12) {
+    return CP{mul2(add2(a.re, a.im), bc(-r)), mul2(sub2(a.re, a.im), bc(r))};
+  } else if constexpr (e == 20) {
+    return CP{mul2(sub2(a.im, a.re), bc(r)), mul2(add2(a.re, a.im), bc(-r))};
+  } else if constexpr (e == 28) {
+    return CP{mul2(add2(a.re, a.im), bc(r)), mul2(sub2(a.im, a.re), bc(r))};
+  } else {
+    constexpr float c = cos32v(e), s = sin32v(e);
+    return CP{fma2(a.re, bc(c), mul2(a.im, bc(-s))), fma2(a.re, bc(s), mul2(a.im, bc(c)))};
+  }
+}
+
+// Butterfly (a, b) -> (a + b, (a - b) exp(+2 pi i E / 32)); the factor i is
+// taken by swapping the subtraction's operands.
+template <int E>
+__device__ __forceinline__ void bfly(CP& a, CP& b) {
+  const CP s = cadd(a, b);
+  if constexpr ((E & 31) == 8)
+    b = CP{sub2(b.im, a.im), sub2(a.re, b.re)};
+  else
+    b = rot32<E>(csub(a, b));
+  a = s;
+}
+
+#define LP_CASE(n) case n: return rot32<n>(a);
+__device__ __forceinline__ CP rot32_rt(CP a, int e) {   // e is a constant after unrolling
+  switch (e & 31) {
+    LP_CASE(0) LP_CASE(1) LP_CASE(2) LP_CASE(3) LP_CASE(4) LP_CASE(5) LP_CASE(6) LP_CASE(7)
+    LP_CASE(8) LP_CASE(9) LP_CASE(10) LP_CASE(11) LP_CASE(12) LP_CASE(13) LP_CASE(14)
+    LP_CASE(15) LP_CASE(16) LP_CASE(17) LP_CASE(18) LP_CASE(19) LP_CASE(20) LP_CASE(21)
+    LP_CASE(22) LP_CASE(23) LP_CASE(24) LP_CASE(25) LP_CASE(26) LP_CASE(27) LP_CASE(28)
+    LP_CASE(29) LP_CASE(30) LP_CASE(31)
+  }
+  return a;
+}
+#undef LP_CASE
+#define LP_CASE(n) case n: bfly<n>(a, b); return;
+__device__ __forceinline__ void bfly_rt(CP& a, CP& b, int e) {
+  switch (e & 31) {
+    LP_CASE(0) LP_CASE(2) LP_CASE(4) LP_CASE(6) LP_CASE(8) LP_CASE(10) LP_CASE(12) LP_CASE(14)
+  }
+}
+#undef LP_CASE
+
+// 16-point DFT with kernel exp(+2 pi i k q / 16), radix-2 decimation in
+// frequency, all stages but the last (whose twiddle is 1); after the last
+// stage v[i] = X[br4(i)].
+__device__ __forceinline__ void dft16_head(CP (&v)[16]) {
 #pragma unroll
-  for (int span = 8; span >= 1; span >>= 1) {
+  for (int span = 8; span >= 2; span >>= 1) {
 #pragma unroll
     for (int start = 0; start < 16; start += 2 * span) {
 #pragma unroll
-      for (int j = 0; j < span; ++j) {
-        const float2 a = v[start + j], b = v[start + j + span];
-        v[start + j] = badd(a, b);
-        // exp(+2 pi i j / (2 span)) = exp(+2 pi i (16 j / span) / 32)
-        v[start + j + span] = rot32_rt(bsub(a, b), j * (16 / span));
-      }
+      for (int j = 0; j < span; ++j) bfly_rt(v[start + j], v[start + j + span], j * (16 / span));
     }
   }
 }
 
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
-// Barrier for the two warps (64 threads) of one frame.
-__device__ __forceinline__ void pair_sync(int id) {
-  asm volatile("bar.sync %0, 64;\n" ::"r"(id) : "memory");
+__device__ __forceinline__ void bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
 }
 
-// Staging of the beam bins of CTA frames r0 .. r0+7 into stage[f][first_bin + k]
-// (asynchronous copies).  Thread t always copies frame f = t & 7 of bins
-// k = t/8 + 64 i, so its source and destination advance by constants.
+// ---- tensor memory (used here as per-thread storage, no MMA) ----
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
+  uint32_t (&u)[32] = reinterpret_cast<uint32_t(&)[32]>(r);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+        "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+        "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]),
+        "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]),
+        "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) {
+  const uint32_t (&u)[16] = reinterpret_cast<const uint32_t(&)[16]>(r);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16};\n" ::"r"(taddr),
+      "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7]),
+      "r"(u[8]), "r"(u[9]), "r"(u[10]), "r"(u[11]), "r"(u[12]), "r"(u[13]), "r"(u[14]),
+      "r"(u[15]));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
+// Staging of the beam bins of CTA frames r0 .. r0+7 into
+// stage[pair][first_bin + k] (16-byte copies of a frame pair: re_a, im_a,
+// re_b, im_b).  DFT thread t copies pair t & 3 of bins k = t/4 + 64 i, so four
+// neighbouring threads read the 64 contiguous bytes of one bin row and the
+// shared-memory granules of a quarter warp fall in distinct banks.
 struct Stager {
-  const float2* src;      // bin t/8, frame t&7 of CTA frame 0
-  float2* dst;            // stage[t&7][first_bin + t/8]
+  const float2* src;      // bin t/4, frame 2 (t&3) of CTA frame 0
+  int dst;                // granule offset of stage[t&3][first_bin + t/4]
   long long src_step;     // 64 rows
   int n;                  // bins this thread copies
-  int f;                  // its frame within the batch
+  int f;                  // first frame of its pair within the batch
 };
 
-__device__ __forceinline__ Stager make_stager(float2* stage, const float2* brow, int K,
-                                              int first_bin, long long row, int tid) {
+__device__ __forceinline__ Stager make_stager(const float2* brow, int K, int first_bin,
+                                              long long row, int tid) {
   Stager st;
-  st.f = tid & 7;
-  const int k0 = tid >> 3;
+  const int q = tid & 3;
+  const int k0 = tid >> 2;
+  st.f = 2 * q;
   st.src = brow + (long long)k0 * row + st.f;
-  st.dst = stage + st.f * SK + first_bin + k0;
+  st.dst = q * SPAIR + first_bin + k0;
   st.src_step = 64 * row;
   st.n = k0 < K ? (K - k0 + 63) / 64 : 0;
   return st;
 }
 
-__device__ __forceinline__ void stage_batch(const Stager& st, long long m0, long long row, int r0,
-                                            int nfr) {
-  const bool live = r0 + st.f < nfr && m0 + r0 + st.f < row;
+__device__ __forceinline__ void stage_batch(const Stager& st, float4* stage, bool live, int r0) {
   const float2* src = st.src + r0;
+  float4* dst = stage + st.dst;
 #pragma unroll 4
   for (int i = 0; i < st.n; ++i) {
     if (live)
-      cp_async8(st.dst + 64 * i, src + i * st.src_step);
+      cp_async16(dst + 64 * i, src + i * st.src_step);
     else
-      st.dst[64 * i] = make_float2(0.f, 0.f);
+      dst[64 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   cp_async_commit();
 }
 
-// Packed FP32 pairs (one instruction for both components of a complex value).
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __fadd2_rn(a, make_float2(-b.x, -b.y));
-}
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 t) {
-  return make_float2(fmaf(a.x, t.x, -a.y * t.y), fmaf(a.x, t.y, a.y * t.x));
-}
-
-// One warp's half of the 32 x 32 inverse DFT of a frame: HALF = 0 computes
-// the even outputs of both 32-point stages, HALF = 1 the odd ones.
-template <int HALF>
-__device__ __forceinline__ void frame_dft(float2* slot, const float2* st,
-                                          const float2* __restrict__ tw, int lane, int pair_id) {
-  float2 v[16];
+// Inverse DFT of one frame pair by its two warps; H = warp mod 2.
+//   slot: the pair's 2 x 1024 float2 ring slots (frame a, then frame b), also
+//         the 32 x 32 granule transpose buffer between the stages;
+//   st:   stage[pair] + lane.
+template <int H>
+__device__ __forceinline__ void pair_dft(float2* slot, const float4* st,
+                                         const float4* __restrict__ tw, int lane, int bar_id) {
+  float4* tb = reinterpret_cast<float4*>(slot);
+  CP v[16];
+  // ---- stage 1 (k2 = lane): T[p1] = sum_{k1<16} c[32 k1 + lane] w32^(k1 p1), p1 = 2 q + H
 #pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) v[k1] = st[32 * k1];
-  if constexpr (HALF) {
-#pragma unroll
-    for (int k1 = 1; k1 < 16; ++k1) v[k1] = rot32_rt(v[k1], k1);
+  for (int k = 0; k < 16; ++k) {
+    const float4 a = st[32 * k];
+    const CP c{make_float2(a.x, a.z), make_float2(a.y, a.w)};
+    v[k] = H ? rot32_rt(c, k) : c;
   }
-  dft16(v);                               // v[i] = T[p1 = 2 br4(i) + HALF]
+  dft16_head(v);
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int p1 = 2 * br4(i) + HALF;
-    slot[lane * 32 + (p1 ^ lane)] = cmul(v[i], __ldg(tw + p1 * 32 + lane));
-  }
-  pair_sync(pair_id);
-  float2 u[16];
+  for (int i = 0; i < 16; i += 2) bfly<0>(v[i], v[i + 1]);
+  {
+    // twiddle exp(+2 pi i lane p1 / 1024); granule (p1 & 24) + ((p1 & 7) ^ (lane & 7))
+    const int l7 = lane & 7;
+    float4* row = tb + lane * 32;
+    float4* wb[4] = {row + ((0 + H) ^ l7), row + ((2 + H) ^ l7), row + ((4 + H) ^ l7),
+                     row + ((6 + H) ^ l7)};
+    const float4* twl = tw + H * 32 + lane;
 #pragma unroll
-  for (int k2 = 0; k2 < 16; ++k2) {
-    const float2 a = slot[k2 * 32 + (lane ^ k2)];
-    const float2 b = slot[(k2 + 16) * 32 + (lane ^ (k2 + 16))];
-    if constexpr (HALF)
-      u[k2] = rot32_rt(bsub(a, b), k2);
-    else
-      u[k2] = badd(a, b);
-  }
-  pair_sync(pair_id);                     // both warps read the slot before it is overwritten
-  dft16(u);                               // u[i] = z[lane + 32 (2 br4(i) + HALF)]
-#pragma unroll
-  for (int i = 0; i < 16; ++i) slot[lane + 32 * (2 * br4(i) + HALF)] = u[i];
-}
-
-// FIR over the batch for one output phase; TAP_REV selects g_{15-t} (the
-// mirror phase).  Fills e2v = |u|^2 and returns its maximum over the batch.
-template <bool TAP_REV, bool WRITE_Y>
-__device__ __forceinline__ float fir_phase(const float2 (&gq)[kTaps], const float2* ga,
-                                           const float2* gb, const float2* gc, int off,
-                                           float* yrow, unsigned ymask, float (&e2v)[FB]) {
-  float2 zw[kHist + FB];
-#pragma unroll
-  for (int w = 0; w < 7; ++w) zw[w] = ga[(w + 1) * kM + off];
-#pragma unroll
-  for (int w = 0; w < FB; ++w) zw[7 + w] = gb[w * kM + off];
-#pragma unroll
-  for (int w = 0; w < FB; ++w) zw[15 + w] = gc[w * kM + off];
-  float emax = 0.f;
-#pragma unroll
-  for (int f = 0; f < FB; ++f) {
-    float2 u = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int t = 0; t < kTaps; ++t)   // both components per instruction, tap (g, g)
-      u = __ffma2_rn(TAP_REV ? gq[kTaps - 1 - t] : gq[t], zw[f + kHist - t], u);
-    if constexpr (WRITE_Y) {
-      if ((ymask >> f) & 1u) yrow[f * kM + off] = u.x;
+    for (int i = 0; i < 16; ++i) {
+      const int q = br4(i);
+      const float4 t = __ldg(twl + q * 64);
+      const float2 c = make_float2(t.x, t.y), s = make_float2(t.z, t.w);
+      const float2 re = fma2(v[i].re, c, mul2(v[i].im, make_float2(-s.x, -s.y)));
+      const float2 im = fma2(v[i].re, s, mul2(v[i].im, c));
+      wb[q & 3][8 * (q >> 2)] = make_float4(re.x, re.y, im.x, im.y);
     }
-    e2v[f] = fmaf(u.x, u.x, u.y * u.y);
-    emax = fmaxf(emax, e2v[f]);          // frames outside the run are filtered later
   }
-  return emax;
+  bar_sync(bar_id, 64);
+  // ---- stage 2 (p1 = lane): inputs T'[k2][lane], folded by output parity H
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float4* r = tb + (lane ^ (k & 7)) + 32 * k;
+    const float4 a = r[0], b = r[512];                  // rows k and k + 16
+    const CP ca{make_float2(a.x, a.y), make_float2(a.z, a.w)};
+    const CP cb{make_float2(b.x, b.y), make_float2(b.z, b.w)};
+    v[k] = H ? rot32_rt(csub(ca, cb), k) : cadd(ca, cb);
+  }
+  bar_sync(bar_id, 64);                  // both warps have read the transpose
+  dft16_head(v);
+  // last butterfly stage in scalar form, written straight out as (re, im) of
+  // each frame: z[lane + 32 p2], p2 = 2 br4(i) + H
+  float2* za = slot + lane + 32 * H;
+  float2* zb = za + kM;
+#pragma unroll
+  for (int i = 0; i < 16; i += 2) {
+    const CP a = v[i], b = v[i + 1];
+    const int o0 = 64 * br4(i), o1 = 64 * br4(i + 1);
+    za[o0] = make_float2(a.re.x + b.re.x, a.im.x + b.im.x);
+    zb[o0] = make_float2(a.re.y + b.re.y, a.im.y + b.im.y);
+    za[o1] = make_float2(a.re.x - b.re.x, a.im.x - b.im.x);
+    zb[o1] = make_float2(a.re.y - b.re.y, a.im.y - b.im.y);
+  }
 }
 
-template <bool WRITE_Y>
-__device__ __forceinline__ void fir_batch(const float2 (&gq)[kTaps], const float2* ga,
-                                          const float2* gb, const float2* gc, int tid, int lane,
-                                          float* yrow, unsigned ymask, unsigned vmask, float th2,
-                                          long long n_row0, int j, int P, int Tr, float sig,
-                                          TriggerRec* trig, unsigned long long* trig_count,
-                                          long long trig_cap);
+// Trigger output of a launch (kernel parameter; read from the constant bank).
+struct TrigOut {
+  TriggerRec* trig;
+  unsigned long long* count;
+  long long cap;
+  int P, Tr;
+};
 
-__device__ __forceinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmask, float th2,
-                                              int lane, int p, long long n_row0, int j, int P,
-                                              int Tr, float sig, TriggerRec* trig,
-                                              unsigned long long* trig_count, long long trig_cap) {
+__device__ __noinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmask, float th2,
+                                           int p, long long n_row0, const TrigOut& o,
+                                           const float* __restrict__ theta, float k_sigma) {
+  const int lane = threadIdx.x & 31, j = blockIdx.y;
+  const int P = o.P, Tr = o.Tr;
+  const float sig = theta[j] / k_sigma;
 #pragma unroll
   for (int f = 0; f < FB; ++f) {
     const bool hit = ((vmask >> f) & 1u) && e2v[f] > th2;
@@ -258,11 +348,11 @@ __device__ __forceinline__ void emit_triggers(const float (&e2v)[FB], unsigned v
     if (!mask) continue;
     const int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(trig_count, (unsigned long long)__popc(mask));
+    if (lane == leader) base = atomicAdd(o.count, (unsigned long long)__popc(mask));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (hit) {
       const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
-      if ((long long)idx < trig_cap) {
+      if ((long long)idx < o.cap) {
         TriggerRec rec;
         rec.n = n_row0 + (long long)f * kM + p;
         rec.pol = j % P;
@@ -271,122 +361,198 @@ __device__ __forceinline__ void emit_triggers(const float (&e2v)[FB], unsigned v
         rec.stream = j;
         rec.env = sqrtf(e2v[f]);
         rec.sigma = sig;
-        trig[idx] = rec;
+        o.trig[idx] = rec;
       }
     }
   }
 }
 
-template <bool WRITE_Y>
-__device__ __forceinline__ void fir_batch(const float2 (&gq)[kTaps], const float2* ga,
-                                          const float2* gb, const float2* gc, int tid, int lane,
-                                          float* yrow, unsigned ymask, unsigned vmask, float th2,
-                                          long long n_row0, int j, int P, int Tr, float sig,
-                                          TriggerRec* trig, unsigned long long* trig_count,
-                                          long long trig_cap) {
+// Per-batch context of the FIR role.
+struct FirCtx {
+  float th2;
+  unsigned ymask, vmask;   // output frames of the batch / those that may trigger
+  long long n_row0;        // sample index of batch row 0, phase 0
+  float* yrow;             // y of batch row 0 (or null)
+};
+
+// FIR of one phase over one batch.  hist: the phase's 16 history slots (frame
+// r at slot r mod 16, (re, im) in consecutive columns); zn: the 8 new frames.
+// ODD selects where the 15 history frames r0-15 .. r0-1 sit (r0 mod 16 = 8 ODD).
+template <int ODD, bool TAP_REV>
+__device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float (&hist)[32],
+                                          const float2 (&zn)[FB], int p, const FirCtx& c,
+                                          const TrigOut& o, const float* __restrict__ theta,
+                                          float k_sigma) {
+  float2 w[kHist + FB];
+#pragma unroll
+  for (int i = 0; i < kHist; ++i) {
+    const int slot = (ODD ? 9 + i : 1 + i) & 15;
+    w[i] = make_float2(hist[2 * slot], hist[2 * slot + 1]);
+  }
+#pragma unroll
+  for (int f = 0; f < FB; ++f) w[kHist + f] = zn[f];
   float e2v[FB];
-  {
-    const float em = fir_phase<false, WRITE_Y>(gq, ga, gb, gc, tid, yrow, ymask, e2v);
-    if (__any_sync(0xffffffffu, em > th2))
-      emit_triggers(e2v, vmask, th2, lane, tid, n_row0, j, P, Tr, sig, trig, trig_count,
-                    trig_cap);
+  float emax = 0.f;
+#pragma unroll
+  for (int f = 0; f < FB; ++f) {
+    float2 u = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < kTaps; ++t)   // both components per instruction, tap (g, g)
+      u = __ffma2_rn(TAP_REV ? gq[kTaps - 1 - t] : gq[t], w[f + kHist - t], u);
+    if (c.yrow && ((c.ymask >> f) & 1u)) c.yrow[f * kM + p] = u.x;
+    e2v[f] = fmaf(u.x, u.x, u.y * u.y);
+    emax = fmaxf(emax, e2v[f]);         // frames outside the run are filtered by vmask
   }
-  {
-    const int p = kM - 1 - tid;
-    const float em = fir_phase<true, WRITE_Y>(gq, ga, gb, gc, p, yrow, ymask, e2v);
-    if (__any_sync(0xffffffffu, em > th2))
-      emit_triggers(e2v, vmask, th2, lane, p, n_row0, j, P, Tr, sig, trig, trig_count,
-                    trig_cap);
+  if (__any_sync(0xffffffffu, emax > c.th2))
+    emit_triggers(e2v, c.vmask, c.th2, p, c.n_row0, o, theta, k_sigma);
+}
+
+// Bits [lo, hi) of an 8-bit frame mask (lo, hi clamped to [0, 8]).
+__device__ __forceinline__ unsigned frame_bits(int lo, int hi) {
+  lo = max(0, min(lo, FB));
+  hi = max(lo, min(hi, FB));
+  return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+}
+
+// One phase of the FIR role for batch r0: new frames from the ring, history
+// from tensor memory, new frames into the history slots r0 mod 16 ...
+template <bool TAP_REV>
+__device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t thist,
+                                        const float2* zr, int p, int r0, bool outputs,
+                                        const FirCtx& c, const TrigOut& o,
+                                        const float* __restrict__ theta, float k_sigma) {
+  float2 zn[FB];
+#pragma unroll
+  for (int f = 0; f < FB; ++f) zn[f] = zr[f * kM + p];
+  if (outputs) {
+    float hist[32];
+    tmem_ld32(thist, hist);
+    tmem_wait_ld();
+    if (r0 & 8)
+      fir_phase<1, TAP_REV>(gq, hist, zn, p, c, o, theta, k_sigma);
+    else
+      fir_phase<0, TAP_REV>(gq, hist, zn, p, c, o, theta, k_sigma);
   }
+  float nr[16];
+#pragma unroll
+  for (int f = 0; f < FB; ++f) {
+    nr[2 * f] = zn[f].x;
+    nr[2 * f + 1] = zn[f].y;
+  }
+  tmem_st16(thist + 2 * (r0 & 8), nr);
 }
 
 __global__ void __launch_bounds__(NT, 1) k_ippf(
     const float2* __restrict__ beams, int K, int first_bin, long long F, long long row,
-    int frames_per_cta, const float* __restrict__ g, const float2* __restrict__ tw,
+    int frames_per_cta, const float* __restrict__ g, const float4* __restrict__ tw,
     const float* __restrict__ theta, const float* __restrict__ theta2, float k_sigma,
-    const long long* __restrict__ blk, long long F_total, long long f_base, int P, int Tr,
-    float* __restrict__ y,
-    TriggerRec* __restrict__ trig, unsigned long long* __restrict__ trig_count,
-    long long trig_cap) {
-  extern __shared__ float2 smem[];
-  float2* ring = smem;                      // [3 groups][8 frames][1024]
-  float2* stage = ring + RING * kM;         // [8 frames][SK], bins 0..511
+    const long long* __restrict__ blk, long long F_total, long long f_base, float* __restrict__ y,
+    const __grid_constant__ TrigOut tout) {
+  extern __shared__ float4 smem4[];
+  float2* ring = reinterpret_cast<float2*>(smem4);      // [2 buffers][8 frames][1024]
+  float4* stage = smem4 + FB * kM;                        // [2 buffers][4 pairs][SPAIR]
+  __shared__ uint32_t tmem_slot;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int fr = warp >> 1, half = warp & 1;   // frame of the batch, output parity
   const int j = blockIdx.y;
   const long long m0 = (long long)blockIdx.x * frames_per_cta;
   const long long m1 = min((long long)(m0 + frames_per_cta), (long long)(F));
   const int nout = (int)(m1 - m0);
   const int nfr = nout + kPrefix;          // frames run through the inverse DFT
   const int nbatch = (nfr + FB - 1) / FB;
-  const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
 
+  if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
   // bins outside the selection stay zero for the whole run
-  for (int i = tid; i < FB * SK; i += NT) stage[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < 2 * NPAIR * SPAIR; i += NT) stage[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  tc_fence_before();
   __syncthreads();
-  const Stager stg = make_stager(stage, brow, K, first_bin, row, tid);
-  stage_batch(stg, m0, row, 0, nfr);
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
 
-  float2 gq[kTaps];                        // taps (g, g) of phase tid (mirrored for 1023 - tid)
-#pragma unroll
-  for (int t = 0; t < kTaps; ++t) {
-    const float gt = g[t * kM + tid];
-    gq[t] = make_float2(gt, gt);
-  }
-  const float th2 = theta2[j];
-  // this launch covers block frames [f_base, f_base + F) (one chunk, or the block)
-  float* yj = y ? y + ((long long)j * F_total + f_base) * kM : nullptr;
-  // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
-  // m < 15 of the first block) never trigger
-  const long long bidx = *blk;
-  const long long n_first = (bidx * F_total + f_base - kHist) * (long long)kM;
-  const int frame_min_trigger = (bidx == 0 && f_base == 0) ? kHist : 0;
-
-  for (int bi = 0; bi < nbatch; ++bi) {
-    const int r0 = bi * FB;
-    const int gi = bi % 3;
-    cp_async_wait_all();
-    __syncthreads();   // stage of this batch landed; previous FIR is done with the ring
-    // inverse DFT of frame r0+fr by warps (2 fr, 2 fr + 1) into ring group gi, slot fr
-    {
-      float2* slot = ring + (gi * FB + fr) * kM;
-      const float2* st = stage + fr * SK + lane;
-      if (half)
-        frame_dft<1>(slot, st, tw, lane, 1 + fr);
+  if (warp < NDFT / 32) {
+    // ===================== DFT role =====================
+    const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
+    const Stager stg = make_stager(brow, K, first_bin, row, tid);
+    // a pair is copied when both its frames are in the run and inside the row
+    const int live_lim = (int)min((long long)nfr, row - m0);
+    stage_batch(stg, stage, stg.f + 1 < live_lim, 0);
+    const int pr = warp >> 1, h = warp & 1;     // frame pair of the batch, output parity
+    for (int bi = 0; bi < nbatch; ++bi) {
+      const int s = bi & 1;
+      cp_async_wait_all();
+      bar_sync(BAR_DFT, NDFT);   // batch bi staged; stage buffer s^1 no longer read
+      if (bi + 1 < nbatch)
+        stage_batch(stg, stage + (s ^ 1) * NPAIR * SPAIR, (bi + 1) * FB + stg.f + 1 < live_lim,
+                    (bi + 1) * FB);
+      if (bi >= 2) bar_sync(BAR_FREE + s, NT);   // the FIR role is done with ring buffer s
+      float2* slot = ring + (s * FB + 2 * pr) * kM;
+      const float4* st = stage + s * NPAIR * SPAIR + pr * SPAIR + lane;
+      if (h)
+        pair_dft<1>(slot, st, tw, lane, BAR_PAIR + pr);
       else
-        frame_dft<0>(slot, st, tw, lane, 1 + fr);
+        pair_dft<0>(slot, st, tw, lane, BAR_PAIR + pr);
+      bar_arrive(BAR_READY + s, NT);
     }
-    __syncthreads();   // ring group gi written; stage consumed
-    if (bi + 1 < nbatch) stage_batch(stg, m0, row, r0 + FB, nfr);
-    if (r0 + FB <= kPrefix) continue;     // history-only batch (uniform)
-
-    // synthesis FIR + envelope threshold for frames r0 .. r0+7.  History frames
-    // r0-15 .. r0-9 sit in group gi+1 (slots 1..7), r0-8 .. r0-1 in group gi+2.
-    const float2* ga = ring + (((gi + 1) % 3) * FB) * kM;
-    const float2* gb = ring + (((gi + 2) % 3) * FB) * kM;
-    const float2* gc = ring + (gi * FB) * kM;
-    unsigned vmask = 0;                    // output frames of the batch that may trigger
-    unsigned ymask = 0;                    // output frames of the batch
+  } else {
+    // ===================== FIR role =====================
+    const int ft = tid - NDFT;
+    const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 256u * ((warp - 8) >> 2);
+    // taps (g, g) of phases ft and ft + 256 into tensor memory
 #pragma unroll
-    for (int f = 0; f < FB; ++f) {
-      const int r = r0 + f;
-      const long long m = m0 - kPrefix + r;
-      if (r >= kPrefix && r < nfr) {
-        ymask |= 1u << f;
-        if (m >= frame_min_trigger) vmask |= 1u << f;
+    for (int m = 0; m < 2; ++m) {
+      float tq[32];
+#pragma unroll
+      for (int t = 0; t < kTaps; ++t) {
+        const float gt = g[t * kM + ft + 256 * m];
+        tq[2 * t] = gt;
+        tq[2 * t + 1] = gt;
       }
+      tmem_st16(tbase + TC_TAPS + 32 * m, reinterpret_cast<const float(&)[16]>(tq[0]));
+      tmem_st16(tbase + TC_TAPS + 32 * m + 16, reinterpret_cast<const float(&)[16]>(tq[16]));
     }
-    const long long m_row0 = m0 - kPrefix + r0;             // frame of batch row 0
-    float* yrow = yj ? yj + m_row0 * kM : nullptr;
-    const long long n_row0 = n_first + m_row0 * kM;
-    if (yrow)
-      fir_batch<true>(gq, ga, gb, gc, tid, lane, yrow, ymask, vmask, th2, n_row0, j, P, Tr,
-                      theta[j] / k_sigma, trig, trig_count, trig_cap);
-    else
-      fir_batch<false>(gq, ga, gb, gc, tid, lane, yrow, ymask, vmask, th2, n_row0, j, P, Tr,
-                       theta[j] / k_sigma, trig, trig_count, trig_cap);
+    tmem_wait_st();
+    FirCtx c;
+    c.th2 = theta2[j];
+    // this launch covers block frames [f_base, f_base + F) (one chunk, or the block)
+    float* yj = y ? y + ((long long)j * F_total + f_base) * kM : nullptr;
+    // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
+    // m < 15 of the first block) never trigger
+    const long long bidx = *blk;
+    const long long n_first = (bidx * F_total + f_base - kHist) * (long long)kM;
+    const int frame_min_trigger = (bidx == 0 && f_base == 0) ? kHist : 0;
+    // run row r (frame m0 - 16 + r) is an output for r in [16, nfr) and may
+    // trigger for r >= r_trig
+    const int r_trig = (int)max((long long)kPrefix, frame_min_trigger + kPrefix - m0);
+    for (int bi = 0; bi < nbatch; ++bi) {
+      const int s = bi & 1, r0 = bi * FB;
+      bar_sync(BAR_READY + s, NT);       // ring buffer s holds batch bi
+      const float2* zr = ring + s * FB * kM;
+      const bool outputs = r0 >= kPrefix;
+      c.ymask = frame_bits(kPrefix - r0, nfr - r0);
+      c.vmask = c.ymask & frame_bits(r_trig - r0, FB);
+      const long long m_row0 = m0 - kPrefix + r0;             // frame of batch row 0
+      c.yrow = yj ? yj + m_row0 * kM : nullptr;
+      c.n_row0 = n_first + m_row0 * kM;
+#pragma unroll 1
+      for (int m = 0; m < 2; ++m) {
+        float tq[32];
+        tmem_ld32(tbase + TC_TAPS + 32 * m, tq);
+        tmem_wait_ld();
+        float2 gq[kTaps];
+#pragma unroll
+        for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
+        const int p = ft + 256 * m;     // and its mirror M - 1 - p
+        fir_one<false>(gq, tbase + TC_HIST + 64 * m, zr, p, r0, outputs, c, tout, theta, k_sigma);
+        fir_one<true>(gq, tbase + TC_HIST + 64 * m + 32, zr, kM - 1 - p, r0, outputs, c, tout,
+                      theta, k_sigma);
+      }
+      tmem_wait_st();                    // history slots written before the next batch reads them
+      if (bi + 2 < nbatch) bar_arrive(BAR_FREE + s, NT);
+    }
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // Block noise power and running sigma (one block of 256 threads per stream).
@@ -434,7 +600,9 @@ __global__ void k_history_shift(float2* __restrict__ beams, long long rows, long
   beams[r * row + f] = beams[r * row + F + f];
 }
 
-size_t ippf_smem_bytes() { return (size_t)(RING * kM + FB * SK) * sizeof(float2); }
+size_t ippf_smem_bytes() {
+  return (size_t)2 * FB * kM * sizeof(float2) + (size_t)2 * NPAIR * SPAIR * sizeof(float4);
+}
 
 }  // namespace
 
@@ -457,11 +625,11 @@ cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s) {
   const auto& sh = p.shape;
   const int fpc = p.frames_per_cta;
   const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)sh.J());
+  const TrigOut tout{p.buf.trig, p.buf.trig_count, (long long)p.cfg.trigger_cap, sh.P, sh.Tr};
   k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(p.buf.beams, sh.K, p.cfg.first_bin, c.nf, p.row(), fpc,
                                              p.buf.g, p.buf.tw1024, p.buf.theta, p.buf.theta2,
-                                             (float)p.cfg.k_sigma, p.buf.blk, sh.F, c.f_base, sh.P,
-                                             sh.Tr, p.buf.y, p.buf.trig, p.buf.trig_count,
-                                             p.cfg.trigger_cap);
+                                             (float)p.cfg.k_sigma, p.buf.blk, sh.F, c.f_base,
+                                             p.buf.y, tout);
   return cudaGetLastError();
 }
 

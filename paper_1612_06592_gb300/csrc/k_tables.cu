@@ -11,7 +11,9 @@
 //  * Synthesis filter: g[n] = (2/M) M^2 h[n], h the Kaiser-windowed sinc
 //    (beta = 9, zeros every M samples) normalised to sum 1; the factor 2/M is
 //    the analytic inverse FFT's scale folded in.  The same set-up kernel
-//    writes the 32 x 32 twiddles exp(+2 pi i p1 l / 1024) of the inverse DFT.
+//    writes the 32 x 32 twiddles exp(+2 pi i p1 l / 1024) of the inverse DFT,
+//    each as (cos, cos, sin, sin) so that one 16-byte load gives the
+//    broadcast pairs for two frames.
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -33,7 +35,7 @@ __device__ double bessel_i0_series(double x) {
 __global__ void __launch_bounds__(1024) k_prototype(double beta, double* __restrict__ proto,
                                                     double* __restrict__ sums,
                                                     float* __restrict__ g,
-                                                    float2* __restrict__ tw1024) {
+                                                    float4* __restrict__ tw1024) {
   constexpr int L = kM * kTaps;
   __shared__ double red_h[1024];
   __shared__ double red_h2[1024];
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(1024) k_prototype(double beta, double* __restr
     const int i = threadIdx.x;
     double sn, cs;
     sincospi((double)((i >> 5) * (i & 31)) / 512.0, &sn, &cs);
-    tw1024[i] = make_float2((float)cs, (float)sn);
+    tw1024[i] = make_float4((float)cs, (float)cs, (float)sn, (float)sn);
   }
 }
 

@@ -56,7 +56,7 @@ size_t carve(lp_plan& p, char* base) {
   b.dd = (float2*)take(sizeof(float2) * (size_t)sh.K * sh.Tr);
   b.proto = (double*)take(sizeof(double) * kM * lp::kTaps);
   b.g = (float*)take(sizeof(float) * kM * lp::kTaps);
-  b.tw1024 = (float2*)take(sizeof(float2) * kM);
+  b.tw1024 = (float4*)take(sizeof(float4) * kM);
   b.filter_sums = (double*)take(sizeof(double) * 2);
   b.beams = (float2*)take(sizeof(float2) * (size_t)J * sh.K * p.row());
   b.power_part = (float*)take(sizeof(float) * (size_t)J * sh.K * p.n_ftiles_bf);

@@ -40,7 +40,7 @@ struct Buffers {
   float2* dd;              // [K][Tr] de-dispersion phasors
   double* proto;           // [16384] unnormalised prototype (scratch for filter build)
   float* g;                // [16384] synthesis filter * 2/M
-  float2* tw1024;          // [32 p1][32 l] exp(+2 pi i p1 l / 1024)
+  float4* tw1024;          // [32 p1][32 l] exp(+2 pi i p1 l / 1024) as (c, c, s, s)
   double* filter_sums;     // [2]: sum h, sum h^2 of the unnormalised prototype
   float2* beams;           // [J][K][row], row = F + 16, frame m at m + 16
   float* power_part;       // [J][K][n_ftiles] partial sums of |beam|^2

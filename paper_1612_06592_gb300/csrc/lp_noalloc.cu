@@ -102,7 +102,7 @@ extern "C" lp_status lp_process_block_noalloc(
   size_t o_pr = off;  off = up256(off + sizeof(double) * lp::kM * lp::kTaps);
   size_t o_g = off;   off = up256(off + sizeof(float) * lp::kM * lp::kTaps);
   size_t o_fs = off;  off = up256(off + sizeof(double) * 2);
-  size_t o_tw = off;  off = up256(off + sizeof(float2) * lp::kM);
+  size_t o_tw = off;  off = up256(off + sizeof(float4) * lp::kM);
   size_t o_bm = off;  off = up256(off + sizeof(float2) * J * sh.K * p.row());
   size_t o_pp = off;  off = up256(off + sizeof(float) * J * sh.K * p.n_ftiles_bf);
   size_t o_s2 = off;  off = up256(off + sizeof(double) * J);
@@ -140,7 +140,7 @@ extern "C" lp_status lp_process_block_noalloc(
   buf.proto = (double*)(b + o_pr);
   buf.g = (float*)(b + o_g);
   buf.filter_sums = (double*)(b + o_fs);
-  buf.tw1024 = (float2*)(b + o_tw);
+  buf.tw1024 = (float4*)(b + o_tw);
   buf.beams = (float2*)(b + o_bm);
   buf.power_part = (float*)(b + o_pp);
   buf.sigma2 = sigma2 ? sigma2 : (double*)(b + o_s2);
