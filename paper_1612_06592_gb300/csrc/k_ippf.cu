@@ -152,12 +152,13 @@ __device__ __forceinline__ void bfly_rt(CP& a, CP& b, int e) {
 }
 #undef LP_CASE
 
-// 16-point DFT with kernel exp(+2 pi i k q / 16), radix-2 decimation in
-// frequency, all stages but the last (whose twiddle is 1); after the last
-// stage v[i] = X[br4(i)].
-__device__ __forceinline__ void dft16_head(CP (&v)[16]) {
+// Radix-2 decimation-in-frequency stages of the 16-point DFT with kernel
+// exp(+2 pi i k q / 16), from half-size SPAN down to 2; the last stage (twiddle
+// 1) is left to the caller.  After all stages v[i] = X[br4(i)].
+template <int SPAN>
+__device__ __forceinline__ void dft16_stages(CP (&v)[16]) {
 #pragma unroll
-  for (int span = 8; span >= 2; span >>= 1) {
+  for (int span = SPAN; span >= 2; span >>= 1) {
 #pragma unroll
     for (int start = 0; start < 16; start += 2 * span) {
 #pragma unroll
@@ -218,6 +219,10 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) 
       "r"(u[8]), "r"(u[9]), "r"(u[10]), "r"(u[11]), "r"(u[12]), "r"(u[13]), "r"(u[14]),
       "r"(u[15]));
 }
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};\n" ::"r"(taddr),
+               "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)));
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
@@ -273,14 +278,28 @@ __device__ __forceinline__ void pair_dft(float2* slot, const float4* st,
                                          const float4* __restrict__ tw, int lane, int bar_id) {
   float4* tb = reinterpret_cast<float4*>(slot);
   CP v[16];
-  // ---- stage 1 (k2 = lane): T[p1] = sum_{k1<16} c[32 k1 + lane] w32^(k1 p1), p1 = 2 q + H
+  // ---- stage 1 (k2 = lane): T[p1] = sum_{k1<16} c[32 k1 + lane] w32^(k1 p1), p1 = 2 q + H,
+  // a 16-point DFT of d[k1] = c[k1] w32^(k1 H).  Its first stage is taken in
+  // scalar form straight from the stage's (re_a, im_a, re_b, im_b) granules,
+  // which regroups them into frame pairs at no extra cost:
+  //   H = 0: (c_k + c_{k+8},  (c_k - c_{k+8}) w32^(2k))
+  //   H = 1: ((c_k + i c_{k+8}) w32^k,  (c_k - i c_{k+8}) w32^(3k))
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const float4 a = st[32 * k];
-    const CP c{make_float2(a.x, a.z), make_float2(a.y, a.w)};
-    v[k] = H ? rot32_rt(c, k) : c;
+  for (int k = 0; k < 8; ++k) {
+    const float4 a = st[32 * k], b = st[32 * (k + 8)];
+    if constexpr (H == 0) {
+      const CP sm{make_float2(a.x + b.x, a.z + b.z), make_float2(a.y + b.y, a.w + b.w)};
+      const CP df{make_float2(a.x - b.x, a.z - b.z), make_float2(a.y - b.y, a.w - b.w)};
+      v[k] = sm;
+      v[k + 8] = rot32_rt(df, 2 * k);
+    } else {
+      const CP sm{make_float2(a.x - b.y, a.z - b.w), make_float2(a.y + b.x, a.w + b.z)};
+      const CP df{make_float2(a.x + b.y, a.z + b.w), make_float2(a.y - b.x, a.w - b.z)};
+      v[k] = rot32_rt(sm, k);
+      v[k + 8] = rot32_rt(df, 3 * k);
+    }
   }
-  dft16_head(v);
+  dft16_stages<4>(v);
 #pragma unroll
   for (int i = 0; i < 16; i += 2) bfly<0>(v[i], v[i + 1]);
   {
@@ -311,7 +330,7 @@ __device__ __forceinline__ void pair_dft(float2* slot, const float4* st,
     v[k] = H ? rot32_rt(csub(ca, cb), k) : cadd(ca, cb);
   }
   bar_sync(bar_id, 64);                  // both warps have read the transpose
-  dft16_head(v);
+  dft16_stages<8>(v);
   // last butterfly stage in scalar form, written straight out as (re, im) of
   // each frame: z[lane + 32 p2], p2 = 2 br4(i) + H
   float2* za = slot + lane + 32 * H;
@@ -433,13 +452,8 @@ __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t this
     else
       fir_phase<0, TAP_REV>(gq, hist, zn, p, c, o, theta, k_sigma);
   }
-  float nr[16];
 #pragma unroll
-  for (int f = 0; f < FB; ++f) {
-    nr[2 * f] = zn[f].x;
-    nr[2 * f + 1] = zn[f].y;
-  }
-  tmem_st16(thist + 2 * (r0 & 8), nr);
+  for (int f = 0; f < FB; ++f) tmem_st2(thist + 2 * ((r0 & 8) + f), zn[f]);
 }
 
 __global__ void __launch_bounds__(NT, 1) k_ippf(
