@@ -286,6 +286,7 @@ def run_ours(args, rank, world, local_rank):
             plan.lp_get_triggers()
         barrier()
         torch.cuda.synchronize()
+        plan.lp_profile_read()
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.steps):
@@ -295,6 +296,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         barrier()
+        e2e_stages, n_e2e = plan.lp_profile_read()
         e2e = (t_e2e, d2h / args.steps, x.numel() * x.element_size())
 
     if world > 1:
@@ -360,7 +362,8 @@ def run_ours(args, rank, world, local_rank):
         line["e2e"] = {"value": world * block_s / (t_e2e / args.steps), "unit": "x realtime",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": t_e2e / args.steps * 1e3,
-                       "path": "lp_process_block(pinned host block) + lp_get_triggers"}
+                       "path": "lp_process_block(pinned host block) + lp_get_triggers",
+                       "stage_ms": {k: v / max(n_e2e, 1) for k, v in e2e_stages.items()}}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, x, min(args.cpu_sample_frames, w.block_len))
     if args.serve_blocks > 0 and not args.frames:

@@ -148,7 +148,11 @@ lp_status lp_set_tec(lp_plan* plan, const double* tec_tecu, void* stream);
  * pointer (host pointers need host_input = 1; the copy is part of the call).
  * Runs: beamform + de-disperse, block noise power and running sigma, inverse
  * FFT + synthesis FIR + envelope threshold, history shift.  Triggers of the
- * previous block are discarded. */
+ * previous block are discarded.  A host block with P = 2 (not chunked, no
+ * graph) is copied one polarisation at a time on a stream of the plan, and
+ * the work on polarisation 0 overlaps the copy of polarisation 1; the copy
+ * starts once earlier work on `stream` is done, and `stream` finishes after
+ * both copies. */
 lp_status lp_process_block(lp_plan* plan, const void* x, void* stream);
 
 /* As lp_process_block, for a view of a larger array: pol slab p starts
@@ -193,7 +197,8 @@ lp_status lp_reset_stream(lp_plan* plan, void* stream);
 lp_status lp_plan_autotune(lp_plan* plan, const void* x, void* stream, int32_t* best,
                            double* ms_out);
 
-/* Number of kernel launches lp_process_block makes (for accounting). */
+/* Number of kernel launches lp_process_block makes for a device block (for
+ * accounting); a host block processed per polarisation makes 8. */
 int lp_launches_per_block(const lp_plan* plan);
 
 /* Stage timing.  When enabled, lp_process_block records a CUDA event pair

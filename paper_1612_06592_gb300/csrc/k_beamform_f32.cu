@@ -24,13 +24,13 @@ template <typename T2>
 __global__ void __launch_bounds__(FT) k_beamform_f32(
     const T2* __restrict__ x, long long pol_stride, const float2* __restrict__ w,
     const float2* __restrict__ dd, int S, int P, int K, int B, int Tr, long long F, long long row,
-    float2* __restrict__ beams, float* __restrict__ power_part, int n_ftiles) {
+    float2* __restrict__ beams, float* __restrict__ power_part, int n_ftiles, int pol0) {
   extern __shared__ float2 smem[];
   float2* xs = smem;                 // [S][FT]
   float2* ws = smem + S * FT;        // [BC][S]
   __shared__ float red[FT / 32][BC];
 
-  const int tile = blockIdx.x, k = blockIdx.y, pol = blockIdx.z;
+  const int tile = blockIdx.x, k = blockIdx.y, pol = pol0 + (int)blockIdx.z;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long f0 = (long long)tile * FT;
   const long long f = f0 + tid;
@@ -119,19 +119,19 @@ cudaError_t init_f32_attributes(const Shape& sh) {
 }
 
 cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_stride,
-                                cudaStream_t s) {
+                                cudaStream_t s, PolSel ps) {
   const auto& sh = p.shape;
   const int ntile = (int)((sh.F + FT - 1) / FT);
-  const dim3 grid(ntile, sh.K, sh.P);
+  const dim3 grid(ntile, sh.K, ps.npol ? ps.npol : sh.P);
   const size_t smem = f32_smem(sh);
   if (p.cfg.input_dtype == LP_INPUT_INT8) {
     k_beamform_f32<char2><<<grid, FT, smem, s>>>((const char2*)x, pol_stride, p.buf.w32, p.buf.dd,
                                                  sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F, p.row(),
-                                                 p.buf.beams, p.buf.power_part, ntile);
+                                                 p.buf.beams, p.buf.power_part, ntile, ps.pol0);
   } else {
     k_beamform_f32<short2><<<grid, FT, smem, s>>>((const short2*)x, pol_stride, p.buf.w32,
                                                   p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F,
-                                                  p.row(), p.buf.beams, p.buf.power_part, ntile);
+                                                  p.row(), p.buf.beams, p.buf.power_part, ntile, ps.pol0);
   }
   return cudaGetLastError();
 }

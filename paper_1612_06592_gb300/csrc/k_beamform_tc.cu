@@ -26,8 +26,10 @@
 //               accumulator;
 //   warps 6-13  epilogue: two warps per 32-lane TMEM quarter (one per column
 //               half) read the accumulator with tcgen05.ld, pair Re/Im lanes
-//               by shuffle, multiply by D[k,t], write 64-byte runs of the
-//               [stream][k][frame] beam rows, sum |beam|^2 per chunk.
+//               by shuffle, multiply by D[k,t], sum |beam|^2 per chunk, and
+//               stage 16-beam x 16-frame boxes (128-byte swizzle) that a TMA
+//               tensor store (cp.async.bulk.tensor, 5-D map over
+//               [beam][trial][pol][k][frame]) writes to the beam rows.
 // The epilogue of tile i, the MMAs of tile i+1, the conversion of tile i+2
 // and the copies of tiles i+3.. overlap.  Every mbarrier wait is bounded and
 // watches a block-wide abort flag: on timeout the block raises the device
@@ -226,6 +228,7 @@ struct TcArgs {
   long long F_in, f_base;   // input frames per subband row, first input frame of the launch
   int chunk_base, n_chunks_total;   // noise-partial chunk index offset, chunks per block
   int write_beams, write_power;
+  int pol0, npol;           // polarisations of this launch: pol0 .. pol0 + npol - 1
   long long n_items;
   int n_s8, n_sb;           // pipeline depths (int8 ring, FP16 ring)
 };
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
   const long long it0 = blockIdx.x * per;
   const long long it1 = min(a.n_items, it0 + per);
   TileSeq q;
-  q.start(it0, it1, a.n_chunks, a.P, a.F);
+  q.start(it0, it1, a.n_chunks, a.npol, a.F);
 
   if (warp == W_PROD) {
     // ---------------- producer ----------------
@@ -322,7 +325,8 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
         const int k = (int)(km / a.n_mt);
         const int nvalid = (int)min((long long)TN, q.f_hi - q.n0);
         const int8_t* src =
-            a.x + 2 * (q.pol() * a.pol_stride + ((long long)k * a.F_in + a.f_base + q.n0) * a.S);
+            a.x + 2 * ((q.pol() + a.pol0) * a.pol_stride +
+                       ((long long)k * a.F_in + a.f_base + q.n0) * a.S);
         const uint32_t bytes = (uint32_t)nvalid * 2 * a.S;
         mbar_expect_tx(&full8[st], bytes);
         bulk_g2s(s8 + st * t8_bytes, src, bytes, &full8[st]);
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
     for (; q.valid(); q.next()) {
       if (!wait_phase(&tfull[acc], pha, abort_p)) break;
       tc_fence_after();
-      const int pol = q.pol();
+      const int pol = q.pol() + a.pol0;
       const long long km = q.km();
       const int k = (int)(km / a.n_mt), mt = (int)(km % a.n_mt);
       const int b = mt * (TM / 2) + rb;
@@ -611,7 +615,7 @@ cudaError_t init_tc_attributes(const Shape& sh) {
 }
 
 cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_stride,
-                               const Chunk& c, cudaStream_t s) {
+                               const Chunk& c, cudaStream_t s, PolSel ps) {
   const auto& sh = p.shape;
   TcArgs a;
   a.x = static_cast<const int8_t*>(x);
@@ -636,7 +640,9 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_st
   a.n_chunks_total = (int)((sh.F + CHUNK - 1) / CHUNK);
   a.write_beams = c.write_beams ? 1 : 0;
   a.write_power = c.write_power ? 1 : 0;
-  a.n_items = (long long)sh.K * a.n_mt * sh.P * a.n_chunks;
+  a.pol0 = ps.pol0;
+  a.npol = ps.npol ? ps.npol : sh.P;
+  a.n_items = (long long)sh.K * a.n_mt * a.npol * a.n_chunks;
   tc_depths(sh, &a.n_s8, &a.n_sb);
   const long long grid = std::min<long long>(a.n_items, (long long)num_sms());
   k_beamform_tc<<<(unsigned)grid, NT, tc_smem(sh), s>>>(

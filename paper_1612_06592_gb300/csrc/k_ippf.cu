@@ -352,12 +352,14 @@ struct TrigOut {
   unsigned long long* count;
   long long cap;
   int P, Tr;
+  int pol0, npol;          // polarisations of this launch (stream map, sel_stream)
 };
 
 __device__ __noinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmask, float th2,
                                            int p, long long n_row0, const TrigOut& o,
                                            const float* __restrict__ theta, float k_sigma) {
-  const int lane = threadIdx.x & 31, j = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int j = (int)sel_stream(blockIdx.y, o.P, o.pol0, o.npol);
   const int P = o.P, Tr = o.Tr;
   const float sig = theta[j] / k_sigma;
 #pragma unroll
@@ -468,7 +470,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   __shared__ uint32_t tmem_slot;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int j = blockIdx.y;
+  const int j = (int)sel_stream(blockIdx.y, tout.P, tout.pol0, tout.npol);
   const long long m0 = (long long)blockIdx.x * frames_per_cta;
   const long long m1 = min((long long)(m0 + frames_per_cta), (long long)(F));
   const int nout = (int)(m1 - m0);
@@ -578,9 +580,10 @@ __global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, i
                                                const long long* __restrict__ blk,
                                                double* __restrict__ sigma2,
                                                float* __restrict__ theta,
-                                               float* __restrict__ theta2) {
+                                               float* __restrict__ theta2, int P, int pol0,
+                                               int npol) {
   __shared__ double red[256];
-  const int j = blockIdx.x;
+  const long long j = sel_stream(blockIdx.x, P, pol0, npol);
   const float* pj = part + (long long)j * n_per_stream;
   double acc = 0.0;
   for (int i = threadIdx.x; i < n_per_stream; i += 256) acc += (double)pj[i];
@@ -604,13 +607,15 @@ __global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, i
 
 // Carry the last 16 frames of every (stream, bin) row into the row prefix and
 // advance the device block counter.
-__global__ void k_history_shift(float2* __restrict__ beams, long long rows, long long F,
-                                long long row, long long* __restrict__ blk, int advance) {
+__global__ void k_history_shift(float2* __restrict__ beams, long long rows, int K, long long F,
+                                long long row, long long* __restrict__ blk, int advance, int P,
+                                int pol0, int npol) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i == 0 && advance) *blk += 1;
   if (i >= rows * kPrefix) return;
-  const long long r = i / kPrefix;
+  const long long rr = i / kPrefix;      // launch row: stream jj, bin k
   const int f = (int)(i % kPrefix);
+  const long long r = sel_stream(rr / K, P, pol0, npol) * K + rr % K;
   beams[r * row + f] = beams[r * row + F + f];
 }
 
@@ -635,11 +640,13 @@ cudaError_t init_ippf_attributes() {
                               (int)ippf_smem_bytes());
 }
 
-cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s) {
+cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel ps) {
   const auto& sh = p.shape;
   const int fpc = p.frames_per_cta;
-  const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)sh.J());
-  const TrigOut tout{p.buf.trig, p.buf.trig_count, (long long)p.cfg.trigger_cap, sh.P, sh.Tr};
+  const int npol = ps.npol ? ps.npol : sh.P;
+  const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)(sh.J() / sh.P * npol));
+  const TrigOut tout{p.buf.trig, p.buf.trig_count, (long long)p.cfg.trigger_cap, sh.P, sh.Tr,
+                     ps.pol0, npol};
   k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(p.buf.beams, sh.K, p.cfg.first_bin, c.nf, p.row(), fpc,
                                              p.buf.g, p.buf.tw1024, p.buf.theta, p.buf.theta2,
                                              (float)p.cfg.k_sigma, p.buf.blk, sh.F, c.f_base,
@@ -647,20 +654,25 @@ cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s) {
+cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s, PolSel ps) {
   const auto& sh = p.shape;
-  k_sigma<<<sh.J(), 256, 0, s>>>(p.buf.power_part, sh.K * p.n_ftiles_bf, p.buf.filter_sums, sh.F,
-                                 p.cfg.sigma_alpha, p.cfg.k_sigma, p.buf.blk, p.buf.sigma2,
-                                 p.buf.theta, p.buf.theta2);
+  const int npol = ps.npol ? ps.npol : sh.P;
+  k_sigma<<<sh.J() / sh.P * npol, 256, 0, s>>>(p.buf.power_part, sh.K * p.n_ftiles_bf,
+                                               p.buf.filter_sums, sh.F, p.cfg.sigma_alpha,
+                                               p.cfg.k_sigma, p.buf.blk, p.buf.sigma2, p.buf.theta,
+                                               p.buf.theta2, sh.P, ps.pol0, npol);
   return cudaGetLastError();
 }
 
-cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s) {
+cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel ps) {
   const auto& sh = p.shape;
-  const long long rows = (long long)sh.J() * sh.K;
+  const int npol = ps.npol ? ps.npol : sh.P;
+  const long long rows = (long long)sh.J() / sh.P * npol * sh.K;
   const long long n = rows * kPrefix;
-  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, rows, c.nf, p.row(),
-                                                              p.buf.blk, c.last ? 1 : 0);
+  const bool advance = c.last && ps.pol0 + npol == sh.P;
+  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, rows, sh.K, c.nf,
+                                                              p.row(), p.buf.blk, advance ? 1 : 0,
+                                                              sh.P, ps.pol0, npol);
   return cudaGetLastError();
 }
 

@@ -105,13 +105,13 @@ lp_status sync_last(lp_plan* p) {
 }
 
 // Record the start / end event of a stage for the current block (profiling).
-void prof_mark(lp_plan* p, int stage, int end, cudaStream_t s) {
+void prof_mark(lp_plan* p, int stage, int end, cudaStream_t s, int part = 0) {
   if (!p->profiling) return;
   const int slot = p->prof_n % lp_plan::kProfSlots;
-  cudaEvent_t& ev = p->prof_ev[slot][stage][end];
+  cudaEvent_t& ev = p->prof_ev[slot][stage][part][end];
   if (!ev) cudaEventCreate(&ev);
   cudaEventRecord(ev, s);
-  if (end) p->prof_used[slot][stage] = true;
+  if (end) p->prof_used[slot][stage][part] = true;
 }
 
 int stream_of(const lp_plan* p, int beam, int tec, int pol) {
@@ -353,6 +353,64 @@ lp_status lp_plan_autotune(lp_plan* p, const void* x, void* stream, int32_t* bes
 
 namespace {
 
+// Host input, whole block, two polarisations: each polarisation's slab is
+// copied on the plan's copy stream and its streams are beamformed,
+// noise-levelled, synthesised and shifted as soon as it has landed, so the copy
+// of polarisation 1 overlaps the work on polarisation 0 (every stream's noise
+// level needs only its own polarisation).  The copy stream first waits for the
+// caller's stream, so earlier work on the input and on the staging buffer is
+// done.
+lp_status process_host_pipelined(lp_plan* p, const void* x, int64_t pol_stride, cudaStream_t s) {
+  const auto& sh = p->shape;
+  const long long slab = (long long)sh.K * sh.F * sh.S;
+  const size_t bpc = p->cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4;
+  const bool fp16 = p->cfg.precision == LP_PREC_FP16;
+  if (fp16 && ((long long)sh.F * sh.S * bpc) % 16)
+    return fail(p, LP_ERR_ARG, "input and pol stride must be 16-byte aligned");
+  if (!p->copy_stream) {
+    LP_CUDA(p, cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    LP_CUDA(p, cudaEventCreateWithFlags(&p->ev_entry, cudaEventDisableTiming));
+    for (auto& ev : p->ev_pol) LP_CUDA(p, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  char* staging = static_cast<char*>(p->buf.staging);
+  LP_CUDA(p, cudaEventRecord(p->ev_entry, s));
+  LP_CUDA(p, cudaStreamWaitEvent(p->copy_stream, p->ev_entry, 0));
+  for (int pol = 0; pol < 2; ++pol) {
+    prof_mark(p, LP_STAGE_H2D, 0, p->copy_stream, pol);
+    LP_CUDA(p, cudaMemcpyAsync(staging + pol * slab * bpc,
+                               static_cast<const char*>(x) + pol * pol_stride * bpc, slab * bpc,
+                               cudaMemcpyHostToDevice, p->copy_stream));
+    prof_mark(p, LP_STAGE_H2D, 1, p->copy_stream, pol);
+    LP_CUDA(p, cudaEventRecord(p->ev_pol[pol], p->copy_stream));
+  }
+  cudaError_t e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
+  lp::Chunk c;
+  c.nf = sh.F;
+  for (int pol = 0; pol < 2 && e == cudaSuccess; ++pol) {
+    const lp::PolSel ps{pol, 1};
+    e = cudaStreamWaitEvent(s, p->ev_pol[pol], 0);
+    prof_mark(p, LP_STAGE_BEAMFORM, 0, s, pol);
+    if (e == cudaSuccess)
+      e = fp16 ? lp::launch_beamform_tc(*p, staging, slab, c, s, ps)
+               : lp::launch_beamform_f32(*p, staging, slab, s, ps);
+    prof_mark(p, LP_STAGE_BEAMFORM, 1, s, pol);
+    prof_mark(p, LP_STAGE_SIGMA, 0, s, pol);
+    if (e == cudaSuccess) e = lp::launch_sigma(*p, s, ps);
+    prof_mark(p, LP_STAGE_SIGMA, 1, s, pol);
+    prof_mark(p, LP_STAGE_SYNTH, 0, s, pol);
+    if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s, ps);
+    prof_mark(p, LP_STAGE_SYNTH, 1, s, pol);
+    prof_mark(p, LP_STAGE_SHIFT, 0, s, pol);
+    if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s, ps);
+    prof_mark(p, LP_STAGE_SHIFT, 1, s, pol);
+  }
+  LP_CUDA(p, e);
+  if (p->profiling && p->prof_n < lp_plan::kProfSlots) p->prof_n += 1;
+  p->last_stream = s;
+  p->block_index += 1;
+  return LP_OK;
+}
+
 lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, bool tune,
                   double* tune_ms) {
   if (lp_status st = need_bound(p)) return st;
@@ -371,7 +429,11 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, b
   const void* xd = x;
   long long stride = pol_stride;
   const size_t bpc = p->cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4;   // bytes per complex sample
-  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+  const bool host = attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged;
+  const bool graph_mode = p->cfg.use_graph && !p->profiling && !tune;
+  if (host && p->buf.staging && sh.P == 2 && p->fc == sh.F && !tune && !graph_mode)
+    return process_host_pipelined(p, x, pol_stride, s);
+  if (host) {
     if (!p->buf.staging)
       return fail(p, LP_ERR_ARG, "host input needs host_input = 1 in the configuration");
     prof_mark(p, LP_STAGE_H2D, 0, s);
@@ -390,7 +452,7 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, b
       (p->cfg.precision == LP_PREC_FP16 && ((long long)sh.F * sh.S * bpc) % align))
     return fail(p, LP_ERR_ARG, "input and pol stride must be %zu-byte aligned", align);
 
-  const bool graph = p->cfg.use_graph && !p->profiling && !tune;
+  const bool graph = graph_mode;
   if (tune && p->graph_exec) {
     cudaGraphExecDestroy(p->graph_exec);     // the tiling changes
     p->graph_exec = nullptr;
@@ -573,11 +635,14 @@ lp_status lp_profile_read(lp_plan* p, double* total_ms, int64_t* blocks) {
   for (int st = 0; st < LP_NUM_STAGES; ++st) total_ms[st] = 0.0;
   for (int slot = 0; slot < p->prof_n; ++slot) {
     for (int st = 0; st < LP_NUM_STAGES; ++st) {
-      if (!p->prof_used[slot][st]) continue;
-      float ms = 0.f;
-      LP_CUDA(p, cudaEventElapsedTime(&ms, p->prof_ev[slot][st][0], p->prof_ev[slot][st][1]));
-      total_ms[st] += ms;
-      p->prof_used[slot][st] = false;
+      for (int part = 0; part < lp_plan::kProfParts; ++part) {
+        if (!p->prof_used[slot][st][part]) continue;
+        float ms = 0.f;
+        LP_CUDA(p, cudaEventElapsedTime(&ms, p->prof_ev[slot][st][part][0],
+                                        p->prof_ev[slot][st][part][1]));
+        total_ms[st] += ms;
+        p->prof_used[slot][st][part] = false;
+      }
     }
   }
   *blocks = p->prof_n;
@@ -590,8 +655,16 @@ void lp_plan_destroy(lp_plan* p) {
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (auto& slot : p->prof_ev)
     for (auto& st : slot)
-      for (auto& ev : st)
-        if (ev) cudaEventDestroy(ev);
+      for (auto& part : st)
+        for (auto& ev : part)
+          if (ev) cudaEventDestroy(ev);
+  if (p->copy_stream) {
+    cudaStreamSynchronize(p->copy_stream);
+    cudaStreamDestroy(p->copy_stream);
+  }
+  if (p->ev_entry) cudaEventDestroy(p->ev_entry);
+  for (auto& ev : p->ev_pol)
+    if (ev) cudaEventDestroy(ev);
   delete p;
 }
 

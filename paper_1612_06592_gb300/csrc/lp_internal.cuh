@@ -72,6 +72,15 @@ struct Chunk {
   bool write_power = true;   // beamformer writes noise partials
   bool last = true;          // last chunk of the block: the history shift advances the block
 };
+// The polarisations one launch covers: pols [pol0, pol0 + npol) (npol 0: all).
+// Launch stream jj maps to j = (jj / npol) P + pol0 + jj mod npol, the plan's
+// stream order, so npol = P is the identity.
+struct PolSel {
+  int pol0 = 0, npol = 0;
+};
+__host__ __device__ inline long long sel_stream(long long jj, int P, int pol0, int npol) {
+  return (jj / npol) * P + pol0 + jj % npol;
+}
 }  // namespace lp
 
 struct lp_plan {
@@ -93,12 +102,19 @@ struct lp_plan {
   int frames_per_cta = 0;  // synthesis tiling
   double nu_ref = 0;
   std::string err;
-  // stage timing (lp_profile_enable): event pairs per recorded block
+  // stage timing (lp_profile_enable): event pairs per recorded block, one per
+  // part (the polarisations of a host block are processed as separate parts)
   bool profiling = false;
   static constexpr int kProfSlots = 256;
-  cudaEvent_t prof_ev[kProfSlots][LP_NUM_STAGES][2] = {};
-  bool prof_used[kProfSlots][LP_NUM_STAGES] = {};
+  static constexpr int kProfParts = 2;
+  cudaEvent_t prof_ev[kProfSlots][LP_NUM_STAGES][kProfParts][2] = {};
+  bool prof_used[kProfSlots][LP_NUM_STAGES][kProfParts] = {};
   int prof_n = 0;
+  // host input: copies of the next polarisation overlap the work on the
+  // previous one (a copy stream of the plan, one event per polarisation)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_entry = nullptr;
+  cudaEvent_t ev_pol[2] = {};
   // graph mode (cfg.use_graph): the per-block launch sequence captured once
   cudaGraphExec_t graph_exec = nullptr;
   const void* graph_x = nullptr;
@@ -119,12 +135,14 @@ cudaError_t launch_dedisp(const lp_plan& p, cudaStream_t s);
 // x: station block, pol slab p at x + p * pol_stride complex samples, each
 // slab [K][F][S] complex samples contiguous
 cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_stride,
-                                cudaStream_t s);
+                                cudaStream_t s, PolSel ps = {});
 cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_stride,
-                               const Chunk& c, cudaStream_t s);
-cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s);
-cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s);
-cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s);
+                               const Chunk& c, cudaStream_t s, PolSel ps = {});
+cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s, PolSel ps = {});
+cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel ps = {});
+// advances the device block counter when c.last and ps covers the last pol
+cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s,
+                                 PolSel ps = {});
 
 // Opt-in shared-memory limits of the kernels (per device; call with it current).
 cudaError_t init_kernel_attributes(const Shape& sh);

@@ -138,24 +138,36 @@ def test_tiny_workload_with_pulse(cuda_lib):
     assert len(ns) > 0 and np.min(np.abs(ns - t_exp)) < 200
 
 
-def test_host_input_equals_device_input(cuda_lib):
-    S, P, K, B, Tr, F, fb = 4, 2, 12, 2, 1, 96, 250
-    blocks, enu, dirs, tec = random_case(8, S, P, K, B, Tr, F, fb, "int8", 2)
+@pytest.mark.parametrize("precision,pinned", [("fp32", False), ("fp16", True), ("fp32", True)])
+def test_host_input_equals_device_input(cuda_lib, precision, pinned):
+    """A host block (copied one polarisation at a time, the copy of pol 1
+    overlapping the work on pol 0) gives exactly the device block's results:
+    every stream's time series, the noise levels and the triggers of every
+    block, over several blocks (history and running sigma carried)."""
+    S, P, K, B, Tr, F, fb = 8, 2, 12, 2, 2, 96, 250
+    blocks, enu, dirs, tec = random_case(8, S, P, K, B, Tr, F, fb, "int8", 3)
     import torch
     res = []
     for host in (False, True):
-        plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", store_timeseries=True,
-                         host_input=True, k_sigma=3.0)
+        plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision=precision,
+                         store_timeseries=True, host_input=True, k_sigma=3.0)
         plan.lp_set_weights(enu, dirs)
         plan.lp_set_tec(tec)
-        ys = []
+        out = []
         for xb in blocks:
-            x = xb if host else torch.from_numpy(xb).cuda()
+            if host:
+                x = torch.from_numpy(xb).pin_memory() if pinned else xb
+            else:
+                x = torch.from_numpy(xb).cuda()
             plan.lp_process_block(x)
-            ys.append(plan.lp_get_timeseries(1, 0, 1))
-        res.append((np.stack(ys), plan.lp_get_triggers()[0]))
-    np.testing.assert_array_equal(res[0][0], res[1][0])
-    np.testing.assert_array_equal(res[0][1], res[1][1])
+            ys = [plan.lp_get_timeseries(b, t, pol)
+                  for b in range(B) for t in range(Tr) for pol in range(P)]
+            out.append((np.stack(ys), plan.lp_get_sigma().copy(), plan.lp_get_triggers()[0]))
+        res.append(out)
+    for (ya, sa, ta), (yb, sb, tb) in zip(*res):
+        np.testing.assert_array_equal(ya, yb)
+        np.testing.assert_array_equal(sa, sb)
+        np.testing.assert_array_equal(ta, tb)
 
 
 def test_deterministic_reruns(cuda_lib):
