@@ -18,13 +18,16 @@
 //               (256 frames x 2S contiguous bytes) into a ring of stages, and of
 //               the A images (hi and lo weights, pre-arranged by k_weights_tc)
 //               whenever (k, beam tile) changes;
-//   warps 2-5   converters: int8 -> FP16 in the canonical K-major no-swizzle
-//               layout (8-row x 16-byte core matrices), a ring of B stages;
+//   warps 2-9   converters: int8 -> FP16 in the canonical K-major no-swizzle
+//               layout (8-row x 16-byte core matrices), a ring of B stages.
+//               A byte b becomes the FP16 number 1024 + (b ^ 0x80) by placing
+//               it under the exponent pattern of 1024 (byte permute), and one
+//               packed subtraction of 1152 leaves b exactly;
 //   warp 1      MMA: one thread issues 2 * 2S/16 tcgen05.mma (M = 128, N = 256,
 //               K = 16) into one of two 256-column TMEM accumulators and
 //               commits to mbarriers that free the B stage and publish the
 //               accumulator;
-//   warps 6-13  epilogue: two warps per 32-lane TMEM quarter (one per column
+//   warps 10-17 epilogue: two warps per 32-lane TMEM quarter (one per column
 //               half) read the accumulator with tcgen05.ld, pair Re/Im lanes
 //               by shuffle, multiply by D[k,t], sum |beam|^2 per chunk, and
 //               stage 16-beam x 16-frame boxes (128-byte swizzle) that a TMA
@@ -42,13 +45,13 @@
 namespace lp {
 namespace {
 
-constexpr int NT = 448;          // 14 warps: producer, MMA, 4 converters, 8 epilogue
+constexpr int NT = 576;          // 18 warps: producer, MMA, 8 converters, 8 epilogue
 constexpr int TM = 128;          // M rows per tile: 64 beams x (re, im)
 constexpr int TN = 256;          // frames per MMA tile
 constexpr int CHUNK = 2048;      // frames per work item (one noise partial sum)
 constexpr int TMEM_COLS = 512;   // two 256-column accumulators
 constexpr long long WAIT_LIMIT = 1LL << 24;   // bounded mbarrier polls
-constexpr int W_PROD = 0, W_MMA = 1, W_CONV0 = 2, N_CONV = 4, W_EPI0 = 6, N_EPI = 8;
+constexpr int W_PROD = 0, W_MMA = 1, W_CONV0 = 2, N_CONV = 8, W_EPI0 = 10, N_EPI = 8;
 constexpr int MAX_S8 = 3, MAX_SB = 2;
 constexpr int STG_BOX = 16 * 128;             // staged output box: 16 beams x 16 frames x 8 B
 constexpr int STG_BYTES = N_EPI * 2 * STG_BOX; // two boxes per epilogue warp
@@ -134,6 +137,22 @@ __host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
 // Byte offset of element (row, kd) in a K-major no-swizzle tile of KP columns.
 __host__ __device__ inline uint32_t core_off(int row, int kd, int KP) {
   return (uint32_t)((row >> 3) * (KP / 8) * 128 + (kd >> 3) * 128 + (row & 7) * 16 + (kd & 7) * 2);
+}
+
+// Eight int8 samples -> eight FP16 (exact): byte b -> bits 0x6400 | (b ^ 0x80)
+// = 1024 + b + 128, then minus 1152 (0x6480).
+__device__ __forceinline__ uint4 i8x8_to_f16x8(uint2 q) {
+  const uint32_t u0 = q.x ^ 0x80808080u, u1 = q.y ^ 0x80808080u;
+  const uint32_t r[4] = {__byte_perm(u0, 0x64646464u, 0x4140), __byte_perm(u0, 0x64646464u, 0x4342),
+                         __byte_perm(u1, 0x64646464u, 0x4140), __byte_perm(u1, 0x64646464u, 0x4342)};
+  const __half2 bias = __half2half2(__ushort_as_half((unsigned short)0x6480));
+  uint32_t o[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&r[i]), bias);
+    o[i] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 // A-operand images: [k][beam tile][hi/lo][TM x KP] FP16 in the layout above.
@@ -394,10 +413,10 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
       }
     }
   } else if (warp < W_EPI0) {
-    // ---------------- converters (128 threads) ----------------
-    const int ct = tid - W_CONV0 * 32;          // 0..127
-    const int cw = ct >> 5;                     // converter warp 0..3
+    // ---------------- converters (N_CONV warps) ----------------
+    const int cw = warp - W_CONV0;              // converter warp 0..N_CONV-1
     const int n_sub = lane & 7, c_sub = lane >> 3;
+    const int n_cg = (nkg + 3) / 4;             // groups of four 8-sample K chunks
     int st = 0, sb = 0;
     uint32_t ph = 0, phb = 0;
     for (; q.valid(); q.next()) {
@@ -405,25 +424,20 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
       if (!wait_phase(&emptyB[sb], phb ^ 1u, abort_p)) break;
       const unsigned char* src = s8 + st * t8_bytes;
       unsigned char* dst = sbuf + sb * b_bytes;
-      // a warp converts 8 frames x 4 chunks of 8 samples per step
-      const int nsteps = (TN / 8) * ((nkg + 3) / 4);
-      for (int u = cw; u < nsteps; u += N_CONV) {
-        const int ng = u % (TN / 8), cg = u / (TN / 8);
-        const int n = ng * 8 + n_sub, c = cg * 4 + c_sub;
+      // one step converts frames 8 ng + n_sub, K chunk 4 cg + c_sub (8 samples);
+      // warp cw takes the frame groups ng = cw (mod N_CONV)
+      for (int cg = 0; cg < n_cg; ++cg) {
+        const int c = cg * 4 + c_sub;
         if (c >= nkg) continue;
-        uint4 h8 = make_uint4(0, 0, 0, 0);
-        if (8 * c < 2 * a.S) {
-          const uint2 qv = *reinterpret_cast<const uint2*>(src + n * (2 * a.S) + 8 * c);
-          const char4 lo4 = *reinterpret_cast<const char4*>(&qv.x);
-          const char4 hi4 = *reinterpret_cast<const char4*>(&qv.y);
-          __half2 p0 = __floats2half2_rn((float)lo4.x, (float)lo4.y);
-          __half2 p1 = __floats2half2_rn((float)lo4.z, (float)lo4.w);
-          __half2 p2 = __floats2half2_rn((float)hi4.x, (float)hi4.y);
-          __half2 p3 = __floats2half2_rn((float)hi4.z, (float)hi4.w);
-          h8 = make_uint4(*reinterpret_cast<uint32_t*>(&p0), *reinterpret_cast<uint32_t*>(&p1),
-                          *reinterpret_cast<uint32_t*>(&p2), *reinterpret_cast<uint32_t*>(&p3));
+        const bool in = 8 * c < 2 * a.S;        // K padding converts to zeros
+        const unsigned char* sp = src + n_sub * (2 * a.S) + 8 * c;
+        unsigned char* dp = dst + core_off(n_sub, 8 * c, KP);
+#pragma unroll 4
+        for (int ng = cw; ng < TN / 8; ng += N_CONV) {
+          uint4 h8 = make_uint4(0, 0, 0, 0);
+          if (in) h8 = i8x8_to_f16x8(*reinterpret_cast<const uint2*>(sp + ng * 16 * a.S));
+          *reinterpret_cast<uint4*>(dp + ng * (KP / 8) * 128) = h8;
         }
-        *reinterpret_cast<uint4*>(dst + core_off(n, 8 * c, KP)) = h8;
       }
       fence_proxy_async();
       mbar_arrive(&fullB[sb]);
