@@ -53,8 +53,8 @@ constexpr int BAR_READY = 6;       // 6, 7: ring buffer s written
 constexpr int BAR_FREE = 8;        // 8, 9: ring buffer s read
 // tensor-memory columns of a FIR thread (256 per thread: two FIR warps per
 // lane quarter)
-constexpr int TC_TAPS = 0;         // 2 x 32: (g, g) of phases t and t + 256
-constexpr int TC_HIST = 64;        // 4 x 32: 16 frames (re, im) of each phase
+constexpr int TC_TAPS = 0;         // 4 x 32: (g, g) of each of the four phases
+constexpr int TC_HIST = 128;       // 4 x 32: 16 frames (re, im) of each phase
 
 __host__ __device__ constexpr int br4(int i) {
   return ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3);
@@ -331,18 +331,16 @@ __device__ __forceinline__ void pair_dft(float2* slot, const float4* st,
   }
   bar_sync(bar_id, 64);                  // both warps have read the transpose
   dft16_stages<8>(v);
-  // last butterfly stage in scalar form, written straight out as (re, im) of
-  // each frame: z[lane + 32 p2], p2 = 2 br4(i) + H
-  float2* za = slot + lane + 32 * H;
-  float2* zb = za + kM;
+  // The last butterfly stage is left to the FIR warps: outputs p2 and p2 + 16
+  // (p2 = 2 br4(2m) + H, phases P = lane + 32 p2 and P + 512) are a + b and
+  // a - b of a = v[2m], b = v[2m + 1], stored as granules P and P + 512.
+  float4* zg = tb + lane + 32 * H;
 #pragma unroll
-  for (int i = 0; i < 16; i += 2) {
-    const CP a = v[i], b = v[i + 1];
-    const int o0 = 64 * br4(i), o1 = 64 * br4(i + 1);
-    za[o0] = make_float2(a.re.x + b.re.x, a.im.x + b.im.x);
-    zb[o0] = make_float2(a.re.y + b.re.y, a.im.y + b.im.y);
-    za[o1] = make_float2(a.re.x - b.re.x, a.im.x - b.im.x);
-    zb[o1] = make_float2(a.re.y - b.re.y, a.im.y - b.im.y);
+  for (int m = 0; m < 8; ++m) {
+    const int o = 64 * br4(2 * m);
+    const CP a = v[2 * m], b = v[2 * m + 1];
+    zg[o] = make_float4(a.re.x, a.re.y, a.im.x, a.im.y);
+    zg[o + 512] = make_float4(b.re.x, b.re.y, b.im.x, b.im.y);
   }
 }
 
@@ -399,7 +397,7 @@ struct FirCtx {
 // FIR of one phase over one batch.  hist: the phase's 16 history slots (frame
 // r at slot r mod 16, (re, im) in consecutive columns); zn: the 8 new frames.
 // ODD selects where the 15 history frames r0-15 .. r0-1 sit (r0 mod 16 = 8 ODD).
-template <int ODD, bool TAP_REV>
+template <int ODD>
 __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float (&hist)[32],
                                           const float2 (&zn)[FB], int p, const FirCtx& c,
                                           const TrigOut& o, const float* __restrict__ theta,
@@ -419,7 +417,7 @@ __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float
     float2 u = make_float2(0.f, 0.f);
 #pragma unroll
     for (int t = 0; t < kTaps; ++t)   // both components per instruction, tap (g, g)
-      u = __ffma2_rn(TAP_REV ? gq[kTaps - 1 - t] : gq[t], w[f + kHist - t], u);
+      u = __ffma2_rn(gq[t], w[f + kHist - t], u);
     if (c.yrow && ((c.ymask >> f) & 1u)) c.yrow[f * kM + p] = u.x;
     e2v[f] = fmaf(u.x, u.x, u.y * u.y);
     emax = fmaxf(emax, e2v[f]);         // frames outside the run are filtered by vmask
@@ -435,24 +433,20 @@ __device__ __forceinline__ unsigned frame_bits(int lo, int hi) {
   return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
 }
 
-// One phase of the FIR role for batch r0: new frames from the ring, history
-// from tensor memory, new frames into the history slots r0 mod 16 ...
-template <bool TAP_REV>
+// One phase of the FIR role for batch r0: its 8 new frames zn, history from
+// tensor memory; the new frames then replace the history slots r0 mod 16 ...
 __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t thist,
-                                        const float2* zr, int p, int r0, bool outputs,
+                                        const float2 (&zn)[FB], int p, int r0, bool outputs,
                                         const FirCtx& c, const TrigOut& o,
                                         const float* __restrict__ theta, float k_sigma) {
-  float2 zn[FB];
-#pragma unroll
-  for (int f = 0; f < FB; ++f) zn[f] = zr[f * kM + p];
   if (outputs) {
     float hist[32];
     tmem_ld32(thist, hist);
     tmem_wait_ld();
     if (r0 & 8)
-      fir_phase<1, TAP_REV>(gq, hist, zn, p, c, o, theta, k_sigma);
+      fir_phase<1>(gq, hist, zn, p, c, o, theta, k_sigma);
     else
-      fir_phase<0, TAP_REV>(gq, hist, zn, p, c, o, theta, k_sigma);
+      fir_phase<0>(gq, hist, zn, p, c, o, theta, k_sigma);
   }
 #pragma unroll
   for (int f = 0; f < FB; ++f) tmem_st2(thist + 2 * ((r0 & 8) + f), zn[f]);
@@ -511,20 +505,22 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     }
   } else {
     // ===================== FIR role =====================
+    // thread ft owns the butterfly partners (ft, ft + 512) and (511 - ft, 1023 - ft)
     const int ft = tid - NDFT;
     const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 256u * ((warp - 8) >> 2);
-    // taps (g, g) of phases ft and ft + 256 into tensor memory
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
+    // taps (g, g) of the four phases into tensor memory
+#pragma unroll 1
+    for (int ph = 0; ph < 4; ++ph) {
+      const int p = (ph & 2 ? kM / 2 - 1 - ft : ft) + (ph & 1 ? kM / 2 : 0);
       float tq[32];
 #pragma unroll
       for (int t = 0; t < kTaps; ++t) {
-        const float gt = g[t * kM + ft + 256 * m];
+        const float gt = g[t * kM + p];
         tq[2 * t] = gt;
         tq[2 * t + 1] = gt;
       }
-      tmem_st16(tbase + TC_TAPS + 32 * m, reinterpret_cast<const float(&)[16]>(tq[0]));
-      tmem_st16(tbase + TC_TAPS + 32 * m + 16, reinterpret_cast<const float(&)[16]>(tq[16]));
+      tmem_st16(tbase + TC_TAPS + 32 * ph, reinterpret_cast<const float(&)[16]>(tq[0]));
+      tmem_st16(tbase + TC_TAPS + 32 * ph + 16, reinterpret_cast<const float(&)[16]>(tq[16]));
     }
     tmem_wait_st();
     FirCtx c;
@@ -542,7 +538,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     for (int bi = 0; bi < nbatch; ++bi) {
       const int s = bi & 1, r0 = bi * FB;
       bar_sync(BAR_READY + s, NT);       // ring buffer s holds batch bi
-      const float2* zr = ring + s * FB * kM;
+      const float4* zr = reinterpret_cast<const float4*>(ring + s * FB * kM);
       const bool outputs = r0 >= kPrefix;
       c.ymask = frame_bits(kPrefix - r0, nfr - r0);
       c.vmask = c.ymask & frame_bits(r_trig - r0, FB);
@@ -550,17 +546,31 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
       c.yrow = yj ? yj + m_row0 * kM : nullptr;
       c.n_row0 = n_first + m_row0 * kM;
 #pragma unroll 1
-      for (int m = 0; m < 2; ++m) {
-        float tq[32];
-        tmem_ld32(tbase + TC_TAPS + 32 * m, tq);
-        tmem_wait_ld();
-        float2 gq[kTaps];
+      for (int bp = 0; bp < 2; ++bp) {
+        const int pb = bp ? kM / 2 - 1 - ft : ft;
+        // last butterfly: z[pb] = a + b, z[pb + 512] = a - b, for both frames of
+        // each pair (granule = re_a, re_b, im_a, im_b)
+        float2 za[FB], zb[FB];
 #pragma unroll
-        for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
-        const int p = ft + 256 * m;     // and its mirror M - 1 - p
-        fir_one<false>(gq, tbase + TC_HIST + 64 * m, zr, p, r0, outputs, c, tout, theta, k_sigma);
-        fir_one<true>(gq, tbase + TC_HIST + 64 * m + 32, zr, kM - 1 - p, r0, outputs, c, tout,
-                      theta, k_sigma);
+        for (int q = 0; q < FB / 2; ++q) {
+          const float4 a = zr[q * kM + pb], b = zr[q * kM + pb + kM / 2];
+          za[2 * q] = make_float2(a.x + b.x, a.z + b.z);
+          za[2 * q + 1] = make_float2(a.y + b.y, a.w + b.w);
+          zb[2 * q] = make_float2(a.x - b.x, a.z - b.z);
+          zb[2 * q + 1] = make_float2(a.y - b.y, a.w - b.w);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int ph = 2 * bp + h;
+          float tq[32];
+          tmem_ld32(tbase + TC_TAPS + 32 * ph, tq);
+          tmem_wait_ld();
+          float2 gq[kTaps];
+#pragma unroll
+          for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
+          fir_one(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0, outputs, c,
+                  tout, theta, k_sigma);
+        }
       }
       tmem_wait_st();                    // history slots written before the next batch reads them
       if (bi + 2 < nbatch) bar_arrive(BAR_FREE + s, NT);
