@@ -5,9 +5,8 @@
 // [m0, m1) and walks frames m0-16 .. m1-1 in batches of 8 (four frame pairs).
 // Its 16 warps have two roles that run concurrently on a double-buffered ring:
 //
-//  * DFT warps 0..7 (two per frame pair) copy the batch's beam bins into a
-//    zero-padded 512-bin stage with 16-byte cp.async (one batch ahead) and take
-//    the 1024-point inverse DFT
+//  * DFT warps 0..7 (two per frame pair) take, from a zero-padded 512-bin
+//    stage of the batch's beam bins, the 1024-point inverse DFT
 //        z[p] = sum_k c[k] exp(+2 pi i k p / 1024),  c nonzero only in the
 //    selected bins (< 512), as 32 x 32 with k = 32 k1 + k2, p = p1 + 32 p2.
 //    Every value is a pair of frames, so each packed FP32 instruction (FADD2 /
@@ -30,7 +29,9 @@
 //    and compact the (rare) samples above threshold into the trigger list.
 //
 // The roles hand batches over with named barriers: "ready[s]" (DFT warps
-// arrive, FIR warps wait) and "free[s]" (the reverse) for ring buffer s.
+// arrive, FIR warps wait) for ring buffer s, and "free[s]" (the reverse): ring
+// buffer s has been read, and stage buffer s holds the bins of the batch after
+// next, which the FIR warps copy (16-byte cp.async) while they filter.
 // The first 16 frames of a run only fill the FIR history (16/frames_per_cta of
 // extra inverse DFTs).  FP32 throughout.
 #include "lp_internal.cuh"
@@ -48,7 +49,6 @@ constexpr int SPAIR = 514;         // stage granules per frame pair: 512 bins + 
 constexpr int TMEM_COLS = 512;
 // named barriers (0 is __syncthreads)
 constexpr int BAR_PAIR = 1;        // 1..4: the two warps of a frame pair
-constexpr int BAR_DFT = 5;         // the eight DFT warps
 constexpr int BAR_READY = 6;       // 6, 7: ring buffer s written
 constexpr int BAR_FREE = 8;        // 8, 9: ring buffer s read
 // tensor-memory columns of a FIR thread (256 per thread: two FIR warps per
@@ -232,7 +232,7 @@ __device__ __forceinline__ void tmem_wait_st() {
 
 // Staging of the beam bins of CTA frames r0 .. r0+7 into
 // stage[pair][first_bin + k] (16-byte copies of a frame pair: re_a, im_a,
-// re_b, im_b).  DFT thread t copies pair t & 3 of bins k = t/4 + 64 i, so four
+// re_b, im_b).  FIR thread t copies pair t & 3 of bins k = t/4 + 64 i, so four
 // neighbouring threads read the 64 contiguous bytes of one bin row and the
 // shared-memory granules of a quarter warp fall in distinct banks.
 struct Stager {
@@ -478,23 +478,25 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  // the FIR threads stage the bins (thread tid - NDFT); batches 0 and 1 now
+  const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
+  const Stager stg = make_stager(brow, K, first_bin, row, tid - NDFT);
+  // a pair is copied when both its frames are in the run and inside the row
+  const int live_lim = (int)min((long long)nfr, row - m0);
+  if (warp >= NDFT / 32) {
+    stage_batch(stg, stage, stg.f + 1 < live_lim, 0);
+    stage_batch(stg, stage + NPAIR * SPAIR, FB + stg.f + 1 < live_lim, FB);
+    cp_async_wait_all();
+  }
+  __syncthreads();
 
   if (warp < NDFT / 32) {
     // ===================== DFT role =====================
-    const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
-    const Stager stg = make_stager(brow, K, first_bin, row, tid);
-    // a pair is copied when both its frames are in the run and inside the row
-    const int live_lim = (int)min((long long)nfr, row - m0);
-    stage_batch(stg, stage, stg.f + 1 < live_lim, 0);
     const int pr = warp >> 1, h = warp & 1;     // frame pair of the batch, output parity
     for (int bi = 0; bi < nbatch; ++bi) {
       const int s = bi & 1;
-      cp_async_wait_all();
-      bar_sync(BAR_DFT, NDFT);   // batch bi staged; stage buffer s^1 no longer read
-      if (bi + 1 < nbatch)
-        stage_batch(stg, stage + (s ^ 1) * NPAIR * SPAIR, (bi + 1) * FB + stg.f + 1 < live_lim,
-                    (bi + 1) * FB);
-      if (bi >= 2) bar_sync(BAR_FREE + s, NT);   // the FIR role is done with ring buffer s
+      // ring buffer s read by the FIR role, stage buffer s loaded with batch bi
+      if (bi >= 2) bar_sync(BAR_FREE + s, NT);
       float2* slot = ring + (s * FB + 2 * pr) * kM;
       const float4* st = stage + s * NPAIR * SPAIR + pr * SPAIR + lane;
       if (h)
@@ -538,6 +540,10 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     for (int bi = 0; bi < nbatch; ++bi) {
       const int s = bi & 1, r0 = bi * FB;
       bar_sync(BAR_READY + s, NT);       // ring buffer s holds batch bi
+      // stage buffer s is free again: bins of batch bi + 2
+      if (bi + 2 < nbatch)
+        stage_batch(stg, stage + s * NPAIR * SPAIR, (bi + 2) * FB + stg.f + 1 < live_lim,
+                    (bi + 2) * FB);
       const float4* zr = reinterpret_cast<const float4*>(ring + s * FB * kM);
       const bool outputs = r0 >= kPrefix;
       c.ymask = frame_bits(kPrefix - r0, nfr - r0);
@@ -573,7 +579,10 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
         }
       }
       tmem_wait_st();                    // history slots written before the next batch reads them
-      if (bi + 2 < nbatch) bar_arrive(BAR_FREE + s, NT);
+      if (bi + 2 < nbatch) {
+        cp_async_wait_all();             // this thread's copies of batch bi + 2 landed
+        bar_arrive(BAR_FREE + s, NT);
+      }
     }
   }
   tc_fence_before();
