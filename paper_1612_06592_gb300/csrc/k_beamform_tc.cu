@@ -473,48 +473,57 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
         tmem_ld16(lane_addr + c0, r[0]);
         tmem_ld16(lane_addr + c0 + 16, r[1]);
         tmem_ld_wait();
+        // both 16-frame boxes of the 32-column step are staged, then one proxy
+        // fence and one warp sync cover both TMA stores (the fences, not the
+        // stores, were the epilogue's cost)
+        float2 bvh[2][8];
+        long long fbh[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float recv[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)   // even lane sends Re 8-15, odd lane sends Im 0-7
+          for (int i = 0; i < 8; ++i)
             recv[i] = __shfl_xor_sync(0xffffffffu,
                                       __uint_as_float(odd ? r[h][i] : r[h][i + 8]), 1);
-          const long long fb = n0 + col_half * (TN / 2) + c0 + 16 * h;   // box's first frame
-          const long long f0 = fb + (odd ? 8 : 0);
-          float2 bv[8];
+          const long long fb = n0 + col_half * (TN / 2) + c0 + 16 * h;
+          fbh[h] = fb;
+          // frames of this lane's half inside the launch: all 8 except in the
+          // last tile of an item (warp-uniform test first); partials of beams
+          // beyond B are never stored
+          const int nin = fb + 16 <= f_hi ? 8 : (int)max(0LL, min(8LL, f_hi - fb - (odd ? 8 : 0)));
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            bv[i] = odd ? make_float2(recv[i], __uint_as_float(r[h][i + 8]))
-                        : make_float2(__uint_as_float(r[h][i]), recv[i]);
-            if (beam_ok && f0 + i < f_hi) pw = fmaf(bv[i].x, bv[i].x, fmaf(bv[i].y, bv[i].y, pw));
+          for (int i = 0; i < 8; ++i) {   // even lane: (Re, Im) of frames 0-7, odd: 8-15
+            bvh[h][i] = odd ? make_float2(recv[i], __uint_as_float(r[h][i + 8]))
+                            : make_float2(__uint_as_float(r[h][i]), recv[i]);
+            if (i < nin) pw = fmaf(bvh[h][i].x, bvh[h][i].x, fmaf(bvh[h][i].y, bvh[h][i].y, pw));
           }
-          if (fb >= f_hi || !a.write_beams) continue;   // warp-uniform
-          unsigned char* box = stg + (ew * 2 + h) * STG_BOX;
+        }
+        if (fbh[0] < f_hi && a.write_beams) {
           for (int t = 0; t < a.Tr; ++t) {
             const float2 dv = t == 0 ? d0 : a.dd[k * a.Tr + t];
-            // the previous store from this box must have read it (with one trial the
-            // other box's store may still be running)
-            if (lane == 0) {
-              if (a.Tr > 1)
-                bulk_wait_read<0>();
-              else
-                bulk_wait_read<1>();
-            }
+            if (lane == 0) bulk_wait_read<0>();   // earlier stores have read both boxes
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {           // 16-byte chunk c of row rloc, 128B swizzle
-              const float2 u = bv[2 * i], w = bv[2 * i + 1];
-              const int c = (odd ? 4 : 0) + i;
-              *reinterpret_cast<float4*>(box + rloc * 128 + ((c ^ (rloc & 7)) << 4)) =
-                  make_float4(dv.x * u.x - dv.y * u.y, dv.x * u.y + dv.y * u.x,
-                              dv.x * w.x - dv.y * w.y, dv.x * w.y + dv.y * w.x);
+            for (int h = 0; h < 2; ++h) {       // 16-byte chunk c of row rloc, 128B swizzle
+              unsigned char* box = stg + (ew * 2 + h) * STG_BOX;
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const float2 u = bvh[h][2 * i], w = bvh[h][2 * i + 1];
+                const int c = (odd ? 4 : 0) + i;
+                *reinterpret_cast<float4*>(box + rloc * 128 + ((c ^ (rloc & 7)) << 4)) =
+                    make_float4(dv.x * u.x - dv.y * u.y, dv.x * u.y + dv.y * u.x,
+                                dv.x * w.x - dv.y * w.y, dv.x * w.y + dv.y * w.x);
+              }
             }
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0)
-              tma_store_box(&out_map, box, (int)(kPrefix + fb), k, pol, t,
-                            mt * (TM / 2) + quarter * 16);
+            if (lane == 0) {
+              tma_store_box(&out_map, stg + (ew * 2) * STG_BOX, (int)(kPrefix + fbh[0]), k, pol,
+                            t, mt * (TM / 2) + quarter * 16);
+              if (fbh[1] < f_hi)
+                tma_store_box(&out_map, stg + (ew * 2 + 1) * STG_BOX, (int)(kPrefix + fbh[1]), k,
+                              pol, t, mt * (TM / 2) + quarter * 16);
+            }
           }
         }
       }
