@@ -18,12 +18,14 @@
 //    stages come the twiddle exp(+2 pi i k2 p1 / 1024) and a transpose through
 //    the pair's ring slots (16-byte granules, column XOR-swizzled by row mod 8:
 //    free of bank conflicts both ways, addresses affine in the unrolled index).
-//  * FIR warps 8..15: thread t owns the output phases t, 1023 - t, t + 256 and
-//    767 - t.  Mirror phases share one set of 16 taps (g[n] = g[L-1-n] gives
-//    g_t[M-1-p] = g_{15-t}[p]).  The taps, as (g, g) pairs, and the last 16
-//    frames of z of each phase live in the thread's own tensor-memory columns
+//    The DFT warps stop before the last radix-2 stage and leave each butterfly
+//    pair (a, b) of outputs P and P + 512 in the ring as two granules.
+//  * FIR warps 8..15: thread t owns the butterfly partners (t, t + 512) and
+//    (511 - t, 1023 - t): it forms z = a + b and a - b and filters the four
+//    phases.  The taps (as (g, g) pairs, four sets) and the last 16 frames of
+//    z of each phase live in the thread's own tensor-memory columns
 //    (tcgen05.ld / tcgen05.st), so the ring holds only the batch in flight and
-//    the FIR reads each new z once from shared memory.  Per phase it computes
+//    each granule is read once from shared memory.  Per phase it computes
 //        u_m[p] = sum_{t<16} g[t M + p] z_{m-t}[p]     (g holds the 2/M scale),
 //    y = Re u (optionally stored) and |u|^2 against theta^2; the warps vote
 //    and compact the (rare) samples above threshold into the trigger list.
@@ -50,7 +52,7 @@ constexpr int TMEM_COLS = 512;
 // named barriers (0 is __syncthreads)
 constexpr int BAR_PAIR = 1;        // 1..4: the two warps of a frame pair
 constexpr int BAR_READY = 6;       // 6, 7: ring buffer s written
-constexpr int BAR_FREE = 8;        // 8, 9: ring buffer s read
+constexpr int BAR_FREE = 8;        // 8, 9: ring buffer s read, stage buffer s loaded
 // tensor-memory columns of a FIR thread (256 per thread: two FIR warps per
 // lane quarter)
 constexpr int TC_TAPS = 0;         // 4 x 32: (g, g) of each of the four phases

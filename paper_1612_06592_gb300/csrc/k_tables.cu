@@ -41,8 +41,7 @@ __global__ void __launch_bounds__(1024) k_prototype(double beta, double* __restr
   __shared__ double red_h2[1024];
   const double i0b = bessel_i0_series(beta);
   double sh = 0.0, sh2 = 0.0;
-  // the lower half, mirrored: h[L-1-n] = h[n] holds exactly (the synthesis
-  // kernel relies on it to share taps between phases p and M-1-p)
+  // the lower half, mirrored: h[L-1-n] = h[n] holds exactly
   for (int n = threadIdx.x; n < L / 2; n += blockDim.x) {
     const double xs = ((double)n - 0.5 * (L - 1)) / kM;
     const double sinc = (xs == 0.0) ? 1.0 : sinpi(xs) / (M_PI * xs);
