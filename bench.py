@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import subprocess
 import sys
@@ -192,14 +193,24 @@ def cpu_baseline(w, x_dev, frames):
 
 # ------------------------------------------------------------ ncu traffic --
 
+def code_digest(path):
+    """Hash of a CUDA source with comments and whitespace removed, so that a
+    recorded measurement stays attached to the code, not to its comments."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    text = re.sub(r"\s+", "", text)
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
 def recorded_traffic(kernel_file):
-    """DRAM bytes per launch of the synthesis kernel from the committed ncu
-    summary, if it was taken on the current source of that kernel."""
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if it
+    was taken on the current code of that kernel."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     src = os.path.join(ROOT, "paper_1612_06592_gb300", "csrc", kernel_file)
     try:
         rec = json.load(open(path))
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = code_digest(src)
         ent = rec.get(kernel_file)
         if ent and ent.get("source_sha256_16") == digest:
             return ent["bytes_per_full_launch"]
