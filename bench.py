@@ -45,6 +45,16 @@ SMS = 152
 FP32_LANES_PER_SM = 128
 
 
+def fp32_peak_tflops():
+    """FP32 FMA peak from unit counts at the maximum SM clock (from the measured
+    peaks file when it records one)."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    return SMS * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -403,18 +413,18 @@ def run_stress(args):
     plist, contrib = synth.pulse_contributions(w, 0, enu, dirs)
     x = device_block(w, 5000, dev, contrib)     # pulses added before rounding
     chunk = 8192
+    stream = torch.cuda.Stream()                  # graph mode needs a non-default stream
     plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(tec), w.block_len,
                    input_dtype="int8", precision="fp16", first_bin=w.first_bin,
-                   chunk_frames=chunk, trigger_cap=1 << 22)
-    plan.lp_set_weights(enu, dirs)
-    plan.lp_set_tec(tec)
-    plan.lp_profile_enable(True)
-    for _ in range(max(1, args.warmup)):
-        plan.lp_process_block(x)
-        plan.lp_reset_stream()          # every timed block is block 0 of the stream
+                   chunk_frames=chunk, trigger_cap=1 << 22, use_graph=True, stream=stream)
+    plan.lp_set_weights(enu, dirs, stream=stream)
+    plan.lp_set_tec(tec, stream=stream)
+    # synthesis tiling by the autotuner (timed on the block's first chunk)
+    tuned_fpc, tune_ms = plan.lp_plan_autotune(x, stream=stream)
+    for _ in range(max(1, args.warmup)):          # the first block captures the graph
+        plan.lp_reset_stream(stream=stream)       # every timed block is block 0 of the stream
+        plan.lp_process_block(x, stream=stream)
     torch.cuda.synchronize()
-    plan.lp_profile_read()
-    stream = torch.cuda.current_stream()
     clocks = ClockSampler(0)
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -422,9 +432,9 @@ def run_stress(args):
     steps = max(1, min(args.steps, 3))
     ms_tot = 0.0
     for _ in range(steps):
-        plan.lp_reset_stream()
+        plan.lp_reset_stream(stream=stream)
         e0.record(stream)
-        plan.lp_process_block(x)
+        plan.lp_process_block(x, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_tot += e0.elapsed_time(e1)
@@ -453,6 +463,8 @@ def run_stress(args):
     found, snrs = np.array(found), np.array(snrs)
     bins = [(5, 10), (10, 15), (15, 20.01)]
     samples = w.n_streams * w.block_len * M
+    chunk_tflops = (w.n_streams * chunk * M * SYNTH_FLOP_PER_SAMPLE /
+                    (tune_ms[tuned_fpc] / 1e3) / 1e12)
     return {
         "workload": w.name, "metric": "realtime factor at 48x488x200 beams x 8 trials",
         "value": block_s / (ms / 1e3), "unit": "x realtime", "ms_per_block": ms,
@@ -463,6 +475,11 @@ def run_stress(args):
         "pulses": len(plist), "recall": float(found.mean()),
         "recall_by_snr": {f"{a}-{int(b)}": float(found[(snrs >= a) & (snrs < b)].mean())
                           for a, b in bins},
+        "synth_frames_per_cta": tuned_fpc, "autotune_ms_per_chunk": {str(k): round(v, 3) for k, v in tune_ms.items()},
+        "cuda_graph": True,
+        "roofline": {"bound": "alu", "kernel": "k_ippf", "basis": "autotuner's CUDA-event time of the synthesis of one 8192-frame chunk",
+                     "achieved": chunk_tflops, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
+                     "frac": chunk_tflops / fp32_peak_tflops()},
         "triggers": int(n_trig), "trigger_status": int(st),
         "triggers_not_near_a_pulse": int(len(trig) - sum(
             1 for r in trig if (int(r["beam"]), int(r["n"]), int(r["tec"])) in used)),

@@ -129,21 +129,28 @@ def test_serving_admission_waits_for_memory(cuda_lib):
     assert admitted_at[2] >= 2
 
 
-def test_chunked_block_equals_whole_block(cuda_lib):
+@pytest.mark.parametrize("graph", [False, True])
+def test_chunked_block_equals_whole_block(cuda_lib, graph):
     """Frame chunks inside a block (beam rows sized for one chunk, noise level
-    from a first power-only pass) give exactly the unchunked results."""
+    from a first power-only pass), launched directly or from a captured graph,
+    give exactly the unchunked results."""
     import torch
     S, P, K, B, Tr, F, fb = 8, 2, 12, 5, 2, 8192, 140
     blocks, enu, dirs, tec = random_case(45, S, P, K, B, Tr, F, fb, "int8", 2, amp=100)
     res = []
     for chunk in (0, 2048):
+        stream = torch.cuda.Stream()
         plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision="fp16",
-                         store_timeseries=True, k_sigma=3.5, chunk_frames=chunk)
-        plan.lp_set_weights(enu, dirs)
-        plan.lp_set_tec(tec)
+                         store_timeseries=True, k_sigma=3.5, chunk_frames=chunk,
+                         use_graph=graph and chunk > 0, stream=stream)
+        plan.lp_set_weights(enu, dirs, stream=stream)
+        plan.lp_set_tec(tec, stream=stream)
+        xd = torch.empty((P, K, F, S, 2), dtype=torch.int8, device="cuda")
         out = []
-        for xb in blocks:
-            plan.lp_process_block(torch.from_numpy(xb).cuda())
+        for xb in blocks:              # same device address every block: one capture
+            with torch.cuda.stream(stream):
+                xd.copy_(torch.from_numpy(xb))
+            plan.lp_process_block(xd, stream=stream)
             out.append((plan.lp_get_timeseries(4, 1, 1), plan.lp_get_timeseries(0, 0, 0),
                         plan.lp_get_triggers()[0], plan.lp_get_sigma()))
         if chunk:
