@@ -3,101 +3,117 @@
 //     beam[j = (b,t,pol)][k][m] = D[k,t] * sum_s w[k,b,s] * x[pol][k][m][s]
 // as FP32 fused multiply-adds; int8/int16 samples are exact in FP32.
 //
-// One thread block handles (pol, subband k, 128 consecutive frames): the
-// station samples of the tile are read once from HBM (contiguous, S*2 values
-// per frame) into shared memory as [station][frame] complex floats, the
-// weights of a chunk of 32 beams as [beam][station].  Each thread owns one
-// frame and 4 beams at a time (16 FMAs per station and beam quad).  Beams are
-// written as rows of consecutive frames, i.e. coalesced.  The block's partial
-// sum of |beam|^2 (the Parseval noise estimate, |D| = 1) goes to
-// power_part[j][k][tile] in a fixed reduction order (deterministic).
+// One thread block (4 warps) handles (pol, subband k, 256 consecutive frames);
+// each thread owns two consecutive frames.  The tile's station samples are read
+// once from HBM (contiguous, [frame][station]) into shared memory in their
+// input form, station-major with a padded row, so that a thread reads both of
+// its frames of one station in one conflict-free access; the weights of up to
+// 64 beams at a time sit in shared memory as (w_re, w_re, -w_im, w_im).  A
+// complex multiply-add is then two packed FFMA2 per frame,
+//     (acc_re, acc_im) += (w_re, w_re) * (x_re, x_im) + (-w_im, w_im) * (x_im, x_re),
+// a thread keeps 8 beams x 2 frames of accumulators and every weight is one
+// shared-memory broadcast for 4 FFMA2.  Beams are written as 16-byte pairs of
+// frames, coalesced.  Each warp's partial of |beam|^2 over its 64 frames (the
+// Parseval noise estimate, |D| = 1) goes to power_part[j][k][64-frame tile] in
+// a fixed reduction order (deterministic).
 #include "lp_internal.cuh"
 
 namespace lp {
 namespace {
 
-constexpr int FT = 128;        // frames per block (= threads)
-constexpr int BC = 32;         // beams per weight chunk
-constexpr int BR = 4;          // beams per register block
+constexpr int FT = 256;          // frames per block
+constexpr int NTH = 128;         // threads per block, two frames each
+constexpr int FW = 64;           // frames per warp = noise-partial tile
+constexpr int FTP = FT + 2;      // padded station row of the sample tile
+constexpr int BB = 8;            // beams per accumulator pass
+constexpr int BCH = 64;          // beams whose weights sit in shared memory
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// two consecutive frames of one station: int8 or int16 complex pairs
+template <typename T2> struct Pair2;
+template <> struct Pair2<char2> { using T = char4; };
+template <> struct Pair2<short2> { using T = short4; };
 
 template <typename T2>
-__global__ void __launch_bounds__(FT) k_beamform_f32(
+__global__ void __launch_bounds__(NTH, 3) k_beamform_f32(
     const T2* __restrict__ x, long long pol_stride, const float2* __restrict__ w,
     const float2* __restrict__ dd, int S, int P, int K, int B, int Tr, long long F, long long row,
-    float2* __restrict__ beams, float* __restrict__ power_part, int n_ftiles, int pol0) {
-  extern __shared__ float2 smem[];
-  float2* xs = smem;                 // [S][FT]
-  float2* ws = smem + S * FT;        // [BC][S]
-  __shared__ float red[FT / 32][BC];
+    float2* __restrict__ beams, float* __restrict__ power_part, int n_ftiles, int pol0,
+    int bch) {
+  using T4 = typename Pair2<T2>::T;
+  extern __shared__ float4 smem4[];
+  float4* ws = smem4;                                        // [bch][S]
+  T2* xs = reinterpret_cast<T2*>(ws + bch * S);              // [S][FTP]
 
   const int tile = blockIdx.x, k = blockIdx.y, pol = pol0 + (int)blockIdx.z;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long f0 = (long long)tile * FT;
-  const long long f = f0 + tid;
-  const bool valid = f < F;
+  const int nvalid = (int)min((long long)FT, F - f0);
 
   // station samples of this (pol, k) and frame tile -> xs[s][frame]
   const T2* xk = x + (long long)pol * pol_stride + ((long long)k * F + f0) * S;
-  const int nvalid = (int)min((long long)(FT), (long long)(F - f0));
-  for (int e = tid; e < FT * S; e += FT) {
-    const int fr = e / S, s = e - fr * S;
-    float2 v = make_float2(0.f, 0.f);
-    if (fr < nvalid) {
-      const T2 q = xk[e];
-      v = make_float2((float)q.x, (float)q.y);
-    }
-    xs[s * FT + fr] = v;
+  for (int e = tid; e < FT * S; e += NTH) {
+    const int fr = e / S, st = e - fr * S;
+    T2 v;
+    v.x = 0;
+    v.y = 0;
+    if (fr < nvalid) v = xk[e];
+    xs[st * FTP + fr] = v;
   }
 
-  for (int b0 = 0; b0 < B; b0 += BC) {
-    const int nb = min(BC, B - b0);
-    __syncthreads();   // xs ready / previous chunk's ws and red consumed
+  const int fl = 2 * tid;                                    // my frames fl, fl + 1
+  const bool va = fl < nvalid, vb = fl + 1 < nvalid;
+  const int ptile = tile * (FT / FW) + warp;                 // my warp's noise tile
+  const bool ptile_ok = (long long)ptile * FW < F;
+  for (int b0 = 0; b0 < B; b0 += bch) {
+    const int nb = min(bch, B - b0);
+    __syncthreads();   // samples ready / previous weights consumed
     const float2* wk = w + ((long long)k * B + b0) * S;
-    for (int e = tid; e < nb * S; e += FT) ws[e] = wk[e];
-    __syncthreads();
-    for (int bb = 0; bb < nb; bb += BR) {
-      float2 acc[BR];
-#pragma unroll
-      for (int i = 0; i < BR; ++i) acc[i] = make_float2(0.f, 0.f);
-      for (int s = 0; s < S; ++s) {
-        const float2 xv = xs[s * FT + tid];
-#pragma unroll
-        for (int i = 0; i < BR; ++i) {
-          const float2 wv = ws[min(bb + i, nb - 1) * S + s];
-          acc[i].x = fmaf(wv.x, xv.x, acc[i].x);
-          acc[i].x = fmaf(-wv.y, xv.y, acc[i].x);
-          acc[i].y = fmaf(wv.x, xv.y, acc[i].y);
-          acc[i].y = fmaf(wv.y, xv.x, acc[i].y);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < BR; ++i) {
-        const int b = b0 + bb + i;
-        if (bb + i >= nb) break;
-        float pw = valid ? acc[i].x * acc[i].x + acc[i].y * acc[i].y : 0.f;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, off);
-        if (lane == 0) red[warp][bb + i] = pw;
-        if (valid) {
-          for (int t = 0; t < Tr; ++t) {
-            const float2 d = dd[k * Tr + t];
-            const float2 v = make_float2(d.x * acc[i].x - d.y * acc[i].y,
-                                         d.x * acc[i].y + d.y * acc[i].x);
-            const long long j = ((long long)b * Tr + t) * P + pol;
-            beams[(j * K + k) * row + kPrefix + f] = v;
-          }
-        }
-      }
+    for (int e = tid; e < nb * S; e += NTH) {
+      const float2 v = wk[e];
+      ws[e] = make_float4(v.x, v.x, -v.y, v.y);
     }
     __syncthreads();
-    if (tid < nb) {
-      float pw = 0.f;
+    for (int bb = 0; bb < nb; bb += BB) {
+      float2 acc[BB][2];
 #pragma unroll
-      for (int wi = 0; wi < FT / 32; ++wi) pw += red[wi][tid];
-      const int b = b0 + tid;
-      for (int t = 0; t < Tr; ++t) {
-        const long long j = ((long long)b * Tr + t) * P + pol;
-        power_part[(j * K + k) * n_ftiles + tile] = pw;
+      for (int i = 0; i < BB; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int st = 0; st < S; ++st) {
+        const T4 q = *reinterpret_cast<const T4*>(xs + st * FTP + fl);
+        const float2 xa = make_float2((float)q.x, (float)q.y);
+        const float2 xb = make_float2((float)q.z, (float)q.w);
+        const float2 xas = make_float2(xa.y, xa.x), xbs = make_float2(xb.y, xb.x);
+#pragma unroll
+        for (int i = 0; i < BB; ++i) {
+          const float4 wv = ws[min(bb + i, nb - 1) * S + st];   // broadcast
+          const float2 w0 = make_float2(wv.x, wv.y), w1 = make_float2(wv.z, wv.w);
+          acc[i][0] = fma2(w1, xas, fma2(w0, xa, acc[i][0]));
+          acc[i][1] = fma2(w1, xbs, fma2(w0, xb, acc[i][1]));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < BB; ++i) {
+        if (bb + i >= nb) break;                             // uniform
+        const int b = b0 + bb + i;
+        float pw = (va ? fmaf(acc[i][0].x, acc[i][0].x, acc[i][0].y * acc[i][0].y) : 0.f) +
+                   (vb ? fmaf(acc[i][1].x, acc[i][1].x, acc[i][1].y * acc[i][1].y) : 0.f);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, off);
+        for (int t = 0; t < Tr; ++t) {
+          const float2 d = dd[k * Tr + t];
+          const float2 u = acc[i][0], v = acc[i][1];
+          const long long j = ((long long)b * Tr + t) * P + pol;
+          float2* dst = beams + (j * K + k) * row + kPrefix + f0 + fl;
+          if (vb)
+            *reinterpret_cast<float4*>(dst) =
+                make_float4(d.x * u.x - d.y * u.y, d.x * u.y + d.y * u.x,
+                            d.x * v.x - d.y * v.y, d.x * v.y + d.y * v.x);
+          else if (va)
+            *dst = make_float2(d.x * u.x - d.y * u.y, d.x * u.y + d.y * u.x);
+          if (lane == 0 && ptile_ok) power_part[(j * K + k) * n_ftiles + ptile] = pw;
+        }
       }
     }
   }
@@ -105,33 +121,37 @@ __global__ void __launch_bounds__(FT) k_beamform_f32(
 
 }  // namespace
 
-int beamform_f32_frame_tile() { return FT; }
+int beamform_f32_frame_tile() { return FW; }
 
-
-size_t f32_smem(const Shape& sh) { return (size_t)(sh.S * FT + BC * sh.S) * sizeof(float2); }
+// beams with weights in shared memory at a time, and the block's shared memory
+int f32_bch(const Shape& sh) { return sh.B < BCH ? sh.B : BCH; }
+size_t f32_smem(const Shape& sh, size_t sample_bytes) {
+  return (size_t)f32_bch(sh) * sh.S * sizeof(float4) + (size_t)sh.S * FTP * sample_bytes;
+}
 
 cudaError_t init_f32_attributes(const Shape& sh) {
   cudaError_t e = cudaFuncSetAttribute(k_beamform_f32<char2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32_smem(sh));
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f32_smem(sh, sizeof(char2)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_beamform_f32<short2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)f32_smem(sh));
+                              (int)f32_smem(sh, sizeof(short2)));
 }
 
 cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_stride,
                                 cudaStream_t s, PolSel ps) {
   const auto& sh = p.shape;
-  const int ntile = (int)((sh.F + FT - 1) / FT);
-  const dim3 grid(ntile, sh.K, ps.npol ? ps.npol : sh.P);
-  const size_t smem = f32_smem(sh);
+  const int nblk = (int)((sh.F + FT - 1) / FT);
+  const int ntile = p.n_ftiles_bf;                    // 64-frame noise tiles
+  const dim3 grid(nblk, sh.K, ps.npol ? ps.npol : sh.P);
   if (p.cfg.input_dtype == LP_INPUT_INT8) {
-    k_beamform_f32<char2><<<grid, FT, smem, s>>>((const char2*)x, pol_stride, p.buf.w32, p.buf.dd,
-                                                 sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F, p.row(),
-                                                 p.buf.beams, p.buf.power_part, ntile, ps.pol0);
+    k_beamform_f32<char2><<<grid, NTH, f32_smem(sh, sizeof(char2)), s>>>(
+        (const char2*)x, pol_stride, p.buf.w32, p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F,
+        p.row(), p.buf.beams, p.buf.power_part, ntile, ps.pol0, f32_bch(sh));
   } else {
-    k_beamform_f32<short2><<<grid, FT, smem, s>>>((const short2*)x, pol_stride, p.buf.w32,
-                                                  p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F,
-                                                  p.row(), p.buf.beams, p.buf.power_part, ntile, ps.pol0);
+    k_beamform_f32<short2><<<grid, NTH, f32_smem(sh, sizeof(short2)), s>>>(
+        (const short2*)x, pol_stride, p.buf.w32, p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F,
+        p.row(), p.buf.beams, p.buf.power_part, ntile, ps.pol0, f32_bch(sh));
   }
   return cudaGetLastError();
 }
