@@ -72,6 +72,8 @@ def parse():
                          "trials x 262144 frames with injected pulses (recall)")
     ap.add_argument("--synth-frames", type=int, default=0,
                     help="fixed synthesis frames per thread block (0: autotune)")
+    ap.add_argument("--gemm-config", type=int, default=-2,
+                    help="fixed beamformer configuration index (-1: default; -2: autotune)")
     ap.add_argument("--frames", type=int, default=0,
                     help="block length override for small profiling cases (not a bench line)")
     return ap.parse_args()
@@ -84,6 +86,14 @@ def bench_workload(args):
         w = dataclasses.replace(w, name=w.name.replace("65536fr", f"{args.frames}fr"),
                                 block_len=args.frames)
     return w
+
+
+def gemm_desc(precision, cfgs, index):
+    """Readable name of beamformer configuration `index` (-1: the default)."""
+    if index < 0:
+        return "default"
+    a, b = cfgs[index]
+    return f"{a} beams per pass" if precision == "fp32" else f"int8 ring {a}, fp16 ring {b}"
 
 
 def workload_config(w, precision):
@@ -265,7 +275,14 @@ def run_ours(args, rank, world, local_rank):
     plan.lp_set_weights(enu, dirs)
     plan.lp_set_tec(tec)
     stream = torch.cuda.current_stream()
-    # one untimed block picks the synthesis tiling (autotuner), then warm-up
+    # untimed blocks pick the beamformer configuration and the synthesis tiling
+    # (autotuners), then warm-up
+    gemm_cfgs = plan.lp_plan_gemm_configs()
+    if args.gemm_config >= -1:
+        plan.lp_plan_set_gemm_config(args.gemm_config)
+        gemm_best, gemm_ms = args.gemm_config, {}
+    else:
+        gemm_best, gemm_ms = plan.lp_plan_autotune_gemm(x)
     if args.synth_frames:
         tuned_fpc, tune_ms = args.synth_frames, {}
     else:
@@ -355,7 +372,10 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f16 tensor-core beamformer, f32" if args.precision == "fp16" else "f32",
         "data": "synthetic (seeded rounded-Gaussian int8 station noise)",
         "config": dict(workload_config(w, args.precision), synth_frames_per_cta=tuned_fpc,
-                       autotune_ms={str(k): round(v, 3) for k, v in tune_ms.items()}),
+                       autotune_ms={str(k): round(v, 3) for k, v in tune_ms.items()},
+                       gemm_config=gemm_desc(args.precision, gemm_cfgs, gemm_best),
+                       gemm_autotune_ms={gemm_desc(args.precision, gemm_cfgs, gemm_cfgs.index(k)):
+                                         round(v, 3) for k, v in gemm_ms.items()}),
         "samples_per_s": {"station_complex": w.pols * w.subbands * w.block_len * w.stations
                           * world / (ms_step / 1e3),
                           "output_200MHz": samples * world / (ms_step / 1e3)},
@@ -419,7 +439,10 @@ def run_stress(args):
                    chunk_frames=chunk, trigger_cap=1 << 22, use_graph=True, stream=stream)
     plan.lp_set_weights(enu, dirs, stream=stream)
     plan.lp_set_tec(tec, stream=stream)
-    # synthesis tiling by the autotuner (timed on the block's first chunk)
+    # beamformer configuration and synthesis tiling by the autotuners (timed on
+    # the block's first chunk)
+    gemm_cfgs = plan.lp_plan_gemm_configs()
+    gemm_best, gemm_ms = plan.lp_plan_autotune_gemm(x, stream=stream)
     tuned_fpc, tune_ms = plan.lp_plan_autotune(x, stream=stream)
     for _ in range(max(1, args.warmup)):          # the first block captures the graph
         plan.lp_reset_stream(stream=stream)       # every timed block is block 0 of the stream
@@ -476,6 +499,9 @@ def run_stress(args):
         "recall_by_snr": {f"{a}-{int(b)}": float(found[(snrs >= a) & (snrs < b)].mean())
                           for a, b in bins},
         "synth_frames_per_cta": tuned_fpc, "autotune_ms_per_chunk": {str(k): round(v, 3) for k, v in tune_ms.items()},
+        "gemm_config": gemm_desc("fp16", gemm_cfgs, gemm_best),
+        "gemm_autotune_ms_per_chunk": {gemm_desc("fp16", gemm_cfgs, gemm_cfgs.index(k)): round(v, 3)
+                                       for k, v in gemm_ms.items()},
         "cuda_graph": True,
         "roofline": {"bound": "alu", "kernel": "k_ippf", "basis": "autotuner's CUDA-event time of the synthesis of one 8192-frame chunk",
                      "achieved": chunk_tflops, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",

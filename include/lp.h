@@ -197,6 +197,33 @@ lp_status lp_reset_stream(lp_plan* plan, void* stream);
 lp_status lp_plan_autotune(lp_plan* plan, const void* x, void* stream, int32_t* best,
                            double* ms_out);
 
+/* Beamformer configurations (the GEMM autotuner's candidates; no counterpart
+ * in the paper).  Writes up to max pairs into desc[2 i], desc[2 i + 1] and
+ * returns their number (at most LP_MAX_GEMM_CONFIGS), or -1 for an unbound
+ * plan.  FP16 form: (int8 ring stages, FP16 ring stages) of the tensor-core
+ * beamformer that fit the shared memory for this shape, deepest first; FP32
+ * form: (beams per accumulator pass, 0), i.e. (8, 0), (16, 0) and (4, 0).  Every
+ * configuration computes the same beams bit for bit. */
+#define LP_MAX_GEMM_CONFIGS 8
+int lp_plan_gemm_configs(const lp_plan* plan, int32_t* desc, int max);
+
+/* Select beamformer configuration `index` (from lp_plan_gemm_configs) for later
+ * blocks; -1 restores the default (the deepest FP16 rings, 8 FP32 beams).
+ * LP_ERR_ARG for an index out of range.  Drops a captured graph. */
+lp_status lp_plan_set_gemm_config(lp_plan* plan, int index);
+
+/* GEMM autotuner: processes block x exactly as lp_process_block does, and
+ * inside that block times the beamformer launch (the whole block, or the
+ * block's first chunk for a chunked plan) in every configuration of
+ * lp_plan_gemm_configs, mean of 3 timed runs after one warm-up run, on the
+ * same input and beam rows; keeps the fastest for later blocks and returns its
+ * index in *best (ms per configuration in ms_out[LP_MAX_GEMM_CONFIGS] when not
+ * NULL).  The beams do not depend on the configuration, so the block's results
+ * are those of lp_process_block.  Synchronises `stream`; drops a captured graph.
+ * Device input only (contiguous layout). */
+lp_status lp_plan_autotune_gemm(lp_plan* plan, const void* x, void* stream, int32_t* best,
+                                double* ms_out);
+
 /* Number of kernel launches lp_process_block makes for a device block (for
  * accounting); a host block processed per polarisation makes 8. */
 int lp_launches_per_block(const lp_plan* plan);

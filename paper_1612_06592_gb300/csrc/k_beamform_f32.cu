@@ -11,7 +11,8 @@
 // 64 beams at a time sit in shared memory as (w_re, w_re, -w_im, w_im).  A
 // complex multiply-add is then two packed FFMA2 per frame,
 //     (acc_re, acc_im) += (w_re, w_re) * (x_re, x_im) + (-w_im, w_im) * (x_im, x_re),
-// a thread keeps 8 beams x 2 frames of accumulators and every weight is one
+// a thread keeps BB beams x 2 frames of accumulators (BB = 4, 8 or 16, chosen
+// by the GEMM autotuner; 8 by default) and every weight is one
 // shared-memory broadcast for 4 FFMA2.  Beams are written as 16-byte pairs of
 // frames, coalesced.  Each warp's partial of |beam|^2 over its 64 frames (the
 // Parseval noise estimate, |D| = 1) goes to power_part[j][k][64-frame tile] in
@@ -25,7 +26,6 @@ constexpr int FT = 256;          // frames per block
 constexpr int NTH = 128;         // threads per block, two frames each
 constexpr int FW = 64;           // frames per warp = noise-partial tile
 constexpr int FTP = FT + 2;      // padded station row of the sample tile
-constexpr int BB = 8;            // beams per accumulator pass
 constexpr int BCH = 64;          // beams whose weights sit in shared memory
 
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -35,7 +35,7 @@ template <typename T2> struct Pair2;
 template <> struct Pair2<char2> { using T = char4; };
 template <> struct Pair2<short2> { using T = short4; };
 
-template <typename T2>
+template <typename T2, int BB>
 __global__ void __launch_bounds__(NTH, 3) k_beamform_f32(
     const T2* __restrict__ x, long long pol_stride, const float2* __restrict__ w,
     const float2* __restrict__ dd, int S, int P, int K, int B, int Tr, long long F, long long row,
@@ -129,31 +129,67 @@ size_t f32_smem(const Shape& sh, size_t sample_bytes) {
   return (size_t)f32_bch(sh) * sh.S * sizeof(float4) + (size_t)sh.S * FTP * sample_bytes;
 }
 
+template <typename T2, int BB>
+cudaError_t set_f32_attr(const Shape& sh) {
+  return cudaFuncSetAttribute(k_beamform_f32<T2, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)f32_smem(sh, sizeof(T2)));
+}
+
 cudaError_t init_f32_attributes(const Shape& sh) {
-  cudaError_t e = cudaFuncSetAttribute(k_beamform_f32<char2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)f32_smem(sh, sizeof(char2)));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_beamform_f32<short2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)f32_smem(sh, sizeof(short2)));
+  cudaError_t e = set_f32_attr<char2, 8>(sh);
+  if (e == cudaSuccess) e = set_f32_attr<char2, 16>(sh);
+  if (e == cudaSuccess) e = set_f32_attr<char2, 4>(sh);
+  if (e == cudaSuccess) e = set_f32_attr<short2, 8>(sh);
+  if (e == cudaSuccess) e = set_f32_attr<short2, 16>(sh);
+  if (e == cudaSuccess) e = set_f32_attr<short2, 4>(sh);
+  return e;
+}
+
+template <typename T2, int BB>
+void launch_f32(const lp_plan& p, const void* x, long long pol_stride, cudaStream_t s,
+                PolSel ps) {
+  const auto& sh = p.shape;
+  const int nblk = (int)((sh.F + FT - 1) / FT);
+  const dim3 grid(nblk, sh.K, ps.npol ? ps.npol : sh.P);
+  k_beamform_f32<T2, BB><<<grid, NTH, f32_smem(sh, sizeof(T2)), s>>>(
+      (const T2*)x, pol_stride, p.buf.w32, p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F, p.row(),
+      p.buf.beams, p.buf.power_part, p.n_ftiles_bf, ps.pol0, f32_bch(sh));
+}
+
+// beams per accumulator pass of each configuration (the first is the default)
+constexpr int kF32Beams[3] = {8, 16, 4};
+
+template <typename T2>
+void launch_f32_bb(const lp_plan& p, const void* x, long long pol_stride, cudaStream_t s,
+                   PolSel ps) {
+  const int bb = p.gemm_cfg >= 0 && p.gemm_cfg < 3 ? kF32Beams[p.gemm_cfg] : kF32Beams[0];
+  if (bb == 16)
+    launch_f32<T2, 16>(p, x, pol_stride, s, ps);
+  else if (bb == 4)
+    launch_f32<T2, 4>(p, x, pol_stride, s, ps);
+  else
+    launch_f32<T2, 8>(p, x, pol_stride, s, ps);
 }
 
 cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_stride,
                                 cudaStream_t s, PolSel ps) {
-  const auto& sh = p.shape;
-  const int nblk = (int)((sh.F + FT - 1) / FT);
-  const int ntile = p.n_ftiles_bf;                    // 64-frame noise tiles
-  const dim3 grid(nblk, sh.K, ps.npol ? ps.npol : sh.P);
-  if (p.cfg.input_dtype == LP_INPUT_INT8) {
-    k_beamform_f32<char2><<<grid, NTH, f32_smem(sh, sizeof(char2)), s>>>(
-        (const char2*)x, pol_stride, p.buf.w32, p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F,
-        p.row(), p.buf.beams, p.buf.power_part, ntile, ps.pol0, f32_bch(sh));
-  } else {
-    k_beamform_f32<short2><<<grid, NTH, f32_smem(sh, sizeof(short2)), s>>>(
-        (const short2*)x, pol_stride, p.buf.w32, p.buf.dd, sh.S, sh.P, sh.K, sh.B, sh.Tr, sh.F,
-        p.row(), p.buf.beams, p.buf.power_part, ntile, ps.pol0, f32_bch(sh));
-  }
+  if (p.cfg.input_dtype == LP_INPUT_INT8)
+    launch_f32_bb<char2>(p, x, pol_stride, s, ps);
+  else
+    launch_f32_bb<short2>(p, x, pol_stride, s, ps);
   return cudaGetLastError();
+}
+
+int tc_configs(const Shape& sh, int* desc, int max);
+
+int beamform_gemm_configs(const lp_plan& p, int* desc, int max) {
+  if (p.cfg.precision == LP_PREC_FP16) return tc_configs(p.shape, desc, max);
+  int n = 0;
+  for (int i = 0; i < 3 && n < max; ++i, ++n) {
+    desc[2 * n] = kF32Beams[i];
+    desc[2 * n + 1] = 0;
+  }
+  return n;
 }
 
 }  // namespace lp

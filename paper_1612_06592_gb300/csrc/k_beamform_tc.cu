@@ -622,14 +622,36 @@ cudaError_t encode_beams_map(lp_plan& p) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-size_t tc_smem(const Shape& sh) {
-  int n8, nb;
-  tc_depths(sh, &n8, &nb);
+size_t tc_smem_for(const Shape& sh, int n8, int nb) {
   const size_t KP = kpad(sh.S);
   // at least 120 KB: one block per SM (it takes all 512 TMEM columns)
   return std::max<size_t>(1024 + STG_BYTES + 2 * TM * KP * 2 + (size_t)n8 * TN * 2 * sh.S +
                               (size_t)nb * TN * KP * 2,
                           120 * 1024);
+}
+
+// (int8 stages, FP16 stages) that fit the shared memory, deepest first
+int tc_configs(const Shape& sh, int* desc, int max) {
+  const size_t limit = 227 * 1024 - 2048 - STG_BYTES - 1024;
+  const size_t KP = kpad(sh.S);
+  const size_t a = 2 * TM * KP * 2, t8 = (size_t)TN * 2 * sh.S, b = TN * KP * 2;
+  int n = 0;
+  for (int nb = MAX_SB; nb >= 1; --nb)
+    for (int n8 = MAX_S8; n8 >= 1; --n8)
+      if (a + nb * b + n8 * t8 <= limit && n < max) {
+        desc[2 * n] = n8;
+        desc[2 * n + 1] = nb;
+        ++n;
+      }
+  return n;
+}
+
+size_t tc_smem(const Shape& sh) {            // the largest configuration
+  int desc[2 * MAX_S8 * MAX_SB];
+  const int n = tc_configs(sh, desc, MAX_S8 * MAX_SB);
+  size_t m = 0;
+  for (int i = 0; i < n; ++i) m = std::max(m, tc_smem_for(sh, desc[2 * i], desc[2 * i + 1]));
+  return m;
 }
 
 cudaError_t init_tc_attributes(const Shape& sh) {
@@ -667,8 +689,16 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_st
   a.npol = ps.npol ? ps.npol : sh.P;
   a.n_items = (long long)sh.K * a.n_mt * a.npol * a.n_chunks;
   tc_depths(sh, &a.n_s8, &a.n_sb);
+  if (p.gemm_cfg >= 0) {                       // autotuned depths
+    int desc[2 * MAX_S8 * MAX_SB];
+    const int n = tc_configs(sh, desc, MAX_S8 * MAX_SB);
+    if (p.gemm_cfg < n) {
+      a.n_s8 = desc[2 * p.gemm_cfg];
+      a.n_sb = desc[2 * p.gemm_cfg + 1];
+    }
+  }
   const long long grid = std::min<long long>(a.n_items, (long long)num_sms());
-  k_beamform_tc<<<(unsigned)grid, NT, tc_smem(sh), s>>>(
+  k_beamform_tc<<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(
       a, *reinterpret_cast<const CUtensorMap*>(p.beams_map));
   return cudaGetLastError();
 }

@@ -285,49 +285,107 @@ lp_status lp_set_tec(lp_plan* p, const double* tec, void* stream) {
 
 namespace {
 
-// Synthesis of one chunk while timing the candidate tilings (autotuner): each
-// candidate reruns the same launch on the same beam rows (before the history
-// shift), the fastest is kept and run last, so the outputs are a normal run's.
-cudaError_t tune_ippf(lp_plan* p, const lp::Chunk& c, cudaStream_t s, double* ms_out) {
-  const int cand[6] = {64, 128, 256, 512, 1024, 2048};
+enum Tune { kTuneNone = 0, kTuneSynth = 1, kTuneGemm = 2 };
+
+extern "C++" {
+// Mean CUDA-event time of runs 2-4 of launch() on s (the first run warms up).
+template <class Launch>
+cudaError_t time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, Launch&& launch,
+                        double* ms_mean) {
+  double ms_sum = 0.0;
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) ms_sum += ms;
+  }
+  *ms_mean = ms_sum / 3.0;
+  return e;
+}
+
+// Runs launch() under each of n settings (set(i) selects one) while timing it,
+// keeps the fastest and runs it once more, so that what the launch leaves in
+// device memory is a normal run's.  The launches must be idempotent.
+template <class Set, class Launch>
+cudaError_t tune_launch(int n, cudaStream_t s, Set&& set, Launch&& launch, double* ms_out,
+                        int* best) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   double best_ms = 1e30;
-  int best_fpc = p->frames_per_cta;
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
     if (ms_out) ms_out[i] = 0.0;
-    if (cand[i] > c.nf) continue;
-    p->frames_per_cta = cand[i];
-    double ms_sum = 0.0;
-    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-      e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
-      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-      if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) ms_sum += ms;                 // the first run warms up
-    }
+    if (!set(i)) continue;                     // candidate not applicable
+    double ms = 0.0;
+    e = time_launch(s, e0, e1, launch, &ms);
     if (e == cudaSuccess) {
-      const double ms = ms_sum / 3.0;
       if (ms_out) ms_out[i] = ms;
       if (ms < best_ms) {
         best_ms = ms;
-        best_fpc = cand[i];
+        *best = i;
       }
     }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  p->frames_per_cta = best_fpc;
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s);
+  if (e == cudaSuccess) set(*best);
+  if (e == cudaSuccess) e = launch();
   return e;
 }
 
-lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, bool tune,
+}  // extern "C++"
+
+// Synthesis of one chunk while timing the candidate tilings (autotuner): each
+// candidate reruns the same launch on the same beam rows (before the history
+// shift).
+cudaError_t tune_ippf(lp_plan* p, const lp::Chunk& c, cudaStream_t s, double* ms_out) {
+  static const int cand[6] = {64, 128, 256, 512, 1024, 2048};
+  int best = -1;
+  for (int i = 0; i < 6; ++i)
+    if (cand[i] == p->frames_per_cta) best = i;
+  const int keep = p->frames_per_cta;
+  auto set = [&](int i) {
+    if (i < 0) {
+      p->frames_per_cta = keep;
+      return true;
+    }
+    if (cand[i] > c.nf) return false;
+    p->frames_per_cta = cand[i];
+    return true;
+  };
+  auto launch = [&]() {
+    cudaError_t e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
+    return e == cudaSuccess ? lp::launch_ippf(*p, c, s) : e;
+  };
+  return tune_launch(6, s, set, launch, ms_out, &best);
+}
+
+// Beamformer launch over chunk c while timing the configurations (GEMM
+// autotuner): each reruns the same launch on the same input; it rewrites the
+// chunk's beam rows and noise partials.
+cudaError_t tune_gemm(lp_plan* p, const void* x, long long stride, const lp::Chunk& c,
+                      cudaStream_t s, double* ms_out) {
+  int desc[2 * LP_MAX_GEMM_CONFIGS];
+  const int n = lp::beamform_gemm_configs(*p, desc, LP_MAX_GEMM_CONFIGS);
+  if (ms_out)
+    for (int i = n; i < LP_MAX_GEMM_CONFIGS; ++i) ms_out[i] = 0.0;
+  int best = -1;
+  auto set = [&](int i) {
+    p->gemm_cfg = i;
+    return true;
+  };
+  auto launch = [&]() {
+    return p->cfg.precision == LP_PREC_FP16 ? lp::launch_beamform_tc(*p, x, stride, c, s)
+                                            : lp::launch_beamform_f32(*p, x, stride, s);
+  };
+  return tune_launch(n, s, set, launch, ms_out, &best);
+}
+
+lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, Tune tune,
                   double* tune_ms);
 
 }  // namespace
@@ -335,19 +393,52 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, b
 lp_status lp_process_block(lp_plan* p, const void* x, void* stream) {
   if (!p) return LP_ERR_ARG;
   const auto& sh = p->shape;
-  return process(p, x, (int64_t)sh.K * sh.F * sh.S, stream, false, nullptr);
+  return process(p, x, (int64_t)sh.K * sh.F * sh.S, stream, kTuneNone, nullptr);
 }
 
 lp_status lp_process_block_strided(lp_plan* p, const void* x, int64_t pol_stride, void* stream) {
-  return process(p, x, pol_stride, stream, false, nullptr);
+  return process(p, x, pol_stride, stream, kTuneNone, nullptr);
 }
 
 lp_status lp_plan_autotune(lp_plan* p, const void* x, void* stream, int32_t* best,
                            double* ms_out) {
   if (!p || !best) return LP_ERR_ARG;
   const auto& sh = p->shape;
-  const lp_status st = process(p, x, (int64_t)sh.K * sh.F * sh.S, stream, true, ms_out);
+  const lp_status st = process(p, x, (int64_t)sh.K * sh.F * sh.S, stream, kTuneSynth, ms_out);
   if (st == LP_OK) *best = p->frames_per_cta;
+  return st;
+}
+
+int lp_plan_gemm_configs(const lp_plan* p, int32_t* desc, int max) {
+  if (!p || !p->bound || max < 0 || (max > 0 && !desc)) return -1;
+  int all[2 * LP_MAX_GEMM_CONFIGS];
+  const int n = lp::beamform_gemm_configs(*p, all, LP_MAX_GEMM_CONFIGS);
+  for (int i = 0; i < 2 * std::min(n, max); ++i) desc[i] = all[i];
+  return n;
+}
+
+lp_status lp_plan_set_gemm_config(lp_plan* p, int index) {
+  if (lp_status st = need_bound(p)) return st;
+  int all[2 * LP_MAX_GEMM_CONFIGS];
+  const int n = lp::beamform_gemm_configs(*p, all, LP_MAX_GEMM_CONFIGS);
+  if (index < -1 || index >= n)
+    return fail(p, LP_ERR_ARG, "gemm configuration %d not in [-1, %d)", index, n);
+  if (p->graph_exec) {
+    if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+    if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  p->gemm_cfg = index;
+  return LP_OK;
+}
+
+lp_status lp_plan_autotune_gemm(lp_plan* p, const void* x, void* stream, int32_t* best,
+                                double* ms_out) {
+  if (!p || !best) return LP_ERR_ARG;
+  const auto& sh = p->shape;
+  const lp_status st = process(p, x, (int64_t)sh.K * sh.F * sh.S, stream, kTuneGemm, ms_out);
+  if (st == LP_OK) *best = p->gemm_cfg;
   return st;
 }
 
@@ -411,7 +502,7 @@ lp_status process_host_pipelined(lp_plan* p, const void* x, int64_t pol_stride, 
   return LP_OK;
 }
 
-lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, bool tune,
+lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, Tune tune,
                   double* tune_ms) {
   if (lp_status st = need_bound(p)) return st;
   if (!p->weights_set || !p->tec_set)
@@ -469,14 +560,16 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, b
       c.nf = sh.F;
       prof_mark(p, LP_STAGE_BEAMFORM, 0, s);
       if (e == cudaSuccess)
-        e = fp16 ? lp::launch_beamform_tc(*p, xd, stride, c, s)
-                 : lp::launch_beamform_f32(*p, xd, stride, s);
+        e = tune == kTuneGemm ? tune_gemm(p, xd, stride, c, s, tune_ms)
+            : fp16            ? lp::launch_beamform_tc(*p, xd, stride, c, s)
+                              : lp::launch_beamform_f32(*p, xd, stride, s);
       prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
       prof_mark(p, LP_STAGE_SIGMA, 0, s);
       if (e == cudaSuccess) e = lp::launch_sigma(*p, s);
       prof_mark(p, LP_STAGE_SIGMA, 1, s);
       prof_mark(p, LP_STAGE_SYNTH, 0, s);
-      if (e == cudaSuccess) e = tune ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
+      if (e == cudaSuccess)
+        e = tune == kTuneSynth ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
       prof_mark(p, LP_STAGE_SYNTH, 1, s);
       prof_mark(p, LP_STAGE_SHIFT, 0, s);
       if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
@@ -499,9 +592,11 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, b
         c.nf = p->fc;
         c.write_power = false;
         c.last = f0 + p->fc >= sh.F;
-        e = lp::launch_beamform_tc(*p, xd, stride, c, s);
+        e = tune == kTuneGemm && f0 == 0 ? tune_gemm(p, xd, stride, c, s, tune_ms)
+                                         : lp::launch_beamform_tc(*p, xd, stride, c, s);
         if (e == cudaSuccess)
-          e = tune && f0 == 0 ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
+          e = tune == kTuneSynth && f0 == 0 ? tune_ippf(p, c, s, tune_ms)
+                                            : lp::launch_ippf(*p, c, s);
         if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
       }
       prof_mark(p, LP_STAGE_BEAMFORM, 1, s);

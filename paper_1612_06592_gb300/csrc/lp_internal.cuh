@@ -120,6 +120,7 @@ struct lp_plan {
   const void* graph_x = nullptr;
   long long graph_stride = -1;
   long long tune_blk = 0;    // host copy of the device block counter (autotuner)
+  int gemm_cfg = -1;         // beamformer configuration (index into beamform_gemm_configs; -1: default)
   // TMA map of the beam rows (CUtensorMap, 128 bytes) for the FP16 form
   alignas(64) unsigned char beams_map[128] = {};
 };
@@ -148,6 +149,10 @@ cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t 
 cudaError_t init_kernel_attributes(const Shape& sh);
 
 int beamform_f32_frame_tile();
+// Beamformer configurations the GEMM autotuner may pick, two ints each: FP16 form
+// (int8 stages, FP16 stages) that fit the shared memory; FP32 form (beams per
+// accumulator pass, 0).  Returns the count (at most max).
+int beamform_gemm_configs(const lp_plan& p, int* desc, int max);
 int beamform_tc_frame_tile();
 int beamform_tc_partials(long long F);
 size_t beamform_tc_weight_bytes(const Shape& sh);

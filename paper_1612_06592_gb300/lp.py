@@ -79,6 +79,9 @@ SIGNATURES = {
     "lp_reset_stream": (ctypes.c_int, [_P, _P]),
     "lp_launches_per_block": (ctypes.c_int, [_P]),
     "lp_plan_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
+    "lp_plan_gemm_configs": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "lp_plan_set_gemm_config": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lp_plan_autotune_gemm": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
     "lp_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "lp_profile_read": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
     "lp_process_block_noalloc": (ctypes.c_int, [
@@ -272,6 +275,31 @@ class Plan:
                                           ctypes.byref(best), ms.ctypes.data), "lp_plan_autotune")
         cand = (64, 128, 256, 512, 1024, 2048)
         return best.value, {c: m for c, m in zip(cand, ms.tolist()) if m > 0}
+
+    MAX_GEMM_CONFIGS = 8
+
+    def lp_plan_gemm_configs(self):
+        """Beamformer configurations: [(int8 stages, FP16 stages)] for the FP16
+        form, [(beams per pass, 0)] for the FP32 form."""
+        desc = np.zeros(2 * self.MAX_GEMM_CONFIGS, dtype=np.int32)
+        n = _lib.lp_plan_gemm_configs(self._h, desc.ctypes.data, self.MAX_GEMM_CONFIGS)
+        if n < 0:
+            raise LPError(LP_ERR_STATE, "lp_plan_gemm_configs: plan not bound")
+        return [(int(desc[2 * i]), int(desc[2 * i + 1])) for i in range(n)]
+
+    def lp_plan_set_gemm_config(self, index):
+        self._check(_lib.lp_plan_set_gemm_config(self._h, int(index)), "lp_plan_set_gemm_config")
+
+    def lp_plan_autotune_gemm(self, x, stream=None):
+        """Process block x while picking the beamformer configuration by timing;
+        returns (index, {configuration: ms})."""
+        best = ctypes.c_int32()
+        ms = np.zeros(self.MAX_GEMM_CONFIGS, dtype=np.float64)
+        self._check(_lib.lp_plan_autotune_gemm(self._h, _ptr(x), _stream_ptr(stream),
+                                               ctypes.byref(best), ms.ctypes.data),
+                    "lp_plan_autotune_gemm")
+        cfgs = self.lp_plan_gemm_configs()
+        return best.value, {c: m for c, m in zip(cfgs, ms.tolist()) if m > 0}
 
     STAGES = ("h2d", "beamform", "sigma", "synth", "shift")
 

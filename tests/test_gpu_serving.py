@@ -185,3 +185,53 @@ def test_autotune_keeps_results(cuda_lib):
         np.testing.assert_array_equal(plan.lp_get_timeseries(5, 0, 1), ref.lp_get_timeseries(5, 0, 1))
         np.testing.assert_array_equal(plan.lp_get_triggers()[0], ref.lp_get_triggers()[0])
         np.testing.assert_array_equal(plan.lp_get_sigma(), ref.lp_get_sigma())
+
+
+@pytest.mark.parametrize("precision,chunk", [("fp32", 0), ("fp16", 0), ("fp16", 2048)])
+def test_gemm_configs_bit_identical(cuda_lib, precision, chunk):
+    """Every beamformer configuration the GEMM autotuner may pick (ring depths of
+    the tensor-core form, beams per pass of the FP32 form) gives the same beams,
+    noise level, time series and triggers bit for bit; so does a block processed
+    by the autotuner itself."""
+    import torch
+    S, P, K, B, Tr, F, fb = 24, 2, 12, 37, 2, 4096, 230
+    blocks, enu, dirs, tec = random_case(47, S, P, K, B, Tr, F, fb, "int8", 2, amp=60)
+    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision=precision,
+                     store_timeseries=True, k_sigma=5.0, chunk_frames=chunk)
+    plan.lp_set_weights(enu, dirs)
+    plan.lp_set_tec(tec)
+    cfgs = plan.lp_plan_gemm_configs()
+    if precision == "fp32":
+        assert cfgs == [(8, 0), (16, 0), (4, 0)]
+    else:
+        assert len(cfgs) >= 2 and all(1 <= a <= 3 and 1 <= b <= 2 for a, b in cfgs)
+    xds = [torch.from_numpy(xb).cuda() for xb in blocks]
+
+    def run(index, tune=False):
+        plan.lp_reset_stream()
+        if not tune:
+            plan.lp_plan_set_gemm_config(index)
+        out = []
+        for i, xd in enumerate(xds):
+            if tune and i == 0:
+                best, ms = plan.lp_plan_autotune_gemm(xd)
+                assert 0 <= best < len(cfgs) and cfgs[best] in ms
+                assert len(ms) == len(cfgs) and all(v > 0 for v in ms.values())
+            else:
+                plan.lp_process_block(xd)
+            trig, n_trig, st = plan.lp_get_triggers()
+            assert st == 0 and 0 < n_trig == len(trig)   # the whole list (no overflow)
+            out.append((plan.lp_get_beams(36, 1, 1) if not chunk else None,
+                        plan.lp_get_timeseries(36, 1, 1), plan.lp_get_timeseries(3, 0, 0),
+                        plan.lp_get_sigma(), trig))
+        return out
+
+    ref = run(-1)
+    for i in list(range(len(cfgs))) + ["tune"]:
+        got = run(-1, tune=True) if i == "tune" else run(i)
+        for a, b in zip(ref, got):
+            for u, v in zip(a, b):
+                if u is not None:
+                    np.testing.assert_array_equal(u, v)
+    with pytest.raises(Exception):
+        plan.lp_plan_set_gemm_config(len(cfgs))
