@@ -29,6 +29,7 @@ __all__ = [
     "bessel_i0", "prototype_filter", "synthesis_filter", "fft_radix2",
     "ippf", "parseval_power", "update_sigma2", "find_triggers",
     "Pipeline", "stream_window", "brute_force_stream",
+    "INT16_MAX", "group_centres", "prebeam_weights", "prebeam", "transport_int16",
 ]
 
 # Sec. 2: antennas are sampled every 5 ns  ->  fs = 200 MHz.
@@ -133,6 +134,86 @@ def beamform(x: np.ndarray, w: np.ndarray, d: np.ndarray) -> np.ndarray:
     out = acc[:, None, :, :, :] * d.T[None, :, None, :, None]
     assert out.shape == (B, Tr, P, K, F)
     return out
+
+
+# --------------------------------------------------------------------------
+# Two-stage beamforming (Sec. 4, network paragraph)
+# --------------------------------------------------------------------------
+#
+# The paper: fewer than ten stations' worth of 16-bit data fit through the link
+# to the processing cluster, so preliminary beams are first formed from subsets
+# of stations by the correlator's regular beamformer, sent on, and combined into
+# the final beams there.  Readings (the paper gives no more than that):
+#   * the subsets are disjoint station groups; a station in no group is unused;
+#   * each group forms one preliminary beam, toward a direction of its own
+#     (normally the pointing centre), phased to the group's phase centre r_g =
+#     the mean position of its stations, so the preliminary beam is a "station"
+#     at r_g for the final stage;
+#   * it travels as complex int16 like station data: round half to even of
+#     scale * value, saturated to [-32767, 32767];
+#   * the final stage is the ordinary beamformer of this module with the group
+#     centres as station positions.
+
+INT16_MAX = 32767
+
+
+def group_centres(station_enu: np.ndarray, group_of_station: np.ndarray,
+                  n_groups: int) -> np.ndarray:
+    """Phase centre of each station group: the mean ENU position of its
+    stations, [G, 3] (reading above).  Every group must have a station."""
+    r = np.asarray(station_enu, dtype=np.float64)
+    grp = np.asarray(group_of_station)
+    out = np.zeros((n_groups, 3))
+    for g in range(n_groups):
+        members = np.flatnonzero(grp == g)
+        if members.size == 0:
+            raise ValueError(f"group {g} has no station")
+        out[g] = r[members].sum(axis=0) / members.size
+    return out
+
+
+def prebeam_weights(nu_hz: np.ndarray, station_enu: np.ndarray, group_of_station: np.ndarray,
+                    group_dir: np.ndarray) -> np.ndarray:
+    """Preliminary-beam weights w1[k, g, s] (Sec. 4 network paragraph, Sec. 3 first
+    paragraph): the tied-array weight of station s toward the group's direction
+    s_g, relative to the group's phase centre r_g, for the stations of group g,
+    and zero for the others:
+        w1[k, g, s] = exp(-2 pi i nu_k ((r_s - r_g) . s_g) / c)  if s in g.
+    """
+    nu = np.asarray(nu_hz, dtype=np.float64)
+    r = np.asarray(station_enu, dtype=np.float64)
+    grp = np.asarray(group_of_station)
+    d = np.asarray(group_dir, dtype=np.float64)
+    G = d.shape[0]
+    centres = group_centres(r, grp, G)
+    w1 = np.zeros((nu.size, G, r.shape[0]), dtype=np.complex128)
+    for s in range(r.shape[0]):
+        g = int(grp[s])
+        if g < 0:
+            continue
+        cycles = nu * ((r[s] - centres[g]) @ d[g]) / C_LIGHT
+        w1[:, g, s] = np.exp(-2j * np.pi * cycles)
+    return w1
+
+
+def prebeam(x: np.ndarray, w1: np.ndarray) -> np.ndarray:
+    """Preliminary beams pb[p, k, m, g] = sum_s w1[k, g, s] x[p, k, m, s] as a
+    direct sum over stations (complex128).  x: complex [P, K, F, S]."""
+    x = np.asarray(x, dtype=np.complex128)
+    P, K, F, S = x.shape
+    G = w1.shape[1]
+    out = np.zeros((P, K, F, G), dtype=np.complex128)
+    for s in range(S):
+        out += w1[None, :, None, :, s] * x[:, :, :, s, None]
+    return out
+
+
+def transport_int16(v: np.ndarray, scale: float) -> np.ndarray:
+    """Complex value -> the int16 transport code [..., 2] (re, im): round half to
+    even of scale * value, saturated to [-INT16_MAX, INT16_MAX] (reading)."""
+    v = np.asarray(v, dtype=np.complex128) * scale
+    out = np.stack([np.rint(v.real), np.rint(v.imag)], axis=-1)
+    return np.clip(out, -INT16_MAX, INT16_MAX).astype(np.int16)
 
 
 # --------------------------------------------------------------------------

@@ -21,6 +21,7 @@ import numpy as np
 from scipy.special import ndtri
 
 __all__ = [
+    "station_groups",
     "Workload", "TINY", "FULLBAND", "PRECISION", "SERVING", "STRESS", "WORKLOADS",
     "station_positions", "pointing_enu", "hex_beam_directions", "gaussian_table",
     "noise_slab", "analysis_filter", "forward_ppf", "dispersed_pulse",
@@ -146,6 +147,37 @@ def hex_beam_directions(n_beams: int, spacing_deg: float = 0.06,
         v = s0 + sp * l * e1 + sp * m * e2
         out.append(v / np.linalg.norm(v))
     return np.array(out)
+
+
+def station_groups(station_enu: np.ndarray, n_groups: int, iters: int = 50) -> np.ndarray:
+    """Compact disjoint station groups for two-stage beamforming, [S] group index.
+
+    Lloyd's k-means on the ENU positions, started from the farthest-point
+    sequence beginning at the station nearest the array centre (deterministic);
+    ties go to the lower group index.  Input geometry only: the pipeline and the
+    oracle take any grouping.
+    """
+    r = np.asarray(station_enu, dtype=np.float64)
+    first = int(np.argmin(np.linalg.norm(r - r.mean(axis=0), axis=1)))
+    seeds = [first]
+    dist = np.linalg.norm(r - r[first], axis=1)
+    while len(seeds) < n_groups:
+        nxt = int(np.argmax(dist))
+        seeds.append(nxt)
+        dist = np.minimum(dist, np.linalg.norm(r - r[nxt], axis=1))
+    centres = r[seeds].copy()
+    grp = np.zeros(r.shape[0], dtype=np.int32)
+    for _ in range(iters):
+        d2 = ((r[:, None, :] - centres[None, :, :]) ** 2).sum(axis=2)
+        new = np.argmin(d2, axis=1).astype(np.int32)
+        for g in range(n_groups):
+            if not np.any(new == g):          # keep every group populated
+                new[int(np.argmin(d2[:, g]))] = g
+        if np.array_equal(new, grp) and _ > 0:
+            break
+        grp = new
+        centres = np.stack([r[grp == g].mean(axis=0) for g in range(n_groups)])
+    return grp
 
 
 def make_geometry(w: Workload):

@@ -167,6 +167,107 @@ def test_two_station_off_beam_response():
                                rtol=1e-10)
 
 
+# ------------------------------------------- two-stage beamforming --------
+
+def _plane_wave(nu, enu, src, x0):
+    """Station data of a plane wave from unit vector src: station s sees
+    exp(+2 pi i nu (r_s . src) / c) x0 (the arrival model of the pins above)."""
+    tau = enu @ src / O.C_LIGHT
+    return x0[..., None] * np.exp(2j * np.pi * nu[:, None, None] * tau[None, None, :])
+
+
+def test_group_centre_is_member_mean():
+    enu = np.array([[0.0, 0, 0], [30, 0, 0], [0, 60, 0], [500, 500, 0], [700, 500, 0]])
+    grp = np.array([0, 0, 0, 1, 1])
+    np.testing.assert_allclose(O.group_centres(enu, grp, 2), [[10, 20, 0], [600, 500, 0]])
+    with pytest.raises(ValueError):
+        O.group_centres(enu, grp, 3)
+
+
+def test_singleton_groups_pass_samples_through():
+    """A group of one station is phased to that station: w1 = 1, pb = x."""
+    S, K = 6, 3
+    enu = synth.station_positions(S, 4)
+    nu = O.sky_frequencies(150, K)
+    dirs = synth.hex_beam_directions(S)
+    w1 = O.prebeam_weights(nu, enu, np.arange(S), dirs)
+    np.testing.assert_allclose(w1, np.broadcast_to(np.eye(S), (K, S, S)), atol=1e-15)
+    rng = np.random.default_rng(5)
+    x = rng.integers(-100, 100, size=(2, K, 7, S)) + 1j * rng.integers(-100, 100, size=(2, K, 7, S))
+    np.testing.assert_array_equal(O.prebeam(x, w1), x)
+
+
+def test_preliminary_beam_of_a_plane_wave_from_its_direction():
+    """Plane wave from the group direction: pb_g = n_g x0 exp(+2 pi i nu r_g . s / c)
+    (closed form: the group sums coherently at its phase centre)."""
+    S, K, G = 12, 4, 3
+    enu = synth.station_positions(S, 6)
+    grp = np.arange(S) % G
+    s0 = synth.pointing_enu(170, 50)
+    nu = O.sky_frequencies(300, K)
+    rng = np.random.default_rng(8)
+    x0 = rng.normal(size=(K, 5)) + 1j * rng.normal(size=(K, 5))
+    x = _plane_wave(nu, enu, s0, x0)[None]                      # [1, K, 5, S]
+    pb = O.prebeam(x, O.prebeam_weights(nu, enu, grp, np.tile(s0, (G, 1))))
+    cen = enu.reshape(S // G, G, 3).mean(axis=0)                # members g, g+G, ...
+    want = (S // G) * x0[:, :, None] * np.exp(
+        2j * np.pi * nu[:, None, None] * (cen @ s0)[None, None, :] / O.C_LIGHT)
+    np.testing.assert_allclose(pb[0], want, rtol=1e-12, atol=1e-12)
+
+
+def test_two_stage_equals_one_stage_toward_the_preliminary_direction():
+    """w1 (relative to r_g) times the final weight at r_g is the single-stage
+    weight at r_s, so on the preliminary direction the two stages compose to the
+    single-stage beam for any data (exact up to rounding)."""
+    S, K, G = 10, 3, 4
+    enu = synth.station_positions(S, 9)
+    grp = synth.station_groups(enu, G)
+    s0 = synth.pointing_enu()
+    nu = O.sky_frequencies(120, K)
+    rng = np.random.default_rng(10)
+    x = rng.normal(size=(2, K, 6, S)) + 1j * rng.normal(size=(2, K, 6, S))
+    pb = O.prebeam(x, O.prebeam_weights(nu, enu, grp, np.tile(s0, (G, 1))))
+    d = O.dedispersion_weights(nu, [0.0, 15.0], nu.mean())
+    cen = O.group_centres(enu, grp, G)
+    two = O.beamform(pb, O.geometric_weights(nu, cen, s0[None]), d)
+    one = O.beamform(x, O.geometric_weights(nu, enu, s0[None]), d)
+    np.testing.assert_allclose(two, one, rtol=1e-11, atol=1e-11)
+
+
+def test_two_station_group_response_off_its_direction():
+    """Two stations at r_g +- a: a plane wave from s != s_g gives
+    |pb| = 2 |cos(2 pi nu a . (s - s_g) / c)| (closed form)."""
+    a = np.array([220.0, -90.0, 0.0])
+    rg = np.array([-400.0, 300.0, 0.0])
+    enu = np.stack([rg + a, rg - a])
+    sg = synth.pointing_enu(180, 45)
+    src = synth.pointing_enu(180.2, 45.1)
+    nu = O.sky_frequencies(250, 5)
+    x = _plane_wave(nu, enu, src, np.ones((5, 1)))[None]
+    pb = O.prebeam(x, O.prebeam_weights(nu, enu, np.array([0, 0]), sg[None]))
+    want = 2 * np.abs(np.cos(2 * np.pi * nu * (a @ (src - sg)) / O.C_LIGHT))
+    np.testing.assert_allclose(np.abs(pb[0, :, 0, 0]), want, rtol=1e-10)
+
+
+def test_transport_int16_rounds_half_to_even_and_saturates():
+    v = np.array([0.5, 1.5, -2.5, 2.4999, 40000.0, -40000.0, 32767.4]) + 1j * np.array(
+        [-0.5, 3.5, 7.0, -7.5, 0.0, 1e9, -32768.0])
+    got = O.transport_int16(v, 1.0)
+    np.testing.assert_array_equal(got[:, 0], [0, 2, -2, 2, 32767, -32767, 32767])
+    np.testing.assert_array_equal(got[:, 1], [0, 4, 7, -8, 0, 32767, -32767])
+    np.testing.assert_array_equal(O.transport_int16(np.array([1.25 - 0.75j]), 2.0),
+                                  [[2, -2]])
+
+
+def test_station_groups_are_a_kmeans_partition():
+    enu = synth.station_positions(48, 3)
+    grp = synth.station_groups(enu, 8)
+    assert grp.shape == (48,) and set(grp.tolist()) == set(range(8))
+    cen = O.group_centres(enu, grp, 8)
+    d2 = ((enu[:, None, :] - cen[None]) ** 2).sum(axis=2)
+    assert np.all(d2[np.arange(48), grp] <= d2.min(axis=1) + 1e-6)   # Lloyd fixpoint
+
+
 # ------------------------------------------------------- dispersion --------
 
 def test_kappa_from_codata():
