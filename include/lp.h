@@ -278,6 +278,55 @@ void lp_plan_destroy(lp_plan* plan);
 const char* lp_last_error(const lp_plan* plan);
 const char* lp_status_string(lp_status s);
 
+/* ---- Two-stage beamforming: preliminary beams of station groups --------
+ *
+ * Sec. 4 (network paragraph): only a few 16-bit station streams fit through
+ * the link to the processing cluster, so the correlator first forms
+ * preliminary beams from subsets of stations and the final beams are formed
+ * from those.  lp_prebeam is that first stage on the GPU:
+ *     pb[p][k][m][g] = sum over stations s of group g of w1[k][s] x[p][k][m][s],
+ *     w1[k][s] = exp(-2 pi i nu_k ((r_s - r_g) . s_g) / c),
+ * r_g the group's phase centre (mean position of its stations), s_g the
+ * group's direction, nu_k the sky frequency of bin first_bin + k.  Each value
+ * leaves as complex int16, round half to even of scale * pb, saturated to
+ * [-32767, 32767], in the station-block layout [P][K][F][G][2] (re, im), so
+ * that an lp_plan with stations = G, LP_INPUT_INT16 and the group centres as
+ * station positions (lp_prebeam_group_centres) forms the final beams.
+ * Groups are disjoint; a station in no group is unused.  FP32 products and
+ * sums; the phase argument in FP64 cycles. */
+typedef struct lp_prebeam lp_prebeam;
+
+/* Shapes only (no device work): stations S, pols 1 or 2, subbands K, frames F,
+ * groups 1 <= G <= S, bins [first_bin, first_bin + K) inside [1, 512),
+ * LP_INPUT_INT8 or LP_INPUT_INT16.  LP_ERR_ARG for anything out of range. */
+lp_status lp_prebeam_create(lp_prebeam** out, int stations, int pols, int subbands,
+                            int64_t block_len, int groups, int first_bin, int input_dtype);
+
+/* group_of_station[S] in [-1, G) (-1: unused; every group needs a station),
+ * station_enu[S][3] metres, group_dir[G][3] unit vectors (host arrays, read
+ * before return).  Computes the phase centres and the weight table on the
+ * device current at the first call (which allocates the plan's device memory)
+ * on `stream`.  LP_ERR_ARG for a bad table, LP_ERR_CUDA for a CUDA failure. */
+lp_status lp_prebeam_set_groups(lp_prebeam* pb, const int32_t* group_of_station,
+                                const double* station_enu, const double* group_dir,
+                                void* stream);
+
+/* The group phase centres, host doubles [G][3] (the final stage's station
+ * positions).  LP_ERR_STATE before lp_prebeam_set_groups. */
+lp_status lp_prebeam_group_centres(lp_prebeam* pb, double* centre_enu);
+
+/* One block: x device [P][K][F][S][2] int8 or int16 (the plan's dtype, aligned
+ * to its complex sample), y device [P][K][F][G][2] int16 (4-byte aligned, the
+ * caller's), scale > 0.  Asynchronous on `stream`; y must not overlap x. */
+lp_status lp_prebeam_run(lp_prebeam* pb, const void* x, void* y, float scale, void* stream);
+
+/* Synchronises the last stream used and returns, in *n, how many int16 values
+ * saturated since the previous call (then resets the count). */
+lp_status lp_prebeam_saturated(lp_prebeam* pb, int64_t* n);
+
+const char* lp_prebeam_last_error(const lp_prebeam* pb);
+void lp_prebeam_destroy(lp_prebeam* pb);
+
 #ifdef __cplusplus
 }
 #endif

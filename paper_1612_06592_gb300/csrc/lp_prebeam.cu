@@ -1,0 +1,398 @@
+// Preliminary beams of station groups: the first stage of two-stage
+// beamforming (Sec. 4, network paragraph).  Only a few 16-bit station streams
+// fit through the link to the processing cluster, so disjoint groups of
+// stations are first combined, each into one preliminary beam toward its own
+// direction s_g, phased to the group's phase centre r_g (the mean position of
+// its stations); the preliminary beams travel as complex int16 like station
+// data and the final beams are formed from them by the ordinary pipeline with
+// the group centres as station positions.
+//
+//     pb[p][k][m][g] = sum_{s in g} w1[k][s] x[p][k][m][s],
+//     w1[k][s] = exp(-2 pi i nu_k ((r_s - r_g) . s_g) / c),
+//     y = round half to even (scale * pb), saturated to [-32767, 32767].
+//
+// k_prebeam: one 4-warp block per (pol, subband, 256 frames), two frames per
+// thread.  The tile's samples are read once from HBM (contiguous [frame][S])
+// into shared memory station-major, so that a thread reads both of its frames
+// of one station in one access; the group sums run over the stations of each
+// group in turn (member list sorted by group) with FP32 FMAs; the int16 codes
+// are gathered in shared memory and written back as one contiguous
+// [frame][group] range of the output.  HBM-bound: 2 S (int8) or 4 S (int16)
+// bytes in and 4 G bytes out per frame, 8 S FLOP.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+struct lp_prebeam {
+  int S = 0, P = 0, K = 0, G = 0, first_bin = 0, input_dtype = 0;
+  long long F = 0;
+  int device = -1;
+  int E = 0;                            // stations in some group
+  void* mem = nullptr;                  // one device allocation, carved below
+  float2* w1 = nullptr;                 // [K][E] weights in member order
+  int* member = nullptr;                // [E] station of member e (sorted by group)
+  int* goff = nullptr;                  // [G + 1] first member of each group
+  double* rel = nullptr;                // [E][3] r_s - r_g
+  double* mdir = nullptr;               // [E][3] direction of the member's group
+  unsigned long long* n_sat = nullptr;  // saturated int16 codes since the last read
+  std::vector<double> centres;          // [G][3]
+  bool groups_set = false;
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+};
+
+namespace lp {
+namespace {
+
+constexpr int PB_NTH = 128;          // threads per block, two frames each
+constexpr int PB_FT = 2 * PB_NTH;    // frames per block
+constexpr int PB_FTP = PB_FT + 2;    // padded station row of the sample tile
+constexpr int PB_YP = PB_FT + 1;     // padded group row of the output tile
+
+template <typename T2> struct PbPair;
+template <> struct PbPair<char2> { using T = char4; };
+template <> struct PbPair<short2> { using T = short4; };
+
+// int16 transport code of scale * v: round half to even, saturate to +-32767
+__device__ __forceinline__ short pb_code(float v, float scale, int& sat) {
+  int q = __float2int_rn(v * scale);
+  if (q > 32767) {
+    q = 32767;
+    sat += 1;
+  } else if (q < -32767) {
+    q = -32767;
+    sat += 1;
+  }
+  return (short)q;
+}
+
+template <typename T2>
+__global__ void __launch_bounds__(PB_NTH) k_prebeam(
+    const T2* __restrict__ x, const float2* __restrict__ w1, const int* __restrict__ member,
+    const int* __restrict__ goff, int S, int K, int G, int E, long long F, float scale,
+    short2* __restrict__ y, unsigned long long* __restrict__ n_sat) {
+  using T4 = typename PbPair<T2>::T;
+  extern __shared__ float2 pb_smem[];
+  float2* ws = pb_smem;                                        // [E]
+  T2* xs = reinterpret_cast<T2*>(ws + E);                      // [S][PB_FTP]
+  short2* ys = reinterpret_cast<short2*>(xs + (size_t)S * PB_FTP);   // [G][PB_YP]
+  int* ms = reinterpret_cast<int*>(ys + (size_t)G * PB_YP);   // [E]
+  int* go = ms + E;                                            // [G + 1]
+
+  const int tile = blockIdx.x, k = blockIdx.y, pol = blockIdx.z;
+  const int tid = threadIdx.x;
+  const long long f0 = (long long)tile * PB_FT;
+  const int nvalid = (int)min((long long)PB_FT, F - f0);
+  for (int e = tid; e < E; e += PB_NTH) {
+    ws[e] = w1[(long long)k * E + e];
+    ms[e] = member[e];
+  }
+  for (int g = tid; g <= G; g += PB_NTH) go[g] = goff[g];
+  // samples of this (pol, k) and frame tile -> xs[s][frame]; frames past the
+  // block end read as zero
+  const T2* xk = x + ((long long)pol * K + k) * F * S + f0 * S;
+  for (int e = tid; e < PB_FT * S; e += PB_NTH) {
+    const int fr = e / S, st = e - fr * S;
+    T2 v;
+    v.x = 0;
+    v.y = 0;
+    if (fr < nvalid) v = xk[e];
+    xs[st * PB_FTP + fr] = v;
+  }
+  __syncthreads();
+
+  const int fl = 2 * tid;                                      // my frames fl, fl + 1
+  int sat = 0;
+  for (int g = 0; g < G; ++g) {
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+    const int e1 = go[g + 1];
+    for (int e = go[g]; e < e1; ++e) {
+      const float2 w = ws[e];
+      const T4 q = *reinterpret_cast<const T4*>(xs + ms[e] * PB_FTP + fl);
+      // (w.x + i w.y) (q.x + i q.y), frame fl;  (q.z + i q.w), frame fl + 1
+      a0.x = fmaf(w.x, (float)q.x, fmaf(-w.y, (float)q.y, a0.x));
+      a0.y = fmaf(w.x, (float)q.y, fmaf(w.y, (float)q.x, a0.y));
+      a1.x = fmaf(w.x, (float)q.z, fmaf(-w.y, (float)q.w, a1.x));
+      a1.y = fmaf(w.x, (float)q.w, fmaf(w.y, (float)q.z, a1.y));
+    }
+    short2 c0, c1;
+    c0.x = pb_code(a0.x, scale, sat);
+    c0.y = pb_code(a0.y, scale, sat);
+    c1.x = pb_code(a1.x, scale, sat);
+    c1.y = pb_code(a1.y, scale, sat);
+    ys[g * PB_YP + fl] = c0;
+    ys[g * PB_YP + fl + 1] = c1;
+  }
+  // saturations past the block end do not occur: those frames are zero
+  const int wsat = __reduce_add_sync(0xffffffffu, sat);
+  if ((tid & 31) == 0 && wsat) atomicAdd(n_sat, (unsigned long long)wsat);
+  __syncthreads();
+  // [frame][group] codes of the valid frames: one contiguous output range
+  short2* yk = y + (((long long)pol * K + k) * F + f0) * G;
+  for (int e = tid; e < nvalid * G; e += PB_NTH) {
+    const int fr = e / G, g = e - fr * G;
+    yk[e] = ys[g * PB_YP + fr];
+  }
+}
+
+// w1[k][e] = exp(-2 pi i nu_k ((r_s - r_g) . s_g) / c): the argument in FP64
+// cycles, reduced to [-1/2, 1/2] before the FP32 sincospif
+__global__ void k_prebeam_weights(const double* __restrict__ rel, const double* __restrict__ dir,
+                                  int K, int E, int first_bin, float2* __restrict__ w1) {
+  const long long total = (long long)K * E;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(i % E);
+    const int k = (int)(i / E);
+    const double nu = kNu0 + (double)(first_bin + k) * (kFs / kM);
+    const double dot = rel[3 * e] * dir[3 * e] + rel[3 * e + 1] * dir[3 * e + 1] +
+                       rel[3 * e + 2] * dir[3 * e + 2];
+    const double cyc = nu * dot / kC;
+    const double r = cyc - rint(cyc);
+    float sn, cs;
+    sincospif(2.0f * (float)r, &sn, &cs);
+    w1[i] = make_float2(cs, -sn);
+  }
+}
+
+size_t prebeam_smem(const lp_prebeam& pb) {
+  const size_t t2 = pb.input_dtype == LP_INPUT_INT8 ? sizeof(char2) : sizeof(short2);
+  return sizeof(float2) * pb.E + t2 * (size_t)pb.S * PB_FTP +
+         sizeof(short2) * (size_t)pb.G * PB_YP + sizeof(int) * (size_t)(pb.E + pb.G + 1);
+}
+
+lp_status pb_fail(lp_prebeam* pb, lp_status st, const char* fmt, ...) {
+  if (pb) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    pb->err = buf;
+  }
+  return st;
+}
+
+#define PB_CUDA(pb, call)                                                            \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return pb_fail(pb, LP_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                     __FILE__, __LINE__);                                            \
+  } while (0)
+
+lp_status pb_set_device(lp_prebeam* pb) {
+  int cur = -1;
+  PB_CUDA(pb, cudaGetDevice(&cur));
+  if (cur != pb->device) PB_CUDA(pb, cudaSetDevice(pb->device));
+  return LP_OK;
+}
+
+lp_status pb_device_pointer(lp_prebeam* pb, const void* ptr, const char* what) {
+  cudaPointerAttributes attr;
+  PB_CUDA(pb, cudaPointerGetAttributes(&attr, ptr));
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return pb_fail(pb, LP_ERR_ARG, "%s is not device memory", what);
+  if (attr.device != pb->device)
+    return pb_fail(pb, LP_ERR_ARG, "%s lives on device %d, the groups on %d", what, attr.device,
+                   pb->device);
+  return LP_OK;
+}
+
+}  // namespace
+}  // namespace lp
+
+extern "C" {
+
+lp_status lp_prebeam_create(lp_prebeam** out, int stations, int pols, int subbands,
+                            int64_t block_len, int groups, int first_bin, int input_dtype) {
+  if (!out) return LP_ERR_ARG;
+  *out = nullptr;
+  if (stations < 1 || stations > 4096 || (pols != 1 && pols != 2) || subbands < 1 ||
+      block_len < 1 || groups < 1 || groups > stations || groups > 4096)
+    return LP_ERR_ARG;
+  if (first_bin < 1 || first_bin + subbands > lp::kBins) return LP_ERR_ARG;
+  if (input_dtype != LP_INPUT_INT8 && input_dtype != LP_INPUT_INT16) return LP_ERR_ARG;
+  lp_prebeam* pb = new (std::nothrow) lp_prebeam;
+  if (!pb) return LP_ERR_OOM;
+  pb->S = stations;
+  pb->P = pols;
+  pb->K = subbands;
+  pb->F = block_len;
+  pb->G = groups;
+  pb->first_bin = first_bin;
+  pb->input_dtype = input_dtype;
+  *out = pb;
+  return LP_OK;
+}
+
+lp_status lp_prebeam_set_groups(lp_prebeam* pb, const int32_t* group_of_station,
+                                const double* station_enu, const double* group_dir,
+                                void* stream) {
+  using namespace lp;
+  if (!pb) return LP_ERR_ARG;
+  if (!group_of_station || !station_enu || !group_dir)
+    return pb_fail(pb, LP_ERR_ARG, "null group table, positions or directions");
+  const int S = pb->S, G = pb->G;
+  std::vector<int> count(G, 0);
+  for (int s = 0; s < S; ++s) {
+    const int g = group_of_station[s];
+    if (g < -1 || g >= G) return pb_fail(pb, LP_ERR_ARG, "station %d: group %d not in [-1, %d)", s, g, G);
+    if (g >= 0) count[g] += 1;
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(station_enu[3 * s + c]))
+        return pb_fail(pb, LP_ERR_ARG, "station %d position not finite", s);
+  }
+  for (int g = 0; g < G; ++g) {
+    if (!count[g]) return pb_fail(pb, LP_ERR_ARG, "group %d has no station", g);
+    const double* d = group_dir + 3 * g;
+    const double n2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(std::fabs(n2 - 1.0) < 1e-6))
+      return pb_fail(pb, LP_ERR_ARG, "direction of group %d is not a unit vector", g);
+  }
+  // phase centres (member means) and the member list sorted by group
+  std::vector<double> centres(3 * (size_t)G, 0.0);
+  for (int s = 0; s < S; ++s) {
+    const int g = group_of_station[s];
+    if (g < 0) continue;
+    for (int c = 0; c < 3; ++c) centres[3 * g + c] += station_enu[3 * s + c];
+  }
+  for (int g = 0; g < G; ++g)
+    for (int c = 0; c < 3; ++c) centres[3 * g + c] /= count[g];
+  std::vector<int> member, goff(G + 1, 0);
+  std::vector<double> rel, mdir;
+  for (int g = 0; g < G; ++g) {
+    goff[g] = (int)member.size();
+    for (int s = 0; s < S; ++s) {
+      if (group_of_station[s] != g) continue;
+      member.push_back(s);
+      for (int c = 0; c < 3; ++c) {
+        rel.push_back(station_enu[3 * s + c] - centres[3 * g + c]);
+        mdir.push_back(group_dir[3 * g + c]);
+      }
+    }
+  }
+  goff[G] = (int)member.size();
+  const int E = goff[G];
+
+  if (!pb->mem) {
+    PB_CUDA(pb, cudaGetDevice(&pb->device));
+    // sized for every station in a group, so later calls never reallocate
+    const size_t bytes = sizeof(float2) * (size_t)pb->K * S + sizeof(int) * (S + G + 1) +
+                         2 * sizeof(double) * 3 * (size_t)S + sizeof(unsigned long long) + 6 * 256;
+    PB_CUDA(pb, cudaMalloc(&pb->mem, bytes));
+    char* base = static_cast<char*>(pb->mem);
+    size_t off = 0;
+    auto take = [&](size_t n) {
+      off = (off + 255) / 256 * 256;
+      char* p = base + off;
+      off += n;
+      return p;
+    };
+    pb->w1 = (float2*)take(sizeof(float2) * (size_t)pb->K * S);
+    pb->rel = (double*)take(sizeof(double) * 3 * (size_t)S);
+    pb->mdir = (double*)take(sizeof(double) * 3 * (size_t)S);
+    pb->member = (int*)take(sizeof(int) * S);
+    pb->goff = (int*)take(sizeof(int) * (G + 1));
+    pb->n_sat = (unsigned long long*)take(sizeof(unsigned long long));
+    PB_CUDA(pb, cudaMemset(pb->n_sat, 0, sizeof(unsigned long long)));
+  } else if (pb_set_device(pb) != LP_OK) {
+    return LP_ERR_CUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  pb->E = E;
+  // pageable host memory: the copies are complete for the host on return
+  PB_CUDA(pb, cudaMemcpyAsync(pb->member, member.data(), sizeof(int) * E, cudaMemcpyHostToDevice, s));
+  PB_CUDA(pb, cudaMemcpyAsync(pb->goff, goff.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, s));
+  PB_CUDA(pb, cudaMemcpyAsync(pb->rel, rel.data(), sizeof(double) * 3 * E, cudaMemcpyHostToDevice, s));
+  PB_CUDA(pb, cudaMemcpyAsync(pb->mdir, mdir.data(), sizeof(double) * 3 * E, cudaMemcpyHostToDevice, s));
+  const long long total = (long long)pb->K * E;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  k_prebeam_weights<<<blocks, 256, 0, s>>>(pb->rel, pb->mdir, pb->K, E, pb->first_bin, pb->w1);
+  PB_CUDA(pb, cudaGetLastError());
+  const int smem = (int)prebeam_smem(*pb);
+  if (smem > 227 * 1024) return pb_fail(pb, LP_ERR_ARG, "too many stations for one tile");
+  if (pb->input_dtype == LP_INPUT_INT8)
+    PB_CUDA(pb, cudaFuncSetAttribute(k_prebeam<char2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  else
+    PB_CUDA(pb, cudaFuncSetAttribute(k_prebeam<short2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  pb->centres = centres;
+  pb->last_stream = s;
+  pb->groups_set = true;
+  return LP_OK;
+}
+
+lp_status lp_prebeam_group_centres(lp_prebeam* pb, double* centre_enu) {
+  if (!pb || !centre_enu) return LP_ERR_ARG;
+  if (!pb->groups_set) return lp::pb_fail(pb, LP_ERR_STATE, "lp_prebeam_set_groups first");
+  for (size_t i = 0; i < pb->centres.size(); ++i) centre_enu[i] = pb->centres[i];
+  return LP_OK;
+}
+
+lp_status lp_prebeam_run(lp_prebeam* pb, const void* x, void* y, float scale, void* stream) {
+  using namespace lp;
+  if (!pb) return LP_ERR_ARG;
+  if (!pb->groups_set) return pb_fail(pb, LP_ERR_STATE, "lp_prebeam_set_groups first");
+  if (!x || !y) return pb_fail(pb, LP_ERR_ARG, "null input or output");
+  if (!(scale > 0.f) || !std::isfinite(scale))
+    return pb_fail(pb, LP_ERR_ARG, "scale must be positive and finite");
+  if (pb_set_device(pb) != LP_OK) return LP_ERR_CUDA;
+  if (lp_status st = pb_device_pointer(pb, x, "input")) return st;
+  if (lp_status st = pb_device_pointer(pb, y, "output")) return st;
+  const size_t t2 = pb->input_dtype == LP_INPUT_INT8 ? 2 : 4;
+  if (reinterpret_cast<uintptr_t>(x) % t2 || reinterpret_cast<uintptr_t>(y) % 4)
+    return pb_fail(pb, LP_ERR_ARG, "input must be %zu-byte and output 4-byte aligned", t2);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const dim3 grid((unsigned)((pb->F + PB_FT - 1) / PB_FT), pb->K, pb->P);
+  const size_t smem = prebeam_smem(*pb);
+  if (pb->input_dtype == LP_INPUT_INT8)
+    k_prebeam<char2><<<grid, PB_NTH, smem, s>>>(static_cast<const char2*>(x), pb->w1, pb->member,
+                                                pb->goff, pb->S, pb->K, pb->G, pb->E, pb->F,
+                                                scale, static_cast<short2*>(y), pb->n_sat);
+  else
+    k_prebeam<short2><<<grid, PB_NTH, smem, s>>>(static_cast<const short2*>(x), pb->w1,
+                                                 pb->member, pb->goff, pb->S, pb->K, pb->G,
+                                                 pb->E, pb->F, scale, static_cast<short2*>(y),
+                                                 pb->n_sat);
+  PB_CUDA(pb, cudaGetLastError());
+  pb->last_stream = s;
+  return LP_OK;
+}
+
+lp_status lp_prebeam_saturated(lp_prebeam* pb, int64_t* n) {
+  using namespace lp;
+  if (!pb || !n) return LP_ERR_ARG;
+  *n = 0;
+  if (!pb->mem) return LP_OK;
+  if (pb_set_device(pb) != LP_OK) return LP_ERR_CUDA;
+  PB_CUDA(pb, cudaStreamSynchronize(pb->last_stream));
+  unsigned long long v = 0;
+  PB_CUDA(pb, cudaMemcpy(&v, pb->n_sat, sizeof v, cudaMemcpyDeviceToHost));
+  PB_CUDA(pb, cudaMemset(pb->n_sat, 0, sizeof v));
+  *n = (int64_t)v;
+  return LP_OK;
+}
+
+const char* lp_prebeam_last_error(const lp_prebeam* pb) {
+  return pb ? pb->err.c_str() : "null preliminary-beam plan";
+}
+
+void lp_prebeam_destroy(lp_prebeam* pb) {
+  if (!pb) return;
+  if (pb->mem) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != pb->device) cudaSetDevice(pb->device);
+    cudaFree(pb->mem);
+    if (cur >= 0 && cur != pb->device) cudaSetDevice(cur);
+  }
+  delete pb;
+}
+
+}  // extern "C"

@@ -89,6 +89,15 @@ SIGNATURES = {
         ctypes.POINTER(lp_config), _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P,
         ctypes.c_char_p, ctypes.c_size_t]),
     "lp_plan_destroy": (None, [_P]),
+    "lp_prebeam_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int]),
+    "lp_prebeam_set_groups": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "lp_prebeam_group_centres": (ctypes.c_int, [_P, _P]),
+    "lp_prebeam_run": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P]),
+    "lp_prebeam_saturated": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lp_prebeam_last_error": (ctypes.c_char_p, [_P]),
+    "lp_prebeam_destroy": (None, [_P]),
     "lp_last_error": (ctypes.c_char_p, [_P]),
     "lp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -318,6 +327,67 @@ class Plan:
             _lib.lp_plan_destroy(self._h)
             self._h = _P()
             self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Prebeam:
+    """Preliminary beams of station groups (the first stage of two-stage
+    beamforming): station block [P, K, F, S, 2] int8/int16 on the device ->
+    int16 [P, K, F, G, 2], the input of a Plan with stations = G."""
+
+    def __init__(self, stations, pols, subbands, block_len, groups, *, first_bin=12,
+                 input_dtype="int8"):
+        self.shape = (stations, pols, subbands, block_len, groups)
+        self._h = _P()
+        dt = LP_INPUT_INT8 if input_dtype == "int8" else LP_INPUT_INT16
+        st = _lib.lp_prebeam_create(ctypes.byref(self._h), stations, pols, subbands, block_len,
+                                    groups, first_bin, dt)
+        if st != LP_OK:
+            raise LPError(st, "lp_prebeam_create: shape out of range")
+
+    def _check(self, st, what):
+        if st != LP_OK:
+            msg = _lib.lp_prebeam_last_error(self._h).decode() if self._h else ""
+            raise LPError(st, f"{what}: {msg}")
+
+    def lp_prebeam_set_groups(self, group_of_station, station_enu, group_dir, stream=None):
+        S, G = self.shape[0], self.shape[4]
+        grp = np.ascontiguousarray(group_of_station, dtype=np.int32)
+        enu = np.ascontiguousarray(station_enu, dtype=np.float64)
+        gd = np.ascontiguousarray(group_dir, dtype=np.float64)
+        if grp.shape != (S,) or enu.shape != (S, 3) or gd.shape != (G, 3):
+            raise ValueError("group_of_station must be [S], station_enu [S,3], group_dir [G,3]")
+        self._check(_lib.lp_prebeam_set_groups(self._h, grp.ctypes.data, enu.ctypes.data,
+                                               gd.ctypes.data, _stream_ptr(stream)),
+                    "lp_prebeam_set_groups")
+
+    def lp_prebeam_group_centres(self):
+        out = np.zeros((self.shape[4], 3), dtype=np.float64)
+        self._check(_lib.lp_prebeam_group_centres(self._h, out.ctypes.data),
+                    "lp_prebeam_group_centres")
+        return out
+
+    def lp_prebeam_run(self, x, y, scale, stream=None):
+        S, P, K, F, G = self.shape
+        if tuple(x.shape) != (P, K, F, S, 2) or tuple(y.shape) != (P, K, F, G, 2):
+            raise ValueError(f"x must be {(P, K, F, S, 2)} and y {(P, K, F, G, 2)}")
+        self._check(_lib.lp_prebeam_run(self._h, _ptr(x), _ptr(y), float(scale),
+                                        _stream_ptr(stream)), "lp_prebeam_run")
+
+    def lp_prebeam_saturated(self):
+        n = ctypes.c_int64()
+        self._check(_lib.lp_prebeam_saturated(self._h, ctypes.byref(n)), "lp_prebeam_saturated")
+        return n.value
+
+    def close(self):
+        if self._h:
+            _lib.lp_prebeam_destroy(self._h)
+            self._h = _P()
 
     def __del__(self):
         try:

@@ -109,3 +109,32 @@ def test_serving_requests_and_workspace_sizes(lib):
     big = workspace_bytes(48, 2, 488, 50, 4, 65536, 12)
     # the beam intermediate (streams x subbands x (F + 16) complex floats) dominates
     assert big > 400 * 488 * 65552 * 8 > small
+
+
+def test_prebeam_validates_shape_and_groups_before_any_cuda_call(lib):
+    import numpy as np
+    c = lib._lib
+    h = ctypes.c_void_p()
+    for bad in [(0, 2, 16, 64, 1, 12, 1), (6, 3, 16, 64, 1, 12, 1), (6, 2, 0, 64, 1, 12, 1),
+                (6, 2, 16, 0, 1, 12, 1), (6, 2, 16, 64, 0, 12, 1), (6, 2, 16, 64, 7, 12, 1),
+                (6, 2, 16, 64, 2, 0, 1), (6, 2, 16, 64, 2, 500, 1), (6, 2, 16, 64, 2, 12, 3)]:
+        assert c.lp_prebeam_create(ctypes.byref(h), *bad) == lib.LP_ERR_ARG, bad
+        assert not h.value
+    assert c.lp_prebeam_create(ctypes.byref(h), 6, 2, 16, 64, 2, 12, 1) == lib.LP_OK and h.value
+    enu = np.zeros((6, 3))
+    dirs = np.array([[0.0, 0.0, 1.0], [0.0, 0.6, 0.8]])
+    for grp, d in [([0, 0, 0, 0, 0, 0], dirs),            # group 1 empty
+                   ([0, 1, 2, 0, 1, 0], dirs),            # group index out of range
+                   ([0, 1, -2, 0, 1, 0], dirs),
+                   ([0, 1, 0, 1, 0, 1], dirs * 1.01)]:    # not unit vectors
+        g = np.array(grp, dtype=np.int32)
+        dd = np.ascontiguousarray(d)
+        assert c.lp_prebeam_set_groups(h, g.ctypes.data, enu.ctypes.data, dd.ctypes.data,
+                                       None) == lib.LP_ERR_ARG
+        assert c.lp_prebeam_last_error(h)
+    out = np.zeros((2, 3))
+    assert c.lp_prebeam_group_centres(h, out.ctypes.data) == lib.LP_ERR_STATE
+    assert c.lp_prebeam_run(h, 16, 16, ctypes.c_float(1.0), None) == lib.LP_ERR_STATE
+    n = ctypes.c_int64(5)
+    assert c.lp_prebeam_saturated(h, ctypes.byref(n)) == lib.LP_OK and n.value == 0
+    c.lp_prebeam_destroy(h)
