@@ -45,13 +45,18 @@ SMS = 152
 FP32_LANES_PER_SM = 128
 
 
+def measured_peaks():
+    """The measured peaks file (copy bandwidth, bf16 GEMM, clocks), or {}."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
 def fp32_peak_tflops():
     """FP32 FMA peak from unit counts at the maximum SM clock (from the measured
     peaks file when it records one)."""
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        peaks = {}
+    peaks = measured_peaks()
     return SMS * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
 
 
@@ -67,7 +72,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--serve-blocks", type=int, default=32,
                     help="blocks of the realtime serving leg (p50/p99 latency); 0 skips it")
-    ap.add_argument("--workload", default="precision", choices=["precision", "stress"],
+    ap.add_argument("--workload", default="precision", choices=["precision", "stress", "two-stage"],
                     help="precision: the 48x488x50 headline block; stress: 200 beams x 8 "
                          "trials x 262144 frames with injected pulses (recall)")
     ap.add_argument("--synth-frames", type=int, default=0,
@@ -466,11 +471,12 @@ def run_stress(args):
     ms = ms_tot / steps
     block_s = w.block_len * M / FS_HZ
     # recall: a pulse counts when its beam has a trigger near the arrival time of
-    # some trial (the de-dispersed pulse sits at n0 + A_trial / nu_ref^2)
-    import oracle as O
-    nu = O.sky_frequencies(w.first_bin, w.subbands)
-    nu_ref = 0.5 * (nu[0] + nu[-1])
-    delay = O.dispersion_coefficient_hz(tec) / nu_ref ** 2 * FS_HZ
+    # some trial; the de-dispersed pulse sits at n0 + A_trial / nu_ref^2 (A =
+    # 40.308 m^3/s^2 * STEC / c, nu_ref the centre of the selected band)
+    nu_lo = FS_HZ / 2 + w.first_bin * FS_HZ / M
+    nu_hi = FS_HZ / 2 + (w.first_bin + w.subbands - 1) * FS_HZ / M
+    nu_ref = 0.5 * (nu_lo + nu_hi)
+    delay = 40.308 * np.asarray(tec) * 1e16 / 299792458.0 / nu_ref ** 2 * FS_HZ
     by_beam = {}
     for r in trig:
         by_beam.setdefault(int(r["beam"]), []).append((int(r["n"]), int(r["tec"])))
@@ -510,6 +516,94 @@ def run_stress(args):
         "triggers_not_near_a_pulse": int(len(trig) - sum(
             1 for r in trig if (int(r["beam"]), int(r["n"]), int(r["tec"])) in used)),
         "clocks": clk, "data": "synthetic (device noise + host-built dispersed pulses)",
+    }
+
+
+def run_two_stage(args):
+    """Two-stage beamforming at the precision configuration: the 48 stations in
+    8 compact groups form 8 int16 preliminary beams toward the pointing centre
+    (lp_prebeam), from which the 50 final beams, the synthesis and the triggers
+    follow (an lp_plan with the group centres as its 8 stations; FP32 form, the
+    form that takes int16).  One step = both stages on one block."""
+    import torch
+    from paper_1612_06592_gb300 import build
+    build()
+    from paper_1612_06592_gb300 import lp
+    w = bench_workload(args)
+    G, scale = 8, 4.0
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    enu, dirs, tec = synth.make_geometry(w)
+    x = device_block(w, 1000, dev)
+    grp = synth.station_groups(enu, G)
+    pb = lp.Prebeam(w.stations, w.pols, w.subbands, w.block_len, G, first_bin=w.first_bin,
+                    input_dtype=w.dtype)
+    pb.lp_prebeam_set_groups(grp, enu, np.tile(synth.pointing_enu(), (G, 1)))
+    y = torch.empty((w.pols, w.subbands, w.block_len, G, 2), dtype=torch.int16, device=dev)
+    plan = lp.Plan(G, w.pols, w.subbands, w.beams, len(tec), w.block_len, input_dtype="int16",
+                   precision="fp32", first_bin=w.first_bin)
+    plan.lp_set_weights(pb.lp_prebeam_group_centres(), dirs)
+    plan.lp_set_tec(tec)
+    stream = torch.cuda.current_stream()
+    pb.lp_prebeam_run(x, y, scale)
+    gemm_cfgs = plan.lp_plan_gemm_configs()
+    gemm_best, gemm_ms = plan.lp_plan_autotune_gemm(y)
+    tuned_fpc, tune_ms = plan.lp_plan_autotune(y)
+    for _ in range(max(3, args.warmup)):
+        pb.lp_prebeam_run(x, y, scale)
+        plan.lp_process_block(y)
+    torch.cuda.synchronize()
+    pb.lp_prebeam_saturated()
+    plan.lp_profile_enable(True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for a, b in ev:
+        a.record(stream)
+        pb.lp_prebeam_run(x, y, scale)
+        b.record(stream)
+        plan.lp_process_block(y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    pre_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    stages, nrec = plan.lp_profile_read()
+    n_sat = pb.lp_prebeam_saturated()
+    block_s = w.block_len * M / FS_HZ
+    in_bytes = x.numel() * x.element_size()
+    out_bytes = y.numel() * y.element_size()
+    hbm_peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    pre_gbs = (in_bytes + out_bytes) / (pre_ms / 1e3) / 1e9
+    return {
+        "metric": "realtime factor, two-stage beamforming (48 stations in 8 groups) x 488 "
+                  "subbands x 50 beams",
+        "value": block_s / (ms_step / 1e3), "unit": "x realtime", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (int16 preliminary beams)", "data": "synthetic (seeded rounded-Gaussian "
+        "int8 station noise)",
+        "config": dict(workload_config(w, "fp32"), workload="two-stage-48st-8grp-488sb-50bm-"
+                       f"{w.block_len}fr", groups=G, group_sizes=np.bincount(grp).tolist(),
+                       preliminary_direction="pointing centre", transport="complex int16",
+                       scale=scale, synth_frames_per_cta=tuned_fpc,
+                       gemm_config=gemm_desc("fp32", gemm_cfgs, gemm_best),
+                       gemm_autotune_ms={gemm_desc("fp32", gemm_cfgs, gemm_cfgs.index(k)):
+                                         round(v, 3) for k, v in gemm_ms.items()}),
+        "stage_ms": dict({"prebeam": pre_ms}, **{k: v / max(nrec, 1) for k, v in stages.items()
+                                                  if k != "h2d"}),
+        "roofline_prebeam": {"bound": "hbm", "kernel": "k_prebeam", "achieved": pre_gbs,
+                             "peak": hbm_peak, "unit": "GB/s", "frac": pre_gbs / hbm_peak,
+                             "bytes": in_bytes + out_bytes,
+                             "note": "station block read + int16 preliminary beams written"},
+        "saturated_codes_per_block": n_sat / args.steps,
+        "gpu_launches": args.steps * (1 + plan.lp_launches_per_block()),
+        "clocks": clk,
     }
 
 
@@ -555,6 +649,8 @@ def main():
         line = run_reference(args, rank, world)
     elif args.workload == "stress":
         line = run_stress(args) if rank == 0 else None
+    elif args.workload == "two-stage":
+        line = run_two_stage(args) if rank == 0 else None
     else:
         if world > 1:
             import torch

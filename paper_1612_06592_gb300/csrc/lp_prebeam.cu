@@ -12,10 +12,12 @@
 //     y = round half to even (scale * pb), saturated to [-32767, 32767].
 //
 // k_prebeam: one 4-warp block per (pol, subband, 256 frames), two frames per
-// thread.  The tile's samples are read once from HBM (contiguous [frame][S])
-// into shared memory station-major, so that a thread reads both of its frames
-// of one station in one access; the group sums run over the stations of each
-// group in turn (member list sorted by group) with FP32 FMAs; the int16 codes
+// thread.  The tile's samples are read once from HBM (contiguous [frame][S],
+// 16-byte chunks with several loads in flight per thread) into shared memory
+// station-major, so that a thread reads both of its frames of one station in
+// one access; the group sums run over the stations of each group in turn
+// (member list sorted by group, weight and tile offset in one broadcast
+// 16-byte load) with FP32 FMAs; the int16 codes
 // are gathered in shared memory and written back as one contiguous
 // [frame][group] range of the output.  HBM-bound: 2 S (int8) or 4 S (int16)
 // bytes in and 4 G bytes out per frame, 8 S FLOP.
@@ -60,51 +62,112 @@ template <> struct PbPair<char2> { using T = char4; };
 template <> struct PbPair<short2> { using T = short4; };
 
 // int16 transport code of scale * v: round half to even, saturate to +-32767
+// (|scale v| >= 32767.5 is exactly when the rounded value leaves the range)
 __device__ __forceinline__ short pb_code(float v, float scale, int& sat) {
-  int q = __float2int_rn(v * scale);
-  if (q > 32767) {
-    q = 32767;
-    sat += 1;
-  } else if (q < -32767) {
-    q = -32767;
-    sat += 1;
-  }
-  return (short)q;
+  const float s = v * scale;
+  sat += fabsf(s) >= 32767.5f ? 1 : 0;
+  return (short)__float2int_rn(fminf(fmaxf(s, -32767.f), 32767.f));
+}
+
+// One tile element (a station sample of one frame) into the station-major tile.
+template <typename T2>
+__device__ __forceinline__ void put_sample(T2* xs, int e, int S, T2 v) {
+  const int fr = e / S;
+  xs[(e - fr * S) * PB_FTP + fr] = v;
+}
+
+// Exact int8 / int16 -> FP32 without a conversion instruction: the sample plus
+// its bias (2^7 or 2^15) is placed in the low mantissa bits of 2^23, and 2^23
+// plus the bias is subtracted (all values involved are exact in FP32).
+struct Pair4f {
+  float a, b, c, d;   // elements 0..3 of a char4 / short4
+};
+__device__ __forceinline__ Pair4f to_f32(char4 q) {
+  const uint32_t u = *reinterpret_cast<const uint32_t*>(&q) ^ 0x80808080u;
+  constexpr float off = 8388608.0f + 128.0f;
+  return {__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7650)) - off,
+          __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7651)) - off,
+          __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7652)) - off,
+          __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7653)) - off};
+}
+__device__ __forceinline__ Pair4f to_f32(short4 q) {
+  const uint2 u2 = *reinterpret_cast<const uint2*>(&q);
+  const uint32_t lo = u2.x ^ 0x80008000u, hi = u2.y ^ 0x80008000u;
+  constexpr float off = 8388608.0f + 32768.0f;
+  return {__uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7610)) - off,
+          __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7632)) - off,
+          __uint_as_float(__byte_perm(hi, 0x4B000000u, 0x7610)) - off,
+          __uint_as_float(__byte_perm(hi, 0x4B000000u, 0x7632)) - off};
 }
 
 template <typename T2>
 __global__ void __launch_bounds__(PB_NTH) k_prebeam(
     const T2* __restrict__ x, const float2* __restrict__ w1, const int* __restrict__ member,
-    const int* __restrict__ goff, int S, int K, int G, int E, long long F, float scale,
+    const int* __restrict__ goff, int S, int K, int G, int E, long long F, float scale, int vec,
     short2* __restrict__ y, unsigned long long* __restrict__ n_sat) {
   using T4 = typename PbPair<T2>::T;
-  extern __shared__ float2 pb_smem[];
-  float2* ws = pb_smem;                                        // [E]
+  constexpr int PER = 16 / sizeof(T2);                         // samples per 16-byte chunk
+  extern __shared__ float4 pb_smem[];
+  float4* ws = pb_smem;                                        // [E] (w.re, w.im, tile offset, 0)
   T2* xs = reinterpret_cast<T2*>(ws + E);                      // [S][PB_FTP]
   short2* ys = reinterpret_cast<short2*>(xs + (size_t)S * PB_FTP);   // [G][PB_YP]
-  int* ms = reinterpret_cast<int*>(ys + (size_t)G * PB_YP);   // [E]
-  int* go = ms + E;                                            // [G + 1]
+  int* go = reinterpret_cast<int*>(ys + (size_t)G * PB_YP);   // [G + 1]
 
   const int tile = blockIdx.x, k = blockIdx.y, pol = blockIdx.z;
   const int tid = threadIdx.x;
   const long long f0 = (long long)tile * PB_FT;
   const int nvalid = (int)min((long long)PB_FT, F - f0);
   for (int e = tid; e < E; e += PB_NTH) {
-    ws[e] = w1[(long long)k * E + e];
-    ms[e] = member[e];
+    const float2 w = w1[(long long)k * E + e];
+    ws[e] = make_float4(w.x, w.y, __int_as_float(member[e] * PB_FTP), 0.f);
   }
   for (int g = tid; g <= G; g += PB_NTH) go[g] = goff[g];
-  // samples of this (pol, k) and frame tile -> xs[s][frame]; frames past the
-  // block end read as zero
-  const T2* xk = x + ((long long)pol * K + k) * F * S + f0 * S;
-  for (int e = tid; e < PB_FT * S; e += PB_NTH) {
-    const int fr = e / S, st = e - fr * S;
-    T2 v;
-    v.x = 0;
-    v.y = 0;
-    if (fr < nvalid) v = xk[e];
-    xs[st * PB_FTP + fr] = v;
+  // samples of this (pol, k) and frame tile -> xs[s][frame]: the tile is one
+  // contiguous range of nvalid * S samples; with vec (16-byte aligned slabs)
+  // it is read in 16-byte chunks, four loads in flight per thread before their
+  // samples are stored, and the ragged end sample by sample
+  const T2* xk = x + (((long long)pol * K + k) * F + f0) * S;
+  const int n_el = nvalid * S;
+  int done = 0;
+  if (vec) {
+    const int n_ch = n_el / PER;
+    const uint4* xc = reinterpret_cast<const uint4*>(xk);
+    // (frame, station) of the first sample of chunk c, kept for c = tid,
+    // tid + PB_NTH, ... by adding PB_NTH * PER samples with a carry
+    int fr_c = (tid * PER) / S, st_c = tid * PER - fr_c * S;
+    const int dq = (PB_NTH * PER) / S, dr = PB_NTH * PER - dq * S;
+    for (int c0 = tid; c0 < n_ch; c0 += 4 * PB_NTH) {
+      uint4 v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = c0 + i * PB_NTH;
+        if (c < n_ch) v[i] = __ldg(xc + c);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = c0 + i * PB_NTH;
+        if (c >= n_ch) break;
+        const T2* el = reinterpret_cast<const T2*>(&v[i]);
+        int fr = fr_c, st = st_c;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+          xs[st * PB_FTP + fr] = el[j];
+          if (++st == S) {
+            st = 0;
+            ++fr;
+          }
+        }
+        st_c += dr;
+        fr_c += dq;
+        if (st_c >= S) {
+          st_c -= S;
+          ++fr_c;
+        }
+      }
+    }
+    done = n_ch * PER;
   }
+  for (int e = done + tid; e < n_el; e += PB_NTH) put_sample(xs, e, S, xk[e]);
   __syncthreads();
 
   const int fl = 2 * tid;                                      // my frames fl, fl + 1
@@ -112,32 +175,45 @@ __global__ void __launch_bounds__(PB_NTH) k_prebeam(
   for (int g = 0; g < G; ++g) {
     float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
     const int e1 = go[g + 1];
+#pragma unroll 2
     for (int e = go[g]; e < e1; ++e) {
-      const float2 w = ws[e];
-      const T4 q = *reinterpret_cast<const T4*>(xs + ms[e] * PB_FTP + fl);
-      // (w.x + i w.y) (q.x + i q.y), frame fl;  (q.z + i q.w), frame fl + 1
-      a0.x = fmaf(w.x, (float)q.x, fmaf(-w.y, (float)q.y, a0.x));
-      a0.y = fmaf(w.x, (float)q.y, fmaf(w.y, (float)q.x, a0.y));
-      a1.x = fmaf(w.x, (float)q.z, fmaf(-w.y, (float)q.w, a1.x));
-      a1.y = fmaf(w.x, (float)q.w, fmaf(w.y, (float)q.z, a1.y));
+      const float4 w = ws[e];                                  // broadcast
+      const Pair4f q = to_f32(*reinterpret_cast<const T4*>(xs + __float_as_int(w.z) + fl));
+      // (w.x + i w.y) (q.a + i q.b), frame fl;  (q.c + i q.d), frame fl + 1
+      a0.x = fmaf(w.x, q.a, fmaf(-w.y, q.b, a0.x));
+      a0.y = fmaf(w.x, q.b, fmaf(w.y, q.a, a0.y));
+      a1.x = fmaf(w.x, q.c, fmaf(-w.y, q.d, a1.x));
+      a1.y = fmaf(w.x, q.d, fmaf(w.y, q.c, a1.y));
     }
+    // frames past the block end hold stale samples: their codes are never
+    // written and their saturations not counted
+    int s0 = 0, s1 = 0;
     short2 c0, c1;
-    c0.x = pb_code(a0.x, scale, sat);
-    c0.y = pb_code(a0.y, scale, sat);
-    c1.x = pb_code(a1.x, scale, sat);
-    c1.y = pb_code(a1.y, scale, sat);
+    c0.x = pb_code(a0.x, scale, s0);
+    c0.y = pb_code(a0.y, scale, s0);
+    c1.x = pb_code(a1.x, scale, s1);
+    c1.y = pb_code(a1.y, scale, s1);
+    sat += (fl < nvalid ? s0 : 0) + (fl + 1 < nvalid ? s1 : 0);
     ys[g * PB_YP + fl] = c0;
     ys[g * PB_YP + fl + 1] = c1;
   }
-  // saturations past the block end do not occur: those frames are zero
   const int wsat = __reduce_add_sync(0xffffffffu, sat);
   if ((tid & 31) == 0 && wsat) atomicAdd(n_sat, (unsigned long long)wsat);
   __syncthreads();
   // [frame][group] codes of the valid frames: one contiguous output range
   short2* yk = y + (((long long)pol * K + k) * F + f0) * G;
-  for (int e = tid; e < nvalid * G; e += PB_NTH) {
-    const int fr = e / G, g = e - fr * G;
-    yk[e] = ys[g * PB_YP + fr];
+  {
+    int fr = tid / G, g = tid - fr * G;                        // (frame, group) of e
+    const int dq = PB_NTH / G, dr = PB_NTH - dq * G;
+    for (int e = tid; e < nvalid * G; e += PB_NTH) {
+      yk[e] = ys[g * PB_YP + fr];
+      g += dr;
+      fr += dq;
+      if (g >= G) {
+        g -= G;
+        ++fr;
+      }
+    }
   }
 }
 
@@ -163,8 +239,8 @@ __global__ void k_prebeam_weights(const double* __restrict__ rel, const double* 
 
 size_t prebeam_smem(const lp_prebeam& pb) {
   const size_t t2 = pb.input_dtype == LP_INPUT_INT8 ? sizeof(char2) : sizeof(short2);
-  return sizeof(float2) * pb.E + t2 * (size_t)pb.S * PB_FTP +
-         sizeof(short2) * (size_t)pb.G * PB_YP + sizeof(int) * (size_t)(pb.E + pb.G + 1);
+  return sizeof(float4) * pb.E + t2 * (size_t)pb.S * PB_FTP +
+         sizeof(short2) * (size_t)pb.G * PB_YP + sizeof(int) * (size_t)(pb.G + 1);
 }
 
 lp_status pb_fail(lp_prebeam* pb, lp_status st, const char* fmt, ...) {
@@ -351,15 +427,18 @@ lp_status lp_prebeam_run(lp_prebeam* pb, const void* x, void* y, float scale, vo
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const dim3 grid((unsigned)((pb->F + PB_FT - 1) / PB_FT), pb->K, pb->P);
   const size_t smem = prebeam_smem(*pb);
+  // 16-byte chunk reads when every (pol, subband) slab starts 16-byte aligned
+  // (tiles then do too: 256 frames of S samples of 2 or 4 bytes)
+  const int vec = reinterpret_cast<uintptr_t>(x) % 16 == 0 && (pb->F * pb->S * t2) % 16 == 0;
   if (pb->input_dtype == LP_INPUT_INT8)
     k_prebeam<char2><<<grid, PB_NTH, smem, s>>>(static_cast<const char2*>(x), pb->w1, pb->member,
                                                 pb->goff, pb->S, pb->K, pb->G, pb->E, pb->F,
-                                                scale, static_cast<short2*>(y), pb->n_sat);
+                                                scale, vec, static_cast<short2*>(y), pb->n_sat);
   else
     k_prebeam<short2><<<grid, PB_NTH, smem, s>>>(static_cast<const short2*>(x), pb->w1,
                                                  pb->member, pb->goff, pb->S, pb->K, pb->G,
-                                                 pb->E, pb->F, scale, static_cast<short2*>(y),
-                                                 pb->n_sat);
+                                                 pb->E, pb->F, scale, vec,
+                                                 static_cast<short2*>(y), pb->n_sat);
   PB_CUDA(pb, cudaGetLastError());
   pb->last_stream = s;
   return LP_OK;

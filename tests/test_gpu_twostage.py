@@ -47,10 +47,13 @@ def _check_codes(got, want, v, window):
     return np.count_nonzero(diff)
 
 
-@pytest.mark.parametrize("dtype,amp,scale", [("int8", 128, 2.0), ("int16", 3000, 4.0)])
-def test_prebeam_matches_oracle(cuda_lib, dtype, amp, scale):
+@pytest.mark.parametrize("dtype,amp,scale,S", [("int8", 128, 2.0, 20), ("int16", 3000, 4.0, 20),
+                                                ("int8", 128, 2.0, 21)])
+def test_prebeam_matches_oracle(cuda_lib, dtype, amp, scale, S):
+    """20 stations: 16-byte chunk reads; 21 (int8): slabs not 16-byte aligned,
+    sample-by-sample reads."""
     import torch
-    S, P, K, F, G, fb = 20, 2, 6, 700, 5, 130          # 700 frames: two tiles + a ragged one
+    P, K, F, G, fb = 2, 6, 700, 5, 130                 # 700 frames: two tiles + a ragged one
     rng = np.random.default_rng(61)
     info = np.iinfo(dtype)
     x = rng.integers(max(info.min, -amp), min(info.max, amp) + 1,

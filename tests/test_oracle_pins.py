@@ -453,3 +453,19 @@ def test_constants_agree_with_paper_figures():
     assert abs(flops / g["value"] - 1) < g["rel_tol"]
     # one 2^26-sample block lasts 0.336 s, inside the 5 s budget
     assert n / O.FS_HZ < gold["realtime_budget_s"]["value"]
+
+
+def test_two_stage_gain_table_reproduces():
+    """The stored two-stage gain table is what the oracle gives (and the
+    pointing-centre beam keeps the full single-stage gain)."""
+    import importlib.util
+    path = os.path.join(GOLDEN, "two_stage_gain.py")
+    spec = importlib.util.spec_from_file_location("two_stage_gain", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    nu, offs, g, sizes = mod.gains()
+    ref = json.load(open(os.path.join(GOLDEN, "two_stage_gain.json")))
+    np.testing.assert_allclose(g, ref["power_gain"], atol=1e-5)
+    assert sizes == ref["group_sizes"]
+    assert np.all(g <= 1 + 1e-12)
+    np.testing.assert_allclose(g[:, np.argmin(offs)], 1.0, atol=1e-12)
