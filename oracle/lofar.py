@@ -30,6 +30,8 @@ __all__ = [
     "ippf", "parseval_power", "update_sigma2", "find_triggers",
     "Pipeline", "stream_window", "brute_force_stream",
     "INT16_MAX", "group_centres", "prebeam_weights", "prebeam", "transport_int16",
+    "FINE_TAPS", "FINE_DELAY", "FINE_BETA", "FINE_GRID", "fine_dedispersion_taps",
+    "fine_dedisperse",
 ]
 
 # Sec. 2: antennas are sampled every 5 ns  ->  fs = 200 MHz.
@@ -133,6 +135,80 @@ def beamform(x: np.ndarray, w: np.ndarray, d: np.ndarray) -> np.ndarray:
         acc += w[:, :, s].T[:, None, :, None] * x[None, :, :, :, s]
     out = acc[:, None, :, :, :] * d.T[None, :, None, :, None]
     assert out.shape == (B, Tr, P, K, F)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Fine-resolution de-dispersion in the channel domain (Sec. 3, third paragraph)
+# --------------------------------------------------------------------------
+#
+# The paper de-disperses by multiplying the spectrum at full resolution.  The
+# per-subband weight D[k, t] above applies that phase at each subband centre
+# only; what is left inside subband k is
+#     psi(nu_k + dnu) = phi(nu_k + dnu) - phi(nu_k)      [cycles],
+# mostly a delay A (1/nu_ref^2 - 1/nu_k^2) (a fraction of a frame) and a tiny
+# chirp.  A subband's frame series carries the band nu_k + dnu, |dnu| < dnu_sb/2,
+# at the frame rate (bin centres are whole cycles per frame), so the rest of
+# the phase is a filter along frames with frequency response
+#     R(f) = exp(-2 pi i (psi(f * dnu_sb) + f * FINE_DELAY)),  f in [-1/2, 1/2),
+# f the frame-rate frequency, dnu_sb = fs / M.  Readings: the taps are R's
+# inverse DTFT by the midpoint rule on FINE_GRID points, kept for q in
+# [0, FINE_TAPS), times a Kaiser window (beta FINE_BETA) centred on the
+# subband's first-order group delay c_k = FINE_DELAY + A dnu_sb (1/nu_ref^2 -
+# 1/nu_k^2) frames with the largest half-width that fits the taps on both
+# sides, min(c_k, FINE_TAPS - 1 - c_k) (a window or a support off that centre
+# pulls the delay toward its own centre); the extra common delay of
+# FINE_DELAY frames makes
+# the filter causal (a pulse appears FINE_DELAY * M samples later).  The noise
+# level stays the raw beams' (the filter passes power unchanged in band).
+
+FINE_TAPS = 17
+FINE_DELAY = 8
+FINE_BETA = 4.0
+FINE_GRID = 1024
+
+
+def fine_dedispersion_taps(nu_hz, tec_tecu, nu_ref_hz: float, taps: int = FINE_TAPS,
+                           delay: int = FINE_DELAY, beta: float = FINE_BETA,
+                           grid: int = FINE_GRID) -> np.ndarray:
+    """Channel-domain de-dispersion taps r[k, t, q], complex [K, Tr, taps]
+    (readings above): r[q] = w_k[q] (1/grid) sum_j R(f_j) exp(+2 pi i f_j q),
+    f_j = (j + 1/2)/grid - 1/2, psi = phi(nu_k + f dnu_sb) - phi(nu_k) from
+    ``dedispersion_cycles``."""
+    nu = np.asarray(nu_hz, dtype=np.float64)
+    tec = np.asarray(tec_tecu, dtype=np.float64)
+    f = (np.arange(grid) + 0.5) / grid - 0.5
+    dnu = f * (FS_HZ / M)
+    q = np.arange(taps)
+    basis = np.exp(2j * np.pi * np.outer(f, q)) / grid                 # [grid, taps]
+    a = dispersion_coefficient_hz(tec)                                   # [Tr]
+    out = np.zeros((nu.size, tec.size, taps), dtype=np.complex128)
+    for k in range(nu.size):
+        centre = dedispersion_cycles(nu[k:k + 1], tec, nu_ref_hz)[0]    # [Tr]
+        full = dedispersion_cycles(nu[k] + dnu, tec, nu_ref_hz)         # [grid, Tr]
+        resp = np.exp(-2j * np.pi * (full - centre[None, :] + f[:, None] * delay))
+        c = delay + a * (FS_HZ / M) * (1.0 / nu_ref_hz ** 2 - 1.0 / nu[k] ** 2)   # [Tr]
+        hw = np.minimum(c, taps - 1 - c)                                 # [Tr]
+        x = np.clip(1.0 - ((q[None, :] - c[:, None]) / hw[:, None]) ** 2, 0.0, None)
+        win = bessel_i0(beta * np.sqrt(x)) / bessel_i0(beta)             # [Tr, taps]
+        out[k] = (resp.T @ basis) * win
+    return out
+
+
+def fine_dedisperse(frames_ext: np.ndarray, r_k: np.ndarray) -> np.ndarray:
+    """One stream's channel-domain de-dispersion filter along frames.
+
+    frames_ext: complex [taps - 1 + F, K], the stream's beam frames (already
+    multiplied by D[k, t]) with the taps - 1 frames before the block first;
+    r_k: complex [K, taps], the taps of the stream's trial.  Returns [F, K]:
+        out[m, k] = sum_q r_k[k, q] frames_ext[taps - 1 + m - q, k].
+    """
+    frames_ext = np.asarray(frames_ext, dtype=np.complex128)
+    taps = r_k.shape[1]
+    F = frames_ext.shape[0] - (taps - 1)
+    out = np.zeros((F, frames_ext.shape[1]), dtype=np.complex128)
+    for q in range(taps):
+        out += r_k[None, :, q] * frames_ext[taps - 1 - q: taps - 1 - q + F]
     return out
 
 
@@ -406,9 +482,11 @@ class Pipeline:
     sigma_alpha: float = 0.25
     beta: float = 9.0
     keep_timeseries: bool = True
+    fine_dedispersion: bool = False
     # state
     block_index: int = 0
     history: np.ndarray | None = field(default=None, repr=False)
+    fine_history: np.ndarray | None = field(default=None, repr=False)
     sigma2: np.ndarray | None = None
 
     def __post_init__(self):
@@ -420,6 +498,9 @@ class Pipeline:
         self.g = synthesis_filter(M, TAPS, self.beta)
         J = self.beams * self.tec_trials * self.pols
         self.history = np.zeros((J, TAPS - 1, self.subbands), dtype=np.complex128)
+        if self.fine_dedispersion:
+            self.fine_taps = fine_dedispersion_taps(self.nu, np.asarray(self.tec), self.nu_ref_hz)
+            self.fine_history = np.zeros((J, FINE_TAPS - 1, self.subbands), dtype=np.complex128)
 
     @property
     def n_streams(self) -> int:
@@ -431,7 +512,8 @@ class Pipeline:
     def process_block(self, x):
         """x: station block [P, K, F, S, 2] integers (or complex [P, K, F, S]).
 
-        Returns dict with beams [J, F, K], sigma [J], theta [J], n_first,
+        Returns dict with beams [J, F, K] (after the fine de-dispersion filter
+        when it is on), sigma [J], theta [J], n_first,
         y/env [J, F*M] (if keep_timeseries) and triggers: list of
         (n, beam, tec, pol, env, sigma) sorted by (beam, tec, pol, n).
         """
@@ -444,6 +526,14 @@ class Pipeline:
         pi = parseval_power(frames, self.g)
         self.sigma2 = update_sigma2(self.sigma2, pi, self.sigma_alpha,
                                     self.block_index == 0)
+        if self.fine_dedispersion:
+            fine = np.empty_like(frames)
+            for j in range(J):
+                t = (j // self.pols) % self.tec_trials
+                fext = np.concatenate([self.fine_history[j], frames[j]], axis=0)
+                fine[j] = fine_dedisperse(fext, self.fine_taps[:, t, :])
+                self.fine_history[j] = fext[-(FINE_TAPS - 1):]
+            frames = fine
         sigma = np.sqrt(self.sigma2)
         theta = self.k_sigma * sigma
         n_first = (self.block_index * F - (TAPS - 1)) * M

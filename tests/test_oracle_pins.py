@@ -359,6 +359,126 @@ def test_dedispersion_at_true_tec_recovers_the_pulse():
     assert abs(peaks[tec][1] - (n0 + tau_ref * O.FS_HZ)) < 30
 
 
+# ------------------------------------------- fine de-dispersion -----------
+
+def test_fine_taps_at_zero_tec_are_a_pure_delay():
+    """TEC = 0: R(f) = exp(-2 pi i f delay), whose midpoint-rule inverse DTFT is
+    exactly the unit impulse at the delay (closed form)."""
+    nu = O.sky_frequencies(12, 488)
+    r = O.fine_dedispersion_taps(nu[::61], [0.0], nu.mean())
+    want = np.zeros(O.FINE_TAPS)
+    want[O.FINE_DELAY] = 1.0
+    np.testing.assert_allclose(r[:, 0, :], np.broadcast_to(want, r[:, 0, :].shape), atol=1e-13)
+
+
+def test_fine_residual_phase_against_40_digit_closed_form():
+    """psi = phi(nu_k + dnu) - phi(nu_k) = A dnu (1/nu_ref^2 - 1/((nu_k + dnu) nu_k))
+    (algebra on the factored phase), evaluated in 40 digits, against the
+    oracle's difference of de-dispersion phases."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    nu = O.sky_frequencies(12, 488)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    for ki in (0, 200, 487):
+        for dnu in (-97000.0, 31000.0, 97000.0):
+            got = (O.dedispersion_cycles(np.array([nu[ki] + dnu]), [40.0], nu_ref)
+                   - O.dedispersion_cycles(nu[ki:ki + 1], [40.0], nu_ref))[0, 0]
+            a = mpmath.mpf(O.KAPPA) * 40 * mpmath.mpf(O.TECU) / mpmath.mpf(O.C_LIGHT)
+            v, d, r = mpmath.mpf(nu[ki]), mpmath.mpf(dnu), mpmath.mpf(nu_ref)
+            ref = a * d * (1 / (r * r) - 1 / ((v + d) * v))
+            assert abs(float(ref) - got) < 1e-9
+
+
+@pytest.mark.parametrize("ki", [0, 243, 487])
+def test_fine_taps_delay_and_gain(ki):
+    """Response of the taps near f = 0: unit gain and group delay
+    FINE_DELAY + A dnu_sb (1/nu_ref^2 - 1/nu_k^2) frames (first-order closed form),
+    to 0.05 frame: a 17-tap windowed fractional delay is good to a few hundredths
+    of a frame, while a wrong sign of the delay misses by up to 1.07 frames and a
+    missing factor by ~0.5."""
+    nu = O.sky_frequencies(12, 488)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    tec = 40.0
+    r = O.fine_dedispersion_taps(nu[ki:ki + 1], [tec], nu_ref)[0, 0]
+    q = np.arange(O.FINE_TAPS)
+    h = lambda f: np.sum(r * np.exp(-2j * np.pi * f * q))
+    df = 1e-4
+    gd = -(np.angle(h(df) / h(-df))) / (2 * np.pi * 2 * df)
+    a = O.dispersion_coefficient_hz(tec)
+    want = O.FINE_DELAY + a * (O.FS_HZ / O.M) * (1 / nu_ref ** 2 - 1 / nu[ki] ** 2)
+    assert abs(gd - want) < 0.05
+    for f in (0.0, 0.1, 0.25, 0.4):
+        assert abs(abs(h(f)) - 1) < 0.01
+
+
+def test_fine_dedisperse_matches_brute_force():
+    rng = np.random.default_rng(21)
+    K, F = 5, 9
+    ext = rng.normal(size=(O.FINE_TAPS - 1 + F, K)) + 1j * rng.normal(size=(O.FINE_TAPS - 1 + F, K))
+    r = rng.normal(size=(K, O.FINE_TAPS)) + 1j * rng.normal(size=(K, O.FINE_TAPS))
+    got = O.fine_dedisperse(ext, r)
+    for m in range(F):
+        for k in range(K):
+            want = sum(r[k, q] * ext[O.FINE_TAPS - 1 + m - q, k] for q in range(O.FINE_TAPS))
+            assert abs(got[m, k] - want) < 1e-12
+
+
+def test_fine_dedispersion_recovers_at_least_the_subband_phase_result():
+    """A dispersed pulse, per-subband phase then the fine filter: the peak is at
+    the reference-frequency delay plus FINE_DELAY frames, and at 40 TECU over the
+    full band it beats the per-subband phase alone; with TEC = 0 the filter is a
+    pure delay that keeps the undispersed peak."""
+    for tec, fb, K, gain in ((40.0, 12, 488, 1.03), (25.0, 60, 192, 1.0)):
+        frames, n0 = _single_pulse_block(tec, first_bin=fb, K=K, F=120)
+        ref, _ = _single_pulse_block(0.0, first_bin=fb, K=K, F=120)
+        g = O.synthesis_filter()
+        nu = O.sky_frequencies(fb, K)
+        nu_ref = 0.5 * (nu[0] + nu[-1])
+        d = O.dedispersion_weights(nu, [tec], nu_ref)[:, 0]
+        ext = lambda f: np.concatenate([np.zeros((15, K)), f])
+        fext = lambda f: np.concatenate([np.zeros((O.FINE_TAPS - 1, K)), f])
+        r = O.fine_dedispersion_taps(nu, [tec, 0.0], nu_ref)
+        env_c = np.abs(O.ippf(ext(frames * d[None]), fb, g)).reshape(-1)
+        env_f = np.abs(O.ippf(ext(O.fine_dedisperse(fext(frames * d[None]), r[:, 0])),
+                              fb, g)).reshape(-1)
+        env_0 = np.abs(O.ippf(ext(ref), fb, g)).reshape(-1)
+        env_0f = np.abs(O.ippf(ext(O.fine_dedisperse(fext(ref), r[:, 1])), fb, g)).reshape(-1)
+        assert env_f.max() >= gain * env_c.max()
+        assert abs(env_0f.max() / env_0.max() - 1) < 1e-12
+        assert int(np.argmax(env_0f)) - int(np.argmax(env_0)) == O.FINE_DELAY * O.M
+        tau_ref = O.dispersion_coefficient_hz(tec) / nu_ref ** 2
+        n_peak = int(np.argmax(env_f)) - 15 * O.M
+        assert abs(n_peak - (n0 + tau_ref * O.FS_HZ + O.FINE_DELAY * O.M)) < 30
+
+
+def test_pipeline_fine_mode_equals_its_definition():
+    """Pipeline with the fine filter: two blocks equal the per-stream definition
+    (beamform, D, filter with zero history, synthesis) on the concatenated block."""
+    S, P, K, B, Tr, F, fb = 3, 2, 6, 2, 2, 40, 150
+    rng = np.random.default_rng(22)
+    x = rng.integers(-30, 31, size=(P, K, 2 * F, S, 2))
+    enu = synth.station_positions(S, 3)
+    dirs = synth.hex_beam_directions(B)
+    tec = np.array([8.0, 33.0])
+    pipe = O.Pipeline(S, P, K, B, Tr, F, fb, enu, dirs, tec, fine_dedispersion=True)
+    ys = [pipe.process_block(x[:, :, i * F:(i + 1) * F])["y"] for i in range(2)]
+    nu = O.sky_frequencies(fb, K)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    w = O.geometric_weights(nu, enu, dirs)
+    d = O.dedispersion_weights(nu, tec, nu_ref)
+    r = O.fine_dedispersion_taps(nu, tec, nu_ref)
+    g = O.synthesis_filter()
+    xc = x[..., 0] + 1j * x[..., 1]
+    bm = O.beamform(xc, w, d)                                 # [B, Tr, P, K, 2F]
+    for b, t, p in ((0, 0, 0), (1, 1, 1), (1, 0, 1)):
+        j = (b * Tr + t) * P + p
+        fr = bm[b, t, p].T                                    # [2F, K]
+        fine = O.fine_dedisperse(np.concatenate([np.zeros((O.FINE_TAPS - 1, K)), fr]), r[:, t])
+        u = O.ippf(np.concatenate([np.zeros((15, K)), fine]), fb, g).reshape(-1)
+        np.testing.assert_allclose(np.concatenate([ys[0][j], ys[1][j]]), u.real,
+                                   rtol=0, atol=1e-9 * np.abs(u).max())
+
+
 # ------------------------------------------------------- noise / trigger ---
 
 @pytest.fixture(scope="module")
