@@ -77,6 +77,9 @@ def parse():
                          "trials x 262144 frames with injected pulses (recall)")
     ap.add_argument("--synth-frames", type=int, default=0,
                     help="fixed synthesis frames per thread block (0: autotune)")
+    ap.add_argument("--fine", action="store_true",
+                    help="fine (channel-domain) de-dispersion filter on (a separate line, "
+                         "not the headline)")
     ap.add_argument("--gemm-config", type=int, default=-2,
                     help="fixed beamformer configuration index (-1: default; -2: autotune)")
     ap.add_argument("--frames", type=int, default=0,
@@ -276,7 +279,8 @@ def run_ours(args, rank, world, local_rank):
     x = device_block(w, 1000 + rank, dev)
     plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(w.tec_trials), w.block_len,
                    input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
-                   host_input=not args.no_e2e, frames_per_cta=args.synth_frames)
+                   host_input=not args.no_e2e, frames_per_cta=args.synth_frames,
+                   fine_dedisp=args.fine)
     plan.lp_set_weights(enu, dirs)
     plan.lp_set_tec(tec)
     stream = torch.cuda.current_stream()
@@ -384,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
         "samples_per_s": {"station_complex": w.pols * w.subbands * w.block_len * w.stations
                           * world / (ms_step / 1e3),
                           "output_200MHz": samples * world / (ms_step / 1e3)},
-        "stage_ms": {k: v / max(nrec, 1) for k, v in stages.items()},
+        "stage_ms": {k: v / max(nrec, 1) for k, v in stages.items() if k != "fine" or args.fine},
         "roofline": {"bound": "alu", "kernel": "k_ippf (inverse FFT + synthesis FIR + trigger)",
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
@@ -410,6 +414,18 @@ def run_ours(args, rank, world, local_rank):
                        "ms_per_step": t_e2e / args.steps * 1e3,
                        "path": "lp_process_block(pinned host block) + lp_get_triggers",
                        "stage_ms": {k: v / max(n_e2e, 1) for k, v in e2e_stages.items()}}
+    if args.fine:
+        fine_ms = stages["fine"] / max(nrec, 1)
+        fine_bytes = 2 * beams_bytes                      # beam rows read + filtered rows written
+        line["metric"] += ", fine de-dispersion on"
+        line["config"]["workload"] += "-fine"
+        line["config"]["fine_dedispersion"] = "17-tap channel-domain filter per (subband, trial)"
+        line["roofline_fine"] = {"bound": "hbm", "kernel": "k_fine",
+                                 "achieved": fine_bytes / (fine_ms / 1e3) / 1e9,
+                                 "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": fine_bytes / (fine_ms / 1e3) / 1e9 / hbm_peak,
+                                 "bytes": fine_bytes,
+                                 "traffic": recorded_traffic("k_fine.cu")}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, x, min(args.cpu_sample_frames, w.block_len))
     if args.serve_blocks > 0 and not args.frames:

@@ -87,7 +87,14 @@ typedef struct {
                                intermediate is sized for one chunk; a first beamformer
                                pass sums |beam|^2 over the whole block for the noise
                                level (the same sigma as unchunked) */
-  int32_t reserved;
+  int32_t fine_dedisp;      /* 1: after the per-subband STEC phase, filter each
+                               (subband, trial) along frames with the rest of the
+                               phase across the subband (Sec. 3, third paragraph,
+                               at channel resolution: 17 taps, delay within 4
+                               frames of centre, else lp_set_tec fails).  Pulses
+                               appear 8 frames (8192 samples) later; needs a second
+                               beam-row buffer; not with chunk_frames; lp_get_beams
+                               returns the rows before the filter.  0: off */
 } lp_config;
 
 /* One trigger: envelope sample above k_sigma * sigma of its stream. */
@@ -225,17 +232,19 @@ lp_status lp_plan_autotune_gemm(lp_plan* plan, const void* x, void* stream, int3
                                 double* ms_out);
 
 /* Number of kernel launches lp_process_block makes for a device block (for
- * accounting); a host block processed per polarisation makes 8. */
+ * accounting: 4, or 5 with fine_dedisp); a host block processed per
+ * polarisation makes twice that. */
 int lp_launches_per_block(const lp_plan* plan);
 
 /* Stage timing.  When enabled, lp_process_block records a CUDA event pair
  * around each stage on the stream it launches on (the host-to-device copy,
- * the beamformer, the noise level, the synthesis, the history shift), for up
+ * the beamformer, the noise level, the synthesis, the history shift, the fine
+ * de-dispersion filter), for up
  * to 256 blocks.  lp_profile_read synchronises, adds the durations of every
  * recorded block into total_ms[LP_NUM_STAGES] (milliseconds), stores their
  * number in *blocks and forgets them. */
 enum { LP_STAGE_H2D = 0, LP_STAGE_BEAMFORM = 1, LP_STAGE_SIGMA = 2, LP_STAGE_SYNTH = 3,
-       LP_STAGE_SHIFT = 4, LP_NUM_STAGES = 5 };
+       LP_STAGE_SHIFT = 4, LP_STAGE_FINE = 5, LP_NUM_STAGES = 6 };
 lp_status lp_profile_enable(lp_plan* plan, int enable);
 lp_status lp_profile_read(lp_plan* plan, double* total_ms, int64_t* blocks);
 

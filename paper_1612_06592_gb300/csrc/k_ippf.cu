@@ -628,9 +628,12 @@ __global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, i
 
 // Carry the last 16 frames of every (stream, bin) row into the row prefix and
 // advance the device block counter.
-__global__ void k_history_shift(float2* __restrict__ beams, long long rows, int K, long long F,
-                                long long row, long long* __restrict__ blk, int advance, int P,
-                                int pol0, int npol) {
+// The last 16 frames of each row become the next block's prefix, in the beam
+// rows and (fine de-dispersion) in the filtered rows.
+__global__ void k_history_shift(float2* __restrict__ beams, float2* __restrict__ fine,
+                                long long rows, int K, long long F, long long row,
+                                long long* __restrict__ blk, int advance, int P, int pol0,
+                                int npol) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i == 0 && advance) *blk += 1;
   if (i >= rows * kPrefix) return;
@@ -638,6 +641,7 @@ __global__ void k_history_shift(float2* __restrict__ beams, long long rows, int 
   const int f = (int)(i % kPrefix);
   const long long r = sel_stream(rr / K, P, pol0, npol) * K + rr % K;
   beams[r * row + f] = beams[r * row + F + f];
+  if (fine) fine[r * row + f] = fine[r * row + F + f];
 }
 
 size_t ippf_smem_bytes() {
@@ -668,7 +672,7 @@ cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel
   const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)(sh.J() / sh.P * npol));
   const TrigOut tout{p.buf.trig, p.buf.trig_count, (long long)p.cfg.trigger_cap, sh.P, sh.Tr,
                      ps.pol0, npol};
-  k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(p.buf.beams, sh.K, p.cfg.first_bin, c.nf, p.row(), fpc,
+  k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(synth_rows(p), sh.K, p.cfg.first_bin, c.nf, p.row(), fpc,
                                              p.buf.g, p.buf.tw1024, p.buf.theta, p.buf.theta2,
                                              (float)p.cfg.k_sigma, p.buf.blk, sh.F, c.f_base,
                                              p.buf.y, tout);
@@ -691,7 +695,7 @@ cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t 
   const long long rows = (long long)sh.J() / sh.P * npol * sh.K;
   const long long n = rows * kPrefix;
   const bool advance = c.last && ps.pol0 + npol == sh.P;
-  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, rows, sh.K, c.nf,
+  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, p.buf.beams_fine, rows, sh.K, c.nf,
                                                               p.row(), p.buf.blk, advance ? 1 : 0,
                                                               sh.P, ps.pol0, npol);
   return cudaGetLastError();

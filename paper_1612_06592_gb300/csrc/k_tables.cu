@@ -19,18 +19,6 @@
 namespace lp {
 namespace {
 
-__device__ double bessel_i0_series(double x) {
-  // I0(x) = sum_k ((x/2)^k / k!)^2, summed until the terms vanish.
-  const double q = 0.25 * x * x;
-  double term = 1.0, sum = 1.0;
-  for (int k = 1; k < 200; ++k) {
-    term *= q / ((double)k * (double)k);
-    sum += term;
-    if (term <= 1e-18 * sum) break;
-  }
-  return sum;
-}
-
 // One block of 1024 threads builds the whole 16384-tap filter deterministically.
 __global__ void __launch_bounds__(1024) k_prototype(double beta, double* __restrict__ proto,
                                                     double* __restrict__ sums,

@@ -59,6 +59,10 @@ size_t carve(lp_plan& p, char* base) {
   b.tw1024 = (float4*)take(sizeof(float4) * kM);
   b.filter_sums = (double*)take(sizeof(double) * 2);
   b.beams = (float2*)take(sizeof(float2) * (size_t)J * sh.K * p.row());
+  const bool fine = p.cfg.fine_dedisp != 0;
+  b.beams_fine = fine ? (float2*)take(sizeof(float2) * (size_t)J * sh.K * p.row()) : nullptr;
+  b.fine_taps = fine ? (float4*)take(sizeof(float4) * (size_t)sh.K * sh.Tr * lp::kFineTaps)
+                     : nullptr;
   b.power_part = (float*)take(sizeof(float) * (size_t)J * sh.K * p.n_ftiles_bf);
   b.sigma2 = (double*)take(sizeof(double) * J);
   b.theta = (float*)take(sizeof(float) * J);
@@ -184,6 +188,10 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
     return fail(p, LP_ERR_ARG, "trigger_cap out of range");
   if (c->frames_per_cta != 0 && (c->frames_per_cta < 8 || c->frames_per_cta % 8 != 0))
     return fail(p, LP_ERR_ARG, "frames_per_cta must be 0 or a positive multiple of 8");
+  if (c->fine_dedisp != 0 && c->fine_dedisp != 1)
+    return fail(p, LP_ERR_ARG, "fine_dedisp must be 0 or 1");
+  if (c->fine_dedisp && c->chunk_frames != 0)
+    return fail(p, LP_ERR_ARG, "fine_dedisp does not combine with chunk_frames");
   if (c->chunk_frames != 0) {
     if (c->precision != LP_PREC_FP16)
       return fail(p, LP_ERR_ARG, "chunk_frames needs the FP16 form");
@@ -274,10 +282,24 @@ lp_status lp_set_tec(lp_plan* p, const double* tec, void* stream) {
   for (int t = 0; t < sh.Tr; ++t)
     if (!std::isfinite(tec[t]) || std::fabs(tec[t]) > 1e4)
       return fail(p, LP_ERR_ARG, "tec[%d] out of range", t);
+  if (p->cfg.fine_dedisp) {
+    // the fine filter's taps hold subband delays within 4 frames of its centre
+    const double dnu_sb = lp::kFs / kM;
+    for (int t = 0; t < sh.Tr; ++t)
+      for (int k : {0, sh.K - 1}) {
+        const double nu = lp::kNu0 + (p->cfg.first_bin + k) * dnu_sb;
+        const double a = lp::kKappa * tec[t] * lp::kTecu / lp::kC;
+        const double d = a * dnu_sb * (1.0 / (p->nu_ref * p->nu_ref) - 1.0 / (nu * nu));
+        if (std::fabs(d) > 4.0)
+          return fail(p, LP_ERR_ARG, "tec[%d]: subband delay %.2f frames exceeds the fine "
+                      "filter's 4-frame range", t, d);
+      }
+  }
   if (set_device(p) != LP_OK) return LP_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LP_CUDA(p, cudaMemcpyAsync(p->buf.tec, tec, sizeof(double) * sh.Tr, cudaMemcpyHostToDevice, s));
   LP_CUDA(p, lp::launch_dedisp(*p, s));
+  if (p->cfg.fine_dedisp) LP_CUDA(p, lp::launch_fine_taps(*p, s));
   p->last_stream = s;
   p->tec_set = true;
   return LP_OK;
@@ -488,6 +510,11 @@ lp_status process_host_pipelined(lp_plan* p, const void* x, int64_t pol_stride, 
     prof_mark(p, LP_STAGE_SIGMA, 0, s, pol);
     if (e == cudaSuccess) e = lp::launch_sigma(*p, s, ps);
     prof_mark(p, LP_STAGE_SIGMA, 1, s, pol);
+    if (p->cfg.fine_dedisp) {
+      prof_mark(p, LP_STAGE_FINE, 0, s, pol);
+      if (e == cudaSuccess) e = lp::launch_fine(*p, s, ps);
+      prof_mark(p, LP_STAGE_FINE, 1, s, pol);
+    }
     prof_mark(p, LP_STAGE_SYNTH, 0, s, pol);
     if (e == cudaSuccess) e = lp::launch_ippf(*p, c, s, ps);
     prof_mark(p, LP_STAGE_SYNTH, 1, s, pol);
@@ -567,6 +594,11 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, T
       prof_mark(p, LP_STAGE_SIGMA, 0, s);
       if (e == cudaSuccess) e = lp::launch_sigma(*p, s);
       prof_mark(p, LP_STAGE_SIGMA, 1, s);
+      if (p->cfg.fine_dedisp) {
+        prof_mark(p, LP_STAGE_FINE, 0, s);
+        if (e == cudaSuccess) e = lp::launch_fine(*p, s);
+        prof_mark(p, LP_STAGE_FINE, 1, s);
+      }
       prof_mark(p, LP_STAGE_SYNTH, 0, s);
       if (e == cudaSuccess)
         e = tune == kTuneSynth ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
@@ -702,6 +734,9 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
   const auto& sh = p->shape;
   LP_CUDA(p, cudaMemsetAsync(p->buf.beams, 0,
                              sizeof(float2) * (size_t)sh.J() * sh.K * p->row(), s));
+  if (p->buf.beams_fine)
+    LP_CUDA(p, cudaMemsetAsync(p->buf.beams_fine, 0,
+                               sizeof(float2) * (size_t)sh.J() * sh.K * p->row(), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.sigma2, 0, sizeof(double) * sh.J(), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.blk, 0, sizeof(long long), s));
@@ -711,8 +746,9 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
 }
 
 int lp_launches_per_block(const lp_plan* p) {
-  // beamformer, sigma, synthesis, history shift; chunked: power pass + sigma + 3 per chunk
-  if (!p || p->fc == 0 || p->fc == p->shape.F) return 4;
+  // beamformer, sigma, (fine filter,) synthesis, history shift; chunked: power
+  // pass + sigma + 3 per chunk
+  if (!p || p->fc == 0 || p->fc == p->shape.F) return p && p->cfg.fine_dedisp ? 5 : 4;
   return 2 + 3 * (int)(p->shape.F / p->fc);
 }
 

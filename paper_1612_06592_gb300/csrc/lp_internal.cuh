@@ -22,6 +22,27 @@ constexpr double kC = 299792458.0;
 constexpr double kKappa = 40.308;     // e^2 / (8 pi^2 eps0 m_e), m^3 s^-2
 constexpr double kTecu = 1e16;
 
+// Channel-domain fine de-dispersion (Sec. 3, third paragraph): taps along
+// frames per (subband, STEC trial), common delay in frames, Kaiser beta of the
+// taps' window, frequency points of the taps' inverse DTFT.
+constexpr int kFineTaps = 17;
+constexpr int kFineDelay = 8;
+constexpr double kFineBeta = 4.0;
+constexpr int kFineGrid = 1024;
+static_assert(kFineTaps - 1 <= kPrefix, "the filter's history must fit the row prefix");
+
+// I0(x) = sum_k ((x/2)^k / k!)^2, summed until the terms vanish (Kaiser windows).
+__device__ inline double bessel_i0_series(double x) {
+  const double q = 0.25 * x * x;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 200; ++k) {
+    term *= q / ((double)k * (double)k);
+    sum += term;
+    if (term <= 1e-18 * sum) break;
+  }
+  return sum;
+}
+
 // Device trigger record; same layout as lp_trigger.
 struct TriggerRec {
   long long n;
@@ -43,6 +64,8 @@ struct Buffers {
   float4* tw1024;          // [32 p1][32 l] exp(+2 pi i p1 l / 1024) as (c, c, s, s)
   double* filter_sums;     // [2]: sum h, sum h^2 of the unnormalised prototype
   float2* beams;           // [J][K][row], row = F + 16, frame m at m + 16
+  float2* beams_fine;      // same layout, after the fine de-dispersion filter, or null
+  float4* fine_taps;       // [K][Tr][kFineTaps] (r.re, r.re, -r.im, r.im), or null
   float* power_part;       // [J][K][n_ftiles] partial sums of |beam|^2
   double* sigma2;          // [J]
   float* theta;            // [J] k_sigma * sigma
@@ -144,6 +167,12 @@ cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel
 // advances the device block counter when c.last and ps covers the last pol
 cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s,
                                  PolSel ps = {});
+// fine de-dispersion: the taps (from the STEC values) and the filter of the
+// block's beam rows into the second row buffer
+cudaError_t launch_fine_taps(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_fine(const lp_plan& p, cudaStream_t s, PolSel ps = {});
+// the rows the synthesis reads: the filtered ones when fine de-dispersion is on
+inline const float2* synth_rows(const lp_plan& p);
 
 // Opt-in shared-memory limits of the kernels (per device; call with it current).
 cudaError_t init_kernel_attributes(const Shape& sh);
@@ -159,3 +188,7 @@ size_t beamform_tc_weight_bytes(const Shape& sh);
 int ippf_default_frames_per_cta(const Shape& sh);
 
 }  // namespace lp
+
+inline const float2* lp::synth_rows(const lp_plan& p) {
+  return p.buf.beams_fine ? p.buf.beams_fine : p.buf.beams;
+}

@@ -39,7 +39,7 @@ class lp_config(ctypes.Structure):
         ("frames_per_cta", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
         ("chunk_frames", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("fine_dedisp", ctypes.c_int32),
     ]
 
 
@@ -162,8 +162,8 @@ class Plan:
                  input_dtype="int8", precision="fp32", first_bin=12, k_sigma=6.0,
                  sigma_alpha=0.25, nu_ref_hz=0.0, trigger_cap=1 << 20,
                  store_timeseries=False, host_input=False, frames_per_cta=0,
-                 kaiser_beta=9.0, use_graph=False, chunk_frames=0, stream=None,
-                 workspace=None):
+                 kaiser_beta=9.0, use_graph=False, chunk_frames=0, fine_dedisp=False,
+                 stream=None, workspace=None):
         import torch
         self.shape = (stations, pols, subbands, beams, tec_trials, block_len)
         self._h = _P()
@@ -183,6 +183,7 @@ class Plan:
         c.kaiser_beta = kaiser_beta
         c.use_graph = int(bool(use_graph))
         c.chunk_frames = int(chunk_frames)
+        c.fine_dedisp = int(bool(fine_dedisp))
         self.config = c
         self._check(_lib.lp_plan_configure(self._h, ctypes.byref(c)), "lp_plan_configure")
         nbytes = ctypes.c_size_t()
@@ -310,7 +311,7 @@ class Plan:
         cfgs = self.lp_plan_gemm_configs()
         return best.value, {c: m for c, m in zip(cfgs, ms.tolist()) if m > 0}
 
-    STAGES = ("h2d", "beamform", "sigma", "synth", "shift")
+    STAGES = ("h2d", "beamform", "sigma", "synth", "shift", "fine")
 
     def lp_profile_enable(self, enable=True):
         self._check(_lib.lp_profile_enable(self._h, int(bool(enable))), "lp_profile_enable")
