@@ -13,13 +13,16 @@
 // 16 frames before it, which the beam rows hold in their prefix.
 //
 // k_fine_taps: one warp per (subband, trial); FP64 arguments and sums.
-// k_fine: one 4-warp block per (stream, subband, 1024 frames); the frames (and
-// the 16 before them) are staged in shared memory in rows of 8 frames padded to
+// k_fine: one 4-warp block per (stream, subband, 1024 frames) (the index
+// arithmetic of a block is four 32-bit divisions); the frames (and the 16
+// before them) are copied by cp.async, all at once, into shared memory in rows of 8 frames padded to
 // 20 words, so that both the 16-byte stores and each thread's 16-byte reads of
 // three consecutive rows are conflict-free; a thread filters 8 consecutive
 // frames from a 24-frame window in registers, two packed FFMA2 per tap and
 // frame with the taps as (r.re, r.re, -r.im, r.im).  HBM-bound: 8 bytes in and
 // 8 out per bin-frame, 136 FLOP.
+#include <algorithm>
+
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -80,27 +83,39 @@ __global__ void __launch_bounds__(128) k_fine_taps(const double* __restrict__ te
 
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// grid: x = frame tile, y = launch row (stream jj, bin k) - row0; 32-bit index
+// arithmetic (rows < 2^32), the stream map only when it is not the identity
 __global__ void __launch_bounds__(FN_NTH) k_fine(const float2* __restrict__ beams,
                                                  float2* __restrict__ out,
-                                                 const float4* __restrict__ taps, int K, int Tr,
-                                                 int P, long long F, long long row, int pol0,
-                                                 int npol, long long n_tiles) {
+                                                 const float4* __restrict__ taps, unsigned K,
+                                                 unsigned Tr, unsigned P, long long F,
+                                                 long long row, unsigned pol0, unsigned npol,
+                                                 unsigned row0) {
   __shared__ __align__(16) float tile[FN_ROWS * FN_ROWW];
   __shared__ float4 tp[kFineTaps];
-  const long long b = blockIdx.x;
-  const long long rr = b / n_tiles, ti = b - rr * n_tiles;   // launch row (stream jj, bin k), tile
-  const int k = (int)(rr % K);
-  const long long j = sel_stream(rr / K, P, pol0, npol);
-  const int t = (int)((j / P) % Tr);
-  const long long m0 = ti * FN_FT;
+  const unsigned rr = row0 + blockIdx.y;
+  const unsigned jj = rr / K, k = rr - jj * K;
+  const unsigned j = npol == P ? jj : (jj / npol) * P + pol0 + jj % npol;
+  const unsigned t = (j / P) % Tr;
+  const long long m0 = (long long)blockIdx.x * FN_FT;
   const int nval = (int)min((long long)FN_FT, F - m0);       // a multiple of 8
-  const long long base = (j * K + k) * row + kPrefix + m0;   // frame m0 of the row
-  // frames [m0 - 16, m0 + nval) as 16-byte pairs (rows and prefix are even)
+  const long long base = ((long long)j * K + k) * row + kPrefix + m0;   // frame m0 of the row
+  // frames [m0 - 16, m0 + nval) as 16-byte pairs (rows and prefix are even),
+  // all copies in flight at once
   const float4* src = reinterpret_cast<const float4*>(beams + base - kPrefix);
   for (int i = threadIdx.x; i < (nval + kPrefix) / 2; i += FN_NTH)
-    *reinterpret_cast<float4*>(&tile[(i >> 2) * FN_ROWW + (i & 3) * 4]) = src[i];
+    cp_async16(&tile[(i >> 2) * FN_ROWW + (i & 3) * 4], src + i);
   if (threadIdx.x < kFineTaps)
-    tp[threadIdx.x] = taps[((long long)k * Tr + t) * kFineTaps + threadIdx.x];
+    cp_async16(&tp[threadIdx.x], taps + ((long long)k * Tr + t) * kFineTaps + threadIdx.x);
+  cp_async_wait_all();
   __syncthreads();
   const int m = threadIdx.x * FN_FPT;                        // my first frame in the tile
   if (m >= nval) return;
@@ -148,11 +163,13 @@ cudaError_t launch_fine_taps(const lp_plan& p, cudaStream_t s) {
 cudaError_t launch_fine(const lp_plan& p, cudaStream_t s, PolSel ps) {
   const auto& sh = p.shape;
   const int npol = ps.npol ? ps.npol : sh.P;
-  const long long n_tiles = (sh.F + FN_FT - 1) / FN_FT;
+  const unsigned n_tiles = (unsigned)((sh.F + FN_FT - 1) / FN_FT);
   const long long rows = (long long)sh.J() / sh.P * npol * sh.K;
-  k_fine<<<(unsigned)(rows * n_tiles), FN_NTH, 0, s>>>(p.buf.beams, p.buf.beams_fine,
-                                                      p.buf.fine_taps, sh.K, sh.Tr, sh.P, sh.F,
-                                                      p.row(), ps.pol0, npol, n_tiles);
+  for (long long r0 = 0; r0 < rows; r0 += 65535) {            // grid y is at most 65535
+    const dim3 grid(n_tiles, (unsigned)std::min<long long>(65535, rows - r0));
+    k_fine<<<grid, FN_NTH, 0, s>>>(p.buf.beams, p.buf.beams_fine, p.buf.fine_taps, sh.K, sh.Tr,
+                                   sh.P, sh.F, p.row(), ps.pol0, npol, (unsigned)r0);
+  }
   return cudaGetLastError();
 }
 

@@ -746,9 +746,12 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
 }
 
 int lp_launches_per_block(const lp_plan* p) {
-  // beamformer, sigma, (fine filter,) synthesis, history shift; chunked: power
-  // pass + sigma + 3 per chunk
-  if (!p || p->fc == 0 || p->fc == p->shape.F) return p && p->cfg.fine_dedisp ? 5 : 4;
+  // beamformer, sigma, (fine filter: one launch per 65535 rows,) synthesis,
+  // history shift; chunked: power pass + sigma + 3 per chunk
+  if (!p) return 4;
+  const long long rows = (long long)p->shape.J() * p->shape.K;
+  const int fine = p->cfg.fine_dedisp ? (int)((rows + 65534) / 65535) : 0;
+  if (p->fc == 0 || p->fc == p->shape.F) return 4 + fine;
   return 2 + 3 * (int)(p->shape.F / p->fc);
 }
 
