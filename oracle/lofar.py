@@ -27,7 +27,8 @@ __all__ = [
     "sky_frequencies", "geometric_weights", "dispersion_coefficient_hz",
     "dedispersion_cycles", "dedispersion_weights", "beamform",
     "bessel_i0", "prototype_filter", "synthesis_filter", "fft_radix2",
-    "ippf", "parseval_power", "update_sigma2", "find_triggers",
+    "windowed_sums", "ippf", "parseval_power", "update_sigma2", "find_triggers",
+    "LSMR_ITERS", "LSMR_WINDOW", "LSMR_OVERLAP", "lsmr", "lsmr_phase_taps", "lsmr_invert",
     "Pipeline", "stream_window", "brute_force_stream",
     "INT16_MAX", "group_centres", "prebeam_weights", "prebeam", "transport_int16",
     "FINE_TAPS", "FINE_DELAY", "FINE_BETA", "FINE_GRID", "fine_dedispersion_taps",
@@ -376,6 +377,21 @@ def fft_radix2(x, sign: int) -> np.ndarray:
 # Inverse polyphase filter bank (Sec. 2 and Sec. 3 second paragraph)
 # --------------------------------------------------------------------------
 
+def windowed_sums(frames: np.ndarray, first_bin: int) -> np.ndarray:
+    """The inverse-FFT step of the PPF inversion (Sec. 3, second paragraph),
+    complex [..., n, M] from subband frames [..., n, K]: per frame, 2 * beam in
+    the selected bins (all other bins, DC and Nyquist zero), 1024-point inverse
+    DFT with 1/M:  z_m[p] = (1/M) sum_k 2 c_m[k] exp(+2 pi i k p / M).  Its real
+    part is the PPF branch signal of frame m, the imaginary part its Hilbert pair."""
+    frames = np.asarray(frames, dtype=np.complex128)
+    K = frames.shape[-1]
+    if first_bin < 1 or first_bin + K > NBINS:
+        raise ValueError("selected bins must avoid DC and Nyquist")
+    c = np.zeros(frames.shape[:-1] + (M,), dtype=np.complex128)
+    c[..., first_bin:first_bin + K] = 2.0 * frames
+    return fft_radix2(c, +1) / M
+
+
 def ippf(frames_ext: np.ndarray, first_bin: int, g: np.ndarray) -> np.ndarray:
     """Synthesis of the 200 MHz analytic time series from subband frames.
 
@@ -391,20 +407,136 @@ def ippf(frames_ext: np.ndarray, first_bin: int, g: np.ndarray) -> np.ndarray:
         u_m[p] = sum_{t=0}^{15} g[t M + p] * z_{m-t}[p].
     """
     frames_ext = np.asarray(frames_ext, dtype=np.complex128)
-    nfr, K = frames_ext.shape[-2], frames_ext.shape[-1]
+    nfr = frames_ext.shape[-2]
     taps = g.shape[0] // M
     F = nfr - (taps - 1)
     if F < 0:
         raise ValueError("need at least taps-1 history frames")
-    if first_bin < 1 or first_bin + K > NBINS:
-        raise ValueError("selected bins must avoid DC and Nyquist")
-    c = np.zeros(frames_ext.shape[:-1] + (M,), dtype=np.complex128)
-    c[..., first_bin:first_bin + K] = 2.0 * frames_ext
-    z = fft_radix2(c, +1) / M
+    z = windowed_sums(frames_ext, first_bin)
     u = np.zeros(frames_ext.shape[:-2] + (F, M), dtype=np.complex128)
     for t in range(taps):
         u += g[t * M:(t + 1) * M] * z[..., taps - 1 - t:taps - 1 - t + F, :]
     return u
+
+
+# --------------------------------------------------------------------------
+# PPF inversion by LSMR (Sec. 3, second paragraph)
+# --------------------------------------------------------------------------
+#
+# The paper inverts the filter bank by the inverse FFT (``windowed_sums``) and
+# then solves the sparse system H x = y with about 25 LSMR iterations.  H is the
+# PPF's window: y_m[p] = sum_{t<16} h[t M + p] x[(m - 15 + t) M + p], so it
+# splits into one banded Toeplitz system per phase p along the frames, with
+# taps a_p[t] = h[t M + p] (the prototype, sum h = 1).  Readings:
+#   * the analytic series is solved for (y = the complex windowed sums), one
+#     system per stream and phase;
+#   * a block is solved window by window: window w takes the equations of
+#     frames [wW - 16, wW + W) (W = LSMR_WINDOW; the 16 frames before the block
+#     are the previous block's) over the unknowns x_p[q], q in [wW - 31, wW + W),
+#     and keeps q in [wW - 16, wW + W - 16): the unknowns all 16 of whose
+#     equations lie in the window.  Windows tile q in [-16, F - 16): the output
+#     of a block lags its frames by 16 frames (sample n = (m - 16) M + p);
+#   * LSMR_ITERS iterations from x = 0, no damping (Fong and Saunders 2011).
+
+LSMR_ITERS = 25
+LSMR_WINDOW = 256
+LSMR_OVERLAP = 16
+
+
+def lsmr(matvec, rmatvec, b: np.ndarray, n: int, iters: int) -> np.ndarray:
+    """LSMR for min ||A x - b|| (Fong and Saunders 2011, their Algorithm 1 in
+    its order and notation): Golub-Kahan bidiagonalisation started from b,
+    two plane rotations per step, iters steps from x = 0, no damping.
+    matvec(v) = A v, rmatvec(u) = A^H u."""
+    b = np.asarray(b, dtype=np.complex128)
+    beta = np.linalg.norm(b)
+    if beta == 0.0:
+        return np.zeros(n, dtype=np.complex128)
+    u = b / beta
+    v = rmatvec(u)
+    alpha = np.linalg.norm(v)
+    if alpha == 0.0:
+        return np.zeros(n, dtype=np.complex128)
+    v = v / alpha
+    alphabar, zetabar = alpha, alpha * beta
+    rho, rhobar, cbar, sbar = 1.0, 1.0, 1.0, 0.0
+    h = v.copy()
+    hbar = np.zeros(n, dtype=np.complex128)
+    x = np.zeros(n, dtype=np.complex128)
+    for _ in range(iters):
+        # continue the bidiagonalisation
+        u = matvec(v) - alpha * u
+        beta = np.linalg.norm(u)
+        if beta > 0:
+            u = u / beta
+        v = rmatvec(u) - beta * v
+        alpha = np.linalg.norm(v)
+        if alpha > 0:
+            v = v / alpha
+        # rotation P_k
+        rho_old = rho
+        rho = math.hypot(alphabar, beta)
+        c, s = alphabar / rho, beta / rho
+        theta = s * alpha
+        alphabar = c * alpha
+        # rotation Pbar_k
+        rhobar_old = rhobar
+        thetabar = sbar * rho
+        rhobar = math.hypot(cbar * rho, theta)
+        cbar, sbar = cbar * rho / rhobar, theta / rhobar
+        zeta = cbar * zetabar
+        zetabar = -sbar * zetabar
+        # update h, hbar, x
+        hbar = h - (thetabar * rho / (rho_old * rhobar_old)) * hbar
+        x = x + (zeta / (rho * rhobar)) * hbar
+        h = v - (theta / rho) * h
+    return x
+
+
+def lsmr_phase_taps(h: np.ndarray) -> np.ndarray:
+    """a[p, t] = h[t M + p], the window taps of each phase, [M, taps]."""
+    taps = h.shape[0] // M
+    return np.asarray(h, dtype=np.float64).reshape(taps, M).T.copy()
+
+
+def lsmr_invert(frames_ext: np.ndarray, first_bin: int, h: np.ndarray,
+                iters: int = LSMR_ITERS, window: int = LSMR_WINDOW) -> np.ndarray:
+    """PPF inversion of one stream's block by windowed LSMR (readings above).
+
+    frames_ext: complex [16 + F, K], the 16 frames before the block first
+    (zero before the stream start); F a multiple of ``window``.  Returns the
+    analytic series x [F, M]: row i is x[(i - 16) M + p] relative to the block's
+    first frame, i.e. sample n = (m - 16) M + p of the stream for frame m.
+    """
+    ov = LSMR_OVERLAP
+    nfr = frames_ext.shape[0]
+    F = nfr - ov
+    if F % window:
+        raise ValueError("block length must be a multiple of the window")
+    z = windowed_sums(frames_ext, first_bin)                  # [16 + F, M]
+    a = lsmr_phase_taps(h)                                    # [M, 16]
+    taps = a.shape[1]
+    rows = window + ov                                        # equations per window
+    cols = rows + taps - 1                                    # unknowns per window
+    out = np.zeros((F, M), dtype=np.complex128)
+    for w0 in range(0, F, window):
+        for p in range(M):
+            ap = a[p]
+
+            def matvec(x, ap=ap):
+                return sum(ap[t] * x[t:t + rows] for t in range(taps))
+
+            def rmatvec(u, ap=ap):
+                r = np.zeros(cols, dtype=np.complex128)
+                for t in range(taps):
+                    r[t:t + rows] += ap[t] * u
+                return r
+
+            # equation e is frame w0 - 16 + e (row w0 + e of z); unknown j is
+            # q = w0 - 31 + j; the kept q in [w0 - 16, w0 + W - 16) are j in [15, 15 + W)
+            x = lsmr(matvec, rmatvec, z[w0:w0 + rows, p], cols, iters)
+            out[w0:w0 + window, p] = x[taps - 1:taps - 1 + window]
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -479,6 +479,98 @@ def test_pipeline_fine_mode_equals_its_definition():
                                    rtol=0, atol=1e-9 * np.abs(u).max())
 
 
+# ------------------------------------------------ LSMR PPF inversion -------
+
+@pytest.mark.parametrize("iters", [1, 3, 25])
+def test_lsmr_matches_library(iters):
+    """The oracle's LSMR (written from the algorithm) equals scipy's on a
+    random complex problem, iteration count for iteration count."""
+    from scipy.sparse.linalg import LinearOperator, lsmr as lib_lsmr
+    rng = np.random.default_rng(iters)
+    A = rng.normal(size=(40, 30)) + 1j * rng.normal(size=(40, 30))
+    b = rng.normal(size=40) + 1j * rng.normal(size=40)
+    got = O.lsmr(lambda v: A @ v, lambda u: A.conj().T @ u, b, 30, iters)
+    op = LinearOperator((40, 30), matvec=lambda v: A @ v, rmatvec=lambda u: A.conj().T @ u,
+                        dtype=complex)
+    want = lib_lsmr(op, b, maxiter=iters, atol=0, btol=0, conlim=0)[0]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-10 * np.abs(want).max())
+
+
+def test_lsmr_reaches_the_least_squares_solution():
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(60, 12)) + 1j * rng.normal(size=(60, 12))
+    b = rng.normal(size=60) + 1j * rng.normal(size=60)
+    x = O.lsmr(lambda v: A @ v, lambda u: A.conj().T @ u, b, 12, 40)
+    np.testing.assert_allclose(x, np.linalg.lstsq(A, b, rcond=None)[0], atol=1e-9)
+
+
+def test_lsmr_phase_system_is_the_ppf_window():
+    """For each phase the window's equations are the PPF's branch sums
+    y_m[p] = sum_t h[tM + p] x[(m - 15 + t) M + p] (brute force over samples),
+    and its adjoint passes the dot test."""
+    h = O.prototype_filter()
+    a = O.lsmr_phase_taps(h)
+    rng = np.random.default_rng(5)
+    rows = 40
+    x = rng.normal(size=(rows + 15) * O.M) + 1j * rng.normal(size=(rows + 15) * O.M)
+    for p in (0, 333, 1023):
+        xp = x[p::O.M]                                         # x_p[j] = x[j M + p]
+        sums = np.array([sum(h[t * O.M + p] * x[(m + t) * O.M + p] for t in range(16))
+                         for m in range(rows)])
+        mv = sum(a[p, t] * xp[t:t + rows] for t in range(16))
+        np.testing.assert_allclose(mv, sums, rtol=1e-12)
+        u = rng.normal(size=rows) + 1j * rng.normal(size=rows)
+        at = np.zeros(rows + 15, dtype=complex)
+        for t in range(16):
+            at[t:t + rows] += a[p, t] * u
+        assert abs(np.vdot(u, mv) - np.vdot(at, xp)) < 1e-12 * abs(np.vdot(u, mv))
+
+
+def _band_case(F=256, fb=200, K=40, tone=None, seed=3):
+    """Frames of a real signal band-limited to the selected bins (or a tone at
+    bin fb + 10 + tone) through the station-side PPF, and its analytic truth."""
+    M = O.M
+    n_total = (F + 40) * M
+    n_start = -20 * M
+    n = np.arange(n_total) + n_start
+    if tone is None:
+        x = np.random.default_rng(seed).normal(size=n_total)
+        X = np.fft.rfft(x)
+        f = np.arange(X.size) * M / n_total
+        band = (f >= fb - 0.5) & (f < fb + K - 0.5)
+        xr = np.fft.irfft(X * band, n_total)
+        Xa = np.zeros(n_total, complex)
+        Xa[:X.size] = 2 * X * band
+        xa = np.fft.ifft(Xa)
+    else:
+        fr = (fb + 10 + tone) / M
+        xr = np.cos(2 * np.pi * fr * n)
+        xa = np.exp(2j * np.pi * fr * n)
+    frames = synth.forward_ppf(xr, n_start, -16, F, np.arange(fb, fb + K), synth.analysis_filter())
+
+    def truth(lag):
+        return xa[(np.arange(F)[:, None] - lag) * M + np.arange(M)[None, :] - n_start]
+    return frames, truth
+
+
+@pytest.mark.parametrize("tone", [None, 0.45])
+def test_lsmr_inversion_recovers_what_the_fir_synthesis_loses(tone):
+    """The paper's reason for the sparse solve: at a subband edge (tone 0.45
+    subband off centre) the FIR synthesis loses ~40 % of the signal and LSMR
+    well under 2 %; on broadband noise 18 % against under 7 %."""
+    frames, truth = _band_case(tone=tone)
+    fb = 200
+    xl = O.lsmr_invert(frames, fb, O.prototype_filter())
+    u = O.ippf(frames[1:], fb, O.synthesis_filter())
+    sl = slice(20, 236)
+    rel = lambda a, b: np.sqrt(np.mean(np.abs(a - b) ** 2) / np.mean(np.abs(b) ** 2))
+    e_lsmr, e_fir = rel(xl[sl], truth(16)[sl]), rel(u[sl], truth(15)[sl])
+    if tone is None:
+        assert e_lsmr < 0.07 and e_fir > 0.15
+    else:
+        assert e_lsmr < 0.02 and e_fir > 0.3
+
+
 # ------------------------------------------------------- noise / trigger ---
 
 @pytest.fixture(scope="module")
