@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--fine", action="store_true",
                     help="fine (channel-domain) de-dispersion filter on (a separate line, "
                          "not the headline)")
+    ap.add_argument("--lsmr", action="store_true",
+                    help="PPF inversion by windowed LSMR instead of the FIR synthesis (a "
+                         "separate line, not the headline; no triggers on that path)")
     ap.add_argument("--gemm-config", type=int, default=-2,
                     help="fixed beamformer configuration index (-1: default; -2: autotune)")
     ap.add_argument("--frames", type=int, default=0,
@@ -279,8 +282,9 @@ def run_ours(args, rank, world, local_rank):
     x = device_block(w, 1000 + rank, dev)
     plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(w.tec_trials), w.block_len,
                    input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
-                   host_input=not args.no_e2e, frames_per_cta=args.synth_frames,
-                   fine_dedisp=args.fine)
+                   host_input=not args.no_e2e and not args.lsmr,
+                   frames_per_cta=args.synth_frames, fine_dedisp=args.fine,
+                   inversion="lsmr" if args.lsmr else "fir")
     plan.lp_set_weights(enu, dirs)
     plan.lp_set_tec(tec)
     stream = torch.cuda.current_stream()
@@ -292,7 +296,7 @@ def run_ours(args, rank, world, local_rank):
         gemm_best, gemm_ms = args.gemm_config, {}
     else:
         gemm_best, gemm_ms = plan.lp_plan_autotune_gemm(x)
-    if args.synth_frames:
+    if args.synth_frames or args.lsmr:
         tuned_fpc, tune_ms = args.synth_frames, {}
     else:
         tuned_fpc, tune_ms = plan.lp_plan_autotune(x)
@@ -426,6 +430,27 @@ def run_ours(args, rank, world, local_rank):
                                  "frac": fine_bytes / (fine_ms / 1e3) / 1e9 / hbm_peak,
                                  "bytes": fine_bytes,
                                  "traffic": recorded_traffic("k_fine.cu")}
+    if args.lsmr:
+        # per window and LSMR step: A v and A^T u (272 x 16 complex x real taps,
+        # 4 FLOP each), two norms and two scalings of 287-element vectors, the
+        # h / hbar / x updates; plus the start (one norm, A^T u, one norm)
+        rows, cols, taps, iters = 272, 287, 16, 25
+        per_step = 2 * rows * taps * 4 + 2 * cols * 4 + 2 * cols * 2 + 3 * cols * 4
+        per_window = iters * per_step + rows * taps * 4 + rows * 4 + cols * 4
+        windows = w.n_streams * M * (w.block_len // 256)
+        inv_ms = stages["synth"] / max(nrec, 1)
+        ach = windows * per_window / (inv_ms / 1e3) / 1e12
+        line["metric"] = line["metric"].replace("realtime factor", "realtime factor, LSMR PPF "
+                                                "inversion (no triggers),")
+        line["config"]["workload"] += "-lsmr"
+        line["config"]["inversion"] = ("windowed LSMR: 256-frame windows, 16 frames of "
+                                       "overlap, 25 iterations, per stream and phase")
+        line["roofline"] = {"bound": "alu", "kernel": "k_zt + k_lsmr (inverse FFT + LSMR)",
+                            "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                            "frac": ach / alu_peak, "traffic": None,
+                            "flop_per_window": per_window, "windows": windows,
+                            "peak_note": line["roofline"]["peak_note"]}
+        line.pop("e2e", None)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, x, min(args.cpu_sample_frames, w.block_len))
     if args.serve_blocks > 0 and not args.frames:

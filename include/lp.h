@@ -95,7 +95,21 @@ typedef struct {
                                appear 8 frames (8192 samples) later; needs a second
                                beam-row buffer; not with chunk_frames; lp_get_beams
                                returns the rows before the filter.  0: off */
+  int32_t inversion;        /* LP_INV_FIR (0): inverse FFT + 16-tap synthesis FIR, with
+                               the trigger.  LP_INV_LSMR (1): the paper's inverse FFT
+                               + sparse solve (Sec. 3, second paragraph): per stream
+                               and phase the PPF window's banded system, solved in
+                               windows of 256 frames (16 of overlap) by lsmr_iters
+                               LSMR iterations; block_len a multiple of 256; no
+                               triggers (the noise level is still kept); the series
+                               lags the frames by 16 (sample (m - 16) M + p) and
+                               lp_get_timeseries returns its real part; not with
+                               chunk_frames or host blocks per polarisation (a host
+                               block is copied whole first) */
+  int32_t lsmr_iters;       /* LSMR iterations per window (25); 1 .. 1000 */
 } lp_config;
+
+enum { LP_INV_FIR = 0, LP_INV_LSMR = 1 };
 
 /* One trigger: envelope sample above k_sigma * sigma of its stream. */
 typedef struct {

@@ -1,0 +1,259 @@
+// PPF inversion by windowed LSMR (Sec. 3, second paragraph): the inverse FFT
+// of each frame, then the sparse system H x = y solved with LSMR (Fong and
+// Saunders 2011).  H is the PPF's window; it splits into one banded Toeplitz
+// system per phase p along the frames,
+//     y_m[p] = sum_{t<16} a_p[t] x_p[m - 15 + t],   a_p[t] = h[t M + p],
+// h the prototype (sum h = 1).  A block is solved window by window: window w
+// takes the 272 equations of frames [256 w - 16, 256 w + 256) over the 287
+// unknowns x_p[q], q in [256 w - 31, 256 w + 256), and keeps q in
+// [256 w - 16, 256 w + 240), the unknowns all 16 of whose equations lie in the
+// window; the output of a block lags its frames by 16 (sample (m - 16) M + p).
+//
+// k_zt: the inverse DFT of 4 frames per block (radix-2, in shared memory, the
+// 2 * beam bins placed in bit-reversed order), written phase-major
+// zt[stream][p][frame + 16] so that a phase's frames are contiguous.
+// k_lsmr: one warp per (stream, phase, window); lane l owns elements
+// [9 l, 9 l + 9) of every vector.  A v and A^T u read a 24-element window of
+// the other vector from shared memory once and slide the 16 taps over it in
+// registers (complex x real tap = one packed FFMA2); norms by warp reduction;
+// the scalar recurrences run redundantly in every lane.  FP32 throughout.
+#include <algorithm>
+
+#include "lp_internal.cuh"
+
+namespace lp {
+namespace {
+
+constexpr int ZT_FR = 4;                       // frames per k_zt block
+constexpr int ZT_NTH = 256;
+constexpr int LS_W = 256;                      // unknowns kept per window
+constexpr int LS_ROWS = LS_W + kPrefix;        // 272 equations
+constexpr int LS_COLS = LS_ROWS + kTaps - 1;   // 287 unknowns
+constexpr int LS_PER = 9;                      // elements per lane (32 * 9 >= 287)
+constexpr int LS_WARPS = 8;                    // warps (phases) per block
+constexpr int LS_PAD = 16;                     // zero guard before / after a vector in smem
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__global__ void __launch_bounds__(ZT_NTH) k_zt(const float2* __restrict__ rows, int K,
+                                               int first_bin, long long row, long long nfr,
+                                               float2* __restrict__ zt) {
+  __shared__ float2 zs[ZT_FR * kM];
+  const long long j = blockIdx.y;
+  const long long f0 = (long long)blockIdx.x * ZT_FR;        // row position (frame + 16)
+  const int tid = threadIdx.x;
+  for (int i = tid; i < ZT_FR * kM; i += ZT_NTH) zs[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = tid; i < ZT_FR * K; i += ZT_NTH) {
+    const int f = i % ZT_FR, k = i / ZT_FR;
+    const float2 v = rows[(j * K + k) * row + f0 + f];
+    const int pos = (int)(__brev((unsigned)(first_bin + k)) >> 22);   // 10-bit reversal
+    zs[f * kM + pos] = make_float2(2.f * v.x, 2.f * v.y);
+  }
+  __syncthreads();
+  for (int s = 0; s < 10; ++s) {                             // half-size 2^s
+    const int hs = 1 << s;
+    for (int b = tid; b < ZT_FR * (kM / 2); b += ZT_NTH) {
+      const int f = b >> 9, bb = b & 511;
+      const int pos = bb & (hs - 1);
+      const int i0 = f * kM + ((bb >> s) << (s + 1)) + pos, i1 = i0 + hs;
+      float sn, cs;
+      sincospif((float)pos / (float)hs, &sn, &cs);           // exp(+2 pi i pos / 2 hs)
+      const float2 x0 = zs[i0], x1 = zs[i1];
+      const float2 t = make_float2(cs * x1.x - sn * x1.y, cs * x1.y + sn * x1.x);
+      zs[i0] = make_float2(x0.x + t.x, x0.y + t.y);
+      zs[i1] = make_float2(x0.x - t.x, x0.y - t.y);
+    }
+    __syncthreads();
+  }
+  constexpr float inv_m = 1.0f / kM;
+  for (int i = tid; i < ZT_FR * kM; i += ZT_NTH) {
+    const int f = i % ZT_FR, p = i / ZT_FR;
+    const float2 v = zs[f * kM + p];
+    zt[(j * kM + p) * nfr + f0 + f] = make_float2(v.x * inv_m, v.y * inv_m);
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__global__ void __launch_bounds__(LS_WARPS * 32) k_lsmr(const float2* __restrict__ zt,
+                                                        const double* __restrict__ proto,
+                                                        const double* __restrict__ sums,
+                                                        long long nfr, long long F, int n_win,
+                                                        int iters, long long j0,
+                                                        float2* __restrict__ out) {
+  __shared__ float2 us[LS_WARPS][LS_PAD + LS_ROWS + LS_PAD + 16];
+  __shared__ float2 vs[LS_WARPS][LS_COLS + LS_PAD + 16];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = (blockIdx.x % (kM / LS_WARPS)) * LS_WARPS + warp;
+  const int w = blockIdx.x / (kM / LS_WARPS);
+  const long long j = j0 + blockIdx.y;
+  float2* u_s = us[warp];
+  float2* v_s = vs[warp];
+  // taps of this phase, (a, a) pairs
+  float2 a[kTaps];
+  const double inv_sum = 1.0 / sums[0];
+#pragma unroll
+  for (int t = 0; t < kTaps; ++t) {
+    const float at = (float)(proto[t * kM + p] * inv_sum);
+    a[t] = make_float2(at, at);
+  }
+  const int e0 = LS_PER * lane;                              // my elements e0 .. e0 + 8
+  // guards and tails of the shared vectors are zero
+  for (int i = lane; i < LS_PAD + LS_ROWS + LS_PAD + 16; i += 32) u_s[i] = make_float2(0.f, 0.f);
+  for (int i = lane; i < LS_COLS + LS_PAD + 16; i += 32) v_s[i] = make_float2(0.f, 0.f);
+  __syncwarp();
+
+  // right-hand side: equations e = frames w W - 16 + e = zt positions w W + e
+  const float2* b = zt + (j * kM + p) * nfr + (long long)w * LS_W;
+  float2 u[LS_PER], v[LS_PER], h[LS_PER], hb[LS_PER], x[LS_PER];
+  float part = 0.f;
+#pragma unroll
+  for (int i = 0; i < LS_PER; ++i) {
+    const int e = e0 + i;
+    u[i] = e < LS_ROWS ? b[e] : make_float2(0.f, 0.f);
+    part = fmaf(u[i].x, u[i].x, fmaf(u[i].y, u[i].y, part));
+  }
+  float beta = sqrtf(warp_sum(part));
+  const float2 zero = make_float2(0.f, 0.f);
+  // u <- u / n, v <- v / n (no change for a zero norm)
+  auto norm_u = [&](float nrm) {
+    const float r = nrm > 0.f ? 1.f / nrm : 1.f;
+#pragma unroll
+    for (int i = 0; i < LS_PER; ++i) u[i] = make_float2(u[i].x * r, u[i].y * r);
+  };
+  auto norm_v = [&](float nrm) {
+    const float r = nrm > 0.f ? 1.f / nrm : 1.f;
+#pragma unroll
+    for (int i = 0; i < LS_PER; ++i) v[i] = make_float2(v[i].x * r, v[i].y * r);
+  };
+  // A^T u - c v, into v; returns the new norm
+  auto rmatvec = [&](float c) {
+#pragma unroll
+    for (int i = 0; i < LS_PER; ++i)
+      if (e0 + i < LS_ROWS) u_s[LS_PAD + e0 + i] = u[i];
+    __syncwarp();
+    // unknown n = e0 + i takes u[n - t], t < 16: window u[e0 - 15 .. e0 + 8]
+    float2 win[LS_PER + kTaps - 1];
+#pragma unroll
+    for (int i = 0; i < LS_PER + kTaps - 1; ++i) win[i] = u_s[LS_PAD + e0 - (kTaps - 1) + i];
+    float pt = 0.f;
+#pragma unroll
+    for (int i = 0; i < LS_PER; ++i) {
+      float2 acc = make_float2(-c * v[i].x, -c * v[i].y);
+#pragma unroll
+      for (int t = 0; t < kTaps; ++t) acc = fma2(a[t], win[i + (kTaps - 1) - t], acc);
+      v[i] = e0 + i < LS_COLS ? acc : zero;
+      pt = fmaf(v[i].x, v[i].x, fmaf(v[i].y, v[i].y, pt));
+    }
+    __syncwarp();
+    return sqrtf(warp_sum(pt));
+  };
+  // A v - c u, into u; returns the new norm
+  auto matvec = [&](float c) {
+#pragma unroll
+    for (int i = 0; i < LS_PER; ++i)
+      if (e0 + i < LS_COLS) v_s[e0 + i] = v[i];
+    __syncwarp();
+    // equation e = e0 + i takes v[e + t], t < 16: window v[e0 .. e0 + 23]
+    float2 win[LS_PER + kTaps - 1];
+#pragma unroll
+    for (int i = 0; i < LS_PER + kTaps - 1; ++i) win[i] = v_s[e0 + i];
+    float pt = 0.f;
+#pragma unroll
+    for (int i = 0; i < LS_PER; ++i) {
+      float2 acc = make_float2(-c * u[i].x, -c * u[i].y);
+#pragma unroll
+      for (int t = 0; t < kTaps; ++t) acc = fma2(a[t], win[i + t], acc);
+      u[i] = e0 + i < LS_ROWS ? acc : zero;
+      pt = fmaf(u[i].x, u[i].x, fmaf(u[i].y, u[i].y, pt));
+    }
+    __syncwarp();
+    return sqrtf(warp_sum(pt));
+  };
+
+#pragma unroll
+  for (int i = 0; i < LS_PER; ++i) {
+    v[i] = zero;
+    h[i] = zero;
+    hb[i] = zero;
+    x[i] = zero;
+  }
+  if (beta > 0.f) {
+    norm_u(beta);
+    float alpha = rmatvec(0.f);
+    if (alpha > 0.f) {
+      norm_v(alpha);
+      float alphabar = alpha, zetabar = alpha * beta;
+      float rho = 1.f, rhobar = 1.f, cbar = 1.f, sbar = 0.f;
+#pragma unroll
+      for (int i = 0; i < LS_PER; ++i) h[i] = v[i];
+      for (int it = 0; it < iters; ++it) {
+        // continue the bidiagonalisation
+        beta = matvec(alpha);
+        norm_u(beta);
+        alpha = rmatvec(beta);
+        norm_v(alpha);
+        // rotation P_k
+        const float rho_old = rho;
+        rho = hypotf(alphabar, beta);
+        const float c = alphabar / rho, s = beta / rho;
+        const float theta = s * alpha;
+        alphabar = c * alpha;
+        // rotation Pbar_k
+        const float rhobar_old = rhobar;
+        const float thetabar = sbar * rho;
+        rhobar = hypotf(cbar * rho, theta);
+        const float cbar_new = cbar * rho / rhobar;
+        sbar = theta / rhobar;
+        cbar = cbar_new;
+        const float zeta = cbar * zetabar;
+        zetabar = -sbar * zetabar;
+        // update h, hbar, x
+        const float f1 = thetabar * rho / (rho_old * rhobar_old);
+        const float f2 = zeta / (rho * rhobar);
+        const float f3 = theta / rho;
+#pragma unroll
+        for (int i = 0; i < LS_PER; ++i) {
+          hb[i] = make_float2(h[i].x - f1 * hb[i].x, h[i].y - f1 * hb[i].y);
+          x[i] = make_float2(fmaf(f2, hb[i].x, x[i].x), fmaf(f2, hb[i].y, x[i].y));
+          h[i] = make_float2(v[i].x - f3 * h[i].x, v[i].y - f3 * h[i].y);
+        }
+      }
+    }
+  }
+  // keep unknowns 15 .. 15 + W - 1: output frames w W .. w W + W - 1
+  const long long o = (j * kM + p) * F + (long long)w * LS_W;
+#pragma unroll
+  for (int i = 0; i < LS_PER; ++i) {
+    const int n = e0 + i;
+    if (n >= kTaps - 1 && n < kTaps - 1 + LS_W) out[o + n - (kTaps - 1)] = x[i];
+  }
+}
+
+}  // namespace
+
+int lsmr_window() { return LS_W; }
+
+cudaError_t launch_lsmr(const lp_plan& p, cudaStream_t s) {
+  const auto& sh = p.shape;
+  const long long nfr = sh.F + kPrefix;
+  const long long J = sh.J();
+  for (long long j0 = 0; j0 < J; j0 += 65535) {             // grid y is at most 65535
+    const unsigned nj = (unsigned)std::min<long long>(65535, J - j0);
+    k_zt<<<dim3((unsigned)(nfr / ZT_FR), nj), ZT_NTH, 0, s>>>(
+        synth_rows(p) + j0 * sh.K * p.row(), sh.K, p.cfg.first_bin, p.row(), nfr,
+        p.buf.zt + j0 * kM * nfr);
+    const int n_win = (int)(sh.F / LS_W);
+    k_lsmr<<<dim3((unsigned)(kM / LS_WARPS * n_win), nj), LS_WARPS * 32, 0, s>>>(
+        p.buf.zt, p.buf.proto, p.buf.filter_sums, nfr, sh.F, n_win, p.cfg.lsmr_iters, j0,
+        p.buf.xhat);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lp

@@ -63,6 +63,9 @@ size_t carve(lp_plan& p, char* base) {
   b.beams_fine = fine ? (float2*)take(sizeof(float2) * (size_t)J * sh.K * p.row()) : nullptr;
   b.fine_taps = fine ? (float4*)take(sizeof(float4) * (size_t)sh.K * sh.Tr * lp::kFineTaps)
                      : nullptr;
+  const bool lsmr = p.cfg.inversion == LP_INV_LSMR;
+  b.zt = lsmr ? (float2*)take(sizeof(float2) * (size_t)J * kM * (sh.F + lp::kPrefix)) : nullptr;
+  b.xhat = lsmr ? (float2*)take(sizeof(float2) * (size_t)J * kM * sh.F) : nullptr;
   b.power_part = (float*)take(sizeof(float) * (size_t)J * sh.K * p.n_ftiles_bf);
   b.sigma2 = (double*)take(sizeof(double) * J);
   b.theta = (float*)take(sizeof(float) * J);
@@ -145,6 +148,9 @@ void lp_config_default(lp_config* c) {
   c->frames_per_cta = 0;
   c->use_graph = 0;
   c->chunk_frames = 0;
+  c->fine_dedisp = 0;
+  c->inversion = LP_INV_FIR;
+  c->lsmr_iters = 25;
 }
 
 lp_status lp_plan_create(lp_plan** out, int stations, int pols, int subbands, int beams,
@@ -190,6 +196,17 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
     return fail(p, LP_ERR_ARG, "frames_per_cta must be 0 or a positive multiple of 8");
   if (c->fine_dedisp != 0 && c->fine_dedisp != 1)
     return fail(p, LP_ERR_ARG, "fine_dedisp must be 0 or 1");
+  if (c->inversion != LP_INV_FIR && c->inversion != LP_INV_LSMR)
+    return fail(p, LP_ERR_ARG, "inversion must be LP_INV_FIR or LP_INV_LSMR");
+  if (c->inversion == LP_INV_LSMR) {
+    if (sh.F % lp::lsmr_window() != 0)
+      return fail(p, LP_ERR_ARG, "LSMR inversion needs block_len a multiple of %d",
+                  lp::lsmr_window());
+    if (c->lsmr_iters < 1 || c->lsmr_iters > 1000)
+      return fail(p, LP_ERR_ARG, "lsmr_iters must be in [1, 1000]");
+    if (c->chunk_frames != 0)
+      return fail(p, LP_ERR_ARG, "LSMR inversion does not combine with chunk_frames");
+  }
   if (c->fine_dedisp && c->chunk_frames != 0)
     return fail(p, LP_ERR_ARG, "fine_dedisp does not combine with chunk_frames");
   if (c->chunk_frames != 0) {
@@ -549,7 +566,8 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, T
   const size_t bpc = p->cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4;   // bytes per complex sample
   const bool host = attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged;
   const bool graph_mode = p->cfg.use_graph && !p->profiling && !tune;
-  if (host && p->buf.staging && sh.P == 2 && p->fc == sh.F && !tune && !graph_mode)
+  if (host && p->buf.staging && sh.P == 2 && p->fc == sh.F && !tune && !graph_mode &&
+      p->cfg.inversion == LP_INV_FIR)
     return process_host_pipelined(p, x, pol_stride, s);
   if (host) {
     if (!p->buf.staging)
@@ -601,7 +619,9 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, T
       }
       prof_mark(p, LP_STAGE_SYNTH, 0, s);
       if (e == cudaSuccess)
-        e = tune == kTuneSynth ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
+        e = p->cfg.inversion == LP_INV_LSMR ? lp::launch_lsmr(*p, s)
+            : tune == kTuneSynth            ? tune_ippf(p, c, s, tune_ms)
+                                            : lp::launch_ippf(*p, c, s);
       prof_mark(p, LP_STAGE_SYNTH, 1, s);
       prof_mark(p, LP_STAGE_SHIFT, 0, s);
       if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
@@ -687,9 +707,21 @@ lp_status lp_get_triggers(lp_plan* p, lp_trigger* out, int64_t cap, int64_t* n_t
 
 lp_status lp_get_timeseries(lp_plan* p, int beam, int tec, int pol, float* out) {
   if (lp_status st = need_bound(p)) return st;
-  if (!p->buf.y) return fail(p, LP_ERR_STATE, "store_timeseries is off");
   const int j = stream_of(p, beam, tec, pol);
   if (j < 0 || !out) return fail(p, LP_ERR_ARG, "bad stream or buffer");
+  if (p->buf.xhat) {
+    // LSMR inversion: the real part of the recovered series, stored phase-major
+    if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+    if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
+    const size_t F = (size_t)p->shape.F;
+    std::vector<float2> xs(F * kM);
+    LP_CUDA(p, cudaMemcpy(xs.data(), p->buf.xhat + (size_t)j * kM * F, sizeof(float2) * F * kM,
+                          cudaMemcpyDeviceToHost));
+    for (size_t q = 0; q < (size_t)kM; ++q)
+      for (size_t i = 0; i < F; ++i) out[i * kM + q] = xs[q * F + i].x;
+    return LP_OK;
+  }
+  if (!p->buf.y) return fail(p, LP_ERR_STATE, "store_timeseries is off");
   if (set_device(p) != LP_OK) return LP_ERR_CUDA;
   if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
   const size_t n = (size_t)p->shape.F * kM;
@@ -751,6 +783,8 @@ int lp_launches_per_block(const lp_plan* p) {
   if (!p) return 4;
   const long long rows = (long long)p->shape.J() * p->shape.K;
   const int fine = p->cfg.fine_dedisp ? (int)((rows + 65534) / 65535) : 0;
+  if (p->cfg.inversion == LP_INV_LSMR)   // inverse FFT + LSMR per 65535 streams
+    return 3 + fine + 2 * (int)((p->shape.J() + 65534) / 65535);
   if (p->fc == 0 || p->fc == p->shape.F) return 4 + fine;
   return 2 + 3 * (int)(p->shape.F / p->fc);
 }

@@ -20,6 +20,7 @@ LP_OK, LP_ERR_ARG, LP_ERR_CUDA, LP_ERR_OOM, LP_ERR_STATE, LP_ERR_OVERFLOW, LP_ER
     LP_ERR_BUSY = range(8)
 LP_INPUT_INT8, LP_INPUT_INT16 = 1, 2
 LP_PREC_FP32, LP_PREC_FP16 = 0, 1
+LP_INV_FIR, LP_INV_LSMR = 0, 1
 LP_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -40,6 +41,8 @@ class lp_config(ctypes.Structure):
         ("use_graph", ctypes.c_int32),
         ("chunk_frames", ctypes.c_int32),
         ("fine_dedisp", ctypes.c_int32),
+        ("inversion", ctypes.c_int32),
+        ("lsmr_iters", ctypes.c_int32),
     ]
 
 
@@ -163,7 +166,7 @@ class Plan:
                  sigma_alpha=0.25, nu_ref_hz=0.0, trigger_cap=1 << 20,
                  store_timeseries=False, host_input=False, frames_per_cta=0,
                  kaiser_beta=9.0, use_graph=False, chunk_frames=0, fine_dedisp=False,
-                 stream=None, workspace=None):
+                 inversion="fir", lsmr_iters=25, stream=None, workspace=None):
         import torch
         self.shape = (stations, pols, subbands, beams, tec_trials, block_len)
         self._h = _P()
@@ -184,6 +187,8 @@ class Plan:
         c.use_graph = int(bool(use_graph))
         c.chunk_frames = int(chunk_frames)
         c.fine_dedisp = int(bool(fine_dedisp))
+        c.inversion = LP_INV_LSMR if inversion == "lsmr" else LP_INV_FIR
+        c.lsmr_iters = int(lsmr_iters)
         self.config = c
         self._check(_lib.lp_plan_configure(self._h, ctypes.byref(c)), "lp_plan_configure")
         nbytes = ctypes.c_size_t()

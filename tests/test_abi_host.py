@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported_and_bound(lib):
 def test_struct_layouts(lib):
     assert ctypes.sizeof(lib.lp_trigger) == 32
     assert lib.TRIGGER_DTYPE.itemsize == 32
-    assert ctypes.sizeof(lib.lp_config) == 80
+    assert ctypes.sizeof(lib.lp_config) == 88
 
 
 def _create(lib, *shape):

@@ -1,0 +1,86 @@
+"""PPF inversion by windowed LSMR on the GPU against the FP64 oracle.
+
+The oracle beamforms and de-disperses each stream (the same definitions as
+the plain path), carries the last 16 frames of the previous block, and
+inverts each block with ``lsmr_invert``.  Tolerance: in the kernel the
+vectors and scalars are FP32; 25 LSMR steps on these window systems move the
+FP32 iterate ~1e-7 (relative) from the FP64 one, the inverse FFT adds ~1e-6:
+TOL_LSMR = 1e-5 for the FP32 beamformer, the FP16 form's own 1e-4 above it.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import TOL_TS_FP16, make_plan, random_case, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+TOL_LSMR = 1e-5
+
+
+def _oracle_series(blocks, enu, dirs, tec, fb, P, K, B, Tr, F):
+    """Re of the LSMR series per block and stream [J, F*M], carrying 16 frames."""
+    nu = O.sky_frequencies(fb, K)
+    w = O.geometric_weights(nu, enu, dirs)
+    d = O.dedispersion_weights(nu, tec, 0.5 * (nu[0] + nu[-1]))
+    h = O.prototype_filter()
+    J = B * Tr * P
+    hist = np.zeros((J, O.LSMR_OVERLAP, K), dtype=complex)
+    out = []
+    for xb in blocks:
+        xc = xb[..., 0].astype(np.float64) + 1j * xb[..., 1]
+        bm = O.beamform(xc, w, d)                                # [B, Tr, P, K, F]
+        ys = np.zeros((J, F * O.M))
+        for b in range(B):
+            for t in range(Tr):
+                for p in range(P):
+                    j = (b * Tr + t) * P + p
+                    fr = np.concatenate([hist[j], bm[b, t, p].T])
+                    ys[j] = O.lsmr_invert(fr, fb, h).real.reshape(-1)
+                    hist[j] = fr[-O.LSMR_OVERLAP:]
+        out.append(ys)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_lsmr_inversion_matches_oracle(cuda_lib, precision):
+    """Two blocks of two windows each (history across the block boundary)."""
+    S, P, K, B, Tr, F, fb = 8, 1, 12, 2, 1, 512, 200
+    blocks, enu, dirs, tec = random_case(51, S, P, K, B, Tr, F, fb, "int8", 2, amp=60)
+    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision=precision,
+                     inversion="lsmr")
+    assert plan.lp_launches_per_block() == 5
+    plan.lp_set_weights(enu, dirs)
+    plan.lp_set_tec(tec)
+    want = _oracle_series(blocks, enu, dirs, tec, fb, P, K, B, Tr, F)
+    import torch
+    for xb, ys in zip(blocks, want):
+        plan.lp_process_block(torch.from_numpy(xb).cuda())
+        got = np.stack([plan.lp_get_timeseries(b, 0, 0) for b in range(B)])
+        tol = TOL_LSMR if precision == "fp32" else TOL_TS_FP16
+        assert rel_rms(got, ys) < tol
+        trig, n, st = plan.lp_get_triggers()
+        assert n == 0                                     # no trigger on this path
+        assert np.all(plan.lp_get_sigma() > 0)
+
+
+def test_lsmr_iterations_and_limits(cuda_lib):
+    """A different iteration count follows the oracle too; the block length must
+    be a multiple of the window."""
+    S, P, K, B, Tr, F, fb = 4, 1, 6, 1, 1, 256, 300
+    blocks, enu, dirs, tec = random_case(52, S, P, K, B, Tr, F, fb, "int16", 1, amp=300)
+    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int16", inversion="lsmr", lsmr_iters=7)
+    plan.lp_set_weights(enu, dirs)
+    plan.lp_set_tec(tec)
+    import torch
+    plan.lp_process_block(torch.from_numpy(blocks[0]).cuda())
+    nu = O.sky_frequencies(fb, K)
+    xc = blocks[0][..., 0].astype(np.float64) + 1j * blocks[0][..., 1]
+    bm = O.beamform(xc, O.geometric_weights(nu, enu, dirs),
+                    O.dedispersion_weights(nu, tec, 0.5 * (nu[0] + nu[-1])))
+    fr = np.concatenate([np.zeros((O.LSMR_OVERLAP, K)), bm[0, 0, 0].T])
+    want = O.lsmr_invert(fr, fb, O.prototype_filter(), iters=7).real.reshape(-1)
+    assert rel_rms(plan.lp_get_timeseries(0, 0, 0), want) < TOL_LSMR
+    with pytest.raises(cuda_lib.LPError):
+        make_plan(cuda_lib, S, P, K, B, Tr, 384, fb, "int16", inversion="lsmr")
