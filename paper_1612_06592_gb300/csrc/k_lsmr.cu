@@ -30,7 +30,7 @@ constexpr int LS_W = 256;                      // unknowns kept per window
 constexpr int LS_ROWS = LS_W + kPrefix;        // 272 equations
 constexpr int LS_COLS = LS_ROWS + kTaps - 1;   // 287 unknowns
 constexpr int LS_PER = 9;                      // elements per lane (32 * 9 >= 287)
-constexpr int LS_WARPS = 8;                    // warps (phases) per block
+constexpr int LS_WARPS = 4;                    // warps (phases) per block (3 blocks per SM)
 constexpr int LS_PAD = 16;                     // zero guard before / after a vector in smem
 
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -80,7 +80,7 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(LS_WARPS * 32) k_lsmr(const float2* __restrict__ zt,
+__global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restrict__ zt,
                                                         const double* __restrict__ proto,
                                                         const double* __restrict__ sums,
                                                         long long nfr, long long F, int n_win,
