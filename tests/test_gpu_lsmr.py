@@ -84,3 +84,63 @@ def test_lsmr_iterations_and_limits(cuda_lib):
     assert rel_rms(plan.lp_get_timeseries(0, 0, 0), want) < TOL_LSMR
     with pytest.raises(cuda_lib.LPError):
         make_plan(cuda_lib, S, P, K, B, Tr, 384, fb, "int16", inversion="lsmr")
+
+
+def test_lsmr_host_input_and_graph_equal_device_input(cuda_lib):
+    """A host block (copied whole, then inverted) and a graph replay give the
+    device block's series bit for bit, over blocks with carried history."""
+    import torch
+    S, P, K, B, Tr, F, fb = 4, 2, 8, 1, 1, 256, 150
+    blocks, enu, dirs, tec = random_case(53, S, P, K, B, Tr, F, fb, "int8", 2, amp=50)
+    res = []
+    for mode in ("device", "host", "graph"):
+        stream = torch.cuda.Stream()
+        plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", inversion="lsmr",
+                         host_input=mode == "host", use_graph=mode == "graph", stream=stream)
+        plan.lp_set_weights(enu, dirs, stream=stream)
+        plan.lp_set_tec(tec, stream=stream)
+        xd = torch.empty((P, K, F, S, 2), dtype=torch.int8, device="cuda")
+        out = []
+        for xb in blocks:
+            if mode == "host":
+                plan.lp_process_block(torch.from_numpy(xb).pin_memory(), stream=stream)
+            else:
+                with torch.cuda.stream(stream):
+                    xd.copy_(torch.from_numpy(xb))
+                plan.lp_process_block(xd, stream=stream)
+            out.append(np.stack([plan.lp_get_timeseries(0, 0, p) for p in range(P)]))
+        res.append(out)
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_fine_dedispersion_then_lsmr_matches_oracle(cuda_lib):
+    """The channel-domain filter feeds the LSMR inversion (both histories carried)."""
+    S, P, K, B, Tr, F, fb = 6, 1, 16, 1, 2, 256, 60
+    blocks, enu, dirs, tec = random_case(54, S, P, K, B, Tr, F, fb, "int16", 2, amp=200)
+    tec = np.array([9.0, 31.0])
+    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int16", inversion="lsmr",
+                     fine_dedisp=True)
+    plan.lp_set_weights(enu, dirs)
+    plan.lp_set_tec(tec)
+    nu = O.sky_frequencies(fb, K)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    w = O.geometric_weights(nu, enu, dirs)
+    d = O.dedispersion_weights(nu, tec, nu_ref)
+    r = O.fine_dedispersion_taps(nu, tec, nu_ref)
+    h = O.prototype_filter()
+    fine_hist = np.zeros((Tr, O.FINE_TAPS - 1, K), dtype=complex)
+    lsmr_hist = np.zeros((Tr, O.LSMR_OVERLAP, K), dtype=complex)
+    import torch
+    for xb in blocks:
+        plan.lp_process_block(torch.from_numpy(xb).cuda())
+        bm = O.beamform(xb[..., 0].astype(np.float64) + 1j * xb[..., 1], w, d)
+        for t in range(Tr):
+            fext = np.concatenate([fine_hist[t], bm[0, t, 0].T])
+            fr = O.fine_dedisperse(fext, r[:, t])
+            fine_hist[t] = fext[-(O.FINE_TAPS - 1):]
+            lext = np.concatenate([lsmr_hist[t], fr])
+            want = O.lsmr_invert(lext, fb, h).real.reshape(-1)
+            lsmr_hist[t] = lext[-O.LSMR_OVERLAP:]
+            assert rel_rms(plan.lp_get_timeseries(0, t, 0), want) < TOL_LSMR
