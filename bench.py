@@ -637,7 +637,7 @@ def run_two_stage(args):
                        gemm_autotune_ms={gemm_desc("fp32", gemm_cfgs, gemm_cfgs.index(k)):
                                          round(v, 3) for k, v in gemm_ms.items()}),
         "stage_ms": dict({"prebeam": pre_ms}, **{k: v / max(nrec, 1) for k, v in stages.items()
-                                                  if k != "h2d"}),
+                                                  if k not in ("h2d", "fine")}),
         "roofline_prebeam": {"bound": "hbm", "kernel": "k_prebeam", "achieved": pre_gbs,
                              "peak": hbm_peak, "unit": "GB/s", "frac": pre_gbs / hbm_peak,
                              "bytes": in_bytes + out_bytes,

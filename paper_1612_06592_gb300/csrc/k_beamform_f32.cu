@@ -51,15 +51,25 @@ __global__ void __launch_bounds__(NTH, 3) k_beamform_f32(
   const long long f0 = (long long)tile * FT;
   const int nvalid = (int)min((long long)FT, F - f0);
 
-  // station samples of this (pol, k) and frame tile -> xs[s][frame]
+  // station samples of this (pol, k) and frame tile -> xs[s][frame]; the
+  // (frame, station) of sample e is carried from one e to the next (e += NTH)
   const T2* xk = x + (long long)pol * pol_stride + ((long long)k * F + f0) * S;
-  for (int e = tid; e < FT * S; e += NTH) {
-    const int fr = e / S, st = e - fr * S;
-    T2 v;
-    v.x = 0;
-    v.y = 0;
-    if (fr < nvalid) v = xk[e];
-    xs[st * FTP + fr] = v;
+  {
+    int fr = tid / S, st = tid - fr * S;
+    const int dq = NTH / S, dr = NTH - dq * S;
+    for (int e = tid; e < FT * S; e += NTH) {
+      T2 v;
+      v.x = 0;
+      v.y = 0;
+      if (fr < nvalid) v = xk[e];
+      xs[st * FTP + fr] = v;
+      st += dr;
+      fr += dq;
+      if (st >= S) {
+        st -= S;
+        ++fr;
+      }
+    }
   }
 
   const int fl = 2 * tid;                                    // my frames fl, fl + 1

@@ -111,25 +111,27 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
   // right-hand side: equations e = frames w W - 16 + e = zt positions w W + e
   const float2* b = zt + (j * kM + p) * nfr + (long long)w * LS_W;
   float2 u[LS_PER], v[LS_PER], h[LS_PER], hb[LS_PER], x[LS_PER];
-  float part = 0.f;
+  const float2 zero = make_float2(0.f, 0.f);
+  float2 part = zero;
 #pragma unroll
   for (int i = 0; i < LS_PER; ++i) {
     const int e = e0 + i;
-    u[i] = e < LS_ROWS ? b[e] : make_float2(0.f, 0.f);
-    part = fmaf(u[i].x, u[i].x, fmaf(u[i].y, u[i].y, part));
+    u[i] = e < LS_ROWS ? b[e] : zero;
+    part = fma2(u[i], u[i], part);
   }
-  float beta = sqrtf(warp_sum(part));
-  const float2 zero = make_float2(0.f, 0.f);
-  // u <- u / n, v <- v / n (no change for a zero norm)
+  float beta = sqrtf(warp_sum(part.x + part.y));
+  // u <- u / n, v <- v / n (no change for a zero norm); packed FMUL2
   auto norm_u = [&](float nrm) {
     const float r = nrm > 0.f ? 1.f / nrm : 1.f;
+    const float2 r2 = make_float2(r, r);
 #pragma unroll
-    for (int i = 0; i < LS_PER; ++i) u[i] = make_float2(u[i].x * r, u[i].y * r);
+    for (int i = 0; i < LS_PER; ++i) u[i] = __fmul2_rn(u[i], r2);
   };
   auto norm_v = [&](float nrm) {
     const float r = nrm > 0.f ? 1.f / nrm : 1.f;
+    const float2 r2 = make_float2(r, r);
 #pragma unroll
-    for (int i = 0; i < LS_PER; ++i) v[i] = make_float2(v[i].x * r, v[i].y * r);
+    for (int i = 0; i < LS_PER; ++i) v[i] = __fmul2_rn(v[i], r2);
   };
   // A^T u - c v, into v; returns the new norm
   auto rmatvec = [&](float c) {
@@ -141,17 +143,18 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
     float2 win[LS_PER + kTaps - 1];
 #pragma unroll
     for (int i = 0; i < LS_PER + kTaps - 1; ++i) win[i] = u_s[LS_PAD + e0 - (kTaps - 1) + i];
-    float pt = 0.f;
+    const float2 mc = make_float2(-c, -c);
+    float2 pt = zero;
 #pragma unroll
     for (int i = 0; i < LS_PER; ++i) {
-      float2 acc = make_float2(-c * v[i].x, -c * v[i].y);
+      float2 acc = __fmul2_rn(mc, v[i]);
 #pragma unroll
       for (int t = 0; t < kTaps; ++t) acc = fma2(a[t], win[i + (kTaps - 1) - t], acc);
       v[i] = e0 + i < LS_COLS ? acc : zero;
-      pt = fmaf(v[i].x, v[i].x, fmaf(v[i].y, v[i].y, pt));
+      pt = fma2(v[i], v[i], pt);
     }
     __syncwarp();
-    return sqrtf(warp_sum(pt));
+    return sqrtf(warp_sum(pt.x + pt.y));
   };
   // A v - c u, into u; returns the new norm
   auto matvec = [&](float c) {
@@ -163,17 +166,18 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
     float2 win[LS_PER + kTaps - 1];
 #pragma unroll
     for (int i = 0; i < LS_PER + kTaps - 1; ++i) win[i] = v_s[e0 + i];
-    float pt = 0.f;
+    const float2 mc = make_float2(-c, -c);
+    float2 pt = zero;
 #pragma unroll
     for (int i = 0; i < LS_PER; ++i) {
-      float2 acc = make_float2(-c * u[i].x, -c * u[i].y);
+      float2 acc = __fmul2_rn(mc, u[i]);
 #pragma unroll
       for (int t = 0; t < kTaps; ++t) acc = fma2(a[t], win[i + t], acc);
       u[i] = e0 + i < LS_ROWS ? acc : zero;
-      pt = fmaf(u[i].x, u[i].x, fmaf(u[i].y, u[i].y, pt));
+      pt = fma2(u[i], u[i], pt);
     }
     __syncwarp();
-    return sqrtf(warp_sum(pt));
+    return sqrtf(warp_sum(pt.x + pt.y));
   };
 
 #pragma unroll
@@ -217,11 +221,13 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
         const float f1 = thetabar * rho / (rho_old * rhobar_old);
         const float f2 = zeta / (rho * rhobar);
         const float f3 = theta / rho;
+        const float2 m1 = make_float2(-f1, -f1), p2 = make_float2(f2, f2),
+                     m3 = make_float2(-f3, -f3);
 #pragma unroll
         for (int i = 0; i < LS_PER; ++i) {
-          hb[i] = make_float2(h[i].x - f1 * hb[i].x, h[i].y - f1 * hb[i].y);
-          x[i] = make_float2(fmaf(f2, hb[i].x, x[i].x), fmaf(f2, hb[i].y, x[i].y));
-          h[i] = make_float2(v[i].x - f3 * h[i].x, v[i].y - f3 * h[i].y);
+          hb[i] = fma2(m1, hb[i], h[i]);
+          x[i] = fma2(p2, hb[i], x[i]);
+          h[i] = fma2(m3, h[i], v[i]);
         }
       }
     }
