@@ -29,6 +29,7 @@ __all__ = [
     "bessel_i0", "prototype_filter", "synthesis_filter", "fft_radix2",
     "windowed_sums", "ippf", "parseval_power", "update_sigma2", "find_triggers",
     "LSMR_ITERS", "LSMR_WINDOW", "LSMR_OVERLAP", "lsmr", "lsmr_phase_taps", "lsmr_invert",
+    "lsmr_noise_power",
     "Pipeline", "stream_window", "brute_force_stream",
     "INT16_MAX", "group_centres", "prebeam_weights", "prebeam", "transport_int16",
     "FINE_TAPS", "FINE_DELAY", "FINE_BETA", "FINE_GRID", "fine_dedispersion_taps",
@@ -537,6 +538,18 @@ def lsmr_invert(frames_ext: np.ndarray, first_bin: int, h: np.ndarray,
             x = lsmr(matvec, rmatvec, z[w0:w0 + rows, p], cols, iters)
             out[w0:w0 + window, p] = x[taps - 1:taps - 1 + window]
     return out
+
+
+def lsmr_noise_power(xhat: np.ndarray) -> np.ndarray:
+    """Noise level of one block of the LSMR series, per phase (reading):
+    Pi_p = mean over the block's rows of |x[i, p]|^2 / 2, [M].  The solver's
+    noise gain differs from phase to phase (ill-conditioned phase systems
+    amplify it, by up to ~4x in power), so a single level per stream would
+    over-trigger on the noisy phases; per phase, |x| follows the Rayleigh law.
+    The levels feed the same running update as the FIR path
+    (``update_sigma2``), and a sample triggers iff |x| > k_sigma sigma_p."""
+    x = np.asarray(xhat)
+    return np.mean(x.real ** 2 + x.imag ** 2, axis=0) / 2.0
 
 
 # --------------------------------------------------------------------------

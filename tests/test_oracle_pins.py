@@ -571,6 +571,24 @@ def test_lsmr_inversion_recovers_what_the_fir_synthesis_loses(tone):
         assert e_lsmr < 0.02 and e_fir > 0.3
 
 
+def test_lsmr_series_of_noise_follows_the_rayleigh_tail():
+    """White complex noise in the subbands: per phase the LSMR series is
+    circular Gaussian, so against its per-phase noise level
+    P(|x| > k sigma_p) = exp(-k^2 / 2) (Rayleigh); the phases' levels differ."""
+    rng = np.random.default_rng(6)
+    F, K, fb = 256, 64, 120
+    frames = rng.normal(size=(16 + F, K)) + 1j * rng.normal(size=(16 + F, K))
+    x = O.lsmr_invert(frames, fb, O.prototype_filter())[16:]
+    pw = O.lsmr_noise_power(x)
+    assert pw.shape == (O.M,) and pw.max() / pw.min() > 2          # phase-dependent gain
+    sigma = np.sqrt(pw)
+    for k in (1.0, 1.5, 2.0):
+        assert abs(np.mean(np.abs(x) > k * sigma[None, :]) / math.exp(-k * k / 2) - 1) < 0.05
+    # one level per stream would not follow the law in the tail
+    s1 = math.sqrt(pw.mean())
+    assert np.mean(np.abs(x) > 3 * s1) / math.exp(-4.5) > 1.3
+
+
 # ------------------------------------------------------- noise / trigger ---
 
 @pytest.fixture(scope="module")
