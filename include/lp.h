@@ -100,10 +100,11 @@ typedef struct {
                                + sparse solve (Sec. 3, second paragraph): per stream
                                and phase the PPF window's banded system, solved in
                                windows of 256 frames (16 of overlap) by lsmr_iters
-                               LSMR iterations; block_len a multiple of 256; no
-                               triggers (the noise level is still kept); the series
-                               lags the frames by 16 (sample (m - 16) M + p) and
-                               lp_get_timeseries returns its real part; not with
+                               LSMR iterations; block_len a multiple of 256; the
+                               trigger runs on the recovered series against a noise
+                               level per stream and phase (lp_get_lsmr_sigma); the
+                               series lags the frames by 16 (sample (m - 16) M + p)
+                               and lp_get_timeseries returns its real part; not with
                                chunk_frames or host blocks per polarisation (a host
                                block is copied whole first) */
   int32_t lsmr_iters;       /* LSMR iterations per window (25); 1 .. 1000 */
@@ -201,8 +202,15 @@ lp_status lp_get_timeseries(lp_plan* plan, int beam, int tec, int pol,
  * stream for the last block, host floats [K][F][2]. */
 lp_status lp_get_beams(lp_plan* plan, int beam, int tec, int pol, float* out_host);
 
-/* Synchronise and copy the running sigma_y of every stream, host doubles [J]. */
+/* Synchronise and copy the running sigma_y of every stream, host doubles [J]
+ * (LSMR inversion: the RMS over phases of the per-phase levels). */
 lp_status lp_get_sigma(lp_plan* plan, double* sigma_host);
+
+/* LSMR inversion only: the running noise level of the recovered series per
+ * stream and phase, host doubles [J][1024] (the solver's noise gain depends on
+ * the phase, so the trigger compares |x| with k_sigma times this level).
+ * LP_ERR_STATE on a plan without the LSMR inversion. */
+lp_status lp_get_lsmr_sigma(lp_plan* plan, double* sigma_host);
 
 /* Forget the stream: zero synthesis history and noise state, block counter 0. */
 lp_status lp_reset_stream(lp_plan* plan, void* stream);

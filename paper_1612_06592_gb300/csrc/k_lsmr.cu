@@ -17,6 +17,9 @@
 // the other vector from shared memory once and slide the 16 taps over it in
 // registers (complex x real tap = one packed FFMA2); norms by warp reduction;
 // the scalar recurrences run redundantly in every lane.  FP32 throughout.
+// k_lsmr_sigma / k_lsmr_trigger: the series' noise level per (stream, phase)
+// (its gain depends on the phase's system) with the running update of the FIR
+// path, and the threshold with warp-ballot compaction.
 #include <algorithm>
 
 #include "lp_internal.cuh"
@@ -32,6 +35,7 @@ constexpr int LS_COLS = LS_ROWS + kTaps - 1;   // 287 unknowns
 constexpr int LS_PER = 9;                      // elements per lane (32 * 9 >= 287)
 constexpr int LS_WARPS = 4;                    // warps (phases) per block (3 blocks per SM)
 constexpr int LS_PAD = 16;                     // zero guard before / after a vector in smem
+constexpr int kLsmrLag = kPrefix;              // output row i is frame i - 16 of the block
 
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
@@ -241,6 +245,86 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
   }
 }
 
+// Noise level of the LSMR series per (stream, phase): one warp per row of F
+// samples (contiguous, phase-major), FP64 sum of |x|^2 / 2 in a fixed order,
+// then the running update of the FIR path.
+__global__ void __launch_bounds__(256) k_lsmr_sigma(const float2* __restrict__ xhat, long long F,
+                                                    double alpha, double k_sigma,
+                                                    const long long* __restrict__ blk,
+                                                    double* __restrict__ sigma2,
+                                                    float* __restrict__ theta2, long long rows) {
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;   // j * M + p
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;                                     // whole warps
+  const float2* row = xhat + r * F;
+  // 8 loads in flight per lane (F is a multiple of 256), partial sums in FP32
+  // over 8 samples, FP64 across them
+  double acc = 0.0;
+  for (long long i0 = lane; i0 < F; i0 += 32 * 8) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldg(row + i0 + 32 * u);
+    float part = 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) part = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, part));
+    acc += (double)part;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) {
+    const double pi = 0.5 * acc / (double)F;
+    const double s2 = *blk == 0 ? pi : (1.0 - alpha) * sigma2[r] + alpha * pi;
+    sigma2[r] = s2;
+    theta2[r] = (float)(k_sigma * k_sigma * s2);
+  }
+}
+
+// Trigger on the LSMR series: |x|^2 > theta2[j][p] for samples n >= 0,
+// n = (block F + i - 16) M + p; warp-ballot compaction into the trigger list.
+__global__ void __launch_bounds__(256) k_lsmr_trigger(const float2* __restrict__ xhat, long long F,
+                                                      const float* __restrict__ theta2,
+                                                      float k_sigma,
+                                                      const long long* __restrict__ blk, int P,
+                                                      int Tr, long long j0,
+                                                      TriggerRec* __restrict__ trig,
+                                                      unsigned long long* __restrict__ count,
+                                                      long long cap) {
+  const int p = blockIdx.y;
+  const long long j = j0 + blockIdx.z;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const long long r = j * kM + p;
+  const float th2 = theta2[r];
+  const long long n = (*blk * F + i - kLsmrLag) * kM + p;
+  bool hit = false;
+  float e2 = 0.f;
+  if (i < F) {
+    const float2 v = xhat[r * F + i];
+    e2 = v.x * v.x + v.y * v.y;
+    hit = n >= 0 && e2 > th2;
+  }
+  const unsigned mask = __ballot_sync(0xffffffffu, hit);
+  if (!mask) return;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (hit) {
+    const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
+    if ((long long)idx < cap) {
+      TriggerRec rec;
+      rec.n = n;
+      rec.pol = (int)(j % P);
+      rec.tec = (int)((j / P) % Tr);
+      rec.beam = (int)(j / ((long long)P * Tr));
+      rec.stream = (int)j;
+      rec.env = sqrtf(e2);
+      rec.sigma = sqrtf(th2) / k_sigma;
+      trig[idx] = rec;
+    }
+  }
+}
+
 }  // namespace
 
 int lsmr_window() { return LS_W; }
@@ -258,6 +342,21 @@ cudaError_t launch_lsmr(const lp_plan& p, cudaStream_t s) {
     k_lsmr<<<dim3((unsigned)(kM / LS_WARPS * n_win), nj), LS_WARPS * 32, 0, s>>>(
         p.buf.zt, p.buf.proto, p.buf.filter_sums, nfr, sh.F, n_win, p.cfg.lsmr_iters, j0,
         p.buf.xhat);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lsmr_trigger(const lp_plan& p, cudaStream_t s) {
+  const auto& sh = p.shape;
+  const long long rows = (long long)sh.J() * kM;
+  k_lsmr_sigma<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(
+      p.buf.xhat, sh.F, p.cfg.sigma_alpha, p.cfg.k_sigma, p.buf.blk, p.buf.lsmr_sigma2,
+      p.buf.lsmr_theta2, rows);
+  for (long long j0 = 0; j0 < sh.J(); j0 += 65535) {
+    const unsigned nj = (unsigned)std::min<long long>(65535, sh.J() - j0);
+    k_lsmr_trigger<<<dim3((unsigned)((sh.F + 255) / 256), kM, nj), 256, 0, s>>>(
+        p.buf.xhat, sh.F, p.buf.lsmr_theta2, (float)p.cfg.k_sigma, p.buf.blk, sh.P, sh.Tr, j0,
+        p.buf.trig, p.buf.trig_count, p.cfg.trigger_cap);
   }
   return cudaGetLastError();
 }

@@ -66,6 +66,8 @@ size_t carve(lp_plan& p, char* base) {
   const bool lsmr = p.cfg.inversion == LP_INV_LSMR;
   b.zt = lsmr ? (float2*)take(sizeof(float2) * (size_t)J * kM * (sh.F + lp::kPrefix)) : nullptr;
   b.xhat = lsmr ? (float2*)take(sizeof(float2) * (size_t)J * kM * sh.F) : nullptr;
+  b.lsmr_sigma2 = lsmr ? (double*)take(sizeof(double) * (size_t)J * kM) : nullptr;
+  b.lsmr_theta2 = lsmr ? (float*)take(sizeof(float) * (size_t)J * kM) : nullptr;
   b.power_part = (float*)take(sizeof(float) * (size_t)J * sh.K * p.n_ftiles_bf);
   b.sigma2 = (double*)take(sizeof(double) * J);
   b.theta = (float*)take(sizeof(float) * J);
@@ -610,7 +612,7 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, T
                               : lp::launch_beamform_f32(*p, xd, stride, s);
       prof_mark(p, LP_STAGE_BEAMFORM, 1, s);
       prof_mark(p, LP_STAGE_SIGMA, 0, s);
-      if (e == cudaSuccess) e = lp::launch_sigma(*p, s);
+      if (e == cudaSuccess && p->cfg.inversion == LP_INV_FIR) e = lp::launch_sigma(*p, s);
       prof_mark(p, LP_STAGE_SIGMA, 1, s);
       if (p->cfg.fine_dedisp) {
         prof_mark(p, LP_STAGE_FINE, 0, s);
@@ -618,10 +620,12 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, T
         prof_mark(p, LP_STAGE_FINE, 1, s);
       }
       prof_mark(p, LP_STAGE_SYNTH, 0, s);
-      if (e == cudaSuccess)
-        e = p->cfg.inversion == LP_INV_LSMR ? lp::launch_lsmr(*p, s)
-            : tune == kTuneSynth            ? tune_ippf(p, c, s, tune_ms)
-                                            : lp::launch_ippf(*p, c, s);
+      if (e == cudaSuccess && p->cfg.inversion == LP_INV_LSMR) {
+        e = lp::launch_lsmr(*p, s);
+        if (e == cudaSuccess) e = lp::launch_lsmr_trigger(*p, s);
+      } else if (e == cudaSuccess) {
+        e = tune == kTuneSynth ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
+      }
       prof_mark(p, LP_STAGE_SYNTH, 1, s);
       prof_mark(p, LP_STAGE_SHIFT, 0, s);
       if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
@@ -753,9 +757,34 @@ lp_status lp_get_sigma(lp_plan* p, double* out) {
   if (set_device(p) != LP_OK) return LP_ERR_CUDA;
   if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
   const int J = p->shape.J();
+  if (p->buf.lsmr_sigma2) {
+    // LSMR inversion: the RMS over phases of the per-phase levels
+    std::vector<double> s2((size_t)J * kM);
+    LP_CUDA(p, cudaMemcpy(s2.data(), p->buf.lsmr_sigma2, sizeof(double) * s2.size(),
+                          cudaMemcpyDeviceToHost));
+    for (int j = 0; j < J; ++j) {
+      double acc = 0.0;
+      for (int q = 0; q < kM; ++q) acc += s2[(size_t)j * kM + q];
+      out[j] = std::sqrt(acc / kM);
+    }
+    return LP_OK;
+  }
   std::vector<double> s2(J);
   LP_CUDA(p, cudaMemcpy(s2.data(), p->buf.sigma2, sizeof(double) * J, cudaMemcpyDeviceToHost));
   for (int j = 0; j < J; ++j) out[j] = std::sqrt(s2[j]);
+  return LP_OK;
+}
+
+lp_status lp_get_lsmr_sigma(lp_plan* p, double* out) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!out) return fail(p, LP_ERR_ARG, "null output");
+  if (!p->buf.lsmr_sigma2) return fail(p, LP_ERR_STATE, "the plan does not use the LSMR inversion");
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
+  const size_t n = (size_t)p->shape.J() * kM;
+  std::vector<double> s2(n);
+  LP_CUDA(p, cudaMemcpy(s2.data(), p->buf.lsmr_sigma2, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < n; ++i) out[i] = std::sqrt(s2[i]);
   return LP_OK;
 }
 
@@ -770,6 +799,8 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
     LP_CUDA(p, cudaMemsetAsync(p->buf.beams_fine, 0,
                                sizeof(float2) * (size_t)sh.J() * sh.K * p->row(), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.sigma2, 0, sizeof(double) * sh.J(), s));
+  if (p->buf.lsmr_sigma2)
+    LP_CUDA(p, cudaMemsetAsync(p->buf.lsmr_sigma2, 0, sizeof(double) * sh.J() * kM, s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.blk, 0, sizeof(long long), s));
   p->last_stream = s;
@@ -783,8 +814,10 @@ int lp_launches_per_block(const lp_plan* p) {
   if (!p) return 4;
   const long long rows = (long long)p->shape.J() * p->shape.K;
   const int fine = p->cfg.fine_dedisp ? (int)((rows + 65534) / 65535) : 0;
-  if (p->cfg.inversion == LP_INV_LSMR)   // inverse FFT + LSMR per 65535 streams
-    return 3 + fine + 2 * (int)((p->shape.J() + 65534) / 65535);
+  if (p->cfg.inversion == LP_INV_LSMR) {  // beamformer, inverse FFT + LSMR + trigger per
+    const int nj = (int)((p->shape.J() + 65534) / 65535);   // 65535 streams, sigma, shift
+    return 3 + fine + 3 * nj;
+  }
   if (p->fc == 0 || p->fc == p->shape.F) return 4 + fine;
   return 2 + 3 * (int)(p->shape.F / p->fc);
 }

@@ -68,6 +68,8 @@ struct Buffers {
   float4* fine_taps;       // [K][Tr][kFineTaps] (r.re, r.re, -r.im, r.im), or null
   float2* zt;              // LSMR inversion: [J][M][F + 16] windowed sums, phase-major, or null
   float2* xhat;            // LSMR inversion: [J][M][F] recovered analytic series, or null
+  double* lsmr_sigma2;     // LSMR inversion: [J][M] running noise variance per phase
+  float* lsmr_theta2;      // LSMR inversion: [J][M] (k_sigma sigma)^2
   float* power_part;       // [J][K][n_ftiles] partial sums of |beam|^2
   double* sigma2;          // [J]
   float* theta;            // [J] k_sigma * sigma
@@ -175,6 +177,7 @@ cudaError_t launch_fine_taps(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_fine(const lp_plan& p, cudaStream_t s, PolSel ps = {});
 // PPF inversion by windowed LSMR (replaces the synthesis and the trigger)
 cudaError_t launch_lsmr(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_lsmr_trigger(const lp_plan& p, cudaStream_t s);
 int lsmr_window();
 // the rows the synthesis reads: the filtered ones when fine de-dispersion is on
 inline const float2* synth_rows(const lp_plan& p);

@@ -79,6 +79,7 @@ SIGNATURES = {
     "lp_get_timeseries": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "lp_get_beams": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "lp_get_sigma": (ctypes.c_int, [_P, _P]),
+    "lp_get_lsmr_sigma": (ctypes.c_int, [_P, _P]),
     "lp_reset_stream": (ctypes.c_int, [_P, _P]),
     "lp_launches_per_block": (ctypes.c_int, [_P]),
     "lp_plan_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
@@ -273,6 +274,12 @@ class Plan:
     def lp_get_sigma(self):
         out = np.empty(self.n_streams, dtype=np.float64)
         self._check(_lib.lp_get_sigma(self._h, out.ctypes.data), "lp_get_sigma")
+        return out
+
+    def lp_get_lsmr_sigma(self):
+        """Per-phase noise levels of the LSMR series, [n_streams, 1024]."""
+        out = np.empty((self.n_streams, 1024), dtype=np.float64)
+        self._check(_lib.lp_get_lsmr_sigma(self._h, out.ctypes.data), "lp_get_lsmr_sigma")
         return out
 
     def lp_reset_stream(self, stream=None):

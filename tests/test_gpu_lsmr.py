@@ -19,50 +19,75 @@ pytestmark = pytest.mark.gpu
 TOL_LSMR = 1e-5
 
 
-def _oracle_series(blocks, enu, dirs, tec, fb, P, K, B, Tr, F):
-    """Re of the LSMR series per block and stream [J, F*M], carrying 16 frames."""
+def _oracle_series(blocks, enu, dirs, tec, fb, P, K, B, Tr, F, k_sigma=6.0, alpha=0.25):
+    """Per block: the LSMR series per stream [J, F, M], its per-phase noise
+    levels [J, M] (running update) and the set of triggers {(j, n)}."""
     nu = O.sky_frequencies(fb, K)
     w = O.geometric_weights(nu, enu, dirs)
     d = O.dedispersion_weights(nu, tec, 0.5 * (nu[0] + nu[-1]))
     h = O.prototype_filter()
     J = B * Tr * P
     hist = np.zeros((J, O.LSMR_OVERLAP, K), dtype=complex)
+    s2 = None
     out = []
-    for xb in blocks:
+    for bi, xb in enumerate(blocks):
         xc = xb[..., 0].astype(np.float64) + 1j * xb[..., 1]
         bm = O.beamform(xc, w, d)                                # [B, Tr, P, K, F]
-        ys = np.zeros((J, F * O.M))
+        xs = np.zeros((J, F, O.M), dtype=complex)
         for b in range(B):
             for t in range(Tr):
                 for p in range(P):
                     j = (b * Tr + t) * P + p
                     fr = np.concatenate([hist[j], bm[b, t, p].T])
-                    ys[j] = O.lsmr_invert(fr, fb, h).real.reshape(-1)
+                    xs[j] = O.lsmr_invert(fr, fb, h)
                     hist[j] = fr[-O.LSMR_OVERLAP:]
-        out.append(ys)
+        pw = np.stack([O.lsmr_noise_power(xs[j]) for j in range(J)])
+        s2 = O.update_sigma2(s2, pw, alpha, bi == 0)
+        sig = np.sqrt(s2)
+        n = ((bi * F + np.arange(F) - O.LSMR_OVERLAP)[:, None] * O.M + np.arange(O.M)[None, :])
+        trig = set()
+        for j in range(J):
+            hit = (np.abs(xs[j]) > k_sigma * sig[j][None, :]) & (n >= 0)
+            trig |= {(j, int(v)) for v in n[hit]}
+        out.append((xs, sig, trig, n))
     return out
+
+
+def _check_lsmr_triggers(gpu_trig, xs, sig, trig, n, k_sigma, tau):
+    """Triggers equal except samples within tau of their per-phase threshold."""
+    got = {(int(r["stream"]), int(r["n"])) for r in gpu_trig}
+    first = int(n[0, 0])
+    for (j, nn) in got ^ trig:
+        i, p = divmod(nn - first, O.M)
+        th = k_sigma * sig[j, p]
+        assert abs(abs(xs[j, i, p]) - th) <= tau * th, (j, nn)
+    return len(got), len(trig)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_lsmr_inversion_matches_oracle(cuda_lib, precision):
-    """Two blocks of two windows each (history across the block boundary)."""
-    S, P, K, B, Tr, F, fb = 8, 1, 12, 2, 1, 512, 200
+    """Two blocks of two windows each (history across the block boundary): the
+    series, the per-phase noise levels (running update) and the triggers."""
+    S, P, K, B, Tr, F, fb, ks = 8, 1, 12, 2, 1, 512, 200, 3.5
     blocks, enu, dirs, tec = random_case(51, S, P, K, B, Tr, F, fb, "int8", 2, amp=60)
     plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision=precision,
-                     inversion="lsmr")
-    assert plan.lp_launches_per_block() == 5
+                     inversion="lsmr", k_sigma=ks)
+    assert plan.lp_launches_per_block() == 6
     plan.lp_set_weights(enu, dirs)
     plan.lp_set_tec(tec)
-    want = _oracle_series(blocks, enu, dirs, tec, fb, P, K, B, Tr, F)
+    want = _oracle_series(blocks, enu, dirs, tec, fb, P, K, B, Tr, F, k_sigma=ks)
     import torch
-    for xb, ys in zip(blocks, want):
+    tol = TOL_LSMR if precision == "fp32" else TOL_TS_FP16
+    for xb, (xs, sig, trig, n) in zip(blocks, want):
         plan.lp_process_block(torch.from_numpy(xb).cuda())
         got = np.stack([plan.lp_get_timeseries(b, 0, 0) for b in range(B)])
-        tol = TOL_LSMR if precision == "fp32" else TOL_TS_FP16
-        assert rel_rms(got, ys) < tol
-        trig, n, st = plan.lp_get_triggers()
-        assert n == 0                                     # no trigger on this path
-        assert np.all(plan.lp_get_sigma() > 0)
+        assert rel_rms(got, xs.real.reshape(B, -1)) < tol
+        np.testing.assert_allclose(plan.lp_get_lsmr_sigma(), sig, rtol=10 * tol)
+        np.testing.assert_allclose(plan.lp_get_sigma(), np.sqrt(np.mean(sig ** 2, axis=1)),
+                                   rtol=10 * tol)
+        g_trig, n_total, st = plan.lp_get_triggers()
+        ng, no = _check_lsmr_triggers(g_trig, xs, sig, trig, n, ks, 10 * tol)
+        assert no > 0
 
 
 def test_lsmr_iterations_and_limits(cuda_lib):
