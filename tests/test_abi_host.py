@@ -138,3 +138,69 @@ def test_prebeam_validates_shape_and_groups_before_any_cuda_call(lib):
     n = ctypes.c_int64(5)
     assert c.lp_prebeam_saturated(h, ctypes.byref(n)) == lib.LP_OK and n.value == 0
     c.lp_prebeam_destroy(h)
+
+
+def _workspace(lib, shape, **fields):
+    st, h = _create(lib, *shape)
+    assert st == lib.LP_OK
+    c = lib.config_default()
+    c.first_bin = 100
+    for k, v in fields.items():
+        setattr(c, k, v)
+    st = lib._lib.lp_plan_configure(h, ctypes.byref(c))
+    n = ctypes.c_size_t()
+    if st == lib.LP_OK:
+        assert lib._lib.lp_plan_workspace_bytes(h, ctypes.byref(n)) == lib.LP_OK
+    err = lib._lib.lp_last_error(h)
+    lib._lib.lp_plan_destroy(h)
+    return st, n.value, err
+
+
+def test_fine_and_lsmr_options_validate_and_size_the_workspace(lib):
+    """Host-side checks of the optional paths: their options are validated and
+    the workspace grows by exactly their buffers (256-byte aligned pieces)."""
+    S, P, K, B, Tr, F = 6, 2, 16, 2, 3, 512
+    shape = (S, P, K, B, Tr, F)
+    J = B * Tr * P
+    st, base, _ = _workspace(lib, shape)
+    assert st == lib.LP_OK
+    # fine de-dispersion: a second beam-row buffer and 17 taps per (subband, trial)
+    st, fine, _ = _workspace(lib, shape, fine_dedisp=1)
+    assert st == lib.LP_OK
+    rows = J * K * (F + 16) * 8
+    taps = K * Tr * 17 * 16
+    assert 0 <= fine - base - rows - taps < 3 * 256
+    # LSMR: phase-major windowed sums, the series, per-phase noise levels
+    st, lsmr, _ = _workspace(lib, shape, inversion=lib.LP_INV_LSMR)
+    assert st == lib.LP_OK
+    extra = J * 1024 * (F + 16) * 8 + J * 1024 * F * 8 + J * 1024 * (8 + 4)
+    assert 0 <= lsmr - base - extra < 5 * 256
+    for bad in [dict(fine_dedisp=2), dict(inversion=2),
+                dict(inversion=lib.LP_INV_LSMR, lsmr_iters=0),
+                dict(inversion=lib.LP_INV_LSMR, lsmr_iters=1001),
+                dict(fine_dedisp=1, precision=lib.LP_PREC_FP16, chunk_frames=2048)]:
+        st, _, err = _workspace(lib, (8, 1, 4, 1, 1, 4096), **bad)
+        assert st == lib.LP_ERR_ARG, bad
+        assert err
+    # LSMR windows need block_len a multiple of 256
+    st, _, err = _workspace(lib, (S, P, K, B, Tr, 264), inversion=lib.LP_INV_LSMR)
+    assert st == lib.LP_ERR_ARG and b"256" in err
+    st, _, _ = _workspace(lib, (8, 1, 4, 1, 1, 4096), inversion=lib.LP_INV_LSMR,
+                          precision=lib.LP_PREC_FP16, chunk_frames=2048)
+    assert st == lib.LP_ERR_ARG
+
+
+def test_launch_counts_of_the_paths(lib):
+    """lp_launches_per_block is host arithmetic: 4 kernels for a device block,
+    one more with the fine filter, six with the LSMR inversion."""
+    for fields, want in [({}, 4), ({"fine_dedisp": 1}, 5),
+                         ({"inversion": lib.LP_INV_LSMR}, 6),
+                         ({"inversion": lib.LP_INV_LSMR, "fine_dedisp": 1}, 7)]:
+        st, h = _create(lib, 6, 2, 16, 2, 1, 512)
+        c = lib.config_default()
+        c.first_bin = 100
+        for k, v in fields.items():
+            setattr(c, k, v)
+        assert lib._lib.lp_plan_configure(h, ctypes.byref(c)) == lib.LP_OK
+        assert lib._lib.lp_launches_per_block(h) == want, fields
+        lib._lib.lp_plan_destroy(h)
