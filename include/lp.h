@@ -194,7 +194,10 @@ lp_status lp_get_triggers(lp_plan* plan, lp_trigger* out, int64_t cap,
                           int64_t* n_total);
 
 /* Synchronise and copy y = Re u of one stream for the last block, F*1024
- * floats to host memory (store_timeseries = 1 only). */
+ * floats to host memory, sample (m - 15) M + p of frame m at [m M + p]
+ * (store_timeseries = 1 only).  With the LSMR inversion: the real part of the
+ * recovered series, sample (m - 16) M + p at [m M + p] (always kept).
+ * LP_ERR_STATE when no series is kept. */
 lp_status lp_get_timeseries(lp_plan* plan, int beam, int tec, int pol,
                             float* out_host);
 
@@ -254,8 +257,11 @@ lp_status lp_plan_autotune_gemm(lp_plan* plan, const void* x, void* stream, int3
                                 double* ms_out);
 
 /* Number of kernel launches lp_process_block makes for a device block (for
- * accounting: 4, or 5 with fine_dedisp); a host block processed per
- * polarisation makes twice that. */
+ * accounting): 4 (beamformer, noise level, synthesis, history shift), one more
+ * with fine_dedisp, 6 with the LSMR inversion (beamformer, inverse FFT, LSMR,
+ * noise level, trigger, history shift); the fine filter adds a launch and the
+ * LSMR kernels three per 65535 rows / streams beyond the first.  A host block
+ * processed per polarisation makes twice the FIR-path count. */
 int lp_launches_per_block(const lp_plan* plan);
 
 /* Stage timing.  When enabled, lp_process_block records a CUDA event pair
