@@ -15,9 +15,10 @@
 // k_fine_taps: one warp per (subband, trial); FP64 arguments and sums.
 // k_fine: one 4-warp block per (stream, subband, 1024 frames) (the index
 // arithmetic of a block is four 32-bit divisions); the frames (and the 16
-// before them) are copied by cp.async, all at once, into shared memory in rows of 8 frames padded to
-// 20 words, so that both the 16-byte stores and each thread's 16-byte reads of
-// three consecutive rows are conflict-free; a thread filters 8 consecutive
+// before them) are copied by cp.async, all at once, into shared memory in
+// rows of 8 frames padded to 20 words, so that both the 16-byte copies and
+// each thread's 16-byte reads of three consecutive rows are conflict-free; a
+// thread filters 8 consecutive
 // frames from a 24-frame window in registers, two packed FFMA2 per tap and
 // frame with the taps as (r.re, r.re, -r.im, r.im).  HBM-bound: 8 bytes in and
 // 8 out per bin-frame, 136 FLOP.
