@@ -29,6 +29,8 @@ namespace {
 
 constexpr int ZT_FR = 4;                       // frames per k_zt block
 constexpr int ZT_NTH = 256;
+constexpr int ZT_LD = kM + 4;                  // padded frame stride: the 4 frames' elements
+                                               // p fall in different banks
 constexpr int LS_W = 256;                      // unknowns kept per window
 constexpr int LS_ROWS = LS_W + kPrefix;        // 272 equations
 constexpr int LS_COLS = LS_ROWS + kTaps - 1;   // 287 unknowns
@@ -42,17 +44,17 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __global__ void __launch_bounds__(ZT_NTH) k_zt(const float2* __restrict__ rows, int K,
                                                int first_bin, long long row, long long nfr,
                                                float2* __restrict__ zt) {
-  __shared__ float2 zs[ZT_FR * kM];
+  __shared__ float2 zs[ZT_FR * ZT_LD];
   const long long j = blockIdx.y;
   const long long f0 = (long long)blockIdx.x * ZT_FR;        // row position (frame + 16)
   const int tid = threadIdx.x;
-  for (int i = tid; i < ZT_FR * kM; i += ZT_NTH) zs[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < ZT_FR * ZT_LD; i += ZT_NTH) zs[i] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int i = tid; i < ZT_FR * K; i += ZT_NTH) {
     const int f = i % ZT_FR, k = i / ZT_FR;
     const float2 v = rows[(j * K + k) * row + f0 + f];
     const int pos = (int)(__brev((unsigned)(first_bin + k)) >> 22);   // 10-bit reversal
-    zs[f * kM + pos] = make_float2(2.f * v.x, 2.f * v.y);
+    zs[f * ZT_LD + pos] = make_float2(2.f * v.x, 2.f * v.y);
   }
   __syncthreads();
   for (int s = 0; s < 10; ++s) {                             // half-size 2^s
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(ZT_NTH) k_zt(const float2* __restrict__ rows, 
     for (int b = tid; b < ZT_FR * (kM / 2); b += ZT_NTH) {
       const int f = b >> 9, bb = b & 511;
       const int pos = bb & (hs - 1);
-      const int i0 = f * kM + ((bb >> s) << (s + 1)) + pos, i1 = i0 + hs;
+      const int i0 = f * ZT_LD + ((bb >> s) << (s + 1)) + pos, i1 = i0 + hs;
       float sn, cs;
       sincospif((float)pos / (float)hs, &sn, &cs);           // exp(+2 pi i pos / 2 hs)
       const float2 x0 = zs[i0], x1 = zs[i1];
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(ZT_NTH) k_zt(const float2* __restrict__ rows, 
   constexpr float inv_m = 1.0f / kM;
   for (int i = tid; i < ZT_FR * kM; i += ZT_NTH) {
     const int f = i % ZT_FR, p = i / ZT_FR;
-    const float2 v = zs[f * kM + p];
+    const float2 v = zs[f * ZT_LD + p];
     zt[(j * kM + p) * nfr + f0 + f] = make_float2(v.x * inv_m, v.y * inv_m);
   }
 }
