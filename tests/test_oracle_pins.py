@@ -451,6 +451,31 @@ def test_fine_dedispersion_recovers_at_least_the_subband_phase_result():
         assert abs(n_peak - (n0 + tau_ref * O.FS_HZ + O.FINE_DELAY * O.M)) < 30
 
 
+def test_pipeline_fine_mode_at_zero_tec_is_the_plain_pipeline_delayed():
+    """At TEC 0 the fine filter is the unit impulse at 8 frames, so over two
+    blocks (history carried) the fine pipeline's series is the plain one's,
+    8 frames (8192 samples) later, and the noise levels are the same."""
+    S, P, K, B, Tr, F, fb = 3, 1, 5, 1, 1, 24, 220
+    rng = np.random.default_rng(23)
+    x = rng.integers(-40, 41, size=(P, K, 2 * F, S, 2))
+    enu = synth.station_positions(S, 4)
+    dirs = synth.pointing_enu()[None]
+    tec = np.array([0.0])
+    plain = O.Pipeline(S, P, K, B, Tr, F, fb, enu, dirs, tec)
+    fine = O.Pipeline(S, P, K, B, Tr, F, fb, enu, dirs, tec, fine_dedispersion=True)
+    yp, yf = [], []
+    for i in range(2):
+        blk = x[:, :, i * F:(i + 1) * F]
+        op, of = plain.process_block(blk), fine.process_block(blk)
+        np.testing.assert_array_equal(op["sigma"], of["sigma"])
+        yp.append(op["y"][0])
+        yf.append(of["y"][0])
+    yp, yf = np.concatenate(yp), np.concatenate(yf)
+    d = O.FINE_DELAY * O.M
+    np.testing.assert_allclose(yf[d:], yp[:-d], rtol=0, atol=1e-12 * np.abs(yp).max())
+    assert np.abs(yf[:d]).max() <= 1e-12 * np.abs(yp).max()     # taps exact to rounding
+
+
 def test_pipeline_fine_mode_equals_its_definition():
     """Pipeline with the fine filter: two blocks equal the per-stream definition
     (beamform, D, filter with zero history, synthesis) on the concatenated block."""
