@@ -93,22 +93,18 @@ def test_calls_before_bind_report_state_errors(lib):
     assert lib._lib.lp_process_block(h, None, None) == lib.LP_ERR_STATE
     # workspace size needs a configuration first
     assert lib._lib.lp_plan_workspace_bytes(h, ctypes.byref(ctypes.c_size_t())) == lib.LP_ERR_STATE
+    # the autotuners, the configuration list and the LSMR levels need a bound plan
+    best = ctypes.c_int32()
+    assert lib._lib.lp_plan_gemm_configs(h, None, 0) == -1
+    assert lib._lib.lp_plan_set_gemm_config(h, 0) == lib.LP_ERR_STATE
+    assert lib._lib.lp_plan_autotune_gemm(h, None, None, ctypes.byref(best), None) == lib.LP_ERR_STATE
+    assert lib._lib.lp_plan_autotune(h, None, None, ctypes.byref(best), None) == lib.LP_ERR_STATE
+    assert lib._lib.lp_get_lsmr_sigma(h, None) in (lib.LP_ERR_STATE, lib.LP_ERR_ARG)
+    out = (ctypes.c_double * 4)()
+    assert lib._lib.lp_get_lsmr_sigma(h, out) == lib.LP_ERR_STATE
+    assert lib._lib.lp_get_sigma(h, out) == lib.LP_ERR_STATE
+    assert lib._lib.lp_plan_autotune_gemm(h, None, None, None, None) == lib.LP_ERR_ARG
     lib._lib.lp_plan_destroy(h)
-
-
-def test_serving_requests_and_workspace_sizes(lib):
-    from paper_1612_06592_gb300.serve import make_requests, workspace_bytes
-    reqs = make_requests(4, 200)
-    assert len(reqs) > 40
-    for r in reqs:
-        assert 1 <= len(r.beams) <= 50 and len(set(r.beams.tolist())) == len(r.beams)
-        assert 122 <= r.nsub <= 488 and 0 <= r.k0 and r.k0 + r.nsub <= 488
-        assert 1 <= len(r.tec) <= 4 and (5.0 <= r.tec).all() and (r.tec <= 40.0).all()
-    assert make_requests(4, 200)[7].beams.tolist() == reqs[7].beams.tolist()
-    small = workspace_bytes(48, 2, 122, 1, 1, 65536, 12)
-    big = workspace_bytes(48, 2, 488, 50, 4, 65536, 12)
-    # the beam intermediate (streams x subbands x (F + 16) complex floats) dominates
-    assert big > 400 * 488 * 65552 * 8 > small
 
 
 def test_prebeam_validates_shape_and_groups_before_any_cuda_call(lib):
