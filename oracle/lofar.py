@@ -33,7 +33,7 @@ __all__ = [
     "Pipeline", "stream_window", "brute_force_stream",
     "INT16_MAX", "group_centres", "prebeam_weights", "prebeam", "transport_int16",
     "FINE_TAPS", "FINE_DELAY", "FINE_BETA", "FINE_GRID", "fine_dedispersion_taps",
-    "fine_dedisperse",
+    "fine_dedisperse", "fullrate_dedisperse",
 ]
 
 # Sec. 2: antennas are sampled every 5 ns  ->  fs = 200 MHz.
@@ -212,6 +212,25 @@ def fine_dedisperse(frames_ext: np.ndarray, r_k: np.ndarray) -> np.ndarray:
     for q in range(taps):
         out += r_k[None, :, q] * frames_ext[taps - 1 - q: taps - 1 - q + F]
     return out
+
+
+def fullrate_dedisperse(u: np.ndarray, tec_tecu: float, nu_ref_hz: float) -> np.ndarray:
+    """De-dispersion of a recovered 200 MHz analytic series at full resolution
+    (Sec. 3, third paragraph, in the paper's order: after the PPF inversion).
+
+    The series' frequency f (cycles per sample, the band lies in f >= 0) is the
+    sky frequency nu = fs/2 + f fs; its spectrum is multiplied by
+    exp(-2 pi i phi(nu)) with phi from ``dedispersion_cycles`` (zero phase for
+    f < 0, where an analytic series has no content).  The whole series is one
+    discrete Fourier transform (a library FFT as a step): circular, so the
+    series must extend past the dispersion span on both sides.  Reference for
+    the loss table of the de-dispersion chains; no GPU path computes it."""
+    u = np.asarray(u, dtype=np.complex128)
+    f = np.fft.fftfreq(u.size)
+    phi = np.zeros(u.size)
+    pos = f >= 0
+    phi[pos] = dedispersion_cycles(NU0_HZ + f[pos] * FS_HZ, [tec_tecu], nu_ref_hz)[:, 0]
+    return np.fft.ifft(np.fft.fft(u) * np.exp(-2j * np.pi * phi))
 
 
 # --------------------------------------------------------------------------

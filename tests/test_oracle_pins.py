@@ -451,6 +451,30 @@ def test_fine_dedispersion_recovers_at_least_the_subband_phase_result():
         assert abs(n_peak - (n0 + tau_ref * O.FS_HZ + O.FINE_DELAY * O.M)) < 30
 
 
+def test_fullrate_dedispersion_undoes_the_dispersion_up_to_the_reference_delay():
+    """A band-limited analytic pulse dispersed by exp(+2 pi i A / nu) comes back
+    as the same pulse delayed by A / nu_ref^2 with a constant phase (closed
+    form: A / nu - phi(nu) = A (2 / nu_ref - nu / nu_ref^2) cycles, and with
+    nu = fs/2 + f fs the constant is A (2 / nu_ref - (fs/2) / nu_ref^2)); at
+    TEC 0 the transform is the identity."""
+    N = 1 << 14
+    f = np.fft.fftfreq(N)
+    band = (f > 0.1) & (f < 0.35)
+    rng = np.random.default_rng(30)
+    spec = np.where(band, rng.normal(size=N) + 1j * rng.normal(size=N), 0)
+    x = np.fft.ifft(spec)
+    nu = np.where(band, O.NU0_HZ + f * O.FS_HZ, O.NU0_HZ)    # outside the band: unused
+    tec, nu_ref = 30.0, 150e6
+    a = O.dispersion_coefficient_hz(tec)
+    disp = np.fft.ifft(spec * np.exp(np.where(band, 2j * np.pi * a / nu, 0)))
+    got = O.fullrate_dedisperse(disp, tec, nu_ref)
+    delay = a / nu_ref ** 2 * O.FS_HZ                        # samples (fractional)
+    const = a * (2 / nu_ref - O.NU0_HZ / nu_ref ** 2)
+    want = np.fft.ifft(spec * np.exp(np.where(band, 2j * np.pi * (const - f * delay), 0)))
+    np.testing.assert_allclose(got, want, atol=1e-9 * np.abs(want).max())
+    np.testing.assert_allclose(O.fullrate_dedisperse(x, 0.0, nu_ref), x, atol=1e-15)
+
+
 def test_pipeline_fine_mode_at_zero_tec_is_the_plain_pipeline_delayed():
     """At TEC 0 the fine filter is the unit impulse at 8 frames, so over two
     blocks (history carried) the fine pipeline's series is the plain one's,
@@ -724,3 +748,20 @@ def test_two_stage_gain_table_reproduces():
     assert sizes == ref["group_sizes"]
     assert np.all(g <= 1 + 1e-12)
     np.testing.assert_allclose(g[:, np.argmin(offs)], 1.0, atol=1e-12)
+
+
+def test_dedispersion_chain_table_reproduces():
+    """The stored peak-recovery table of the de-dispersion chains is what the
+    oracle gives; the paper's order (LSMR, then full-rate) recovers the most."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "dedispersion_chains", os.path.join(GOLDEN, "dedispersion_chains.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    ref = json.load(open(os.path.join(GOLDEN, "dedispersion_chains.json")))
+    for case in ref["cases"]:
+        got = mod.chains(case["tec_tecu"], case["first_bin"], case["subbands"])
+        for k, v in case["peak_ratio"].items():
+            assert abs(got[k] - v) < 2e-4, (case["tec_tecu"], k)
+        assert got["LSMR + full-rate"] > 0.95
+        assert got["LSMR + full-rate"] > got["FIR + full-rate"] >= got["subband phase + FIR"]
