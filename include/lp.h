@@ -196,7 +196,9 @@ lp_status lp_get_triggers(lp_plan* plan, lp_trigger* out, int64_t cap,
 /* Synchronise and copy y = Re u of one stream for the last block, F*1024
  * floats to host memory, sample (m - 15) M + p of frame m at [m M + p]
  * (store_timeseries = 1 only).  With the LSMR inversion: the real part of the
- * recovered series, sample (m - 16) M + p at [m M + p] (always kept).
+ * recovered series, sample (m - 16) M + p at [m M + p] (always kept; the
+ * stream's complex series, stored phase-major on the device, passes through a
+ * temporary host buffer of F * 1024 * 8 bytes for the reordering).
  * LP_ERR_STATE when no series is kept. */
 lp_status lp_get_timeseries(lp_plan* plan, int beam, int tec, int pol,
                             float* out_host);
