@@ -23,9 +23,7 @@ import hashlib
 import json
 import re
 import os
-import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -53,11 +51,27 @@ def measured_peaks():
         return {}
 
 
+def fp32_peak():
+    """FP32 FMA peak (TFLOP/s, SM MHz it was measured at, note): the measurement of
+    the peak microbenchmark (profiles/fp32_peak.json) when recorded, else unit
+    counts at the maximum SM clock."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "fp32_peak.json")))
+        form = rec["forms"][rec["peak_form"]]
+        mhz = form["clocks"].get("sm_mhz")
+        return (float(rec["peak_tflops"]), mhz,
+                f"measured: {rec['peak_form'].upper()} chains on all SMs "
+                f"(python -m paper_1612_06592_gb300.microbench.peaks, median SM clock {mhz} MHz; "
+                f"{rec['reading']})")
+    except (OSError, ValueError, KeyError):
+        mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
+        return (SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, mhz,
+                f"unit counts: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {mhz:.0f} MHz "
+                "(no measurement recorded)")
+
+
 def fp32_peak_tflops():
-    """FP32 FMA peak from unit counts at the maximum SM clock (from the measured
-    peaks file when it records one)."""
-    peaks = measured_peaks()
-    return SMS * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    return fp32_peak()[0]
 
 
 def parse():
@@ -125,57 +139,7 @@ def workload_config(w, precision):
 
 # ------------------------------------------------------------ clocks -------
 
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
-        self.lines = []
-
-    def start(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-        except OSError:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
-    def stop(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": float(max(mx)) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+from paper_1612_06592_gb300.clocks import ClockSampler  # noqa: E402
 
 
 # ------------------------------------------------------------ inputs -------
@@ -369,8 +333,7 @@ def run_ours(args, rank, world, local_rank):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    alu_peak, alu_peak_mhz, alu_peak_note = fp32_peak()
     achieved = flop / (synth_ms / 1e3) / 1e12
     traffic = recorded_traffic("k_ippf.cu")
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -396,11 +359,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "k_ippf (inverse FFT + synthesis FIR + trigger)",
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
-                     "peak_note": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
-                                  f"{sm_max:.0f} MHz (max SM clock)",
+                     "peak_note": alu_peak_note,
                      "flop_per_sample": SYNTH_FLOP_PER_SAMPLE,
-                     "frac_at_sampled_clock": (achieved / (alu_peak * clk["sm_mhz"] / sm_max))
-                     if clk.get("sm_mhz") else None},
+                     "frac_at_sampled_clock": (achieved / (alu_peak * clk["sm_mhz"] / alu_peak_mhz))
+                     if clk.get("sm_mhz") and alu_peak_mhz else None},
         "roofline_beamform": {"bound": "hbm", "achieved": bf_gbs, "peak": hbm_peak,
                               "unit": "GB/s", "frac": bf_gbs / hbm_peak,
                               "bytes": in_bytes + beams_bytes,

@@ -1,8 +1,10 @@
-"""Build the CUDA library (sm_103a) in-tree: paper_1612_06592_gb300/_build/liblp.so.
+"""Build the CUDA libraries (sm_103a) in-tree under paper_1612_06592_gb300/_build/.
 
-Each .cu file is compiled by nvcc in parallel, then linked into one shared
-library with a plain C ABI (include/lp.h).  Rebuilds only when a source or
-header is newer than the library.
+liblp.so: the pipeline (csrc/*.cu) with the plain C ABI of include/lp.h.
+libmb.so: the peak microbenchmarks (microbench/*.cu) that measure the roofline
+denominators the repository reports against; not part of the pipeline.
+Each .cu file is compiled by nvcc in parallel; a library is rebuilt only when
+one of its sources or headers is newer than it.
 """
 
 from __future__ import annotations
@@ -18,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblp.so")
+MB_SRC = os.path.join(HERE, "microbench")
+MB_LIB = os.path.join(BUILD, "libmb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
@@ -39,11 +43,19 @@ def _deps():
         os.path.join(ROOT, "include", "lp.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def _mb_sources():
+    return sorted(glob.glob(os.path.join(MB_SRC, "*.cu")))
+
+
+def _fresh(lib, deps) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    t = os.path.getmtime(lib)
+    return all(os.path.getmtime(d) <= t for d in deps)
+
+
+def up_to_date() -> bool:
+    return _fresh(LIB, _deps()) and _fresh(MB_LIB, _mb_sources() + [os.path.abspath(__file__)])
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
@@ -51,11 +63,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    objs = []
+    objs, mb_objs = [], []
     cmds = []
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
+        cmds.append([nvcc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj])
+    for src in _mb_sources():
+        obj = os.path.join(BUILD, "mb_" + os.path.basename(src)[:-3] + ".o")
+        mb_objs.append(obj)
         cmds.append([nvcc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj])
 
     def run(cmd):
@@ -69,9 +85,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 4))) as ex:
         list(ex.map(run, cmds))
-    tmp = LIB + ".tmp"
-    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+    for lib, lib_objs in ((LIB, objs), (MB_LIB, mb_objs)):
+        tmp = lib + ".tmp"
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *lib_objs])
+        os.replace(tmp, lib)
     return LIB
 
 
