@@ -165,7 +165,13 @@ lp_status lp_set_weights(lp_plan* plan, const double* station_enu_m,
  * (nu_k nu_ref^2)), A_t = 40.308 * STEC_t * 1e16 / c, formed in FP64. */
 lp_status lp_set_tec(lp_plan* plan, const double* tec_tecu, void* stream);
 
-/* Process one block of station data, asynchronously on `stream`.
+/* Process one block of station data, asynchronously on `stream`: the whole
+ * realtime chain of Sec. 2 (last paragraph, Fig. 1) on one block -- station
+ * signals summed into beams with complex weights (Sec. 3, first paragraph),
+ * the STEC phase in the frequency domain (Sec. 3, third paragraph), the
+ * inverse FFT of the PPF inversion (Sec. 3, second paragraph) followed here by
+ * the 16-tap synthesis FIR, and the envelope trigger that would start the
+ * read-out of the transient buffers (Sec. 2, fourth paragraph).
  * x: [P][K][F][S][2] (re, im) int8 or int16, C order, host or device
  * pointer (host pointers need host_input = 1; the copy is part of the call).
  * Runs: beamform + de-disperse, block noise power and running sigma, inverse
@@ -185,16 +191,21 @@ lp_status lp_process_block(lp_plan* plan, const void* x, void* stream);
 lp_status lp_process_block_strided(lp_plan* plan, const void* x, int64_t pol_stride,
                                    void* stream);
 
-/* Synchronise and copy the triggers of the last processed block to host
- * memory `out` (capacity `cap`, may be NULL when cap == 0), sorted by
+/* The trigger read-out (Sec. 2, fourth paragraph: the recovered nanosecond
+ * signal is used only to trigger the read-out of the transient buffer boards;
+ * Fig. 1, last step).  Synchronise and copy the triggers of the last processed
+ * block to host memory `out` (capacity `cap`, may be NULL when cap == 0), sorted by
  * (beam, tec, pol, n).  *n_total receives the number found.  Returns
  * LP_ERR_OVERFLOW when *n_total exceeds cap or the device buffer (the first
  * min(cap, trigger_cap) records, in sorted order of those kept, are copied). */
 lp_status lp_get_triggers(lp_plan* plan, lp_trigger* out, int64_t cap,
                           int64_t* n_total);
 
-/* Synchronise and copy y = Re u of one stream for the last block, F*1024
- * floats to host memory, sample (m - 15) M + p of frame m at [m M + p]
+/* The recovered nanosecond-resolution series of one beam (Sec. 3, second
+ * paragraph: the inverse FFT of the filtered signal and the inversion of the
+ * PPF window; Sec. 2, fourth paragraph: the 5 ns time resolution the PPF had
+ * reduced to about 5 us).  Synchronise and copy y = Re u of one stream for the
+ * last block, F*1024 floats to host memory, sample (m - 15) M + p of frame m at [m M + p]
  * (store_timeseries = 1 only).  With the LSMR inversion: the real part of the
  * recovered series, sample (m - 16) M + p at [m M + p] (always kept; the
  * stream's complex series, stored phase-major on the device, passes through a
@@ -283,28 +294,35 @@ lp_status lp_profile_read(lp_plan* plan, double* total_ms, int64_t* blocks);
 #define LP_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 
 /* The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory (a host that owns the device heap or forbids
- * allocation once running, code that must not allocate during stream
- * capture) and so cannot bind a plan workspace.  It runs one block of the
- * FP32 form (beam weights and de-dispersion tables, beamforming, noise level,
- * synthesis and trigger) as the first block of a stream (zero history) and
- * allocates nothing: its scratch is a static device array of
- * LP_NOALLOC_SCRATCH_BYTES.
+ * cannot allocate device memory -- code running inside a host process that
+ * forbids device allocation once it is running (a real-time loop with a fixed
+ * memory budget) or that owns the device heap itself (a plug-in handed only
+ * the buffers its framework planned) -- and so cannot bind a plan workspace.
+ * It runs one block of the FP32 form (beam weights and de-dispersion tables,
+ * beamforming, noise level, synthesis and trigger) as the first block of a
+ * stream (zero history) and allocates nothing: its scratch is a static device
+ * array of LP_NOALLOC_SCRATCH_BYTES.
  *   Shape arguments as lp_plan_create; cfg as lp_plan_configure (precision
  *   must be LP_PREC_FP32; store_timeseries and host_input are ignored).
  *   station_enu_m [S][3], beam_dir [B][3], tec_tecu [Tr]: host doubles.
- *   x: device block [P][K][F][S][2] on the current device.
+ *   x: device block [P][K][F][S][2], aligned to one complex sample (2 bytes
+ *   int8, 4 bytes int16).
  *   y: device floats [J][F*1024], y = Re u of every stream (written).
  *   sigma2: device doubles [J] (written) or NULL: the block's sigma_y^2.
  *   triggers: device records, capacity trigger_cap (>= 0), unsorted;
  *   trigger_count: device counter (set to the number found) or NULL.
+ *   Every device argument must be device or managed memory of the current
+ *   device, aligned to its element type; otherwise LP_ERR_ARG before any
+ *   GPU work.
  *   err/errlen: optional host buffer for a message.
  * Returns LP_ERR_ARG, without touching the device, for a shape whose scratch
- * would exceed LP_NOALLOC_SCRATCH_BYTES.  Asynchronous on `stream`.  All
- * calls on a device share the scratch (it keeps the last call's contents;
- * the call clears what must start at zero), so calls whose GPU work overlaps
- * race and must be serialised by the caller.  The first call on a device
- * looks up the scratch address and must come before any stream capture. */
+ * would exceed LP_NOALLOC_SCRATCH_BYTES.  Asynchronous on `stream`; the host
+ * geometry arrays are copied from pageable memory, so they may be reused on
+ * return.  All calls on a device share the scratch (it keeps the last call's
+ * contents; the call clears what must start at zero), so calls whose GPU work
+ * overlaps race and must be serialised by the caller.  The first call on a
+ * device looks up the scratch address and should come before any stream
+ * capture. */
 lp_status lp_process_block_noalloc(int stations, int pols, int subbands, int beams,
                                    int tec_trials, int64_t block_len, const lp_config* cfg,
                                    const double* station_enu_m, const double* beam_dir,
@@ -341,11 +359,24 @@ typedef struct lp_prebeam lp_prebeam;
 lp_status lp_prebeam_create(lp_prebeam** out, int stations, int pols, int subbands,
                             int64_t block_len, int groups, int first_bin, int input_dtype);
 
+/* Device workspace of the preliminary-beam plan in bytes (weight table,
+ * member lists, saturation counter; sized for every station in a group).  Like
+ * the pipeline plan, lp_prebeam allocates no device memory: the caller
+ * allocates the workspace and binds it. */
+lp_status lp_prebeam_workspace_bytes(const lp_prebeam* pb, size_t* bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, >= the workspace bytes)
+ * on the device it lives on; clears the saturation counter on `stream`.  Once
+ * per plan (LP_ERR_STATE for a second bind); the caller frees the memory after
+ * lp_prebeam_destroy. */
+lp_status lp_prebeam_bind_workspace(lp_prebeam* pb, void* device_ptr, size_t bytes,
+                                    void* stream);
+
 /* group_of_station[S] in [-1, G) (-1: unused; every group needs a station),
  * station_enu[S][3] metres, group_dir[G][3] unit vectors (host arrays, read
- * before return).  Computes the phase centres and the weight table on the
- * device current at the first call (which allocates the plan's device memory)
- * on `stream`.  LP_ERR_ARG for a bad table, LP_ERR_CUDA for a CUDA failure. */
+ * before return).  Computes the phase centres and the weight table in the
+ * bound workspace on `stream`.  LP_ERR_STATE before a workspace is bound,
+ * LP_ERR_ARG for a bad table, LP_ERR_CUDA for a CUDA failure. */
 lp_status lp_prebeam_set_groups(lp_prebeam* pb, const int32_t* group_of_station,
                                 const double* station_enu, const double* group_dir,
                                 void* stream);

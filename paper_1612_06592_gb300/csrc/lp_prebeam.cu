@@ -36,7 +36,7 @@ struct lp_prebeam {
   long long F = 0;
   int device = -1;
   int E = 0;                            // stations in some group
-  void* mem = nullptr;                  // one device allocation, carved below
+  void* mem = nullptr;                  // the caller's workspace, carved below
   float2* w1 = nullptr;                 // [K][E] weights in member order
   int* member = nullptr;                // [E] station of member e (sorted by group)
   int* goff = nullptr;                  // [G + 1] first member of each group
@@ -270,6 +270,26 @@ lp_status pb_set_device(lp_prebeam* pb) {
   return LP_OK;
 }
 
+// Carve the workspace (sized for every station in a group, so later
+// lp_prebeam_set_groups calls never need more); base == nullptr: size only.
+size_t pb_carve(lp_prebeam& pb, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t n) -> char* {
+    off = (off + 255) / 256 * 256;
+    char* p = base ? base + off : nullptr;
+    off += n;
+    return p;
+  };
+  const int S = pb.S, G = pb.G;
+  pb.w1 = (float2*)take(sizeof(float2) * (size_t)pb.K * S);
+  pb.rel = (double*)take(sizeof(double) * 3 * (size_t)S);
+  pb.mdir = (double*)take(sizeof(double) * 3 * (size_t)S);
+  pb.member = (int*)take(sizeof(int) * S);
+  pb.goff = (int*)take(sizeof(int) * (G + 1));
+  pb.n_sat = (unsigned long long*)take(sizeof(unsigned long long));
+  return (off + 255) / 256 * 256;
+}
+
 lp_status pb_device_pointer(lp_prebeam* pb, const void* ptr, const char* what) {
   cudaPointerAttributes attr;
   PB_CUDA(pb, cudaPointerGetAttributes(&attr, ptr));
@@ -305,6 +325,39 @@ lp_status lp_prebeam_create(lp_prebeam** out, int stations, int pols, int subban
   pb->first_bin = first_bin;
   pb->input_dtype = input_dtype;
   *out = pb;
+  return LP_OK;
+}
+
+lp_status lp_prebeam_workspace_bytes(const lp_prebeam* pb, size_t* bytes) {
+  if (!pb || !bytes) return LP_ERR_ARG;
+  lp_prebeam tmp;
+  tmp.S = pb->S;
+  tmp.K = pb->K;
+  tmp.G = pb->G;
+  *bytes = lp::pb_carve(tmp, nullptr);
+  return LP_OK;
+}
+
+lp_status lp_prebeam_bind_workspace(lp_prebeam* pb, void* dev, size_t bytes, void* stream) {
+  using namespace lp;
+  if (!pb) return LP_ERR_ARG;
+  if (pb->mem) return pb_fail(pb, LP_ERR_STATE, "a workspace is already bound");
+  if (!dev || (reinterpret_cast<uintptr_t>(dev) & 255u))
+    return pb_fail(pb, LP_ERR_ARG, "workspace must be a 256-byte aligned device pointer");
+  size_t need = 0;
+  lp_prebeam_workspace_bytes(pb, &need);
+  if (bytes < need) return pb_fail(pb, LP_ERR_OOM, "workspace %zu bytes < %zu needed", bytes, need);
+  cudaPointerAttributes attr;
+  PB_CUDA(pb, cudaPointerGetAttributes(&attr, dev));
+  if (attr.type != cudaMemoryTypeDevice)
+    return pb_fail(pb, LP_ERR_ARG, "workspace is not device memory");
+  pb->device = attr.device;
+  if (pb_set_device(pb) != LP_OK) return LP_ERR_CUDA;
+  pb->mem = dev;
+  pb_carve(*pb, static_cast<char*>(dev));
+  PB_CUDA(pb, cudaMemsetAsync(pb->n_sat, 0, sizeof(unsigned long long),
+                              static_cast<cudaStream_t>(stream)));
+  pb->last_stream = static_cast<cudaStream_t>(stream);
   return LP_OK;
 }
 
@@ -356,31 +409,9 @@ lp_status lp_prebeam_set_groups(lp_prebeam* pb, const int32_t* group_of_station,
   }
   goff[G] = (int)member.size();
   const int E = goff[G];
+  if (!pb->mem) return pb_fail(pb, LP_ERR_STATE, "bind a workspace first");
 
-  if (!pb->mem) {
-    PB_CUDA(pb, cudaGetDevice(&pb->device));
-    // sized for every station in a group, so later calls never reallocate
-    const size_t bytes = sizeof(float2) * (size_t)pb->K * S + sizeof(int) * (S + G + 1) +
-                         2 * sizeof(double) * 3 * (size_t)S + sizeof(unsigned long long) + 6 * 256;
-    PB_CUDA(pb, cudaMalloc(&pb->mem, bytes));
-    char* base = static_cast<char*>(pb->mem);
-    size_t off = 0;
-    auto take = [&](size_t n) {
-      off = (off + 255) / 256 * 256;
-      char* p = base + off;
-      off += n;
-      return p;
-    };
-    pb->w1 = (float2*)take(sizeof(float2) * (size_t)pb->K * S);
-    pb->rel = (double*)take(sizeof(double) * 3 * (size_t)S);
-    pb->mdir = (double*)take(sizeof(double) * 3 * (size_t)S);
-    pb->member = (int*)take(sizeof(int) * S);
-    pb->goff = (int*)take(sizeof(int) * (G + 1));
-    pb->n_sat = (unsigned long long*)take(sizeof(unsigned long long));
-    PB_CUDA(pb, cudaMemset(pb->n_sat, 0, sizeof(unsigned long long)));
-  } else if (pb_set_device(pb) != LP_OK) {
-    return LP_ERR_CUDA;
-  }
+  if (pb_set_device(pb) != LP_OK) return LP_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   pb->E = E;
   // pageable host memory: the copies are complete for the host on return
@@ -463,15 +494,7 @@ const char* lp_prebeam_last_error(const lp_prebeam* pb) {
 }
 
 void lp_prebeam_destroy(lp_prebeam* pb) {
-  if (!pb) return;
-  if (pb->mem) {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (cur != pb->device) cudaSetDevice(pb->device);
-    cudaFree(pb->mem);
-    if (cur >= 0 && cur != pb->device) cudaSetDevice(cur);
-  }
-  delete pb;
+  delete pb;   // the workspace stays the caller's
 }
 
 }  // extern "C"

@@ -96,6 +96,8 @@ SIGNATURES = {
     "lp_prebeam_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int]),
+    "lp_prebeam_workspace_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "lp_prebeam_bind_workspace": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "lp_prebeam_set_groups": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "lp_prebeam_group_centres": (ctypes.c_int, [_P, _P]),
     "lp_prebeam_run": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P]),
@@ -351,10 +353,12 @@ class Plan:
 class Prebeam:
     """Preliminary beams of station groups (the first stage of two-stage
     beamforming): station block [P, K, F, S, 2] int8/int16 on the device ->
-    int16 [P, K, F, G, 2], the input of a Plan with stations = G."""
+    int16 [P, K, F, G, 2], the input of a Plan with stations = G.  The device
+    workspace is a torch uint8 tensor on the current CUDA device."""
 
     def __init__(self, stations, pols, subbands, block_len, groups, *, first_bin=12,
-                 input_dtype="int8"):
+                 input_dtype="int8", stream=None, workspace=None):
+        import torch
         self.shape = (stations, pols, subbands, block_len, groups)
         self._h = _P()
         dt = LP_INPUT_INT8 if input_dtype == "int8" else LP_INPUT_INT16
@@ -362,6 +366,15 @@ class Prebeam:
                                     groups, first_bin, dt)
         if st != LP_OK:
             raise LPError(st, "lp_prebeam_create: shape out of range")
+        nbytes = ctypes.c_size_t()
+        self._check(_lib.lp_prebeam_workspace_bytes(self._h, ctypes.byref(nbytes)),
+                    "lp_prebeam_workspace_bytes")
+        if workspace is None:
+            workspace = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        self._check(_lib.lp_prebeam_bind_workspace(self._h, workspace.data_ptr(),
+                                                   workspace.numel(), _stream_ptr(stream)),
+                    "lp_prebeam_bind_workspace")
 
     def _check(self, st, what):
         if st != LP_OK:
@@ -401,6 +414,7 @@ class Prebeam:
         if self._h:
             _lib.lp_prebeam_destroy(self._h)
             self._h = _P()
+            self.workspace = None
 
     def __del__(self):
         try:

@@ -128,6 +128,16 @@ def test_prebeam_validates_shape_and_groups_before_any_cuda_call(lib):
         assert c.lp_prebeam_set_groups(h, g.ctypes.data, enu.ctypes.data, dd.ctypes.data,
                                        None) == lib.LP_ERR_ARG
         assert c.lp_prebeam_last_error(h)
+    # a valid table still needs a bound workspace (the plan allocates nothing)
+    g = np.array([0, 1, 0, 1, 0, 1], dtype=np.int32)
+    assert c.lp_prebeam_set_groups(h, g.ctypes.data, enu.ctypes.data, dirs.ctypes.data,
+                                   None) == lib.LP_ERR_STATE
+    nbytes = ctypes.c_size_t(0)
+    assert c.lp_prebeam_workspace_bytes(h, ctypes.byref(nbytes)) == lib.LP_OK
+    assert nbytes.value >= 8 * 16 * 6 and nbytes.value % 256 == 0
+    assert c.lp_prebeam_bind_workspace(h, None, nbytes.value, None) == lib.LP_ERR_ARG
+    assert c.lp_prebeam_bind_workspace(h, 4096 + 16, nbytes.value, None) == lib.LP_ERR_ARG
+    assert c.lp_prebeam_bind_workspace(h, 4096, nbytes.value - 1, None) == lib.LP_ERR_OOM
     out = np.zeros((2, 3))
     assert c.lp_prebeam_group_centres(h, out.ctypes.data) == lib.LP_ERR_STATE
     assert c.lp_prebeam_run(h, 16, 16, ctypes.c_float(1.0), None) == lib.LP_ERR_STATE
