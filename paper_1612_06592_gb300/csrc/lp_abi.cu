@@ -115,12 +115,12 @@ lp_status sync_last(lp_plan* p) {
 
 // Record the start / end event of a stage for the current block (profiling).
 void prof_mark(lp_plan* p, int stage, int end, cudaStream_t s, int part = 0) {
-  if (!p->profiling) return;
+  if (!p->profiling || !p->prof) return;
   const int slot = p->prof_n % lp_plan::kProfSlots;
-  cudaEvent_t& ev = p->prof_ev[slot][stage][part][end];
+  cudaEvent_t& ev = p->prof->ev[slot][stage][part][end];
   if (!ev) cudaEventCreate(&ev);
   cudaEventRecord(ev, s);
-  if (end) p->prof_used[slot][stage][part] = true;
+  if (end) p->prof->used[slot][stage][part] = true;
 }
 
 int stream_of(const lp_plan* p, int beam, int tec, int pol) {
@@ -824,6 +824,11 @@ int lp_launches_per_block(const lp_plan* p) {
 
 lp_status lp_profile_enable(lp_plan* p, int enable) {
   if (!p) return LP_ERR_ARG;
+  if (enable && !p->prof) {
+    lp_plan::ProfTable* t = new (std::nothrow) lp_plan::ProfTable();
+    if (!t) return fail(p, LP_ERR_OOM, "no host memory for the profiling table");
+    p->prof.reset(t);
+  }
   p->profiling = enable != 0;
   return LP_OK;
 }
@@ -834,15 +839,15 @@ lp_status lp_profile_read(lp_plan* p, double* total_ms, int64_t* blocks) {
   if (set_device(p) != LP_OK) return LP_ERR_CUDA;
   if (sync_last(p) != LP_OK) return LP_ERR_CUDA;
   for (int st = 0; st < LP_NUM_STAGES; ++st) total_ms[st] = 0.0;
-  for (int slot = 0; slot < p->prof_n; ++slot) {
+  for (int slot = 0; p->prof && slot < p->prof_n; ++slot) {
     for (int st = 0; st < LP_NUM_STAGES; ++st) {
       for (int part = 0; part < lp_plan::kProfParts; ++part) {
-        if (!p->prof_used[slot][st][part]) continue;
+        if (!p->prof->used[slot][st][part]) continue;
         float ms = 0.f;
-        LP_CUDA(p, cudaEventElapsedTime(&ms, p->prof_ev[slot][st][part][0],
-                                        p->prof_ev[slot][st][part][1]));
+        LP_CUDA(p, cudaEventElapsedTime(&ms, p->prof->ev[slot][st][part][0],
+                                        p->prof->ev[slot][st][part][1]));
         total_ms[st] += ms;
-        p->prof_used[slot][st][part] = false;
+        p->prof->used[slot][st][part] = false;
       }
     }
   }
@@ -854,11 +859,12 @@ lp_status lp_profile_read(lp_plan* p, double* total_ms, int64_t* blocks) {
 void lp_plan_destroy(lp_plan* p) {
   if (!p) return;
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-  for (auto& slot : p->prof_ev)
-    for (auto& st : slot)
-      for (auto& part : st)
-        for (auto& ev : part)
-          if (ev) cudaEventDestroy(ev);
+  if (p->prof)
+    for (auto& slot : p->prof->ev)
+      for (auto& st : slot)
+        for (auto& part : st)
+          for (auto& ev : part)
+            if (ev) cudaEventDestroy(ev);
   if (p->copy_stream) {
     cudaStreamSynchronize(p->copy_stream);
     cudaStreamDestroy(p->copy_stream);

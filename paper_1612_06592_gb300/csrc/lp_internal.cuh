@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <memory>
 #include <string>
 
 #include "../../include/lp.h"
@@ -134,8 +135,11 @@ struct lp_plan {
   bool profiling = false;
   static constexpr int kProfSlots = 256;
   static constexpr int kProfParts = 2;
-  cudaEvent_t prof_ev[kProfSlots][LP_NUM_STAGES][kProfParts][2] = {};
-  bool prof_used[kProfSlots][LP_NUM_STAGES][kProfParts] = {};
+  struct ProfTable {       // ~52 KB: on the heap, made by lp_profile_enable
+    cudaEvent_t ev[kProfSlots][LP_NUM_STAGES][kProfParts][2] = {};
+    bool used[kProfSlots][LP_NUM_STAGES][kProfParts] = {};
+  };
+  std::shared_ptr<ProfTable> prof;
   int prof_n = 0;
   // host input: copies of the next polarisation overlap the work on the
   // previous one (a copy stream of the plan, one event per polarisation)

@@ -2,9 +2,9 @@
 // cannot allocate device memory.
 //
 // Some callers run where cudaMalloc is not available to them: code inside a
-// host that forbids device allocation after start-up (a real-time loop with a
-// fixed memory budget, a plug-in of a framework that owns the device heap), or
-// code that must not allocate while a stream is being captured.  They cannot
+// host process that forbids device allocation after start-up (a real-time
+// loop with a fixed memory budget, or a plug-in of a framework that owns the
+// device heap and hands out only the buffers it has planned).  They cannot
 // bind a plan workspace.  This entry point keeps everything it needs besides
 // the caller's inputs and outputs (phase tables, synthesis filter, the beam
 // intermediate, noise partial sums) in one file-scope device array of
@@ -14,11 +14,12 @@
 //
 // The array is shared by all calls on a device and keeps the last call's
 // contents; the call clears what must start at zero (the history prefix of
-// the beam rows, the block counter and the trigger counter).  Calls whose GPU work overlaps
-// (different streams, or host threads) race on the array and must be
-// serialised by the caller.  The first call on a device looks up the array's
-// device address (cudaGetSymbolAddress, with that device current) and caches
-// it; make that first call before any stream capture.
+// the beam rows, the block counter and the trigger counter).  Calls whose GPU
+// work overlaps (different streams, or host threads) race on the array and
+// must be serialised by the caller.  The first call on a device looks up the
+// array's device address (cudaGetSymbolAddress, with that device current) and
+// caches it; make that first call before any stream capture.
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -123,14 +124,38 @@ extern "C" lp_status lp_process_block_noalloc(
 
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return report(err, errlen, LP_ERR_CUDA, cudaGetErrorString(e));
+  // every device argument: device (or managed) memory of the current device,
+  // aligned to its element; refused before anything touches the GPU
+  const size_t x_align = c.input_dtype == LP_INPUT_INT8 ? 2 : 4;   // one complex sample
+  const struct {
+    const void* ptr;
+    size_t align;
+    const char* name;
+  } args[] = {{x, x_align, "x"},
+              {y, sizeof(float), "y"},
+              {sigma2, sizeof(double), "sigma2"},
+              {triggers, 8, "triggers"},
+              {trigger_count, sizeof(unsigned long long), "trigger_count"}};
+  for (const auto& a : args) {
+    if (!a.ptr) continue;
+    if (reinterpret_cast<uintptr_t>(a.ptr) % a.align) {
+      snprintf(msg, sizeof msg, "%s must be %zu-byte aligned", a.name, a.align);
+      return report(err, errlen, LP_ERR_ARG, msg);
+    }
+    cudaPointerAttributes attr;
+    e = cudaPointerGetAttributes(&attr, a.ptr);
+    if (e != cudaSuccess) return report(err, errlen, LP_ERR_CUDA, cudaGetErrorString(e));
+    if ((attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) ||
+        attr.device != dev) {
+      snprintf(msg, sizeof msg, "%s must be device or managed memory of the current device",
+               a.name);
+      return report(err, errlen, LP_ERR_ARG, msg);
+    }
+  }
   void* base = nullptr;
-  if (e == cudaSuccess) e = scratch_address(dev, &base);
+  e = scratch_address(dev, &base);
   if (e != cudaSuccess) return report(err, errlen, LP_ERR_CUDA, cudaGetErrorString(e));
-  cudaPointerAttributes attr;
-  e = cudaPointerGetAttributes(&attr, x);
-  if (e != cudaSuccess) return report(err, errlen, LP_ERR_CUDA, cudaGetErrorString(e));
-  if (attr.type != cudaMemoryTypeDevice || attr.device != dev)
-    return report(err, errlen, LP_ERR_ARG, "x must be device memory of the current device");
 
   char* b = static_cast<char*>(base);
   auto& buf = p.buf;
