@@ -11,6 +11,20 @@ Tolerances (derived from the arithmetic, stated once here):
     target is 1e-4, the tests allow TOL_TS_FP16 = 1e-4.
   * Triggers: both lists must agree except for samples whose oracle envelope
     lies within TAU * theta of the threshold (TAU = 1e-5 FP32, 1e-4 FP16).
+  * Per sample (assert_samples_close), on top of the relative RMS: every sample
+    must satisfy |y - y_ref| <= C * eps * (sigma_y + env_local), eps = 2^-24,
+    sigma_y the stream's noise level and env_local the largest oracle envelope
+    within 16 frames of the sample (the FIR reaches 15 frames back and a
+    frame's inverse FFT mixes all its bins, so the rounding error of a sample
+    scales with the magnitudes in that window, not with the sample itself).
+    C: an output sample collects about S products and S roundings in its beams
+    (S <= 64), 2 log2(1024) = 20 in the inverse FFT and 16 in the FIR, so its
+    error is near Gaussian with a standard deviation of at most
+    sqrt(64 + 20 + 16) = 10 eps in those units; the largest of up to 1e8
+    samples stays below 6.5 standard deviations, 65 eps.  C_FP32 = 128 keeps a
+    factor two.  The FP16 form's weights carry 2^-22 (4 eps) from the hi/lo
+    split on each of the S products: sqrt(16 * 64 + 36) = 33 eps, times 6.5 =
+    213; C_FP16 = 512.  One sample off by 1e-3 sigma_y already fails both.
 """
 
 from __future__ import annotations
@@ -24,6 +38,37 @@ TOL_TS_FP32 = 2e-5
 TOL_TS_FP16 = 1e-4
 TAU_FP32 = 1e-5
 TAU_FP16 = 1e-4
+EPS32 = 2.0 ** -24
+C_FP32 = 128.0
+C_FP16 = 512.0
+
+
+REL_FP32 = C_FP32 * EPS32
+REL_FP16 = C_FP16 * EPS32
+
+
+def assert_samples_close(got, ref, env, sigma, rel, what="y"):
+    """Per-sample bound |got - ref| <= rel * (sigma + env_local) on streams of
+    whole frames (rel = C * eps, REL_FP32 or REL_FP16): got, ref, env [J, N] (or
+    [N]) with N a multiple of 1024, sigma [J] (or scalar).  env_local = max of
+    env over the sample's frame and the 16 frames on either side."""
+    from scipy.ndimage import maximum_filter1d
+    got = np.atleast_2d(np.asarray(got, dtype=np.float64))
+    ref = np.atleast_2d(np.asarray(ref, dtype=np.float64))
+    env = np.atleast_2d(np.asarray(env, dtype=np.float64))
+    sig = np.broadcast_to(np.atleast_1d(np.asarray(sigma, dtype=np.float64)), (got.shape[0],))
+    J, N = got.shape
+    assert ref.shape == got.shape == env.shape and N % 1024 == 0, (got.shape, ref.shape, env.shape)
+    fr = env.reshape(J, N // 1024, 1024).max(axis=2)
+    loc = maximum_filter1d(fr, size=33, axis=1, mode="nearest")
+    bound = rel * (sig[:, None] + np.repeat(loc, 1024, axis=1))
+    err = np.abs(got - ref)
+    ratio = err / bound
+    worst = np.unravel_index(int(np.argmax(ratio)), ratio.shape)
+    assert ratio[worst] <= 1.0, (
+        f"{what}: sample {worst} off by {err[worst]:.3e} > bound {bound[worst]:.3e} "
+        f"(ref {ref[worst]:.4e}, sigma {sig[worst[0]]:.4e})")
+    return float(ratio[worst])
 
 
 def rel_rms(got, ref):

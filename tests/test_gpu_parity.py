@@ -10,8 +10,9 @@ import pytest
 
 import oracle as O
 import synth
-from gpu_common import (TAU_FP16, TAU_FP32, TOL_TS_FP16, TOL_TS_FP32, compare_triggers,
-                        gpu_blocks, make_plan, oracle_blocks, random_case, rel_rms)
+from gpu_common import (REL_FP16, REL_FP32, TAU_FP16, TAU_FP32, TOL_TS_FP16, TOL_TS_FP32,
+                        assert_samples_close, compare_triggers, gpu_blocks, make_plan,
+                        oracle_blocks, random_case, rel_rms)
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +40,7 @@ def test_fp32_path_matches_oracle(cuda_lib, case):
         # beams: oracle [J, F, K], GPU [J, K, F]
         assert rel_rms(gb["beams"], ob["beams"].transpose(0, 2, 1)) < TOL_TS_FP32
         assert rel_rms(gb["y"], ob["y"]) < TOL_TS_FP32
+        assert_samples_close(gb["y"], ob["y"], ob["env"], ob["sigma"], REL_FP32)
         np.testing.assert_allclose(gb["sigma"], ob["sigma"], rtol=1e-5)
         ng, no, nd, bad = compare_triggers(gb["trig"], ob, P, Tr, TAU_FP32)
         assert not bad, bad[:5]
@@ -68,6 +70,7 @@ def test_fp16_tensor_core_path_matches_oracle(cuda_lib, case):
         # hi/lo FP16 weights keep the beams near FP32 accuracy
         assert eb < 1e-5, eb
         assert ey < TOL_TS_FP16 and ey < 1e-5, ey
+        assert_samples_close(gb["y"], ob["y"], ob["env"], ob["sigma"], REL_FP16)
         np.testing.assert_allclose(gb["sigma"], ob["sigma"], rtol=1e-5)
         ng, no, nd, bad = compare_triggers(gb["trig"], ob, P, Tr, TAU_FP16)
         assert not bad, bad[:5]
@@ -128,6 +131,7 @@ def test_tiny_workload_with_pulse(cuda_lib):
                          w.block_len, w.first_bin, blocks, enu, dirs, tec)
     for gb, ob in zip(g, o):
         assert rel_rms(gb["y"], ob["y"]) < TOL_TS_FP32
+        assert_samples_close(gb["y"], ob["y"], ob["env"], ob["sigma"], REL_FP32)
         ng, no, nd, bad = compare_triggers(gb["trig"], ob, w.pols, 1, TAU_FP32)
         assert not bad
     # the injected pulse triggers near its de-dispersed arrival time
