@@ -77,6 +77,10 @@ def fp32_peak_tflops():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--shard", default="beams", choices=["beams", "replicas"],
+                    help="N > 1: beams (each rank runs its share of the 50 beams on the same "
+                         "block, triggers merged on rank 0; strong scaling) or replicas (every "
+                         "rank the whole problem on its own block; weak scaling)")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -226,9 +230,10 @@ def max_over_ranks(values, device=None):
     return [float(v) for v in t.cpu()]
 
 
-def whole_job_rate(world, block_s, ms_step_max):
-    """Realtime factor of N replicas each processing one block per step."""
-    return world * block_s / (ms_step_max / 1e3)
+def whole_job_rate(world, block_s, ms_step_max, sharded=False):
+    """Realtime factor of the whole job: N replicas each processing one block
+    per step, or (sharded) N ranks sharing the beams of one block per step."""
+    return (1 if sharded else world) * block_s / (ms_step_max / 1e3)
 
 
 # ------------------------------------------------------------ main ---------
@@ -243,14 +248,27 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     w = bench_workload(args)
     enu, dirs, tec = synth.make_geometry(w)
-    x = device_block(w, 1000 + rank, dev)
-    plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(w.tec_trials), w.block_len,
-                   input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
+    sharded = world > 1 and args.shard == "beams"
+    # beam sharding: every rank holds the same block (its own copy on its own
+    # GPU) and runs its beams; replicas: every rank its own block
+    x = device_block(w, 1000 if sharded else 1000 + rank, dev)
+    plan_kw = dict(input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
                    host_input=not args.no_e2e and not args.lsmr,
                    frames_per_cta=args.synth_frames, fine_dedisp=args.fine,
                    inversion="lsmr" if args.lsmr else "fir")
-    plan.lp_set_weights(enu, dirs)
+    shard = None
+    if sharded:
+        from paper_1612_06592_gb300.shard import BeamShard
+        shard = BeamShard(w.stations, w.pols, w.subbands, w.beams, len(w.tec_trials),
+                          w.block_len, rank=rank, world=world, **plan_kw)
+        plan = shard.plan
+        shard.lp_set_weights(enu, dirs)
+    else:
+        plan = lp.Plan(w.stations, w.pols, w.subbands, w.beams, len(w.tec_trials), w.block_len,
+                       **plan_kw)
+        plan.lp_set_weights(enu, dirs)
     plan.lp_set_tec(tec)
+    n_streams_local = plan.shape[3] * plan.shape[4] * plan.shape[1]
     stream = torch.cuda.current_stream()
     # untimed blocks pick the beamformer configuration and the synthesis tiling
     # (autotuners), then warm-up
@@ -306,7 +324,13 @@ def run_ours(args, rank, world, local_rank):
         d2h = 0
         for _ in range(args.steps):
             plan.lp_process_block(xh)
-            trig, n, _ = plan.lp_get_triggers()
+            if shard is not None:
+                # this rank's triggers relabelled to global beams, merged on rank 0
+                from paper_1612_06592_gb300.shard import gather_triggers
+                trig, n, _ = shard.lp_get_triggers()
+                gather_triggers(trig)
+            else:
+                trig, n, _ = plan.lp_get_triggers()
             d2h += 8 + 32 * len(trig)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
@@ -323,11 +347,13 @@ def run_ours(args, rank, world, local_rank):
 
     block_s = w.block_len * M / FS_HZ
     ms_step = ms / args.steps
-    rtf = whole_job_rate(world, block_s, ms_step)
+    rtf = whole_job_rate(world, block_s, ms_step, sharded)
+    blocks_per_step = 1 if sharded else world
     synth_ms = stages["synth"] / max(nrec, 1)
     bf_ms = stages["beamform"] / max(nrec, 1)
     samples = w.n_streams * w.block_len * M
-    flop = samples * SYNTH_FLOP_PER_SAMPLE
+    # the roofline is rank 0's own synthesis launch (its share of the beams)
+    flop = n_streams_local * w.block_len * M * SYNTH_FLOP_PER_SAMPLE
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -338,23 +364,26 @@ def run_ours(args, rank, world, local_rank):
     traffic = recorded_traffic("k_ippf.cu")
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     in_bytes = x.numel() * x.element_size()
-    beams_bytes = w.n_streams * w.subbands * w.block_len * 8
+    beams_bytes = n_streams_local * w.subbands * w.block_len * 8
     bf_gbs = (in_bytes + beams_bytes) / (bf_ms / 1e3) / 1e9
     line = {
         "metric": "realtime factor at 48 stations×488 subbands×50 beams",
         "value": rtf, "unit": "x realtime", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": "f16 tensor-core beamformer, f32" if args.precision == "fp16" else "f32",
         "data": "synthetic (seeded rounded-Gaussian int8 station noise)",
         "config": dict(workload_config(w, args.precision), synth_frames_per_cta=tuned_fpc,
+                       parallelism=(f"beams sharded over {world} GPUs (ranks own contiguous "
+                                    "beam ranges of one block; triggers merged on rank 0)"
+                                    if sharded else f"{world} replica(s), one block each"),
                        autotune_ms={str(k): round(v, 3) for k, v in tune_ms.items()},
                        gemm_config=gemm_desc(args.precision, gemm_cfgs, gemm_best),
                        gemm_autotune_ms={gemm_desc(args.precision, gemm_cfgs, gemm_cfgs.index(k)):
                                          round(v, 3) for k, v in gemm_ms.items()}),
         "samples_per_s": {"station_complex": w.pols * w.subbands * w.block_len * w.stations
-                          * world / (ms_step / 1e3),
-                          "output_200MHz": samples * world / (ms_step / 1e3)},
+                          * blocks_per_step / (ms_step / 1e3),
+                          "output_200MHz": samples * blocks_per_step / (ms_step / 1e3)},
         "stage_ms": {k: v / max(nrec, 1) for k, v in stages.items() if k != "fine" or args.fine},
         "roofline": {"bound": "alu", "kernel": "k_ippf (inverse FFT + synthesis FIR + trigger)",
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
@@ -375,7 +404,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if e2e:
         t_e2e, d2h, h2d = e2e
-        line["e2e"] = {"value": world * block_s / (t_e2e / args.steps), "unit": "x realtime",
+        line["e2e"] = {"value": blocks_per_step * block_s / (t_e2e / args.steps), "unit": "x realtime",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": t_e2e / args.steps * 1e3,
                        "path": "lp_process_block(pinned host block) + lp_get_triggers",

@@ -150,7 +150,7 @@ def test_stress_shape_chunked_graph_sampled_parity(cuda_lib):
     end) match the oracle, with their triggers."""
     import torch
     w = synth.STRESS
-    F, chunk, k_sigma = 4096, 2048, 4.0
+    F, chunk, k_sigma = 4096, 2048, 5.0
     enu, dirs, tec = synth.make_geometry(w)
     x = np.empty((w.pols, w.subbands, F, w.stations, 2), dtype=w.dtype)
     for pol in range(w.pols):

@@ -41,9 +41,11 @@ def test_max_over_ranks_gloo_two_ranks():
     assert out[0] == [150.0, 14.0] and out[1] == [150.0, 14.0]
 
 
-def test_whole_job_rate_is_weak_scaling():
+def test_whole_job_rate_weak_and_sharded():
     import bench
     block_s = 65536 * 1024 / 200e6
     assert bench.whole_job_rate(1, block_s, 100.0) == pytest.approx(3.3554432)
     # two replicas, slowest rank 110 ms per block
     assert bench.whole_job_rate(2, block_s, 110.0) == pytest.approx(2 * block_s / 0.110)
+    # two ranks sharing the beams of one block, slowest rank 60 ms
+    assert bench.whole_job_rate(2, block_s, 60.0, sharded=True) == pytest.approx(block_s / 0.060)
