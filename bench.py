@@ -103,6 +103,12 @@ def parse():
                          "separate line, not the headline; no triggers on that path)")
     ap.add_argument("--gemm-config", type=int, default=-2,
                     help="fixed beamformer configuration index (-1: default; -2: autotune)")
+    ap.add_argument("--chunk-frames", type=int, default=0,
+                    help="beam rows for chunks of this many frames (multiple of 256; 0: the "
+                         "whole block), with a first power-only beamformer pass")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay each block's launches from a captured CUDA graph (on a side "
+                         "stream; stage times are then not recorded)")
     ap.add_argument("--frames", type=int, default=0,
                     help="block length override for small profiling cases (not a bench line)")
     return ap.parse_args()
@@ -255,7 +261,10 @@ def run_ours(args, rank, world, local_rank):
     plan_kw = dict(input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
                    host_input=not args.no_e2e and not args.lsmr,
                    frames_per_cta=args.synth_frames, fine_dedisp=args.fine,
-                   inversion="lsmr" if args.lsmr else "fir")
+                   inversion="lsmr" if args.lsmr else "fir", chunk_frames=args.chunk_frames,
+                   use_graph=args.graph)
+    if args.graph:
+        torch.cuda.set_stream(torch.cuda.Stream())   # graph capture needs a non-default stream
     shard = None
     if sharded:
         from paper_1612_06592_gb300.shard import BeamShard
@@ -282,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
         tuned_fpc, tune_ms = args.synth_frames, {}
     else:
         tuned_fpc, tune_ms = plan.lp_plan_autotune(x)
-    plan.lp_profile_enable(True)
+    plan.lp_profile_enable(not args.graph)
     for _ in range(args.warmup):
         plan.lp_process_block(x)
     torch.cuda.synchronize()
@@ -360,12 +369,12 @@ def run_ours(args, rank, world, local_rank):
     except OSError:
         pass
     alu_peak, alu_peak_mhz, alu_peak_note = fp32_peak()
-    achieved = flop / (synth_ms / 1e3) / 1e12
+    achieved = flop / (synth_ms / 1e3) / 1e12 if synth_ms > 0 else float("nan")
     traffic = recorded_traffic("k_ippf.cu")
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     in_bytes = x.numel() * x.element_size()
     beams_bytes = n_streams_local * w.subbands * w.block_len * 8
-    bf_gbs = (in_bytes + beams_bytes) / (bf_ms / 1e3) / 1e9
+    bf_gbs = (in_bytes + beams_bytes) / (bf_ms / 1e3) / 1e9 if bf_ms > 0 else float("nan")
     line = {
         "metric": "realtime factor at 48 stations×488 subbands×50 beams",
         "value": rtf, "unit": "x realtime", "n_gpus": world, "steps": args.steps,

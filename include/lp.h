@@ -82,7 +82,7 @@ typedef struct {
                                when the input address or pol stride changes; not with
                                profiling) */
   int32_t chunk_frames;     /* 0: the beam rows hold the whole block.  > 0 (FP16 form,
-                               multiple of 2048 dividing block_len): the block is
+                               multiple of 256 dividing block_len): the block is
                                processed in chunks of this many frames, so the beam
                                intermediate is sized for one chunk; a first beamformer
                                pass sums |beam|^2 over the whole block for the noise

@@ -561,7 +561,7 @@ int num_sms() {
 
 }  // namespace
 
-int beamform_tc_frame_tile() { return CHUNK; }
+int beamform_tc_frame_tile() { return TN; }
 // noise partials per (stream, subband): two column halves per 2048-frame chunk
 int beamform_tc_partials(long long F) { return 2 * (int)((F + CHUNK - 1) / CHUNK); }
 
