@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=16384)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
-    ap.add_argument("--serve-blocks", type=int, default=32,
+    ap.add_argument("--serve-blocks", type=int, default=200,
                     help="blocks of the realtime serving leg (p50/p99 latency); 0 skips it")
     ap.add_argument("--workload", default="precision", choices=["precision", "stress", "two-stage"],
                     help="precision: the 48x488x50 headline block; stress: 200 beams x 8 "

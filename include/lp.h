@@ -289,6 +289,48 @@ enum { LP_STAGE_H2D = 0, LP_STAGE_BEAMFORM = 1, LP_STAGE_SIGMA = 2, LP_STAGE_SYN
 lp_status lp_profile_enable(lp_plan* plan, int enable);
 lp_status lp_profile_read(lp_plan* plan, double* total_ms, int64_t* blocks);
 
+/* ---- Groups: several plans' blocks in shared launches ---------------------
+ *
+ * No counterpart in the paper; this is the serving loop's batching.  Requests
+ * that subscribe to one station stream each own a plan (their beams, STEC
+ * trials and contiguous subband range, with their own history, noise level
+ * and trigger list).  A group fuses the per-block launches of up to
+ * LP_MAX_GROUP such plans: one beamformer launch over every plan's work items,
+ * one noise-level launch (which also clears every plan's trigger counter), one
+ * synthesis launch over every plan's streams and one history shift -- four
+ * launches per block however many plans.  Each plan computes exactly what its
+ * own lp_process_block computes, bit for bit.
+ *
+ * Member plans: bound, lp_set_weights and lp_set_tec done, the FP16 form,
+ * whole blocks (chunk_frames 0), the FIR synthesis without fine
+ * de-dispersion, one device, equal stations, polarisations, block length and
+ * input type.  The group uses the first plan's synthesis tiling and
+ * beamformer configuration (results do not depend on either) and reports a
+ * timed-out device wait through the first plan's lp_get_triggers. */
+#define LP_MAX_GROUP 32
+typedef struct lp_group lp_group;
+
+/* Host only: a group of n distinct plans (1 <= n <= LP_MAX_GROUP).  The plans
+ * stay owned by the caller and must outlive the group.  LP_ERR_ARG for a bad
+ * list, LP_ERR_STATE when a plan does not qualify (see above). */
+lp_status lp_group_create(lp_group** out, lp_plan* const* plans, int n);
+
+/* One block for every plan of the group, asynchronously on `stream`.
+ * x: device block [P][subbands][F][S][2] complex int8 holding the contiguous
+ * bins [first_bin, first_bin + subbands), 16-byte aligned with 16-byte
+ * aligned subband rows (F * S * 2 bytes); each plan reads its own bins.
+ * Afterwards each plan's lp_get_triggers / lp_get_sigma / lp_get_timeseries
+ * read its results as after lp_process_block. */
+lp_status lp_group_process_block(lp_group* group, const void* x, int32_t subbands,
+                                 int32_t first_bin, void* stream);
+
+/* Plans in the group; kernel launches per block (4). */
+int lp_group_size(const lp_group* group);
+int lp_group_launches_per_block(const lp_group* group);
+const char* lp_group_last_error(const lp_group* group);
+/* Frees the host object only (the plans are the caller's). */
+void lp_group_destroy(lp_group* group);
+
 /* Size of the static device scratch of lp_process_block_noalloc: 16 MiB,
  * held by every GPU that loads the library until the process exits. */
 #define LP_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)

@@ -141,8 +141,7 @@ size_t f32_smem(const Shape& sh, size_t sample_bytes) {
 
 template <typename T2, int BB>
 cudaError_t set_f32_attr(const Shape& sh) {
-  return cudaFuncSetAttribute(k_beamform_f32<T2, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)f32_smem(sh, sizeof(T2)));
+  return raise_smem_limit((const void*)k_beamform_f32<T2, BB>, f32_smem(sh, sizeof(T2)));
 }
 
 cudaError_t init_f32_attributes(const Shape& sh) {

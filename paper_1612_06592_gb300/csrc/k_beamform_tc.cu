@@ -40,6 +40,8 @@
 // returns.
 #include <cuda.h>
 
+#include <cstring>
+
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -234,15 +236,23 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
   return true;
 }
 
-struct TcArgs {
+// Per-plan part of a launch: the plan's input view, weights, tables and
+// outputs.  One launch serves one plan, or a group of plans (lp_group) on
+// different subband ranges and beams of one station block.
+struct TcPlan {
   const int8_t* x;          // pol slabs [K][F][S][2], pol_stride complex samples apart
   long long pol_stride;
   const __half* wtc;        // A images
   const float2* dd;         // [K][Tr]
-  float2* beams;            // [J][K][row]
   float* power_part;        // [J][K][n_chunks]
-  int* err;                 // device error word
-  int S, P, K, B, Tr, n_mt, n_chunks;
+  int K, B, Tr, n_mt;
+  long long item_end;       // items of plans 0 .. this one
+  long long km0;            // group-wide index of the plan's first (subband, beam tile)
+};
+
+struct TcArgs {
+  int* err;                 // device error word (of the first plan)
+  int S, P, n_chunks;
   long long F, row;         // frames of this launch, beam-row length (chunk + prefix)
   long long F_in, f_base;   // input frames per subband row, first input frame of the launch
   int chunk_base, n_chunks_total;   // noise-partial chunk index offset, chunks per block
@@ -250,26 +260,42 @@ struct TcArgs {
   int pol0, npol;           // polarisations of this launch: pol0 .. pol0 + npol - 1
   long long n_items;
   int n_s8, n_sb;           // pipeline depths (int8 ring, FP16 ring)
+  int n;                    // plans
+  TcPlan pl[kMaxGroup];
+  CUtensorMap maps[kMaxGroup];   // TMA map of each plan's beam rows
 };
 
-// The tile sequence every role walks: items [it0, it1), 256-frame tiles each.
+// The tile sequence every role walks: items [it0, it1) of the launch (plan 0's
+// items, then plan 1's, ...), 256-frame tiles each.
 struct TileSeq {
-  long long it, it1, n0, f_hi;
-  int n_chunks, P;
+  long long it, it1, n0, f_hi, p_begin;
+  int n_chunks, P, pidx;
   long long F;
-  __device__ void start(long long a, long long b, int nc, int p, long long f) {
-    it = a; it1 = b; n_chunks = nc; P = p; F = f;
+  const TcArgs* a;
+  __device__ void start(const TcArgs* args, long long b0, long long b1) {
+    a = args;
+    it = b0; it1 = b1; n_chunks = a->n_chunks; P = a->npol; F = a->F;
+    pidx = 0;
+    p_begin = 0;
     if (it < it1) set_item();
   }
   __device__ void set_item() {
-    const long long chunk = it % n_chunks;
+    while (it >= a->pl[pidx].item_end) {
+      p_begin = a->pl[pidx].item_end;
+      ++pidx;
+    }
+    const long long chunk = local() % n_chunks;
     n0 = chunk * CHUNK;
     f_hi = min(F, n0 + CHUNK);
   }
+  __device__ long long local() const { return it - p_begin; }
+  __device__ const TcPlan& plan() const { return a->pl[pidx]; }
   __device__ bool valid() const { return it < it1; }
-  __device__ int chunk() const { return (int)(it % n_chunks); }
-  __device__ int pol() const { return (int)((it / n_chunks) % P); }
-  __device__ long long km() const { return it / ((long long)n_chunks * P); }
+  __device__ int chunk() const { return (int)(local() % n_chunks); }
+  __device__ int pol() const { return (int)((local() / n_chunks) % P); }
+  // (subband, beam tile) within the plan, and its group-wide index
+  __device__ long long km() const { return local() / ((long long)n_chunks * P); }
+  __device__ long long kmg() const { return a->pl[pidx].km0 + km(); }
   __device__ bool last_of_item() const { return n0 + TN >= f_hi; }
   __device__ void next() {
     n0 += TN;
@@ -280,8 +306,7 @@ struct TileSeq {
   }
 };
 
-__global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
-                                                       const __grid_constant__ CUtensorMap out_map) {
+__global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int KP = kpad(a.S);
   const int nkg = KP / 8;
@@ -318,7 +343,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
   const long long it0 = blockIdx.x * per;
   const long long it1 = min(a.n_items, it0 + per);
   TileSeq q;
-  q.start(it0, it1, a.n_chunks, a.npol, a.F);
+  q.start(&a, it0, it1);
 
   if (warp == W_PROD) {
     // ---------------- producer ----------------
@@ -329,23 +354,24 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
       uint32_t issued = 0, last_par = 0;        // per stage: copy issued, its phase parity
       bool a_issued = false;
       for (; q.valid(); q.next()) {
-        const long long km = q.km();
-        if (km != cur_km) {
+        const TcPlan& pl = q.plan();
+        const long long km = q.km(), kmg = q.kmg();
+        if (kmg != cur_km) {
           if (cur_km >= 0) {
             if (!wait_phase(&a_empty, aph, abort_p)) break;
             aph ^= 1u;
           }
           mbar_expect_tx(&a_full, 2 * a_bytes);
-          bulk_g2s(sa, a.wtc + km * 2 * (long long)TM * KP, 2 * a_bytes, &a_full);
+          bulk_g2s(sa, pl.wtc + km * 2 * (long long)TM * KP, 2 * a_bytes, &a_full);
           a_issued = true;
-          cur_km = km;
+          cur_km = kmg;
         }
         if (!wait_phase(&empty8[st], ph ^ 1u, abort_p)) break;
-        const int k = (int)(km / a.n_mt);
+        const int k = (int)(km / pl.n_mt);
         const int nvalid = (int)min((long long)TN, q.f_hi - q.n0);
         const int8_t* src =
-            a.x + 2 * ((q.pol() + a.pol0) * a.pol_stride +
-                       ((long long)k * a.F_in + a.f_base + q.n0) * a.S);
+            pl.x + 2 * ((q.pol() + a.pol0) * pl.pol_stride +
+                        ((long long)k * a.F_in + a.f_base + q.n0) * a.S);
         const uint32_t bytes = (uint32_t)nvalid * 2 * a.S;
         mbar_expect_tx(&full8[st], bytes);
         bulk_g2s(s8 + st * t8_bytes, src, bytes, &full8[st]);
@@ -381,7 +407,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
       int last_acc = -1;
       uint32_t last_par = 0;
       for (; q.valid(); q.next()) {
-        const long long km = q.km();
+        const long long km = q.kmg();
         if (km != cur_km) {
           if (cur_km >= 0) mma_commit(&a_empty);   // old A free once its MMAs finish
           if (!wait_phase(&a_full, aph, abort_p)) break;
@@ -459,14 +485,16 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
       if (!wait_phase(&tfull[acc], pha, abort_p)) break;
       tc_fence_after();
       const int pol = q.pol() + a.pol0;
+      const TcPlan& pl = q.plan();
+      const CUtensorMap* out_map = &a.maps[q.pidx];
       const long long km = q.km();
-      const int k = (int)(km / a.n_mt), mt = (int)(km % a.n_mt);
+      const int k = (int)(km / pl.n_mt), mt = (int)(km % pl.n_mt);
       const int b = mt * (TM / 2) + rb;
-      const bool beam_ok = b < a.B;
+      const bool beam_ok = b < pl.B;
       const long long f_hi = q.f_hi, n0 = q.n0;
       const uint32_t lane_addr =
           tmem + acc * TN + ((uint32_t)(quarter * 32) << 16) + col_half * (TN / 2);
-      const float2 d0 = a.dd[k * a.Tr];
+      const float2 d0 = pl.dd[k * pl.Tr];
       const int rloc = lane >> 1;                // beam row inside the warp's 16-beam box
       for (int c0 = 0; c0 < TN / 2; c0 += 32) {
         uint32_t r[2][16];
@@ -499,8 +527,8 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
           }
         }
         if (fbh[0] < f_hi && a.write_beams) {
-          for (int t = 0; t < a.Tr; ++t) {
-            const float2 dv = t == 0 ? d0 : a.dd[k * a.Tr + t];
+          for (int t = 0; t < pl.Tr; ++t) {
+            const float2 dv = t == 0 ? d0 : pl.dd[k * pl.Tr + t];
             if (lane == 0) bulk_wait_read<0>();   // earlier stores have read both boxes
             __syncwarp();
 #pragma unroll
@@ -518,10 +546,10 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) {
-              tma_store_box(&out_map, stg + (ew * 2) * STG_BOX, (int)(kPrefix + fbh[0]), k, pol,
+              tma_store_box(out_map, stg + (ew * 2) * STG_BOX, (int)(kPrefix + fbh[0]), k, pol,
                             t, mt * (TM / 2) + quarter * 16);
               if (fbh[1] < f_hi)
-                tma_store_box(&out_map, stg + (ew * 2 + 1) * STG_BOX, (int)(kPrefix + fbh[1]), k,
+                tma_store_box(out_map, stg + (ew * 2 + 1) * STG_BOX, (int)(kPrefix + fbh[1]), k,
                               pol, t, mt * (TM / 2) + quarter * 16);
             }
           }
@@ -535,9 +563,9 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const TcArgs a,
         // two halves of beam rb; k_sigma adds the two column halves
         pw += __shfl_xor_sync(0xffffffffu, pw, 1);
         if (beam_ok && !odd && a.write_power) {
-          for (int t = 0; t < a.Tr; ++t) {
-            const long long j = ((long long)b * a.Tr + t) * a.P + pol;
-            a.power_part[(j * a.K + k) * (2LL * a.n_chunks_total) +
+          for (int t = 0; t < pl.Tr; ++t) {
+            const long long j = ((long long)b * pl.Tr + t) * a.P + pol;
+            pl.power_part[(j * pl.K + k) * (2LL * a.n_chunks_total) +
                          2 * (a.chunk_base + q.chunk()) + col_half] = pw;
           }
         }
@@ -655,30 +683,24 @@ size_t tc_smem(const Shape& sh) {            // the largest configuration
 }
 
 cudaError_t init_tc_attributes(const Shape& sh) {
-  return cudaFuncSetAttribute(k_beamform_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem(sh));
+  return raise_smem_limit((const void*)k_beamform_tc, tc_smem(sh));
 }
 
-cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_stride,
-                               const Chunk& c, cudaStream_t s, PolSel ps) {
-  const auto& sh = p.shape;
+// Plans plans[0..n) (same stations, polarisations, block length and chunking;
+// the first plan's ring depths), plan i reading its pol slabs at xs[i], in one
+// launch.
+cudaError_t launch_beamform_tc_plans(const lp_plan* const* plans, const void* const* xs,
+                                     long long pol_stride, int n, const Chunk& c, cudaStream_t s,
+                                     PolSel ps) {
+  const lp_plan& p0 = *plans[0];
+  const auto& sh = p0.shape;
   TcArgs a;
-  a.x = static_cast<const int8_t*>(x);
-  a.pol_stride = pol_stride;
-  a.wtc = p.buf.wtc;
-  a.dd = p.buf.dd;
-  a.beams = p.buf.beams;
-  a.power_part = p.buf.power_part;
-  a.err = p.buf.err;
+  a.err = p0.buf.err;
   a.S = sh.S;
   a.P = sh.P;
-  a.K = sh.K;
-  a.B = sh.B;
-  a.Tr = sh.Tr;
-  a.n_mt = (sh.B + TM / 2 - 1) / (TM / 2);
   a.n_chunks = (int)((c.nf + CHUNK - 1) / CHUNK);
   a.F = c.nf;
-  a.row = p.row();
+  a.row = p0.row();
   a.F_in = sh.F;
   a.f_base = c.f_base;
   a.chunk_base = (int)(c.f_base / CHUNK);
@@ -687,20 +709,45 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_st
   a.write_power = c.write_power ? 1 : 0;
   a.pol0 = ps.pol0;
   a.npol = ps.npol ? ps.npol : sh.P;
-  a.n_items = (long long)sh.K * a.n_mt * a.npol * a.n_chunks;
+  a.n = n;
+  long long items = 0, kms = 0;
+  for (int i = 0; i < n; ++i) {
+    const lp_plan& p = *plans[i];
+    TcPlan& q = a.pl[i];
+    q.x = static_cast<const int8_t*>(xs[i]);
+    q.pol_stride = pol_stride;
+    q.wtc = p.buf.wtc;
+    q.dd = p.buf.dd;
+    q.power_part = p.buf.power_part;
+    q.K = p.shape.K;
+    q.B = p.shape.B;
+    q.Tr = p.shape.Tr;
+    q.n_mt = (p.shape.B + TM / 2 - 1) / (TM / 2);
+    q.km0 = kms;
+    kms += (long long)q.K * q.n_mt;
+    items += (long long)q.K * q.n_mt * a.npol * a.n_chunks;
+    q.item_end = items;
+    std::memcpy(&a.maps[i], p.beams_map, sizeof(CUtensorMap));
+  }
+  a.n_items = items;
   tc_depths(sh, &a.n_s8, &a.n_sb);
-  if (p.gemm_cfg >= 0) {                       // autotuned depths
+  if (p0.gemm_cfg >= 0) {                      // autotuned depths
     int desc[2 * MAX_S8 * MAX_SB];
-    const int n = tc_configs(sh, desc, MAX_S8 * MAX_SB);
-    if (p.gemm_cfg < n) {
-      a.n_s8 = desc[2 * p.gemm_cfg];
-      a.n_sb = desc[2 * p.gemm_cfg + 1];
+    const int nc = tc_configs(sh, desc, MAX_S8 * MAX_SB);
+    if (p0.gemm_cfg < nc) {
+      a.n_s8 = desc[2 * p0.gemm_cfg];
+      a.n_sb = desc[2 * p0.gemm_cfg + 1];
     }
   }
   const long long grid = std::min<long long>(a.n_items, (long long)num_sms());
-  k_beamform_tc<<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(
-      a, *reinterpret_cast<const CUtensorMap*>(p.beams_map));
+  k_beamform_tc<<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_stride,
+                               const Chunk& c, cudaStream_t s, PolSel ps) {
+  const lp_plan* one = &p;
+  return launch_beamform_tc_plans(&one, &x, pol_stride, 1, c, s, ps);
 }
 
 }  // namespace lp

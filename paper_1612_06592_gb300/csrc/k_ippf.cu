@@ -346,22 +346,23 @@ __device__ __forceinline__ void pair_dft(float2* slot, const float4* st,
   }
 }
 
-// Trigger output of a launch (kernel parameter; read from the constant bank).
-struct TrigOut {
-  TriggerRec* trig;
-  unsigned long long* count;
-  long long cap;
-  int P, Tr;
-  int pol0, npol;          // polarisations of this launch (stream map, sel_stream)
+// Per-batch context of the FIR role.
+struct FirCtx {
+  float th2;
+  float sig;               // sigma of the stream (trigger records)
+  int j;                   // stream index within its plan
+  unsigned ymask, vmask;   // output frames of the batch / those that may trigger
+  long long n_row0;        // sample index of batch row 0, phase 0
+  float* yrow;             // y of batch row 0 (or null)
 };
 
+// o: the stream's plan in the launch's parameter block; j its stream index in
+// the plan, sig its sigma.
 __device__ __noinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmask, float th2,
-                                           int p, long long n_row0, const TrigOut& o,
-                                           const float* __restrict__ theta, float k_sigma) {
+                                           int p, long long n_row0, int j, float sig,
+                                           const IppfPlan& o) {
   const int lane = threadIdx.x & 31;
-  const int j = (int)sel_stream(blockIdx.y, o.P, o.pol0, o.npol);
   const int P = o.P, Tr = o.Tr;
-  const float sig = theta[j] / k_sigma;
 #pragma unroll
   for (int f = 0; f < FB; ++f) {
     const bool hit = ((vmask >> f) & 1u) && e2v[f] > th2;
@@ -388,22 +389,13 @@ __device__ __noinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmas
   }
 }
 
-// Per-batch context of the FIR role.
-struct FirCtx {
-  float th2;
-  unsigned ymask, vmask;   // output frames of the batch / those that may trigger
-  long long n_row0;        // sample index of batch row 0, phase 0
-  float* yrow;             // y of batch row 0 (or null)
-};
-
 // FIR of one phase over one batch.  hist: the phase's 16 history slots (frame
 // r at slot r mod 16, (re, im) in consecutive columns); zn: the 8 new frames.
 // ODD selects where the 15 history frames r0-15 .. r0-1 sit (r0 mod 16 = 8 ODD).
 template <int ODD>
 __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float (&hist)[32],
                                           const float2 (&zn)[FB], int p, const FirCtx& c,
-                                          const TrigOut& o, const float* __restrict__ theta,
-                                          float k_sigma) {
+                                          const IppfPlan& o) {
   float2 w[kHist + FB];
 #pragma unroll
   for (int i = 0; i < kHist; ++i) {
@@ -425,7 +417,7 @@ __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float
     emax = fmaxf(emax, e2v[f]);         // frames outside the run are filtered by vmask
   }
   if (__any_sync(0xffffffffu, emax > c.th2))
-    emit_triggers(e2v, c.vmask, c.th2, p, c.n_row0, o, theta, k_sigma);
+    emit_triggers(e2v, c.vmask, c.th2, p, c.n_row0, c.j, c.sig, o);
 }
 
 // Bits [lo, hi) of an 8-bit frame mask (lo, hi clamped to [0, 8]).
@@ -439,34 +431,40 @@ __device__ __forceinline__ unsigned frame_bits(int lo, int hi) {
 // tensor memory; the new frames then replace the history slots r0 mod 16 ...
 __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t thist,
                                         const float2 (&zn)[FB], int p, int r0, bool outputs,
-                                        const FirCtx& c, const TrigOut& o,
-                                        const float* __restrict__ theta, float k_sigma) {
+                                        const FirCtx& c, const IppfPlan& o) {
   if (outputs) {
     float hist[32];
     tmem_ld32(thist, hist);
     tmem_wait_ld();
     if (r0 & 8)
-      fir_phase<1>(gq, hist, zn, p, c, o, theta, k_sigma);
+      fir_phase<1>(gq, hist, zn, p, c, o);
     else
-      fir_phase<0>(gq, hist, zn, p, c, o, theta, k_sigma);
+      fir_phase<0>(gq, hist, zn, p, c, o);
   }
 #pragma unroll
   for (int f = 0; f < FB; ++f) tmem_st2(thist + 2 * ((r0 & 8) + f), zn[f]);
 }
 
-__global__ void __launch_bounds__(NT, 1) k_ippf(
-    const float2* __restrict__ beams, int K, int first_bin, long long F, long long row,
-    int frames_per_cta, const float* __restrict__ g, const float4* __restrict__ tw,
-    const float* __restrict__ theta, const float* __restrict__ theta2, float k_sigma,
-    const long long* __restrict__ blk, long long F_total, long long f_base, float* __restrict__ y,
-    const __grid_constant__ TrigOut tout) {
+// One launch covers the streams of a.n plans (one plan, or a group of plans
+// fused into one launch): blockIdx.y counts the launch streams of plan 0, then
+// plan 1, ...; every plan has its own beam rows, thresholds, block counter and
+// trigger list, and all share the frame range and the tiling.
+__global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs a) {
   extern __shared__ float4 smem4[];
   float2* ring = reinterpret_cast<float2*>(smem4);      // [2 buffers][8 frames][1024]
   float4* stage = smem4 + FB * kM;                        // [2 buffers][4 pairs][SPAIR]
   __shared__ uint32_t tmem_slot;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int j = (int)sel_stream(blockIdx.y, tout.P, tout.pol0, tout.npol);
+  int pi = 0;
+  while (pi + 1 < a.n && (int)blockIdx.y >= a.pl[pi].stream_end) ++pi;
+  const IppfPlan& pl = a.pl[pi];
+  const int jj = (int)blockIdx.y - (pi ? a.pl[pi - 1].stream_end : 0);
+  const int j = (int)sel_stream(jj, pl.P, a.pol0, a.npol);
+  const int K = pl.K, first_bin = pl.first_bin, frames_per_cta = a.frames_per_cta;
+  const long long F = a.F, row = a.row;
+  const float2* __restrict__ beams = pl.beams;
+  const float4* __restrict__ tw = pl.tw;
   const long long m0 = (long long)blockIdx.x * frames_per_cta;
   const long long m1 = min((long long)(m0 + frames_per_cta), (long long)(F));
   const int nout = (int)(m1 - m0);
@@ -519,7 +517,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
       float tq[32];
 #pragma unroll
       for (int t = 0; t < kTaps; ++t) {
-        const float gt = g[t * kM + p];
+        const float gt = pl.g[t * kM + p];
         tq[2 * t] = gt;
         tq[2 * t + 1] = gt;
       }
@@ -528,12 +526,15 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     }
     tmem_wait_st();
     FirCtx c;
-    c.th2 = theta2[j];
+    c.th2 = pl.theta2[j];
+    c.sig = pl.theta[j] / pl.k_sigma;
+    c.j = j;
+    const long long F_total = a.F_total, f_base = a.f_base;
     // this launch covers block frames [f_base, f_base + F) (one chunk, or the block)
-    float* yj = y ? y + ((long long)j * F_total + f_base) * kM : nullptr;
+    float* yj = pl.y ? pl.y + ((long long)j * F_total + f_base) * kM : nullptr;
     // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
     // m < 15 of the first block) never trigger
-    const long long bidx = *blk;
+    const long long bidx = *pl.blk;
     const long long n_first = (bidx * F_total + f_base - kHist) * (long long)kM;
     const int frame_min_trigger = (bidx == 0 && f_base == 0) ? kHist : 0;
     // run row r (frame m0 - 16 + r) is an output for r in [16, nfr) and may
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
 #pragma unroll
           for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
           fir_one(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0, outputs, c,
-                  tout, theta, k_sigma);
+                  pl);
         }
       }
       tmem_wait_st();                    // history slots written before the next batch reads them
@@ -592,20 +593,19 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// Block noise power and running sigma (one block of 256 threads per stream).
+// Block noise power and running sigma (one block of 256 threads per stream;
+// the streams of a.n plans, plan 0's first).
 // Pi = (2 G2 / M^3) * (1/F) * sum_{m,k} |beam|^2, G2 = sum g^2 = M^4 sum h^2 / (sum h)^2;
 // s2 = Pi (first block) or (1 - alpha) s2 + alpha Pi; theta = k_sigma sqrt(s2).
-__global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, int n_per_stream,
-                                               const double* __restrict__ sums, long long F,
-                                               double alpha, double k_sigma,
-                                               const long long* __restrict__ blk,
-                                               double* __restrict__ sigma2,
-                                               float* __restrict__ theta,
-                                               float* __restrict__ theta2, int P, int pol0,
-                                               int npol) {
+__global__ void __launch_bounds__(256) k_sigma(const __grid_constant__ SigmaArgs a) {
   __shared__ double red[256];
-  const long long j = sel_stream(blockIdx.x, P, pol0, npol);
-  const float* pj = part + (long long)j * n_per_stream;
+  int pi = 0;
+  while (pi + 1 < a.n && (int)blockIdx.x >= a.pl[pi].stream_end) ++pi;
+  const SigmaPlan& pl = a.pl[pi];
+  const int jj = (int)blockIdx.x - (pi ? a.pl[pi - 1].stream_end : 0);
+  const long long j = sel_stream(jj, pl.P, a.pol0, a.npol);
+  const int n_per_stream = pl.n_per_stream;
+  const float* pj = pl.part + j * n_per_stream;
   double acc = 0.0;
   for (int i = threadIdx.x; i < n_per_stream; i += 256) acc += (double)pj[i];
   red[threadIdx.x] = acc;
@@ -616,32 +616,35 @@ __global__ void __launch_bounds__(256) k_sigma(const float* __restrict__ part, i
   }
   if (threadIdx.x == 0) {
     const double m = (double)kM;
-    const double g2 = m * m * m * m * sums[1] / (sums[0] * sums[0]);
-    const double pi = 2.0 * g2 / (m * m * m) * red[0] / (double)F;
-    const double s2 = *blk == 0 ? pi : (1.0 - alpha) * sigma2[j] + alpha * pi;
-    sigma2[j] = s2;
-    const double th = k_sigma * sqrt(s2);
-    theta[j] = (float)th;
-    theta2[j] = (float)(th * th);
+    const double g2 = m * m * m * m * pl.sums[1] / (pl.sums[0] * pl.sums[0]);
+    const double pw = 2.0 * g2 / (m * m * m) * red[0] / (double)a.F;
+    const double s2 = *pl.blk == 0 ? pw : (1.0 - pl.alpha) * pl.sigma2[j] + pl.alpha * pw;
+    pl.sigma2[j] = s2;
+    const double th = pl.k_sigma * sqrt(s2);
+    pl.theta[j] = (float)th;
+    pl.theta2[j] = (float)(th * th);
+    if (pl.count && jj == 0) *pl.count = 0;
   }
 }
 
 // Carry the last 16 frames of every (stream, bin) row into the row prefix and
-// advance the device block counter.
-// The last 16 frames of each row become the next block's prefix, in the beam
-// rows and (fine de-dispersion) in the filtered rows.
-__global__ void k_history_shift(float2* __restrict__ beams, float2* __restrict__ fine,
-                                long long rows, int K, long long F, long long row,
-                                long long* __restrict__ blk, int advance, int P, int pol0,
-                                int npol) {
+// advance the device block counter: the last 16 frames of each row become the
+// next block's prefix, in the beam rows and (fine de-dispersion) in the
+// filtered rows.  Elements of plan 0's rows first, then plan 1's, ...
+__global__ void k_history_shift(const __grid_constant__ ShiftArgs a) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i == 0 && advance) *blk += 1;
-  if (i >= rows * kPrefix) return;
-  const long long rr = i / kPrefix;      // launch row: stream jj, bin k
-  const int f = (int)(i % kPrefix);
-  const long long r = sel_stream(rr / K, P, pol0, npol) * K + rr % K;
-  beams[r * row + f] = beams[r * row + F + f];
-  if (fine) fine[r * row + f] = fine[r * row + F + f];
+  int pi = 0;
+  while (pi + 1 < a.n && i >= a.pl[pi].elem_end) ++pi;
+  const ShiftPlan& pl = a.pl[pi];
+  const long long i0 = pi ? a.pl[pi - 1].elem_end : 0;
+  if (i == i0 && a.advance) *pl.blk += 1;
+  if (i >= pl.elem_end) return;
+  const long long rr = (i - i0) / kPrefix;      // launch row of the plan: stream jj, bin k
+  const int f = (int)((i - i0) % kPrefix);
+  const long long r = sel_stream(rr / pl.K, pl.P, a.pol0, a.npol) * pl.K + rr % pl.K;
+  const long long row = a.row, F = a.F;
+  pl.beams[r * row + f] = pl.beams[r * row + F + f];
+  if (pl.fine) pl.fine[r * row + f] = pl.fine[r * row + F + f];
 }
 
 size_t ippf_smem_bytes() {
@@ -661,44 +664,126 @@ int ippf_default_frames_per_cta(const Shape& sh) {
 }
 
 cudaError_t init_ippf_attributes() {
-  return cudaFuncSetAttribute(k_ippf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)ippf_smem_bytes());
+  return raise_smem_limit((const void*)k_ippf, ippf_smem_bytes());
+}
+
+IppfPlan ippf_plan(const lp_plan& p) {
+  IppfPlan q{};
+  q.beams = synth_rows(p);
+  q.g = p.buf.g;
+  q.tw = p.buf.tw1024;
+  q.theta = p.buf.theta;
+  q.theta2 = p.buf.theta2;
+  q.blk = p.buf.blk;
+  q.y = p.buf.y;
+  q.trig = p.buf.trig;
+  q.count = p.buf.trig_count;
+  q.cap = (long long)p.cfg.trigger_cap;
+  q.k_sigma = (float)p.cfg.k_sigma;
+  q.K = p.shape.K;
+  q.first_bin = p.cfg.first_bin;
+  q.P = p.shape.P;
+  q.Tr = p.shape.Tr;
+  return q;
+}
+
+// Plans plans[0..n) (same block length, chunking and tiling) in one launch.
+cudaError_t launch_ippf_plans(const lp_plan* const* plans, int n, const Chunk& c, cudaStream_t s,
+                              PolSel ps) {
+  const lp_plan& p0 = *plans[0];
+  const int fpc = p0.frames_per_cta;
+  const int npol = ps.npol ? ps.npol : p0.shape.P;
+  IppfArgs a;
+  a.F = c.nf;
+  a.row = p0.row();
+  a.F_total = p0.shape.F;
+  a.f_base = c.f_base;
+  a.frames_per_cta = fpc;
+  a.pol0 = ps.pol0;
+  a.npol = npol;
+  a.n = n;
+  int streams = 0;
+  for (int i = 0; i < n; ++i) {
+    a.pl[i] = ippf_plan(*plans[i]);
+    streams += plans[i]->shape.J() / plans[i]->shape.P * npol;
+    a.pl[i].stream_end = streams;
+  }
+  const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)streams);
+  k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel ps) {
-  const auto& sh = p.shape;
-  const int fpc = p.frames_per_cta;
-  const int npol = ps.npol ? ps.npol : sh.P;
-  const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)(sh.J() / sh.P * npol));
-  const TrigOut tout{p.buf.trig, p.buf.trig_count, (long long)p.cfg.trigger_cap, sh.P, sh.Tr,
-                     ps.pol0, npol};
-  k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(synth_rows(p), sh.K, p.cfg.first_bin, c.nf, p.row(), fpc,
-                                             p.buf.g, p.buf.tw1024, p.buf.theta, p.buf.theta2,
-                                             (float)p.cfg.k_sigma, p.buf.blk, sh.F, c.f_base,
-                                             p.buf.y, tout);
+  const lp_plan* one = &p;
+  return launch_ippf_plans(&one, 1, c, s, ps);
+}
+
+cudaError_t launch_sigma_plans(const lp_plan* const* plans, int n, bool zero_counts,
+                               cudaStream_t s, PolSel ps) {
+  const lp_plan& p0 = *plans[0];
+  const int npol = ps.npol ? ps.npol : p0.shape.P;
+  SigmaArgs a;
+  a.F = p0.shape.F;
+  a.pol0 = ps.pol0;
+  a.npol = npol;
+  a.n = n;
+  int streams = 0;
+  for (int i = 0; i < n; ++i) {
+    const lp_plan& p = *plans[i];
+    SigmaPlan& q = a.pl[i];
+    q.part = p.buf.power_part;
+    q.sums = p.buf.filter_sums;
+    q.blk = p.buf.blk;
+    q.sigma2 = p.buf.sigma2;
+    q.theta = p.buf.theta;
+    q.theta2 = p.buf.theta2;
+    q.count = zero_counts ? p.buf.trig_count : nullptr;
+    q.alpha = p.cfg.sigma_alpha;
+    q.k_sigma = p.cfg.k_sigma;
+    q.n_per_stream = p.shape.K * p.n_ftiles_bf;
+    q.P = p.shape.P;
+    streams += p.shape.J() / p.shape.P * npol;
+    q.stream_end = streams;
+  }
+  k_sigma<<<streams, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s, PolSel ps) {
-  const auto& sh = p.shape;
-  const int npol = ps.npol ? ps.npol : sh.P;
-  k_sigma<<<sh.J() / sh.P * npol, 256, 0, s>>>(p.buf.power_part, sh.K * p.n_ftiles_bf,
-                                               p.buf.filter_sums, sh.F, p.cfg.sigma_alpha,
-                                               p.cfg.k_sigma, p.buf.blk, p.buf.sigma2, p.buf.theta,
-                                               p.buf.theta2, sh.P, ps.pol0, npol);
+  const lp_plan* one = &p;
+  return launch_sigma_plans(&one, 1, false, s, ps);
+}
+
+cudaError_t launch_history_shift_plans(const lp_plan* const* plans, int n, const Chunk& c,
+                                       cudaStream_t s, PolSel ps) {
+  const lp_plan& p0 = *plans[0];
+  const int npol = ps.npol ? ps.npol : p0.shape.P;
+  ShiftArgs a;
+  a.F = c.nf;
+  a.row = p0.row();
+  a.advance = c.last && ps.pol0 + npol == p0.shape.P ? 1 : 0;
+  a.pol0 = ps.pol0;
+  a.npol = npol;
+  a.n = n;
+  long long elems = 0;
+  for (int i = 0; i < n; ++i) {
+    const lp_plan& p = *plans[i];
+    ShiftPlan& q = a.pl[i];
+    q.beams = p.buf.beams;
+    q.fine = p.buf.beams_fine;
+    q.blk = p.buf.blk;
+    q.K = p.shape.K;
+    q.P = p.shape.P;
+    elems += (long long)p.shape.J() / p.shape.P * npol * p.shape.K * kPrefix;
+    q.elem_end = elems;
+  }
+  k_history_shift<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel ps) {
-  const auto& sh = p.shape;
-  const int npol = ps.npol ? ps.npol : sh.P;
-  const long long rows = (long long)sh.J() / sh.P * npol * sh.K;
-  const long long n = rows * kPrefix;
-  const bool advance = c.last && ps.pol0 + npol == sh.P;
-  k_history_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.buf.beams, p.buf.beams_fine, rows, sh.K, c.nf,
-                                                              p.row(), p.buf.blk, advance ? 1 : 0,
-                                                              sh.P, ps.pol0, npol);
-  return cudaGetLastError();
+  const lp_plan* one = &p;
+  return launch_history_shift_plans(&one, 1, c, s, ps);
 }
 
 cudaError_t init_kernel_attributes(const Shape& sh) {

@@ -93,6 +93,65 @@ struct Shape {
 }  // namespace lp
 
 namespace lp {
+// Plans whose per-block launches can be fused into one launch of each kernel
+// (lp_group): their per-plan parameters travel in the kernel's parameter block.
+constexpr int kMaxGroup = LP_MAX_GROUP;
+
+// Per-plan parameters of the synthesis kernel.
+struct IppfPlan {
+  const float2* beams;     // rows the synthesis reads (the plan's synth_rows)
+  const float* g;
+  const float4* tw;
+  const float* theta;
+  const float* theta2;
+  const long long* blk;
+  float* y;
+  TriggerRec* trig;
+  unsigned long long* count;
+  long long cap;
+  float k_sigma;
+  int K, first_bin, P, Tr;
+  int stream_end;          // launch streams of plans 0 .. this one
+};
+struct IppfArgs {
+  long long F, row, F_total, f_base;   // frames of the launch, row length, block frames, offset
+  int frames_per_cta, pol0, npol, n;
+  IppfPlan pl[kMaxGroup];
+};
+
+// Per-plan parameters of the noise-level kernel.
+struct SigmaPlan {
+  const float* part;             // noise partials [J][n_per_stream]
+  const double* sums;            // sum h, sum h^2 of the prototype
+  const long long* blk;
+  double* sigma2;
+  float* theta;
+  float* theta2;
+  unsigned long long* count;     // trigger counter zeroed here (group launches) or null
+  double alpha, k_sigma;
+  int n_per_stream, P;
+  int stream_end;
+};
+struct SigmaArgs {
+  long long F;
+  int pol0, npol, n;
+  SigmaPlan pl[kMaxGroup];
+};
+
+// Per-plan parameters of the history shift.
+struct ShiftPlan {
+  float2* beams;
+  float2* fine;
+  long long* blk;
+  int K, P;
+  long long elem_end;            // shifted elements (rows x 16) of plans 0 .. this one
+};
+struct ShiftArgs {
+  long long F, row;
+  int advance, pol0, npol, n;
+  ShiftPlan pl[kMaxGroup];
+};
+
 // One launch range of a block: frames [f_base, f_base + nf) of the block.
 struct Chunk {
   long long f_base = 0, nf = 0;
@@ -172,6 +231,18 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_st
                                const Chunk& c, cudaStream_t s, PolSel ps = {});
 cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s, PolSel ps = {});
 cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel ps = {});
+// One launch of a kernel for the plans of a group (see lp_group in lp.h):
+// plan i reads its polarisation slabs at xs[i].  zero_counts: the noise-level
+// launch also zeroes every plan's trigger counter.
+cudaError_t launch_beamform_tc_plans(const lp_plan* const* plans, const void* const* xs,
+                                     long long pol_stride, int n, const Chunk& c, cudaStream_t s,
+                                     PolSel ps = {});
+cudaError_t launch_sigma_plans(const lp_plan* const* plans, int n, bool zero_counts,
+                               cudaStream_t s, PolSel ps = {});
+cudaError_t launch_ippf_plans(const lp_plan* const* plans, int n, const Chunk& c, cudaStream_t s,
+                              PolSel ps = {});
+cudaError_t launch_history_shift_plans(const lp_plan* const* plans, int n, const Chunk& c,
+                                       cudaStream_t s, PolSel ps = {});
 // advances the device block counter when c.last and ps covers the last pol
 cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t s,
                                  PolSel ps = {});
@@ -188,6 +259,10 @@ inline const float2* synth_rows(const lp_plan& p);
 
 // Opt-in shared-memory limits of the kernels (per device; call with it current).
 cudaError_t init_kernel_attributes(const Shape& sh);
+// The opt-in limit is a property of the kernel on the current device, shared by
+// every plan of the process: it is only ever raised (to the largest need seen),
+// so a plan that needs less never lowers the limit another plan launches with.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
 
 int beamform_f32_frame_tile();
 // Beamformer configurations the GEMM autotuner may pick, two ints each: FP16 form

@@ -426,9 +426,9 @@ lp_status lp_prebeam_set_groups(lp_prebeam* pb, const int32_t* group_of_station,
   const int smem = (int)prebeam_smem(*pb);
   if (smem > 227 * 1024) return pb_fail(pb, LP_ERR_ARG, "too many stations for one tile");
   if (pb->input_dtype == LP_INPUT_INT8)
-    PB_CUDA(pb, cudaFuncSetAttribute(k_prebeam<char2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PB_CUDA(pb, raise_smem_limit((const void*)k_prebeam<char2>, (size_t)smem));
   else
-    PB_CUDA(pb, cudaFuncSetAttribute(k_prebeam<short2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PB_CUDA(pb, raise_smem_limit((const void*)k_prebeam<short2>, (size_t)smem));
   pb->centres = centres;
   pb->last_stream = s;
   pb->groups_set = true;

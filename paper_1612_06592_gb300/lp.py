@@ -104,9 +104,16 @@ SIGNATURES = {
     "lp_prebeam_saturated": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lp_prebeam_last_error": (ctypes.c_char_p, [_P]),
     "lp_prebeam_destroy": (None, [_P]),
+    "lp_group_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
+    "lp_group_process_block": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "lp_group_size": (ctypes.c_int, [_P]),
+    "lp_group_launches_per_block": (ctypes.c_int, [_P]),
+    "lp_group_last_error": (ctypes.c_char_p, [_P]),
+    "lp_group_destroy": (None, [_P]),
     "lp_last_error": (ctypes.c_char_p, [_P]),
     "lp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
+LP_MAX_GROUP = 32
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -342,6 +349,41 @@ class Plan:
             _lib.lp_plan_destroy(self._h)
             self._h = _P()
             self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Plans whose blocks run in shared launches (lp_group): one beamformer,
+    noise-level, synthesis and history-shift launch per block for all of them.
+    The plans stay the caller's and must outlive the group."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (_P * len(self.plans))(*[p._h for p in self.plans])
+        self._h = _P()
+        st = _lib.lp_group_create(ctypes.byref(self._h), arr, len(self.plans))
+        if st != LP_OK:
+            raise LPError(st, "lp_group_create: the plans cannot form a group")
+
+    def lp_group_process_block(self, x, subbands, first_bin, stream=None):
+        """x: device block [P, subbands, F, S, 2] int8 (bins first_bin ...)."""
+        st = _lib.lp_group_process_block(self._h, _ptr(x), int(subbands), int(first_bin),
+                                          _stream_ptr(stream))
+        if st != LP_OK:
+            raise LPError(st, "lp_group_process_block: " + _lib.lp_group_last_error(self._h).decode())
+
+    def lp_group_launches_per_block(self):
+        return _lib.lp_group_launches_per_block(self._h)
+
+    def close(self):
+        if self._h:
+            _lib.lp_group_destroy(self._h)
+            self._h = _P()
 
     def __del__(self):
         try:

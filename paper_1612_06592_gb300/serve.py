@@ -5,15 +5,21 @@ one block of 65536 frames every 0.336 s.  Requests subscribe to it with their
 own shape: a subset of the 50 beams, a contiguous range of 122..488 subbands,
 1..4 STEC trials, for a number of blocks.  Each admitted request is a session:
 one plan of the C ABI with its own workspace (synthesis history and running
-noise level stay on the device between blocks) and its own CUDA stream.
+noise level stay on the device between blocks).
 
 Per block: the block is copied once from pinned host memory into a device
-buffer shared by all sessions; every active session launches its whole
-pipeline on its stream against its subband range of that buffer (a strided
-view, no copy), so sessions overlap on the device; each session's triggers
-come back to the host.  Requests that arrive wait in a queue and are admitted
-at a block boundary as soon as their workspace fits in the HBM budget next to
-the sessions already running; finished sessions free theirs.
+buffer shared by all sessions.  Batched (the default, FP16 form): the active
+sessions' plans form a group (lp_group) and the whole block runs as four
+launches -- one beamformer over every session's beams and subbands, one noise
+level, one synthesis over every session's streams, one history shift --
+however many sessions there are; each session reads its own subband range of
+the buffer.  Unbatched (FP32 form, or batch=False): every session launches its
+own pipeline on its own CUDA stream and sessions overlap on the device.  Each
+session's triggers come back to the host.  Requests that arrive wait in a
+queue and are admitted at a block boundary as soon as their workspace fits in
+the HBM budget next to the sessions already running and their predicted
+device time fits the time budget; finished sessions free theirs.  The cost
+model of that prediction is measured at start-up (``Server.calibrate``).
 
 Latency of a block = time from its arrival (the realtime clock of the stream)
 to the moment the last session's triggers for it are on the host.  All compute
@@ -97,21 +103,51 @@ def make_requests(seed, n_blocks, n_beams_grid=50, n_sub=488, rate=0.25, min_sub
     return reqs
 
 
-# Device time of one session per block, ms, on GB300 (FP16 form), measured
-# alone: the synthesis costs ~0.30 ms per stream of 65536 frames whatever the
-# subband count (the inverse DFT is always 1024 points); the beamformer ~7.5 ms
-# per 50 beams x 2 pols x 488 subbands.  Sessions sharing the GPU run slower
-# than the sum of their lone times suggests (small grids, interference), so
-# admission multiplies the sum by a correction learned from the measured block
-# times, starting from a conservative value.
-MS_PER_STREAM = 0.30
-MS_PER_BEAM_POL_SUBBAND = 7.5 / (50 * 2 * 488)
-INITIAL_CORRECTION = 2.0
+class CostModel:
+    """Device time of a block of sessions, ms:
+        T = (F / 65536) * (c0 + sum_s (c_stream * J_s + c_bpk * B_s * P * K_s)),
+    J_s = B_s Tr_s P the session's streams (the synthesis costs the same per
+    stream whatever its subband count: the inverse DFT is always 1024 points)
+    and B_s P K_s its beam rows (the beamformer).  The coefficients are
+    measured at start-up by Server.calibrate; until then (and in host-only
+    tests) a prior holds: c0 = 0, 0.3 ms per stream, 7.5 ms per 50 x 2 x 488
+    beam rows (a GB300 measurement of one whole-band session)."""
+
+    def __init__(self, c0=0.0, c_stream=0.30, c_bpk=7.5 / (50 * 2 * 488), measured=False):
+        self.c0, self.c_stream, self.c_bpk, self.measured = c0, c_stream, c_bpk, measured
+
+    def session(self, P, K, B, Tr, F):
+        return F / 65536.0 * (self.c_stream * B * Tr * P + self.c_bpk * B * P * K)
+
+    def fixed(self, F):
+        return F / 65536.0 * self.c0
+
+    @classmethod
+    def fit(cls, samples):
+        """Least squares over samples [(F, [(P, K, B, Tr), ...], ms), ...]."""
+        rows, y = [], []
+        for F, sessions, ms in samples:
+            sc = F / 65536.0
+            rows.append([sc, sc * sum(B * Tr * P for P, K, B, Tr in sessions),
+                         sc * sum(B * P * K for P, K, B, Tr in sessions)])
+            y.append(ms)
+        coef, *_ = np.linalg.lstsq(np.array(rows), np.array(y), rcond=None)
+        c0, cs, cb = (max(0.0, float(v)) for v in coef)
+        return cls(c0, cs, cb, measured=True)
+
+    def as_dict(self):
+        return {"c0_ms": self.c0, "ms_per_stream": self.c_stream,
+                "ms_per_beam_pol_subband": self.c_bpk, "measured": self.measured}
 
 
-def session_cost_ms(P, K, B, Tr, F):
-    scale = F / 65536.0
-    return scale * (MS_PER_STREAM * B * Tr * P + MS_PER_BEAM_POL_SUBBAND * B * P * K)
+PRIOR = CostModel()
+# admission multiplies the modelled time by a correction learned from the
+# measured block times, starting from this margin above the calibrated model
+INITIAL_CORRECTION = 1.25
+
+
+def session_cost_ms(P, K, B, Tr, F, model: CostModel = PRIOR):
+    return model.session(P, K, B, Tr, F)
 
 
 class Server:
@@ -125,7 +161,7 @@ class Server:
 
     def __init__(self, stations, pols, n_sub, first_bin, block_len, station_enu, beam_grid,
                  hbm_budget_bytes, precision="fp16", k_sigma=6.0, use_graph=False, device=0,
-                 time_budget_ms=None):
+                 time_budget_ms=None, batch=True):
         import torch
         self.torch = torch
         self.S, self.P, self.n_sub, self.fb0, self.F = stations, pols, n_sub, first_bin, block_len
@@ -148,6 +184,14 @@ class Server:
         self.cost_corr = INITIAL_CORRECTION   # measured / modelled session time
         self.cost_used = 0.0
         self.copy_ms = 0.0                    # measured ingest time of a block
+        self.model = PRIOR
+        # batched: every session's plan joins one group per block (FP16 form)
+        self.batch = bool(batch) and precision == "fp16"
+        self.stream = torch.cuda.Stream(device=self.device)   # the batched launches
+        self.groups = []
+        self.group_key = None
+        self.launches = []                    # kernel launches per block
+        self.calibration = []
 
     # -- admission ---------------------------------------------------------
     def submit(self, req: Request):
@@ -162,7 +206,10 @@ class Server:
         return self.ws_of[key]
 
     def _cost(self, req):
-        return session_cost_ms(self.P, req.nsub, len(req.beams), len(req.tec), self.F)
+        return self.model.session(self.P, req.nsub, len(req.beams), len(req.tec), self.F)
+
+    def _fixed(self):
+        return self.model.fixed(self.F)
 
     def admit(self):
         """Admit queued requests, in arrival order, while memory and time fit."""
@@ -172,7 +219,8 @@ class Server:
             need = self._ws(req)
             cost = self._cost(req)
             too_slow = (self.time_budget_ms is not None
-                        and self.copy_ms + cost * self.cost_corr > self.time_budget_ms)
+                        and self.copy_ms + (self._fixed() + cost) * self.cost_corr
+                        > self.time_budget_ms)
             if need > self.budget or too_slow:
                 self.pending.popleft()          # can never fit: refuse
                 self.log.append(("refused", req.rid, need))
@@ -180,14 +228,15 @@ class Server:
             if self.used + need > self.budget:
                 break                           # wait for memory to free up
             if (self.time_budget_ms is not None and self.active and
-                    self.copy_ms + (self.cost_used + cost) * self.cost_corr > self.time_budget_ms):
+                    self.copy_ms + (self._fixed() + self.cost_used + cost) * self.cost_corr
+                    > self.time_budget_ms):
                 break                           # wait for a time slot
             self.pending.popleft()
-            stream = self.torch.cuda.Stream(device=self.device)
+            stream = self.stream if self.batch else self.torch.cuda.Stream(device=self.device)
             plan = lp.Plan(self.S, self.P, req.nsub, len(req.beams), len(req.tec), self.F,
                            input_dtype="int8", precision=self.precision,
                            first_bin=self.fb0 + req.k0, k_sigma=self.k_sigma,
-                           use_graph=self.use_graph, stream=stream)
+                           use_graph=self.use_graph and not self.batch, stream=stream)
             plan.lp_set_weights(self.enu, self.grid[req.beams], stream=stream)
             plan.lp_set_tec(req.tec, stream=stream)
             self.active[req.rid] = Session(req, plan, stream)
@@ -198,6 +247,8 @@ class Server:
 
     def retire(self):
         gone = [rid for rid, s in self.active.items() if s.blocks_done >= s.req.blocks]
+        if gone:
+            self._drop_groups()
         for rid in gone:
             s = self.active.pop(rid)
             s.plan.close()
@@ -221,11 +272,17 @@ class Server:
         else:
             start.record(torch.cuda.current_stream(self.device))
             ready.record(torch.cuda.current_stream(self.device))
-        pol_stride = self.n_sub * self.F * self.S           # complex samples
-        for s in self.active.values():
-            s.stream.wait_event(ready)
-            off = s.req.k0 * self.F * self.S * 2                 # bytes (complex int8)
-            s.plan.lp_process_block_strided(self.block_dev[off:], pol_stride, stream=s.stream)
+        if self.batch:
+            self._run_groups(ready)
+        else:
+            pol_stride = self.n_sub * self.F * self.S           # complex samples
+            for s in self.active.values():
+                s.stream.wait_event(ready)
+                off = s.req.k0 * self.F * self.S * 2                 # bytes (complex int8)
+                s.plan.lp_process_block_strided(self.block_dev[off:], pol_stride,
+                                                stream=s.stream)
+            self.launches.append(sum(s.plan.lp_launches_per_block()
+                                     for s in self.active.values()))
         out = {}
         for rid, s in self.active.items():
             trig, n, _ = s.plan.lp_get_triggers()
@@ -236,10 +293,88 @@ class Server:
         self.copy_ms = copy if self.copy_ms == 0.0 else 0.8 * self.copy_ms + 0.2 * copy
         return out
 
+    # -- batched launches ------------------------------------------------------
+    def _drop_groups(self):
+        for g in self.groups:
+            g.close()
+        self.groups, self.group_key = [], None
+
+    def _run_groups(self, ready):
+        """One block for every active session in shared launches: the sessions'
+        plans (in admission order) form groups of at most LP_MAX_GROUP plans."""
+        key = tuple(self.active)
+        if key != self.group_key:
+            self._drop_groups()
+            plans = [s.plan for s in self.active.values()]
+            self.groups = [lp.Group(plans[i:i + lp.LP_MAX_GROUP])
+                           for i in range(0, len(plans), lp.LP_MAX_GROUP)]
+            self.group_key = key
+        self.stream.wait_event(ready)
+        for g in self.groups:
+            g.lp_group_process_block(self.block_dev, self.n_sub, self.fb0, stream=self.stream)
+        self.launches.append(sum(g.lp_group_launches_per_block() for g in self.groups))
+
+    def calibrate(self, shapes=((1, 122, 1), (8, 488, 2), (16, 244, 1)), reps=3):
+        """Measure the cost model on this GPU: time one block of sessions of the
+        given (beams, subbands, trials) shapes -- each alone, then all together
+        -- in the launch form the server uses, and fit CostModel by least
+        squares.  Runs before any request is admitted; the results of these
+        blocks are discarded."""
+        torch = self.torch
+        if self.active:
+            raise RuntimeError("calibrate before admitting requests")
+        # seeded noise in the block buffer (a realistic trigger rate)
+        g = torch.Generator(device=self.device)
+        g.manual_seed(17)
+        self.block_dev.copy_(torch.randint(-12, 13, self.block_dev.shape, generator=g,
+                                           device=self.device, dtype=torch.int8))
+        plans, shp = [], []
+        stream = self.stream
+        for (nb, ns, nt) in shapes:
+            plan = lp.Plan(self.S, self.P, ns, nb, nt, self.F, input_dtype="int8",
+                           precision=self.precision, first_bin=self.fb0, k_sigma=self.k_sigma,
+                           stream=stream)
+            plan.lp_set_weights(self.enu, self.grid[:nb], stream=stream)
+            plan.lp_set_tec(np.linspace(10.0, 30.0, nt), stream=stream)
+            plans.append(plan)
+            shp.append((self.P, ns, nb, nt))
+        combos = [[i] for i in range(len(plans))] + [list(range(len(plans)))]
+        samples = []
+        pol_stride = self.n_sub * self.F * self.S
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for combo in combos:
+            grp = lp.Group([plans[i] for i in combo]) if self.batch else None
+
+            def one_block():
+                if grp is not None:
+                    grp.lp_group_process_block(self.block_dev, self.n_sub, self.fb0,
+                                               stream=stream)
+                else:
+                    for i in combo:
+                        plans[i].lp_process_block_strided(self.block_dev, pol_stride,
+                                                          stream=stream)
+            one_block()                                   # warm-up
+            e0.record(stream)
+            for _ in range(reps):
+                one_block()
+            e1.record(stream)
+            e1.synchronize()
+            samples.append((self.F, [shp[i] for i in combo], e0.elapsed_time(e1) / reps))
+            if grp is not None:
+                grp.close()
+        for plan in plans:
+            plan.close()
+        torch.cuda.empty_cache()
+        self.model = CostModel.fit(samples)
+        self.calibration = [{"sessions": [list(x) for x in ses], "ms": ms}
+                            for _, ses, ms in samples]
+        return self.model
+
     def observe(self, block_ms):
         """Update the cost correction from the measured time of the last block."""
         if self.cost_used > 0 and block_ms > self.copy_ms:
-            r = (block_ms - self.copy_ms) / self.cost_used
+            r = (block_ms - self.copy_ms) / (self._fixed() + self.cost_used)
             self.cost_corr = 0.8 * self.cost_corr + 0.2 * r
 
 
@@ -252,7 +387,9 @@ def run(args):
     period = w.block_len * M / FS_HZ
     srv = Server(w.stations, w.pols, w.subbands, w.first_bin, w.block_len, enu, grid,
                  args.budget_gb * 1e9, precision=args.precision, use_graph=args.graph,
-                 time_budget_ms=args.time_budget * period * 1e3 if args.time_budget > 0 else None)
+                 time_budget_ms=args.time_budget * period * 1e3 if args.time_budget > 0 else None,
+                 batch=args.batch)
+    srv.calibrate()
     reqs = make_requests(args.seed, args.blocks, max_beams=args.max_beams)
     # a few distinct blocks of station data, reused cyclically (pinned host memory)
     hosts = []
@@ -296,6 +433,10 @@ def run(args):
         "sessions_mean": float(np.mean(n_sessions)), "sessions_max": int(np.max(n_sessions)),
         "requests": len(reqs), "refused": sum(1 for e in srv.log if e[0] == "refused"),
         "hbm_budget_gb": args.budget_gb,
+        "batched": srv.batch,
+        "launches_per_block": {"mean": float(np.mean(srv.launches)),
+                               "max": int(np.max(srv.launches))},
+        "cost_model": srv.model.as_dict(), "calibration": srv.calibration,
         "time_budget_frac": args.time_budget, "cost_correction": srv.cost_corr,
         "ingest_ms": srv.copy_ms,
         "sustained_blocks_per_s": args.blocks / wall,
@@ -314,6 +455,8 @@ def build_parser():
     ap.add_argument("--max-beams", type=int, default=50)
     ap.add_argument("--distinct-blocks", type=int, default=2)
     ap.add_argument("--graph", action="store_true")
+    ap.add_argument("--batch", action=argparse.BooleanOptionalAction, default=True,
+                    help="sessions' blocks in shared launches (lp_group; FP16 form)")
     ap.add_argument("--realtime", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--time-budget", type=float, default=0.75,
                     help="admit while the predicted block time stays below this fraction "

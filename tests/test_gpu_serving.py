@@ -70,10 +70,11 @@ def test_graph_mode_equals_direct_launches(cuda_lib):
             np.testing.assert_array_equal(u, v)
 
 
-def _serve(lp, reqs, budget, enu, grid, blocks, F, n_sub, fb0, S=8):
+def _serve(lp, reqs, budget, enu, grid, blocks, F, n_sub, fb0, S=8, batch=True):
     import torch
     from paper_1612_06592_gb300.serve import Server
-    srv = Server(S, 2, n_sub, fb0, F, enu, grid, budget, precision="fp16", k_sigma=3.5)
+    srv = Server(S, 2, n_sub, fb0, F, enu, grid, budget, precision="fp16", k_sigma=3.5,
+                 batch=batch)
     hosts = [torch.from_numpy(np.ascontiguousarray(b).reshape(-1)).pin_memory() for b in blocks]
     got = {r.rid: [] for r in reqs}
     admitted_at = {}
@@ -108,6 +109,56 @@ def test_serving_results_identical_alone_and_in_the_mix(cuda_lib):
             assert ba == bm
             np.testing.assert_array_equal(ta, tm)
             np.testing.assert_array_equal(sa, sm)
+
+
+def test_batched_serving_equals_unbatched_and_launches_do_not_grow(cuda_lib):
+    """The batched server (all sessions in four shared launches per block) gives
+    each request exactly the results of the unbatched one (each session its own
+    launches on its own stream); its launch count per block stays 4 while the
+    unbatched count grows with the sessions."""
+    from paper_1612_06592_gb300.serve import Request, Server
+    S, F, n_sub, fb0 = 8, 256, 40, 150
+    grid = synth.hex_beam_directions(6)
+    enu = synth.station_positions(S, 3)
+    rng = np.random.default_rng(45)
+    blocks = [rng.integers(-90, 91, size=(2, n_sub, F, S, 2)).astype(np.int8) for _ in range(4)]
+    reqs = [Request(0, np.array([0, 2, 5]), 3, 20, np.array([8.0]), 0, 4),
+            Request(1, np.array([1]), 0, 40, np.array([5.0, 12.0, 30.0]), 0, 3),
+            Request(2, np.array([0, 1, 2, 3, 4, 5]), 10, 24, np.array([20.0, 35.0]), 1, 3),
+            Request(3, np.array([4]), 16, 24, np.array([9.0]), 1, 2)]
+    batched, _ = _serve(cuda_lib, reqs, 1e12, enu, grid, blocks, F, n_sub, fb0, batch=True)
+    single, _ = _serve(cuda_lib, reqs, 1e12, enu, grid, blocks, F, n_sub, fb0, batch=False)
+    for r in reqs:
+        assert len(batched[r.rid]) == len(single[r.rid]) == r.blocks
+        for (ba, ta, sa), (bs, ts, ss) in zip(batched[r.rid], single[r.rid]):
+            assert ba == bs
+            np.testing.assert_array_equal(ta, ts)
+            np.testing.assert_array_equal(sa, ss)
+    srv = Server(S, 2, n_sub, fb0, F, enu, grid, 1e12, precision="fp16", k_sigma=3.5)
+    import torch
+    h = torch.from_numpy(np.ascontiguousarray(blocks[0]).reshape(-1)).pin_memory()
+    for n in (1, 3, 6):
+        while len(srv.active) < n:
+            k = len(srv.active)
+            srv.submit(Request(100 + k, np.array([k % 6]), 0, 20, np.array([10.0]), 0, 10))
+            srv.admit()
+        srv.run_block(h)
+    assert srv.launches == [4, 4, 4]
+
+
+def test_serving_calibration_measures_a_positive_cost_model(cuda_lib):
+    from paper_1612_06592_gb300.serve import Server
+    S, F, n_sub, fb0 = 8, 2048, 488, 12
+    grid = synth.hex_beam_directions(16)
+    enu = synth.station_positions(S, 3)
+    srv = Server(S, 2, n_sub, fb0, F, enu, grid, 1e12, precision="fp16")
+    m = srv.calibrate()
+    assert m.measured and m.c_stream > 0 and m.c_bpk > 0
+    assert len(srv.calibration) == 4 and all(c["ms"] > 0 for c in srv.calibration)
+    # the fitted model reproduces the combined block within a factor of two
+    comb = srv.calibration[-1]
+    pred = m.fixed(F) + sum(m.session(P, K, B, Tr, F) for P, K, B, Tr in comb["sessions"])
+    assert 0.5 < pred / comb["ms"] < 2.0
 
 
 def test_serving_admission_waits_for_memory(cuda_lib):

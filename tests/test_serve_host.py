@@ -62,6 +62,10 @@ def _server(serve, monkeypatch, budget, time_budget_ms=None):
     srv.cost_corr = serve.INITIAL_CORRECTION
     srv.cost_used = 0.0
     srv.copy_ms = 0.0
+    srv.model = serve.PRIOR
+    srv.batch = False
+    srv.stream = None
+    srv.groups, srv.group_key, srv.launches = [], None, []
     return srv
 
 
@@ -137,3 +141,17 @@ def test_admission_waits_for_a_time_slot_and_learns_the_cost(serve, monkeypatch)
         srv.observe(0.5 * c)
     assert srv.cost_corr < 0.75 * serve.INITIAL_CORRECTION
     assert srv.admit() == [1]
+
+
+def test_cost_model_fit_recovers_the_coefficients(serve):
+    """The start-up calibration fits T = c0 + c_stream * streams + c_bpk * beam rows
+    by least squares: exact data give back the coefficients, at any block length."""
+    truth = serve.CostModel(1.5, 0.21, 3.0e-4)
+    shapes = [[(2, 122, 1, 1)], [(2, 488, 8, 2)], [(2, 244, 16, 1)],
+              [(2, 122, 1, 1), (2, 488, 8, 2), (2, 244, 16, 1)]]
+    for F in (65536, 16384):
+        samples = [(F, ses, truth.fixed(F) + sum(truth.session(*x, F) for x in ses))
+                   for ses in shapes]
+        m = serve.CostModel.fit(samples)
+        assert m.measured
+        np.testing.assert_allclose([m.c0, m.c_stream, m.c_bpk], [1.5, 0.21, 3.0e-4], rtol=1e-9)

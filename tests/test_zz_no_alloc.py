@@ -93,7 +93,8 @@ def _noalloc(lp, x, shape, fb, enu, dirs, tec, k_sigma, cap=8192, outputs=True):
     recs = np.frombuffer(trig.cpu().numpy().tobytes(), dtype=lp.TRIGGER_DTYPE)
     written = recs[recs["n"] >= 0]
     if outputs:
-        assert int(cnt.item()) == len(written) <= cap
+        assert int(cnt.item()) <= cap, "the case must keep every trigger"
+        assert int(cnt.item()) == len(written)
     trig_set = {(int(r["stream"]), int(r["n"])) for r in written}
     sig = np.sqrt(s2.cpu().numpy()) if outputs else None
     return y.cpu().numpy(), sig, trig_set, written
@@ -116,7 +117,7 @@ def test_noalloc_matches_oracle_and_plan_path_twice(cuda_lib):
     lp = cuda_lib
     shape = (6, 2, 16, 2, 2, 512)
     fb = 154
-    k_sigma = 3.0
+    k_sigma = 4.0
     blocks_a, enu, dirs, tec = random_case(21, *shape, fb, "int16", 1)
     blocks_b, _, _, _ = random_case(22, *shape, fb, "int16", 1)
     for x in (blocks_a[0], blocks_b[0]):         # two calls in a row, different data
@@ -133,7 +134,7 @@ def test_noalloc_larger_then_smaller_shape_and_null_outputs(cuda_lib):
     noise partials and counters must not carry the first call's.  The second
     call leaves sigma2 and trigger_count NULL (they then live in the scratch)."""
     lp = cuda_lib
-    fb, k_sigma = 200, 3.0
+    fb, k_sigma = 200, 4.0
     big = (5, 2, 24, 4, 2, 768)
     small = (5, 1, 24, 1, 1, 256)
     xb, enu, dirs4, tec2 = random_case(41, *big, fb, "int16", 1)
