@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--serve-blocks", type=int, default=200,
                     help="blocks of the realtime serving leg (p50/p99 latency); 0 skips it")
+    ap.add_argument("--stress-blocks", type=int, default=1,
+                    help="blocks of the stress leg (200 beams x 8 trials x 262144 frames, "
+                         "recall and roofline) added to the default line; 0 skips it")
     ap.add_argument("--workload", default="precision", choices=["precision", "stress", "two-stage"],
                     help="precision: the 48x488x50 headline block; stress: 200 beams x 8 "
                          "trials x 262144 frames with injected pulses (recall)")
@@ -699,6 +702,14 @@ def main():
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl")
         line = run_ours(args, rank, world, local_rank)
+        if (line is not None and world == 1 and args.stress_blocks > 0 and not args.frames
+                and not args.fine and not args.lsmr and args.precision == "fp16"):
+            import copy
+            import torch
+            torch.cuda.empty_cache()
+            sargs = copy.copy(args)
+            sargs.steps, sargs.warmup = args.stress_blocks, 1
+            line["stress"] = run_stress(sargs)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

@@ -105,39 +105,50 @@ def make_requests(seed, n_blocks, n_beams_grid=50, n_sub=488, rate=0.25, min_sub
 
 class CostModel:
     """Device time of a block of sessions, ms:
-        T = (F / 65536) * (c0 + sum_s (c_stream * J_s + c_bpk * B_s * P * K_s)),
-    J_s = B_s Tr_s P the session's streams (the synthesis costs the same per
-    stream whatever its subband count: the inverse DFT is always 1024 points)
-    and B_s P K_s its beam rows (the beamformer).  The coefficients are
-    measured at start-up by Server.calibrate; until then (and in host-only
-    tests) a prior holds: c0 = 0, 0.3 ms per stream, 7.5 ms per 50 x 2 x 488
-    beam rows (a GB300 measurement of one whole-band session)."""
+        T = (F / 65536) * (c0 + sum_s (c_in * P K_s ceil(B_s / 64)
+                                        + c_row * J_s K_s + c_stream * J_s)),
+    J_s = B_s Tr_s P the session's streams.  The beamformer reads the session's
+    P K_s subband slabs once per 64-beam tile of the tensor-core GEMM and writes
+    J_s K_s beam rows; the synthesis costs the same per stream whatever its
+    subband count (the inverse DFT is always 1024 points).  The coefficients are
+    measured at start-up by Server.calibrate (non-negative least squares over
+    timed blocks); until then (and in host-only tests) a prior holds, from one
+    GB300 measurement of a whole-band 50-beam session: c_in 1e-3, c_row 4.5e-5,
+    c_stream 0.22 ms."""
 
-    def __init__(self, c0=0.0, c_stream=0.30, c_bpk=7.5 / (50 * 2 * 488), measured=False):
-        self.c0, self.c_stream, self.c_bpk, self.measured = c0, c_stream, c_bpk, measured
+    def __init__(self, c0=0.0, c_in=1.0e-3, c_row=4.5e-5, c_stream=0.22, measured=False):
+        self.c0, self.c_in, self.c_row, self.c_stream = c0, c_in, c_row, c_stream
+        self.measured = measured
+
+    @staticmethod
+    def features(P, K, B, Tr):
+        J = B * Tr * P
+        return np.array([P * K * ((B + 63) // 64), J * K, J], dtype=np.float64)
 
     def session(self, P, K, B, Tr, F):
-        return F / 65536.0 * (self.c_stream * B * Tr * P + self.c_bpk * B * P * K)
+        f = self.features(P, K, B, Tr)
+        return F / 65536.0 * float(np.dot([self.c_in, self.c_row, self.c_stream], f))
 
     def fixed(self, F):
         return F / 65536.0 * self.c0
 
     @classmethod
     def fit(cls, samples):
-        """Least squares over samples [(F, [(P, K, B, Tr), ...], ms), ...]."""
+        """Non-negative least squares over samples [(F, [(P, K, B, Tr), ...], ms), ...]."""
+        from scipy.optimize import nnls
         rows, y = [], []
         for F, sessions, ms in samples:
             sc = F / 65536.0
-            rows.append([sc, sc * sum(B * Tr * P for P, K, B, Tr in sessions),
-                         sc * sum(B * P * K for P, K, B, Tr in sessions)])
+            f = sum((cls.features(*x) for x in sessions), np.zeros(3))
+            rows.append(sc * np.concatenate([[1.0], f]))
             y.append(ms)
-        coef, *_ = np.linalg.lstsq(np.array(rows), np.array(y), rcond=None)
-        c0, cs, cb = (max(0.0, float(v)) for v in coef)
-        return cls(c0, cs, cb, measured=True)
+        coef, _ = nnls(np.array(rows), np.array(y, dtype=np.float64))
+        return cls(*(float(v) for v in coef), measured=True)
 
     def as_dict(self):
-        return {"c0_ms": self.c0, "ms_per_stream": self.c_stream,
-                "ms_per_beam_pol_subband": self.c_bpk, "measured": self.measured}
+        return {"c0_ms": self.c0, "ms_per_slab_beam_tile": self.c_in,
+                "ms_per_stream_subband_row": self.c_row, "ms_per_stream": self.c_stream,
+                "measured": self.measured}
 
 
 PRIOR = CostModel()
@@ -211,6 +222,11 @@ class Server:
     def _fixed(self):
         return self.model.fixed(self.F)
 
+    def _active_cost(self):
+        """Modelled time of the active sessions (recomputed, so that admitting and
+        retiring never leave a rounding residue)."""
+        return sum(self._cost(s.req) for s in self.active.values())
+
     def admit(self):
         """Admit queued requests, in arrival order, while memory and time fit."""
         admitted = []
@@ -241,7 +257,7 @@ class Server:
             plan.lp_set_tec(req.tec, stream=stream)
             self.active[req.rid] = Session(req, plan, stream)
             self.used += need
-            self.cost_used += cost
+            self.cost_used = self._active_cost()
             admitted.append(req.rid)
         return admitted
 
@@ -253,7 +269,7 @@ class Server:
             s = self.active.pop(rid)
             s.plan.close()
             self.used -= self._ws(s.req)
-            self.cost_used -= self._cost(s.req)
+        self.cost_used = self._active_cost()
         return gone
 
     # -- one block -----------------------------------------------------------
@@ -314,7 +330,8 @@ class Server:
             g.lp_group_process_block(self.block_dev, self.n_sub, self.fb0, stream=self.stream)
         self.launches.append(sum(g.lp_group_launches_per_block() for g in self.groups))
 
-    def calibrate(self, shapes=((1, 122, 1), (8, 488, 2), (16, 244, 1)), reps=3):
+    def calibrate(self, shapes=((1, 122, 1), (8, 488, 2), (16, 244, 1), (40, 488, 1),
+                                (2, 488, 4), (24, 160, 3)), reps=3):
         """Measure the cost model on this GPU: time one block of sessions of the
         given (beams, subbands, trials) shapes -- each alone, then all together
         -- in the launch form the server uses, and fit CostModel by least
@@ -373,7 +390,7 @@ class Server:
 
     def observe(self, block_ms):
         """Update the cost correction from the measured time of the last block."""
-        if self.cost_used > 0 and block_ms > self.copy_ms:
+        if self.active and self.cost_used > 1e-6 and block_ms > self.copy_ms:
             r = (block_ms - self.copy_ms) / (self._fixed() + self.cost_used)
             self.cost_corr = 0.8 * self.cost_corr + 0.2 * r
 

@@ -146,15 +146,15 @@ def test_batched_serving_equals_unbatched_and_launches_do_not_grow(cuda_lib):
     assert srv.launches == [4, 4, 4]
 
 
-def test_serving_calibration_measures_a_positive_cost_model(cuda_lib):
+def test_serving_calibration_fits_the_timed_blocks(cuda_lib):
     from paper_1612_06592_gb300.serve import Server
-    S, F, n_sub, fb0 = 8, 2048, 488, 12
-    grid = synth.hex_beam_directions(16)
+    S, F, n_sub, fb0 = 8, 8192, 488, 12
+    grid = synth.hex_beam_directions(40)
     enu = synth.station_positions(S, 3)
     srv = Server(S, 2, n_sub, fb0, F, enu, grid, 1e12, precision="fp16")
     m = srv.calibrate()
-    assert m.measured and m.c_stream > 0 and m.c_bpk > 0
-    assert len(srv.calibration) == 4 and all(c["ms"] > 0 for c in srv.calibration)
+    assert m.measured and m.c_stream >= 0 and m.c_row >= 0 and m.c_in >= 0
+    assert len(srv.calibration) == 7 and all(c["ms"] > 0 for c in srv.calibration)
     # the fitted model reproduces the combined block within a factor of two
     comb = srv.calibration[-1]
     pred = m.fixed(F) + sum(m.session(P, K, B, Tr, F) for P, K, B, Tr in comb["sessions"])

@@ -95,6 +95,7 @@ def test_workspace_query_and_cost_model(serve):
     # beam rows dominate: streams x subbands x (F + 16) complex floats
     assert big >= 50 * 4 * 2 * 488 * (65536 + 16) * 8
     c1 = serve.session_cost_ms(2, 488, 50, 1, 65536)
+    assert c1 > 0
     assert abs(serve.session_cost_ms(2, 488, 50, 1, 32768) - c1 / 2) < 1e-12
     assert serve.session_cost_ms(2, 488, 50, 2, 65536) > c1
 
@@ -144,14 +145,32 @@ def test_admission_waits_for_a_time_slot_and_learns_the_cost(serve, monkeypatch)
 
 
 def test_cost_model_fit_recovers_the_coefficients(serve):
-    """The start-up calibration fits T = c0 + c_stream * streams + c_bpk * beam rows
-    by least squares: exact data give back the coefficients, at any block length."""
-    truth = serve.CostModel(1.5, 0.21, 3.0e-4)
-    shapes = [[(2, 122, 1, 1)], [(2, 488, 8, 2)], [(2, 244, 16, 1)],
-              [(2, 122, 1, 1), (2, 488, 8, 2), (2, 244, 16, 1)]]
+    """The start-up calibration fits T = c0 + c_in * slab-tiles + c_row * rows +
+    c_stream * streams by non-negative least squares: exact data from the
+    calibration shapes give back the coefficients, at any block length."""
+    truth = serve.CostModel(1.5, 2.0e-3, 4.0e-5, 0.21)
+    shapes = [(1, 122, 1), (8, 488, 2), (16, 244, 1), (40, 488, 1), (2, 488, 4), (24, 160, 3)]
+    combos = [[s] for s in shapes] + [shapes]
     for F in (65536, 16384):
-        samples = [(F, ses, truth.fixed(F) + sum(truth.session(*x, F) for x in ses))
-                   for ses in shapes]
+        samples = [(F, [(2, K, B, Tr) for (B, K, Tr) in c],
+                    truth.fixed(F) + sum(truth.session(2, K, B, Tr, F) for (B, K, Tr) in c))
+                   for c in combos]
         m = serve.CostModel.fit(samples)
         assert m.measured
-        np.testing.assert_allclose([m.c0, m.c_stream, m.c_bpk], [1.5, 0.21, 3.0e-4], rtol=1e-9)
+        np.testing.assert_allclose([m.c0, m.c_in, m.c_row, m.c_stream],
+                                   [1.5, 2.0e-3, 4.0e-5, 0.21], rtol=1e-6)
+
+
+def test_cost_used_is_recomputed_without_residue(serve, monkeypatch):
+    srv = _server(serve, monkeypatch, 1 << 62)
+    reqs = [_req(serve, i, 3 + i, 150 + 10 * i, 1 + i % 3, blocks=1) for i in range(5)]
+    for r in reqs:
+        srv.submit(r)
+    srv.admit()
+    for s in srv.active.values():
+        s.blocks_done = 1
+    srv.retire()
+    assert srv.cost_used == 0.0 and not srv.active
+    cc = srv.cost_corr
+    srv.observe(50.0)                      # no session: the correction stays
+    assert srv.cost_corr == cc
