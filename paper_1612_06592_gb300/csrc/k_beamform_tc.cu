@@ -266,36 +266,43 @@ struct TcArgs {
 };
 
 // The tile sequence every role walks: items [it0, it1) of the launch (plan 0's
-// items, then plan 1's, ...), 256-frame tiles each.
+// items, then plan 1's, ...), 256-frame tiles each.  GROUP = false: one plan
+// (index 0 throughout; no plan lookups on the single-plan path).
+template <bool GROUP>
 struct TileSeq {
   long long it, it1, n0, f_hi, p_begin;
   int n_chunks, P, pidx;
   long long F;
   const TcArgs* a;
-  __device__ void start(const TcArgs* args, long long b0, long long b1) {
+  __device__ void start(const TcArgs* args, int nc, int npol, long long f, long long b0,
+                        long long b1) {
     a = args;
-    it = b0; it1 = b1; n_chunks = a->n_chunks; P = a->npol; F = a->F;
+    it = b0; it1 = b1; n_chunks = nc; P = npol; F = f;
     pidx = 0;
     p_begin = 0;
     if (it < it1) set_item();
   }
   __device__ void set_item() {
-    while (it >= a->pl[pidx].item_end) {
-      p_begin = a->pl[pidx].item_end;
-      ++pidx;
+    if constexpr (GROUP) {
+      while (it >= a->pl[pidx].item_end) {
+        p_begin = a->pl[pidx].item_end;
+        ++pidx;
+      }
     }
     const long long chunk = local() % n_chunks;
     n0 = chunk * CHUNK;
     f_hi = min(F, n0 + CHUNK);
   }
-  __device__ long long local() const { return it - p_begin; }
-  __device__ const TcPlan& plan() const { return a->pl[pidx]; }
+  __device__ long long local() const { return GROUP ? it - p_begin : it; }
   __device__ bool valid() const { return it < it1; }
   __device__ int chunk() const { return (int)(local() % n_chunks); }
   __device__ int pol() const { return (int)((local() / n_chunks) % P); }
   // (subband, beam tile) within the plan, and its group-wide index
   __device__ long long km() const { return local() / ((long long)n_chunks * P); }
-  __device__ long long kmg() const { return a->pl[pidx].km0 + km(); }
+  __device__ long long kmg() const {
+    if constexpr (GROUP) return a->pl[pidx].km0 + km();
+    return km();
+  }
   __device__ bool last_of_item() const { return n0 + TN >= f_hi; }
   __device__ void next() {
     n0 += TN;
@@ -306,6 +313,7 @@ struct TileSeq {
   }
 };
 
+template <bool GROUP>
 __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int KP = kpad(a.S);
@@ -342,8 +350,10 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
   const long long per = (a.n_items + gridDim.x - 1) / gridDim.x;
   const long long it0 = blockIdx.x * per;
   const long long it1 = min(a.n_items, it0 + per);
-  TileSeq q;
-  q.start(&a, it0, it1);
+  TileSeq<GROUP> q;
+  q.start(&a, a.n_chunks, a.npol, a.F, it0, it1);
+  // the current item's plan (plan 0 at a fixed parameter offset on the single-plan path)
+  auto plan = [&]() -> const TcPlan& { return a.pl[GROUP ? q.pidx : 0]; };
 
   if (warp == W_PROD) {
     // ---------------- producer ----------------
@@ -354,7 +364,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
       uint32_t issued = 0, last_par = 0;        // per stage: copy issued, its phase parity
       bool a_issued = false;
       for (; q.valid(); q.next()) {
-        const TcPlan& pl = q.plan();
+        const TcPlan& pl = plan();
         const long long km = q.km(), kmg = q.kmg();
         if (kmg != cur_km) {
           if (cur_km >= 0) {
@@ -485,8 +495,8 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
       if (!wait_phase(&tfull[acc], pha, abort_p)) break;
       tc_fence_after();
       const int pol = q.pol() + a.pol0;
-      const TcPlan& pl = q.plan();
-      const CUtensorMap* out_map = &a.maps[q.pidx];
+      const TcPlan& pl = plan();
+      const CUtensorMap* out_map = &a.maps[GROUP ? q.pidx : 0];
       const long long km = q.km();
       const int k = (int)(km / pl.n_mt), mt = (int)(km % pl.n_mt);
       const int b = mt * (TM / 2) + rb;
@@ -683,7 +693,9 @@ size_t tc_smem(const Shape& sh) {            // the largest configuration
 }
 
 cudaError_t init_tc_attributes(const Shape& sh) {
-  return raise_smem_limit((const void*)k_beamform_tc, tc_smem(sh));
+  cudaError_t e = raise_smem_limit((const void*)k_beamform_tc<false>, tc_smem(sh));
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_beamform_tc<true>, tc_smem(sh));
+  return e;
 }
 
 // Plans plans[0..n) (same stations, polarisations, block length and chunking;
@@ -740,7 +752,10 @@ cudaError_t launch_beamform_tc_plans(const lp_plan* const* plans, const void* co
     }
   }
   const long long grid = std::min<long long>(a.n_items, (long long)num_sms());
-  k_beamform_tc<<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
+  if (n == 1)
+    k_beamform_tc<false><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
+  else
+    k_beamform_tc<true><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -349,19 +349,25 @@ __device__ __forceinline__ void pair_dft(float2* slot, const float4* st,
 // Per-batch context of the FIR role.
 struct FirCtx {
   float th2;
-  float sig;               // sigma of the stream (trigger records)
-  int j;                   // stream index within its plan
   unsigned ymask, vmask;   // output frames of the batch / those that may trigger
   long long n_row0;        // sample index of batch row 0, phase 0
   float* yrow;             // y of batch row 0 (or null)
 };
 
-// o: the stream's plan in the launch's parameter block; j its stream index in
-// the plan, sig its sigma.
+// The CTA's stream (index within its plan, sigma, plan), kept in shared memory
+// for the rare trigger path.
+struct StreamInfo {
+  int j;
+  float sig;
+  const IppfPlan* plan;
+};
+
 __device__ __noinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmask, float th2,
-                                           int p, long long n_row0, int j, float sig,
-                                           const IppfPlan& o) {
+                                           int p, long long n_row0, const StreamInfo* si) {
   const int lane = threadIdx.x & 31;
+  const IppfPlan& o = *si->plan;
+  const int j = si->j;
+  const float sig = si->sig;
   const int P = o.P, Tr = o.Tr;
 #pragma unroll
   for (int f = 0; f < FB; ++f) {
@@ -395,7 +401,7 @@ __device__ __noinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmas
 template <int ODD>
 __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float (&hist)[32],
                                           const float2 (&zn)[FB], int p, const FirCtx& c,
-                                          const IppfPlan& o) {
+                                          const StreamInfo* si) {
   float2 w[kHist + FB];
 #pragma unroll
   for (int i = 0; i < kHist; ++i) {
@@ -416,8 +422,7 @@ __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float
     e2v[f] = fmaf(u.x, u.x, u.y * u.y);
     emax = fmaxf(emax, e2v[f]);         // frames outside the run are filtered by vmask
   }
-  if (__any_sync(0xffffffffu, emax > c.th2))
-    emit_triggers(e2v, c.vmask, c.th2, p, c.n_row0, c.j, c.sig, o);
+  if (__any_sync(0xffffffffu, emax > c.th2)) emit_triggers(e2v, c.vmask, c.th2, p, c.n_row0, si);
 }
 
 // Bits [lo, hi) of an 8-bit frame mask (lo, hi clamped to [0, 8]).
@@ -431,15 +436,15 @@ __device__ __forceinline__ unsigned frame_bits(int lo, int hi) {
 // tensor memory; the new frames then replace the history slots r0 mod 16 ...
 __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t thist,
                                         const float2 (&zn)[FB], int p, int r0, bool outputs,
-                                        const FirCtx& c, const IppfPlan& o) {
+                                        const FirCtx& c, const StreamInfo* si) {
   if (outputs) {
     float hist[32];
     tmem_ld32(thist, hist);
     tmem_wait_ld();
     if (r0 & 8)
-      fir_phase<1>(gq, hist, zn, p, c, o);
+      fir_phase<1>(gq, hist, zn, p, c, si);
     else
-      fir_phase<0>(gq, hist, zn, p, c, o);
+      fir_phase<0>(gq, hist, zn, p, c, si);
   }
 #pragma unroll
   for (int f = 0; f < FB; ++f) tmem_st2(thist + 2 * ((r0 & 8) + f), zn[f]);
@@ -448,18 +453,23 @@ __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t this
 // One launch covers the streams of a.n plans (one plan, or a group of plans
 // fused into one launch): blockIdx.y counts the launch streams of plan 0, then
 // plan 1, ...; every plan has its own beam rows, thresholds, block counter and
-// trigger list, and all share the frame range and the tiling.
+// trigger list, and all share the frame range and the tiling.  GROUP = false:
+// one plan, whose parameters are then read at fixed offsets of the parameter
+// block (no indexed lookup on the single-plan path).
+template <bool GROUP>
 __global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs a) {
   extern __shared__ float4 smem4[];
   float2* ring = reinterpret_cast<float2*>(smem4);      // [2 buffers][8 frames][1024]
   float4* stage = smem4 + FB * kM;                        // [2 buffers][4 pairs][SPAIR]
   __shared__ uint32_t tmem_slot;
+  __shared__ StreamInfo sinfo;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int pi = 0;
-  while (pi + 1 < a.n && (int)blockIdx.y >= a.pl[pi].stream_end) ++pi;
-  const IppfPlan& pl = a.pl[pi];
-  const int jj = (int)blockIdx.y - (pi ? a.pl[pi - 1].stream_end : 0);
+  if constexpr (GROUP)
+    while (pi + 1 < a.n && (int)blockIdx.y >= a.pl[pi].stream_end) ++pi;
+  const IppfPlan& pl = a.pl[GROUP ? pi : 0];
+  const int jj = (int)blockIdx.y - (GROUP && pi ? a.pl[pi - 1].stream_end : 0);
   const int j = (int)sel_stream(jj, pl.P, a.pol0, a.npol);
   const int K = pl.K, first_bin = pl.first_bin, frames_per_cta = a.frames_per_cta;
   const long long F = a.F, row = a.row;
@@ -472,6 +482,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs
   const int nbatch = (nfr + FB - 1) / FB;
 
   if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
+  if (tid == 0) sinfo = StreamInfo{j, pl.theta[j] / pl.k_sigma, &pl};
   // bins outside the selection stay zero for the whole run
   for (int i = tid; i < 2 * NPAIR * SPAIR; i += NT) stage[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   tc_fence_before();
@@ -527,8 +538,6 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs
     tmem_wait_st();
     FirCtx c;
     c.th2 = pl.theta2[j];
-    c.sig = pl.theta[j] / pl.k_sigma;
-    c.j = j;
     const long long F_total = a.F_total, f_base = a.f_base;
     // this launch covers block frames [f_base, f_base + F) (one chunk, or the block)
     float* yj = pl.y ? pl.y + ((long long)j * F_total + f_base) * kM : nullptr;
@@ -578,7 +587,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs
 #pragma unroll
           for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
           fir_one(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0, outputs, c,
-                  pl);
+                  &sinfo);
         }
       }
       tmem_wait_st();                    // history slots written before the next batch reads them
@@ -664,7 +673,9 @@ int ippf_default_frames_per_cta(const Shape& sh) {
 }
 
 cudaError_t init_ippf_attributes() {
-  return raise_smem_limit((const void*)k_ippf, ippf_smem_bytes());
+  cudaError_t e = raise_smem_limit((const void*)k_ippf<false>, ippf_smem_bytes());
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_ippf<true>, ippf_smem_bytes());
+  return e;
 }
 
 IppfPlan ippf_plan(const lp_plan& p) {
@@ -709,7 +720,10 @@ cudaError_t launch_ippf_plans(const lp_plan* const* plans, int n, const Chunk& c
     a.pl[i].stream_end = streams;
   }
   const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)streams);
-  k_ippf<<<grid, NT, ippf_smem_bytes(), s>>>(a);
+  if (n == 1)
+    k_ippf<false><<<grid, NT, ippf_smem_bytes(), s>>>(a);
+  else
+    k_ippf<true><<<grid, NT, ippf_smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 
