@@ -349,8 +349,7 @@ __device__ __forceinline__ void pair_dft(float2* slot, const float4* st,
 // Per-batch context of the FIR role.
 struct FirCtx {
   float th2;
-  unsigned ymask, vmask;   // output frames of the batch / those that may trigger
-  long long n_row0;        // sample index of batch row 0, phase 0
+  unsigned ymask;          // output frames of the batch (time-series store)
   float* yrow;             // y of batch row 0 (or null)
 };
 
@@ -360,12 +359,25 @@ struct StreamInfo {
   int j;
   float sig;
   const IppfPlan* plan;
+  int nfr, r_trig;         // frames of the run, first run row that may trigger
+  long long n_first, m0;   // sample index of block frame -15, phase 0; first output frame
 };
 
-__device__ __noinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmask, float th2,
-                                           int p, long long n_row0, const StreamInfo* si) {
+// Bits [lo, hi) of an 8-bit frame mask (lo, hi clamped to [0, 8]).
+__device__ __forceinline__ unsigned frame_bits(int lo, int hi) {
+  lo = max(0, min(lo, FB));
+  hi = max(lo, min(hi, FB));
+  return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+}
+
+// Batch r0 of the run (rows r0 .. r0 + 7): the frames that may trigger and the
+// sample origin follow from the run's constants in shared memory.
+__device__ __noinline__ void emit_triggers(const float (&e2v)[FB], float th2, int p, int r0,
+                                           const StreamInfo* si) {
   const int lane = threadIdx.x & 31;
   const IppfPlan& o = *si->plan;
+  const unsigned vmask = frame_bits(kPrefix - r0, si->nfr - r0) & frame_bits(si->r_trig - r0, FB);
+  const long long n_row0 = si->n_first + (si->m0 - kPrefix + r0) * kM;
   const int j = si->j;
   const float sig = si->sig;
   const int P = o.P, Tr = o.Tr;
@@ -398,9 +410,9 @@ __device__ __noinline__ void emit_triggers(const float (&e2v)[FB], unsigned vmas
 // FIR of one phase over one batch.  hist: the phase's 16 history slots (frame
 // r at slot r mod 16, (re, im) in consecutive columns); zn: the 8 new frames.
 // ODD selects where the 15 history frames r0-15 .. r0-1 sit (r0 mod 16 = 8 ODD).
-template <int ODD>
+template <int ODD, bool STORE_Y>
 __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float (&hist)[32],
-                                          const float2 (&zn)[FB], int p, const FirCtx& c,
+                                          const float2 (&zn)[FB], int p, int r0, const FirCtx& c,
                                           const StreamInfo* si) {
   float2 w[kHist + FB];
 #pragma unroll
@@ -418,22 +430,17 @@ __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float
 #pragma unroll
     for (int t = 0; t < kTaps; ++t)   // both components per instruction, tap (g, g)
       u = __ffma2_rn(gq[t], w[f + kHist - t], u);
-    if (c.yrow && ((c.ymask >> f) & 1u)) c.yrow[f * kM + p] = u.x;
+    if constexpr (STORE_Y)   // (in a group, plans without a stored series have no row)
+      if (c.yrow && ((c.ymask >> f) & 1u)) c.yrow[f * kM + p] = u.x;
     e2v[f] = fmaf(u.x, u.x, u.y * u.y);
     emax = fmaxf(emax, e2v[f]);         // frames outside the run are filtered by vmask
   }
-  if (__any_sync(0xffffffffu, emax > c.th2)) emit_triggers(e2v, c.vmask, c.th2, p, c.n_row0, si);
-}
-
-// Bits [lo, hi) of an 8-bit frame mask (lo, hi clamped to [0, 8]).
-__device__ __forceinline__ unsigned frame_bits(int lo, int hi) {
-  lo = max(0, min(lo, FB));
-  hi = max(lo, min(hi, FB));
-  return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+  if (__any_sync(0xffffffffu, emax > c.th2)) emit_triggers(e2v, c.th2, p, r0, si);
 }
 
 // One phase of the FIR role for batch r0: its 8 new frames zn, history from
 // tensor memory; the new frames then replace the history slots r0 mod 16 ...
+template <bool STORE_Y>
 __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t thist,
                                         const float2 (&zn)[FB], int p, int r0, bool outputs,
                                         const FirCtx& c, const StreamInfo* si) {
@@ -442,9 +449,9 @@ __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t this
     tmem_ld32(thist, hist);
     tmem_wait_ld();
     if (r0 & 8)
-      fir_phase<1>(gq, hist, zn, p, c, si);
+      fir_phase<1, STORE_Y>(gq, hist, zn, p, r0, c, si);
     else
-      fir_phase<0>(gq, hist, zn, p, c, si);
+      fir_phase<0, STORE_Y>(gq, hist, zn, p, r0, c, si);
   }
 #pragma unroll
   for (int f = 0; f < FB; ++f) tmem_st2(thist + 2 * ((r0 & 8) + f), zn[f]);
@@ -456,8 +463,9 @@ __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t this
 // trigger list, and all share the frame range and the tiling.  GROUP = false:
 // one plan, whose parameters are then read at fixed offsets of the parameter
 // block (no indexed lookup on the single-plan path).
-template <bool GROUP>
-__global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs a) {
+template <bool GROUP, bool STORE_Y>
+__global__ void __launch_bounds__(NT, 1) k_ippf(
+    const __grid_constant__ IppfArgsN<GROUP ? kMaxGroup : 1> a) {
   extern __shared__ float4 smem4[];
   float2* ring = reinterpret_cast<float2*>(smem4);      // [2 buffers][8 frames][1024]
   float4* stage = smem4 + FB * kM;                        // [2 buffers][4 pairs][SPAIR]
@@ -482,7 +490,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs
   const int nbatch = (nfr + FB - 1) / FB;
 
   if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
-  if (tid == 0) sinfo = StreamInfo{j, pl.theta[j] / pl.k_sigma, &pl};
+  if (tid == 0) sinfo = StreamInfo{j, pl.theta[j] / pl.k_sigma, &pl, 0, 0, 0, 0};
   // bins outside the selection stay zero for the whole run
   for (int i = tid; i < 2 * NPAIR * SPAIR; i += NT) stage[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   tc_fence_before();
@@ -549,6 +557,12 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs
     // run row r (frame m0 - 16 + r) is an output for r in [16, nfr) and may
     // trigger for r >= r_trig
     const int r_trig = (int)max((long long)kPrefix, frame_min_trigger + kPrefix - m0);
+    if (tid == NDFT) {   // read by the trigger path after the first ready barrier
+      sinfo.nfr = nfr;
+      sinfo.r_trig = r_trig;
+      sinfo.n_first = n_first;
+      sinfo.m0 = m0;
+    }
     for (int bi = 0; bi < nbatch; ++bi) {
       const int s = bi & 1, r0 = bi * FB;
       bar_sync(BAR_READY + s, NT);       // ring buffer s holds batch bi
@@ -559,10 +573,8 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs
       const float4* zr = reinterpret_cast<const float4*>(ring + s * FB * kM);
       const bool outputs = r0 >= kPrefix;
       c.ymask = frame_bits(kPrefix - r0, nfr - r0);
-      c.vmask = c.ymask & frame_bits(r_trig - r0, FB);
       const long long m_row0 = m0 - kPrefix + r0;             // frame of batch row 0
       c.yrow = yj ? yj + m_row0 * kM : nullptr;
-      c.n_row0 = n_first + m_row0 * kM;
 #pragma unroll 1
       for (int bp = 0; bp < 2; ++bp) {
         const int pb = bp ? kM / 2 - 1 - ft : ft;
@@ -586,8 +598,8 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(const __grid_constant__ IppfArgs
           float2 gq[kTaps];
 #pragma unroll
           for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
-          fir_one(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0, outputs, c,
-                  &sinfo);
+          fir_one<STORE_Y>(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0,
+                           outputs, c, &sinfo);
         }
       }
       tmem_wait_st();                    // history slots written before the next batch reads them
@@ -673,8 +685,10 @@ int ippf_default_frames_per_cta(const Shape& sh) {
 }
 
 cudaError_t init_ippf_attributes() {
-  cudaError_t e = raise_smem_limit((const void*)k_ippf<false>, ippf_smem_bytes());
-  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_ippf<true>, ippf_smem_bytes());
+  const void* k[4] = {(const void*)k_ippf<false, false>, (const void*)k_ippf<false, true>,
+                      (const void*)k_ippf<true, false>, (const void*)k_ippf<true, true>};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = raise_smem_limit(k[i], ippf_smem_bytes());
   return e;
 }
 
@@ -720,10 +734,29 @@ cudaError_t launch_ippf_plans(const lp_plan* const* plans, int n, const Chunk& c
     a.pl[i].stream_end = streams;
   }
   const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)streams);
-  if (n == 1)
-    k_ippf<false><<<grid, NT, ippf_smem_bytes(), s>>>(a);
-  else
-    k_ippf<true><<<grid, NT, ippf_smem_bytes(), s>>>(a);
+  if (n == 1) {
+    IppfArgsN<1> a1;
+    a1.F = a.F;
+    a1.row = a.row;
+    a1.F_total = a.F_total;
+    a1.f_base = a.f_base;
+    a1.frames_per_cta = a.frames_per_cta;
+    a1.pol0 = a.pol0;
+    a1.npol = a.npol;
+    a1.n = 1;
+    a1.pl[0] = a.pl[0];
+    if (a1.pl[0].y)
+      k_ippf<false, true><<<grid, NT, ippf_smem_bytes(), s>>>(a1);
+    else
+      k_ippf<false, false><<<grid, NT, ippf_smem_bytes(), s>>>(a1);
+  } else {
+    bool any_y = false;
+    for (int i = 0; i < n; ++i) any_y = any_y || a.pl[i].y;
+    if (any_y)
+      k_ippf<true, true><<<grid, NT, ippf_smem_bytes(), s>>>(a);
+    else
+      k_ippf<true, false><<<grid, NT, ippf_smem_bytes(), s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -113,11 +113,13 @@ struct IppfPlan {
   int K, first_bin, P, Tr;
   int stream_end;          // launch streams of plans 0 .. this one
 };
-struct IppfArgs {
+template <int N>
+struct IppfArgsN {
   long long F, row, F_total, f_base;   // frames of the launch, row length, block frames, offset
   int frames_per_cta, pol0, npol, n;
-  IppfPlan pl[kMaxGroup];
+  IppfPlan pl[N];
 };
+using IppfArgs = IppfArgsN<kMaxGroup>;
 
 // Per-plan parameters of the noise-level kernel.
 struct SigmaPlan {
