@@ -221,10 +221,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) 
       "r"(u[8]), "r"(u[9]), "r"(u[10]), "r"(u[11]), "r"(u[12]), "r"(u[13]), "r"(u[14]),
       "r"(u[15]));
 }
-__device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};\n" ::"r"(taddr),
-               "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)));
-}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
@@ -453,8 +449,8 @@ __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t this
     else
       fir_phase<0, STORE_Y>(gq, hist, zn, p, r0, c, si);
   }
-#pragma unroll
-  for (int f = 0; f < FB; ++f) tmem_st2(thist + 2 * ((r0 & 8) + f), zn[f]);
+  // the 8 new frames fill 16 consecutive history columns: one store
+  tmem_st16(thist + 2 * (r0 & 8), reinterpret_cast<const float(&)[16]>(zn[0]));
 }
 
 // One launch covers the streams of a.n plans (one plan, or a group of plans
@@ -471,6 +467,10 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   float4* stage = smem4 + FB * kM;                        // [2 buffers][4 pairs][SPAIR]
   __shared__ uint32_t tmem_slot;
   __shared__ StreamInfo sinfo;
+  // the run's row origin and copy limit, re-read by the FIR threads every batch
+  // (kept out of their registers)
+  __shared__ const float2* s_brow;
+  __shared__ int s_live_lim;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int pi = 0;
@@ -506,6 +506,10 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     stage_batch(stg, stage, stg.f + 1 < live_lim, 0);
     stage_batch(stg, stage + NPAIR * SPAIR, FB + stg.f + 1 < live_lim, FB);
     cp_async_wait_all();
+  }
+  if (tid == 0) {
+    s_brow = brow;
+    s_live_lim = live_lim;
   }
   __syncthreads();
 
@@ -567,9 +571,11 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
       const int s = bi & 1, r0 = bi * FB;
       bar_sync(BAR_READY + s, NT);       // ring buffer s holds batch bi
       // stage buffer s is free again: bins of batch bi + 2
-      if (bi + 2 < nbatch)
-        stage_batch(stg, stage + s * NPAIR * SPAIR, (bi + 2) * FB + stg.f + 1 < live_lim,
+      if (bi + 2 < nbatch) {
+        const Stager st = make_stager(s_brow, K, first_bin, row, ft);
+        stage_batch(st, stage + s * NPAIR * SPAIR, (bi + 2) * FB + st.f + 1 < s_live_lim,
                     (bi + 2) * FB);
+      }
       const float4* zr = reinterpret_cast<const float4*>(ring + s * FB * kM);
       const bool outputs = r0 >= kPrefix;
       c.ymask = frame_bits(kPrefix - r0, nfr - r0);
