@@ -108,6 +108,13 @@ typedef struct {
                                chunk_frames or host blocks per polarisation (a host
                                block is copied whole first) */
   int32_t lsmr_iters;       /* LSMR iterations per window (25); 1 .. 1000 */
+  int32_t stream_blocks;    /* 1: streaming host blocks (host_input = 1, whole blocks, no
+                               graph, no group): two staging buffers and two trigger lists,
+                               used by alternate blocks, so that the host-to-device copy of
+                               the next block starts as soon as the block two calls back has
+                               been beamformed (not after all earlier work on the stream) and
+                               overlaps this block's synthesis; lp_get_triggers_block reads
+                               a block's triggers while the next block runs.  0: off */
 } lp_config;
 
 enum { LP_INV_FIR = 0, LP_INV_LSMR = 1 };
@@ -200,6 +207,15 @@ lp_status lp_process_block_strided(lp_plan* plan, const void* x, int64_t pol_str
  * min(cap, trigger_cap) records, in sorted order of those kept, are copied). */
 lp_status lp_get_triggers(lp_plan* plan, lp_trigger* out, int64_t cap,
                           int64_t* n_total);
+
+/* The trigger read-out of one of the last two processed blocks (block counts
+ * lp_process_block calls from the plan's start or last lp_reset_stream, from
+ * 0): waits only for that block's work, so with stream_blocks = 1 the next
+ * block may already be in flight (its copy and kernels continue).  Otherwise
+ * as lp_get_triggers.  LP_ERR_STATE for a block that is not one of the last
+ * two (or, without stream_blocks, not the last). */
+lp_status lp_get_triggers_block(lp_plan* plan, int64_t block, lp_trigger* out, int64_t cap,
+                                int64_t* n_total);
 
 /* The recovered nanosecond-resolution series of one beam (Sec. 3, second
  * paragraph: the inverse FFT of the filtered signal and the inversion of the
@@ -345,7 +361,7 @@ void lp_group_destroy(lp_group* group);
  * stream (zero history) and allocates nothing: its scratch is a static device
  * array of LP_NOALLOC_SCRATCH_BYTES.
  *   Shape arguments as lp_plan_create; cfg as lp_plan_configure (precision
- *   must be LP_PREC_FP32; store_timeseries and host_input are ignored).
+ *   must be LP_PREC_FP32; store_timeseries, host_input and stream_blocks are ignored).
  *   station_enu_m [S][3], beam_dir [B][3], tec_tecu [Tr]: host doubles.
  *   x: device block [P][K][F][S][2], aligned to one complex sample (2 bytes
  *   int8, 4 bytes int16).

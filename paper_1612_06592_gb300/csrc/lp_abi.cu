@@ -92,10 +92,19 @@ size_t carve(lp_plan& p, char* base) {
   b.err = (int*)take(sizeof(int));
   b.blk = (long long*)take(sizeof(long long));
   b.trig = (lp::TriggerRec*)take(sizeof(lp::TriggerRec) * (size_t)p.cfg.trigger_cap);
+  // streaming blocks: a second trigger list (and below a second staging buffer)
+  const bool two = p.cfg.stream_blocks != 0;
+  p.trig_buf[0] = b.trig;
+  p.count_buf[0] = b.trig_count;
+  p.count_buf[1] = two ? (unsigned long long*)take(sizeof(unsigned long long)) : nullptr;
+  p.trig_buf[1] =
+      two ? (lp::TriggerRec*)take(sizeof(lp::TriggerRec) * (size_t)p.cfg.trigger_cap) : nullptr;
   b.y = p.cfg.store_timeseries ? (float*)take(sizeof(float) * (size_t)J * sh.F * kM) : nullptr;
   const size_t in_bytes = (size_t)sh.P * sh.K * sh.F * sh.S * 2 *
                           (p.cfg.input_dtype == LP_INPUT_INT8 ? 1 : 2);
   b.staging = p.cfg.host_input ? (void*)take(in_bytes) : nullptr;
+  p.staging_buf[0] = b.staging;
+  p.staging_buf[1] = p.cfg.host_input && two ? (void*)take(in_bytes) : nullptr;
   return align_up(off, 256);
 }
 
@@ -169,6 +178,7 @@ void lp_config_default(lp_config* c) {
   c->fine_dedisp = 0;
   c->inversion = LP_INV_FIR;
   c->lsmr_iters = 25;
+  c->stream_blocks = 0;
 }
 
 lp_status lp_plan_create(lp_plan** out, int stations, int pols, int subbands, int beams,
@@ -227,6 +237,10 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
   }
   if (c->fine_dedisp && c->chunk_frames != 0)
     return fail(p, LP_ERR_ARG, "fine_dedisp does not combine with chunk_frames");
+  if (c->stream_blocks != 0 && c->stream_blocks != 1)
+    return fail(p, LP_ERR_ARG, "stream_blocks must be 0 or 1");
+  if (c->stream_blocks && c->use_graph)
+    return fail(p, LP_ERR_ARG, "stream_blocks does not combine with use_graph");
   if (c->chunk_frames != 0) {
     if (c->precision != LP_PREC_FP16)
       return fail(p, LP_ERR_ARG, "chunk_frames needs the FP16 form");
@@ -521,8 +535,15 @@ lp_status process_host_pipelined(lp_plan* p, const void* x, int64_t pol_stride, 
     for (auto& ev : p->ev_pol) LP_CUDA(p, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   }
   char* staging = static_cast<char*>(p->buf.staging);
-  LP_CUDA(p, cudaEventRecord(p->ev_entry, s));
-  LP_CUDA(p, cudaStreamWaitEvent(p->copy_stream, p->ev_entry, 0));
+  const int par = (int)(p->block_index & 1);
+  if (p->cfg.stream_blocks) {
+    // streaming: this staging buffer was last read by the beamformer of the
+    // block two calls back; the copy waits for that, not for all earlier work
+    if (p->free_recorded[par]) LP_CUDA(p, cudaStreamWaitEvent(p->copy_stream, p->ev_free[par], 0));
+  } else {
+    LP_CUDA(p, cudaEventRecord(p->ev_entry, s));
+    LP_CUDA(p, cudaStreamWaitEvent(p->copy_stream, p->ev_entry, 0));
+  }
   for (int pol = 0; pol < 2; ++pol) {
     prof_mark(p, LP_STAGE_H2D, 0, p->copy_stream, pol);
     LP_CUDA(p, cudaMemcpyAsync(staging + pol * slab * bpc,
@@ -541,6 +562,10 @@ lp_status process_host_pipelined(lp_plan* p, const void* x, int64_t pol_stride, 
     if (e == cudaSuccess)
       e = fp16 ? lp::launch_beamform_tc(*p, staging, slab, c, s, ps)
                : lp::launch_beamform_f32(*p, staging, slab, s, ps);
+    if (e == cudaSuccess && pol == 1 && p->cfg.stream_blocks) {
+      e = cudaEventRecord(p->ev_free[par], s);      // staging buffer read for the last time
+      p->free_recorded[par] = e == cudaSuccess;
+    }
     prof_mark(p, LP_STAGE_BEAMFORM, 1, s, pol);
     prof_mark(p, LP_STAGE_SIGMA, 0, s, pol);
     if (e == cudaSuccess) e = lp::launch_sigma(*p, s, ps);
@@ -564,8 +589,8 @@ lp_status process_host_pipelined(lp_plan* p, const void* x, int64_t pol_stride, 
   return LP_OK;
 }
 
-lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, Tune tune,
-                  double* tune_ms) {
+lp_status process_inner(lp_plan* p, const void* x, int64_t pol_stride, void* stream, Tune tune,
+                        double* tune_ms) {
   if (lp_status st = need_bound(p)) return st;
   if (!p->weights_set || !p->tec_set)
     return fail(p, LP_ERR_STATE, "lp_set_weights and lp_set_tec must precede lp_process_block");
@@ -697,7 +722,84 @@ lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, T
   return LP_OK;
 }
 
+// One block: with stream_blocks, block b uses staging buffer and trigger list
+// b mod 2 and the end of its work is recorded for lp_get_triggers_block.
+lp_status process(lp_plan* p, const void* x, int64_t pol_stride, void* stream, Tune tune,
+                  double* tune_ms) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!p->cfg.stream_blocks) return process_inner(p, x, pol_stride, stream, tune, tune_ms);
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  for (int i = 0; i < 2; ++i) {
+    if (!p->ev_free[i]) LP_CUDA(p, cudaEventCreateWithFlags(&p->ev_free[i], cudaEventDisableTiming));
+    if (!p->ev_done[i]) LP_CUDA(p, cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming));
+  }
+  if (!p->read_stream)
+    LP_CUDA(p, cudaStreamCreateWithFlags(&p->read_stream, cudaStreamNonBlocking));
+  const long long blk = p->block_index;
+  const int par = (int)(blk & 1);
+  p->buf.trig = p->trig_buf[par];
+  p->buf.trig_count = p->count_buf[par];
+  if (p->staging_buf[par]) p->buf.staging = p->staging_buf[par];
+  const lp_status st = process_inner(p, x, pol_stride, stream, tune, tune_ms);
+  if (st != LP_OK) return st;
+  LP_CUDA(p, cudaEventRecord(p->ev_done[par], static_cast<cudaStream_t>(stream)));
+  p->block_in[par] = blk;
+  return LP_OK;
+}
+
+// Sorted copy of n records of a trigger list (device) to the caller.
+lp_status read_triggers(lp_plan* p, const lp::TriggerRec* trig, unsigned long long cnt,
+                        cudaStream_t rs, lp_trigger* out, int64_t cap, int64_t* n_total) {
+  *n_total = (int64_t)cnt;
+  const long long kept = std::min<long long>((long long)cnt, p->cfg.trigger_cap);
+  std::vector<lp_trigger> all((size_t)kept);
+  if (kept > 0) {
+    LP_CUDA(p, cudaMemcpyAsync(all.data(), trig, sizeof(lp_trigger) * (size_t)kept,
+                               cudaMemcpyDeviceToHost, rs));
+    LP_CUDA(p, cudaStreamSynchronize(rs));
+  }
+  std::sort(all.begin(), all.end(), [](const lp_trigger& a, const lp_trigger& b) {
+    if (a.beam != b.beam) return a.beam < b.beam;
+    if (a.tec != b.tec) return a.tec < b.tec;
+    if (a.pol != b.pol) return a.pol < b.pol;
+    return a.n < b.n;
+  });
+  const long long ncopy = std::min<long long>(kept, cap);
+  if (ncopy > 0) std::memcpy(out, all.data(), sizeof(lp_trigger) * (size_t)ncopy);
+  if ((long long)cnt > cap || (long long)cnt > p->cfg.trigger_cap)
+    return fail(p, LP_ERR_OVERFLOW, "%llu triggers, %lld copied", cnt, ncopy);
+  return LP_OK;
+}
+
 }  // namespace
+
+lp_status lp_get_triggers_block(lp_plan* p, int64_t block, lp_trigger* out, int64_t cap,
+                                int64_t* n_total) {
+  if (lp_status st = need_bound(p)) return st;
+  if (!n_total || cap < 0 || (cap > 0 && !out)) return fail(p, LP_ERR_ARG, "bad output buffer");
+  if (!p->cfg.stream_blocks) {
+    if (block != p->block_index - 1)
+      return fail(p, LP_ERR_STATE, "block %lld is not the last processed block",
+                  (long long)block);
+    return lp_get_triggers(p, out, cap, n_total);
+  }
+  const int par = (int)(block & 1);
+  if (block < 0 || p->block_in[par] != block)
+    return fail(p, LP_ERR_STATE, "block %lld is not one of the last two processed blocks",
+                (long long)block);
+  if (set_device(p) != LP_OK) return LP_ERR_CUDA;
+  // wait for that block only; reads on a stream of their own, so that neither
+  // the next block's kernels nor its host copy are waited for
+  LP_CUDA(p, cudaEventSynchronize(p->ev_done[par]));
+  cudaStream_t rs = p->read_stream;
+  int err = 0;
+  unsigned long long cnt = 0;
+  LP_CUDA(p, cudaMemcpyAsync(&err, p->buf.err, sizeof err, cudaMemcpyDeviceToHost, rs));
+  LP_CUDA(p, cudaMemcpyAsync(&cnt, p->count_buf[par], sizeof cnt, cudaMemcpyDeviceToHost, rs));
+  LP_CUDA(p, cudaStreamSynchronize(rs));
+  if (err) return fail(p, LP_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core beamformer)");
+  return read_triggers(p, p->trig_buf[par], cnt, rs, out, cap, n_total);
+}
 
 lp_status lp_get_triggers(lp_plan* p, lp_trigger* out, int64_t cap, int64_t* n_total) {
   if (lp_status st = need_bound(p)) return st;
@@ -818,6 +920,9 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
   if (p->buf.lsmr_sigma2)
     LP_CUDA(p, cudaMemsetAsync(p->buf.lsmr_sigma2, 0, sizeof(double) * sh.J() * kM, s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
+  if (p->count_buf[1])
+    LP_CUDA(p, cudaMemsetAsync(p->count_buf[1], 0, sizeof(unsigned long long), s));
+  p->block_in[0] = p->block_in[1] = -1;
   LP_CUDA(p, cudaMemsetAsync(p->buf.blk, 0, sizeof(long long), s));
   p->last_stream = s;
   p->block_index = 0;
@@ -886,6 +991,11 @@ void lp_plan_destroy(lp_plan* p) {
     cudaStreamDestroy(p->copy_stream);
   }
   if (p->ev_entry) cudaEventDestroy(p->ev_entry);
+  for (int i = 0; i < 2; ++i) {
+    if (p->ev_free[i]) cudaEventDestroy(p->ev_free[i]);
+    if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
+  }
+  if (p->read_stream) cudaStreamDestroy(p->read_stream);
   for (auto& ev : p->ev_pol)
     if (ev) cudaEventDestroy(ev);
   delete p;

@@ -46,6 +46,7 @@ const char* incompatible(const lp_plan& p0, const lp_plan& q) {
     return "a plan is not bound or lacks lp_set_weights / lp_set_tec";
   if (q.cfg.precision != LP_PREC_FP16) return "group launches take the FP16 tensor-core form";
   if (q.fc != q.shape.F) return "group launches take whole blocks (chunk_frames = 0)";
+  if (q.cfg.stream_blocks) return "group launches do not take stream_blocks plans";
   if (q.cfg.fine_dedisp || q.cfg.inversion != LP_INV_FIR)
     return "group launches take the FIR synthesis without fine de-dispersion";
   if (q.device != p0.device) return "the plans live on different devices";

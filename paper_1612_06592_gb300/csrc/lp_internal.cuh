@@ -207,6 +207,17 @@ struct lp_plan {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_entry = nullptr;
   cudaEvent_t ev_pol[2] = {};
+  // streaming host blocks (cfg.stream_blocks): block b uses staging buffer and
+  // trigger list b mod 2; ev_free[i] marks the last beamformer read of staging
+  // buffer i, ev_done[i] the end of the block in trigger list i
+  void* staging_buf[2] = {};
+  lp::TriggerRec* trig_buf[2] = {};
+  unsigned long long* count_buf[2] = {};
+  cudaEvent_t ev_free[2] = {};
+  cudaEvent_t ev_done[2] = {};
+  cudaStream_t read_stream = nullptr;    // trigger reads of lp_get_triggers_block
+  bool free_recorded[2] = {};
+  long long block_in[2] = {-1, -1};
   // graph mode (cfg.use_graph): the per-block launch sequence captured once
   cudaGraphExec_t graph_exec = nullptr;
   const void* graph_x = nullptr;

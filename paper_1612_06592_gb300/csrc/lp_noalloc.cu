@@ -91,6 +91,7 @@ extern "C" lp_status lp_process_block_noalloc(
   c.host_input = 0;
   c.trigger_cap = trigger_cap > 0 ? trigger_cap : 1;
   c.chunk_frames = 0;
+  c.stream_blocks = 0;
   if (lp_plan_configure(&p, &c) != LP_OK) return report(err, errlen, LP_ERR_ARG, p.err.c_str());
   p.cfg.trigger_cap = trigger_cap;
 

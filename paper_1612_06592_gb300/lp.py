@@ -43,6 +43,7 @@ class lp_config(ctypes.Structure):
         ("fine_dedisp", ctypes.c_int32),
         ("inversion", ctypes.c_int32),
         ("lsmr_iters", ctypes.c_int32),
+        ("stream_blocks", ctypes.c_int32),
     ]
 
 
@@ -76,6 +77,8 @@ SIGNATURES = {
     "lp_process_block": (ctypes.c_int, [_P, _P, _P]),
     "lp_process_block_strided": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "lp_get_triggers": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "lp_get_triggers_block": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64,
+                                             ctypes.POINTER(ctypes.c_int64)]),
     "lp_get_timeseries": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "lp_get_beams": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "lp_get_sigma": (ctypes.c_int, [_P, _P]),
@@ -176,7 +179,8 @@ class Plan:
                  sigma_alpha=0.25, nu_ref_hz=0.0, trigger_cap=1 << 20,
                  store_timeseries=False, host_input=False, frames_per_cta=0,
                  kaiser_beta=9.0, use_graph=False, chunk_frames=0, fine_dedisp=False,
-                 inversion="fir", lsmr_iters=25, stream=None, workspace=None):
+                 inversion="fir", lsmr_iters=25, stream_blocks=False, stream=None,
+                 workspace=None):
         import torch
         self.shape = (stations, pols, subbands, beams, tec_trials, block_len)
         self._h = _P()
@@ -199,6 +203,7 @@ class Plan:
         c.fine_dedisp = int(bool(fine_dedisp))
         c.inversion = LP_INV_LSMR if inversion == "lsmr" else LP_INV_FIR
         c.lsmr_iters = int(lsmr_iters)
+        c.stream_blocks = int(bool(stream_blocks))
         self.config = c
         self._check(_lib.lp_plan_configure(self._h, ctypes.byref(c)), "lp_plan_configure")
         nbytes = ctypes.c_size_t()
@@ -209,6 +214,7 @@ class Plan:
         self.workspace = workspace
         self._check(_lib.lp_plan_bind_workspace(self._h, workspace.data_ptr(), workspace.numel(),
                                                 _stream_ptr(stream)), "bind_workspace")
+        self.blocks = 0       # blocks processed since bind or the last reset (block numbers)
 
     # -- helpers ------------------------------------------------------------
     def _check(self, st, what):
@@ -243,12 +249,14 @@ class Plan:
         shape = tuple(x.shape)
         if shape != (P, K, F, S, 2):
             raise ValueError(f"block shape {shape} != {(P, K, F, S, 2)}")
+        self.blocks += 1
         self._check(_lib.lp_process_block(self._h, _ptr(x), _stream_ptr(stream)),
                     "lp_process_block")
 
     def lp_process_block_strided(self, x, pol_stride, stream=None):
         """x: tensor whose data_ptr is pol 0 / subband 0 of the view; pol_stride in
         complex samples."""
+        self.blocks += 1
         self._check(_lib.lp_process_block_strided(self._h, _ptr(x), int(pol_stride),
                                                   _stream_ptr(stream)), "lp_process_block_strided")
 
@@ -261,6 +269,21 @@ class Plan:
         st = _lib.lp_get_triggers(self._h, out.ctypes.data, cap, ctypes.byref(n))
         if st not in (LP_OK, LP_ERR_OVERFLOW):
             self._check(st, "lp_get_triggers")
+        return out[:min(cap, n.value)], n.value, st
+
+    def lp_get_triggers_block(self, block, cap=None):
+        """Triggers of one of the last two processed blocks (0-based block count);
+        with stream_blocks the next block may still be running."""
+        n = ctypes.c_int64()
+        if cap is None:
+            self._check_overflow_ok(_lib.lp_get_triggers_block(self._h, int(block), None, 0,
+                                                               ctypes.byref(n)))
+            cap = n.value
+        out = np.zeros(max(cap, 1), dtype=TRIGGER_DTYPE)
+        st = _lib.lp_get_triggers_block(self._h, int(block), out.ctypes.data, cap,
+                                        ctypes.byref(n))
+        if st not in (LP_OK, LP_ERR_OVERFLOW):
+            self._check(st, "lp_get_triggers_block")
         return out[:min(cap, n.value)], n.value, st
 
     def _check_overflow_ok(self, st):
@@ -293,6 +316,7 @@ class Plan:
 
     def lp_reset_stream(self, stream=None):
         self._check(_lib.lp_reset_stream(self._h, _stream_ptr(stream)), "lp_reset_stream")
+        self.blocks = 0
 
     def lp_launches_per_block(self):
         return _lib.lp_launches_per_block(self._h)
@@ -302,6 +326,7 @@ class Plan:
         (frames_per_cta, {candidate: ms})."""
         best = ctypes.c_int32()
         ms = np.zeros(6, dtype=np.float64)
+        self.blocks += 1
         self._check(_lib.lp_plan_autotune(self._h, _ptr(x), _stream_ptr(stream),
                                           ctypes.byref(best), ms.ctypes.data), "lp_plan_autotune")
         cand = (64, 128, 256, 512, 1024, 2048)
@@ -326,6 +351,7 @@ class Plan:
         returns (index, {configuration: ms})."""
         best = ctypes.c_int32()
         ms = np.zeros(self.MAX_GEMM_CONFIGS, dtype=np.float64)
+        self.blocks += 1
         self._check(_lib.lp_plan_autotune_gemm(self._h, _ptr(x), _stream_ptr(stream),
                                                ctypes.byref(best), ms.ctypes.data),
                     "lp_plan_autotune_gemm")

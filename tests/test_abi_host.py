@@ -36,7 +36,8 @@ def test_every_declared_symbol_is_exported_and_bound(lib):
 def test_struct_layouts(lib):
     assert ctypes.sizeof(lib.lp_trigger) == 32
     assert lib.TRIGGER_DTYPE.itemsize == 32
-    assert ctypes.sizeof(lib.lp_config) == 88
+    assert ctypes.sizeof(lib.lp_config) == 96
+    assert lib.lp_config.stream_blocks.offset == 88
 
 
 def _create(lib, *shape):
@@ -210,3 +211,33 @@ def test_launch_counts_of_the_paths(lib):
         assert lib._lib.lp_plan_configure(h, ctypes.byref(c)) == lib.LP_OK
         assert lib._lib.lp_launches_per_block(h) == want, fields
         lib._lib.lp_plan_destroy(h)
+
+
+def test_stream_blocks_configuration_is_checked(lib):
+    c = lib._lib
+    st, h = _create(lib, 4, 2, 8, 2, 1, 256)
+    cfg = lib.config_default()
+    assert cfg.stream_blocks == 0
+    for bad in (dict(stream_blocks=2), dict(stream_blocks=1, use_graph=1)):
+        k = lib.config_default()
+        for f, v in bad.items():
+            setattr(k, f, v)
+        assert c.lp_plan_configure(h, ctypes.byref(k)) == lib.LP_ERR_ARG, bad
+    k = lib.config_default()
+    k.stream_blocks = 1
+    k.host_input = 1
+    assert c.lp_plan_configure(h, ctypes.byref(k)) == lib.LP_OK
+    # two staging buffers and two trigger lists
+    n2 = ctypes.c_size_t()
+    assert c.lp_plan_workspace_bytes(h, ctypes.byref(n2)) == lib.LP_OK
+    c.lp_plan_destroy(h)
+    st, h = _create(lib, 4, 2, 8, 2, 1, 256)
+    k.stream_blocks = 0
+    assert c.lp_plan_configure(h, ctypes.byref(k)) == lib.LP_OK
+    n1 = ctypes.c_size_t()
+    assert c.lp_plan_workspace_bytes(h, ctypes.byref(n1)) == lib.LP_OK
+    one_block = 2 * 8 * 256 * 4 * 2
+    assert n2.value - n1.value >= one_block + 32 * k.trigger_cap
+    n = ctypes.c_int64()
+    assert c.lp_get_triggers_block(h, 0, None, 0, ctypes.byref(n)) == lib.LP_ERR_STATE
+    c.lp_plan_destroy(h)
