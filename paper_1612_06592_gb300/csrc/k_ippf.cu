@@ -431,7 +431,13 @@ __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float
     e2v[f] = fmaf(u.x, u.x, u.y * u.y);
     emax = fmaxf(emax, e2v[f]);         // frames outside the run are filtered by vmask
   }
-  if (__any_sync(0xffffffffu, emax > c.th2)) emit_triggers(e2v, c.th2, p, r0, si);
+  if (__any_sync(0xffffffffu, emax > c.th2)) {
+    // the rare trigger path gets its own copy, so that e2v stays in registers
+    float e2c[FB];
+#pragma unroll
+    for (int f = 0; f < FB; ++f) e2c[f] = e2v[f];
+    emit_triggers(e2c, c.th2, p, r0, si);
+  }
 }
 
 // One phase of the FIR role for batch r0: its 8 new frames zn, history from
