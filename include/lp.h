@@ -407,12 +407,8 @@ const char* lp_status_string(lp_status s);
  * [-32767, 32767], in the station-block layout [P][K][F][G][2] (re, im), so
  * that an lp_plan with stations = G, LP_INPUT_INT16 and the group centres as
  * station positions (lp_prebeam_group_centres) forms the final beams.
- * Groups are disjoint; a station in no group is unused.  The phase argument
- * in FP64 cycles.  Int8 input with a multiple of 4 stations (at most 64), at
- * most 64 groups and 16-byte aligned subband rows: the group sums run on the
- * tensor cores as the beamformer's GEMM with block-diagonal weights (int8
- * exact in FP16, each weight an FP16 high and low part, FP32 accumulation);
- * otherwise FP32 products and sums on the CUDA cores. */
+ * Groups are disjoint; a station in no group is unused.  FP32 products and
+ * sums; the phase argument in FP64 cycles. */
 typedef struct lp_prebeam lp_prebeam;
 
 /* Shapes only (no device work): stations S, pols 1 or 2, subbands K, frames F,

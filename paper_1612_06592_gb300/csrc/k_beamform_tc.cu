@@ -263,14 +263,7 @@ struct TcArgs {
   int n;                    // plans
   TcPlan pl[kMaxGroup];
   CUtensorMap maps[kMaxGroup];   // TMA map of each plan's beam rows
-  // int16-code epilogue (preliminary beams of station groups): codes [P][K][F][B]
-  // of round-half-even(scale * beam) saturated to +-32767, saturations counted
-  short2* codes;
-  float scale;
-  unsigned long long* n_sat;
 };
-
-enum { EPI_BEAMS = 0, EPI_CODES = 1 };
 
 // The tile sequence every role walks: items [it0, it1) of the launch (plan 0's
 // items, then plan 1's, ...), 256-frame tiles each.  GROUP = false: one plan
@@ -320,9 +313,7 @@ struct TileSeq {
   }
 };
 
-// EPI = EPI_BEAMS: de-dispersed FP32 beam rows by TMA and noise partials;
-// EPI = EPI_CODES: int16 transport codes of the (group) beams, no de-dispersion.
-template <bool GROUP, int EPI>
+template <bool GROUP>
 __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int KP = kpad(a.S);
@@ -500,7 +491,6 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
     int acc = 0;
     uint32_t pha = 0;
     float pw = 0.f;
-    int sat = 0;                                // saturated codes (EPI_CODES)
     for (; q.valid(); q.next()) {
       if (!wait_phase(&tfull[acc], pha, abort_p)) break;
       tc_fence_after();
@@ -514,7 +504,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
       const long long f_hi = q.f_hi, n0 = q.n0;
       const uint32_t lane_addr =
           tmem + acc * TN + ((uint32_t)(quarter * 32) << 16) + col_half * (TN / 2);
-      const float2 d0 = EPI == EPI_BEAMS ? pl.dd[k * pl.Tr] : make_float2(1.f, 0.f);
+      const float2 d0 = pl.dd[k * pl.Tr];
       const int rloc = lane >> 1;                // beam row inside the warp's 16-beam box
       for (int c0 = 0; c0 < TN / 2; c0 += 32) {
         uint32_t r[2][16];
@@ -526,7 +516,6 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
         // stores, were the epilogue's cost)
         float2 bvh[2][8];
         long long fbh[2];
-        int ninh[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float recv[8];
@@ -540,7 +529,6 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
           // last tile of an item (warp-uniform test first); partials of beams
           // beyond B are never stored
           const int nin = fb + 16 <= f_hi ? 8 : (int)max(0LL, min(8LL, f_hi - fb - (odd ? 8 : 0)));
-          ninh[h] = nin;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {   // even lane: (Re, Im) of frames 0-7, odd: 8-15
             bvh[h][i] = odd ? make_float2(recv[i], __uint_as_float(r[h][i + 8]))
@@ -548,27 +536,7 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
             if (i < nin) pw = fmaf(bvh[h][i].x, bvh[h][i].x, fmaf(bvh[h][i].y, bvh[h][i].y, pw));
           }
         }
-        if constexpr (EPI == EPI_CODES) {
-          // lanes 2r, 2r+1 hold frames 0-7 / 8-15 of group b; a frame's codes of
-          // consecutive groups are consecutive words of the output
-          if (beam_ok) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const long long f0 = a.f_base + fbh[h] + (odd ? 8 : 0);
-              short2* out = a.codes + ((long long)(pol * pl.K + k) * a.F_in + f0) * pl.B + b;
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                if (i < ninh[h]) {
-                  const float sr = bvh[h][i].x * a.scale, si = bvh[h][i].y * a.scale;
-                  sat += (fabsf(sr) >= 32767.5f ? 1 : 0) + (fabsf(si) >= 32767.5f ? 1 : 0);
-                  out[(long long)i * pl.B] =
-                      make_short2((short)__float2int_rn(fminf(fmaxf(sr, -32767.f), 32767.f)),
-                                  (short)__float2int_rn(fminf(fmaxf(si, -32767.f), 32767.f)));
-                }
-              }
-            }
-          }
-        } else if (fbh[0] < f_hi && a.write_beams) {
+        if (fbh[0] < f_hi && a.write_beams) {
           for (int t = 0; t < pl.Tr; ++t) {
             const float2 dv = t == 0 ? d0 : pl.dd[k * pl.Tr + t];
             if (lane == 0) bulk_wait_read<0>();   // earlier stores have read both boxes
@@ -615,10 +583,6 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
       }
     }
     if (lane == 0) bulk_wait_all();     // staged boxes read and written before exit
-    if constexpr (EPI == EPI_CODES) {
-      for (int off = 16; off > 0; off >>= 1) sat += __shfl_xor_sync(0xffffffffu, sat, off);
-      if (lane == 0 && sat) atomicAdd(a.n_sat, (unsigned long long)sat);
-    }
   }
   tc_fence_before();
   __syncthreads();
@@ -729,9 +693,8 @@ size_t tc_smem(const Shape& sh) {            // the largest configuration
 }
 
 cudaError_t init_tc_attributes(const Shape& sh) {
-  cudaError_t e = raise_smem_limit((const void*)k_beamform_tc<false, EPI_BEAMS>, tc_smem(sh));
-  if (e == cudaSuccess)
-    e = raise_smem_limit((const void*)k_beamform_tc<true, EPI_BEAMS>, tc_smem(sh));
+  cudaError_t e = raise_smem_limit((const void*)k_beamform_tc<false>, tc_smem(sh));
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_beamform_tc<true>, tc_smem(sh));
   return e;
 }
 
@@ -789,13 +752,10 @@ cudaError_t launch_beamform_tc_plans(const lp_plan* const* plans, const void* co
     }
   }
   const long long grid = std::min<long long>(a.n_items, (long long)num_sms());
-  a.codes = nullptr;
-  a.scale = 1.f;
-  a.n_sat = nullptr;
   if (n == 1)
-    k_beamform_tc<false, EPI_BEAMS><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
+    k_beamform_tc<false><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
   else
-    k_beamform_tc<true, EPI_BEAMS><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
+    k_beamform_tc<true><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -803,70 +763,6 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_st
                                const Chunk& c, cudaStream_t s, PolSel ps) {
   const lp_plan* one = &p;
   return launch_beamform_tc_plans(&one, &x, pol_stride, 1, c, s, ps);
-}
-
-// ---- preliminary beams of station groups on the tensor cores -------------
-// The group sums are the beamformer's GEMM with block-diagonal weights (a
-// station's weight in its own group's row, zero elsewhere): the same kernel
-// with the int16-code epilogue.
-
-size_t prebeam_tc_weight_bytes(int K, int G, int S) {
-  const int n_mt = (G + TM / 2 - 1) / (TM / 2);
-  return (size_t)K * n_mt * 2 * TM * kpad(S) * sizeof(__half);
-}
-
-cudaError_t launch_weights_tc_raw(const float2* w32, int K, int G, int S, __half* wtc,
-                                  cudaStream_t s) {
-  const int n_mt = (G + TM / 2 - 1) / (TM / 2);
-  const long long total = (long long)K * n_mt * TM * kpad(S);
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
-  k_weights_tc<<<blocks, 256, 0, s>>>(w32, K, G, S, n_mt, wtc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_prebeam_tc(const int8_t* x, long long pol_stride, int S, int P, int K,
-                              long long F, int G, const __half* wtc, short2* codes, float scale,
-                              unsigned long long* n_sat, int* err, cudaStream_t s) {
-  const Shape sh{S, P, K, G, 1, F};
-  cudaError_t e = raise_smem_limit((const void*)k_beamform_tc<false, EPI_CODES>, tc_smem(sh));
-  if (e != cudaSuccess) return e;
-  TcArgs a;
-  std::memset(&a, 0, sizeof a);
-  a.err = err;
-  a.S = S;
-  a.P = P;
-  a.n_chunks = (int)((F + CHUNK - 1) / CHUNK);
-  a.F = F;
-  a.row = F + kPrefix;
-  a.F_in = F;
-  a.f_base = 0;
-  a.chunk_base = 0;
-  a.n_chunks_total = a.n_chunks;
-  a.write_beams = 0;
-  a.write_power = 0;
-  a.pol0 = 0;
-  a.npol = P;
-  a.n = 1;
-  TcPlan& q = a.pl[0];
-  q.x = x;
-  q.pol_stride = pol_stride;
-  q.wtc = wtc;
-  q.dd = nullptr;
-  q.power_part = nullptr;
-  q.K = K;
-  q.B = G;
-  q.Tr = 1;
-  q.n_mt = (G + TM / 2 - 1) / (TM / 2);
-  q.km0 = 0;
-  q.item_end = (long long)K * q.n_mt * P * a.n_chunks;
-  a.n_items = q.item_end;
-  a.codes = codes;
-  a.scale = scale;
-  a.n_sat = n_sat;
-  tc_depths(sh, &a.n_s8, &a.n_sb);
-  const long long grid = std::min<long long>(a.n_items, (long long)num_sms());
-  k_beamform_tc<false, EPI_CODES><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
-  return cudaGetLastError();
 }
 
 }  // namespace lp

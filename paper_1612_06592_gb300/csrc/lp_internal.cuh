@@ -283,16 +283,6 @@ int beamform_f32_frame_tile();
 // accumulator pass, 0).  Returns the count (at most max).
 int beamform_gemm_configs(const lp_plan& p, int* desc, int max);
 int beamform_tc_frame_tile();
-// Preliminary beams of station groups on the tensor cores (int8 input, 4 | S,
-// S <= 64, G <= 64): FP16 hi/lo images of the block-diagonal weights w32
-// [K][G][S], then the group sums as int16 codes [P][K][F][G] (round half to
-// even of scale * value, saturated to +-32767, saturations added to *n_sat).
-size_t prebeam_tc_weight_bytes(int K, int G, int S);
-cudaError_t launch_weights_tc_raw(const float2* w32, int K, int G, int S, __half* wtc,
-                                  cudaStream_t s);
-cudaError_t launch_prebeam_tc(const int8_t* x, long long pol_stride, int S, int P, int K,
-                              long long F, int G, const __half* wtc, short2* codes, float scale,
-                              unsigned long long* n_sat, int* err, cudaStream_t s);
 int beamform_tc_partials(long long F);
 size_t beamform_tc_weight_bytes(const Shape& sh);
 int ippf_default_frames_per_cta(const Shape& sh);

@@ -43,12 +43,6 @@ struct lp_prebeam {
   double* rel = nullptr;                // [E][3] r_s - r_g
   double* mdir = nullptr;               // [E][3] direction of the member's group
   unsigned long long* n_sat = nullptr;  // saturated int16 codes since the last read
-  // tensor-core form (int8 input, 4 | S <= 64, G <= 64): the block-diagonal
-  // weights [K][G][S] and their FP16 hi/lo images; a device error word
-  bool tc = false;
-  float2* w32 = nullptr;
-  __half* wtc = nullptr;
-  int* dev_err = nullptr;               // 1: a bounded wait of the tensor-core form gave up
   std::vector<double> centres;          // [G][3]
   bool groups_set = false;
   cudaStream_t last_stream = nullptr;
@@ -225,25 +219,6 @@ __global__ void __launch_bounds__(PB_NTH) k_prebeam(
 
 // w1[k][e] = exp(-2 pi i nu_k ((r_s - r_g) . s_g) / c): the argument in FP64
 // cycles, reduced to [-1/2, 1/2] before the FP32 sincospif
-// Block-diagonal weights of the tensor-core form: w32[k][g][s] = w1[k][e] for
-// member e = station s of group g, zero for stations of other groups.
-__global__ void k_prebeam_expand(const float2* __restrict__ w1, const int* __restrict__ member,
-                                 const int* __restrict__ goff, int K, int G, int S, int E,
-                                 float2* __restrict__ w32) {
-  const long long total = (long long)K * G * S;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x)
-    w32[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  // one block: the scatter follows its own zeroing (a single-block launch)
-  for (long long i = threadIdx.x; i < (long long)K * E; i += blockDim.x) {
-    const int k = (int)(i / E), e = (int)(i % E);
-    int g = 0;
-    while (g + 1 < G && e >= goff[g + 1]) ++g;
-    w32[((long long)k * G + g) * S + member[e]] = w1[i];
-  }
-}
-
 __global__ void k_prebeam_weights(const double* __restrict__ rel, const double* __restrict__ dir,
                                   int K, int E, int first_bin, float2* __restrict__ w1) {
   const long long total = (long long)K * E;
@@ -312,10 +287,6 @@ size_t pb_carve(lp_prebeam& pb, char* base) {
   pb.member = (int*)take(sizeof(int) * S);
   pb.goff = (int*)take(sizeof(int) * (G + 1));
   pb.n_sat = (unsigned long long*)take(sizeof(unsigned long long));
-  pb.tc = pb.input_dtype == LP_INPUT_INT8 && S % 4 == 0 && S <= 64 && G <= 64;
-  pb.w32 = pb.tc ? (float2*)take(sizeof(float2) * (size_t)pb.K * G * S) : nullptr;
-  pb.wtc = pb.tc ? (__half*)take(lp::prebeam_tc_weight_bytes(pb.K, G, S)) : nullptr;
-  pb.dev_err = (int*)take(sizeof(int));
   return (off + 255) / 256 * 256;
 }
 
@@ -363,7 +334,6 @@ lp_status lp_prebeam_workspace_bytes(const lp_prebeam* pb, size_t* bytes) {
   tmp.S = pb->S;
   tmp.K = pb->K;
   tmp.G = pb->G;
-  tmp.input_dtype = pb->input_dtype;
   *bytes = lp::pb_carve(tmp, nullptr);
   return LP_OK;
 }
@@ -387,7 +357,6 @@ lp_status lp_prebeam_bind_workspace(lp_prebeam* pb, void* dev, size_t bytes, voi
   pb_carve(*pb, static_cast<char*>(dev));
   PB_CUDA(pb, cudaMemsetAsync(pb->n_sat, 0, sizeof(unsigned long long),
                               static_cast<cudaStream_t>(stream)));
-  PB_CUDA(pb, cudaMemsetAsync(pb->dev_err, 0, sizeof(int), static_cast<cudaStream_t>(stream)));
   pb->last_stream = static_cast<cudaStream_t>(stream);
   return LP_OK;
 }
@@ -454,11 +423,6 @@ lp_status lp_prebeam_set_groups(lp_prebeam* pb, const int32_t* group_of_station,
   const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
   k_prebeam_weights<<<blocks, 256, 0, s>>>(pb->rel, pb->mdir, pb->K, E, pb->first_bin, pb->w1);
   PB_CUDA(pb, cudaGetLastError());
-  if (pb->tc) {
-    k_prebeam_expand<<<1, 1024, 0, s>>>(pb->w1, pb->member, pb->goff, pb->K, G, S, E, pb->w32);
-    PB_CUDA(pb, cudaGetLastError());
-    PB_CUDA(pb, launch_weights_tc_raw(pb->w32, pb->K, G, S, pb->wtc, s));
-  }
   const int smem = (int)prebeam_smem(*pb);
   if (smem > 227 * 1024) return pb_fail(pb, LP_ERR_ARG, "too many stations for one tile");
   if (pb->input_dtype == LP_INPUT_INT8)
@@ -497,12 +461,7 @@ lp_status lp_prebeam_run(lp_prebeam* pb, const void* x, void* y, float scale, vo
   // 16-byte chunk reads when every (pol, subband) slab starts 16-byte aligned
   // (tiles then do too: 256 frames of S samples of 2 or 4 bytes)
   const int vec = reinterpret_cast<uintptr_t>(x) % 16 == 0 && (pb->F * pb->S * t2) % 16 == 0;
-  if (pb->tc && vec) {
-    // the tensor-core form: bulk copies of 16-byte aligned subband rows
-    PB_CUDA(pb, launch_prebeam_tc(static_cast<const int8_t*>(x), (long long)pb->K * pb->F * pb->S,
-                                  pb->S, pb->P, pb->K, pb->F, pb->G, pb->wtc,
-                                  static_cast<short2*>(y), scale, pb->n_sat, pb->dev_err, s));
-  } else if (pb->input_dtype == LP_INPUT_INT8)
+  if (pb->input_dtype == LP_INPUT_INT8)
     k_prebeam<char2><<<grid, PB_NTH, smem, s>>>(static_cast<const char2*>(x), pb->w1, pb->member,
                                                 pb->goff, pb->S, pb->K, pb->G, pb->E, pb->F,
                                                 scale, vec, static_cast<short2*>(y), pb->n_sat);
@@ -527,12 +486,6 @@ lp_status lp_prebeam_saturated(lp_prebeam* pb, int64_t* n) {
   PB_CUDA(pb, cudaMemcpy(&v, pb->n_sat, sizeof v, cudaMemcpyDeviceToHost));
   PB_CUDA(pb, cudaMemset(pb->n_sat, 0, sizeof v));
   *n = (int64_t)v;
-  int derr = 0;
-  PB_CUDA(pb, cudaMemcpy(&derr, pb->dev_err, sizeof derr, cudaMemcpyDeviceToHost));
-  if (derr) {
-    PB_CUDA(pb, cudaMemset(pb->dev_err, 0, sizeof derr));
-    return pb_fail(pb, LP_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core form)");
-  }
   return LP_OK;
 }
 
