@@ -59,8 +59,10 @@ typedef enum {
 enum { LP_INPUT_INT8 = 1, LP_INPUT_INT16 = 2 };
 
 /* Beamformer arithmetic.  LP_PREC_FP32: plain FP32 FMA station sum.
- * LP_PREC_FP16: tensor-core CGEMM, int8 samples exact in FP16, weights split
- * into an FP16 high and low part, FP32 accumulation (int8 input only). */
+ * LP_PREC_FP16: tensor-core CGEMM, weights split into an FP16 high and low
+ * part, FP32 accumulation; int8 samples are exact in FP16, int16 samples v
+ * enter as the two exact FP16 parts 256 (v >> 8) and v & 255 (four products
+ * per sample instead of two).  Needs a multiple of 4 stations. */
 enum { LP_PREC_FP32 = 0, LP_PREC_FP16 = 1 };
 
 typedef struct {
@@ -261,7 +263,7 @@ lp_status lp_plan_autotune(lp_plan* plan, const void* x, void* stream, int32_t* 
 /* Beamformer configurations (the GEMM autotuner's candidates; no counterpart
  * in the paper).  Writes up to max pairs into desc[2 i], desc[2 i + 1] and
  * returns their number (at most LP_MAX_GEMM_CONFIGS), or -1 for an unbound
- * plan.  FP16 form: (int8 ring stages, FP16 ring stages) of the tensor-core
+ * plan.  FP16 form: (input ring stages, FP16 ring stages) of the tensor-core
  * beamformer that fit the shared memory for this shape, deepest first; FP32
  * form: (beams per accumulator pass, 0), i.e. (8, 0), (16, 0) and (4, 0).  Every
  * configuration computes the same beams bit for bit. */
@@ -332,9 +334,10 @@ typedef struct lp_group lp_group;
 lp_status lp_group_create(lp_group** out, lp_plan* const* plans, int n);
 
 /* One block for every plan of the group, asynchronously on `stream`.
- * x: device block [P][subbands][F][S][2] complex int8 holding the contiguous
- * bins [first_bin, first_bin + subbands), 16-byte aligned with 16-byte
- * aligned subband rows (F * S * 2 bytes); each plan reads its own bins.
+ * x: device block [P][subbands][F][S][2] complex int8 or int16 (the plans'
+ * type) holding the contiguous bins [first_bin, first_bin + subbands),
+ * 16-byte aligned with 16-byte aligned subband rows (F * S * 2 or 4 bytes);
+ * each plan reads its own bins.
  * Afterwards each plan's lp_get_triggers / lp_get_sigma / lp_get_timeseries
  * read its results as after lp_process_block. */
 lp_status lp_group_process_block(lp_group* group, const void* x, int32_t subbands,

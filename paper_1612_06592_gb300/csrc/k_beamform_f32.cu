@@ -189,10 +189,11 @@ cudaError_t launch_beamform_f32(const lp_plan& p, const void* x, long long pol_s
   return cudaGetLastError();
 }
 
-int tc_configs(const Shape& sh, int* desc, int max);
+int tc_configs(const Shape& sh, int esz, int* desc, int max);
 
 int beamform_gemm_configs(const lp_plan& p, int* desc, int max) {
-  if (p.cfg.precision == LP_PREC_FP16) return tc_configs(p.shape, desc, max);
+  if (p.cfg.precision == LP_PREC_FP16)
+    return tc_configs(p.shape, p.cfg.input_dtype == LP_INPUT_INT8 ? 1 : 2, desc, max);
   int n = 0;
   for (int i = 0; i < 3 && n < max; ++i, ++n) {
     desc[2 * n] = kF32Beams[i];

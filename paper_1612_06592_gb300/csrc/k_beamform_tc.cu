@@ -9,21 +9,24 @@
 // The int8 samples are exact in FP16; each weight is split into an FP16 high
 // part and an FP16 low part (w - hi), and both products accumulate in FP32 in
 // tensor memory, which keeps the weight error near 1e-7 (one FP16 part alone
-// would leave ~1.5e-4 relative error in the beams).
+// would leave ~1.5e-4 relative error in the beams).  int16 samples v are split
+// as v = 256 h + l (h = v >> 8 in [-128, 127], l = v & 255), and 256 h and l
+// are both exact in FP16: two B images, four products per K step.
 //
 // Work items: (subband k, beam tile of 64 beams, pol, chunk of 2048 frames),
 // eight 256-frame tiles each.  One persistent block per SM walks a contiguous
 // item range as a warp-specialised pipeline:
-//   warp 0      producer: cp.async.bulk copies of each tile's int8 samples
-//               (256 frames x 2S contiguous bytes) into a ring of stages, and of
+//   warp 0      producer: cp.async.bulk copies of each tile's samples
+//               (256 frames x 2S contiguous int8 or int16) into a ring of stages, and of
 //               the A images (hi and lo weights, pre-arranged by k_weights_tc)
 //               whenever (k, beam tile) changes;
 //   warps 2-9   converters: int8 -> FP16 in the canonical K-major no-swizzle
 //               layout (8-row x 16-byte core matrices), a ring of B stages.
 //               A byte b becomes the FP16 number 1024 + (b ^ 0x80) by placing
 //               it under the exponent pattern of 1024 (byte permute), and one
-//               packed subtraction of 1152 leaves b exactly;
-//   warp 1      MMA: one thread issues 2 * 2S/16 tcgen05.mma (M = 128, N = 256,
+//               packed subtraction of 1152 leaves b exactly (int16: the high
+//               byte so, then times 256; the low byte as 1024 + l minus 1024);
+//   warp 1      MMA: one thread issues 2 * 2S/16 (int16: 4 * 2S/16) tcgen05.mma (M = 128, N = 256,
 //               K = 16) into one of two 256-column TMEM accumulators and
 //               commits to mbarriers that free the B stage and publish the
 //               accumulator;
@@ -157,6 +160,28 @@ __device__ __forceinline__ uint4 i8x8_to_f16x8(uint2 q) {
   return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
+// Eight int16 samples (16 bytes) -> the FP16 images of 256 h and of l,
+// v = 256 h + l: the high byte h as above (then times 256, exact), the low
+// byte l (0..255) as 1024 + l minus 1024.
+__device__ __forceinline__ void i16x8_to_f16x8x2(uint4 q, uint4& hi, uint4& lo) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  const __half2 b_hi = __half2half2(__ushort_as_half((unsigned short)0x6480));
+  const __half2 b_lo = __half2half2(__ushort_as_half((unsigned short)0x6400));
+  const __half2 s256 = __half2half2(__ushort_as_half((unsigned short)0x5C00));
+  uint32_t oh[4], ol[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t ph = __byte_perm(w[i] ^ 0x80808080u, 0x64646464u, 0x4341);
+    const uint32_t pl = __byte_perm(w[i], 0x64646464u, 0x4240);
+    const __half2 h = __hmul2(__hsub2(*reinterpret_cast<const __half2*>(&ph), b_hi), s256);
+    const __half2 l = __hsub2(*reinterpret_cast<const __half2*>(&pl), b_lo);
+    oh[i] = *reinterpret_cast<const uint32_t*>(&h);
+    ol[i] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+  hi = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+  lo = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+}
+
 // A-operand images: [k][beam tile][hi/lo][TM x KP] FP16 in the layout above.
 __global__ void k_weights_tc(const float2* __restrict__ w32, int K, int B, int S, int n_mt,
                              __half* __restrict__ wtc) {
@@ -240,7 +265,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
 // outputs.  One launch serves one plan, or a group of plans (lp_group) on
 // different subband ranges and beams of one station block.
 struct TcPlan {
-  const int8_t* x;          // pol slabs [K][F][S][2], pol_stride complex samples apart
+  const int8_t* x;          // pol slabs [K][F][S][2] (int8 or int16), pol_stride complex samples apart
   long long pol_stride;
   const __half* wtc;        // A images
   const float2* dd;         // [K][Tr]
@@ -313,14 +338,17 @@ struct TileSeq {
   }
 };
 
-template <bool GROUP>
+// X16: int16 input (two B images per stage: 256 h, then l).
+template <bool GROUP, bool X16>
 __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int ESZ = X16 ? 2 : 1;               // bytes per real sample value
   const int KP = kpad(a.S);
   const int nkg = KP / 8;
   const uint32_t a_bytes = TM * KP * 2;          // one of hi / lo
-  const uint32_t b_bytes = TN * KP * 2;
-  const uint32_t t8_bytes = TN * 2 * a.S;        // int8 tile
+  const uint32_t img_bytes = TN * KP * 2;        // one FP16 B image
+  const uint32_t b_bytes = img_bytes * ESZ;      // one B stage
+  const uint32_t t8_bytes = TN * 2 * a.S * ESZ;  // input tile
   // output staging boxes, aligned to 1024 bytes of the shared window (128-byte swizzle)
   unsigned char* stg = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);
   unsigned char* sa = stg + STG_BYTES;           // A hi, A lo
@@ -380,9 +408,9 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
         const int k = (int)(km / pl.n_mt);
         const int nvalid = (int)min((long long)TN, q.f_hi - q.n0);
         const int8_t* src =
-            pl.x + 2 * ((q.pol() + a.pol0) * pl.pol_stride +
-                        ((long long)k * a.F_in + a.f_base + q.n0) * a.S);
-        const uint32_t bytes = (uint32_t)nvalid * 2 * a.S;
+            pl.x + 2 * ESZ * ((q.pol() + a.pol0) * pl.pol_stride +
+                              ((long long)k * a.F_in + a.f_base + q.n0) * a.S);
+        const uint32_t bytes = (uint32_t)nvalid * 2 * ESZ * a.S;
         mbar_expect_tx(&full8[st], bytes);
         bulk_g2s(s8 + st * t8_bytes, src, bytes, &full8[st]);
         issued |= 1u << st;
@@ -430,9 +458,12 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
         const uint32_t b0 = smem_u32(sbuf + sb * b_bytes);
         const uint32_t d = tmem + acc * TN;
         for (int ks = 0; ks < KP / 16; ++ks) {
-          const uint64_t bd = smem_desc(b0 + ks * 256, 128, sbo);
-          mma_f16(d, smem_desc(a0 + ks * 256, 128, sbo), bd, idesc, ks > 0 ? 1u : 0u);
-          mma_f16(d, smem_desc(a0 + a_bytes + ks * 256, 128, sbo), bd, idesc, 1u);
+#pragma unroll
+          for (int im = 0; im < ESZ; ++im) {
+            const uint64_t bd = smem_desc(b0 + im * img_bytes + ks * 256, 128, sbo);
+            mma_f16(d, smem_desc(a0 + ks * 256, 128, sbo), bd, idesc, ks + im > 0 ? 1u : 0u);
+            mma_f16(d, smem_desc(a0 + a_bytes + ks * 256, 128, sbo), bd, idesc, 1u);
+          }
         }
         mma_commit(&emptyB[sb]);
         mma_commit(&tfull[acc]);
@@ -466,13 +497,23 @@ __global__ void __launch_bounds__(NT, 1) k_beamform_tc(const __grid_constant__ T
         const int c = cg * 4 + c_sub;
         if (c >= nkg) continue;
         const bool in = 8 * c < 2 * a.S;        // K padding converts to zeros
-        const unsigned char* sp = src + n_sub * (2 * a.S) + 8 * c;
+        const unsigned char* sp = src + n_sub * (2 * ESZ * a.S) + 8 * ESZ * c;
         unsigned char* dp = dst + core_off(n_sub, 8 * c, KP);
+        if constexpr (X16) {
 #pragma unroll 4
-        for (int ng = cw; ng < TN / 8; ng += N_CONV) {
-          uint4 h8 = make_uint4(0, 0, 0, 0);
-          if (in) h8 = i8x8_to_f16x8(*reinterpret_cast<const uint2*>(sp + ng * 16 * a.S));
-          *reinterpret_cast<uint4*>(dp + ng * (KP / 8) * 128) = h8;
+          for (int ng = cw; ng < TN / 8; ng += N_CONV) {
+            uint4 hi = make_uint4(0, 0, 0, 0), lo = hi;
+            if (in) i16x8_to_f16x8x2(*reinterpret_cast<const uint4*>(sp + ng * 32 * a.S), hi, lo);
+            *reinterpret_cast<uint4*>(dp + ng * (KP / 8) * 128) = hi;
+            *reinterpret_cast<uint4*>(dp + img_bytes + ng * (KP / 8) * 128) = lo;
+          }
+        } else {
+#pragma unroll 4
+          for (int ng = cw; ng < TN / 8; ng += N_CONV) {
+            uint4 h8 = make_uint4(0, 0, 0, 0);
+            if (in) h8 = i8x8_to_f16x8(*reinterpret_cast<const uint2*>(sp + ng * 16 * a.S));
+            *reinterpret_cast<uint4*>(dp + ng * (KP / 8) * 128) = h8;
+          }
         }
       }
       fence_proxy_async();
@@ -617,12 +658,12 @@ cudaError_t launch_weights_tc(const lp_plan& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Pipeline depths that fit the 227 KB of shared memory: A (hi + lo), int8
-// stages, FP16 stages.
-void tc_depths(const Shape& sh, int* n_s8, int* n_sb) {
+// Pipeline depths that fit the 227 KB of shared memory: A (hi + lo), input
+// stages, FP16 stages; esz = bytes per real input value (1: int8, 2: int16).
+void tc_depths(const Shape& sh, int esz, int* n_s8, int* n_sb) {
   const size_t limit = 227 * 1024 - 2048 - STG_BYTES - 1024;
   const size_t KP = kpad(sh.S);
-  const size_t a = 2 * TM * KP * 2, t8 = (size_t)TN * 2 * sh.S, b = TN * KP * 2;
+  const size_t a = 2 * TM * KP * 2, t8 = (size_t)TN * 2 * sh.S * esz, b = TN * KP * 2 * esz;
   *n_sb = a + 2 * b + t8 <= limit ? 2 : 1;
   *n_s8 = 1;
   while (*n_s8 < MAX_S8 && a + *n_sb * b + (*n_s8 + 1) * t8 <= limit) ++*n_s8;
@@ -660,19 +701,19 @@ cudaError_t encode_beams_map(lp_plan& p) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-size_t tc_smem_for(const Shape& sh, int n8, int nb) {
+size_t tc_smem_for(const Shape& sh, int esz, int n8, int nb) {
   const size_t KP = kpad(sh.S);
   // at least 120 KB: one block per SM (it takes all 512 TMEM columns)
-  return std::max<size_t>(1024 + STG_BYTES + 2 * TM * KP * 2 + (size_t)n8 * TN * 2 * sh.S +
-                              (size_t)nb * TN * KP * 2,
+  return std::max<size_t>(1024 + STG_BYTES + 2 * TM * KP * 2 + (size_t)n8 * TN * 2 * sh.S * esz +
+                              (size_t)nb * TN * KP * 2 * esz,
                           120 * 1024);
 }
 
-// (int8 stages, FP16 stages) that fit the shared memory, deepest first
-int tc_configs(const Shape& sh, int* desc, int max) {
+// (input stages, FP16 stages) that fit the shared memory, deepest first
+int tc_configs(const Shape& sh, int esz, int* desc, int max) {
   const size_t limit = 227 * 1024 - 2048 - STG_BYTES - 1024;
   const size_t KP = kpad(sh.S);
-  const size_t a = 2 * TM * KP * 2, t8 = (size_t)TN * 2 * sh.S, b = TN * KP * 2;
+  const size_t a = 2 * TM * KP * 2, t8 = (size_t)TN * 2 * sh.S * esz, b = TN * KP * 2 * esz;
   int n = 0;
   for (int nb = MAX_SB; nb >= 1; --nb)
     for (int n8 = MAX_S8; n8 >= 1; --n8)
@@ -684,17 +725,20 @@ int tc_configs(const Shape& sh, int* desc, int max) {
   return n;
 }
 
-size_t tc_smem(const Shape& sh) {            // the largest configuration
+size_t tc_smem(const Shape& sh, int esz) {  // the largest configuration
   int desc[2 * MAX_S8 * MAX_SB];
-  const int n = tc_configs(sh, desc, MAX_S8 * MAX_SB);
+  const int n = tc_configs(sh, esz, desc, MAX_S8 * MAX_SB);
   size_t m = 0;
-  for (int i = 0; i < n; ++i) m = std::max(m, tc_smem_for(sh, desc[2 * i], desc[2 * i + 1]));
+  for (int i = 0; i < n; ++i)
+    m = std::max(m, tc_smem_for(sh, esz, desc[2 * i], desc[2 * i + 1]));
   return m;
 }
 
 cudaError_t init_tc_attributes(const Shape& sh) {
-  cudaError_t e = raise_smem_limit((const void*)k_beamform_tc<false>, tc_smem(sh));
-  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_beamform_tc<true>, tc_smem(sh));
+  cudaError_t e = raise_smem_limit((const void*)k_beamform_tc<false, false>, tc_smem(sh, 1));
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_beamform_tc<true, false>, tc_smem(sh, 1));
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_beamform_tc<false, true>, tc_smem(sh, 2));
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_beamform_tc<true, true>, tc_smem(sh, 2));
   return e;
 }
 
@@ -742,20 +786,27 @@ cudaError_t launch_beamform_tc_plans(const lp_plan* const* plans, const void* co
     std::memcpy(&a.maps[i], p.beams_map, sizeof(CUtensorMap));
   }
   a.n_items = items;
-  tc_depths(sh, &a.n_s8, &a.n_sb);
+  const bool x16 = p0.cfg.input_dtype == LP_INPUT_INT16;
+  const int esz = x16 ? 2 : 1;
+  tc_depths(sh, esz, &a.n_s8, &a.n_sb);
   if (p0.gemm_cfg >= 0) {                      // autotuned depths
     int desc[2 * MAX_S8 * MAX_SB];
-    const int nc = tc_configs(sh, desc, MAX_S8 * MAX_SB);
+    const int nc = tc_configs(sh, esz, desc, MAX_S8 * MAX_SB);
     if (p0.gemm_cfg < nc) {
       a.n_s8 = desc[2 * p0.gemm_cfg];
       a.n_sb = desc[2 * p0.gemm_cfg + 1];
     }
   }
   const long long grid = std::min<long long>(a.n_items, (long long)num_sms());
-  if (n == 1)
-    k_beamform_tc<false><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
+  const size_t smem = tc_smem_for(sh, esz, a.n_s8, a.n_sb);
+  if (n == 1 && !x16)
+    k_beamform_tc<false, false><<<(unsigned)grid, NT, smem, s>>>(a);
+  else if (!x16)
+    k_beamform_tc<true, false><<<(unsigned)grid, NT, smem, s>>>(a);
+  else if (n == 1)
+    k_beamform_tc<false, true><<<(unsigned)grid, NT, smem, s>>>(a);
   else
-    k_beamform_tc<true><<<(unsigned)grid, NT, tc_smem_for(sh, a.n_s8, a.n_sb), s>>>(a);
+    k_beamform_tc<true, true><<<(unsigned)grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

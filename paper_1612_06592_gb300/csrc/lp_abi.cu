@@ -205,8 +205,6 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
     return fail(p, LP_ERR_ARG, "input_dtype must be LP_INPUT_INT8 or LP_INPUT_INT16");
   if (c->precision != LP_PREC_FP32 && c->precision != LP_PREC_FP16)
     return fail(p, LP_ERR_ARG, "precision must be LP_PREC_FP32 or LP_PREC_FP16");
-  if (c->precision == LP_PREC_FP16 && c->input_dtype != LP_INPUT_INT8)
-    return fail(p, LP_ERR_ARG, "the FP16 tensor-core form takes int8 input only");
   if (c->precision == LP_PREC_FP16 && sh.S % 4 != 0)
     return fail(p, LP_ERR_ARG, "the FP16 tensor-core form needs a multiple of 4 stations");
   if (c->first_bin < 1 || c->first_bin + sh.K > lp::kBins)

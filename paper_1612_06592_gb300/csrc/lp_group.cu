@@ -104,9 +104,10 @@ lp_status lp_group_process_block(lp_group* g, const void* x, int32_t subbands,
   if ((attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) ||
       attr.device != g->device)
     return gfail(g, LP_ERR_ARG, "the block must be device memory of the plans' device");
-  // int8 complex samples; every plan's slab offset keeps the 16-byte alignment
-  // of the beamformer's bulk copies
-  const long long slab = (long long)sh.F * sh.S * 2;          // bytes of one subband row
+  // every plan's slab offset keeps the 16-byte alignment of the beamformer's
+  // bulk copies
+  const long long slab = (long long)sh.F * sh.S *
+                         (p0.cfg.input_dtype == LP_INPUT_INT8 ? 2 : 4);   // bytes of one subband row
   if (reinterpret_cast<uintptr_t>(x) % 16 || slab % 16)
     return gfail(g, LP_ERR_ARG, "block and subband rows must be 16-byte aligned");
   const int n = (int)g->plans.size();

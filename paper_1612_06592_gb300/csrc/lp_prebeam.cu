@@ -21,6 +21,16 @@
 // are gathered in shared memory and written back as one contiguous
 // [frame][group] range of the output.  HBM-bound: 2 S (int8) or 4 S (int16)
 // bytes in and 4 G bytes out per frame, 8 S FLOP.
+//
+// k_prebeam_pairs (int8 input, S a multiple of 8, G = 4, 8 or 16, 16-byte
+// aligned input and output): the same sums with about a third of the
+// instructions per sample.  A thread owns a frame pair: it reads the pair's
+// 16-byte chunks straight from HBM (through L1) and stores, per member
+// station, one word holding both frames' (re, im) bytes into a member-major
+// shared tile; the group sums then take one word, four byte-permutes, two
+// paired FP32 adds and four paired FMAs per station for both frames; the codes
+// are rounded by the 1.5 * 2^23 addition (round half to even, exact below
+// 2^22) and leave the thread as 16-byte stores of its 2 G contiguous words.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -217,6 +227,158 @@ __global__ void __launch_bounds__(PB_NTH) k_prebeam(
   }
 }
 
+constexpr int PF_NTH = 128;          // threads per block = frame pairs per tile
+constexpr int PF_FT = 2 * PF_NTH;    // frames per tile
+
+// Member row stride (words) of the shared tile for CW chunk slots per pair:
+// with the staging lane map below, the eight stores of one step hit 32
+// distinct banks (CW = 4: 8 c R = 8 c mod 32; CW = 2: 8 c R = 16 c mod 32).
+template <int CW>
+__host__ __device__ constexpr int pf_row() { return PF_NTH + (CW == 2 ? 2 : 1); }
+
+// Stores the member word v of frame pair p in member row r (the row's word
+// offset; -1: the station is in no group).
+__device__ __forceinline__ void pf_put(uint32_t* xs, int r, int p, uint32_t v) {
+  if (r >= 0) xs[r + p] = v;
+}
+
+// G groups; CW = 4 (at least 4 chunks of 8 stations per frame) or 2.
+template <int G, int CW>
+__global__ void __launch_bounds__(PF_NTH, 8) k_prebeam_pairs(
+    const int8_t* __restrict__ x, const float2* __restrict__ w1, const int* __restrict__ member,
+    const int* __restrict__ goff, int S, int K, int E, long long F, float scale,
+    short2* __restrict__ y, unsigned long long* __restrict__ n_sat) {
+  constexpr int R = pf_row<CW>();
+  constexpr int PPW = 32 / CW;                                // pairs per warp and pass
+  extern __shared__ float4 pf_smem[];
+  float4* ws = pf_smem;                                       // [E] (wx, wx, wy, wy)
+  int* mrow = reinterpret_cast<int*>(ws + E);                 // [S] row word offset or -1
+  int* go = mrow + S;                                         // [G + 1]
+  uint32_t* xs = reinterpret_cast<uint32_t*>(go + G + 1);    // [E][R]
+
+  const int tile = blockIdx.x, k = blockIdx.y, pol = blockIdx.z;
+  const int tid = threadIdx.x, fp = tid;
+  const long long f0 = (long long)tile * PF_FT;
+  const int nvalid = (int)min((long long)PF_FT, F - f0);
+  for (int s = tid; s < S; s += PF_NTH) mrow[s] = -1;
+  for (int g = tid; g <= G; g += PF_NTH) go[g] = goff[g];
+  for (int e = tid; e < E; e += PF_NTH) {
+    const float2 w = w1[(long long)k * E + e];
+    ws[e] = make_float4(w.x, w.x, w.y, w.y);
+  }
+  __syncthreads();
+  for (int e = tid; e < E; e += PF_NTH) mrow[member[e]] = e * R;
+  __syncthreads();
+
+  // Staging: frame pair p = 2 frames = 2 nq chunks of 16 bytes (frame a's nq,
+  // then frame b's; chunk c holds stations 8c .. 8c + 7).  A lane takes chunk
+  // slot cl of pair pl of its warp's PPW pairs, i.e. chunks c = cl, cl + CW,
+  // ... of frames a and b: one load request covers PPW runs of 16 CW bytes,
+  // and its samples go to the member rows as one word per station holding
+  // (a.re, a.im, b.re, b.im).  Frames past the block end read as zero and are
+  // never written.
+  const int nq = S >> 3;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int pl = lane / CW, cl = lane % CW;
+  const uint4* xt = reinterpret_cast<const uint4*>(x + 2 * (((long long)pol * K + k) * F + f0) * S);
+  const uint32_t m = 0x80808080u;                             // bytes offset by 128
+#pragma unroll 2
+  for (int pass = 0; pass < CW; ++pass) {
+    const int p = warp * PPW + pl + pass * 4 * PPW;
+    const bool va = 2 * p < nvalid, vb = 2 * p + 1 < nvalid;
+    const uint4* xp = xt + (long long)p * 2 * nq;
+    for (int c0 = cl; c0 < nq; c0 += 2 * CW) {
+      uint4 a[2], b[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = c0 + u * CW;
+        a[u] = make_uint4(0u, 0u, 0u, 0u);
+        b[u] = a[u];
+        if (c < nq) {
+          if (va) a[u] = __ldg(xp + c);
+          if (vb) b[u] = __ldg(xp + nq + c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = c0 + u * CW;
+        if (c >= nq) break;
+        const int4 r0 = *reinterpret_cast<const int4*>(mrow + 8 * c);
+        const int4 r1 = *reinterpret_cast<const int4*>(mrow + 8 * c + 4);
+        pf_put(xs, r0.x, p, __byte_perm(a[u].x, b[u].x, 0x5410) ^ m);
+        pf_put(xs, r0.y, p, __byte_perm(a[u].x, b[u].x, 0x7632) ^ m);
+        pf_put(xs, r0.z, p, __byte_perm(a[u].y, b[u].y, 0x5410) ^ m);
+        pf_put(xs, r0.w, p, __byte_perm(a[u].y, b[u].y, 0x7632) ^ m);
+        pf_put(xs, r1.x, p, __byte_perm(a[u].z, b[u].z, 0x5410) ^ m);
+        pf_put(xs, r1.y, p, __byte_perm(a[u].z, b[u].z, 0x7632) ^ m);
+        pf_put(xs, r1.z, p, __byte_perm(a[u].w, b[u].w, 0x5410) ^ m);
+        pf_put(xs, r1.w, p, __byte_perm(a[u].w, b[u].w, 0x7632) ^ m);
+      }
+    }
+  }
+  __syncthreads();
+  const bool va = 2 * fp < nvalid, vb = 2 * fp + 1 < nvalid;
+
+  // an unsigned byte u lands in the low mantissa bits of 2^23: the float is
+  // 2^23 + u, and 2^23 + 128 + q = 2^23 + u recovers the sample q exactly
+  const float2 boff = make_float2(-(8388608.0f + 128.0f), -(8388608.0f + 128.0f));
+  const float2 sc = make_float2(scale, scale);
+  const float2 rnd = make_float2(12582912.0f, 12582912.0f);   // 1.5 * 2^23
+  uint32_t ca[G], cb[G];                                      // codes of frames a, b
+  int sat = 0;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    // re = sum wx A - sum wy B, im = sum wx B + sum wy A over the members,
+    // A = (re of a, re of b), B = (im of a, im of b)
+    float2 r1 = make_float2(0.f, 0.f), r2 = r1, im = r1;
+    const int e1 = go[g + 1];
+#pragma unroll 2
+    for (int e = go[g]; e < e1; ++e) {
+      const float4 w = ws[e];                                 // broadcast
+      const uint32_t u = xs[e * R + fp];
+      const float2 A = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7650)),
+                                              __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7652))),
+                                  boff);
+      const float2 B = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7651)),
+                                              __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7653))),
+                                  boff);
+      const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
+      r1 = __ffma2_rn(wx, A, r1);
+      r2 = __ffma2_rn(wy, B, r2);
+      im = __ffma2_rn(wx, B, im);
+      im = __ffma2_rn(wy, A, im);
+    }
+    float2 vr = __fmul2_rn(__fadd2_rn(r1, make_float2(-r2.x, -r2.y)), sc);
+    float2 vi = __fmul2_rn(im, sc);
+    const float mx = fmaxf(fmaxf(fabsf(vr.x), fabsf(vr.y)), fmaxf(fabsf(vi.x), fabsf(vi.y)));
+    if (mx >= 32767.5f) {
+      // saturation (rare): count the codes of valid frames, clamp all four
+      sat += va ? (fabsf(vr.x) >= 32767.5f) + (fabsf(vi.x) >= 32767.5f) : 0;
+      sat += vb ? (fabsf(vr.y) >= 32767.5f) + (fabsf(vi.y) >= 32767.5f) : 0;
+      vr = make_float2(fminf(fmaxf(vr.x, -32767.f), 32767.f), fminf(fmaxf(vr.y, -32767.f), 32767.f));
+      vi = make_float2(fminf(fmaxf(vi.x, -32767.f), 32767.f), fminf(fmaxf(vi.y, -32767.f), 32767.f));
+    }
+    // |v| <= 32767: v + 1.5 * 2^23 rounds v to an integer (half to even) whose
+    // two's-complement low 16 bits are the float's low 16 bits
+    const float2 qr = __fadd2_rn(vr, rnd), qi = __fadd2_rn(vi, rnd);
+    ca[g] = __byte_perm(__float_as_uint(qr.x), __float_as_uint(qi.x), 0x5410);
+    cb[g] = __byte_perm(__float_as_uint(qr.y), __float_as_uint(qi.y), 0x5410);
+  }
+  const int wsat = __reduce_add_sync(0xffffffffu, sat);
+  if ((threadIdx.x & 31) == 0 && wsat) atomicAdd(n_sat, (unsigned long long)wsat);
+  // [frame][group] codes: frames a and b are 2 G contiguous words (16-byte aligned)
+  uint4* yo = reinterpret_cast<uint4*>(y + (((long long)pol * K + k) * F + f0 + 2 * fp) * G);
+  if (va) {
+#pragma unroll
+    for (int i = 0; i < G / 4; ++i) yo[i] = make_uint4(ca[4 * i], ca[4 * i + 1], ca[4 * i + 2], ca[4 * i + 3]);
+  }
+  if (vb) {
+#pragma unroll
+    for (int i = 0; i < G / 4; ++i)
+      yo[G / 4 + i] = make_uint4(cb[4 * i], cb[4 * i + 1], cb[4 * i + 2], cb[4 * i + 3]);
+  }
+}
+
 // w1[k][e] = exp(-2 pi i nu_k ((r_s - r_g) . s_g) / c): the argument in FP64
 // cycles, reduced to [-1/2, 1/2] before the FP32 sincospif
 __global__ void k_prebeam_weights(const double* __restrict__ rel, const double* __restrict__ dir,
@@ -241,6 +403,26 @@ size_t prebeam_smem(const lp_prebeam& pb) {
   const size_t t2 = pb.input_dtype == LP_INPUT_INT8 ? sizeof(char2) : sizeof(short2);
   return sizeof(float4) * pb.E + t2 * (size_t)pb.S * PB_FTP +
          sizeof(short2) * (size_t)pb.G * PB_YP + sizeof(int) * (size_t)(pb.G + 1);
+}
+
+size_t prebeam_pairs_smem(const lp_prebeam& pb) {
+  return sizeof(float4) * pb.E + sizeof(int) * ((size_t)pb.S + pb.G + 1) +
+         sizeof(uint32_t) * (size_t)pb.E * pf_row<2>();
+}
+
+// The frame-pair kernel's shape conditions (the 16-byte alignment of the
+// input and output pointers is checked per call).
+bool prebeam_pairs_shape(const lp_prebeam& pb) {
+  return pb.input_dtype == LP_INPUT_INT8 && pb.S % 8 == 0 && pb.S >= 16 &&
+         (pb.G == 4 || pb.G == 8 || pb.G == 16) && prebeam_pairs_smem(pb) <= 227 * 1024;
+}
+
+const void* prebeam_pairs_kernel(int G, int S) {
+  if (S >= 32)
+    return G == 4 ? (const void*)k_prebeam_pairs<4, 4>
+                  : G == 8 ? (const void*)k_prebeam_pairs<8, 4> : (const void*)k_prebeam_pairs<16, 4>;
+  return G == 4 ? (const void*)k_prebeam_pairs<4, 2>
+                : G == 8 ? (const void*)k_prebeam_pairs<8, 2> : (const void*)k_prebeam_pairs<16, 2>;
 }
 
 lp_status pb_fail(lp_prebeam* pb, lp_status st, const char* fmt, ...) {
@@ -429,6 +611,8 @@ lp_status lp_prebeam_set_groups(lp_prebeam* pb, const int32_t* group_of_station,
     PB_CUDA(pb, raise_smem_limit((const void*)k_prebeam<char2>, (size_t)smem));
   else
     PB_CUDA(pb, raise_smem_limit((const void*)k_prebeam<short2>, (size_t)smem));
+  if (prebeam_pairs_shape(*pb))
+    PB_CUDA(pb, raise_smem_limit(prebeam_pairs_kernel(G, S), prebeam_pairs_smem(*pb)));
   pb->centres = centres;
   pb->last_stream = s;
   pb->groups_set = true;
@@ -461,7 +645,17 @@ lp_status lp_prebeam_run(lp_prebeam* pb, const void* x, void* y, float scale, vo
   // 16-byte chunk reads when every (pol, subband) slab starts 16-byte aligned
   // (tiles then do too: 256 frames of S samples of 2 or 4 bytes)
   const int vec = reinterpret_cast<uintptr_t>(x) % 16 == 0 && (pb->F * pb->S * t2) % 16 == 0;
-  if (pb->input_dtype == LP_INPUT_INT8)
+  if (vec && reinterpret_cast<uintptr_t>(y) % 16 == 0 && prebeam_pairs_shape(*pb)) {
+    const dim3 pgrid((unsigned)((pb->F + PF_FT - 1) / PF_FT), pb->K, pb->P);
+    const size_t psmem = prebeam_pairs_smem(*pb);
+    const int8_t* x8 = static_cast<const int8_t*>(x);
+    short2* y2 = static_cast<short2*>(y);
+    const void* kern = prebeam_pairs_kernel(pb->G, pb->S);
+    void* args[] = {(void*)&x8, (void*)&pb->w1, (void*)&pb->member, (void*)&pb->goff,
+                    (void*)&pb->S, (void*)&pb->K, (void*)&pb->E, (void*)&pb->F,
+                    (void*)&scale, (void*)&y2, (void*)&pb->n_sat};
+    PB_CUDA(pb, cudaLaunchKernel(kern, pgrid, dim3(PF_NTH), args, psmem, s));
+  } else if (pb->input_dtype == LP_INPUT_INT8)
     k_prebeam<char2><<<grid, PB_NTH, smem, s>>>(static_cast<const char2*>(x), pb->w1, pb->member,
                                                 pb->goff, pb->S, pb->K, pb->G, pb->E, pb->F,
                                                 scale, vec, static_cast<short2*>(y), pb->n_sat);

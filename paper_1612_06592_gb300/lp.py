@@ -335,7 +335,7 @@ class Plan:
     MAX_GEMM_CONFIGS = 8
 
     def lp_plan_gemm_configs(self):
-        """Beamformer configurations: [(int8 stages, FP16 stages)] for the FP16
+        """Beamformer configurations: [(input stages, FP16 stages)] for the FP16
         form, [(beams per pass, 0)] for the FP32 form."""
         desc = np.zeros(2 * self.MAX_GEMM_CONFIGS, dtype=np.int32)
         n = _lib.lp_plan_gemm_configs(self._h, desc.ctypes.data, self.MAX_GEMM_CONFIGS)
@@ -397,7 +397,8 @@ class Group:
             raise LPError(st, "lp_group_create: the plans cannot form a group")
 
     def lp_group_process_block(self, x, subbands, first_bin, stream=None):
-        """x: device block [P, subbands, F, S, 2] int8 (bins first_bin ...)."""
+        """x: device block [P, subbands, F, S, 2] int8 or int16, the plans' type
+        (bins first_bin ...)."""
         st = _lib.lp_group_process_block(self._h, _ptr(x), int(subbands), int(first_bin),
                                           _stream_ptr(stream))
         if st != LP_OK:

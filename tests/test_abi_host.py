@@ -74,9 +74,9 @@ def test_configure_validates_and_sizes_workspace(lib):
     bad = lib.config_default()
     bad.first_bin = 154
     bad.precision = lib.LP_PREC_FP16
-    bad.input_dtype = lib.LP_INPUT_INT16     # FP16 form takes int8 only
+    bad.input_dtype = lib.LP_INPUT_INT16     # FP16 form: a multiple of 4 stations (6 is not)
     assert lib._lib.lp_plan_configure(h, ctypes.byref(bad)) == lib.LP_ERR_ARG
-    assert b"int8" in lib._lib.lp_last_error(h)
+    assert b"multiple of 4" in lib._lib.lp_last_error(h)
     bad = lib.config_default()
     bad.first_bin = 154
     bad.taps = 8

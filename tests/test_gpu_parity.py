@@ -47,20 +47,23 @@ def test_fp32_path_matches_oracle(cuda_lib, case):
 
 
 FP16_CASES = [
-    # S, P, K, B, Tr, F, first_bin, nblocks: int8 input, tensor-core beamformer
-    (4, 2, 8, 3, 1, 256, 200, 2),
-    (48, 2, 12, 50, 1, 600, 100, 2),              # 50 beams, ragged 256-frame tile
-    (8, 1, 5, 70, 2, 2104, 300, 1),               # two beam tiles, two 2048-frame chunks
-    (64, 2, 3, 64, 1, 72, 12, 1),                 # 64 stations (K = 128), exactly one tile
-    (12, 1, 2, 1, 3, 40, 450, 2),                 # one beam, three trials, tiny block
+    # S, P, K, B, Tr, F, first_bin, nblocks, dtype: tensor-core beamformer
+    (4, 2, 8, 3, 1, 256, 200, 2, "int8"),
+    (48, 2, 12, 50, 1, 600, 100, 2, "int8"),      # 50 beams, ragged 256-frame tile
+    (8, 1, 5, 70, 2, 2104, 300, 1, "int8"),       # two beam tiles, two 2048-frame chunks
+    (64, 2, 3, 64, 1, 72, 12, 1, "int8"),         # 64 stations (K = 128), exactly one tile
+    (12, 1, 2, 1, 3, 40, 450, 2, "int8"),         # one beam, three trials, tiny block
+    (8, 2, 10, 50, 1, 600, 150, 2, "int16"),      # int16 (full range): two B images
+    (36, 1, 4, 70, 2, 2104, 300, 1, "int16"),     # int16, two beam tiles, K = 72 (padded 80)
 ]
 
 
-@pytest.mark.parametrize("case", FP16_CASES, ids=lambda c: "S%d_P%d_K%d_B%d_T%d_F%d_b%d_x%d" % c)
+@pytest.mark.parametrize("case", FP16_CASES, ids=lambda c: "S%d_P%d_K%d_B%d_T%d_F%d_b%d_x%d_%s" % c)
 def test_fp16_tensor_core_path_matches_oracle(cuda_lib, case):
-    S, P, K, B, Tr, F, fb, nb = case
-    blocks, enu, dirs, tec = random_case(31, S, P, K, B, Tr, F, fb, "int8", nb, amp=127)
-    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision="fp16",
+    S, P, K, B, Tr, F, fb, nb, dtype = case
+    amp = 127 if dtype == "int8" else 32767
+    blocks, enu, dirs, tec = random_case(31, S, P, K, B, Tr, F, fb, dtype, nb, amp=amp)
+    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, dtype, precision="fp16",
                      store_timeseries=True, frames_per_cta=64 if F >= 64 else 8, k_sigma=4.0)
     g = gpu_blocks(cuda_lib, plan, blocks, enu, dirs, tec)
     _, o = oracle_blocks(S, P, K, B, Tr, F, fb, blocks, enu, dirs, tec, k_sigma=4.0)

@@ -47,13 +47,16 @@ def _check_codes(got, want, v, window):
     return np.count_nonzero(diff)
 
 
-@pytest.mark.parametrize("dtype,amp,scale,S", [("int8", 128, 2.0, 20), ("int16", 3000, 4.0, 20),
-                                                ("int8", 128, 2.0, 21)])
-def test_prebeam_matches_oracle(cuda_lib, dtype, amp, scale, S):
-    """20 stations: 16-byte chunk reads; 21 (int8): slabs not 16-byte aligned,
-    sample-by-sample reads."""
+@pytest.mark.parametrize("dtype,amp,scale,S,G,F", [
+    ("int8", 128, 2.0, 20, 5, 700), ("int16", 3000, 4.0, 20, 5, 700), ("int8", 128, 2.0, 21, 5, 700),
+    ("int8", 128, 2.0, 24, 8, 701), ("int8", 128, 64.0, 16, 4, 700), ("int8", 128, 2.0, 48, 16, 512)])
+def test_prebeam_matches_oracle(cuda_lib, dtype, amp, scale, S, G, F):
+    """20 stations, 5 groups: 16-byte chunk reads; 21 (int8): slabs not 16-byte
+    aligned, sample-by-sample reads.  int8 with S a multiple of 8 and 4, 8 or 16
+    groups: the frame-pair kernel (701 frames: a last pair with one frame;
+    scale 64: saturating codes)."""
     import torch
-    P, K, F, G, fb = 2, 6, 700, 5, 130                 # 700 frames: two tiles + a ragged one
+    P, K, fb = 2, 6, 130                               # 700 frames: two tiles + a ragged one
     rng = np.random.default_rng(61)
     info = np.iinfo(dtype)
     x = rng.integers(max(info.min, -amp), min(info.max, amp) + 1,
@@ -77,17 +80,18 @@ def test_prebeam_matches_oracle(cuda_lib, dtype, amp, scale, S):
     sat_oracle = int(np.count_nonzero(np.abs(np.rint(v)) > O.INT16_MAX))
     near_edge = int(np.count_nonzero(np.abs(np.abs(v) - (O.INT16_MAX + 0.5)) < window))
     assert abs(n_sat - sat_oracle) <= near_edge
-    if dtype == "int16":
+    if dtype == "int16" or scale > 8:
         assert sat_oracle > 0                          # the case does saturate
     assert pb.lp_prebeam_saturated() == 0              # the count resets
 
 
-def test_two_stage_chain_matches_oracle(cuda_lib):
+@pytest.mark.parametrize("G", [6, 8])
+def test_two_stage_chain_matches_oracle(cuda_lib, G):
     """Station block -> preliminary beams (GPU) -> final beams, synthesis and
     triggers (GPU, stations = groups at their centres), against the oracle
-    doing the same two stages in FP64."""
+    doing the same two stages in FP64 (8 groups: the frame-pair stage 1)."""
     import torch
-    S, P, K, F, G, fb = 24, 2, 10, 1024, 6, 200
+    S, P, K, F, fb = 24, 2, 10, 1024, 200
     B, Tr, scale, nblocks = 3, 2, 4.0, 2
     rng = np.random.default_rng(63)
     blocks = [rng.integers(-20, 21, size=(P, K, F, S, 2)).astype(np.int8) for _ in range(nblocks)]
@@ -122,3 +126,34 @@ def test_two_stage_chain_matches_oracle(cuda_lib):
         assert rel_rms(g_["y"], o_["y"]) < TOL_TS_FP32 + 3 * tie
         n_g, n_o, n_diff, bad = compare_triggers(g_["trig"], o_, P, Tr, TAU_FP32)
         assert n_o > 0 and not bad
+
+
+def test_prebeam_full_size_sampled(cuda_lib):
+    """The benchmarked stage-1 launch (48 stations in 8 groups, 488 subbands,
+    a whole 65536-frame block, int8; the frame-pair kernel): every subband and
+    group at three sampled frame windows (start, middle, end) against the
+    oracle, code for code; the noise block cannot saturate at scale 4."""
+    import torch
+    w = synth.PRECISION
+    G, scale = 8, 4.0
+    enu, _, _ = synth.make_geometry(w)
+    x = np.empty((w.pols, w.subbands, w.block_len, w.stations, 2), dtype=w.dtype)
+    for pol in range(w.pols):
+        for k in range(w.subbands):
+            x[pol, k] = synth.noise_slab(w.seed, 0, pol, k, w.block_len, w.stations,
+                                         w.noise_sigma, w.dtype)
+    grp = synth.station_groups(enu, G)
+    gdir = np.tile(synth.pointing_enu(), (G, 1))
+    pb = cuda_lib.Prebeam(w.stations, w.pols, w.subbands, w.block_len, G,
+                          first_bin=w.first_bin, input_dtype=w.dtype)
+    pb.lp_prebeam_set_groups(grp, enu, gdir)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty((w.pols, w.subbands, w.block_len, G, 2), dtype=torch.int16, device="cuda")
+    pb.lp_prebeam_run(xd, yd, scale)
+    del xd
+    assert pb.lp_prebeam_saturated() == 0
+    F = w.block_len
+    for (m0, m1) in [(0, 64), (31000, 31064), (F - 64, F)]:
+        got = yd[:, :, m0:m1].cpu().numpy()
+        want, v, window = _oracle_codes(x[:, :, m0:m1], enu, grp, gdir, w.first_bin, scale)
+        _check_codes(got, want, v, window)
