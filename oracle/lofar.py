@@ -34,6 +34,8 @@ __all__ = [
     "INT16_MAX", "group_centres", "prebeam_weights", "prebeam", "transport_int16",
     "FINE_TAPS", "FINE_DELAY", "FINE_BETA", "FINE_GRID", "fine_dedispersion_taps",
     "fine_dedisperse", "fullrate_dedisperse",
+    "FULLRATE_TAPS", "FULLRATE_DELAY", "FULLRATE_FLAT", "FULLRATE_GRID", "fullrate_max_delay",
+    "fullrate_taps", "fullrate_filter",
 ]
 
 # Sec. 2: antennas are sampled every 5 ns  ->  fs = 200 MHz.
@@ -231,6 +233,76 @@ def fullrate_dedisperse(u: np.ndarray, tec_tecu: float, nu_ref_hz: float) -> np.
     pos = f >= 0
     phi[pos] = dedispersion_cycles(NU0_HZ + f[pos] * FS_HZ, [tec_tecu], nu_ref_hz)[:, 0]
     return np.fft.ifft(np.fft.fft(u) * np.exp(-2j * np.pi * phi))
+
+
+# Full-rate de-dispersion as a streaming filter (Sec. 3, third paragraph, on a
+# continuous stream).  Readings (the paper gives only "FFT, multiply, inverse
+# FFT" of the time series):
+#   * it follows the inversion, on the 200 MHz analytic series, and carries the
+#     whole STEC phase (no per-subband phase is applied before the inversion);
+#   * the whole-series transform becomes a linear filter of FULLRATE_TAPS taps:
+#     the response of ``fullrate_dedisperse`` (exp(-2 pi i phi(nu)) for f >= 0,
+#     1 for f < 0) sampled on FULLRATE_GRID frequencies and inverted, taken over
+#     the delays -FULLRATE_DELAY .. FULLRATE_TAPS - 1 - FULLRATE_DELAY, times a
+#     Tukey window (1 within FULLRATE_FLAT / 2 of zero delay, a half-cosine
+#     down to 0 at the ends), then delayed by FULLRATE_DELAY samples so that it
+#     is causal: a pulse appears FULLRATE_DELAY samples (one frame) later;
+#   * the series is filtered continuously across blocks (the last
+#     FULLRATE_TAPS - 1 samples of a block are the next block's history; zero
+#     before the stream start);
+#   * the noise level and threshold are the unfiltered series' (the response
+#     has unit modulus).
+# The window holds the response's group delays when they lie within
+# FULLRATE_FLAT / 2 of zero delay over the whole 100-200 MHz band (checked by
+# ``fullrate_max_delay``).
+
+FULLRATE_TAPS = 2048
+FULLRATE_DELAY = 1024
+FULLRATE_FLAT = 1536
+FULLRATE_GRID = 8192
+
+
+def fullrate_max_delay(tec_tecu, nu_ref_hz: float) -> np.ndarray:
+    """Largest |group delay| of the full-rate response over 100-200 MHz, in
+    samples, [Tr]: A |1/nu^2 - 1/nu_ref^2| fs at the band ends (the delay
+    A (1/nu^2 - 1/nu_ref^2) is monotonic in nu)."""
+    a = dispersion_coefficient_hz(tec_tecu)
+    ends = np.array([NU0_HZ, FS_HZ])
+    d = np.abs(a[:, None] * (1.0 / ends[None, :] ** 2 - 1.0 / nu_ref_hz ** 2)) * FS_HZ
+    return d.max(axis=1)
+
+
+def fullrate_taps(tec_tecu, nu_ref_hz: float, taps: int = FULLRATE_TAPS,
+                  delay: int = FULLRATE_DELAY, flat: int = FULLRATE_FLAT,
+                  grid: int = FULLRATE_GRID) -> np.ndarray:
+    """Causal taps h[t, l], complex [Tr, taps] (readings above):
+    h[l] = w(l - delay) (1/grid) sum_j H_j exp(+2 pi i j (l - delay) / grid),
+    H_j = exp(-2 pi i phi(fs/2 + f_j fs)) for f_j = j / grid < 1/2, else 1, and
+    w(d) = 1 for |d| <= flat/2, (1 + cos(pi (|d| - flat/2) / ((taps - flat)/2))) / 2
+    beyond.  The inverse transform is this module's own FFT."""
+    tec = np.atleast_1d(np.asarray(tec_tecu, dtype=np.float64))
+    j = np.arange(grid)
+    pos = j < grid // 2
+    d = np.arange(taps) - delay
+    half, ramp = flat / 2.0, (taps - flat) / 2.0
+    win = np.where(np.abs(d) <= half, 1.0,
+                   0.5 * (1.0 + np.cos(np.pi * np.clip(np.abs(d) - half, 0.0, ramp) / ramp)))
+    out = np.zeros((tec.size, taps), dtype=np.complex128)
+    for t in range(tec.size):
+        phi = np.zeros(grid)
+        phi[pos] = dedispersion_cycles(NU0_HZ + (j[pos] / grid) * FS_HZ, tec[t:t + 1],
+                                       nu_ref_hz)[:, 0]
+        h = fft_radix2(np.exp(-2j * np.pi * phi), +1) / grid     # h[n], n mod grid
+        out[t] = win * h[d % grid]
+    return out
+
+
+def fullrate_filter(u_ext: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """One stream's full-rate filter: u_ext complex [taps - 1 + n], the stream's
+    series with the taps - 1 samples before the block first; h complex [taps].
+    Returns v [n], v[o] = sum_l h[l] u_ext[taps - 1 + o - l] (a library
+    convolution as the step)."""
+    return np.convolve(np.asarray(u_ext, dtype=np.complex128), h, mode="valid")
 
 
 # --------------------------------------------------------------------------
@@ -647,10 +719,12 @@ class Pipeline:
     beta: float = 9.0
     keep_timeseries: bool = True
     fine_dedispersion: bool = False
+    fullrate_dedispersion: bool = False
     # state
     block_index: int = 0
     history: np.ndarray | None = field(default=None, repr=False)
     fine_history: np.ndarray | None = field(default=None, repr=False)
+    fullrate_history: np.ndarray | None = field(default=None, repr=False)
     sigma2: np.ndarray | None = None
 
     def __post_init__(self):
@@ -662,6 +736,11 @@ class Pipeline:
         self.g = synthesis_filter(M, TAPS, self.beta)
         J = self.beams * self.tec_trials * self.pols
         self.history = np.zeros((J, TAPS - 1, self.subbands), dtype=np.complex128)
+        if self.fullrate_dedispersion:
+            # the whole STEC phase is applied at full rate, none per subband
+            self.d = np.ones_like(self.d)
+            self.fullrate_h = fullrate_taps(np.asarray(self.tec), self.nu_ref_hz)
+            self.fullrate_history = np.zeros((J, FULLRATE_TAPS - 1), dtype=np.complex128)
         if self.fine_dedispersion:
             self.fine_taps = fine_dedispersion_taps(self.nu, np.asarray(self.tec), self.nu_ref_hz)
             self.fine_history = np.zeros((J, FINE_TAPS - 1, self.subbands), dtype=np.complex128)
@@ -678,6 +757,8 @@ class Pipeline:
 
         Returns dict with beams [J, F, K] (after the fine de-dispersion filter
         when it is on), sigma [J], theta [J], n_first,
+        (full-rate mode: y, env and the triggers are those of the filtered
+        series v; u is the synthesis output before the filter)
         y/env [J, F*M] (if keep_timeseries) and triggers: list of
         (n, beam, tec, pol, env, sigma) sorted by (beam, tec, pol, n).
         """
@@ -708,6 +789,11 @@ class Pipeline:
         for j in range(J):
             ext = np.concatenate([self.history[j], frames[j]], axis=0)
             u = ippf(ext, self.first_bin, self.g).reshape(F * M)
+            if self.fullrate_dedispersion:
+                t = (j // self.pols) % self.tec_trials
+                uext = np.concatenate([self.fullrate_history[j], u])
+                self.fullrate_history[j] = uext[-(FULLRATE_TAPS - 1):]
+                u = fullrate_filter(uext, self.fullrate_h[t])
             env = np.abs(u)
             if self.keep_timeseries:
                 y[j] = u.real

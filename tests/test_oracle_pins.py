@@ -475,6 +475,168 @@ def test_fullrate_dedispersion_undoes_the_dispersion_up_to_the_reference_delay()
     np.testing.assert_allclose(O.fullrate_dedisperse(x, 0.0, nu_ref), x, atol=1e-15)
 
 
+def test_fullrate_taps_at_zero_tec_are_a_pure_delay():
+    """STEC 0: the response is 1 everywhere, its inverse transform the unit
+    impulse at zero delay, so the causal taps are exactly the impulse at
+    FULLRATE_DELAY (the window is 1 there)."""
+    h = O.fullrate_taps([0.0], 150e6)[0]
+    want = np.zeros(O.FULLRATE_TAPS, dtype=complex)
+    want[O.FULLRATE_DELAY] = 1.0
+    np.testing.assert_allclose(h, want, rtol=0, atol=1e-15)
+
+
+def _band_series(N, lo_bin, hi_bin, seed):
+    """A complex series with a random spectrum on filter-bank bins
+    [lo_bin, hi_bin) of 1024 (frequencies lo_bin/1024 .. hi_bin/1024 of fs)."""
+    f = np.fft.fftfreq(N)
+    band = (f >= lo_bin / O.M) & (f < hi_bin / O.M)
+    rng = np.random.default_rng(seed)
+    return np.fft.ifft(np.where(band, rng.normal(size=N) + 1j * rng.normal(size=N), 0)), f, band
+
+
+@pytest.mark.parametrize("tec", [10.0, 40.0, 50.0])
+def test_fullrate_filter_equals_the_whole_series_transform(tec):
+    """On a periodic band-limited series, the causal filter equals the paper's
+    whole-series transform delayed by FULLRATE_DELAY, apart from the truncation
+    to FULLRATE_TAPS taps: within 1e-4 rel. RMS over the full band (bins
+    12-500, the error coming from the response's jumps at 100 and 200 MHz)
+    while the delays stay within the window's flat part, and within 2e-6 for a
+    band away from those ends."""
+    L = O.FULLRATE_TAPS
+    for (lo, hi), bound in (((12, 500), 1e-4), ((60, 252), 2e-6)):
+        u, f, band = _band_series(1 << 14, lo, hi, 31)
+        nu_ref = O.NU0_HZ + 0.5 * (lo + hi) / O.M * O.FS_HZ
+        assert O.fullrate_max_delay([tec], nu_ref)[0] <= O.FULLRATE_FLAT / 2
+        v = O.fullrate_filter(np.concatenate([u[-(L - 1):], u]), O.fullrate_taps([tec], nu_ref)[0])
+        want = np.roll(O.fullrate_dedisperse(u, tec, nu_ref), O.FULLRATE_DELAY)
+        assert rel(v, want) < bound
+
+
+def rel(a, b):
+    return float(np.sqrt(np.mean(np.abs(a - b) ** 2) / np.mean(np.abs(b) ** 2)))
+
+
+def test_fullrate_filter_undoes_a_dispersed_pulse():
+    """A pulse with a smooth spectrum (Gaussian about fs/4, so compact in time
+    and far from the series ends) dispersed by exp(+2 pi i A / nu) and filtered
+    with zero history comes back as the undispersed pulse delayed by
+    A / nu_ref^2 + FULLRATE_DELAY samples with a constant phase (closed form as
+    for the whole-series transform), to the truncation's 1e-4, and keeps its
+    peak."""
+    N, tec, nu_ref = 1 << 14, 35.0, 150e6
+    f = np.fft.fftfreq(N)
+    band = (f > 0) & (f < 0.5)
+    n0 = 3000
+    spec = np.where(band, np.exp(-((f - 0.25) / 0.08) ** 2 - 2j * np.pi * f * n0), 0)
+    a = O.dispersion_coefficient_hz(tec)
+    nu = np.where(band, O.NU0_HZ + f * O.FS_HZ, O.NU0_HZ)
+    disp = np.fft.ifft(spec * np.exp(np.where(band, 2j * np.pi * a / nu, 0)))
+    v = O.fullrate_filter(np.concatenate([np.zeros(O.FULLRATE_TAPS - 1), disp]),
+                          O.fullrate_taps([tec], nu_ref)[0])
+    delay = a / nu_ref ** 2 * O.FS_HZ + O.FULLRATE_DELAY
+    const = a * (2 / nu_ref - O.NU0_HZ / nu_ref ** 2)
+    want = np.fft.ifft(spec * np.exp(np.where(band, 2j * np.pi * (const - f * delay), 0)))
+    assert rel(v, want) < 1e-4
+    assert abs(np.abs(v).max() / np.abs(want).max() - 1) < 1e-4
+    assert abs(int(np.argmax(np.abs(v))) - (n0 + delay)) <= 1
+    assert np.abs(disp).max() < 0.3 * np.abs(want).max()     # the dispersion did spread it
+
+
+def test_fullrate_filter_is_continuous_across_blocks():
+    """Filtering a series in two blocks, the second with the last
+    FULLRATE_TAPS - 1 samples of the first as history, equals filtering it
+    whole; and the filter is the plain sum over taps (brute force on a short
+    stretch)."""
+    rng = np.random.default_rng(32)
+    u = rng.normal(size=6000) + 1j * rng.normal(size=6000)
+    h = O.fullrate_taps([22.0], 140e6)[0]
+    L = O.FULLRATE_TAPS
+    z = np.zeros(L - 1)
+    whole = O.fullrate_filter(np.concatenate([z, u]), h)
+    first = O.fullrate_filter(np.concatenate([z, u[:2500]]), h)
+    second = O.fullrate_filter(np.concatenate([np.concatenate([z, u[:2500]])[-(L - 1):],
+                                               u[2500:]]), h)
+    np.testing.assert_allclose(np.concatenate([first, second]), whole, rtol=0, atol=1e-12)
+    ext = np.concatenate([z, u])
+    for o in (0, 700, 5999):
+        acc = sum(h[l] * ext[L - 1 + o - l] for l in range(L))
+        assert abs(acc - whole[o]) < 1e-12
+
+
+def test_fullrate_max_delay_is_the_band_end_delay():
+    """The response's group delay -d phi / d nu = A (1/nu^2 - 1/nu_ref^2)
+    (seconds) at the band ends 100 and 200 MHz, by a numerical derivative of
+    the phase."""
+    tec, nu_ref = 40.0, 150e6
+    d = O.fullrate_max_delay([tec], nu_ref)[0]
+    want = 0.0
+    for nu in (O.NU0_HZ, O.FS_HZ):
+        dn = 1e3
+        slope = (O.dedispersion_cycles([nu + dn], [tec], nu_ref)[0, 0]
+                 - O.dedispersion_cycles([nu - dn], [tec], nu_ref)[0, 0]) / (2 * dn)
+        want = max(want, abs(slope) * O.FS_HZ)
+    assert abs(d - want) < 1e-3 * want
+
+
+def test_pipeline_fullrate_mode_at_zero_tec_is_the_plain_pipeline_delayed():
+    """At STEC 0 the full-rate taps are the unit impulse at one frame, so over
+    two blocks the full-rate pipeline's series is the plain one's 1024 samples
+    later, with the same noise levels."""
+    S, P, K, B, Tr, F, fb = 3, 1, 5, 1, 1, 24, 220
+    rng = np.random.default_rng(24)
+    x = rng.integers(-40, 41, size=(P, K, 2 * F, S, 2))
+    enu = synth.station_positions(S, 4)
+    dirs = synth.pointing_enu()[None]
+    tec = np.array([0.0])
+    plain = O.Pipeline(S, P, K, B, Tr, F, fb, enu, dirs, tec)
+    full = O.Pipeline(S, P, K, B, Tr, F, fb, enu, dirs, tec, fullrate_dedispersion=True)
+    yp, yf = [], []
+    for i in range(2):
+        blk = x[:, :, i * F:(i + 1) * F]
+        op, of = plain.process_block(blk), full.process_block(blk)
+        np.testing.assert_array_equal(op["sigma"], of["sigma"])
+        yp.append(op["y"][0])
+        yf.append(of["y"][0])
+    yp, yf = np.concatenate(yp), np.concatenate(yf)
+    d = O.FULLRATE_DELAY
+    np.testing.assert_allclose(yf[d:], yp[:-d], rtol=0, atol=1e-12 * np.abs(yp).max())
+    assert np.abs(yf[:d]).max() == 0.0
+
+
+def test_pipeline_fullrate_mode_equals_its_definition():
+    """Pipeline in full-rate mode: two blocks equal the per-stream definition
+    (beamform without the subband phase, synthesis, full-rate filter with zero
+    history) on the concatenated block, and the noise level is the plain one's."""
+    S, P, K, B, Tr, F, fb = 3, 2, 6, 2, 2, 40, 150
+    rng = np.random.default_rng(25)
+    x = rng.integers(-30, 31, size=(P, K, 2 * F, S, 2))
+    enu = synth.station_positions(S, 3)
+    dirs = synth.hex_beam_directions(B)
+    tec = np.array([8.0, 33.0])
+    pipe = O.Pipeline(S, P, K, B, Tr, F, fb, enu, dirs, tec, fullrate_dedispersion=True)
+    plain = O.Pipeline(S, P, K, B, Tr, F, fb, enu, dirs, tec)
+    outs = [pipe.process_block(x[:, :, i * F:(i + 1) * F]) for i in range(2)]
+    for i in range(2):
+        np.testing.assert_allclose(outs[i]["sigma"],
+                                   plain.process_block(x[:, :, i * F:(i + 1) * F])["sigma"],
+                                   rtol=1e-12)
+    nu = O.sky_frequencies(fb, K)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    w = O.geometric_weights(nu, enu, dirs)
+    h = O.fullrate_taps(tec, nu_ref)
+    g = O.synthesis_filter()
+    xc = x[..., 0] + 1j * x[..., 1]
+    bm = O.beamform(xc, w, np.ones((K, Tr)))                 # [B, Tr, P, K, 2F]
+    for b, t, p in ((0, 0, 0), (1, 1, 1), (1, 0, 1)):
+        j = (b * Tr + t) * P + p
+        u = O.ippf(np.concatenate([np.zeros((15, K)), bm[b, t, p].T]), fb, g).reshape(-1)
+        v = O.fullrate_filter(np.concatenate([np.zeros(O.FULLRATE_TAPS - 1), u]), h[t])
+        np.testing.assert_allclose(np.concatenate([outs[0]["y"][j], outs[1]["y"][j]]), v.real,
+                                   rtol=0, atol=1e-9 * np.abs(v).max())
+        np.testing.assert_allclose(np.concatenate([outs[0]["env"][j], outs[1]["env"][j]]),
+                                   np.abs(v), rtol=0, atol=1e-9 * np.abs(v).max())
+
+
 def test_pipeline_fine_mode_at_zero_tec_is_the_plain_pipeline_delayed():
     """At TEC 0 the fine filter is the unit impulse at 8 frames, so over two
     blocks (history carried) the fine pipeline's series is the plain one's,
