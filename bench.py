@@ -101,6 +101,9 @@ def parse():
     ap.add_argument("--fine", action="store_true",
                     help="fine (channel-domain) de-dispersion filter on (a separate line, "
                          "not the headline)")
+    ap.add_argument("--fullrate", action="store_true",
+                    help="full-rate de-dispersion of the synthesised series (2048-tap "
+                         "overlap-save filter; a separate line, not the headline)")
     ap.add_argument("--lsmr", action="store_true",
                     help="PPF inversion by windowed LSMR instead of the FIR synthesis (a "
                          "separate line, not the headline; no triggers on that path)")
@@ -261,10 +264,11 @@ def run_ours(args, rank, world, local_rank):
     # beam sharding: every rank holds the same block (its own copy on its own
     # GPU) and runs its beams; replicas: every rank its own block
     x = device_block(w, 1000 if sharded else 1000 + rank, dev)
-    e2e_stream = not args.no_e2e and not args.lsmr and not args.graph
+    e2e_stream = not args.no_e2e and not args.lsmr and not args.graph and not args.fullrate
     plan_kw = dict(input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
                    host_input=not args.no_e2e and not args.lsmr, stream_blocks=e2e_stream,
                    frames_per_cta=args.synth_frames, fine_dedisp=args.fine,
+                   fullrate_dedisp=args.fullrate,
                    inversion="lsmr" if args.lsmr else "fir", chunk_frames=args.chunk_frames,
                    use_graph=args.graph)
     if args.graph:
@@ -338,21 +342,23 @@ def run_ours(args, rank, world, local_rank):
 
         def read(block):
             # streaming host blocks: block `block`'s triggers are read while the
-            # next block's copy and kernels run
+            # next block's copy and kernels run (otherwise the last block's, after it)
+            t, n, _ = (plan.lp_get_triggers_block(block) if e2e_stream
+                       else plan.lp_get_triggers())
             if shard is not None:
                 # this rank's triggers relabelled to global beams, merged on rank 0
                 from paper_1612_06592_gb300.shard import gather_triggers, to_global
-                t, n, _ = plan.lp_get_triggers_block(block)
                 gather_triggers(to_global(t, shard.b0, shard.tec_trials, shard.pols))
-            else:
-                t, n, _ = plan.lp_get_triggers_block(block)
             return t
 
         for i in range(args.steps):
             plan.lp_process_block(xh)
-            if i:
+            if not e2e_stream:
+                d2h += 8 + 32 * len(read(plan.blocks - 1))
+            elif i:
                 d2h += 8 + 32 * len(read(plan.blocks - 2))
-        d2h += 8 + 32 * len(read(plan.blocks - 1))
+        if e2e_stream:
+            d2h += 8 + 32 * len(read(plan.blocks - 1))
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         barrier()
@@ -405,7 +411,8 @@ def run_ours(args, rank, world, local_rank):
         "samples_per_s": {"station_complex": w.pols * w.subbands * w.block_len * w.stations
                           * blocks_per_step / (ms_step / 1e3),
                           "output_200MHz": samples * blocks_per_step / (ms_step / 1e3)},
-        "stage_ms": {k: v / max(nrec, 1) for k, v in stages.items() if k != "fine" or args.fine},
+        "stage_ms": {k: v / max(nrec, 1) for k, v in stages.items()
+                     if (k != "fine" or args.fine) and (k != "fullrate" or args.fullrate)},
         "roofline": {"bound": "alu", "kernel": "k_ippf (inverse FFT + synthesis FIR + trigger)",
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
@@ -428,9 +435,12 @@ def run_ours(args, rank, world, local_rank):
         line["e2e"] = {"value": blocks_per_step * block_s / (t_e2e / args.steps), "unit": "x realtime",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": t_e2e / args.steps * 1e3,
-                       "path": "lp_process_block(pinned host block, streaming: the next "
-                               "block's host copy overlaps this block's kernels) + "
-                               "lp_get_triggers_block of the previous block each step",
+                       "path": ("lp_process_block(pinned host block, streaming: the next "
+                                "block's host copy overlaps this block's kernels) + "
+                                "lp_get_triggers_block of the previous block each step"
+                                if e2e_stream else
+                                "lp_process_block(pinned host block: copy per polarisation, "
+                                "then the kernels) + lp_get_triggers each step"),
                        "stage_ms": {k: v / max(n_e2e, 1) for k, v in e2e_stages.items()}}
     if args.fine:
         fine_ms = stages["fine"] / max(nrec, 1)
@@ -444,6 +454,24 @@ def run_ours(args, rank, world, local_rank):
                                  "frac": fine_bytes / (fine_ms / 1e3) / 1e9 / hbm_peak,
                                  "bytes": fine_bytes,
                                  "traffic": recorded_traffic("k_fine.cu")}
+    if args.fullrate:
+        fr_ms = stages["fullrate"] / max(nrec, 1)
+        # per 8192-point segment (6144 outputs): forward and inverse transforms
+        # (5 N log2 N each) and the product with the taps' spectrum (6 N)
+        fr_flop = (2 * 5 * 8192 * 13 + 6 * 8192) / 6144 * samples
+        fr_bytes = samples * 8 * 8192 / 6144               # series rows read (segments overlap)
+        line["metric"] += ", full-rate de-dispersion on"
+        line["config"]["workload"] += "-fullrate"
+        line["config"]["fullrate_dedispersion"] = ("2048-tap streaming filter of the synthesised "
+                                                   "series (8192-point overlap-save), whole STEC "
+                                                   "phase at full rate")
+        line["roofline_fullrate"] = {"bound": "alu", "kernel": "k_fullrate",
+                                     "achieved": fr_flop / (fr_ms / 1e3) / 1e12,
+                                     "peak": alu_peak, "unit": "TFLOP/s",
+                                     "frac": fr_flop / (fr_ms / 1e3) / 1e12 / alu_peak,
+                                     "flop_per_sample": fr_flop / samples,
+                                     "hbm_gbs": fr_bytes / (fr_ms / 1e3) / 1e9,
+                                     "traffic": recorded_traffic("k_fullrate.cu")}
     if args.lsmr:
         # per window and LSMR step: A v and A^T u (272 x 16 complex x real taps,
         # 4 FLOP each), two norms and two scalings of 287-element vectors, the

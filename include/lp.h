@@ -117,6 +117,20 @@ typedef struct {
                                been beamformed (not after all earlier work on the stream) and
                                overlaps this block's synthesis; lp_get_triggers_block reads
                                a block's triggers while the next block runs.  0: off */
+  int32_t fullrate_dedisp;  /* 1: de-disperse at full resolution after the inversion (Sec. 3,
+                               third paragraph: the STEC phase on the spectrum of the
+                               200 MHz series): the beamformer applies no per-subband
+                               phase, the synthesis keeps each stream's analytic series
+                               and a streaming filter of 2048 taps (the response sampled
+                               on 8192 frequencies and inverted, a Tukey window flat over
+                               the central 1536 taps, a delay of 1024 samples: pulses
+                               appear one frame later) applies the whole phase; the trigger
+                               and the stored time series are those of the filtered
+                               series, the noise level that of the synthesis.  lp_set_tec
+                               refuses STEC values whose group delays over 100-200 MHz
+                               leave 768 samples of the reference delay.  FIR inversion
+                               only; not with chunk_frames, fine_dedisp, stream_blocks or
+                               in a plan group.  0: off */
 } lp_config;
 
 enum { LP_INV_FIR = 0, LP_INV_LSMR = 1 };
@@ -303,7 +317,7 @@ int lp_launches_per_block(const lp_plan* plan);
  * recorded block into total_ms[LP_NUM_STAGES] (milliseconds), stores their
  * number in *blocks and forgets them. */
 enum { LP_STAGE_H2D = 0, LP_STAGE_BEAMFORM = 1, LP_STAGE_SIGMA = 2, LP_STAGE_SYNTH = 3,
-       LP_STAGE_SHIFT = 4, LP_STAGE_FINE = 5, LP_NUM_STAGES = 6 };
+       LP_STAGE_SHIFT = 4, LP_STAGE_FINE = 5, LP_STAGE_FULLRATE = 6, LP_NUM_STAGES = 7 };
 lp_status lp_profile_enable(lp_plan* plan, int enable);
 lp_status lp_profile_read(lp_plan* plan, double* total_ms, int64_t* blocks);
 

@@ -1,0 +1,414 @@
+// Full-rate de-dispersion of the synthesised 200 MHz series (Sec. 3, third
+// paragraph: the STEC phase applied to the spectrum of the time series at full
+// resolution), as a streaming filter after the inversion:
+//
+//     v[o] = sum_{l < 2048} h[l] u[o - l]       (u: a stream's analytic series)
+//
+// h: the response exp(-2 pi i phi(nu)) (nu = 100 MHz + f fs for f >= 0, 1 for
+// f < 0) sampled on 8192 frequencies and inverted, kept over the delays
+// -1024 .. 1023 with a Tukey window (flat within 768 of zero delay, half-cosine
+// tapers beyond) and delayed by 1024 samples, so pulses appear one frame later.
+// The whole STEC phase is applied here; the beamformer's per-subband phase is
+// then 1.
+//
+// k_fullrate, overlap-save: a stream's series row holds 2048 samples of the
+// previous block, then the block's F * 1024 samples.  Segment s covers row
+// samples [6144 s, 6144 s + 8192): one 8192-point FFT, the product with the
+// taps' spectrum, an inverse FFT; positions 2048 .. 8191 of the result are the
+// block's outputs 6144 s .. 6144 s + 6143 (no wrap-around reaches them).  The
+// envelope |v| is compared with the stream's threshold and triggers are
+// compacted by warp ballots, as in the synthesis kernel; Re v is the stored
+// time series.
+//
+// The FFT: decimation in frequency, radices 16 x 16 x 16 x 2, in place in
+// shared memory.  A thread owns 16 values per pass (a 16-point DFT in
+// registers by radix-2 stages with constant twiddles); positions are padded by
+// 2 per 32 so that the half-warps' 8-byte accesses of every pass fall on
+// distinct banks; the last radix-2 step pairs neighbouring lanes by shuffles.
+// The spectrum stays in digit-reversed order (position 512 k1 + 32 k2 + 2 k3
+// + k4 holds frequency k1 + 16 k2 + 256 k3 + 4096 k4): the taps' spectrum is
+// stored in the same order, per thread and value, and the inverse transform
+// runs the same network backwards (decimation in time, conjugate twiddles),
+// ending in natural order.  1/8192 is folded into the taps' spectrum.
+//
+// Set-up (per STEC set, FP64): the response on the 8192-point grid, the taps by
+// a direct inverse transform, the window, and the taps' spectrum by a direct
+// transform, rounded to FP32 once.
+#include "lp_internal.cuh"
+
+#include <cstdint>
+
+namespace lp {
+namespace {
+
+constexpr int FR_NT = 512;                  // threads per block, 16 values each
+constexpr int FR_N = kFrN;                  // 8192-point transforms
+constexpr int FR_V = kFrN - kFrTaps;        // 6144 outputs per segment
+static_assert(FR_N == 16 * FR_NT, "16 values per thread");
+
+// padded shared-memory position of transform position i
+__host__ __device__ constexpr int frp(int i) { return i + 2 * (i >> 5); }
+constexpr int FR_SMEM = (frp(FR_N - 1) + 1) * (int)sizeof(float2);
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+  return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 w) {   // a * conj(w)
+  return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+}
+
+// a * exp(S 2 pi i e / 16) for e in [0, 8) (a constant after unrolling).
+template <int S>
+__device__ __forceinline__ float2 rot16(float2 a, int e) {
+  constexpr float r = 0.70710678118654752440f;
+  constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
+  constexpr float fs = (float)S;
+  switch (e) {
+    case 0: return a;
+    case 1: return make_float2(a.x * c1 - fs * s1 * a.y, fs * s1 * a.x + c1 * a.y);
+    case 2: return make_float2((a.x - fs * a.y) * r, (a.y + fs * a.x) * r);
+    case 3: return make_float2(a.x * s1 - fs * c1 * a.y, fs * c1 * a.x + s1 * a.y);
+    case 4: return make_float2(-fs * a.y, fs * a.x);
+    case 5: return make_float2(-a.x * s1 - fs * c1 * a.y, fs * c1 * a.x - s1 * a.y);
+    case 6: return make_float2((-a.x - fs * a.y) * r, (-a.y + fs * a.x) * r);
+    default: return make_float2(-a.x * c1 - fs * s1 * a.y, fs * s1 * a.x - c1 * a.y);
+  }
+}
+
+__host__ __device__ constexpr int br4(int i) {
+  return ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3);
+}
+
+// v[k] <- sum_r v[r] exp(S 2 pi i r k / 16): radix-2 decimation in frequency,
+// then the bit reversal (register renaming).
+template <int S>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+#pragma unroll
+  for (int span = 8; span >= 1; span >>= 1) {
+#pragma unroll
+    for (int st = 0; st < 16; st += 2 * span) {
+#pragma unroll
+      for (int j = 0; j < span; ++j) {
+        const float2 a = v[st + j], b = v[st + j + span];
+        v[st + j] = cadd(a, b);
+        v[st + j + span] = rot16<S>(csub(a, b), j * (8 / span));
+      }
+    }
+  }
+  float2 o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) o[br4(i)] = v[i];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = o[i];
+}
+
+// The radix-2 step across the lane pair (t, t ^ 1): lane b keeps
+// y0 + (-1)^b y1 (y_b: lane b's value); its own inverse up to the factor 2.
+__device__ __forceinline__ void pair_step(float2 (&v)[16], int b) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, v[k].x, 1),
+                                 __shfl_xor_sync(0xffffffffu, v[k].y, 1));
+    v[k] = b ? csub(p, v[k]) : cadd(v[k], p);
+  }
+}
+
+// exp(-2 pi i k / 32), k in [0, 16) (a constant after unrolling)
+__device__ __forceinline__ float2 w32(int k) {
+  constexpr float c[16] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
+                           0.83146961230254523708f, 0.70710678118654752440f,
+                           0.55557023301960222474f, 0.38268343236508977173f,
+                           0.19509032201612826785f, 0.0f, -0.19509032201612826785f,
+                           -0.38268343236508977173f, -0.55557023301960222474f,
+                           -0.70710678118654752440f, -0.83146961230254523708f,
+                           -0.92387953251128675613f, -0.98078528040323044913f};
+  constexpr float s[16] = {0.0f, 0.19509032201612826785f, 0.38268343236508977173f,
+                           0.55557023301960222474f, 0.70710678118654752440f,
+                           0.83146961230254523708f, 0.92387953251128675613f,
+                           0.98078528040323044913f, 1.0f, 0.98078528040323044913f,
+                           0.92387953251128675613f, 0.83146961230254523708f,
+                           0.70710678118654752440f, 0.55557023301960222474f,
+                           0.38268343236508977173f, 0.19509032201612826785f};
+  return make_float2(c[k], -s[k]);
+}
+
+struct FullrateArgs {
+  const float2* u;          // [J][u_row]: 2048 history samples, then the block
+  long long u_row;
+  long long F;              // frames of the block
+  const float2* hd;         // [Tr][16][512]: taps' spectrum / N, value k of thread t
+  const float2* tw1;        // [16][512] exp(-2 pi i b k / 8192)
+  const float2* tw2;        // [16][32]  exp(-2 pi i b k / 512)
+  const float* theta;
+  const float* theta2;
+  const long long* blk;
+  float* y;                 // [J][F M] Re v, or null
+  TriggerRec* trig;
+  unsigned long long* count;
+  long long cap;
+  float k_sigma;
+  int P, Tr, pol0, npol;
+};
+
+template <bool STORE_Y>
+__global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ FullrateArgs a) {
+  extern __shared__ float2 xs[];
+  const int t = threadIdx.x;
+  const int j = (int)sel_stream(blockIdx.y, a.P, a.pol0, a.npol);
+  const int tr = (j / a.P) % a.Tr;
+  const float2* __restrict__ urow = a.u + (long long)j * a.u_row;
+  const long long base = (long long)blockIdx.x * FR_V;
+  float2 v[16];
+
+  // ---- forward pass 1: blocks of 8192, stride 512 (thread t: position t + 512 r)
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const long long i = base + t + 512 * r;
+    v[r] = i < a.u_row ? __ldg(urow + i) : make_float2(0.f, 0.f);
+  }
+  dft16<-1>(v);
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(a.tw1 + k * 512 + t));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) xs[frp(t + 512 * k)] = v[k];
+  __syncthreads();
+  // ---- pass 2: blocks of 512, stride 32
+  const int b2 = t & 31, o2 = (t >> 5) * 512 + b2;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = xs[frp(o2 + 32 * r)];
+  dft16<-1>(v);
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(a.tw2 + k * 32 + b2));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) xs[frp(o2 + 32 * k)] = v[k];
+  __syncthreads();
+  // ---- pass 3: blocks of 32, stride 2; pass 4: pairs across neighbouring lanes
+  const int b3 = t & 1, o3 = (t >> 1) * 32 + b3;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = xs[frp(o3 + 2 * r)];
+  dft16<-1>(v);
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], b3 ? w32(k) : make_float2(1.f, 0.f));
+  pair_step(v, b3);
+  // ---- the product with the taps' spectrum (same order)
+  const float2* hd = a.hd + (long long)tr * FR_N + t;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], __ldg(hd + k * FR_NT));
+  // ---- inverse: passes 4, 3, 2, 1 backwards
+  pair_step(v, b3);
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], b3 ? w32(k) : make_float2(1.f, 0.f));
+  dft16<1>(v);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) xs[frp(o3 + 2 * r)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = xs[frp(o2 + 32 * k)];
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], __ldg(a.tw2 + k * 32 + b2));
+  dft16<1>(v);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) xs[frp(o2 + 32 * r)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = xs[frp(t + 512 * k)];
+#pragma unroll
+  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], __ldg(a.tw1 + k * 512 + t));
+  dft16<1>(v);
+
+  // ---- v[r] = result at position t + 512 r; positions >= 2048 are outputs
+  const long long FM = a.F * kM;
+  const long long n_first = (*a.blk * a.F - kHist) * (long long)kM;
+  const float th2 = a.theta2[j];
+  float* yj = STORE_Y ? a.y + (long long)j * FM : nullptr;
+  const int lane = t & 31;
+#pragma unroll
+  for (int r = 4; r < 16; ++r) {
+    const long long o = base + t + 512 * (r - 4);
+    const bool in = o < FM;
+    if (STORE_Y && in) yj[o] = v[r].x;
+    const float e2 = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+    const bool hit = in && e2 > th2 && n_first + o >= 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (!mask) continue;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long at = 0;
+    if (lane == leader) at = atomicAdd(a.count, (unsigned long long)__popc(mask));
+    at = __shfl_sync(0xffffffffu, at, leader);
+    if (hit) {
+      const unsigned long long idx = at + __popc(mask & ((1u << lane) - 1u));
+      if ((long long)idx < a.cap) {
+        TriggerRec rec;
+        rec.n = n_first + o;
+        rec.pol = j % a.P;
+        rec.tec = tr;
+        rec.beam = j / (a.P * a.Tr);
+        rec.stream = j;
+        rec.env = sqrtf(e2);
+        rec.sigma = a.theta[j] / a.k_sigma;
+        a.trig[idx] = rec;
+      }
+    }
+  }
+}
+
+// The last 2048 samples of every series row become the next block's history
+// (rows of at least 2048 block samples: the ranges do not overlap).
+__global__ void k_fullrate_shift(float2* __restrict__ u, long long u_row, long long FM, int P,
+                                 int pol0, int npol, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long j = sel_stream(i / kFrTaps, P, pol0, npol);
+  const int l = (int)(i % kFrTaps);
+  float2* row = u + j * u_row;
+  row[l] = row[FM + l];
+}
+
+// ---- set-up, FP64 ----------------------------------------------------------
+// E[m] = exp(+2 pi i m / N); H[m] = exp(-2 pi i phi(nu_m)) for m < N/2 (nu_m =
+// 100 MHz + m fs / N), 1 above; the FFT twiddle tables.
+__global__ void k_fr_tables(const double* __restrict__ tec, int t, double nu_ref,
+                            double2* __restrict__ H, double2* __restrict__ E,
+                            float2* __restrict__ tw1, float2* __restrict__ tw2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= FR_N) return;
+  double s, c;
+  sincospi(2.0 * (double)i / FR_N, &s, &c);
+  E[i] = make_double2(c, s);
+  if (i < FR_N / 2) {
+    const double nu = kNu0 + (double)i * (kFs / FR_N);
+    const double a = kKappa * tec[t] * kTecu / kC;
+    const double dnu = nu - nu_ref;
+    const double cyc = a * (dnu * dnu) / (nu * nu_ref * nu_ref);
+    const double r = cyc - rint(cyc);
+    sincospi(2.0 * r, &s, &c);
+    H[i] = make_double2(c, -s);
+  } else {
+    H[i] = make_double2(1.0, 0.0);
+  }
+  {
+    const int k = i / 512, b = i % 512;        // i < 16 * 512 = N
+    const int e = (b * k) % FR_N;
+    sincospi(2.0 * (double)e / FR_N, &s, &c);
+    tw1[i] = make_float2((float)c, (float)-s);
+  }
+  if (i < 16 * 32) {
+    const int k = i / 32, b = i % 32;
+    const int e = (b * k) % 512;
+    sincospi(2.0 * (double)e / 512.0, &s, &c);
+    tw2[i] = make_float2((float)c, (float)-s);
+  }
+}
+
+// h[l] = w(l - D) (1/N) sum_m H[m] E[(m (l - D)) mod N], l < 2048, D = 1024;
+// w(d) = 1 for |d| <= 768, (1 + cos(pi (|d| - 768) / 256)) / 2 beyond.
+__global__ void k_fr_taps(const double2* __restrict__ H, const double2* __restrict__ E,
+                          double2* __restrict__ h) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= kFrTaps) return;
+  const int d = l - kFrDelay;
+  const int dm = ((d % FR_N) + FR_N) % FR_N;
+  double re = 0.0, im = 0.0;
+  int m = 0;
+  for (int q = 0; q < FR_N; ++q) {
+    const double2 a = H[q], e = E[m];
+    re = fma(a.x, e.x, fma(-a.y, e.y, re));
+    im = fma(a.x, e.y, fma(a.y, e.x, im));
+    m += dm;
+    if (m >= FR_N) m -= FR_N;
+  }
+  const double half = 0.5 * kFrFlat, ramp = 0.5 * (kFrTaps - kFrFlat);
+  const double ad = fabs((double)d);
+  const double w = ad <= half ? 1.0 : 0.5 * (1.0 + cospi(fmin(ad - half, ramp) / ramp));
+  h[l] = make_double2(re * w / FR_N, im * w / FR_N);
+}
+
+// The taps' spectrum / N in the kernel's order: entry (k, t) is frequency
+// K = k1 + 16 k2 + 256 k + 4096 b (t = 2 (16 k1 + k2) + b).
+__global__ void k_fr_spectrum(const double2* __restrict__ h, const double2* __restrict__ E,
+                              float2* __restrict__ hd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= FR_N) return;
+  const int k = i / FR_NT, t = i % FR_NT, B = t >> 1, b = t & 1;
+  const int K = (B >> 4) + 16 * (B & 15) + 256 * k + 4096 * b;
+  double re = 0.0, im = 0.0;
+  int m = 0;
+  for (int l = 0; l < kFrTaps; ++l) {
+    const double2 a = h[l], e = E[m];        // a * conj(e)
+    re = fma(a.x, e.x, fma(a.y, e.y, re));
+    im = fma(a.y, e.x, fma(-a.x, e.y, im));
+    m += K;
+    if (m >= FR_N) m -= FR_N;
+  }
+  hd[i] = make_float2((float)(re / FR_N), (float)(im / FR_N));
+}
+
+}  // namespace
+
+long long fullrate_row(const lp_plan& p) { return kFrTaps + p.shape.F * kM; }
+
+size_t fullrate_table_bytes() {
+  return sizeof(float2) * (16 * 512 + 16 * 32);
+}
+
+cudaError_t init_fullrate_attributes() {
+  cudaError_t e = raise_smem_limit((const void*)k_fullrate<false>, FR_SMEM);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_fullrate<true>, FR_SMEM);
+  return e;
+}
+
+cudaError_t launch_fullrate_taps(const lp_plan& p, cudaStream_t s) {
+  const Buffers& b = p.buf;
+  float2* tw2 = b.fr_tw + 16 * 512;
+  for (int t = 0; t < p.shape.Tr; ++t) {
+    k_fr_tables<<<FR_N / 256, 256, 0, s>>>(b.tec, t, p.nu_ref, b.fr_H, b.fr_E, b.fr_tw, tw2);
+    k_fr_taps<<<kFrTaps / 128, 128, 0, s>>>(b.fr_H, b.fr_E, b.fr_h);
+    k_fr_spectrum<<<FR_N / 128, 128, 0, s>>>(b.fr_h, b.fr_E, b.fr_hd + (size_t)t * FR_N);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps) {
+  const Buffers& b = p.buf;
+  const int npol = ps.npol ? ps.npol : p.shape.P;
+  FullrateArgs a;
+  a.u = b.ufull;
+  a.u_row = fullrate_row(p);
+  a.F = p.shape.F;
+  a.hd = b.fr_hd;
+  a.tw1 = b.fr_tw;
+  a.tw2 = b.fr_tw + 16 * 512;
+  a.theta = b.theta;
+  a.theta2 = b.theta2;
+  a.blk = b.blk;
+  a.y = b.y;
+  a.trig = b.trig;
+  a.count = b.trig_count;
+  a.cap = (long long)p.cfg.trigger_cap;
+  a.k_sigma = (float)p.cfg.k_sigma;
+  a.P = p.shape.P;
+  a.Tr = p.shape.Tr;
+  a.pol0 = ps.pol0;
+  a.npol = npol;
+  const long long FM = p.shape.F * kM;
+  const dim3 grid((unsigned)((FM + FR_V - 1) / FR_V), (unsigned)(p.shape.J() / p.shape.P * npol));
+  if (b.y)
+    k_fullrate<true><<<grid, FR_NT, FR_SMEM, s>>>(a);
+  else
+    k_fullrate<false><<<grid, FR_NT, FR_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fullrate_shift(const lp_plan& p, cudaStream_t s, PolSel ps) {
+  const int npol = ps.npol ? ps.npol : p.shape.P;
+  const long long n = (long long)p.shape.J() / p.shape.P * npol * kFrTaps;
+  k_fullrate_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      p.buf.ufull, fullrate_row(p), p.shape.F * kM, p.shape.P, ps.pol0, npol, n);
+  return cudaGetLastError();
+}
+
+}  // namespace lp

@@ -347,6 +347,7 @@ struct FirCtx {
   float th2;
   unsigned ymask;          // output frames of the batch (time-series store)
   float* yrow;             // y of batch row 0 (or null)
+  float2* urow;            // u of batch row 0 (full-rate mode)
 };
 
 // The CTA's stream (index within its plan, sigma, plan), kept in shared memory
@@ -406,7 +407,8 @@ __device__ __noinline__ void emit_triggers(const float (&e2v)[FB], float th2, in
 // FIR of one phase over one batch.  hist: the phase's 16 history slots (frame
 // r at slot r mod 16, (re, im) in consecutive columns); zn: the 8 new frames.
 // ODD selects where the 15 history frames r0-15 .. r0-1 sit (r0 mod 16 = 8 ODD).
-template <int ODD, bool STORE_Y>
+// OUT: 0 trigger, 1 trigger and y = Re u, 2 (full-rate mode) u stored, no trigger.
+template <int ODD, int OUT>
 __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float (&hist)[32],
                                           const float2 (&zn)[FB], int p, int r0, const FirCtx& c,
                                           const StreamInfo* si) {
@@ -418,6 +420,16 @@ __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float
   }
 #pragma unroll
   for (int f = 0; f < FB; ++f) w[kHist + f] = zn[f];
+  if constexpr (OUT == 2) {
+#pragma unroll
+    for (int f = 0; f < FB; ++f) {
+      float2 u = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < kTaps; ++t) u = __ffma2_rn(gq[t], w[f + kHist - t], u);
+      if ((c.ymask >> f) & 1u) c.urow[f * kM + p] = u;
+    }
+    return;
+  }
   float e2v[FB];
   float emax = 0.f;
 #pragma unroll
@@ -426,7 +438,7 @@ __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float
 #pragma unroll
     for (int t = 0; t < kTaps; ++t)   // both components per instruction, tap (g, g)
       u = __ffma2_rn(gq[t], w[f + kHist - t], u);
-    if constexpr (STORE_Y)   // (in a group, plans without a stored series have no row)
+    if constexpr (OUT == 1)  // (in a group, plans without a stored series have no row)
       if (c.yrow && ((c.ymask >> f) & 1u)) c.yrow[f * kM + p] = u.x;
     e2v[f] = fmaf(u.x, u.x, u.y * u.y);
     emax = fmaxf(emax, e2v[f]);         // frames outside the run are filtered by vmask
@@ -442,7 +454,7 @@ __device__ __forceinline__ void fir_phase(const float2 (&gq)[kTaps], const float
 
 // One phase of the FIR role for batch r0: its 8 new frames zn, history from
 // tensor memory; the new frames then replace the history slots r0 mod 16 ...
-template <bool STORE_Y>
+template <int OUT>
 __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t thist,
                                         const float2 (&zn)[FB], int p, int r0, bool outputs,
                                         const FirCtx& c, const StreamInfo* si) {
@@ -451,9 +463,9 @@ __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t this
     tmem_ld32(thist, hist);
     tmem_wait_ld();
     if (r0 & 8)
-      fir_phase<1, STORE_Y>(gq, hist, zn, p, r0, c, si);
+      fir_phase<1, OUT>(gq, hist, zn, p, r0, c, si);
     else
-      fir_phase<0, STORE_Y>(gq, hist, zn, p, r0, c, si);
+      fir_phase<0, OUT>(gq, hist, zn, p, r0, c, si);
   }
   // the 8 new frames fill 16 consecutive history columns: one store
   tmem_st16(thist + 2 * (r0 & 8), reinterpret_cast<const float(&)[16]>(zn[0]));
@@ -465,7 +477,7 @@ __device__ __forceinline__ void fir_one(const float2 (&gq)[kTaps], uint32_t this
 // trigger list, and all share the frame range and the tiling.  GROUP = false:
 // one plan, whose parameters are then read at fixed offsets of the parameter
 // block (no indexed lookup on the single-plan path).
-template <bool GROUP, bool STORE_Y>
+template <bool GROUP, int OUT>
 __global__ void __launch_bounds__(NT, 1) k_ippf(
     const __grid_constant__ IppfArgsN<GROUP ? kMaxGroup : 1> a) {
   extern __shared__ float4 smem4[];
@@ -558,7 +570,9 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
     c.th2 = pl.theta2[j];
     const long long F_total = a.F_total, f_base = a.f_base;
     // this launch covers block frames [f_base, f_base + F) (one chunk, or the block)
-    float* yj = pl.y ? pl.y + ((long long)j * F_total + f_base) * kM : nullptr;
+    float* yj = OUT == 1 && pl.y ? pl.y + ((long long)j * F_total + f_base) * kM : nullptr;
+    // full-rate mode: the series row of the stream (history first)
+    float2* uj = OUT == 2 ? pl.u + (long long)j * pl.u_row + kFrTaps + f_base * kM : nullptr;
     // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
     // m < 15 of the first block) never trigger
     const long long bidx = *pl.blk;
@@ -587,6 +601,7 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
       c.ymask = frame_bits(kPrefix - r0, nfr - r0);
       const long long m_row0 = m0 - kPrefix + r0;             // frame of batch row 0
       c.yrow = yj ? yj + m_row0 * kM : nullptr;
+      if constexpr (OUT == 2) c.urow = uj + m_row0 * kM;
 #pragma unroll 1
       for (int bp = 0; bp < 2; ++bp) {
         const int pb = bp ? kM / 2 - 1 - ft : ft;
@@ -610,8 +625,8 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
           float2 gq[kTaps];
 #pragma unroll
           for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
-          fir_one<STORE_Y>(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0,
-                           outputs, c, &sinfo);
+          fir_one<OUT>(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0,
+                       outputs, c, &sinfo);
         }
       }
       tmem_wait_st();                    // history slots written before the next batch reads them
@@ -697,10 +712,11 @@ int ippf_default_frames_per_cta(const Shape& sh) {
 }
 
 cudaError_t init_ippf_attributes() {
-  const void* k[4] = {(const void*)k_ippf<false, false>, (const void*)k_ippf<false, true>,
-                      (const void*)k_ippf<true, false>, (const void*)k_ippf<true, true>};
+  const void* k[5] = {(const void*)k_ippf<false, 0>, (const void*)k_ippf<false, 1>,
+                      (const void*)k_ippf<false, 2>, (const void*)k_ippf<true, 0>,
+                      (const void*)k_ippf<true, 1>};
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = raise_smem_limit(k[i], ippf_smem_bytes());
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = raise_smem_limit(k[i], ippf_smem_bytes());
   return e;
 }
 
@@ -713,6 +729,8 @@ IppfPlan ippf_plan(const lp_plan& p) {
   q.theta2 = p.buf.theta2;
   q.blk = p.buf.blk;
   q.y = p.buf.y;
+  q.u = p.buf.ufull;
+  q.u_row = p.buf.ufull ? fullrate_row(p) : 0;
   q.trig = p.buf.trig;
   q.count = p.buf.trig_count;
   q.cap = (long long)p.cfg.trigger_cap;
@@ -757,17 +775,19 @@ cudaError_t launch_ippf_plans(const lp_plan* const* plans, int n, const Chunk& c
     a1.npol = a.npol;
     a1.n = 1;
     a1.pl[0] = a.pl[0];
-    if (a1.pl[0].y)
-      k_ippf<false, true><<<grid, NT, ippf_smem_bytes(), s>>>(a1);
+    if (a1.pl[0].u)
+      k_ippf<false, 2><<<grid, NT, ippf_smem_bytes(), s>>>(a1);
+    else if (a1.pl[0].y)
+      k_ippf<false, 1><<<grid, NT, ippf_smem_bytes(), s>>>(a1);
     else
-      k_ippf<false, false><<<grid, NT, ippf_smem_bytes(), s>>>(a1);
+      k_ippf<false, 0><<<grid, NT, ippf_smem_bytes(), s>>>(a1);
   } else {
     bool any_y = false;
     for (int i = 0; i < n; ++i) any_y = any_y || a.pl[i].y;
     if (any_y)
-      k_ippf<true, true><<<grid, NT, ippf_smem_bytes(), s>>>(a);
+      k_ippf<true, 1><<<grid, NT, ippf_smem_bytes(), s>>>(a);
     else
-      k_ippf<true, false><<<grid, NT, ippf_smem_bytes(), s>>>(a);
+      k_ippf<true, 0><<<grid, NT, ippf_smem_bytes(), s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -845,8 +865,11 @@ cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t 
   return launch_history_shift_plans(&one, 1, c, s, ps);
 }
 
+cudaError_t init_fullrate_attributes();
+
 cudaError_t init_kernel_attributes(const Shape& sh) {
   cudaError_t e = init_ippf_attributes();
+  if (e == cudaSuccess) e = init_fullrate_attributes();
   if (e == cudaSuccess) e = init_f32_attributes(sh);
   if (e == cudaSuccess) e = init_tc_attributes(sh);
   return e;

@@ -88,9 +88,13 @@ __global__ void k_weights(const double* __restrict__ enu, const double* __restri
 }
 
 __global__ void k_dedisp(const double* __restrict__ tec, int K, int Tr, int first_bin,
-                         double nu_ref, float2* __restrict__ dd) {
+                         double nu_ref, int unit, float2* __restrict__ dd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= K * Tr) return;
+  if (unit) {                              // full-rate mode: the phase is applied later
+    dd[i] = make_float2(1.f, 0.f);
+    return;
+  }
   const int t = i % Tr;
   const int k = i / Tr;
   const double nu = kNu0 + (double)(first_bin + k) * (kFs / kM);
@@ -124,7 +128,7 @@ cudaError_t launch_dedisp(const lp_plan& p, cudaStream_t s) {
   const auto& sh = p.shape;
   const int n = sh.K * sh.Tr;
   k_dedisp<<<(n + 255) / 256, 256, 0, s>>>(p.buf.tec, sh.K, sh.Tr, p.cfg.first_bin, p.nu_ref,
-                                            p.buf.dd);
+                                            p.cfg.fullrate_dedisp ? 1 : 0, p.buf.dd);
   return cudaGetLastError();
 }
 

@@ -100,6 +100,14 @@ size_t carve(lp_plan& p, char* base) {
   p.trig_buf[1] =
       two ? (lp::TriggerRec*)take(sizeof(lp::TriggerRec) * (size_t)p.cfg.trigger_cap) : nullptr;
   b.y = p.cfg.store_timeseries ? (float*)take(sizeof(float) * (size_t)J * sh.F * kM) : nullptr;
+  const bool fr = p.cfg.fullrate_dedisp != 0;
+  b.ufull = fr ? (float2*)take(sizeof(float2) * (size_t)J * (lp::kFrTaps + (size_t)sh.F * kM))
+               : nullptr;
+  b.fr_hd = fr ? (float2*)take(sizeof(float2) * (size_t)sh.Tr * lp::kFrN) : nullptr;
+  b.fr_tw = fr ? (float2*)take(lp::fullrate_table_bytes()) : nullptr;
+  b.fr_h = fr ? (double2*)take(sizeof(double2) * lp::kFrTaps) : nullptr;
+  b.fr_H = fr ? (double2*)take(sizeof(double2) * lp::kFrN) : nullptr;
+  b.fr_E = fr ? (double2*)take(sizeof(double2) * lp::kFrN) : nullptr;
   const size_t in_bytes = (size_t)sh.P * sh.K * sh.F * sh.S * 2 *
                           (p.cfg.input_dtype == LP_INPUT_INT8 ? 1 : 2);
   b.staging = p.cfg.host_input ? (void*)take(in_bytes) : nullptr;
@@ -179,6 +187,7 @@ void lp_config_default(lp_config* c) {
   c->inversion = LP_INV_FIR;
   c->lsmr_iters = 25;
   c->stream_blocks = 0;
+  c->fullrate_dedisp = 0;
 }
 
 lp_status lp_plan_create(lp_plan** out, int stations, int pols, int subbands, int beams,
@@ -237,6 +246,12 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
     return fail(p, LP_ERR_ARG, "fine_dedisp does not combine with chunk_frames");
   if (c->stream_blocks != 0 && c->stream_blocks != 1)
     return fail(p, LP_ERR_ARG, "stream_blocks must be 0 or 1");
+  if (c->fullrate_dedisp != 0 && c->fullrate_dedisp != 1)
+    return fail(p, LP_ERR_ARG, "fullrate_dedisp must be 0 or 1");
+  if (c->fullrate_dedisp &&
+      (c->inversion != LP_INV_FIR || c->chunk_frames != 0 || c->fine_dedisp || c->stream_blocks))
+    return fail(p, LP_ERR_ARG, "fullrate_dedisp needs the FIR inversion and does not combine "
+                "with chunk_frames, fine_dedisp or stream_blocks");
   if (c->stream_blocks && c->use_graph)
     return fail(p, LP_ERR_ARG, "stream_blocks does not combine with use_graph");
   if (c->chunk_frames != 0) {
@@ -342,11 +357,24 @@ lp_status lp_set_tec(lp_plan* p, const double* tec, void* stream) {
                       "filter's 4-frame range", t, d);
       }
   }
+  if (p->cfg.fullrate_dedisp) {
+    // the full-rate taps' window holds group delays within 768 samples of the
+    // reference delay over the whole 100-200 MHz band
+    for (int t = 0; t < sh.Tr; ++t)
+      for (double nu : {lp::kNu0, lp::kFs}) {
+        const double a = lp::kKappa * tec[t] * lp::kTecu / lp::kC;
+        const double d = a * (1.0 / (nu * nu) - 1.0 / (p->nu_ref * p->nu_ref)) * lp::kFs;
+        if (std::fabs(d) > 0.5 * lp::kFrFlat)
+          return fail(p, LP_ERR_ARG, "tec[%d]: group delay %.0f samples exceeds the full-rate "
+                      "filter's %d-sample range", t, d, lp::kFrFlat / 2);
+      }
+  }
   if (set_device(p) != LP_OK) return LP_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LP_CUDA(p, cudaMemcpyAsync(p->buf.tec, tec, sizeof(double) * sh.Tr, cudaMemcpyHostToDevice, s));
   LP_CUDA(p, lp::launch_dedisp(*p, s));
   if (p->cfg.fine_dedisp) LP_CUDA(p, lp::launch_fine_taps(*p, s));
+  if (p->cfg.fullrate_dedisp) LP_CUDA(p, lp::launch_fullrate_taps(*p, s));
   p->last_stream = s;
   p->tec_set = true;
   return LP_OK;
@@ -608,7 +636,7 @@ lp_status process_inner(lp_plan* p, const void* x, int64_t pol_stride, void* str
   const bool host = attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged;
   const bool graph_mode = p->cfg.use_graph && !p->profiling && !tune;
   if (host && p->buf.staging && sh.P == 2 && p->fc == sh.F && !tune && !graph_mode &&
-      p->cfg.inversion == LP_INV_FIR)
+      p->cfg.inversion == LP_INV_FIR && !p->cfg.fullrate_dedisp)
     return process_host_pipelined(p, x, pol_stride, s);
   if (host) {
     if (!p->buf.staging)
@@ -666,8 +694,14 @@ lp_status process_inner(lp_plan* p, const void* x, int64_t pol_stride, void* str
         e = tune == kTuneSynth ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
       }
       prof_mark(p, LP_STAGE_SYNTH, 1, s);
+      if (p->cfg.fullrate_dedisp) {
+        prof_mark(p, LP_STAGE_FULLRATE, 0, s);
+        if (e == cudaSuccess) e = lp::launch_fullrate(*p, s);
+        prof_mark(p, LP_STAGE_FULLRATE, 1, s);
+      }
       prof_mark(p, LP_STAGE_SHIFT, 0, s);
       if (e == cudaSuccess) e = lp::launch_history_shift(*p, c, s);
+      if (e == cudaSuccess && p->cfg.fullrate_dedisp) e = lp::launch_fullrate_shift(*p, s);
       prof_mark(p, LP_STAGE_SHIFT, 1, s);
     } else {
       // chunked block: the noise level needs the whole block, so a first
@@ -915,6 +949,9 @@ lp_status lp_reset_stream(lp_plan* p, void* stream) {
     LP_CUDA(p, cudaMemsetAsync(p->buf.beams_fine, 0,
                                sizeof(float2) * (size_t)sh.J() * sh.K * p->row(), s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.sigma2, 0, sizeof(double) * sh.J(), s));
+  if (p->buf.ufull)                    // the series history of the full-rate filter
+    LP_CUDA(p, cudaMemset2DAsync(p->buf.ufull, sizeof(float2) * lp::fullrate_row(*p), 0,
+                                 sizeof(float2) * lp::kFrTaps, sh.J(), s));
   if (p->buf.lsmr_sigma2)
     LP_CUDA(p, cudaMemsetAsync(p->buf.lsmr_sigma2, 0, sizeof(double) * sh.J() * kM, s));
   LP_CUDA(p, cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s));
@@ -937,7 +974,7 @@ int lp_launches_per_block(const lp_plan* p) {
     const int nj = (int)((p->shape.J() + 65534) / 65535);   // 65535 streams, sigma, shift
     return 3 + fine + 3 * nj;
   }
-  if (p->fc == 0 || p->fc == p->shape.F) return 4 + fine;
+  if (p->fc == 0 || p->fc == p->shape.F) return 4 + fine + (p->cfg.fullrate_dedisp ? 2 : 0);
   return 2 + 3 * (int)(p->shape.F / p->fc);
 }
 

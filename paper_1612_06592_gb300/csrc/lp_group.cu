@@ -47,8 +47,8 @@ const char* incompatible(const lp_plan& p0, const lp_plan& q) {
   if (q.cfg.precision != LP_PREC_FP16) return "group launches take the FP16 tensor-core form";
   if (q.fc != q.shape.F) return "group launches take whole blocks (chunk_frames = 0)";
   if (q.cfg.stream_blocks) return "group launches do not take stream_blocks plans";
-  if (q.cfg.fine_dedisp || q.cfg.inversion != LP_INV_FIR)
-    return "group launches take the FIR synthesis without fine de-dispersion";
+  if (q.cfg.fine_dedisp || q.cfg.fullrate_dedisp || q.cfg.inversion != LP_INV_FIR)
+    return "group launches take the FIR synthesis without fine or full-rate de-dispersion";
   if (q.device != p0.device) return "the plans live on different devices";
   if (q.shape.S != p0.shape.S || q.shape.P != p0.shape.P || q.shape.F != p0.shape.F)
     return "the plans differ in stations, polarisations or block length";

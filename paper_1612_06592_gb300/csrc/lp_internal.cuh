@@ -32,6 +32,15 @@ constexpr double kFineBeta = 4.0;
 constexpr int kFineGrid = 1024;
 static_assert(kFineTaps - 1 <= kPrefix, "the filter's history must fit the row prefix");
 
+// Full-rate de-dispersion (Sec. 3, third paragraph, at full resolution): taps
+// of the streaming filter of the synthesised series, their common delay, the
+// flat part of their window and the transform size of the set-up and of the
+// overlap-save filter.
+constexpr int kFrTaps = 2048;
+constexpr int kFrDelay = 1024;
+constexpr int kFrFlat = 1536;
+constexpr int kFrN = 8192;
+
 // I0(x) = sum_k ((x/2)^k / k!)^2, summed until the terms vanish (Kaiser windows).
 __device__ inline double bessel_i0_series(double x) {
   const double q = 0.25 * x * x;
@@ -78,6 +87,12 @@ struct Buffers {
   unsigned long long* trig_count;  // [1]
   TriggerRec* trig;        // [trigger_cap]
   float* y;                // [J][F*M] or null
+  float2* ufull;           // full-rate mode: [J][kFrTaps + F*M] synthesised series, history first
+  float2* fr_hd;           // full-rate mode: [Tr][16][512] taps' spectrum / kFrN (kernel order)
+  float2* fr_tw;           // full-rate mode: FFT twiddles [16][512], then [16][32]
+  double2* fr_h;           // full-rate set-up scratch: [kFrTaps] taps of one trial
+  double2* fr_H;           // full-rate set-up scratch: [kFrN] response of one trial
+  double2* fr_E;           // full-rate set-up scratch: [kFrN] exp(+2 pi i m / kFrN)
   void* staging;           // one block of input or null
   int* err;                // device error word: 1 = a bounded wait gave up
   long long* blk;          // device block counter (advanced by the history shift)
@@ -106,6 +121,9 @@ struct IppfPlan {
   const float* theta2;
   const long long* blk;
   float* y;
+  float2* u;               // full-rate mode: series rows (the kernel then stores u and
+                           // does not trigger), or null
+  long long u_row;
   TriggerRec* trig;
   unsigned long long* count;
   long long cap;
@@ -263,6 +281,13 @@ cudaError_t launch_history_shift(const lp_plan& p, const Chunk& c, cudaStream_t 
 // block's beam rows into the second row buffer
 cudaError_t launch_fine_taps(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_fine(const lp_plan& p, cudaStream_t s, PolSel ps = {});
+// full-rate de-dispersion: the taps' spectrum (from the STEC values), the
+// filter of the synthesised series with the trigger, and the series history
+cudaError_t launch_fullrate_taps(const lp_plan& p, cudaStream_t s);
+cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps = {});
+cudaError_t launch_fullrate_shift(const lp_plan& p, cudaStream_t s, PolSel ps = {});
+long long fullrate_row(const lp_plan& p);
+size_t fullrate_table_bytes();
 // PPF inversion by windowed LSMR (replaces the synthesis and the trigger)
 cudaError_t launch_lsmr(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_lsmr_trigger(const lp_plan& p, cudaStream_t s);

@@ -72,9 +72,9 @@ extern "C" lp_status lp_process_block_noalloc(
     return report(err, errlen, LP_ERR_ARG, "null argument");
   if (cfg->precision != LP_PREC_FP32)
     return report(err, errlen, LP_ERR_ARG, "the no-allocation entry point runs the FP32 form only");
-  if (cfg->fine_dedisp || cfg->inversion != LP_INV_FIR)
-    return report(err, errlen, LP_ERR_ARG,
-                  "the no-allocation entry point runs the FIR synthesis without fine de-dispersion");
+  if (cfg->fine_dedisp || cfg->fullrate_dedisp || cfg->inversion != LP_INV_FIR)
+    return report(err, errlen, LP_ERR_ARG, "the no-allocation entry point runs the FIR synthesis "
+                  "without fine or full-rate de-dispersion");
   if (trigger_cap < 0 || (trigger_cap > 0 && !triggers))
     return report(err, errlen, LP_ERR_ARG, "bad trigger buffer");
   for (int i = 0; i < beams; ++i) {

@@ -44,6 +44,7 @@ class lp_config(ctypes.Structure):
         ("inversion", ctypes.c_int32),
         ("lsmr_iters", ctypes.c_int32),
         ("stream_blocks", ctypes.c_int32),
+        ("fullrate_dedisp", ctypes.c_int32),
     ]
 
 
@@ -179,8 +180,8 @@ class Plan:
                  sigma_alpha=0.25, nu_ref_hz=0.0, trigger_cap=1 << 20,
                  store_timeseries=False, host_input=False, frames_per_cta=0,
                  kaiser_beta=9.0, use_graph=False, chunk_frames=0, fine_dedisp=False,
-                 inversion="fir", lsmr_iters=25, stream_blocks=False, stream=None,
-                 workspace=None):
+                 inversion="fir", lsmr_iters=25, stream_blocks=False, fullrate_dedisp=False,
+                 stream=None, workspace=None):
         import torch
         self.shape = (stations, pols, subbands, beams, tec_trials, block_len)
         self._h = _P()
@@ -204,6 +205,7 @@ class Plan:
         c.inversion = LP_INV_LSMR if inversion == "lsmr" else LP_INV_FIR
         c.lsmr_iters = int(lsmr_iters)
         c.stream_blocks = int(bool(stream_blocks))
+        c.fullrate_dedisp = int(bool(fullrate_dedisp))
         self.config = c
         self._check(_lib.lp_plan_configure(self._h, ctypes.byref(c)), "lp_plan_configure")
         nbytes = ctypes.c_size_t()
@@ -358,7 +360,7 @@ class Plan:
         cfgs = self.lp_plan_gemm_configs()
         return best.value, {c: m for c, m in zip(cfgs, ms.tolist()) if m > 0}
 
-    STAGES = ("h2d", "beamform", "sigma", "synth", "shift", "fine")
+    STAGES = ("h2d", "beamform", "sigma", "synth", "shift", "fine", "fullrate")
 
     def lp_profile_enable(self, enable=True):
         self._check(_lib.lp_profile_enable(self._h, int(bool(enable))), "lp_profile_enable")
