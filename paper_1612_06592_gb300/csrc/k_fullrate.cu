@@ -48,34 +48,60 @@ static_assert(FR_N == 16 * FR_NT, "16 values per thread");
 
 // padded shared-memory position of transform position i
 __host__ __device__ constexpr int frp(int i) { return i + 2 * (i >> 5); }
-constexpr int FR_SMEM = (frp(FR_N - 1) + 1) * (int)sizeof(float2);
+constexpr int FR_SMEM = (frp(FR_N - 1) + 1) * (int)sizeof(float4);
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+// One transform position of the block's two segments: re = (re_a, re_b),
+// im = (im_a, im_b), so every packed FP32 instruction does the same step for
+// both segments.
+struct CP {
+  float2 re, im;
+};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
-__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
-  return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ CP cadd(CP a, CP b) { return CP{add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ CP csub(CP a, CP b) { return CP{sub2(a.re, b.re), sub2(a.im, b.im)}; }
+// a * w, w = (c, c, s, s) for the complex factor c + i s
+__device__ __forceinline__ CP cmul(CP a, float4 w) {
+  const float2 c = make_float2(w.x, w.y), s = make_float2(w.z, w.w);
+  return CP{fma2(a.re, c, mul2(a.im, make_float2(-s.x, -s.y))), fma2(a.re, s, mul2(a.im, c))};
 }
-__device__ __forceinline__ float2 cmulc(float2 a, float2 w) {   // a * conj(w)
-  return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+// a * conj(w)
+__device__ __forceinline__ CP cmulc(CP a, float4 w) {
+  const float2 c = make_float2(w.x, w.y), s = make_float2(w.z, w.w);
+  return CP{fma2(a.re, c, mul2(a.im, s)), fma2(a.im, c, mul2(a.re, make_float2(-s.x, -s.y)))};
+}
+__device__ __forceinline__ CP cmul_const(CP a, float c, float s) {    // a * (c + i s)
+  return CP{fma2(a.re, bc(c), mul2(a.im, bc(-s))), fma2(a.re, bc(s), mul2(a.im, bc(c)))};
 }
 
 // a * exp(S 2 pi i e / 16) for e in [0, 8) (a constant after unrolling).
 template <int S>
-__device__ __forceinline__ float2 rot16(float2 a, int e) {
+__device__ __forceinline__ CP rot16(CP a, int e) {
   constexpr float r = 0.70710678118654752440f;
   constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
   constexpr float fs = (float)S;
   switch (e) {
     case 0: return a;
-    case 1: return make_float2(a.x * c1 - fs * s1 * a.y, fs * s1 * a.x + c1 * a.y);
-    case 2: return make_float2((a.x - fs * a.y) * r, (a.y + fs * a.x) * r);
-    case 3: return make_float2(a.x * s1 - fs * c1 * a.y, fs * c1 * a.x + s1 * a.y);
-    case 4: return make_float2(-fs * a.y, fs * a.x);
-    case 5: return make_float2(-a.x * s1 - fs * c1 * a.y, fs * c1 * a.x - s1 * a.y);
-    case 6: return make_float2((-a.x - fs * a.y) * r, (-a.y + fs * a.x) * r);
-    default: return make_float2(-a.x * c1 - fs * s1 * a.y, fs * s1 * a.x - c1 * a.y);
+    case 1: return cmul_const(a, c1, fs * s1);
+    case 2:   // (re - S im, im + S re) / sqrt 2
+      return fs > 0 ? CP{mul2(sub2(a.re, a.im), bc(r)), mul2(add2(a.im, a.re), bc(r))}
+                    : CP{mul2(add2(a.re, a.im), bc(r)), mul2(sub2(a.im, a.re), bc(r))};
+    case 3: return cmul_const(a, s1, fs * c1);
+    case 4:   // S i
+      return fs > 0 ? CP{make_float2(-a.im.x, -a.im.y), a.re}
+                    : CP{a.im, make_float2(-a.re.x, -a.re.y)};
+    case 5: return cmul_const(a, -s1, fs * c1);
+    case 6:   // (-re - S im, -im + S re) / sqrt 2
+      return fs > 0 ? CP{mul2(add2(a.re, a.im), bc(-r)), mul2(sub2(a.re, a.im), bc(r))}
+                    : CP{mul2(sub2(a.im, a.re), bc(r)), mul2(add2(a.re, a.im), bc(-r))};
+    default: return cmul_const(a, -c1, fs * s1);
   }
 }
 
@@ -86,20 +112,20 @@ __host__ __device__ constexpr int br4(int i) {
 // v[k] <- sum_r v[r] exp(S 2 pi i r k / 16): radix-2 decimation in frequency,
 // then the bit reversal (register renaming).
 template <int S>
-__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+__device__ __forceinline__ void dft16(CP (&v)[16]) {
 #pragma unroll
   for (int span = 8; span >= 1; span >>= 1) {
 #pragma unroll
     for (int st = 0; st < 16; st += 2 * span) {
 #pragma unroll
       for (int j = 0; j < span; ++j) {
-        const float2 a = v[st + j], b = v[st + j + span];
+        const CP a = v[st + j], b = v[st + j + span];
         v[st + j] = cadd(a, b);
         v[st + j + span] = rot16<S>(csub(a, b), j * (8 / span));
       }
     }
   }
-  float2 o[16];
+  CP o[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) o[br4(i)] = v[i];
 #pragma unroll
@@ -108,17 +134,19 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 
 // The radix-2 step across the lane pair (t, t ^ 1): lane b keeps
 // y0 + (-1)^b y1 (y_b: lane b's value); its own inverse up to the factor 2.
-__device__ __forceinline__ void pair_step(float2 (&v)[16], int b) {
+__device__ __forceinline__ float2 shfl2(float2 v) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ void pair_step(CP (&v)[16], int b) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, v[k].x, 1),
-                                 __shfl_xor_sync(0xffffffffu, v[k].y, 1));
+    const CP p{shfl2(v[k].re), shfl2(v[k].im)};
     v[k] = b ? csub(p, v[k]) : cadd(v[k], p);
   }
 }
 
-// exp(-2 pi i k / 32), k in [0, 16) (a constant after unrolling)
-__device__ __forceinline__ float2 w32(int k) {
+// exp(-2 pi i k / 32) for lane parity b (1 for b = 0), k in [0, 16): (c, c, s, s)
+__device__ __forceinline__ float4 w32(int k, int b) {
   constexpr float c[16] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
                            0.83146961230254523708f, 0.70710678118654752440f,
                            0.55557023301960222474f, 0.38268343236508977173f,
@@ -133,16 +161,18 @@ __device__ __forceinline__ float2 w32(int k) {
                            0.92387953251128675613f, 0.83146961230254523708f,
                            0.70710678118654752440f, 0.55557023301960222474f,
                            0.38268343236508977173f, 0.19509032201612826785f};
-  return make_float2(c[k], -s[k]);
+  const float cc = b ? c[k] : 1.0f, ss = b ? -s[k] : 0.0f;
+  return make_float4(cc, cc, ss, ss);
 }
 
 struct FullrateArgs {
   const float2* u;          // [J][u_row]: 2048 history samples, then the block
   long long u_row;
   long long F;              // frames of the block
-  const float2* hd;         // [Tr][16][512]: taps' spectrum / N, value k of thread t
-  const float2* tw1;        // [16][512] exp(-2 pi i b k / 8192)
-  const float2* tw2;        // [16][32]  exp(-2 pi i b k / 512)
+  long long nseg;           // segments per stream
+  const float4* hd;         // [Tr][16][512]: taps' spectrum / N as (re, re, im, im)
+  const float4* tw1;        // [16][512] exp(-2 pi i b k / 8192) as (c, c, s, s)
+  const float4* tw2;        // [16][32]  exp(-2 pi i b k / 512)
   const float* theta;
   const float* theta2;
   const long long* blk;
@@ -154,104 +184,148 @@ struct FullrateArgs {
   int P, Tr, pol0, npol;
 };
 
+// Trigger compaction of one output of each lane (hit: above threshold).
+__device__ __forceinline__ void emit(bool hit, float e2, long long n, int j, int tr,
+                                     const FullrateArgs& a) {
+  const unsigned mask = __ballot_sync(0xffffffffu, hit);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long at = 0;
+  if (lane == leader) at = atomicAdd(a.count, (unsigned long long)__popc(mask));
+  at = __shfl_sync(0xffffffffu, at, leader);
+  if (hit) {
+    const unsigned long long idx = at + __popc(mask & ((1u << lane) - 1u));
+    if ((long long)idx < a.cap) {
+      TriggerRec rec;
+      rec.n = n;
+      rec.pol = j % a.P;
+      rec.tec = tr;
+      rec.beam = j / (a.P * a.Tr);
+      rec.stream = j;
+      rec.env = sqrtf(e2);
+      rec.sigma = a.theta[j] / a.k_sigma;
+      a.trig[idx] = rec;
+    }
+  }
+}
+
+// One block: segments 2 x and 2 x + 1 of stream y (the second may lie past the
+// block's end: it then reads zeros and emits nothing).
 template <bool STORE_Y>
 __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ FullrateArgs a) {
-  extern __shared__ float2 xs[];
+  extern __shared__ float4 xs[];
   const int t = threadIdx.x;
   const int j = (int)sel_stream(blockIdx.y, a.P, a.pol0, a.npol);
   const int tr = (j / a.P) % a.Tr;
-  const float2* __restrict__ urow = a.u + (long long)j * a.u_row;
-  const long long base = (long long)blockIdx.x * FR_V;
-  float2 v[16];
+  const long long base = (long long)blockIdx.x * (2 * FR_V);   // row index of segment a's sample 0
+  const float2* __restrict__ ua = a.u + (long long)j * a.u_row + base + t;
+  const long long rem = a.u_row - base - t;                     // row samples left from ua
+  CP v[16];
 
   // ---- forward pass 1: blocks of 8192, stride 512 (thread t: position t + 512 r)
+  if (rem >= FR_V + FR_N) {                                     // both segments inside the row
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const long long i = base + t + 512 * r;
-    v[r] = i < a.u_row ? __ldg(urow + i) : make_float2(0.f, 0.f);
+    for (int r = 0; r < 16; ++r) {
+      const float2 x0 = __ldg(ua + 512 * r), x1 = __ldg(ua + FR_V + 512 * r);
+      v[r] = CP{make_float2(x0.x, x1.x), make_float2(x0.y, x1.y)};
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const float2 z = make_float2(0.f, 0.f);
+      const float2 x0 = 512 * r < rem ? __ldg(ua + 512 * r) : z;
+      const float2 x1 = FR_V + 512 * r < rem ? __ldg(ua + FR_V + 512 * r) : z;
+      v[r] = CP{make_float2(x0.x, x1.x), make_float2(x0.y, x1.y)};
+    }
   }
   dft16<-1>(v);
 #pragma unroll
   for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(a.tw1 + k * 512 + t));
 #pragma unroll
-  for (int k = 0; k < 16; ++k) xs[frp(t + 512 * k)] = v[k];
+  for (int k = 0; k < 16; ++k)
+    xs[frp(t + 512 * k)] = make_float4(v[k].re.x, v[k].re.y, v[k].im.x, v[k].im.y);
   __syncthreads();
   // ---- pass 2: blocks of 512, stride 32
   const int b2 = t & 31, o2 = (t >> 5) * 512 + b2;
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = xs[frp(o2 + 32 * r)];
+  for (int r = 0; r < 16; ++r) {
+    const float4 q = xs[frp(o2 + 32 * r)];
+    v[r] = CP{make_float2(q.x, q.y), make_float2(q.z, q.w)};
+  }
   dft16<-1>(v);
 #pragma unroll
   for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(a.tw2 + k * 32 + b2));
 #pragma unroll
-  for (int k = 0; k < 16; ++k) xs[frp(o2 + 32 * k)] = v[k];
+  for (int k = 0; k < 16; ++k)
+    xs[frp(o2 + 32 * k)] = make_float4(v[k].re.x, v[k].re.y, v[k].im.x, v[k].im.y);
   __syncthreads();
   // ---- pass 3: blocks of 32, stride 2; pass 4: pairs across neighbouring lanes
   const int b3 = t & 1, o3 = (t >> 1) * 32 + b3;
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = xs[frp(o3 + 2 * r)];
+  for (int r = 0; r < 16; ++r) {
+    const float4 q = xs[frp(o3 + 2 * r)];
+    v[r] = CP{make_float2(q.x, q.y), make_float2(q.z, q.w)};
+  }
   dft16<-1>(v);
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], b3 ? w32(k) : make_float2(1.f, 0.f));
+  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], w32(k, b3));
   pair_step(v, b3);
-  // ---- the product with the taps' spectrum (same order)
-  const float2* hd = a.hd + (long long)tr * FR_N + t;
+  // ---- the product with the taps' spectrum (same order, same for both segments)
+  const float4* hd = a.hd + (long long)tr * FR_N + t;
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], __ldg(hd + k * FR_NT));
   // ---- inverse: passes 4, 3, 2, 1 backwards
   pair_step(v, b3);
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], b3 ? w32(k) : make_float2(1.f, 0.f));
+  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], w32(k, b3));
   dft16<1>(v);
 #pragma unroll
-  for (int r = 0; r < 16; ++r) xs[frp(o3 + 2 * r)] = v[r];
+  for (int r = 0; r < 16; ++r)
+    xs[frp(o3 + 2 * r)] = make_float4(v[r].re.x, v[r].re.y, v[r].im.x, v[r].im.y);
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = xs[frp(o2 + 32 * k)];
+  for (int k = 0; k < 16; ++k) {
+    const float4 q = xs[frp(o2 + 32 * k)];
+    v[k] = CP{make_float2(q.x, q.y), make_float2(q.z, q.w)};
+  }
 #pragma unroll
   for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], __ldg(a.tw2 + k * 32 + b2));
   dft16<1>(v);
 #pragma unroll
-  for (int r = 0; r < 16; ++r) xs[frp(o2 + 32 * r)] = v[r];
+  for (int r = 0; r < 16; ++r)
+    xs[frp(o2 + 32 * r)] = make_float4(v[r].re.x, v[r].re.y, v[r].im.x, v[r].im.y);
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = xs[frp(t + 512 * k)];
+  for (int k = 0; k < 16; ++k) {
+    const float4 q = xs[frp(t + 512 * k)];
+    v[k] = CP{make_float2(q.x, q.y), make_float2(q.z, q.w)};
+  }
 #pragma unroll
   for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], __ldg(a.tw1 + k * 512 + t));
   dft16<1>(v);
 
-  // ---- v[r] = result at position t + 512 r; positions >= 2048 are outputs
+  // ---- v[r] = result at position t + 512 r of both segments; positions >= 2048
+  // are outputs base + (segment) 6144 + t + 512 (r - 4)
   const long long FM = a.F * kM;
   const long long n_first = (*a.blk * a.F - kHist) * (long long)kM;
-  const float th2 = a.theta2[j];
+  const float2 th2 = bc(a.theta2[j]);
   float* yj = STORE_Y ? a.y + (long long)j * FM : nullptr;
-  const int lane = t & 31;
+  const long long o0 = base + t - 2048;                      // output index of position t + 512 * 0
 #pragma unroll
   for (int r = 4; r < 16; ++r) {
-    const long long o = base + t + 512 * (r - 4);
-    const bool in = o < FM;
-    if (STORE_Y && in) yj[o] = v[r].x;
-    const float e2 = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
-    const bool hit = in && e2 > th2 && n_first + o >= 0;
-    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    if (!mask) continue;
-    const int leader = __ffs(mask) - 1;
-    unsigned long long at = 0;
-    if (lane == leader) at = atomicAdd(a.count, (unsigned long long)__popc(mask));
-    at = __shfl_sync(0xffffffffu, at, leader);
-    if (hit) {
-      const unsigned long long idx = at + __popc(mask & ((1u << lane) - 1u));
-      if ((long long)idx < a.cap) {
-        TriggerRec rec;
-        rec.n = n_first + o;
-        rec.pol = j % a.P;
-        rec.tec = tr;
-        rec.beam = j / (a.P * a.Tr);
-        rec.stream = j;
-        rec.env = sqrtf(e2);
-        rec.sigma = a.theta[j] / a.k_sigma;
-        a.trig[idx] = rec;
-      }
+    const long long oa = o0 + 512 * r, ob = oa + FR_V;
+    const bool ina = oa < FM, inb = ob < FM;
+    if (STORE_Y) {
+      if (ina) yj[oa] = v[r].re.x;
+      if (inb) yj[ob] = v[r].re.y;
+    }
+    const float2 e2 = fma2(v[r].re, v[r].re, mul2(v[r].im, v[r].im));
+    const bool ha = ina && e2.x > th2.x && n_first + oa >= 0;
+    const bool hb = inb && e2.y > th2.y && n_first + ob >= 0;
+    if (__any_sync(0xffffffffu, ha || hb)) {
+      emit(ha, e2.x, n_first + oa, j, tr, a);
+      emit(hb, e2.y, n_first + ob, j, tr, a);
     }
   }
 }
@@ -273,7 +347,7 @@ __global__ void k_fullrate_shift(float2* __restrict__ u, long long u_row, long l
 // 100 MHz + m fs / N), 1 above; the FFT twiddle tables.
 __global__ void k_fr_tables(const double* __restrict__ tec, int t, double nu_ref,
                             double2* __restrict__ H, double2* __restrict__ E,
-                            float2* __restrict__ tw1, float2* __restrict__ tw2) {
+                            float4* __restrict__ tw1, float4* __restrict__ tw2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= FR_N) return;
   double s, c;
@@ -294,13 +368,13 @@ __global__ void k_fr_tables(const double* __restrict__ tec, int t, double nu_ref
     const int k = i / 512, b = i % 512;        // i < 16 * 512 = N
     const int e = (b * k) % FR_N;
     sincospi(2.0 * (double)e / FR_N, &s, &c);
-    tw1[i] = make_float2((float)c, (float)-s);
+    tw1[i] = make_float4((float)c, (float)c, (float)-s, (float)-s);
   }
   if (i < 16 * 32) {
     const int k = i / 32, b = i % 32;
     const int e = (b * k) % 512;
     sincospi(2.0 * (double)e / 512.0, &s, &c);
-    tw2[i] = make_float2((float)c, (float)-s);
+    tw2[i] = make_float4((float)c, (float)c, (float)-s, (float)-s);
   }
 }
 
@@ -330,7 +404,7 @@ __global__ void k_fr_taps(const double2* __restrict__ H, const double2* __restri
 // The taps' spectrum / N in the kernel's order: entry (k, t) is frequency
 // K = k1 + 16 k2 + 256 k + 4096 b (t = 2 (16 k1 + k2) + b).
 __global__ void k_fr_spectrum(const double2* __restrict__ h, const double2* __restrict__ E,
-                              float2* __restrict__ hd) {
+                              float4* __restrict__ hd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= FR_N) return;
   const int k = i / FR_NT, t = i % FR_NT, B = t >> 1, b = t & 1;
@@ -344,7 +418,8 @@ __global__ void k_fr_spectrum(const double2* __restrict__ h, const double2* __re
     m += K;
     if (m >= FR_N) m -= FR_N;
   }
-  hd[i] = make_float2((float)(re / FR_N), (float)(im / FR_N));
+  const float hr = (float)(re / FR_N), hi = (float)(im / FR_N);
+  hd[i] = make_float4(hr, hr, hi, hi);
 }
 
 }  // namespace
@@ -352,7 +427,7 @@ __global__ void k_fr_spectrum(const double2* __restrict__ h, const double2* __re
 long long fullrate_row(const lp_plan& p) { return kFrTaps + p.shape.F * kM; }
 
 size_t fullrate_table_bytes() {
-  return sizeof(float2) * (16 * 512 + 16 * 32);
+  return sizeof(float4) * (16 * 512 + 16 * 32);
 }
 
 cudaError_t init_fullrate_attributes() {
@@ -363,7 +438,7 @@ cudaError_t init_fullrate_attributes() {
 
 cudaError_t launch_fullrate_taps(const lp_plan& p, cudaStream_t s) {
   const Buffers& b = p.buf;
-  float2* tw2 = b.fr_tw + 16 * 512;
+  float4* tw2 = b.fr_tw + 16 * 512;
   for (int t = 0; t < p.shape.Tr; ++t) {
     k_fr_tables<<<FR_N / 256, 256, 0, s>>>(b.tec, t, p.nu_ref, b.fr_H, b.fr_E, b.fr_tw, tw2);
     k_fr_taps<<<kFrTaps / 128, 128, 0, s>>>(b.fr_H, b.fr_E, b.fr_h);
@@ -379,6 +454,7 @@ cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps) {
   a.u = b.ufull;
   a.u_row = fullrate_row(p);
   a.F = p.shape.F;
+  a.nseg = (p.shape.F * kM + FR_V - 1) / FR_V;
   a.hd = b.fr_hd;
   a.tw1 = b.fr_tw;
   a.tw2 = b.fr_tw + 16 * 512;
@@ -395,7 +471,7 @@ cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps) {
   a.pol0 = ps.pol0;
   a.npol = npol;
   const long long FM = p.shape.F * kM;
-  const dim3 grid((unsigned)((FM + FR_V - 1) / FR_V), (unsigned)(p.shape.J() / p.shape.P * npol));
+  const dim3 grid((unsigned)((a.nseg + 1) / 2), (unsigned)(p.shape.J() / p.shape.P * npol));
   if (b.y)
     k_fullrate<true><<<grid, FR_NT, FR_SMEM, s>>>(a);
   else
