@@ -465,7 +465,10 @@ def run_ours(args, rank, world, local_rank):
         line["config"]["fullrate_dedispersion"] = ("2048-tap streaming filter of the synthesised "
                                                    "series (8192-point overlap-save), whole STEC "
                                                    "phase at full rate")
-        line["roofline_fullrate"] = {"bound": "alu", "kernel": "k_fullrate",
+        line["roofline_fullrate"] = {"bound": "alu", "kernel": "k_fullrate" + (
+                                         " (stage time with the series transpose, the per-phase "
+                                         "noise level and the trigger of the LSMR path)"
+                                         if args.lsmr else ""),
                                      "achieved": fr_flop / (fr_ms / 1e3) / 1e12,
                                      "peak": alu_peak, "unit": "TFLOP/s",
                                      "frac": fr_flop / (fr_ms / 1e3) / 1e12 / alu_peak,

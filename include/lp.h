@@ -126,11 +126,14 @@ typedef struct {
                                the central 1536 taps, a delay of 1024 samples: pulses
                                appear one frame later) applies the whole phase; the trigger
                                and the stored time series are those of the filtered
-                               series, the noise level that of the synthesis.  lp_set_tec
-                               refuses STEC values whose group delays over 100-200 MHz
-                               leave 768 samples of the reference delay.  FIR inversion
-                               only; not with chunk_frames, fine_dedisp, stream_blocks or
-                               in a plan group.  0: off */
+                               series, the noise level that of the synthesis.  With
+                               inversion = LP_INV_LSMR (the paper's order) the filter runs
+                               on the recovered series and the LSMR path's per-phase noise
+                               level and trigger then run on the filtered series.
+                               lp_set_tec refuses STEC values whose group delays over
+                               100-200 MHz leave 768 samples of the reference delay.  Not
+                               with chunk_frames, fine_dedisp, stream_blocks or in a plan
+                               group.  0: off */
 } lp_config;
 
 enum { LP_INV_FIR = 0, LP_INV_LSMR = 1 };

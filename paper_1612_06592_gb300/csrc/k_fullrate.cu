@@ -18,7 +18,9 @@
 // block's outputs 6144 s .. 6144 s + 6143 (no wrap-around reaches them).  The
 // envelope |v| is compared with the stream's threshold and triggers are
 // compacted by warp ballots, as in the synthesis kernel; Re v is the stored
-// time series.
+// time series.  After the LSMR inversion (the paper's order) the filter reads
+// the recovered series (k_lsmr_rows lays it out sample-major) and writes v back
+// phase-major for the LSMR path's per-phase noise level and trigger.
 //
 // The FFT: decimation in frequency, radices 16 x 16 x 16 x 2, in place in
 // shared memory.  A thread owns 16 values per pass (a 16-point DFT in
@@ -36,6 +38,7 @@
 // transform, rounded to FP32 once.
 #include "lp_internal.cuh"
 
+#include <algorithm>
 #include <cstdint>
 
 namespace lp {
@@ -177,10 +180,12 @@ struct FullrateArgs {
   const float* theta2;
   const long long* blk;
   float* y;                 // [J][F M] Re v, or null
+  float2* vph;              // LSMR chain: [J][M][F] v phase-major (no trigger here), or null
   TriggerRec* trig;
   unsigned long long* count;
   long long cap;
   float k_sigma;
+  int lag;                  // frames between a block's first output and its first frame
   int P, Tr, pol0, npol;
 };
 
@@ -211,8 +216,9 @@ __device__ __forceinline__ void emit(bool hit, float e2, long long n, int j, int
 }
 
 // One block: segments 2 x and 2 x + 1 of stream y (the second may lie past the
-// block's end: it then reads zeros and emits nothing).
-template <bool STORE_Y>
+// block's end: it then reads zeros and emits nothing).  OUT: 0 trigger, 1
+// trigger and Re v, 2 (LSMR chain) v stored phase-major, no trigger.
+template <int OUT>
 __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ FullrateArgs a) {
   extern __shared__ float4 xs[];
   const int t = threadIdx.x;
@@ -308,15 +314,26 @@ __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ F
   // ---- v[r] = result at position t + 512 r of both segments; positions >= 2048
   // are outputs base + (segment) 6144 + t + 512 (r - 4)
   const long long FM = a.F * kM;
-  const long long n_first = (*a.blk * a.F - kHist) * (long long)kM;
-  const float2 th2 = bc(a.theta2[j]);
-  float* yj = STORE_Y ? a.y + (long long)j * FM : nullptr;
   const long long o0 = base + t - 2048;                      // output index of position t + 512 * 0
+  if constexpr (OUT == 2) {
+    // output o = i M + p goes to row (j, p), column i
+    float2* vj = a.vph + (long long)j * FM;
+#pragma unroll
+    for (int r = 4; r < 16; ++r) {
+      const long long oa = o0 + 512 * r, ob = oa + FR_V;
+      if (oa < FM) vj[(oa & (kM - 1)) * a.F + (oa >> 10)] = make_float2(v[r].re.x, v[r].im.x);
+      if (ob < FM) vj[(ob & (kM - 1)) * a.F + (ob >> 10)] = make_float2(v[r].re.y, v[r].im.y);
+    }
+    return;
+  }
+  const long long n_first = (*a.blk * a.F - a.lag) * (long long)kM;
+  const float2 th2 = bc(a.theta2[j]);
+  float* yj = OUT == 1 ? a.y + (long long)j * FM : nullptr;
 #pragma unroll
   for (int r = 4; r < 16; ++r) {
     const long long oa = o0 + 512 * r, ob = oa + FR_V;
     const bool ina = oa < FM, inb = ob < FM;
-    if (STORE_Y) {
+    if (OUT == 1) {
       if (ina) yj[oa] = v[r].re.x;
       if (inb) yj[ob] = v[r].re.y;
     }
@@ -337,9 +354,35 @@ __global__ void k_fullrate_shift(float2* __restrict__ u, long long u_row, long l
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const long long j = sel_stream(i / kFrTaps, P, pol0, npol);
+  // (rows of at least 2048 block samples: source and destination do not overlap)
   const int l = (int)(i % kFrTaps);
   float2* row = u + j * u_row;
   row[l] = row[FM + l];
+}
+
+// LSMR chain: the recovered series xhat[j][p][i] (phase-major) into the series
+// row of stream j, sample i M + p after the 2048 history samples; 32 x 32
+// tiles through shared memory (reads along frames, writes along phases).
+__global__ void __launch_bounds__(256) k_lsmr_rows(const float2* __restrict__ xhat, long long F,
+                                                   float2* __restrict__ u, long long u_row) {
+  __shared__ float2 tile[32][33];
+  const long long j = blockIdx.z;
+  const long long i0 = (long long)blockIdx.x * 32;            // frames
+  const int p0 = blockIdx.y * 32;                              // phases
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
+  const float2* src = xhat + j * kM * F;
+#pragma unroll
+  for (int q = 0; q < 32; q += 8) {
+    const long long i = i0 + tx;
+    tile[ty + q][tx] = i < F ? src[(long long)(p0 + ty + q) * F + i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2* dst = u + j * u_row + kFrTaps;
+#pragma unroll
+  for (int q = 0; q < 32; q += 8) {
+    const long long i = i0 + ty + q;
+    if (i < F) dst[i * kM + p0 + tx] = tile[tx][ty + q];
+  }
 }
 
 // ---- set-up, FP64 ----------------------------------------------------------
@@ -431,8 +474,9 @@ size_t fullrate_table_bytes() {
 }
 
 cudaError_t init_fullrate_attributes() {
-  cudaError_t e = raise_smem_limit((const void*)k_fullrate<false>, FR_SMEM);
-  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_fullrate<true>, FR_SMEM);
+  cudaError_t e = raise_smem_limit((const void*)k_fullrate<0>, FR_SMEM);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_fullrate<1>, FR_SMEM);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_fullrate<2>, FR_SMEM);
   return e;
 }
 
@@ -461,7 +505,10 @@ cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps) {
   a.theta = b.theta;
   a.theta2 = b.theta2;
   a.blk = b.blk;
-  a.y = b.y;
+  const bool lsmr = p.cfg.inversion == LP_INV_LSMR;
+  a.y = lsmr ? nullptr : b.y;
+  a.vph = lsmr ? b.xhat : nullptr;
+  a.lag = lsmr ? kPrefix : kHist;
   a.trig = b.trig;
   a.count = b.trig_count;
   a.cap = (long long)p.cfg.trigger_cap;
@@ -472,10 +519,22 @@ cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps) {
   a.npol = npol;
   const long long FM = p.shape.F * kM;
   const dim3 grid((unsigned)((a.nseg + 1) / 2), (unsigned)(p.shape.J() / p.shape.P * npol));
-  if (b.y)
-    k_fullrate<true><<<grid, FR_NT, FR_SMEM, s>>>(a);
+  if (a.vph)
+    k_fullrate<2><<<grid, FR_NT, FR_SMEM, s>>>(a);
+  else if (a.y)
+    k_fullrate<1><<<grid, FR_NT, FR_SMEM, s>>>(a);
   else
-    k_fullrate<false><<<grid, FR_NT, FR_SMEM, s>>>(a);
+    k_fullrate<0><<<grid, FR_NT, FR_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lsmr_rows(const lp_plan& p, cudaStream_t s) {
+  const long long F = p.shape.F;
+  for (long long j0 = 0; j0 < p.shape.J(); j0 += 65535) {
+    const unsigned nj = (unsigned)std::min<long long>(65535, p.shape.J() - j0);
+    k_lsmr_rows<<<dim3((unsigned)((F + 31) / 32), kM / 32, nj), 256, 0, s>>>(
+        p.buf.xhat + j0 * kM * F, F, p.buf.ufull + j0 * fullrate_row(p), fullrate_row(p));
+  }
   return cudaGetLastError();
 }
 

@@ -248,10 +248,9 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
     return fail(p, LP_ERR_ARG, "stream_blocks must be 0 or 1");
   if (c->fullrate_dedisp != 0 && c->fullrate_dedisp != 1)
     return fail(p, LP_ERR_ARG, "fullrate_dedisp must be 0 or 1");
-  if (c->fullrate_dedisp &&
-      (c->inversion != LP_INV_FIR || c->chunk_frames != 0 || c->fine_dedisp || c->stream_blocks))
-    return fail(p, LP_ERR_ARG, "fullrate_dedisp needs the FIR inversion and does not combine "
-                "with chunk_frames, fine_dedisp or stream_blocks");
+  if (c->fullrate_dedisp && (c->chunk_frames != 0 || c->fine_dedisp || c->stream_blocks))
+    return fail(p, LP_ERR_ARG, "fullrate_dedisp does not combine with chunk_frames, fine_dedisp "
+                "or stream_blocks");
   if (c->stream_blocks && c->use_graph)
     return fail(p, LP_ERR_ARG, "stream_blocks does not combine with use_graph");
   if (c->chunk_frames != 0) {
@@ -687,16 +686,21 @@ lp_status process_inner(lp_plan* p, const void* x, int64_t pol_stride, void* str
         prof_mark(p, LP_STAGE_FINE, 1, s);
       }
       prof_mark(p, LP_STAGE_SYNTH, 0, s);
-      if (e == cudaSuccess && p->cfg.inversion == LP_INV_LSMR) {
+      const bool lsmr = p->cfg.inversion == LP_INV_LSMR;
+      if (e == cudaSuccess && lsmr) {
         e = lp::launch_lsmr(*p, s);
-        if (e == cudaSuccess) e = lp::launch_lsmr_trigger(*p, s);
+        // the paper's order: the inversion, then the full-rate filter of the
+        // recovered series, then the per-phase noise level and the trigger
+        if (e == cudaSuccess && !p->cfg.fullrate_dedisp) e = lp::launch_lsmr_trigger(*p, s);
       } else if (e == cudaSuccess) {
         e = tune == kTuneSynth ? tune_ippf(p, c, s, tune_ms) : lp::launch_ippf(*p, c, s);
       }
       prof_mark(p, LP_STAGE_SYNTH, 1, s);
       if (p->cfg.fullrate_dedisp) {
         prof_mark(p, LP_STAGE_FULLRATE, 0, s);
+        if (e == cudaSuccess && lsmr) e = lp::launch_lsmr_rows(*p, s);
         if (e == cudaSuccess) e = lp::launch_fullrate(*p, s);
+        if (e == cudaSuccess && lsmr) e = lp::launch_lsmr_trigger(*p, s);
         prof_mark(p, LP_STAGE_FULLRATE, 1, s);
       }
       prof_mark(p, LP_STAGE_SHIFT, 0, s);
@@ -972,7 +976,8 @@ int lp_launches_per_block(const lp_plan* p) {
   const int fine = p->cfg.fine_dedisp ? (int)((rows + 65534) / 65535) : 0;
   if (p->cfg.inversion == LP_INV_LSMR) {  // beamformer, inverse FFT + LSMR + trigger per
     const int nj = (int)((p->shape.J() + 65534) / 65535);   // 65535 streams, sigma, shift
-    return 3 + fine + 3 * nj;
+    // full-rate filter: the series rows (per 65535 streams), the filter, its history shift
+    return 3 + fine + 3 * nj + (p->cfg.fullrate_dedisp ? 2 + nj : 0);
   }
   if (p->fc == 0 || p->fc == p->shape.F) return 4 + fine + (p->cfg.fullrate_dedisp ? 2 : 0);
   return 2 + 3 * (int)(p->shape.F / p->fc);

@@ -124,10 +124,75 @@ def test_fullrate_limits(cuda_lib):
     with pytest.raises(cuda_lib.LPError):
         plan.lp_set_tec(np.array([80.0]))           # group delay beyond 768 samples
     plan.lp_set_tec(np.array([40.0]))
-    for kw in ({"fine_dedisp": True}, {"inversion": "lsmr"}, {"stream_blocks": True,
-                                                               "host_input": True}):
+    for kw in ({"fine_dedisp": True}, {"stream_blocks": True, "host_input": True}):
         with pytest.raises(cuda_lib.LPError):
             make_plan(cuda_lib, 8, 1, 4, 1, 1, 4096, 100, "int8", fullrate_dedisp=True, **kw)
     with pytest.raises(cuda_lib.LPError):
         make_plan(cuda_lib, 8, 1, 4, 1, 1, 4096, 100, "int8", precision="fp16",
                   chunk_frames=2048, fullrate_dedisp=True)
+
+
+def test_lsmr_then_fullrate_matches_oracle(cuda_lib):
+    """The paper's order: the LSMR inversion, then the full-rate filter of the
+    recovered series (both histories carried over two blocks), then the LSMR
+    path's per-phase noise level (running) and trigger on the filtered series,
+    against the oracle composing lsmr_invert, fullrate_filter,
+    lsmr_noise_power and update_sigma2.  Tolerances: the LSMR path's own
+    (1e-5, its iterate's FP32 error dominating the filter's), per-sample
+    factor 8 as there."""
+    import torch
+    S, P, K, B, Tr, F, fb, ks = 8, 1, 12, 2, 1, 512, 200, 3.5
+    blocks, enu, dirs, _ = random_case(55, S, P, K, B, Tr, F, fb, "int8", 2, amp=60)
+    tec = np.array([30.0])
+    plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", inversion="lsmr",
+                     fullrate_dedisp=True, k_sigma=ks)
+    assert plan.lp_launches_per_block() == 9
+    plan.lp_set_weights(enu, dirs)
+    plan.lp_set_tec(tec)
+    nu = O.sky_frequencies(fb, K)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    w = O.geometric_weights(nu, enu, dirs)
+    taps = O.fullrate_taps(tec, nu_ref)
+    h = O.prototype_filter()
+    J = B * Tr * P
+    lsmr_hist = np.zeros((J, O.LSMR_OVERLAP, K), dtype=complex)
+    fr_hist = np.zeros((J, O.FULLRATE_TAPS - 1), dtype=complex)
+    s2 = None
+    tol = 1e-5
+    n_oracle = 0
+    for bi, xb in enumerate(blocks):
+        plan.lp_process_block(torch.from_numpy(xb).cuda())
+        bm = O.beamform(xb[..., 0].astype(np.float64) + 1j * xb[..., 1], w, np.ones((K, Tr)))
+        vs = np.zeros((J, F, O.M), dtype=complex)
+        for b in range(B):
+            j = b * Tr * P
+            lext = np.concatenate([lsmr_hist[j], bm[b, 0, 0].T])
+            x = O.lsmr_invert(lext, fb, h).reshape(-1)
+            lsmr_hist[j] = lext[-O.LSMR_OVERLAP:]
+            uext = np.concatenate([fr_hist[j], x])
+            vs[j] = O.fullrate_filter(uext, taps[0]).reshape(F, O.M)
+            fr_hist[j] = uext[-(O.FULLRATE_TAPS - 1):]
+        pw = np.stack([O.lsmr_noise_power(vs[j]) for j in range(J)])
+        s2 = O.update_sigma2(s2, pw, 0.25, bi == 0)
+        sig = np.sqrt(s2)
+        got = np.stack([plan.lp_get_timeseries(b, 0, 0) for b in range(B)])
+        want = vs.real.reshape(J, -1)
+        assert rel_rms(got, want) < tol
+        assert_samples_close(got, want, np.abs(vs).reshape(J, -1),
+                             np.sqrt(np.mean(sig ** 2, axis=1)), 8 * tol)
+        np.testing.assert_allclose(plan.lp_get_lsmr_sigma(), sig, rtol=10 * tol)
+        n = ((bi * F + np.arange(F) - O.LSMR_OVERLAP)[:, None] * O.M + np.arange(O.M)[None, :])
+        want_trig = set()
+        for j in range(J):
+            hit = (np.abs(vs[j]) > ks * sig[j][None, :]) & (n >= 0)
+            want_trig |= {(j, int(v)) for v in n[hit]}
+        g_trig, _, st = plan.lp_get_triggers()
+        assert st == 0
+        got_trig = {(int(r["stream"]), int(r["n"])) for r in g_trig}
+        first = int(n[0, 0])
+        for (j, nn) in got_trig ^ want_trig:
+            i, p = divmod(nn - first, O.M)
+            th = ks * sig[j, p]
+            assert abs(abs(vs[j, i, p]) - th) <= 10 * tol * th, (j, nn)
+        n_oracle += len(want_trig)
+    assert n_oracle > 0
