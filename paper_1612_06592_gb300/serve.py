@@ -18,8 +18,11 @@ own pipeline on its own CUDA stream and sessions overlap on the device.  Each
 session's triggers come back to the host.  Requests that arrive wait in a
 queue and are admitted at a block boundary as soon as their workspace fits in
 the HBM budget next to the sessions already running and their predicted
-device time fits the time budget; finished sessions free theirs.  The cost
-model of that prediction is measured at start-up (``Server.calibrate``).
+device time fits the time budget; finished sessions free theirs.  Admission
+and retirement run between blocks, after a block's triggers are back: a
+request that arrived by then is set up (plan, workspace, tables) there and
+joins from the next block, so no block waits for another session's set-up.
+The cost model of the prediction is measured at start-up (``Server.calibrate``).
 
 Latency of a block = time from its arrival (the realtime clock of the stream)
 to the moment the last session's triggers for it are on the host.  All compute
@@ -419,6 +422,11 @@ def run(args):
     torch.cuda.synchronize()
     lat, dev_busy, n_sessions, n_out = [], [], [], 0
     qi = 0
+    # requests that arrived before the first block join it
+    while qi < len(reqs) and reqs[qi].arrival <= 0:
+        srv.submit(reqs[qi])
+        qi += 1
+    srv.admit()
     t0 = time.perf_counter()
     for b in range(args.blocks):
         arrival = t0 + b * period if args.realtime else time.perf_counter()
@@ -426,11 +434,6 @@ def run(args):
             dt = arrival - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-        while qi < len(reqs) and reqs[qi].arrival <= b:
-            srv.submit(reqs[qi])
-            qi += 1
-        srv.retire()
-        srv.admit()
         ts = time.perf_counter()
         out = srv.run_block(hosts[b % len(hosts)])
         te = time.perf_counter()
@@ -439,6 +442,14 @@ def run(args):
         dev_busy.append(te - ts)
         n_sessions.append(len(out))
         n_out += sum(len(s.req.beams) * len(s.req.tec) * w.pols for s in srv.active.values())
+        # between blocks, off the latency path: finished sessions leave, and the
+        # requests that have arrived by now are set up (plan, workspace, tables)
+        # to join from the next block
+        while qi < len(reqs) and reqs[qi].arrival <= b:
+            srv.submit(reqs[qi])
+            qi += 1
+        srv.retire()
+        srv.admit()
     wall = time.perf_counter() - t0
     lat_ms = np.array(lat) * 1e3
     res = {

@@ -10,6 +10,8 @@
   the whole block, and the trigger lists on those windows.
 * Stress shape: 48 stations x 488 subbands x 200 beams x 8 trials, chunked
   beam rows replayed from a captured graph, sampled windows of eight streams.
+* Precision block with full-rate de-dispersion: sampled windows of six
+  streams of the filtered series and their triggers.
 """
 
 import numpy as np
@@ -198,3 +200,62 @@ def test_stress_shape_chunked_graph_sampled_parity(cuda_lib):
         assert abs(sig_gpu[j] / sigma - 1) < 1e-5, (b, t, pol)
         _window_checks(ys[(b, t, pol)], x, wts[:, b, :], dd[:, t], pol, w.first_bin, g, windows,
                        sigma, k_sigma * sigma, by_stream.get(j, set()), REL_FP16, TAU_FP16)
+
+
+def test_precision_block_fullrate_sampled_parity(cuda_lib):
+    """The benchmarked block (48 x 488 x 50, 65536 frames, FP16 form) with
+    full-rate de-dispersion: for six streams the filtered series and its
+    triggers on sampled windows (start, middle, end) against the oracle, which
+    synthesises each window's series from two frames earlier (the filter's
+    2047 samples of reach) with stream_window and filters it with
+    fullrate_filter; each stream's noise level from the whole block."""
+    import torch
+    w = synth.PRECISION
+    enu, dirs, tec = synth.make_geometry(w)
+    x = _noise_block(w)
+    k_sigma = 4.5
+    plan = cuda_lib.Plan(w.stations, w.pols, w.subbands, w.beams, len(tec), w.block_len,
+                         input_dtype="int8", precision="fp16", first_bin=w.first_bin,
+                         store_timeseries=True, k_sigma=k_sigma, fullrate_dedisp=True)
+    plan.lp_set_weights(enu, dirs)
+    plan.lp_set_tec(tec)
+    xd = torch.from_numpy(x).cuda()
+    plan.lp_process_block(xd)
+    trig, n, st = plan.lp_get_triggers()
+    assert st == cuda_lib.LP_OK
+    del xd
+    nu = O.sky_frequencies(w.first_bin, w.subbands)
+    nu_ref = 0.5 * (nu[0] + nu[-1])
+    wts = O.geometric_weights(nu, enu, dirs)
+    ones = np.ones(w.subbands, dtype=complex)                 # no per-subband phase
+    g = O.synthesis_filter()
+    h = O.fullrate_taps(tec, nu_ref)[0]
+    F, L = w.block_len, O.FULLRATE_TAPS
+    windows = [(0, 24), (40000, 40024), (F - 24, F)]
+    sig_gpu = plan.lp_get_sigma()
+    by_stream = {}
+    for r in trig:
+        by_stream.setdefault(int(r["stream"]), set()).add(int(r["n"]))
+    for (b, pol) in [(0, 0), (11, 1), (24, 0), (37, 1), (48, 1), (49, 0)]:
+        j = (b * len(tec)) * w.pols + pol
+        sigma = _noise_level(x, wts[:, b:b + 1, :], ones, g, pol, F)[0]
+        assert abs(sig_gpu[j] / sigma - 1) < 1e-5, (b, pol)
+        theta = k_sigma * sigma
+        y = plan.lp_get_timeseries(b, 0, pol)
+        for (m0, m1) in windows:
+            # the window's series and the 2047 samples before it (zero before the start)
+            lo = max(0, m0 - 2)
+            u = O.stream_window(x, wts[:, b, :], ones, pol, w.first_bin, g, lo, m1).reshape(-1)
+            uext = (np.concatenate([np.zeros(L - 1), u]) if m0 == 0
+                    else u[(m0 - lo) * 1024 - (L - 1):])
+            v = O.fullrate_filter(uext, h)
+            assert v.size == (m1 - m0) * 1024
+            yw = y[m0 * 1024:m1 * 1024]
+            assert rel_rms(yw, v.real) < 1e-5
+            assert_samples_close(yw, v.real, np.abs(v), sigma, 2 * REL_FP16)
+            env = np.abs(v)
+            n_first = (m0 - 15) * 1024
+            n_ref, _ = O.find_triggers(env, theta, n_first)
+            g_win = {nn for nn in by_stream.get(j, set()) if n_first <= nn < n_first + env.size}
+            for nn in g_win ^ set(n_ref.tolist()):
+                assert abs(env[nn - n_first] - theta) <= TAU_FP16 * theta
