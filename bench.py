@@ -97,7 +97,8 @@ def parse():
                     help="precision: the 48x488x50 headline block; stress: 200 beams x 8 "
                          "trials x 262144 frames with injected pulses (recall)")
     ap.add_argument("--synth-frames", type=int, default=0,
-                    help="fixed synthesis frames per thread block (0: autotune)")
+                    help="fixed synthesis frames per thread block (0: autotune; -1: the "
+                         "balanced tiling, one block per SM)")
     ap.add_argument("--fine", action="store_true",
                     help="fine (channel-domain) de-dispersion filter on (a separate line, "
                          "not the headline)")
@@ -127,6 +128,11 @@ def bench_workload(args):
         w = dataclasses.replace(w, name=w.name.replace("65536fr", f"{args.frames}fr"),
                                 block_len=args.frames)
     return w
+
+
+def tiling(fpc):
+    """Name of a synthesis tiling: frames per block, or the balanced tiling (0)."""
+    return "balanced (one block per SM)" if fpc == 0 else fpc
 
 
 def gemm_desc(precision, cfgs, index):
@@ -267,7 +273,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_stream = not args.no_e2e and not args.lsmr and not args.graph and not args.fullrate
     plan_kw = dict(input_dtype=w.dtype, precision=args.precision, first_bin=w.first_bin,
                    host_input=not args.no_e2e and not args.lsmr, stream_blocks=e2e_stream,
-                   frames_per_cta=args.synth_frames, fine_dedisp=args.fine,
+                   frames_per_cta=max(0, args.synth_frames), fine_dedisp=args.fine,
                    fullrate_dedisp=args.fullrate,
                    inversion="lsmr" if args.lsmr else "fir", chunk_frames=args.chunk_frames,
                    use_graph=args.graph)
@@ -296,7 +302,7 @@ def run_ours(args, rank, world, local_rank):
     else:
         gemm_best, gemm_ms = plan.lp_plan_autotune_gemm(x)
     if args.synth_frames or args.lsmr:
-        tuned_fpc, tune_ms = args.synth_frames, {}
+        tuned_fpc, tune_ms = max(0, args.synth_frames), {}
     else:
         tuned_fpc, tune_ms = plan.lp_plan_autotune(x)
     plan.lp_profile_enable(not args.graph)
@@ -400,11 +406,11 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": "f16 tensor-core beamformer, f32" if args.precision == "fp16" else "f32",
         "data": "synthetic (seeded rounded-Gaussian int8 station noise)",
-        "config": dict(workload_config(w, args.precision), synth_frames_per_cta=tuned_fpc,
+        "config": dict(workload_config(w, args.precision), synth_frames_per_cta=tiling(tuned_fpc),
                        parallelism=(f"beams sharded over {world} GPUs (ranks own contiguous "
                                     "beam ranges of one block; triggers merged on rank 0)"
                                     if sharded else f"{world} replica(s), one block each"),
-                       autotune_ms={str(k): round(v, 3) for k, v in tune_ms.items()},
+                       autotune_ms={str(tiling(k)): round(v, 3) for k, v in tune_ms.items()},
                        gemm_config=gemm_desc(args.precision, gemm_cfgs, gemm_best),
                        gemm_autotune_ms={gemm_desc(args.precision, gemm_cfgs, gemm_cfgs.index(k)):
                                          round(v, 3) for k, v in gemm_ms.items()}),
@@ -590,7 +596,8 @@ def run_stress(args):
         "pulses": len(plist), "recall": float(found.mean()),
         "recall_by_snr": {f"{a}-{int(b)}": float(found[(snrs >= a) & (snrs < b)].mean())
                           for a, b in bins},
-        "synth_frames_per_cta": tuned_fpc, "autotune_ms_per_chunk": {str(k): round(v, 3) for k, v in tune_ms.items()},
+        "synth_frames_per_cta": tiling(tuned_fpc),
+        "autotune_ms_per_chunk": {str(tiling(k)): round(v, 3) for k, v in tune_ms.items()},
         "gemm_config": gemm_desc("fp16", gemm_cfgs, gemm_best),
         "gemm_autotune_ms_per_chunk": {gemm_desc("fp16", gemm_cfgs, gemm_cfgs.index(k)): round(v, 3)
                                        for k, v in gemm_ms.items()},
@@ -681,7 +688,7 @@ def run_two_stage(args):
         "config": dict(workload_config(w, "fp16"), workload="two-stage-48st-8grp-488sb-50bm-"
                        f"{w.block_len}fr", groups=G, group_sizes=np.bincount(grp).tolist(),
                        preliminary_direction="pointing centre", transport="complex int16",
-                       scale=scale, synth_frames_per_cta=tuned_fpc,
+                       scale=scale, synth_frames_per_cta=tiling(tuned_fpc),
                        gemm_config=gemm_desc("fp16", gemm_cfgs, gemm_best),
                        gemm_autotune_ms={gemm_desc("fp16", gemm_cfgs, gemm_cfgs.index(k)):
                                          round(v, 3) for k, v in gemm_ms.items()}),

@@ -78,7 +78,9 @@ typedef struct {
   int32_t store_timeseries; /* 1: keep y = Re u of every stream for lp_get_timeseries */
   int32_t host_input;       /* 1: reserve a device copy of one block so that
                                lp_process_block accepts host pointers            */
-  int32_t frames_per_cta;   /* synthesis frames per thread block; 0 = automatic */
+  int32_t frames_per_cta;   /* synthesis frames per thread block (a positive multiple of 8);
+                               0 = balanced: one block per SM, each walking an equal,
+                               contiguous range of the streams' frames */
   int32_t use_graph;        /* 1: lp_process_block replays a captured CUDA graph of the
                                block's launches (needs a non-default stream; recaptured
                                when the input address or pol stride changes; not with
@@ -269,9 +271,9 @@ lp_status lp_reset_stream(lp_plan* plan, void* stream);
 /* Autotuner (the paper has no counterpart; it tunes the synthesis kernel's
  * tiling): processes block x exactly as lp_process_block does, and inside that
  * block times the synthesis kernel for frames_per_cta in {64, 128, ..., 2048}
- * (<= the chunk length) on the same beam rows, keeps the fastest for later
- * blocks and returns it in *best (ms per candidate in ms_out[6] when not NULL,
- * 0 for skipped candidates).  The outputs do not depend on the tiling, so the
+ * (<= the chunk length) and the balanced tiling (0) on the same beam rows,
+ * keeps the fastest for later blocks and returns it in *best (ms per candidate
+ * in ms_out[7] when not NULL, in that order, 0 for skipped candidates).  The outputs do not depend on the tiling, so the
  * block's results are those of lp_process_block.  Synchronises `stream`;
  * drops a captured graph.  Device input only (contiguous layout). */
 lp_status lp_plan_autotune(lp_plan* plan, const void* x, void* stream, int32_t* best,

@@ -34,10 +34,14 @@
 // arrive, FIR warps wait) for ring buffer s, and "free[s]" (the reverse): ring
 // buffer s has been read, and stage buffer s holds the bins of the batch after
 // next, which the FIR warps copy (16-byte cp.async) while they filter.
-// The first 16 frames of a run only fill the FIR history (16/frames_per_cta of
-// extra inverse DFTs).  FP32 throughout.
+// The first 16 frames of a run only fill the FIR history (16 extra inverse DFTs
+// per run).  Runs: either frames_per_cta frames of one stream per block, or the
+// balanced tiling (one block per SM walking an equal contiguous range of the
+// streams' frames, a piece per stream it crosses), which leaves no tail wave and
+// pays the 16 history frames once per piece.  FP32 throughout.
 #include "lp_internal.cuh"
 
+#include <algorithm>
 #include <cstdint>
 
 namespace lp {
@@ -167,6 +171,13 @@ __device__ __forceinline__ void dft16_stages(CP (&v)[16]) {
       for (int j = 0; j < span; ++j) bfly_rt(v[start + j], v[start + j + span], j * (16 / span));
     }
   }
+}
+
+int ippf_num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 152;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -491,150 +502,185 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
   __shared__ int s_live_lim;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int pi = 0;
-  if constexpr (GROUP)
-    while (pi + 1 < a.n && (int)blockIdx.y >= a.pl[pi].stream_end) ++pi;
-  const IppfPlan& pl = a.pl[GROUP ? pi : 0];
-  const int jj = (int)blockIdx.y - (GROUP && pi ? a.pl[pi - 1].stream_end : 0);
-  const int j = (int)sel_stream(jj, pl.P, a.pol0, a.npol);
-  const int K = pl.K, first_bin = pl.first_bin, frames_per_cta = a.frames_per_cta;
-  const long long F = a.F, row = a.row;
-  const float2* __restrict__ beams = pl.beams;
-  const float4* __restrict__ tw = pl.tw;
-  const long long m0 = (long long)blockIdx.x * frames_per_cta;
-  const long long m1 = min((long long)(m0 + frames_per_cta), (long long)(F));
-  const int nout = (int)(m1 - m0);
-  const int nfr = nout + kPrefix;          // frames run through the inverse DFT
-  const int nbatch = (nfr + FB - 1) / FB;
-
   if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
-  if (tid == 0) sinfo = StreamInfo{j, pl.theta[j] / pl.k_sigma, &pl, 0, 0, 0, 0};
-  // bins outside the selection stay zero for the whole run
-  for (int i = tid; i < 2 * NPAIR * SPAIR; i += NT) stage[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  // the FIR threads stage the bins (thread tid - NDFT); batches 0 and 1 now
-  const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
-  const Stager stg = make_stager(brow, K, first_bin, row, tid - NDFT);
-  // a pair is copied when both its frames are in the run and inside the row
-  const int live_lim = (int)min((long long)nfr, row - m0);
-  if (warp >= NDFT / 32) {
-    stage_batch(stg, stage, stg.f + 1 < live_lim, 0);
-    stage_batch(stg, stage + NPAIR * SPAIR, FB + stg.f + 1 < live_lim, FB);
-    cp_async_wait_all();
-  }
+  // The block's work, in the launch's (stream, frame) space: frames_per_cta
+  // > 0: run blockIdx.x of frames_per_cta frames of stream blockIdx.y;
+  // frames_per_cta == 0 (balanced): one contiguous range of every stream's
+  // frames in turn, split evenly over the grid in multiples of 8 frames, so
+  // that every block does the same work and a block's pieces are at most a few
+  // streams' runs (each piece pays the 16 history frames once).
+  const long long F = a.F, row = a.row;
+  // the range walked so far lives in shared memory (no registers held across
+  // the roles' loops): [s_pos, s_end)
+  __shared__ long long s_pos, s_end;
   if (tid == 0) {
-    s_brow = brow;
-    s_live_lim = live_lim;
+    long long pos, end;
+    if (a.frames_per_cta > 0) {
+      pos = (long long)blockIdx.y * F + (long long)blockIdx.x * a.frames_per_cta;
+      end = min(pos + a.frames_per_cta, ((long long)blockIdx.y + 1) * F);
+    } else {
+      const long long total = (long long)a.nstreams * F;
+      const long long per = ((total + gridDim.x - 1) / gridDim.x + FB - 1) / FB * FB;
+      pos = min(total, (long long)blockIdx.x * per);
+      end = min(total, pos + per);
+    }
+    s_pos = pos;
+    s_end = end;
   }
   __syncthreads();
+  for (;;) {
+    const long long pos = s_pos, end = s_end;
+    if (pos >= end) break;
+    const int sid = (int)(pos / F);            // launch stream of this piece
+    const long long m0 = pos % F;
+    const long long m1 = min(F, m0 + (end - pos));
+    int pi = 0;
+    if constexpr (GROUP)
+      while (pi + 1 < a.n && sid >= a.pl[pi].stream_end) ++pi;
+    const IppfPlan& pl = a.pl[GROUP ? pi : 0];
+    const int jj = sid - (GROUP && pi ? a.pl[pi - 1].stream_end : 0);
+    const int j = (int)sel_stream(jj, pl.P, a.pol0, a.npol);
+    const int K = pl.K, first_bin = pl.first_bin;
+    const float2* __restrict__ beams = pl.beams;
+    const float4* __restrict__ tw = pl.tw;
+    const int nout = (int)(m1 - m0);
+    const int nfr = nout + kPrefix;          // frames run through the inverse DFT
+    const int nbatch = (nfr + FB - 1) / FB;
 
-  if (warp < NDFT / 32) {
-    // ===================== DFT role =====================
-    const int pr = warp >> 1, h = warp & 1;     // frame pair of the batch, output parity
-    for (int bi = 0; bi < nbatch; ++bi) {
-      const int s = bi & 1;
-      // ring buffer s read by the FIR role, stage buffer s loaded with batch bi
-      if (bi >= 2) bar_sync(BAR_FREE + s, NT);
-      float2* slot = ring + (s * FB + 2 * pr) * kM;
-      const float4* st = stage + s * NPAIR * SPAIR + pr * SPAIR + lane;
-      if (h)
-        pair_dft<1>(slot, st, tw, lane, BAR_PAIR + pr);
-      else
-        pair_dft<0>(slot, st, tw, lane, BAR_PAIR + pr);
-      bar_arrive(BAR_READY + s, NT);
+    if (tid == 0) sinfo = StreamInfo{j, pl.theta[j] / pl.k_sigma, &pl, 0, 0, 0, 0};
+    // bins outside the selection stay zero for the whole piece
+    for (int i = tid; i < 2 * NPAIR * SPAIR; i += NT) stage[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    if (tid == 0) s_pos = pos + (m1 - m0);     // every thread has read s_pos: the next piece
+    // the FIR threads stage the bins (thread tid - NDFT); batches 0 and 1 now
+    const float2* brow = beams + (long long)j * K * row + m0;   // position of frame m0-16
+    const Stager stg = make_stager(brow, K, first_bin, row, tid - NDFT);
+    // a pair is copied when both its frames are in the run and inside the row
+    const int live_lim = (int)min((long long)nfr, row - m0);
+    if (warp >= NDFT / 32) {
+      stage_batch(stg, stage, stg.f + 1 < live_lim, 0);
+      stage_batch(stg, stage + NPAIR * SPAIR, FB + stg.f + 1 < live_lim, FB);
+      cp_async_wait_all();
     }
-  } else {
-    // ===================== FIR role =====================
-    // thread ft owns the butterfly partners (ft, ft + 512) and (511 - ft, 1023 - ft)
-    const int ft = tid - NDFT;
-    const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 256u * ((warp - 8) >> 2);
-    // taps (g, g) of the four phases into tensor memory
-#pragma unroll 1
-    for (int ph = 0; ph < 4; ++ph) {
-      const int p = (ph & 2 ? kM / 2 - 1 - ft : ft) + (ph & 1 ? kM / 2 : 0);
-      float tq[32];
-#pragma unroll
-      for (int t = 0; t < kTaps; ++t) {
-        const float gt = pl.g[t * kM + p];
-        tq[2 * t] = gt;
-        tq[2 * t + 1] = gt;
+    if (tid == 0) {
+      s_brow = brow;
+      s_live_lim = live_lim;
+    }
+    __syncthreads();
+
+    if (warp < NDFT / 32) {
+      // ===================== DFT role =====================
+      const int pr = warp >> 1, h = warp & 1;     // frame pair of the batch, output parity
+      for (int bi = 0; bi < nbatch; ++bi) {
+        const int s = bi & 1;
+        // ring buffer s read by the FIR role, stage buffer s loaded with batch bi
+        if (bi >= 2) bar_sync(BAR_FREE + s, NT);
+        float2* slot = ring + (s * FB + 2 * pr) * kM;
+        const float4* st = stage + s * NPAIR * SPAIR + pr * SPAIR + lane;
+        if (h)
+          pair_dft<1>(slot, st, tw, lane, BAR_PAIR + pr);
+        else
+          pair_dft<0>(slot, st, tw, lane, BAR_PAIR + pr);
+        bar_arrive(BAR_READY + s, NT);
       }
-      tmem_st16(tbase + TC_TAPS + 32 * ph, reinterpret_cast<const float(&)[16]>(tq[0]));
-      tmem_st16(tbase + TC_TAPS + 32 * ph + 16, reinterpret_cast<const float(&)[16]>(tq[16]));
-    }
-    tmem_wait_st();
-    FirCtx c;
-    c.th2 = pl.theta2[j];
-    const long long F_total = a.F_total, f_base = a.f_base;
-    // this launch covers block frames [f_base, f_base + F) (one chunk, or the block)
-    float* yj = OUT == 1 && pl.y ? pl.y + ((long long)j * F_total + f_base) * kM : nullptr;
-    // full-rate mode: the series row of the stream (history first)
-    float2* uj = OUT == 2 ? pl.u + (long long)j * pl.u_row + kFrTaps + f_base * kM : nullptr;
-    // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
-    // m < 15 of the first block) never trigger
-    const long long bidx = *pl.blk;
-    const long long n_first = (bidx * F_total + f_base - kHist) * (long long)kM;
-    const int frame_min_trigger = (bidx == 0 && f_base == 0) ? kHist : 0;
-    // run row r (frame m0 - 16 + r) is an output for r in [16, nfr) and may
-    // trigger for r >= r_trig
-    const int r_trig = (int)max((long long)kPrefix, frame_min_trigger + kPrefix - m0);
-    if (tid == NDFT) {   // read by the trigger path after the first ready barrier
-      sinfo.nfr = nfr;
-      sinfo.r_trig = r_trig;
-      sinfo.n_first = n_first;
-      sinfo.m0 = m0;
-    }
-    for (int bi = 0; bi < nbatch; ++bi) {
-      const int s = bi & 1, r0 = bi * FB;
-      bar_sync(BAR_READY + s, NT);       // ring buffer s holds batch bi
-      // stage buffer s is free again: bins of batch bi + 2
-      if (bi + 2 < nbatch) {
-        const Stager st = make_stager(s_brow, K, first_bin, row, ft);
-        stage_batch(st, stage + s * NPAIR * SPAIR, (bi + 2) * FB + st.f + 1 < s_live_lim,
-                    (bi + 2) * FB);
-      }
-      const float4* zr = reinterpret_cast<const float4*>(ring + s * FB * kM);
-      const bool outputs = r0 >= kPrefix;
-      c.ymask = frame_bits(kPrefix - r0, nfr - r0);
-      const long long m_row0 = m0 - kPrefix + r0;             // frame of batch row 0
-      c.yrow = yj ? yj + m_row0 * kM : nullptr;
-      if constexpr (OUT == 2) c.urow = uj + m_row0 * kM;
-#pragma unroll 1
-      for (int bp = 0; bp < 2; ++bp) {
-        const int pb = bp ? kM / 2 - 1 - ft : ft;
-        // last butterfly: z[pb] = a + b, z[pb + 512] = a - b, for both frames of
-        // each pair (granule = re_a, re_b, im_a, im_b)
-        float2 za[FB], zb[FB];
-#pragma unroll
-        for (int q = 0; q < FB / 2; ++q) {
-          const float4 a = zr[q * kM + pb], b = zr[q * kM + pb + kM / 2];
-          za[2 * q] = make_float2(a.x + b.x, a.z + b.z);
-          za[2 * q + 1] = make_float2(a.y + b.y, a.w + b.w);
-          zb[2 * q] = make_float2(a.x - b.x, a.z - b.z);
-          zb[2 * q + 1] = make_float2(a.y - b.y, a.w - b.w);
+    } else {
+      // ===================== FIR role =====================
+      // thread ft owns the butterfly partners (ft, ft + 512) and (511 - ft, 1023 - ft)
+      const int ft = tid - NDFT;
+      const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 256u * ((warp - 8) >> 2);
+      // taps (g, g) of the four phases into tensor memory
+  #pragma unroll 1
+      for (int ph = 0; ph < 4; ++ph) {
+        const int p = (ph & 2 ? kM / 2 - 1 - ft : ft) + (ph & 1 ? kM / 2 : 0);
+        float tq[32];
+  #pragma unroll
+        for (int t = 0; t < kTaps; ++t) {
+          const float gt = pl.g[t * kM + p];
+          tq[2 * t] = gt;
+          tq[2 * t + 1] = gt;
         }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int ph = 2 * bp + h;
-          float tq[32];
-          tmem_ld32(tbase + TC_TAPS + 32 * ph, tq);
-          tmem_wait_ld();
-          float2 gq[kTaps];
-#pragma unroll
-          for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
-          fir_one<OUT>(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0,
-                       outputs, c, &sinfo);
+        tmem_st16(tbase + TC_TAPS + 32 * ph, reinterpret_cast<const float(&)[16]>(tq[0]));
+        tmem_st16(tbase + TC_TAPS + 32 * ph + 16, reinterpret_cast<const float(&)[16]>(tq[16]));
+      }
+      tmem_wait_st();
+      FirCtx c;
+      c.th2 = pl.theta2[j];
+      const long long F_total = a.F_total, f_base = a.f_base;
+      // this launch covers block frames [f_base, f_base + F) (one chunk, or the block)
+      float* yj = OUT == 1 && pl.y ? pl.y + ((long long)j * F_total + f_base) * kM : nullptr;
+      // full-rate mode: the series row of the stream (history first)
+      float2* uj = OUT == 2 ? pl.u + (long long)j * pl.u_row + kFrTaps + f_base * kM : nullptr;
+      // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
+      // m < 15 of the first block) never trigger
+      const long long bidx = *pl.blk;
+      const long long n_first = (bidx * F_total + f_base - kHist) * (long long)kM;
+      const int frame_min_trigger = (bidx == 0 && f_base == 0) ? kHist : 0;
+      // run row r (frame m0 - 16 + r) is an output for r in [16, nfr) and may
+      // trigger for r >= r_trig
+      const int r_trig = (int)max((long long)kPrefix, frame_min_trigger + kPrefix - m0);
+      if (tid == NDFT) {   // read by the trigger path after the first ready barrier
+        sinfo.nfr = nfr;
+        sinfo.r_trig = r_trig;
+        sinfo.n_first = n_first;
+        sinfo.m0 = m0;
+      }
+      for (int bi = 0; bi < nbatch; ++bi) {
+        const int s = bi & 1, r0 = bi * FB;
+        bar_sync(BAR_READY + s, NT);       // ring buffer s holds batch bi
+        // stage buffer s is free again: bins of batch bi + 2
+        if (bi + 2 < nbatch) {
+          const Stager st = make_stager(s_brow, K, first_bin, row, ft);
+          stage_batch(st, stage + s * NPAIR * SPAIR, (bi + 2) * FB + st.f + 1 < s_live_lim,
+                      (bi + 2) * FB);
+        }
+        const float4* zr = reinterpret_cast<const float4*>(ring + s * FB * kM);
+        const bool outputs = r0 >= kPrefix;
+        c.ymask = frame_bits(kPrefix - r0, nfr - r0);
+        const long long m_row0 = m0 - kPrefix + r0;             // frame of batch row 0
+        c.yrow = yj ? yj + m_row0 * kM : nullptr;
+        if constexpr (OUT == 2) c.urow = uj + m_row0 * kM;
+  #pragma unroll 1
+        for (int bp = 0; bp < 2; ++bp) {
+          const int pb = bp ? kM / 2 - 1 - ft : ft;
+          // last butterfly: z[pb] = a + b, z[pb + 512] = a - b, for both frames of
+          // each pair (granule = re_a, re_b, im_a, im_b)
+          float2 za[FB], zb[FB];
+  #pragma unroll
+          for (int q = 0; q < FB / 2; ++q) {
+            const float4 a = zr[q * kM + pb], b = zr[q * kM + pb + kM / 2];
+            za[2 * q] = make_float2(a.x + b.x, a.z + b.z);
+            za[2 * q + 1] = make_float2(a.y + b.y, a.w + b.w);
+            zb[2 * q] = make_float2(a.x - b.x, a.z - b.z);
+            zb[2 * q + 1] = make_float2(a.y - b.y, a.w - b.w);
+          }
+  #pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int ph = 2 * bp + h;
+            float tq[32];
+            tmem_ld32(tbase + TC_TAPS + 32 * ph, tq);
+            tmem_wait_ld();
+            float2 gq[kTaps];
+  #pragma unroll
+            for (int t = 0; t < kTaps; ++t) gq[t] = make_float2(tq[2 * t], tq[2 * t + 1]);
+            fir_one<OUT>(gq, tbase + TC_HIST + 32 * ph, h ? zb : za, pb + h * (kM / 2), r0,
+                         outputs, c, &sinfo);
+          }
+        }
+        tmem_wait_st();                    // history slots written before the next batch reads them
+        if (bi + 2 < nbatch) {
+          cp_async_wait_all();             // this thread's copies of batch bi + 2 landed
+          bar_arrive(BAR_FREE + s, NT);
         }
       }
-      tmem_wait_st();                    // history slots written before the next batch reads them
-      if (bi + 2 < nbatch) {
-        cp_async_wait_all();             // this thread's copies of batch bi + 2 landed
-        bar_arrive(BAR_FREE + s, NT);
-      }
     }
+    // both roles are done with the ring, the stage buffers and sinfo
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
   tc_fence_before();
   __syncthreads();
@@ -704,13 +750,6 @@ size_t ippf_smem_bytes() {
 cudaError_t init_f32_attributes(const Shape& sh);
 cudaError_t init_tc_attributes(const Shape& sh);
 
-int ippf_default_frames_per_cta(const Shape& sh) {
-  // enough blocks for several waves on 152 SMs, few history frames per block
-  long long fpc = 512;
-  while (fpc > 64 && (long long)sh.J() * ((sh.F + fpc - 1) / fpc) < 152LL * 8) fpc /= 2;
-  return (int)fpc;
-}
-
 cudaError_t init_ippf_attributes() {
   const void* k[5] = {(const void*)k_ippf<false, 0>, (const void*)k_ippf<false, 1>,
                       (const void*)k_ippf<false, 2>, (const void*)k_ippf<true, 0>,
@@ -763,7 +802,12 @@ cudaError_t launch_ippf_plans(const lp_plan* const* plans, int n, const Chunk& c
     streams += plans[i]->shape.J() / plans[i]->shape.P * npol;
     a.pl[i].stream_end = streams;
   }
-  const dim3 grid((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)streams);
+  a.nstreams = streams;
+  // balanced tiling (frames_per_cta 0): one block per SM (one fits), or one per
+  // 8 frames of work if there is less
+  const long long work8 = ((long long)streams * c.nf + FB - 1) / FB;
+  const dim3 grid = fpc > 0 ? dim3((unsigned)((c.nf + fpc - 1) / fpc), (unsigned)streams)
+                            : dim3((unsigned)std::min<long long>(ippf_num_sms(), work8), 1u);
   if (n == 1) {
     IppfArgsN<1> a1;
     a1.F = a.F;
@@ -771,6 +815,7 @@ cudaError_t launch_ippf_plans(const lp_plan* const* plans, int n, const Chunk& c
     a1.F_total = a.F_total;
     a1.f_base = a.f_base;
     a1.frames_per_cta = a.frames_per_cta;
+    a1.nstreams = a.nstreams;
     a1.pol0 = a.pol0;
     a1.npol = a.npol;
     a1.n = 1;

@@ -263,7 +263,7 @@ lp_status lp_plan_configure(lp_plan* p, const lp_config* c) {
   }
   p->cfg = *c;
   p->fc = c->chunk_frames && c->chunk_frames < sh.F ? c->chunk_frames : sh.F;
-  p->frames_per_cta = c->frames_per_cta ? c->frames_per_cta : lp::ippf_default_frames_per_cta(sh);
+  p->frames_per_cta = c->frames_per_cta;      // 0: the balanced tiling
   p->n_ftiles_bf = c->precision == LP_PREC_FP16
                        ? lp::beamform_tc_partials(sh.F)
                        : (int)((sh.F + lp::beamform_f32_frame_tile() - 1) /
@@ -439,9 +439,10 @@ cudaError_t tune_launch(int n, cudaStream_t s, Set&& set, Launch&& launch, doubl
 // candidate reruns the same launch on the same beam rows (before the history
 // shift).
 cudaError_t tune_ippf(lp_plan* p, const lp::Chunk& c, cudaStream_t s, double* ms_out) {
-  static const int cand[6] = {64, 128, 256, 512, 1024, 2048};
+  // runs of 64 .. 2048 frames per block, and the balanced tiling (0)
+  static const int cand[7] = {64, 128, 256, 512, 1024, 2048, 0};
   int best = -1;
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 7; ++i)
     if (cand[i] == p->frames_per_cta) best = i;
   const int keep = p->frames_per_cta;
   auto set = [&](int i) {
@@ -457,7 +458,7 @@ cudaError_t tune_ippf(lp_plan* p, const lp::Chunk& c, cudaStream_t s, double* ms
     cudaError_t e = cudaMemsetAsync(p->buf.trig_count, 0, sizeof(unsigned long long), s);
     return e == cudaSuccess ? lp::launch_ippf(*p, c, s) : e;
   };
-  return tune_launch(6, s, set, launch, ms_out, &best);
+  return tune_launch(7, s, set, launch, ms_out, &best);
 }
 
 // Beamformer launch over chunk c while timing the configurations (GEMM

@@ -135,7 +135,9 @@ struct IppfPlan {
 template <int N>
 struct IppfArgsN {
   long long F, row, F_total, f_base;   // frames of the launch, row length, block frames, offset
-  int frames_per_cta, pol0, npol, n;
+  int frames_per_cta;                  // > 0: runs of this many frames; 0: balanced tiling
+  int nstreams;                        // launch streams (all plans)
+  int pol0, npol, n;
   IppfPlan pl[N];
 };
 using IppfArgs = IppfArgsN<kMaxGroup>;
@@ -207,7 +209,7 @@ struct lp_plan {
   long long block_index = 0;
   cudaStream_t last_stream = nullptr;
   int n_ftiles_bf = 0;     // frame tiles of the beamformer (power partials)
-  int frames_per_cta = 0;  // synthesis tiling
+  int frames_per_cta = 0;  // synthesis tiling: frames per block, 0 = balanced (one block per SM)
   double nu_ref = 0;
   std::string err;
   // stage timing (lp_profile_enable): event pairs per recorded block, one per
@@ -313,7 +315,6 @@ int beamform_gemm_configs(const lp_plan& p, int* desc, int max);
 int beamform_tc_frame_tile();
 int beamform_tc_partials(long long F);
 size_t beamform_tc_weight_bytes(const Shape& sh);
-int ippf_default_frames_per_cta(const Shape& sh);
 
 }  // namespace lp
 

@@ -327,11 +327,11 @@ class Plan:
         """Process block x while picking the synthesis tiling by timing; returns
         (frames_per_cta, {candidate: ms})."""
         best = ctypes.c_int32()
-        ms = np.zeros(6, dtype=np.float64)
+        ms = np.zeros(7, dtype=np.float64)
         self.blocks += 1
         self._check(_lib.lp_plan_autotune(self._h, _ptr(x), _stream_ptr(stream),
                                           ctypes.byref(best), ms.ctypes.data), "lp_plan_autotune")
-        cand = (64, 128, 256, 512, 1024, 2048)
+        cand = (64, 128, 256, 512, 1024, 2048, 0)       # 0: the balanced tiling
         return best.value, {c: m for c, m in zip(cand, ms.tolist()) if m > 0}
 
     MAX_GEMM_CONFIGS = 8

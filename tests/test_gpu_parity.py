@@ -217,3 +217,32 @@ def test_bad_arguments_on_device(cuda_lib):
     plan.lp_process_block(x)
     trig, n, st = plan.lp_get_triggers()
     assert n == 0 and st == cuda_lib.LP_OK
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_balanced_tiling_equals_fixed_runs(cuda_lib, precision):
+    """The balanced synthesis tiling (one block per SM walking an equal range of
+    the streams' frames; here 10 streams x 1000 frames in ranges of 72 frames,
+    so ranges cross stream boundaries) gives the time series, noise levels and
+    triggers of fixed 64-frame runs bit for bit, over two blocks."""
+    import torch
+    S, P, K, B, Tr, F, fb = 8, 2, 20, 5, 1, 1000, 140
+    blocks, enu, dirs, tec = random_case(71, S, P, K, B, Tr, F, fb, "int8", 2, amp=60)
+    plans = [make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision=precision,
+                       store_timeseries=True, k_sigma=3.5, frames_per_cta=fpc)
+             for fpc in (0, 64)]
+    for p in plans:
+        p.lp_set_weights(enu, dirs)
+        p.lp_set_tec(tec)
+    for xb in blocks:
+        xd = torch.from_numpy(xb).cuda()
+        res = []
+        for p in plans:
+            p.lp_process_block(xd)
+            ys = np.stack([p.lp_get_timeseries(b, 0, pol) for b in range(B) for pol in range(P)])
+            res.append((ys, p.lp_get_sigma().copy(), p.lp_get_triggers()[0]))
+        (ya, sa, ta), (yb, sb, tb) = res
+        np.testing.assert_array_equal(ya, yb)
+        np.testing.assert_array_equal(sa, sb)
+        np.testing.assert_array_equal(ta, tb)
+        assert len(ta) > 0
