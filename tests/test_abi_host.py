@@ -38,6 +38,7 @@ def test_struct_layouts(lib):
     assert lib.TRIGGER_DTYPE.itemsize == 32
     assert ctypes.sizeof(lib.lp_config) == 96
     assert lib.lp_config.stream_blocks.offset == 88
+    assert lib.lp_config.fullrate_dedisp.offset == 92
 
 
 def _create(lib, *shape):
@@ -197,12 +198,40 @@ def test_fine_and_lsmr_options_validate_and_size_the_workspace(lib):
     assert st == lib.LP_ERR_ARG
 
 
+def test_fullrate_options_validate_and_size_the_workspace(lib):
+    """Full-rate de-dispersion: the series rows (2048 history samples, then the
+    block) per stream, the taps' spectrum per trial as (re, re, im, im), the
+    FFT twiddles and the FP64 set-up scratch; refused with chunks, the fine
+    filter and streaming blocks."""
+    S, P, K, B, Tr, F = 6, 2, 16, 2, 3, 512
+    shape = (S, P, K, B, Tr, F)
+    J = B * Tr * P
+    st, base, _ = _workspace(lib, shape)
+    assert st == lib.LP_OK
+    st, full, _ = _workspace(lib, shape, fullrate_dedisp=1)
+    assert st == lib.LP_OK
+    extra = (J * (2048 + F * 1024) * 8 + Tr * 8192 * 16 + (16 * 512 + 16 * 32) * 16
+             + 2048 * 16 + 2 * 8192 * 16)
+    assert 0 <= full - base - extra < 7 * 256
+    st, _, _ = _workspace(lib, shape, fullrate_dedisp=1, inversion=lib.LP_INV_LSMR)
+    assert st == lib.LP_OK
+    for bad in [dict(fullrate_dedisp=2), dict(fullrate_dedisp=1, fine_dedisp=1),
+                dict(fullrate_dedisp=1, precision=lib.LP_PREC_FP16, chunk_frames=2048),
+                dict(fullrate_dedisp=1, host_input=1, stream_blocks=1)]:
+        st, _, err = _workspace(lib, (8, 1, 4, 1, 1, 4096), **bad)
+        assert st == lib.LP_ERR_ARG, bad
+        assert err
+
+
 def test_launch_counts_of_the_paths(lib):
     """lp_launches_per_block is host arithmetic: 4 kernels for a device block,
-    one more with the fine filter, six with the LSMR inversion."""
+    one more with the fine filter, six with the LSMR inversion, two more with
+    the full-rate filter (three after the LSMR inversion: the series rows)."""
     for fields, want in [({}, 4), ({"fine_dedisp": 1}, 5),
                          ({"inversion": lib.LP_INV_LSMR}, 6),
-                         ({"inversion": lib.LP_INV_LSMR, "fine_dedisp": 1}, 7)]:
+                         ({"inversion": lib.LP_INV_LSMR, "fine_dedisp": 1}, 7),
+                         ({"fullrate_dedisp": 1}, 6),
+                         ({"inversion": lib.LP_INV_LSMR, "fullrate_dedisp": 1}, 9)]:
         st, h = _create(lib, 6, 2, 16, 2, 1, 512)
         c = lib.config_default()
         c.first_bin = 100
