@@ -80,6 +80,8 @@ __device__ __forceinline__ CP cmulc(CP a, float4 w) {
   const float2 c = make_float2(w.x, w.y), s = make_float2(w.z, w.w);
   return CP{fma2(a.re, c, mul2(a.im, s)), fma2(a.im, c, mul2(a.re, make_float2(-s.x, -s.y)))};
 }
+// the factor c + i s stored as (c, s), widened to the packed pairs
+__device__ __forceinline__ float4 wide(float2 w) { return make_float4(w.x, w.x, w.y, w.y); }
 __device__ __forceinline__ CP cmul_const(CP a, float c, float s) {    // a * (c + i s)
   return CP{fma2(a.re, bc(c), mul2(a.im, bc(-s))), fma2(a.re, bc(s), mul2(a.im, bc(c)))};
 }
@@ -173,9 +175,9 @@ struct FullrateArgs {
   long long u_row;
   long long F;              // frames of the block
   long long nseg;           // segments per stream
-  const float4* hd;         // [Tr][16][512]: taps' spectrum / N as (re, re, im, im)
-  const float4* tw1;        // [16][512] exp(-2 pi i b k / 8192) as (c, c, s, s)
-  const float4* tw2;        // [16][32]  exp(-2 pi i b k / 512)
+  const float2* hd;         // [Tr][16][512]: taps' spectrum / N as (re, im)
+  const float2* tw1;        // [16][512] exp(-2 pi i b k / 8192) as (c, s)
+  const float2* tw2;        // [16][32]  exp(-2 pi i b k / 512)
   const float* theta;
   const float* theta2;
   const long long* blk;
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ F
   }
   dft16<-1>(v);
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(a.tw1 + k * 512 + t));
+  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], wide(__ldg(a.tw1 + k * 512 + t)));
 #pragma unroll
   for (int k = 0; k < 16; ++k)
     xs[frp(t + 512 * k)] = make_float4(v[k].re.x, v[k].re.y, v[k].im.x, v[k].im.y);
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ F
   }
   dft16<-1>(v);
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], __ldg(a.tw2 + k * 32 + b2));
+  for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], wide(__ldg(a.tw2 + k * 32 + b2)));
 #pragma unroll
   for (int k = 0; k < 16; ++k)
     xs[frp(o2 + 32 * k)] = make_float4(v[k].re.x, v[k].re.y, v[k].im.x, v[k].im.y);
@@ -278,9 +280,9 @@ __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ F
   for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], w32(k, b3));
   pair_step(v, b3);
   // ---- the product with the taps' spectrum (same order, same for both segments)
-  const float4* hd = a.hd + (long long)tr * FR_N + t;
+  const float2* hd = a.hd + (long long)tr * FR_N + t;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], __ldg(hd + k * FR_NT));
+  for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], wide(__ldg(hd + k * FR_NT)));
   // ---- inverse: passes 4, 3, 2, 1 backwards
   pair_step(v, b3);
 #pragma unroll
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ F
     v[k] = CP{make_float2(q.x, q.y), make_float2(q.z, q.w)};
   }
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], __ldg(a.tw2 + k * 32 + b2));
+  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], wide(__ldg(a.tw2 + k * 32 + b2)));
   dft16<1>(v);
 #pragma unroll
   for (int r = 0; r < 16; ++r)
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ F
     v[k] = CP{make_float2(q.x, q.y), make_float2(q.z, q.w)};
   }
 #pragma unroll
-  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], __ldg(a.tw1 + k * 512 + t));
+  for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], wide(__ldg(a.tw1 + k * 512 + t)));
   dft16<1>(v);
 
   // ---- v[r] = result at position t + 512 r of both segments; positions >= 2048
@@ -387,10 +389,10 @@ __global__ void __launch_bounds__(256) k_lsmr_rows(const float2* __restrict__ xh
 
 // ---- set-up, FP64 ----------------------------------------------------------
 // E[m] = exp(+2 pi i m / N); H[m] = exp(-2 pi i phi(nu_m)) for m < N/2 (nu_m =
-// 100 MHz + m fs / N), 1 above; the FFT twiddle tables.
+// 100 MHz + m fs / N), 1 above; the FFT twiddle tables (as (c, s) pairs).
 __global__ void k_fr_tables(const double* __restrict__ tec, int t, double nu_ref,
                             double2* __restrict__ H, double2* __restrict__ E,
-                            float4* __restrict__ tw1, float4* __restrict__ tw2) {
+                            float2* __restrict__ tw1, float2* __restrict__ tw2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= FR_N) return;
   double s, c;
@@ -411,13 +413,13 @@ __global__ void k_fr_tables(const double* __restrict__ tec, int t, double nu_ref
     const int k = i / 512, b = i % 512;        // i < 16 * 512 = N
     const int e = (b * k) % FR_N;
     sincospi(2.0 * (double)e / FR_N, &s, &c);
-    tw1[i] = make_float4((float)c, (float)c, (float)-s, (float)-s);
+    tw1[i] = make_float2((float)c, (float)-s);
   }
   if (i < 16 * 32) {
     const int k = i / 32, b = i % 32;
     const int e = (b * k) % 512;
     sincospi(2.0 * (double)e / 512.0, &s, &c);
-    tw2[i] = make_float4((float)c, (float)c, (float)-s, (float)-s);
+    tw2[i] = make_float2((float)c, (float)-s);
   }
 }
 
@@ -447,7 +449,7 @@ __global__ void k_fr_taps(const double2* __restrict__ H, const double2* __restri
 // The taps' spectrum / N in the kernel's order: entry (k, t) is frequency
 // K = k1 + 16 k2 + 256 k + 4096 b (t = 2 (16 k1 + k2) + b).
 __global__ void k_fr_spectrum(const double2* __restrict__ h, const double2* __restrict__ E,
-                              float4* __restrict__ hd) {
+                              float2* __restrict__ hd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= FR_N) return;
   const int k = i / FR_NT, t = i % FR_NT, B = t >> 1, b = t & 1;
@@ -461,8 +463,7 @@ __global__ void k_fr_spectrum(const double2* __restrict__ h, const double2* __re
     m += K;
     if (m >= FR_N) m -= FR_N;
   }
-  const float hr = (float)(re / FR_N), hi = (float)(im / FR_N);
-  hd[i] = make_float4(hr, hr, hi, hi);
+  hd[i] = make_float2((float)(re / FR_N), (float)(im / FR_N));
 }
 
 }  // namespace
@@ -470,7 +471,7 @@ __global__ void k_fr_spectrum(const double2* __restrict__ h, const double2* __re
 long long fullrate_row(const lp_plan& p) { return kFrTaps + p.shape.F * kM; }
 
 size_t fullrate_table_bytes() {
-  return sizeof(float4) * (16 * 512 + 16 * 32);
+  return sizeof(float2) * (16 * 512 + 16 * 32);
 }
 
 cudaError_t init_fullrate_attributes() {
@@ -482,7 +483,7 @@ cudaError_t init_fullrate_attributes() {
 
 cudaError_t launch_fullrate_taps(const lp_plan& p, cudaStream_t s) {
   const Buffers& b = p.buf;
-  float4* tw2 = b.fr_tw + 16 * 512;
+  float2* tw2 = b.fr_tw + 16 * 512;
   for (int t = 0; t < p.shape.Tr; ++t) {
     k_fr_tables<<<FR_N / 256, 256, 0, s>>>(b.tec, t, p.nu_ref, b.fr_H, b.fr_E, b.fr_tw, tw2);
     k_fr_taps<<<kFrTaps / 128, 128, 0, s>>>(b.fr_H, b.fr_E, b.fr_h);

@@ -103,8 +103,8 @@ size_t carve(lp_plan& p, char* base) {
   const bool fr = p.cfg.fullrate_dedisp != 0;
   b.ufull = fr ? (float2*)take(sizeof(float2) * (size_t)J * (lp::kFrTaps + (size_t)sh.F * kM))
                : nullptr;
-  b.fr_hd = fr ? (float4*)take(sizeof(float4) * (size_t)sh.Tr * lp::kFrN) : nullptr;
-  b.fr_tw = fr ? (float4*)take(lp::fullrate_table_bytes()) : nullptr;
+  b.fr_hd = fr ? (float2*)take(sizeof(float2) * (size_t)sh.Tr * lp::kFrN) : nullptr;
+  b.fr_tw = fr ? (float2*)take(lp::fullrate_table_bytes()) : nullptr;
   b.fr_h = fr ? (double2*)take(sizeof(double2) * lp::kFrTaps) : nullptr;
   b.fr_H = fr ? (double2*)take(sizeof(double2) * lp::kFrN) : nullptr;
   b.fr_E = fr ? (double2*)take(sizeof(double2) * lp::kFrN) : nullptr;

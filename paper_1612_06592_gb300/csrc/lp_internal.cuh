@@ -88,9 +88,8 @@ struct Buffers {
   TriggerRec* trig;        // [trigger_cap]
   float* y;                // [J][F*M] or null
   float2* ufull;           // full-rate mode: [J][kFrTaps + F*M] synthesised series, history first
-  float4* fr_hd;           // full-rate mode: [Tr][16][512] taps' spectrum / kFrN (kernel order),
-                           // as (re, re, im, im)
-  float4* fr_tw;           // full-rate mode: FFT twiddles [16][512], then [16][32], as (c, c, s, s)
+  float2* fr_hd;           // full-rate mode: [Tr][16][512] taps' spectrum / kFrN (kernel order)
+  float2* fr_tw;           // full-rate mode: FFT twiddles [16][512], then [16][32], as (c, s)
   double2* fr_h;           // full-rate set-up scratch: [kFrTaps] taps of one trial
   double2* fr_H;           // full-rate set-up scratch: [kFrN] response of one trial
   double2* fr_E;           // full-rate set-up scratch: [kFrN] exp(+2 pi i m / kFrN)

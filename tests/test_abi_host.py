@@ -200,7 +200,7 @@ def test_fine_and_lsmr_options_validate_and_size_the_workspace(lib):
 
 def test_fullrate_options_validate_and_size_the_workspace(lib):
     """Full-rate de-dispersion: the series rows (2048 history samples, then the
-    block) per stream, the taps' spectrum per trial as (re, re, im, im), the
+    block) per stream, the taps' spectrum per trial, the
     FFT twiddles and the FP64 set-up scratch; refused with chunks, the fine
     filter and streaming blocks."""
     S, P, K, B, Tr, F = 6, 2, 16, 2, 3, 512
@@ -210,7 +210,7 @@ def test_fullrate_options_validate_and_size_the_workspace(lib):
     assert st == lib.LP_OK
     st, full, _ = _workspace(lib, shape, fullrate_dedisp=1)
     assert st == lib.LP_OK
-    extra = (J * (2048 + F * 1024) * 8 + Tr * 8192 * 16 + (16 * 512 + 16 * 32) * 16
+    extra = (J * (2048 + F * 1024) * 8 + Tr * 8192 * 8 + (16 * 512 + 16 * 32) * 8
              + 2048 * 16 + 2 * 8192 * 16)
     assert 0 <= full - base - extra < 7 * 256
     st, _, _ = _workspace(lib, shape, fullrate_dedisp=1, inversion=lib.LP_INV_LSMR)
