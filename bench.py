@@ -51,6 +51,17 @@ def measured_peaks():
         return {}
 
 
+def write4_bandwidth():
+    """Streaming bandwidth (GB/s) of a kernel that reads every word once and
+    writes it four times (the beamformer's mix), from profiles/hbm_mix.json, or
+    None when it was not measured."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "hbm_mix.json")))
+        return float(rec["forms"]["fan4"]["gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def fp32_peak():
     """FP32 FMA peak (TFLOP/s, SM MHz it was measured at, note): the measurement of
     the peak microbenchmark (profiles/fp32_peak.json) when recorded, else unit
@@ -431,7 +442,12 @@ def run_ours(args, rank, world, local_rank):
                               "bytes": in_bytes + beams_bytes,
                               "traffic": recorded_traffic("k_beamform_tc.cu")
                               if args.precision == "fp16" else None,
-                              "note": "input read + FP32 beam intermediate write"},
+                              "note": "input read + FP32 beam intermediate write",
+                              "write4_peak": write4_bandwidth(),
+                              "frac_of_write4": (bf_gbs / write4_bandwidth()
+                                                 if write4_bandwidth() else None),
+                              "write4_note": "streaming kernel reading each word once and "
+                                             "writing it four times (profiles/hbm_mix.json)"},
         "gpu_launches": plan.lp_launches_per_block() * args.steps,
         "triggers_last_block": int(ntrig),
         "clocks": clk,
