@@ -188,6 +188,7 @@ struct FullrateArgs {
   long long cap;
   float k_sigma;
   int lag;                  // frames between a block's first output and its first frame
+  int jj0;                  // first launch stream of this launch (grids of at most 65535)
   int P, Tr, pol0, npol;
 };
 
@@ -224,7 +225,7 @@ template <int OUT>
 __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ FullrateArgs a) {
   extern __shared__ float4 xs[];
   const int t = threadIdx.x;
-  const int j = (int)sel_stream(blockIdx.y, a.P, a.pol0, a.npol);
+  const int j = (int)sel_stream(a.jj0 + blockIdx.y, a.P, a.pol0, a.npol);
   const int tr = (j / a.P) % a.Tr;
   const long long base = (long long)blockIdx.x * (2 * FR_V);   // row index of segment a's sample 0
   const float2* __restrict__ ua = a.u + (long long)j * a.u_row + base + t;
@@ -519,13 +520,17 @@ cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps) {
   a.pol0 = ps.pol0;
   a.npol = npol;
   const long long FM = p.shape.F * kM;
-  const dim3 grid((unsigned)((a.nseg + 1) / 2), (unsigned)(p.shape.J() / p.shape.P * npol));
-  if (a.vph)
-    k_fullrate<2><<<grid, FR_NT, FR_SMEM, s>>>(a);
-  else if (a.y)
-    k_fullrate<1><<<grid, FR_NT, FR_SMEM, s>>>(a);
-  else
-    k_fullrate<0><<<grid, FR_NT, FR_SMEM, s>>>(a);
+  const int streams = p.shape.J() / p.shape.P * npol;
+  for (int jj0 = 0; jj0 < streams; jj0 += 65535) {        // grid y is at most 65535
+    a.jj0 = jj0;
+    const dim3 grid((unsigned)((a.nseg + 1) / 2), (unsigned)std::min(65535, streams - jj0));
+    if (a.vph)
+      k_fullrate<2><<<grid, FR_NT, FR_SMEM, s>>>(a);
+    else if (a.y)
+      k_fullrate<1><<<grid, FR_NT, FR_SMEM, s>>>(a);
+    else
+      k_fullrate<0><<<grid, FR_NT, FR_SMEM, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -977,10 +977,12 @@ int lp_launches_per_block(const lp_plan* p) {
   const int fine = p->cfg.fine_dedisp ? (int)((rows + 65534) / 65535) : 0;
   if (p->cfg.inversion == LP_INV_LSMR) {  // beamformer, inverse FFT + LSMR + trigger per
     const int nj = (int)((p->shape.J() + 65534) / 65535);   // 65535 streams, sigma, shift
-    // full-rate filter: the series rows (per 65535 streams), the filter, its history shift
-    return 3 + fine + 3 * nj + (p->cfg.fullrate_dedisp ? 2 + nj : 0);
+    // full-rate filter: the series rows and the filter (per 65535 streams), its history shift
+    return 3 + fine + 3 * nj + (p->cfg.fullrate_dedisp ? 1 + 2 * nj : 0);
   }
-  if (p->fc == 0 || p->fc == p->shape.F) return 4 + fine + (p->cfg.fullrate_dedisp ? 2 : 0);
+  // full-rate filter: one launch per 65535 streams, and its history shift
+  const int nj = (int)((p->shape.J() + 65534) / 65535);
+  if (p->fc == 0 || p->fc == p->shape.F) return 4 + fine + (p->cfg.fullrate_dedisp ? 1 + nj : 0);
   return 2 + 3 * (int)(p->shape.F / p->fc);
 }
 
