@@ -319,24 +319,65 @@ __global__ void __launch_bounds__(FR_NT, 1) k_fullrate(const __grid_constant__ F
   const long long FM = a.F * kM;
   const long long o0 = base + t - 2048;                      // output index of position t + 512 * 0
   if constexpr (OUT == 2) {
-    // output o = i M + p goes to row (j, p), column i
-    float2* vj = a.vph + (long long)j * FM;
+    // output o = i M + p goes to row (j, p), column i.  The two segments are the
+    // 12 frames i0 .. i0 + 11 (i0 = base / 1024); they are staged in shared
+    // memory as [phase][12 frames] (rows of 13 pairs: the half-warps' stores hit
+    // distinct banks) so that each phase's 12 frames leave as 96 contiguous bytes
+    // (F is a multiple of 256 under the LSMR inversion: 16-byte aligned stores)
+    float2* stg = reinterpret_cast<float2*>(xs);
+    constexpr int RS = 13;
+    __syncthreads();                                          // xs read by every thread
 #pragma unroll
     for (int r = 4; r < 16; ++r) {
-      const long long oa = o0 + 512 * r, ob = oa + FR_V;
-      if (oa < FM) vj[(oa & (kM - 1)) * a.F + (oa >> 10)] = make_float2(v[r].re.x, v[r].im.x);
-      if (ob < FM) vj[(ob & (kM - 1)) * a.F + (ob >> 10)] = make_float2(v[r].re.y, v[r].im.y);
+      const int ph = t + 512 * ((r - 4) & 1), f = (r - 4) >> 1;
+      stg[ph * RS + f] = make_float2(v[r].re.x, v[r].im.x);
+      stg[ph * RS + f + 6] = make_float2(v[r].re.y, v[r].im.y);
+    }
+    __syncthreads();
+    const long long i0 = base >> 10;
+    const int nf = (int)min(12LL, a.F - i0);                  // frames of the block left
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ph = t + 512 * h;
+      float2* dst = a.vph + ((long long)j * kM + ph) * a.F + i0;
+      const float2* src = stg + ph * RS;
+      if (nf == 12) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const float2 x0 = src[2 * q], x1 = src[2 * q + 1];
+          reinterpret_cast<float4*>(dst)[q] = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+      } else {
+        for (int f = 0; f < nf; ++f) dst[f] = src[f];
+      }
     }
     return;
   }
   const long long n_first = (*a.blk * a.F - a.lag) * (long long)kM;
   const float2 th2 = bc(a.theta2[j]);
   float* yj = OUT == 1 ? a.y + (long long)j * FM : nullptr;
+  // A block whose 12288 outputs all lie inside the block and at or after the
+  // stream's first sample needs no per-value checks: it stores, and leaves
+  // unless one of a warp's values crosses the threshold.
+  const bool whole = base + 2 * FR_V <= FM && n_first + base >= 0;
+  if (whole) {
+    bool hit = false;
+#pragma unroll
+    for (int r = 4; r < 16; ++r) {
+      if constexpr (OUT == 1) {
+        yj[o0 + 512 * r] = v[r].re.x;
+        yj[o0 + 512 * r + FR_V] = v[r].re.y;
+      }
+      const float2 e2 = fma2(v[r].re, v[r].re, mul2(v[r].im, v[r].im));
+      hit = hit || e2.x > th2.x || e2.y > th2.y;
+    }
+    if (!__any_sync(0xffffffffu, hit)) return;
+  }
 #pragma unroll
   for (int r = 4; r < 16; ++r) {
     const long long oa = o0 + 512 * r, ob = oa + FR_V;
     const bool ina = oa < FM, inb = ob < FM;
-    if (OUT == 1) {
+    if (OUT == 1 && !whole) {
       if (ina) yj[oa] = v[r].re.x;
       if (inb) yj[ob] = v[r].re.y;
     }

@@ -125,21 +125,27 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
     u[i] = e < LS_ROWS ? b[e] : zero;
     part = fma2(u[i], u[i], part);
   }
-  float beta = sqrtf(warp_sum(part.x + part.y));
-  // u <- u / n, v <- v / n (no change for a zero norm); packed FMUL2
-  auto norm_u = [&](float nrm) {
-    const float r = nrm > 0.f ? 1.f / nrm : 1.f;
+  // a norm from its sum of squares ss by one reciprocal square root: returns
+  // 1 / norm (1 for a zero norm, which then leaves the vector unchanged)
+  auto inv_norm = [](float ss, float& nrm) {
+    const float r = ss > 0.f ? rsqrtf(ss) : 1.f;
+    nrm = ss > 0.f ? ss * r : 0.f;
+    return r;
+  };
+  float beta;
+  const float rb0 = inv_norm(warp_sum(part.x + part.y), beta);
+  // u <- u r, v <- v r (r = 1 / norm); packed FMUL2
+  auto norm_u = [&](float r) {
     const float2 r2 = make_float2(r, r);
 #pragma unroll
     for (int i = 0; i < LS_PER; ++i) u[i] = __fmul2_rn(u[i], r2);
   };
-  auto norm_v = [&](float nrm) {
-    const float r = nrm > 0.f ? 1.f / nrm : 1.f;
+  auto norm_v = [&](float r) {
     const float2 r2 = make_float2(r, r);
 #pragma unroll
     for (int i = 0; i < LS_PER; ++i) v[i] = __fmul2_rn(v[i], r2);
   };
-  // A^T u - c v, into v; returns the new norm
+  // A^T u - c v, into v; returns the new sum of squares
   auto rmatvec = [&](float c) {
 #pragma unroll
     for (int i = 0; i < LS_PER; ++i)
@@ -160,9 +166,9 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
       pt = fma2(v[i], v[i], pt);
     }
     __syncwarp();
-    return sqrtf(warp_sum(pt.x + pt.y));
+    return warp_sum(pt.x + pt.y);
   };
-  // A v - c u, into u; returns the new norm
+  // A v - c u, into u; returns the new sum of squares
   auto matvec = [&](float c) {
 #pragma unroll
     for (int i = 0; i < LS_PER; ++i)
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
       pt = fma2(u[i], u[i], pt);
     }
     __syncwarp();
-    return sqrtf(warp_sum(pt.x + pt.y));
+    return warp_sum(pt.x + pt.y);
   };
 
 #pragma unroll
@@ -193,40 +199,48 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
     hb[i] = zero;
     x[i] = zero;
   }
+  // The scalar recurrences run on reciprocals: every norm and both rotations'
+  // lengths come from one reciprocal square root each, and the quotients of
+  // the updates are products with the kept reciprocals 1 / rho, 1 / rhobar
+  // (the warp's dependent chain between two products with A is then a few
+  // multiplications long instead of several divisions).
   if (beta > 0.f) {
-    norm_u(beta);
-    float alpha = rmatvec(0.f);
+    norm_u(rb0);
+    float alpha;
+    float ra = inv_norm(rmatvec(0.f), alpha);
     if (alpha > 0.f) {
-      norm_v(alpha);
+      norm_v(ra);
       float alphabar = alpha, zetabar = alpha * beta;
-      float rho = 1.f, rhobar = 1.f, cbar = 1.f, sbar = 0.f;
+      float irho = 1.f, irhobar = 1.f, cbar = 1.f, sbar = 0.f;   // rho = rhobar = 1
 #pragma unroll
       for (int i = 0; i < LS_PER; ++i) h[i] = v[i];
       for (int it = 0; it < iters; ++it) {
         // continue the bidiagonalisation
-        beta = matvec(alpha);
-        norm_u(beta);
-        alpha = rmatvec(beta);
-        norm_v(alpha);
-        // rotation P_k
-        const float rho_old = rho;
-        rho = hypotf(alphabar, beta);
-        const float c = alphabar / rho, s = beta / rho;
+        norm_u(inv_norm(matvec(alpha), beta));
+        ra = inv_norm(rmatvec(beta), alpha);
+        norm_v(ra);
+        // rotation P_k: rho = |(alphabar, beta)|
+        const float irho_old = irho;
+        const float q = fmaf(alphabar, alphabar, beta * beta);
+        irho = rsqrtf(q);
+        const float rho = q * irho;
+        const float c = alphabar * irho, s = beta * irho;
         const float theta = s * alpha;
         alphabar = c * alpha;
-        // rotation Pbar_k
-        const float rhobar_old = rhobar;
+        // rotation Pbar_k: rhobar = |(cbar rho, theta)|
+        const float irhobar_old = irhobar;
         const float thetabar = sbar * rho;
-        rhobar = hypotf(cbar * rho, theta);
-        const float cbar_new = cbar * rho / rhobar;
-        sbar = theta / rhobar;
-        cbar = cbar_new;
+        const float cr = cbar * rho;
+        const float qb = fmaf(cr, cr, theta * theta);
+        irhobar = rsqrtf(qb);
+        cbar = cr * irhobar;
+        sbar = theta * irhobar;
         const float zeta = cbar * zetabar;
         zetabar = -sbar * zetabar;
         // update h, hbar, x
-        const float f1 = thetabar * rho / (rho_old * rhobar_old);
-        const float f2 = zeta / (rho * rhobar);
-        const float f3 = theta / rho;
+        const float f1 = thetabar * rho * (irho_old * irhobar_old);
+        const float f2 = zeta * (irho * irhobar);
+        const float f3 = theta * irho;
         const float2 m1 = make_float2(-f1, -f1), p2 = make_float2(f2, f2),
                      m3 = make_float2(-f3, -f3);
 #pragma unroll

@@ -21,8 +21,10 @@ the HBM budget next to the sessions already running and their predicted
 device time fits the time budget; finished sessions free theirs.  Admission
 and retirement run between blocks, after a block's triggers are back: a
 request that arrived by then is set up (plan, workspace, tables) there and
-joins from the next block, so no block waits for another session's set-up.
-The cost model of the prediction is measured at start-up (``Server.calibrate``).
+joins from the next block.  Set-ups are timed, and one that would not end,
+at the longest recently measured, before the next block arrives waits for the
+next gap, so that no block waits for another session's set-up.  The cost model
+of the prediction is measured at start-up (``Server.calibrate``).
 
 Latency of a block = time from its arrival (the realtime clock of the stream)
 to the moment the last session's triggers for it are on the host.  All compute
@@ -206,6 +208,13 @@ class Server:
         self.group_key = None
         self.launches = []                    # kernel launches per block
         self.calibration = []
+        self.setup_ms = []                    # measured set-up time of each admission
+        self.deferred = 0                     # admissions put off to a later gap
+
+    def _setup_estimate(self):
+        """Set-up time to plan for: the longest of the recent set-ups (0 before
+        the first)."""
+        return max(self.setup_ms[-8:]) if self.setup_ms else 0.0
 
     # -- admission ---------------------------------------------------------
     def submit(self, req: Request):
@@ -230,8 +239,11 @@ class Server:
         retiring never leave a rounding residue)."""
         return sum(self._cost(s.req) for s in self.active.values())
 
-    def admit(self):
-        """Admit queued requests, in arrival order, while memory and time fit."""
+    def admit(self, until=None):
+        """Admit queued requests, in arrival order, while memory and time fit.
+        until: perf_counter time by which set-up must be done (the next block's
+        arrival); a request whose set-up, at the longest recently measured, would
+        run past it waits for the next gap between blocks."""
         admitted = []
         while self.pending:
             req = self.pending[0]
@@ -250,6 +262,10 @@ class Server:
                     self.copy_ms + (self._fixed() + self.cost_used + cost) * self.cost_corr
                     > self.time_budget_ms):
                 break                           # wait for a time slot
+            if until is not None and time.perf_counter() + self._setup_estimate() * 1e-3 > until:
+                self.deferred += 1
+                break                           # no time before the next block
+            t_set = time.perf_counter()
             self.pending.popleft()
             stream = self.stream if self.batch else self.torch.cuda.Stream(device=self.device)
             plan = lp.Plan(self.S, self.P, req.nsub, len(req.beams), len(req.tec), self.F,
@@ -258,6 +274,8 @@ class Server:
                            use_graph=self.use_graph and not self.batch, stream=stream)
             plan.lp_set_weights(self.enu, self.grid[req.beams], stream=stream)
             plan.lp_set_tec(req.tec, stream=stream)
+            stream.synchronize()                # the tables are built before the next block
+            self.setup_ms.append((time.perf_counter() - t_set) * 1e3)
             self.active[req.rid] = Session(req, plan, stream)
             self.used += need
             self.cost_used = self._active_cost()
@@ -351,11 +369,14 @@ class Server:
         plans, shp = [], []
         stream = self.stream
         for (nb, ns, nt) in shapes:
+            t_set = time.perf_counter()
             plan = lp.Plan(self.S, self.P, ns, nb, nt, self.F, input_dtype="int8",
                            precision=self.precision, first_bin=self.fb0, k_sigma=self.k_sigma,
                            stream=stream)
             plan.lp_set_weights(self.enu, self.grid[:nb], stream=stream)
             plan.lp_set_tec(np.linspace(10.0, 30.0, nt), stream=stream)
+            stream.synchronize()
+            self.setup_ms.append((time.perf_counter() - t_set) * 1e3)
             plans.append(plan)
             shp.append((self.P, ns, nb, nt))
         combos = [[i] for i in range(len(plans))] + [list(range(len(plans)))]
@@ -420,7 +441,7 @@ def run(args):
         hosts.append(h)
         del xb
     torch.cuda.synchronize()
-    lat, dev_busy, n_sessions, n_out = [], [], [], 0
+    lat, dev_busy, n_sessions, n_out, late = [], [], [], 0, []
     qi = 0
     # requests that arrived before the first block join it
     while qi < len(reqs) and reqs[qi].arrival <= 0:
@@ -440,6 +461,9 @@ def run(args):
         srv.observe((te - ts) * 1e3)
         lat.append(te - arrival)
         dev_busy.append(te - ts)
+        if te - arrival > period:
+            late.append({"block": b, "wait_ms": (ts - arrival) * 1e3,
+                         "busy_ms": (te - ts) * 1e3, "sessions": len(out)})
         n_sessions.append(len(out))
         n_out += sum(len(s.req.beams) * len(s.req.tec) * w.pols for s in srv.active.values())
         # between blocks, off the latency path: finished sessions leave, and the
@@ -449,7 +473,7 @@ def run(args):
             srv.submit(reqs[qi])
             qi += 1
         srv.retire()
-        srv.admit()
+        srv.admit(until=t0 + (b + 1) * period if args.realtime else None)
     wall = time.perf_counter() - t0
     lat_ms = np.array(lat) * 1e3
     res = {
@@ -467,6 +491,13 @@ def run(args):
         "cost_model": srv.model.as_dict(), "calibration": srv.calibration,
         "time_budget_frac": args.time_budget, "cost_correction": srv.cost_corr,
         "ingest_ms": srv.copy_ms,
+        "setup_ms": {"mean": float(np.mean(srv.setup_ms)) if srv.setup_ms else 0.0,
+                     "max": float(np.max(srv.setup_ms)) if srv.setup_ms else 0.0,
+                     "n": len(srv.setup_ms)},
+        "admissions_deferred": srv.deferred,
+        "late_blocks": late[:20],
+        "busy_ms_p50": float(np.percentile(np.array(dev_busy) * 1e3, 50)),
+        "busy_ms_max": float(np.max(dev_busy) * 1e3),
         "sustained_blocks_per_s": args.blocks / wall,
         "stream_samples_per_s": n_out * w.block_len * M / wall,
         "station_samples_per_s": args.blocks * w.pols * w.subbands * w.block_len * w.stations / wall,

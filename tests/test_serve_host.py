@@ -1,7 +1,8 @@
 """Host logic of the serving loop, on the CPU: request generation and the
 admission policy (FIFO; wait for memory; refuse what can never fit in memory
-or in time; wait for a time slot; retire frees memory and cost; the cost
-correction follows measured block times).  Plans and CUDA streams are replaced
+or in time; wait for a time slot; set-ups that would run into the next block
+wait for the next gap; retire frees memory and cost; the cost correction
+follows measured block times).  Plans and CUDA streams are replaced
 by fakes; workspace sizes come from the library's host-only query."""
 
 from collections import deque
@@ -34,11 +35,16 @@ class _FakePlan:
         pass
 
 
+class _FakeStream:
+    def synchronize(self):
+        pass
+
+
 class _FakeTorch:
     class cuda:
         @staticmethod
         def Stream(device=None):
-            return object()
+            return _FakeStream()
 
 
 def _server(serve, monkeypatch, budget, time_budget_ms=None):
@@ -66,6 +72,7 @@ def _server(serve, monkeypatch, budget, time_budget_ms=None):
     srv.batch = False
     srv.stream = None
     srv.groups, srv.group_key, srv.launches = [], None, []
+    srv.setup_ms, srv.deferred = [], 0
     return srv
 
 
@@ -174,3 +181,22 @@ def test_cost_used_is_recomputed_without_residue(serve, monkeypatch):
     cc = srv.cost_corr
     srv.observe(50.0)                      # no session: the correction stays
     assert srv.cost_corr == cc
+
+
+def test_setup_waits_for_a_gap_long_enough(serve, monkeypatch):
+    """A set-up that, at the longest recent set-up time, would end after the
+    next block's arrival waits (FIFO kept); with time enough it is admitted and
+    its set-up time recorded."""
+    import time
+    r0, r1 = _req(serve, 0, 4, 122, 1), _req(serve, 1, 4, 122, 1)
+    srv = _server(serve, monkeypatch, 1 << 50)
+    srv.setup_ms = [40.0, 90.0, 60.0]            # longest recent: 90 ms
+    srv.submit(r0)
+    srv.submit(r1)
+    assert srv.admit(until=time.perf_counter() + 0.05) == []
+    assert srv.deferred == 1 and len(srv.pending) == 2
+    assert srv.admit(until=time.perf_counter() + 10.0) == [0, 1]
+    assert len(srv.setup_ms) == 5 and all(t >= 0.0 for t in srv.setup_ms[3:])
+    r2 = _req(serve, 2, 4, 122, 1)
+    srv.submit(r2)
+    assert srv.admit() == [2]                    # no arrival clock: no limit
