@@ -118,7 +118,7 @@ def parse():
                          "overlap-save filter; a separate line, not the headline)")
     ap.add_argument("--lsmr", action="store_true",
                     help="PPF inversion by windowed LSMR instead of the FIR synthesis (a "
-                         "separate line, not the headline; no triggers on that path)")
+                         "separate line, not the headline; trigger on per-phase levels)")
     ap.add_argument("--gemm-config", type=int, default=-2,
                     help="fixed beamformer configuration index (-1: default; -2: autotune)")
     ap.add_argument("--chunk-frames", type=int, default=0,
@@ -508,11 +508,11 @@ def run_ours(args, rank, world, local_rank):
         inv_ms = stages["synth"] / max(nrec, 1)
         ach = windows * per_window / (inv_ms / 1e3) / 1e12
         line["metric"] = line["metric"].replace("realtime factor", "realtime factor, LSMR PPF "
-                                                "inversion (no triggers),")
+                                                "inversion (per-phase level and trigger),")
         line["config"]["workload"] += "-lsmr"
         line["config"]["inversion"] = ("windowed LSMR: 256-frame windows, 16 frames of "
                                        "overlap, 25 iterations, per stream and phase")
-        line["roofline"] = {"bound": "alu", "kernel": "k_zt + k_lsmr (inverse FFT + LSMR)",
+        line["roofline"] = {"bound": "alu", "kernel": "k_ippf (inverse DFT only) + k_lsmr (with k_lsmr_sigma + k_lsmr_trigger unless --fullrate)",
                             "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                             "frac": ach / alu_peak, "traffic": None,
                             "flop_per_window": per_window, "windows": windows,

@@ -39,6 +39,11 @@
 // balanced tiling (one block per SM walking an equal contiguous range of the
 // streams' frames, a piece per stream it crosses), which leaves no tail wave and
 // pays the 16 history frames once per piece.  FP32 throughout.
+//
+// OUT selects what the FIR warps do with z: 0 trigger, 1 trigger and y = Re u,
+// 2 (full-rate mode) u stored, no trigger, 3 (LSMR inversion) no filter: the
+// inverse DFT itself, scaled by 2/M, stored phase-major (a phase's 8 frames of a
+// batch are 64 contiguous bytes) as the right-hand sides of the LSMR systems.
 #include "lp_internal.cuh"
 
 #include <algorithm>
@@ -592,9 +597,10 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
       // thread ft owns the butterfly partners (ft, ft + 512) and (511 - ft, 1023 - ft)
       const int ft = tid - NDFT;
       const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 256u * ((warp - 8) >> 2);
-      // taps (g, g) of the four phases into tensor memory
+      // taps (g, g) of the four phases into tensor memory (not in the LSMR
+      // mode, which does not filter)
   #pragma unroll 1
-      for (int ph = 0; ph < 4; ++ph) {
+      for (int ph = 0; ph < (OUT == 3 ? 0 : 4); ++ph) {
         const int p = (ph & 2 ? kM / 2 - 1 - ft : ft) + (ph & 1 ? kM / 2 : 0);
         float tq[32];
   #pragma unroll
@@ -614,6 +620,11 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
       float* yj = OUT == 1 && pl.y ? pl.y + ((long long)j * F_total + f_base) * kM : nullptr;
       // full-rate mode: the series row of the stream (history first)
       float2* uj = OUT == 2 ? pl.u + (long long)j * pl.u_row + kFrTaps + f_base * kM : nullptr;
+      // LSMR mode: the stream's phase rows of u_row positions each; batch row r
+      // of the run is position m0 + r (frame m0 - 16 + r), written once: rows
+      // r >= 16, and the prefix rows of a stream's first run
+      float2* zj = OUT == 3 ? pl.u + (long long)j * kM * pl.u_row : nullptr;
+      const int r_lo = m0 == 0 ? 0 : kPrefix;
       // block i of the stream starts at sample (i F - 15) M; samples n < 0 (frames
       // m < 15 of the first block) never trigger
       const long long bidx = *pl.blk;
@@ -656,6 +667,28 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
             za[2 * q + 1] = make_float2(a.y + b.y, a.w + b.w);
             zb[2 * q] = make_float2(a.x - b.x, a.z - b.z);
             zb[2 * q + 1] = make_float2(a.y - b.y, a.w - b.w);
+          }
+          if constexpr (OUT == 3) {
+            constexpr float sc = 2.0f / kM;           // a power of two: exact
+            const bool all = r0 >= r_lo && r0 + FB <= nfr;
+  #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float2* z = h ? zb : za;
+              float2* dst = zj + (long long)(pb + h * (kM / 2)) * pl.u_row + m0 + r0;
+              if (all) {
+  #pragma unroll
+                for (int q = 0; q < FB / 2; ++q)
+                  reinterpret_cast<float4*>(dst)[q] =
+                      make_float4(z[2 * q].x * sc, z[2 * q].y * sc, z[2 * q + 1].x * sc,
+                                  z[2 * q + 1].y * sc);
+              } else {
+  #pragma unroll
+                for (int f = 0; f < FB; ++f)
+                  if (r0 + f >= r_lo && r0 + f < nfr)
+                    dst[f] = make_float2(z[f].x * sc, z[f].y * sc);
+              }
+            }
+            continue;
           }
   #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -751,11 +784,11 @@ cudaError_t init_f32_attributes(const Shape& sh);
 cudaError_t init_tc_attributes(const Shape& sh);
 
 cudaError_t init_ippf_attributes() {
-  const void* k[5] = {(const void*)k_ippf<false, 0>, (const void*)k_ippf<false, 1>,
-                      (const void*)k_ippf<false, 2>, (const void*)k_ippf<true, 0>,
-                      (const void*)k_ippf<true, 1>};
+  const void* k[6] = {(const void*)k_ippf<false, 0>, (const void*)k_ippf<false, 1>,
+                      (const void*)k_ippf<false, 2>, (const void*)k_ippf<false, 3>,
+                      (const void*)k_ippf<true, 0>, (const void*)k_ippf<true, 1>};
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = raise_smem_limit(k[i], ippf_smem_bytes());
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = raise_smem_limit(k[i], ippf_smem_bytes());
   return e;
 }
 
@@ -840,6 +873,32 @@ cudaError_t launch_ippf_plans(const lp_plan* const* plans, int n, const Chunk& c
 cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel ps) {
   const lp_plan* one = &p;
   return launch_ippf_plans(&one, 1, c, s, ps);
+}
+
+// The LSMR right-hand sides: the inverse DFT of every frame of the block and of
+// the 16 before it, zt[j][p][frame + 16] = (2/M) z_frame[p], by the synthesis
+// kernel's DFT role in its balanced tiling (OUT = 3: no filter, no trigger).
+cudaError_t launch_ippf_zt(const lp_plan& p, cudaStream_t s) {
+  IppfArgsN<1> a;
+  a.F = p.shape.F;
+  a.row = p.row();
+  a.F_total = p.shape.F;
+  a.f_base = 0;
+  a.frames_per_cta = 0;
+  a.pol0 = 0;
+  a.npol = p.shape.P;
+  a.n = 1;
+  a.pl[0] = ippf_plan(p);
+  a.pl[0].y = nullptr;
+  a.pl[0].u = p.buf.zt;
+  a.pl[0].u_row = p.shape.F + kPrefix;
+  const int streams = p.shape.J();
+  a.nstreams = streams;
+  a.pl[0].stream_end = streams;
+  const long long work8 = ((long long)streams * a.F + FB - 1) / FB;
+  const dim3 grid((unsigned)std::min<long long>(ippf_num_sms(), work8), 1u);
+  k_ippf<false, 3><<<grid, NT, ippf_smem_bytes(), s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sigma_plans(const lp_plan* const* plans, int n, bool zero_counts,

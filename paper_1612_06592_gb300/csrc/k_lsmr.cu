@@ -9,9 +9,9 @@
 // [256 w - 16, 256 w + 240), the unknowns all 16 of whose equations lie in the
 // window; the output of a block lags its frames by 16 (sample (m - 16) M + p).
 //
-// k_zt: the inverse DFT of 4 frames per block (radix-2, in shared memory, the
-// 2 * beam bins placed in bit-reversed order), written phase-major
-// zt[stream][p][frame + 16] so that a phase's frames are contiguous.
+// The right-hand sides, the inverse DFT of every frame written phase-major
+// zt[stream][p][frame + 16] (a phase's frames contiguous), come from the
+// synthesis kernel's DFT role (launch_ippf_zt).
 // k_lsmr: one warp per (stream, phase, window); lane l owns elements
 // [9 l, 9 l + 9) of every vector.  A v and A^T u read a 24-element window of
 // the other vector from shared memory once and slide the 16 taps over it in
@@ -27,10 +27,6 @@
 namespace lp {
 namespace {
 
-constexpr int ZT_FR = 4;                       // frames per k_zt block
-constexpr int ZT_NTH = 256;
-constexpr int ZT_LD = kM + 4;                  // padded frame stride: the 4 frames' elements
-                                               // p fall in different banks
 constexpr int LS_W = 256;                      // unknowns kept per window
 constexpr int LS_ROWS = LS_W + kPrefix;        // 272 equations
 constexpr int LS_COLS = LS_ROWS + kTaps - 1;   // 287 unknowns
@@ -40,45 +36,6 @@ constexpr int LS_PAD = 16;                     // zero guard before / after a ve
 constexpr int kLsmrLag = kPrefix;              // output row i is frame i - 16 of the block
 
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-__global__ void __launch_bounds__(ZT_NTH) k_zt(const float2* __restrict__ rows, int K,
-                                               int first_bin, long long row, long long nfr,
-                                               float2* __restrict__ zt) {
-  __shared__ float2 zs[ZT_FR * ZT_LD];
-  const long long j = blockIdx.y;
-  const long long f0 = (long long)blockIdx.x * ZT_FR;        // row position (frame + 16)
-  const int tid = threadIdx.x;
-  for (int i = tid; i < ZT_FR * ZT_LD; i += ZT_NTH) zs[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int i = tid; i < ZT_FR * K; i += ZT_NTH) {
-    const int f = i % ZT_FR, k = i / ZT_FR;
-    const float2 v = rows[(j * K + k) * row + f0 + f];
-    const int pos = (int)(__brev((unsigned)(first_bin + k)) >> 22);   // 10-bit reversal
-    zs[f * ZT_LD + pos] = make_float2(2.f * v.x, 2.f * v.y);
-  }
-  __syncthreads();
-  for (int s = 0; s < 10; ++s) {                             // half-size 2^s
-    const int hs = 1 << s;
-    for (int b = tid; b < ZT_FR * (kM / 2); b += ZT_NTH) {
-      const int f = b >> 9, bb = b & 511;
-      const int pos = bb & (hs - 1);
-      const int i0 = f * ZT_LD + ((bb >> s) << (s + 1)) + pos, i1 = i0 + hs;
-      float sn, cs;
-      sincospif((float)pos / (float)hs, &sn, &cs);           // exp(+2 pi i pos / 2 hs)
-      const float2 x0 = zs[i0], x1 = zs[i1];
-      const float2 t = make_float2(cs * x1.x - sn * x1.y, cs * x1.y + sn * x1.x);
-      zs[i0] = make_float2(x0.x + t.x, x0.y + t.y);
-      zs[i1] = make_float2(x0.x - t.x, x0.y - t.y);
-    }
-    __syncthreads();
-  }
-  constexpr float inv_m = 1.0f / kM;
-  for (int i = tid; i < ZT_FR * kM; i += ZT_NTH) {
-    const int f = i % ZT_FR, p = i / ZT_FR;
-    const float2 v = zs[f * ZT_LD + p];
-    zt[(j * kM + p) * nfr + f0 + f] = make_float2(v.x * inv_m, v.y * inv_m);
-  }
-}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -349,11 +306,10 @@ cudaError_t launch_lsmr(const lp_plan& p, cudaStream_t s) {
   const auto& sh = p.shape;
   const long long nfr = sh.F + kPrefix;
   const long long J = sh.J();
+  cudaError_t e = launch_ippf_zt(p, s);
+  if (e != cudaSuccess) return e;
   for (long long j0 = 0; j0 < J; j0 += 65535) {             // grid y is at most 65535
     const unsigned nj = (unsigned)std::min<long long>(65535, J - j0);
-    k_zt<<<dim3((unsigned)(nfr / ZT_FR), nj), ZT_NTH, 0, s>>>(
-        synth_rows(p) + j0 * sh.K * p.row(), sh.K, p.cfg.first_bin, p.row(), nfr,
-        p.buf.zt + j0 * kM * nfr);
     const int n_win = (int)(sh.F / LS_W);
     k_lsmr<<<dim3((unsigned)(kM / LS_WARPS * n_win), nj), LS_WARPS * 32, 0, s>>>(
         p.buf.zt, p.buf.proto, p.buf.filter_sums, nfr, sh.F, n_win, p.cfg.lsmr_iters, j0,

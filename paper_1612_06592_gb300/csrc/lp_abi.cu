@@ -975,10 +975,10 @@ int lp_launches_per_block(const lp_plan* p) {
   if (!p) return 4;
   const long long rows = (long long)p->shape.J() * p->shape.K;
   const int fine = p->cfg.fine_dedisp ? (int)((rows + 65534) / 65535) : 0;
-  if (p->cfg.inversion == LP_INV_LSMR) {  // beamformer, inverse FFT + LSMR + trigger per
+  if (p->cfg.inversion == LP_INV_LSMR) {  // beamformer, inverse FFT, LSMR + trigger per
     const int nj = (int)((p->shape.J() + 65534) / 65535);   // 65535 streams, sigma, shift
     // full-rate filter: the series rows and the filter (per 65535 streams), its history shift
-    return 3 + fine + 3 * nj + (p->cfg.fullrate_dedisp ? 1 + 2 * nj : 0);
+    return 4 + fine + 2 * nj + (p->cfg.fullrate_dedisp ? 1 + 2 * nj : 0);
   }
   // full-rate filter: one launch per 65535 streams, and its history shift
   const int nj = (int)((p->shape.J() + 65534) / 65535);

@@ -122,7 +122,7 @@ struct IppfPlan {
   const long long* blk;
   float* y;
   float2* u;               // full-rate mode: series rows (the kernel then stores u and
-                           // does not trigger), or null
+                           // does not trigger); LSMR right-hand sides: the zt rows; or null
   long long u_row;
   TriggerRec* trig;
   unsigned long long* count;
@@ -264,6 +264,7 @@ cudaError_t launch_beamform_tc(const lp_plan& p, const void* x, long long pol_st
                                const Chunk& c, cudaStream_t s, PolSel ps = {});
 cudaError_t launch_sigma(const lp_plan& p, cudaStream_t s, PolSel ps = {});
 cudaError_t launch_ippf(const lp_plan& p, const Chunk& c, cudaStream_t s, PolSel ps = {});
+cudaError_t launch_ippf_zt(const lp_plan& p, cudaStream_t s);
 // One launch of a kernel for the plans of a group (see lp_group in lp.h):
 // plan i reads its polarisation slabs at xs[i].  zero_counts: the noise-level
 // launch also zeroes every plan's trigger counter.
