@@ -43,7 +43,8 @@
 // OUT selects what the FIR warps do with z: 0 trigger, 1 trigger and y = Re u,
 // 2 (full-rate mode) u stored, no trigger, 3 (LSMR inversion) no filter: the
 // inverse DFT itself, scaled by 2/M, stored phase-major (a phase's 8 frames of a
-// batch are 64 contiguous bytes) as the right-hand sides of the LSMR systems.
+// batch are 64 contiguous bytes, two 32-byte stores) as the right-hand sides of the
+// LSMR systems.
 #include "lp_internal.cuh"
 
 #include <algorithm>
@@ -188,6 +189,12 @@ int ippf_num_sms() {
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src));
+}
+// 32-byte store (address 32-byte aligned)
+__device__ __forceinline__ void st_global_v8(float* p, const float (&v)[8]) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "f"(v[0]),
+               "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -676,11 +683,18 @@ __global__ void __launch_bounds__(NT, 1) k_ippf(
               const float2* z = h ? zb : za;
               float2* dst = zj + (long long)(pb + h * (kM / 2)) * pl.u_row + m0 + r0;
               if (all) {
+                // two 32-byte stores: u_row is a multiple of 16 (block_len a
+                // multiple of 256) and m0 + r0 of 8, so dst is 64-byte aligned
   #pragma unroll
-                for (int q = 0; q < FB / 2; ++q)
-                  reinterpret_cast<float4*>(dst)[q] =
-                      make_float4(z[2 * q].x * sc, z[2 * q].y * sc, z[2 * q + 1].x * sc,
-                                  z[2 * q + 1].y * sc);
+                for (int hf = 0; hf < 2; ++hf) {
+                  float o[8];
+  #pragma unroll
+                  for (int f = 0; f < 4; ++f) {
+                    o[2 * f] = z[4 * hf + f].x * sc;
+                    o[2 * f + 1] = z[4 * hf + f].y * sc;
+                  }
+                  st_global_v8(reinterpret_cast<float*>(dst) + 8 * hf, o);
+                }
               } else {
   #pragma unroll
                 for (int f = 0; f < FB; ++f)
