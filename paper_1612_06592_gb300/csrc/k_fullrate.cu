@@ -19,8 +19,9 @@
 // envelope |v| is compared with the stream's threshold and triggers are
 // compacted by warp ballots, as in the synthesis kernel; Re v is the stored
 // time series.  After the LSMR inversion (the paper's order) the filter reads
-// the recovered series (k_lsmr_rows lays it out sample-major) and writes v back
-// phase-major for the LSMR path's per-phase noise level and trigger.
+// the recovered series (k_lsmr writes it sample-major into the series rows)
+// and writes v back phase-major for the LSMR path's per-phase noise level and
+// trigger.
 //
 // The FFT: decimation in frequency, radices 16 x 16 x 16 x 2, in place in
 // shared memory.  A thread owns 16 values per pass (a 16-point DFT in
@@ -404,31 +405,6 @@ __global__ void k_fullrate_shift(float2* __restrict__ u, long long u_row, long l
   row[l] = row[FM + l];
 }
 
-// LSMR chain: the recovered series xhat[j][p][i] (phase-major) into the series
-// row of stream j, sample i M + p after the 2048 history samples; 32 x 32
-// tiles through shared memory (reads along frames, writes along phases).
-__global__ void __launch_bounds__(256) k_lsmr_rows(const float2* __restrict__ xhat, long long F,
-                                                   float2* __restrict__ u, long long u_row) {
-  __shared__ float2 tile[32][33];
-  const long long j = blockIdx.z;
-  const long long i0 = (long long)blockIdx.x * 32;            // frames
-  const int p0 = blockIdx.y * 32;                              // phases
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
-  const float2* src = xhat + j * kM * F;
-#pragma unroll
-  for (int q = 0; q < 32; q += 8) {
-    const long long i = i0 + tx;
-    tile[ty + q][tx] = i < F ? src[(long long)(p0 + ty + q) * F + i] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  float2* dst = u + j * u_row + kFrTaps;
-#pragma unroll
-  for (int q = 0; q < 32; q += 8) {
-    const long long i = i0 + ty + q;
-    if (i < F) dst[i * kM + p0 + tx] = tile[tx][ty + q];
-  }
-}
-
 // ---- set-up, FP64 ----------------------------------------------------------
 // E[m] = exp(+2 pi i m / N); H[m] = exp(-2 pi i phi(nu_m)) for m < N/2 (nu_m =
 // 100 MHz + m fs / N), 1 above; the FFT twiddle tables (as (c, s) pairs).
@@ -571,16 +547,6 @@ cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps) {
       k_fullrate<1><<<grid, FR_NT, FR_SMEM, s>>>(a);
     else
       k_fullrate<0><<<grid, FR_NT, FR_SMEM, s>>>(a);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_lsmr_rows(const lp_plan& p, cudaStream_t s) {
-  const long long F = p.shape.F;
-  for (long long j0 = 0; j0 < p.shape.J(); j0 += 65535) {
-    const unsigned nj = (unsigned)std::min<long long>(65535, p.shape.J() - j0);
-    k_lsmr_rows<<<dim3((unsigned)((F + 31) / 32), kM / 32, nj), 256, 0, s>>>(
-        p.buf.xhat + j0 * kM * F, F, p.buf.ufull + j0 * fullrate_row(p), fullrate_row(p));
   }
   return cudaGetLastError();
 }

@@ -46,9 +46,11 @@ __device__ __forceinline__ float warp_sum(float v) {
 __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restrict__ zt,
                                                         const double* __restrict__ proto,
                                                         const double* __restrict__ sums,
-                                                        long long nfr, long long F, int n_win,
+                                                        long long nfr, int n_win,
                                                         int iters, long long j0,
-                                                        float2* __restrict__ out) {
+                                                        float2* __restrict__ out,
+                                                        long long o_stream, long long o_phase,
+                                                        long long o_frame) {
   __shared__ float2 us[LS_WARPS][LS_PAD + LS_ROWS + LS_PAD + 16];
   __shared__ float2 vs[LS_WARPS][LS_COLS + LS_PAD + 16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -209,12 +211,13 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 3) k_lsmr(const float2* __restr
       }
     }
   }
-  // keep unknowns 15 .. 15 + W - 1: output frames w W .. w W + W - 1
-  const long long o = (j * kM + p) * F + (long long)w * LS_W;
+  // keep unknowns 15 .. 15 + W - 1: output frames w W .. w W + W - 1; frame i
+  // of phase p of stream j at out[j o_stream + p o_phase + i o_frame]
+  float2* ob = out + j * o_stream + (long long)p * o_phase + (long long)w * LS_W * o_frame;
 #pragma unroll
   for (int i = 0; i < LS_PER; ++i) {
     const int n = e0 + i;
-    if (n >= kTaps - 1 && n < kTaps - 1 + LS_W) out[o + n - (kTaps - 1)] = x[i];
+    if (n >= kTaps - 1 && n < kTaps - 1 + LS_W) ob[(long long)(n - (kTaps - 1)) * o_frame] = x[i];
   }
 }
 
@@ -308,12 +311,20 @@ cudaError_t launch_lsmr(const lp_plan& p, cudaStream_t s) {
   const long long J = sh.J();
   cudaError_t e = launch_ippf_zt(p, s);
   if (e != cudaSuccess) return e;
+  // the recovered series: phase-major (xhat, for the per-phase level and trigger),
+  // or, when the full-rate filter follows, straight into its sample-major series
+  // rows after the 2048 history samples
+  const bool rows = p.cfg.fullrate_dedisp != 0;
+  float2* out = rows ? p.buf.ufull + kFrTaps : p.buf.xhat;
+  const long long o_stream = rows ? fullrate_row(p) : kM * sh.F;
+  const long long o_phase = rows ? 1 : sh.F;
+  const long long o_frame = rows ? kM : 1;
   for (long long j0 = 0; j0 < J; j0 += 65535) {             // grid y is at most 65535
     const unsigned nj = (unsigned)std::min<long long>(65535, J - j0);
     const int n_win = (int)(sh.F / LS_W);
     k_lsmr<<<dim3((unsigned)(kM / LS_WARPS * n_win), nj), LS_WARPS * 32, 0, s>>>(
-        p.buf.zt, p.buf.proto, p.buf.filter_sums, nfr, sh.F, n_win, p.cfg.lsmr_iters, j0,
-        p.buf.xhat);
+        p.buf.zt, p.buf.proto, p.buf.filter_sums, nfr, n_win, p.cfg.lsmr_iters, j0, out,
+        o_stream, o_phase, o_frame);
   }
   return cudaGetLastError();
 }

@@ -699,7 +699,6 @@ lp_status process_inner(lp_plan* p, const void* x, int64_t pol_stride, void* str
       prof_mark(p, LP_STAGE_SYNTH, 1, s);
       if (p->cfg.fullrate_dedisp) {
         prof_mark(p, LP_STAGE_FULLRATE, 0, s);
-        if (e == cudaSuccess && lsmr) e = lp::launch_lsmr_rows(*p, s);
         if (e == cudaSuccess) e = lp::launch_fullrate(*p, s);
         if (e == cudaSuccess && lsmr) e = lp::launch_lsmr_trigger(*p, s);
         prof_mark(p, LP_STAGE_FULLRATE, 1, s);
@@ -977,8 +976,8 @@ int lp_launches_per_block(const lp_plan* p) {
   const int fine = p->cfg.fine_dedisp ? (int)((rows + 65534) / 65535) : 0;
   if (p->cfg.inversion == LP_INV_LSMR) {  // beamformer, inverse FFT, LSMR + trigger per
     const int nj = (int)((p->shape.J() + 65534) / 65535);   // 65535 streams, sigma, shift
-    // full-rate filter: the series rows and the filter (per 65535 streams), its history shift
-    return 4 + fine + 2 * nj + (p->cfg.fullrate_dedisp ? 1 + 2 * nj : 0);
+    // full-rate filter: the filter (per 65535 streams) and its history shift
+    return 4 + fine + 2 * nj + (p->cfg.fullrate_dedisp ? 1 + nj : 0);
   }
   // full-rate filter: one launch per 65535 streams, and its history shift
   const int nj = (int)((p->shape.J() + 65534) / 65535);

@@ -290,7 +290,6 @@ cudaError_t launch_fullrate_taps(const lp_plan& p, cudaStream_t s);
 cudaError_t launch_fullrate(const lp_plan& p, cudaStream_t s, PolSel ps = {});
 cudaError_t launch_fullrate_shift(const lp_plan& p, cudaStream_t s, PolSel ps = {});
 // LSMR chain: the recovered series into the full-rate filter's series rows
-cudaError_t launch_lsmr_rows(const lp_plan& p, cudaStream_t s);
 long long fullrate_row(const lp_plan& p);
 size_t fullrate_table_bytes();
 // PPF inversion by windowed LSMR (replaces the synthesis and the trigger)

@@ -226,12 +226,12 @@ def test_fullrate_options_validate_and_size_the_workspace(lib):
 def test_launch_counts_of_the_paths(lib):
     """lp_launches_per_block is host arithmetic: 4 kernels for a device block,
     one more with the fine filter, six with the LSMR inversion, two more with
-    the full-rate filter (three after the LSMR inversion: the series rows)."""
+    the full-rate filter (after the LSMR inversion too)."""
     for fields, want in [({}, 4), ({"fine_dedisp": 1}, 5),
                          ({"inversion": lib.LP_INV_LSMR}, 6),
                          ({"inversion": lib.LP_INV_LSMR, "fine_dedisp": 1}, 7),
                          ({"fullrate_dedisp": 1}, 6),
-                         ({"inversion": lib.LP_INV_LSMR, "fullrate_dedisp": 1}, 9)]:
+                         ({"inversion": lib.LP_INV_LSMR, "fullrate_dedisp": 1}, 8)]:
         st, h = _create(lib, 6, 2, 16, 2, 1, 512)
         c = lib.config_default()
         c.first_bin = 100

@@ -146,7 +146,7 @@ def test_lsmr_then_fullrate_matches_oracle(cuda_lib):
     tec = np.array([30.0])
     plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", inversion="lsmr",
                      fullrate_dedisp=True, k_sigma=ks)
-    assert plan.lp_launches_per_block() == 9
+    assert plan.lp_launches_per_block() == 8
     plan.lp_set_weights(enu, dirs)
     plan.lp_set_tec(tec)
     nu = O.sky_frequencies(fb, K)
