@@ -196,3 +196,41 @@ def test_lsmr_then_fullrate_matches_oracle(cuda_lib):
             assert abs(abs(vs[j, i, p]) - th) <= 10 * tol * th, (j, nn)
         n_oracle += len(want_trig)
     assert n_oracle > 0
+
+
+def test_lsmr_then_fullrate_host_input_and_graph_equal_device_input(cuda_lib):
+    """The paper's chain (LSMR, then the full-rate filter, whose series rows
+    k_lsmr writes directly) fed from pinned host blocks and replayed from a
+    captured graph gives the device block's results bit for bit, over two
+    blocks and two trials."""
+    import torch
+    S, P, K, B, Tr, F, fb = 8, 2, 12, 1, 2, 256, 200
+    blocks, enu, dirs, _ = random_case(44, S, P, K, B, Tr, F, fb, "int8", 2, amp=60)
+    tec = np.array([12.0, 31.0])
+    res = []
+    for mode in ("device", "host", "graph"):
+        stream = torch.cuda.Stream()
+        plan = make_plan(cuda_lib, S, P, K, B, Tr, F, fb, "int8", precision="fp16",
+                         inversion="lsmr", host_input=mode == "host", k_sigma=3.0,
+                         fullrate_dedisp=True, use_graph=mode == "graph", stream=stream)
+        plan.lp_set_weights(enu, dirs, stream=stream)
+        plan.lp_set_tec(tec, stream=stream)
+        xd = torch.empty((P, K, F, S, 2), dtype=torch.int8, device="cuda")
+        out = []
+        for xb in blocks:
+            if mode == "host":
+                plan.lp_process_block(torch.from_numpy(xb).pin_memory(), stream=stream)
+            else:
+                with torch.cuda.stream(stream):
+                    xd.copy_(torch.from_numpy(xb))
+                plan.lp_process_block(xd, stream=stream)
+            ys = [plan.lp_get_timeseries(b, t, pol)
+                  for b in range(B) for t in range(Tr) for pol in range(P)]
+            out.append((np.stack(ys), plan.lp_get_lsmr_sigma().copy(), plan.lp_get_triggers()[0]))
+        res.append(out)
+    assert any(len(t) for _, _, t in res[0])
+    for other in res[1:]:
+        for (ya, sa, ta), (yb, sb, tb) in zip(res[0], other):
+            np.testing.assert_array_equal(ya, yb)
+            np.testing.assert_array_equal(sa, sb)
+            np.testing.assert_array_equal(ta, tb)
