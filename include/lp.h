@@ -309,9 +309,11 @@ lp_status lp_plan_autotune_gemm(lp_plan* plan, const void* x, void* stream, int3
 /* Number of kernel launches lp_process_block makes for a device block (for
  * accounting): 4 (beamformer, noise level, synthesis, history shift), one more
  * with fine_dedisp, 6 with the LSMR inversion (beamformer, inverse FFT, LSMR,
- * noise level, trigger, history shift); the fine filter adds a launch and the
- * LSMR kernels three per 65535 rows / streams beyond the first.  A host block
- * processed per polarisation makes twice the FIR-path count. */
+ * noise level, trigger, history shift), two more with fullrate_dedisp (the
+ * filter and its history shift); the fine filter adds a launch, and the LSMR
+ * and trigger kernels, and the full-rate filter, one each per 65535 rows /
+ * streams beyond the first.  A host block processed per polarisation makes
+ * twice the FIR-path count. */
 int lp_launches_per_block(const lp_plan* plan);
 
 /* Stage timing.  When enabled, lp_process_block records a CUDA event pair
