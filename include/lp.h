@@ -337,8 +337,9 @@ lp_status lp_profile_read(lp_plan* plan, double* total_ms, int64_t* blocks);
  * LP_MAX_GROUP such plans: one beamformer launch over every plan's work items,
  * one noise-level launch (which also clears every plan's trigger counter), one
  * synthesis launch over every plan's streams and one history shift -- four
- * launches per block however many plans.  Each plan computes exactly what its
- * own lp_process_block computes, bit for bit.
+ * launches per block however many plans (four per polarisation with
+ * lp_group_process_block_pol).  Each plan computes exactly what its own
+ * lp_process_block computes, bit for bit.
  *
  * Member plans: bound, lp_set_weights and lp_set_tec done, the FP16 form,
  * whole blocks (chunk_frames 0), the FIR synthesis without fine
@@ -363,6 +364,15 @@ lp_status lp_group_create(lp_group** out, lp_plan* const* plans, int n);
  * read its results as after lp_process_block. */
 lp_status lp_group_process_block(lp_group* group, const void* x, int32_t subbands,
                                  int32_t first_bin, void* stream);
+
+/* The same block one polarisation at a time (pol = 0, then 1, ... for every
+ * block), four launches per call, with the layout and results of
+ * lp_group_process_block: only x's slab of polarisation `pol` is read, so a
+ * caller can launch a polarisation as soon as its slab has arrived.
+ * LP_ERR_ARG for pol outside [0, P); LP_ERR_STATE for a polarisation out of
+ * order, and for lp_group_process_block in the middle of a block. */
+lp_status lp_group_process_block_pol(lp_group* group, const void* x, int32_t subbands,
+                                     int32_t first_bin, int32_t pol, void* stream);
 
 /* Plans in the group; kernel launches per block (4). */
 int lp_group_size(const lp_group* group);

@@ -8,7 +8,9 @@
 // one beamformer launch (the work items of every plan in one persistent
 // grid), one noise-level launch (which also clears every plan's trigger
 // counter), one synthesis launch over every plan's streams and one history
-// shift: four launches per block whatever the number of plans.  Each plan's
+// shift: four launches per block whatever the number of plans (or four per
+// polarisation with lp_group_process_block_pol, so that the second
+// polarisation's copy can run under the first's kernels).  Each plan's
 // arithmetic is the one its own lp_process_block performs, in the same order,
 // so its results are bit for bit those it gives alone.
 #include <cstdarg>
@@ -23,6 +25,7 @@ struct lp_group {
   std::vector<lp_plan*> plans;
   int device = -1;
   long long blocks = 0;
+  int next_pol = 0;        // per-polarisation calls: the polarisation the block needs next
   std::string err;
 };
 
@@ -56,31 +59,12 @@ const char* incompatible(const lp_plan& p0, const lp_plan& q) {
   return nullptr;
 }
 
-}  // namespace
-
-extern "C" {
-
-lp_status lp_group_create(lp_group** out, lp_plan* const* plans, int n) {
-  if (!out) return LP_ERR_ARG;
-  *out = nullptr;
-  if (!plans || n < 1 || n > lp::kMaxGroup) return LP_ERR_ARG;
-  for (int i = 0; i < n; ++i) {
-    if (!plans[i]) return LP_ERR_ARG;
-    for (int k = 0; k < i; ++k)
-      if (plans[k] == plans[i]) return LP_ERR_ARG;       // a plan appears once
-    if (incompatible(*plans[0], *plans[i])) return LP_ERR_STATE;
-  }
-  lp_group* g = new (std::nothrow) lp_group;
-  if (!g) return LP_ERR_OOM;
-  g->plans.assign(plans, plans + n);
-  g->device = plans[0]->device;
-  *out = g;
-  return LP_OK;
-}
-
-lp_status lp_group_process_block(lp_group* g, const void* x, int32_t subbands,
-                                 int32_t first_bin, void* stream) {
-  if (!g) return LP_ERR_ARG;
+// The block (ps: all polarisations) or one polarisation of it, for every plan:
+// the noise-level launch of the first polarisation clears the trigger
+// counters, and the history shift advances the block counters once ps reaches
+// the last polarisation.
+lp_status group_block(lp_group* g, const void* x, int32_t subbands, int32_t first_bin,
+                      lp::PolSel ps, void* stream) {
   if (!x) return gfail(g, LP_ERR_ARG, "null input");
   const lp_plan& p0 = *g->plans[0];
   const auto& sh = p0.shape;
@@ -119,17 +103,62 @@ lp_status lp_group_process_block(lp_group* g, const void* x, int32_t subbands,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   lp::Chunk c;
   c.nf = sh.F;
-  e = lp::launch_beamform_tc_plans(cp.data(), xs.data(), pol_stride, n, c, s);
-  if (e == cudaSuccess) e = lp::launch_sigma_plans(cp.data(), n, true, s);
-  if (e == cudaSuccess) e = lp::launch_ippf_plans(cp.data(), n, c, s);
-  if (e == cudaSuccess) e = lp::launch_history_shift_plans(cp.data(), n, c, s);
+  const bool first = ps.pol0 == 0;
+  const bool last = ps.npol == 0 || ps.pol0 + ps.npol == sh.P;
+  e = lp::launch_beamform_tc_plans(cp.data(), xs.data(), pol_stride, n, c, s, ps);
+  if (e == cudaSuccess) e = lp::launch_sigma_plans(cp.data(), n, first, s, ps);
+  if (e == cudaSuccess) e = lp::launch_ippf_plans(cp.data(), n, c, s, ps);
+  if (e == cudaSuccess) e = lp::launch_history_shift_plans(cp.data(), n, c, s, ps);
   if (e != cudaSuccess) return gfail(g, LP_ERR_CUDA, "%s", cudaGetErrorString(e));
-  for (lp_plan* p : g->plans) {
-    p->last_stream = s;
-    p->block_index += 1;
+  for (lp_plan* p : g->plans) p->last_stream = s;
+  if (last) {
+    for (lp_plan* p : g->plans) p->block_index += 1;
+    g->blocks += 1;
   }
-  g->blocks += 1;
   return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_group_create(lp_group** out, lp_plan* const* plans, int n) {
+  if (!out) return LP_ERR_ARG;
+  *out = nullptr;
+  if (!plans || n < 1 || n > lp::kMaxGroup) return LP_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) return LP_ERR_ARG;
+    for (int k = 0; k < i; ++k)
+      if (plans[k] == plans[i]) return LP_ERR_ARG;       // a plan appears once
+    if (incompatible(*plans[0], *plans[i])) return LP_ERR_STATE;
+  }
+  lp_group* g = new (std::nothrow) lp_group;
+  if (!g) return LP_ERR_OOM;
+  g->plans.assign(plans, plans + n);
+  g->device = plans[0]->device;
+  *out = g;
+  return LP_OK;
+}
+
+lp_status lp_group_process_block(lp_group* g, const void* x, int32_t subbands,
+                                 int32_t first_bin, void* stream) {
+  if (!g) return LP_ERR_ARG;
+  if (g->next_pol != 0)
+    return gfail(g, LP_ERR_STATE, "the block's polarisation %d has not been processed",
+                 g->next_pol);
+  return group_block(g, x, subbands, first_bin, lp::PolSel{}, stream);
+}
+
+lp_status lp_group_process_block_pol(lp_group* g, const void* x, int32_t subbands,
+                                     int32_t first_bin, int32_t pol, void* stream) {
+  if (!g) return LP_ERR_ARG;
+  const int P = g->plans[0]->shape.P;
+  if (pol < 0 || pol >= P) return gfail(g, LP_ERR_ARG, "polarisation %d outside [0, %d)", pol, P);
+  if (pol != g->next_pol)
+    return gfail(g, LP_ERR_STATE, "polarisation %d expected, %d given", g->next_pol, pol);
+  const lp_status st = group_block(g, x, subbands, first_bin, lp::PolSel{pol, 1}, stream);
+  if (st == LP_OK) g->next_pol = (pol + 1) % P;
+  return st;
 }
 
 int lp_group_size(const lp_group* g) { return g ? (int)g->plans.size() : 0; }

@@ -110,6 +110,8 @@ SIGNATURES = {
     "lp_prebeam_destroy": (None, [_P]),
     "lp_group_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
     "lp_group_process_block": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "lp_group_process_block_pol": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.c_int32, _P]),
     "lp_group_size": (ctypes.c_int, [_P]),
     "lp_group_launches_per_block": (ctypes.c_int, [_P]),
     "lp_group_last_error": (ctypes.c_char_p, [_P]),
@@ -405,6 +407,15 @@ class Group:
                                           _stream_ptr(stream))
         if st != LP_OK:
             raise LPError(st, "lp_group_process_block: " + _lib.lp_group_last_error(self._h).decode())
+
+    def lp_group_process_block_pol(self, x, subbands, first_bin, pol, stream=None):
+        """One polarisation of the block (pol 0, then 1, ...): the same layout and
+        results as lp_group_process_block; only polarisation pol's slab is read."""
+        st = _lib.lp_group_process_block_pol(self._h, _ptr(x), int(subbands), int(first_bin),
+                                             int(pol), _stream_ptr(stream))
+        if st != LP_OK:
+            raise LPError(st, "lp_group_process_block_pol: " +
+                          _lib.lp_group_last_error(self._h).decode())
 
     def lp_group_launches_per_block(self):
         return _lib.lp_group_launches_per_block(self._h)

@@ -9,11 +9,12 @@ noise level stay on the device between blocks).
 
 Per block: the block is copied once from pinned host memory into a device
 buffer shared by all sessions.  Batched (the default, FP16 form): the active
-sessions' plans form a group (lp_group) and the whole block runs as four
-launches -- one beamformer over every session's beams and subbands, one noise
-level, one synthesis over every session's streams, one history shift --
-however many sessions there are; each session reads its own subband range of
-the buffer.  Unbatched (FP32 form, or batch=False): every session launches its
+sessions' plans form a group (lp_group) and each polarisation of the block
+runs as four launches -- one beamformer over every session's beams and
+subbands, one noise level, one synthesis over every session's streams, one
+history shift -- however many sessions there are, as soon as its slab is on
+the device (the other slab's copy runs under them); each session reads its
+own subband range of the buffer.  Unbatched (FP32 form, or batch=False): every session launches its
 own pipeline on its own CUDA stream and sessions overlap on the device.  Each
 session's triggers come back to the host.  Requests that arrive wait in a
 queue and are admitted at a block boundary as soon as their workspace fits in
@@ -299,18 +300,26 @@ class Server:
         triggers are on the host.  host_block: pinned uint8/int8 tensor to copy
         in first (the block's arrival), or None if the buffer is already filled."""
         torch = self.torch
-        ready = torch.cuda.Event(enable_timing=True)
+        # one event per polarisation slab: batched launches start on a slab as
+        # soon as it is on the device (the next slab's copy runs under them)
+        pol_ready = [torch.cuda.Event(enable_timing=True) for _ in range(self.P)]
+        ready = pol_ready[-1]
         start = torch.cuda.Event(enable_timing=True)
         if host_block is not None:
+            hb = host_block.view(torch.int8)
+            n = self.block_dev.numel() // self.P
             with torch.cuda.stream(self.copy_stream):
                 start.record(self.copy_stream)
-                self.block_dev.copy_(host_block.view(torch.int8), non_blocking=True)
-                ready.record(self.copy_stream)
+                for pol in range(self.P):
+                    self.block_dev[pol * n:(pol + 1) * n].copy_(hb[pol * n:(pol + 1) * n],
+                                                                non_blocking=True)
+                    pol_ready[pol].record(self.copy_stream)
         else:
             start.record(torch.cuda.current_stream(self.device))
-            ready.record(torch.cuda.current_stream(self.device))
+            for ev in pol_ready:
+                ev.record(torch.cuda.current_stream(self.device))
         if self.batch:
-            self._run_groups(ready)
+            self._run_groups(pol_ready)
         else:
             pol_stride = self.n_sub * self.F * self.S           # complex samples
             for s in self.active.values():
@@ -336,9 +345,10 @@ class Server:
             g.close()
         self.groups, self.group_key = [], None
 
-    def _run_groups(self, ready):
+    def _run_groups(self, pol_ready):
         """One block for every active session in shared launches: the sessions'
-        plans (in admission order) form groups of at most LP_MAX_GROUP plans."""
+        plans (in admission order) form groups of at most LP_MAX_GROUP plans,
+        run one polarisation at a time, each once its slab has arrived."""
         key = tuple(self.active)
         if key != self.group_key:
             self._drop_groups()
@@ -346,10 +356,12 @@ class Server:
             self.groups = [lp.Group(plans[i:i + lp.LP_MAX_GROUP])
                            for i in range(0, len(plans), lp.LP_MAX_GROUP)]
             self.group_key = key
-        self.stream.wait_event(ready)
-        for g in self.groups:
-            g.lp_group_process_block(self.block_dev, self.n_sub, self.fb0, stream=self.stream)
-        self.launches.append(sum(g.lp_group_launches_per_block() for g in self.groups))
+        for pol, ev in enumerate(pol_ready):
+            self.stream.wait_event(ev)
+            for g in self.groups:
+                g.lp_group_process_block_pol(self.block_dev, self.n_sub, self.fb0, pol,
+                                             stream=self.stream)
+        self.launches.append(self.P * sum(g.lp_group_launches_per_block() for g in self.groups))
 
     def calibrate(self, shapes=((1, 122, 1), (8, 488, 2), (16, 244, 1), (40, 488, 1),
                                 (2, 488, 4), (24, 160, 3)), reps=3):

@@ -71,6 +71,48 @@ def test_group_equals_plans_alone(cuda_lib):
     grp.close()
 
 
+def test_group_per_polarisation_equals_whole_block(cuda_lib):
+    """A block run one polarisation at a time (pol 0, then pol 1) gives every
+    plan's series, noise level and triggers of the whole-block call, bit for
+    bit, over three blocks; polarisations out of order, out of range, or a
+    whole-block call between them are refused."""
+    import torch
+    lp = cuda_lib
+    S, F, n_sub, fb0 = 8, 264, 30, 140
+    grid = synth.hex_beam_directions(5)
+    enu = synth.station_positions(S, 4)
+    rng = np.random.default_rng(72)
+    blocks = [rng.integers(-90, 91, size=(2, n_sub, F, S, 2)).astype(np.int8) for _ in range(3)]
+    shapes = [(np.array([0, 3]), 2, 18, [9.0]), (np.array([1, 2, 4]), 0, 30, [6.0, 25.0])]
+    stream = torch.cuda.Stream()
+    whole = lp.Group(_plans(lp, S, F, n_sub, fb0, enu, grid, shapes, stream))
+    split = lp.Group(_plans(lp, S, F, n_sub, fb0, enu, grid, shapes, stream))
+    xd = torch.empty((2, n_sub, F, S, 2), dtype=torch.int8, device="cuda")
+    with pytest.raises(lp.LPError):
+        split.lp_group_process_block_pol(xd, n_sub, fb0, 1, stream=stream)   # pol 0 first
+    with pytest.raises(lp.LPError):
+        split.lp_group_process_block_pol(xd, n_sub, fb0, 2, stream=stream)   # no pol 2
+    n_trig = 0
+    for i, xb in enumerate(blocks):
+        with torch.cuda.stream(stream):
+            xd.copy_(torch.from_numpy(xb))
+        whole.lp_group_process_block(xd, n_sub, fb0, stream=stream)
+        split.lp_group_process_block_pol(xd, n_sub, fb0, 0, stream=stream)
+        if i == 0:
+            with pytest.raises(lp.LPError):      # the block's pol 1 is still due
+                split.lp_group_process_block(xd, n_sub, fb0, stream=stream)
+        split.lp_group_process_block_pol(xd, n_sub, fb0, 1, stream=stream)
+        for pw, ps in zip(whole.plans, split.plans):
+            (yw, sw, tw), (ys, ss, ts) = _outputs(pw), _outputs(ps)
+            np.testing.assert_array_equal(yw, ys)
+            np.testing.assert_array_equal(sw, ss)
+            np.testing.assert_array_equal(tw, ts)
+            n_trig += len(tw)
+    assert n_trig > 50
+    whole.close()
+    split.close()
+
+
 def test_group_refuses_plans_it_cannot_fuse(cuda_lib):
     lp = cuda_lib
     S, F, fb = 8, 256, 150

@@ -112,10 +112,10 @@ def test_serving_results_identical_alone_and_in_the_mix(cuda_lib):
 
 
 def test_batched_serving_equals_unbatched_and_launches_do_not_grow(cuda_lib):
-    """The batched server (all sessions in four shared launches per block) gives
-    each request exactly the results of the unbatched one (each session its own
-    launches on its own stream); its launch count per block stays 4 while the
-    unbatched count grows with the sessions."""
+    """The batched server (all sessions in four shared launches per polarisation
+    of a block) gives each request exactly the results of the unbatched one (each
+    session its own launches on its own stream); its launch count per block stays
+    8 while the unbatched count grows with the sessions."""
     from paper_1612_06592_gb300.serve import Request, Server
     S, F, n_sub, fb0 = 8, 256, 40, 150
     grid = synth.hex_beam_directions(6)
@@ -143,7 +143,7 @@ def test_batched_serving_equals_unbatched_and_launches_do_not_grow(cuda_lib):
             srv.submit(Request(100 + k, np.array([k % 6]), 0, 20, np.array([10.0]), 0, 10))
             srv.admit()
         srv.run_block(h)
-    assert srv.launches == [4, 4, 4]
+    assert srv.launches == [8, 8, 8]
 
 
 def test_serving_calibration_fits_the_timed_blocks(cuda_lib):
