@@ -370,7 +370,8 @@ lp_status lp_group_process_block(lp_group* group, const void* x, int32_t subband
  * lp_group_process_block: only x's slab of polarisation `pol` is read, so a
  * caller can launch a polarisation as soon as its slab has arrived.
  * LP_ERR_ARG for pol outside [0, P); LP_ERR_STATE for a polarisation out of
- * order, and for lp_group_process_block in the middle of a block. */
+ * order, and for lp_group_process_block in the middle of a block.  A call that
+ * fails leaves the group expecting the same polarisation again. */
 lp_status lp_group_process_block_pol(lp_group* group, const void* x, int32_t subbands,
                                      int32_t first_bin, int32_t pol, void* stream);
 
